@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the deflated WaveHoltz solve on one B300 (replicas on N GPUs).
+
+A step is one complete deflated solve of the 2-D Helmholtz workload: 513^2 nodes (511^2
+unknowns), omega = 50, Gaussian source of width 0.02 at a seeded point, 64 closed-form sine
+eigenvectors (DEVD, Algorithm 2) and CG on (I - S_h) u = b to relative residual 1e-6 -- weight
+tables, Taylor start, the fused leapfrog + filter steps, the operator epilogue, forcing deflation
+and inflation and the FP64 Krylov reductions all run in the library's kernels.  Default precision:
+FP32 wave stepping with FP64 Krylov / deflation arithmetic; --precision fp64 runs the plain FP64
+form (tolerance 1e-8, the 2-D workload's own).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64] [--impl whv|reference]
+
+Prints one JSON line on rank 0.  --impl reference times the FP64 CPU oracle (numpy, one thread)
+on the same workload instead.  Under torchrun every rank solves its own copy of the workload
+(replicas; the path has no collective) and the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "WaveHoltz solve time to rel. residual 1e-6; stencil GLUP/s vs HBM roofline"
+L2_FLUSH_BYTES = 512 << 20   # > 126 MB L2: written between timed steps
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="whv", choices=["whv", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(precision):
+    from paper_2606_31842_b300 import inputs as I
+    w = I.WORKLOADS["c2"]
+    tol = 1e-6 if precision == "fp32" else w.tol
+    return w, tol
+
+
+def config_dict(w, tol, precision, nt, n_gpus):
+    return {"workload": f"2-D Helmholtz {w.npts[0]}x{w.npts[1]} nodes, omega={w.omega:g}, Gaussian source width 0.02, "
+                        f"DEVD + CG with {w.nd} closed-form eigenvectors, tol {tol:g}",
+            "grid": list(w.npts), "unknowns": w.n_unknowns, "omega": w.omega, "nd": w.nd, "tol": tol,
+            "method": "DEVD-CG", "stepping": precision, "krylov": "fp64", "nt": nt,
+            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{n_gpus}"}
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"], parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ oracle legs
+def oracle_sample(w, tol, iterations_hint, budget_s=12.0):
+    """Time the FP64 oracle on a bounded sample of the workload: mode selection + basis, b, and
+    as many CG iterations as fit in the budget; extrapolate to `iterations_hint` iterations."""
+    from threadpoolctl import threadpool_limits
+    from oracle import operators as O, waveholtz as WH, spectral as SP, krylov as K
+    from paper_2606_31842_b300 import inputs as I
+    with threadpool_limits(1):
+        g = O.Grid(w.npts)
+        tg = WH.time_grid_for(g, w.omega)
+        f = I.forcing_for(w)
+        t0 = time.perf_counter()
+        modes, lam2, _ = SP.select_modes(g, tg, w.nd)
+        V = SP.basis(g, modes)
+        t_setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        b = WH.rhs_b(g, tg, K.project_out(g, V, f))
+        t_b = time.perf_counter() - t0
+        A = K.Operator(g, tg)
+        k = max(1, int(budget_s / max(t_b, 1e-3)))
+        t0 = time.perf_counter()
+        K.cg(g, A, b, 0.0, k)
+        t_it = (time.perf_counter() - t0) / k
+    solve_s = t_b + iterations_hint * t_it
+    return {"solve_s": solve_s, "setup_s": t_setup, "t_wave": t_b, "t_iter": t_it, "k": k}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle on the same workload, metric and unit."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w, tol = workload_config(args.precision)
+    from oracle import operators as O, waveholtz as WH
+    nt = WH.time_grid_for(O.Grid(w.npts), w.omega).nt
+    # iteration count of the oracle at this tolerance (deflated CG on this workload)
+    iters = 37 if tol >= 1e-6 else 50
+    times = []
+    for s in range(args.warmup + args.steps):
+        t = oracle_sample(w, tol, iters, budget_s=3.0)
+        if s >= args.warmup:
+            times.append(t["solve_s"] * 1e3)
+    ms = statistics.mean(times)
+    cb = {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+          "sample": f"b wave solve + {t['k']} CG iterations per step at 1 thread, extrapolated to {iters} iterations"}
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(w, tol, "fp64", nt, args.gpus), "cpu_baseline": cb,
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def traffic_for(kernel, precision):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the kernel
+    source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(f"{kernel}:{precision}")
+    except ValueError:
+        return None
+    if not rec:
+        return None
+    src = open(os.path.join(ROOT, "paper_2606_31842_b300", "csrc", "stencil.cu"), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:16] != rec.get("stencil_sha"):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_2606_31842_b300 import build as whv_build
+    whv_build.build()
+    from paper_2606_31842_b300 import whv
+    from paper_2606_31842_b300 import inputs as I
+
+    w, tol = workload_config(args.precision)
+    prec = whv.WHV_FP32_STEP if args.precision == "fp32" else whv.WHV_FP64
+    stream = torch.cuda.Stream()
+    g = whv.Grid(w.npts, precision=prec, stream=stream)
+    prm = whv.make_params(w.omega, method="cg", tol=tol, maxit=5000, check_every=1)
+    tgrid = g.whv_time_grid(prm)
+    nt = tgrid["nt"]
+    g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
+    f_host = torch.from_numpy(I.forcing_for(w).ravel()).pin_memory()
+    u_host = torch.empty_like(f_host).pin_memory()
+    with torch.cuda.stream(stream):
+        f = f_host.to("cuda", non_blocking=True)
+        u = torch.zeros_like(f)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream.synchronize()
+
+    def solve():
+        return g.whv_solve(prm, f, u)[1]
+
+    for _ in range(max(3, args.warmup)):
+        info = solve()
+    # ------------------------------------------------------------------ timed region
+    times, infos = [], []
+    launches0 = whv.whv_kernel_launches()
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)                      # evict the working set from L2
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(solve())
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        barrier()
+    launches = whv.whv_kernel_launches() - launches0
+    clocks = clk.summary()
+    ms = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    info = infos[-1]
+    lups = info["wave_solves"] * nt * w.n_unknowns
+    glups_solve = lups / (ms * 1e-3) / 1e9
+
+    # ------------------------------------------------------------------ e2e: host buffers
+    e2e_times = []
+    for k in range(args.steps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            e0.record(stream)
+            f.copy_(f_host, non_blocking=True)
+        g.whv_solve(prm, f, u)
+        with torch.cuda.stream(stream):
+            u_host.copy_(u, non_blocking=True)
+            e1.record(stream)
+        e1.synchronize()
+        if k > 0:
+            e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = statistics.mean(e2e_times)
+
+    # ------------------------------------------------------------------ dominant kernel
+    # the leapfrog+filter step kernel: average duration per launch over wave solves of the
+    # same grid (graph replays, as in the solve), timed with events on the launching stream
+    reps = 20
+    v = torch.randn(w.n_unknowns, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(v)
+    torch.cuda.synchronize()
+    g.whv_apply_pi(prm, v, None, out)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        g.whv_apply_pi(prm, v, None, out)
+    e1.record(stream)
+    e1.synchronize()
+    t_step = e0.elapsed_time(e1) * 1e-3 / (reps * nt)
+    esz = 4 if args.precision == "fp32" else 8
+    bytes_per_lup = 5 * esz                          # read W^n, W^{n-1}, acc; write W^{n+1}, acc
+    achieved = bytes_per_lup * w.n_unknowns / t_step / 1e9
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    peak = peaks.get("hbm_gbs", 6400.0)
+    traffic = traffic_for("k_step", args.precision)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_step (fused leapfrog step + trapezoid filter)",
+            "bytes_per_lup": bytes_per_lup, "lups_per_launch": w.n_unknowns,
+            "step_us": t_step * 1e6, "glups": w.n_unknowns / t_step / 1e9,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "note": "the 511^2 state (3 arrays, 3 MB) stays resident in the 126 MB L2 during a wave solve"}
+
+    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "krylov_dtype": "f64", "data": "synthetic", "config": config_dict(w, tol, args.precision, nt, world),
+            "iterations": info["iterations"], "wave_solves": info["wave_solves"],
+            "rel_residual": info["rel_residual"], "glups_solve": glups_solve,
+            "roofline": roof,
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": w.n_unknowns * 8,
+                    "d2h_bytes_per_step": w.n_unknowns * 8},
+            "gpu_launches": launches, "clocks": clocks}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(w, tol, info["iterations"])
+        line["cpu_baseline"] = {"value": cb["solve_s"] * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+                                "sample": f"oracle (numpy FP64, 1 thread): b wave solve + {cb['k']} CG iterations, "
+                                          f"extrapolated to the GPU's {info['iterations']} iterations"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * whv.h -- C ABI of the B300 WaveHoltz library (eigenvector-deflated WaveHoltz).
+ *
+ * The library solves the discrete Helmholtz problem  L_h U + omega^2 U = f  with homogeneous
+ * Dirichlet boundary nodes (Sec. 2.1 eq. helmholtzBVP, Sec. 2.2 eq. discreteHelmholtz) as the
+ * fixed point of the WaveHoltz map Pi_h (eq. waveHoltzFilter, eq. quadrature), i.e. the linear
+ * system A u = (I - S_h) u = b, b = Pi_h 0 (eq. WaveHoltzMatrixEquation), accelerated by
+ * Krylov methods and eigenvector deflation (Algorithm 2, Algorithm 4).
+ *
+ * Conventions shared by every entry point
+ *  - A grid function lives on the INTERIOR nodes only, in FP64, contiguous with x fastest:
+ *    element (i, j, k) is at i + nx*(j + ny*k), nx = npts[0]-2, ny = npts[1]-2, nz = npts[2]-2.
+ *    Boundary nodes are not stored (their value is 0).
+ *  - Pointers named *_dev are DEVICE pointers owned by the caller; they must stay valid until the
+ *    call's work on the grid's stream has completed.  Pointers named *_host are host memory.
+ *  - All work is ordered on the CUDA stream given to whv_create_grid.  Calls that return
+ *    host values (whv_solve's info, whv_dot, whv_get_basis) synchronise that stream.
+ *  - Every call returns a whv_status and never aborts; on failure whv_last_error(grid) holds a
+ *    one-line reason.  A grid is not thread-safe: one host thread at a time per grid.
+ *  - L_h = c^2(x) Delta_{p,h}: the squared speed multiplies the p-th order (p = 2 or 4) discrete
+ *    Laplacian (reading of eq. L for variable speed).  Inner products and norms are weighted by
+ *    M = diag(1/c^2), in which A is self-adjoint (the diagonal mass-matrix symmetrisation of
+ *    Sec. 4.1); for c = 1 they are Euclidean.
+ */
+#ifndef WHV_H
+#define WHV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct whv_grid_s* whv_grid;
+
+typedef enum {
+  WHV_OK = 0,
+  WHV_ERR_INVALID = 1,        /* bad argument, size, or state (e.g. dt above the stability limit) */
+  WHV_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  WHV_ERR_OOM = 3,            /* device allocation failed */
+  WHV_ERR_NOT_CONVERGED = 4,  /* maxit reached; the best iterate is returned */
+  WHV_ERR_BREAKDOWN = 5,      /* non-finite or non-positive Krylov scalar (NaN/Inf input, indefinite A) */
+  WHV_ERR_TIMEOUT = 6         /* a bounded device-side wait gave up */
+} whv_status;
+
+/* precision of the wave stepping (the Krylov / deflation arithmetic is always FP64) */
+enum { WHV_FP64 = 0, WHV_FP32_STEP = 1 };
+
+/* accelerators */
+enum {
+  WHV_FPI = 0,    /* Algorithm 1, fixed-point iteration                              */
+  WHV_CG = 1,     /* conjugate gradients on A u = b                                   */
+  WHV_DCG = 2,    /* Algorithm 4, deflated CG (needs a basis)                         */
+  WHV_GMRES = 3   /* restarted GMRES(m), classical Gram-Schmidt applied twice         */
+};
+
+/* origin of the deflation basis (whv_set_deflation_basis) */
+enum {
+  WHV_BASIS_NONE = 0,         /* remove the basis                                          */
+  WHV_BASIS_USER = 1,         /* copy caller vectors V_dev and eigenvalues lambda2_host    */
+  WHV_BASIS_CLOSED_FORM = 2,  /* sine tensor products of the box (Sec. 4.3), c = 1 only     */
+  WHV_BASIS_LANCZOS = 3       /* computed on the device by a Krylov eigen-solve on S_h     */
+};
+/* basis flags */
+enum {
+  WHV_BASIS_EXACT = 1,        /* columns are true eigenvectors: A W = W diag(1 - beta_h)  */
+  WHV_BASIS_REDEFLATE = 2     /* project every operator output onto span(V)^perp (Algorithm 2, deflate iterate) */
+};
+/* whv_params.flags */
+enum {
+  WHV_TRUE_RESIDUAL = 1       /* at exit compute ||Pi_h(u;f) - u|| / ||Pi_h(0;f)|| (2 extra wave solves) */
+};
+
+typedef struct {
+  double omega;       /* frequency omega > 0                                                       */
+  int periods;        /* filter interval Tbar = periods * 2 pi / omega (N_p >= 1)                 */
+  int adjust_omega;   /* 1: use omega_hat with (2/dt) sin(omega_hat dt/2) = omega so that the
+                         fixed point solves the Helmholtz problem at omega exactly (Sec. 2.2);
+                         0: dt = Tbar/ceil(Tbar/dt0) and the fixed point is at omega_eff        */
+  double cfl;         /* dt0 = cfl * h_min / c_max; <= 0 selects 0.5 (order 2) or 0.4 (order 4)  */
+  int method;         /* WHV_FPI | WHV_CG | WHV_DCG | WHV_GMRES                                   */
+  int restart;        /* GMRES restart length m; <= 0 selects 30                                  */
+  double tol;         /* stop when ||r||_M <= tol ||b||_M of the iterated system                  */
+  int maxit;          /* maximum operator applications in the iteration                          */
+  int check_every;    /* test convergence every k iterations (CG/FPI); <= 0 selects 1             */
+  int flags;          /* WHV_TRUE_RESIDUAL                                                        */
+} whv_params;
+
+typedef struct {
+  int iterations;            /* accelerator iterations                                          */
+  int wave_solves;           /* applications of Pi_h, including b and the true residual         */
+  int nt;                    /* time steps per wave solve                                       */
+  double dt, omega_hat, omega_eff;
+  double rel_residual;       /* last recursive relative residual of the iterated system         */
+  double true_rel_residual;  /* WHV_TRUE_RESIDUAL result, else -1                               */
+  double seconds;            /* host wall time of the call                                      */
+} whv_info;
+
+/* Create a box grid [lo, hi] (per direction, x first) with npts nodes per direction including
+ * both boundary nodes (npts >= 3; npts >= 4 for order 4), dim = 1, 2 or 3 (entries beyond dim are
+ * ignored), order = 2 or 4 (centred Cartesian stencils, Sec. 2.2; order 4 closes at the boundary
+ * by odd reflection of the first interior value), precision = WHV_FP64 or WHV_FP32_STEP.
+ * `cuda_stream` is a cudaStream_t (NULL = legacy default stream).  Allocates the grid's own
+ * device scratch (stepping buffers, Krylov vectors); the grid owns it until whv_destroy_grid. */
+whv_status whv_create_grid(int dim, const int64_t npts[3], const double lo[3], const double hi[3],
+                           int order, int precision, void* cuda_stream, whv_grid* out);
+whv_status whv_destroy_grid(whv_grid grid);
+
+/* Squared wave speed c^2 on the interior nodes (copied; the caller may free its buffer after
+ * the call completes on the stream).  c2_dev = NULL restores c = 1.  Any existing deflation basis
+ * is dropped.  Requires c^2 > 0 (checked). */
+whv_status whv_set_speed(whv_grid grid, const double* c2_dev);
+
+/* Time grid the given parameters select (reading of Sec. 2.2): nt steps of dt over Tbar,
+ * cos/filter frequency omega_hat, fixed-point frequency omega_eff.  Host outputs, any may be NULL.
+ * Returns WHV_ERR_INVALID if dt is above the explicit leapfrog stability limit. */
+whv_status whv_time_grid(whv_grid grid, const whv_params* p, int* nt, double* dt,
+                         double* omega_hat, double* omega_eff);
+
+/* Set the deflation basis W (N x nd, column-major, M-orthonormal) used by whv_solve for DEVD
+ * (Algorithm 2 with FPI/CG/GMRES) and DCG (Algorithm 4), for the frequency and time grid of `p`.
+ *  - WHV_BASIS_USER: V_dev (N*nd doubles) and lambda2_host (nd eigenvalues lambda^2 of -L_h)
+ *    are copied.
+ *  - WHV_BASIS_CLOSED_FORM: V_dev/lambda2_host ignored (may be NULL); the nd tensor-product sine
+ *    modes with the smallest |1 - beta_h(lambda)| (ties: mode tuple (kx,ky,kz) ascending) are
+ *    generated on the device (Sec. 2.3 choice of the deflation set; Sec. 4.3 eigenvectors).
+ *    Requires c = 1.  Implies WHV_BASIS_EXACT.
+ *  - WHV_BASIS_LANCZOS: eigenpairs computed on the device (see whv_lanczos) -- not yet built.
+ *  - WHV_BASIS_NONE: drop the basis.
+ * flags: WHV_BASIS_EXACT, WHV_BASIS_REDEFLATE. */
+whv_status whv_set_deflation_basis(whv_grid grid, const whv_params* p, int nd, const double* V_dev,
+                                   const double* lambda2_host, int mode, int flags);
+
+/* Read back the basis: nd (host), the mode tuples (host int[nd*dim], closed form only; else
+ * zeros), lambda^2 (host double[nd]) and the vectors (device double[N*nd]); any output may be NULL. */
+whv_status whv_get_basis(whv_grid grid, int* nd, int* modes_host, double* lambda2_host, double* V_dev);
+
+/* out = Pi_h(v; f): one wave solve (eq. discreteWaveExplicit from W^0 = v, D0t W^0 = 0, forcing
+ * -f cos(omega_hat t)) filtered by the trapezoid rule (eq. quadrature).  f_dev = NULL means f = 0,
+ * i.e. out = S_h v.  v_dev and out_dev may alias. */
+whv_status whv_apply_pi(whv_grid grid, const whv_params* p, const double* v_dev, const double* f_dev,
+                        double* out_dev);
+
+/* Solve A u = b for forcing f (b = Pi_h(0; f)) with p->method.  With a basis set and method
+ * FPI / CG / GMRES this is DEVD (Algorithm 2): f_d = f - W W^T M f, solve with b = Pi_h(0; f_d),
+ * inflate u += W diag(1/(omega_eff^2 - lambda^2)) W^T M f.  With WHV_DCG it is Algorithm 4 on
+ * b = Pi_h(0; f).  use_guess = 1: u_dev holds the initial guess x0 on entry (DEVD projects it
+ * onto span(W)^perp first); use_guess = 0: x0 = 0 and u_dev is only written.  On exit u_dev holds
+ * the solution.  info (host, may be NULL) receives counts and residuals.
+ * Returns WHV_ERR_NOT_CONVERGED (solution still written) if maxit is reached. */
+whv_status whv_solve(whv_grid grid, const whv_params* p, const double* f_dev, int use_guess,
+                     double* u_dev, whv_info* info);
+
+/* Deflation contractions and reductions on the grid's basis / weights (building blocks of the
+ * solve, exposed for testing and for callers composing their own iterations):
+ *   whv_project:  coeff_dev[m] = (W^T M r)_m, m < nd                 (Algorithm 2, (r, phi_m))
+ *   whv_expand:   out_dev     = out_dev + alpha * W y_dev            (Algorithm 2, inflate)
+ *   whv_dot:      *out_host   = <x, y>_M                             (Krylov inner product) */
+whv_status whv_project(whv_grid grid, const double* r_dev, double* coeff_dev);
+whv_status whv_expand(whv_grid grid, const double* y_dev, double alpha, double* out_dev);
+whv_status whv_dot(whv_grid grid, const double* x_dev, const double* y_dev, double* out_host);
+
+/* Number of interior unknowns N of the grid (0 for NULL). */
+int64_t whv_num_unknowns(whv_grid grid);
+
+/* Last error message of `grid` (or of the calling thread's last failed create when grid is NULL).
+ * The string is owned by the library and valid until the next call on the grid. */
+const char* whv_last_error(whv_grid grid);
+
+/* Number of CUDA kernels this library has launched in the process so far (a kernel replayed
+ * inside one of the library's CUDA graphs counts once per replay).  Diagnostic counter. */
+int64_t whv_kernel_launches(void);
+
+/* Library version string. */
+const char* whv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WHV_H */

@@ -1,0 +1,374 @@
+// Grid lifetime, time grid, speed, basis bookkeeping and the small C-ABI entry points.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+
+#include "whv_device.cuh"
+#include "whv_internal.cuh"
+
+namespace whv {
+
+static thread_local std::string t_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+whv_status fail(whv_grid g, whv_status s, const std::string& msg) {
+  if (g) g->err = msg; else t_last_error = msg;
+  return s;
+}
+
+whv_status cuda_fail(whv_grid g, cudaError_t e, const char* what) {
+  std::string m = std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
+                  ") in " + what;
+  return fail(g, e == cudaErrorMemoryAllocation ? WHV_ERR_OOM : WHV_ERR_CUDA, m);
+}
+
+// Time grid of Sec. 2.2 (reading): dt0 = cfl h_min / c_max, Tbar = Np 2 pi / omega,
+// Nt = ceil(Tbar/dt0), dt = Tbar/Nt; with adjust_omega the smallest Nt with
+// dt = 2 sin(pi Np / Nt)/omega <= dt0 and omega_hat = 2 pi Np/(Nt dt), so that
+// (2/dt) sin(omega_hat dt / 2) = omega.  Trapezoid weights of eq. quadrature.
+whv_status make_time_grid(whv_grid g, const whv_params* p, TimeGridH* tg) {
+  if (!p) return fail(g, WHV_ERR_INVALID, "params is NULL");
+  if (!(p->omega > 0.0) || !isfinite(p->omega)) return fail(g, WHV_ERR_INVALID, "omega must be > 0");
+  if (p->periods < 1) return fail(g, WHV_ERR_INVALID, "periods must be >= 1");
+  const double cfl = p->cfl > 0.0 ? p->cfl : (g->order == 2 ? 0.5 : 0.4);
+  double hmin = g->h[0];
+  for (int m = 1; m < g->dim; ++m) hmin = std::min(hmin, g->h[m]);
+  const double cmax = sqrt(g->c2max);
+  const double dt0 = cfl * hmin / cmax;
+  const double pi = 3.14159265358979323846;
+  TimeGridH t;
+  t.omega = p->omega; t.periods = p->periods; t.adjust = p->adjust_omega ? 1 : 0; t.cfl = cfl;
+  if (!t.adjust) {
+    t.tbar = p->periods * 2.0 * pi / p->omega;
+    double q = ceil(t.tbar / dt0);
+    if (q > 1e7) return fail(g, WHV_ERR_INVALID, "more than 1e7 time steps per wave solve");
+    t.nt = (int)q;
+    t.dt = t.tbar / t.nt;
+    t.omega_hat = p->omega;
+  } else {
+    int nt = 2 * p->periods + 1;
+    while (2.0 * sin(pi * p->periods / nt) / p->omega > dt0) {
+      if (++nt > 10000000) return fail(g, WHV_ERR_INVALID, "more than 1e7 time steps per wave solve");
+    }
+    t.nt = nt;
+    t.dt = 2.0 * sin(pi * p->periods / nt) / p->omega;
+    t.omega_hat = 2.0 * pi * p->periods / (nt * t.dt);
+    t.tbar = nt * t.dt;
+  }
+  if (t.nt < 2) return fail(g, WHV_ERR_INVALID, "fewer than 2 time steps per wave solve");
+  t.omega_eff = 2.0 / t.dt * sin(t.omega_hat * t.dt / 2.0);
+  // explicit leapfrog stability: dt^2 lambda_max^2 / 4 <= 1 (Fourier bound of -L_h)
+  const double per = g->order == 2 ? 4.0 : 16.0 / 3.0;
+  double lmax = 0.0;
+  for (int m = 0; m < g->dim; ++m) lmax += per / (g->h[m] * g->h[m]);
+  lmax *= g->c2max;
+  if (t.dt * t.dt * lmax / 4.0 > 1.0)
+    return fail(g, WHV_ERR_INVALID, "time step above the explicit leapfrog stability limit (lower cfl)");
+  t.phase.resize(t.nt + 1);
+  t.weight.resize(t.nt + 1);
+  for (int n = 0; n <= t.nt; ++n) {
+    const double ph = cos(t.omega_hat * (n * t.dt));
+    const double eta = (n == 0 || n == t.nt) ? 0.5 : 1.0;
+    t.phase[n] = ph;
+    t.weight[n] = (2.0 / t.tbar) * eta * (ph - 0.25) * t.dt;
+  }
+  *tg = std::move(t);
+  return WHV_OK;
+}
+
+// ---------------------------------------------------------------------------- kernels
+__global__ void k_speed_setup(const double* __restrict__ c2in, double* __restrict__ c2,
+                              float* __restrict__ c2f, double* __restrict__ mw, int64_t n,
+                              double* partials, unsigned* counter, double* scal) {
+  double bad = 0.0, mx = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = c2in[i];
+    if (!(v > 0.0) || !isfinite(v)) bad += 1.0;
+    c2[i] = v;
+    c2f[i] = (float)v;
+    mw[i] = 1.0 / v;
+    mx = fmax(mx, v);
+  }
+  // max via a second shared pass: reuse the sum reduction on "bad" and keep max in S_TMP2
+  __shared__ double smx[32];
+  mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, 16));
+  mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, 8));
+  mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, 4));
+  mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, 2));
+  mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, 1));
+  if ((threadIdx.x & 31) == 0) smx[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, smx[w]);
+    partials[kRedBlocks + blockIdx.x] = m;  // second half of the channel: block maxima
+  }
+  __syncthreads();
+  double total;
+  if (grid_reduce(bad, partials, counter, &total) && threadIdx.x == 0) {
+    double m = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) m = fmax(m, __ldcg(partials + kRedBlocks + b));
+    scal[S_TMP] = total;
+    scal[S_TMP2] = m;
+  }
+}
+
+}  // namespace whv
+
+using namespace whv;
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char* whv_version(void) { return "whv 0.1 (sm_103a)"; }
+
+int64_t whv_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* whv_last_error(whv_grid g) { return g ? g->err.c_str() : t_last_error.c_str(); }
+
+int64_t whv_num_unknowns(whv_grid g) { return g ? g->N : 0; }
+
+static void free_all(whv_grid g) {
+  if (!g) return;
+  free_plan(g);
+  void* ptrs[] = {g->c2, g->c2f, g->mw, g->wbuf[0], g->wbuf[1], g->acc, g->x, g->r, g->p, g->q,
+                  g->t, g->fd, g->krylov, g->small, g->partials, g->counters, g->scal,
+                  g->basis.V, g->basis.d_coef};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (g->scal_host) cudaFreeHost(g->scal_host);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+}
+
+whv_status whv_create_grid(int dim, const int64_t npts[3], const double lo[3], const double hi[3],
+                           int order, int precision, void* cuda_stream, whv_grid* out) {
+  if (!out) return fail(nullptr, WHV_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (dim < 1 || dim > 3) return fail(nullptr, WHV_ERR_INVALID, "dim must be 1, 2 or 3");
+  if (order != 2 && order != 4) return fail(nullptr, WHV_ERR_INVALID, "order must be 2 or 4");
+  if (precision != WHV_FP64 && precision != WHV_FP32_STEP)
+    return fail(nullptr, WHV_ERR_INVALID, "precision must be WHV_FP64 or WHV_FP32_STEP");
+  if (!npts) return fail(nullptr, WHV_ERR_INVALID, "npts is NULL");
+  whv_grid g = new whv_grid_s();
+  g->dim = dim; g->order = order; g->precision = precision;
+  int64_t N = 1;
+  for (int m = 0; m < 3; ++m) {
+    if (m < dim) {
+      const int64_t minpts = order == 4 ? 4 : 3;
+      if (npts[m] < minpts || npts[m] > (int64_t)1 << 30) {
+        delete g;
+        return fail(nullptr, WHV_ERR_INVALID, "npts out of range (>= 3, >= 4 for order 4)");
+      }
+      g->npts[m] = npts[m];
+      g->n[m] = (int)(npts[m] - 2);
+      g->lo[m] = lo ? lo[m] : 0.0;
+      g->hi[m] = hi ? hi[m] : 1.0;
+      if (!(g->hi[m] > g->lo[m])) {
+        delete g;
+        return fail(nullptr, WHV_ERR_INVALID, "hi must exceed lo");
+      }
+      g->h[m] = (g->hi[m] - g->lo[m]) / (double)(npts[m] - 1);
+      N *= g->n[m];
+    } else {
+      g->npts[m] = 3; g->n[m] = 1; g->h[m] = 1.0;
+    }
+  }
+  if (N > ((int64_t)1 << 31)) {
+    delete g;
+    return fail(nullptr, WHV_ERR_INVALID, "more than 2^31 unknowns");
+  }
+  g->N = N;
+  cudaError_t e;
+  if (cuda_stream) {
+    g->stream = (cudaStream_t)cuda_stream;
+  } else {
+    // legacy default stream cannot be captured into graphs: use a blocking stream, which
+    // still orders itself with the legacy default stream
+    e = cudaStreamCreate(&g->stream);
+    if (e != cudaSuccess) { whv_status s = cuda_fail(nullptr, e, "cudaStreamCreate"); delete g; return s; }
+    g->own_stream = true;
+  }
+  const size_t esz = precision == WHV_FP64 ? sizeof(double) : sizeof(float);
+  const size_t nb = (size_t)N;
+  struct A { void** p; size_t bytes; } allocs[] = {
+      {&g->wbuf[0], nb * esz}, {&g->wbuf[1], nb * esz}, {&g->acc, nb * esz},
+      {(void**)&g->x, nb * 8}, {(void**)&g->r, nb * 8}, {(void**)&g->p, nb * 8},
+      {(void**)&g->q, nb * 8}, {(void**)&g->t, nb * 8}, {(void**)&g->fd, nb * 8},
+      {(void**)&g->small, (size_t)kMaxND * 8},
+      {(void**)&g->partials, (size_t)CH_NCH * kMaxStepBlocks * 8},
+      {(void**)&g->counters, (size_t)CH_NCH * sizeof(unsigned)},
+      {(void**)&g->scal, (size_t)S_NSLOTS * 8}};
+  for (auto& a : allocs) {
+    e = cudaMalloc(a.p, a.bytes);
+    if (e != cudaSuccess) {
+      whv_status s = cuda_fail(nullptr, e, "cudaMalloc (grid scratch)");
+      free_all(g);
+      delete g;
+      return s;
+    }
+  }
+  e = cudaMallocHost((void**)&g->scal_host, S_NSLOTS * 8);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->counters, 0, CH_NCH * sizeof(unsigned), g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->scal, 0, S_NSLOTS * 8, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) {
+    whv_status s = cuda_fail(nullptr, e, "grid setup");
+    free_all(g);
+    delete g;
+    return s;
+  }
+  *out = g;
+  return WHV_OK;
+}
+
+whv_status whv_destroy_grid(whv_grid g) {
+  if (!g) return WHV_OK;
+  cudaStreamSynchronize(g->stream);
+  free_all(g);
+  delete g;
+  return WHV_OK;
+}
+
+whv_status whv_set_speed(whv_grid g, const double* c2_dev) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  // any basis was built for the old operator
+  if (g->basis.V) { cudaFree(g->basis.V); g->basis.V = nullptr; }
+  g->basis = Basis();
+  free_plan(g);
+  if (!c2_dev) {
+    if (g->c2) cudaFree(g->c2);
+    if (g->c2f) cudaFree(g->c2f);
+    if (g->mw) cudaFree(g->mw);
+    g->c2 = nullptr; g->c2f = nullptr; g->mw = nullptr;
+    g->c2max = 1.0;
+    return WHV_OK;
+  }
+  if (!g->c2) WHV_CUDA(g, cudaMalloc(&g->c2, g->N * 8));
+  if (!g->c2f) WHV_CUDA(g, cudaMalloc(&g->c2f, g->N * 4));
+  if (!g->mw) WHV_CUDA(g, cudaMalloc(&g->mw, g->N * 8));
+  k_speed_setup<<<kRedBlocks, 256, 0, g->stream>>>(c2_dev, g->c2, g->c2f, g->mw, g->N,
+                                                   g->partials + CH_DOT * kMaxStepBlocks,
+                                                   g->counters + CH_DOT, g->scal);
+  count_launches(1);
+  WHV_CUDA(g, cudaGetLastError());
+  whv_status st = fetch_scalars(g);
+  if (st != WHV_OK) return st;
+  if (g->scal_host[S_TMP] != 0.0) {
+    cudaFree(g->c2); cudaFree(g->c2f); cudaFree(g->mw);
+    g->c2 = nullptr; g->c2f = nullptr; g->mw = nullptr; g->c2max = 1.0;
+    return fail(g, WHV_ERR_INVALID, "c^2 must be finite and > 0 at every interior node");
+  }
+  g->c2max = g->scal_host[S_TMP2];
+  return WHV_OK;
+}
+
+whv_status whv_time_grid(whv_grid g, const whv_params* p, int* nt, double* dt, double* omega_hat,
+                         double* omega_eff) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  TimeGridH tg;
+  whv_status s = make_time_grid(g, p, &tg);
+  if (s != WHV_OK) return s;
+  if (nt) *nt = tg.nt;
+  if (dt) *dt = tg.dt;
+  if (omega_hat) *omega_hat = tg.omega_hat;
+  if (omega_eff) *omega_eff = tg.omega_eff;
+  return WHV_OK;
+}
+
+whv_status whv_set_deflation_basis(whv_grid g, const whv_params* p, int nd, const double* V_dev,
+                                   const double* lambda2_host, int mode, int flags) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  if (mode == WHV_BASIS_NONE) {
+    if (g->basis.V) cudaFree(g->basis.V);
+    if (g->basis.d_coef) cudaFree(g->basis.d_coef);
+    g->basis = Basis();
+    return WHV_OK;
+  }
+  TimeGridH tg;
+  whv_status s = make_time_grid(g, p, &tg);
+  if (s != WHV_OK) return s;
+  if (nd < 1 || nd > kMaxND || nd > g->N)
+    return fail(g, WHV_ERR_INVALID, "nd must be in [1, min(N, 1024)]");
+  Basis b;
+  b.nd = nd; b.mode = mode; b.flags = flags;
+  b.omega = p->omega; b.periods = p->periods; b.adjust = p->adjust_omega ? 1 : 0; b.cfl = tg.cfl;
+  if (mode == WHV_BASIS_USER) {
+    if (!V_dev || !lambda2_host) return fail(g, WHV_ERR_INVALID, "USER basis needs V_dev and lambda2_host");
+    WHV_CUDA(g, cudaMalloc(&b.V, (size_t)g->N * nd * 8));
+    WHV_CUDA(g, cudaMemcpyAsync(b.V, V_dev, (size_t)g->N * nd * 8, cudaMemcpyDeviceToDevice, g->stream));
+    b.lambda2.assign(lambda2_host, lambda2_host + nd);
+    b.mu.resize(nd);
+    // mu = 1 - beta_h(lambda), the eigenvalue of A on a true eigenvector
+    for (int m = 0; m < nd; ++m) {
+      const double x = 1.0 - 0.5 * tg.dt * tg.dt * b.lambda2[m];
+      if (!(fabs(x) <= 1.0)) { cudaFree(b.V); return fail(g, WHV_ERR_INVALID, "lambda^2 outside the stable range"); }
+      const double th = acos(x);
+      double be = 0.0;
+      for (int n = 0; n <= tg.nt; ++n) be += tg.weight[n] * cos(n * th);
+      b.mu[m] = 1.0 - be;
+    }
+    b.modes.assign((size_t)nd * g->dim, 0);
+  } else if (mode == WHV_BASIS_CLOSED_FORM) {
+    if (g->c2) return fail(g, WHV_ERR_INVALID, "closed-form basis needs c = 1");
+    b.flags |= WHV_BASIS_EXACT;
+    s = closed_form_basis(g, tg, nd, &b);
+    if (s != WHV_OK) { if (b.V) cudaFree(b.V); return s; }
+  } else if (mode == WHV_BASIS_LANCZOS) {
+    return fail(g, WHV_ERR_INVALID, "LANCZOS basis is not available in this build");
+  } else {
+    return fail(g, WHV_ERR_INVALID, "unknown basis mode");
+  }
+  WHV_CUDA(g, cudaMalloc(&b.d_coef, (size_t)kMaxND * 8));
+  if (g->basis.V) cudaFree(g->basis.V);
+  if (g->basis.d_coef) cudaFree(g->basis.d_coef);
+  g->basis = std::move(b);
+  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
+  return WHV_OK;
+}
+
+whv_status whv_get_basis(whv_grid g, int* nd, int* modes_host, double* lambda2_host, double* V_dev) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  const Basis& b = g->basis;
+  if (nd) *nd = b.nd;
+  if (b.nd == 0) return WHV_OK;
+  if (modes_host) std::memcpy(modes_host, b.modes.data(), b.modes.size() * sizeof(int));
+  if (lambda2_host) std::memcpy(lambda2_host, b.lambda2.data(), b.nd * sizeof(double));
+  if (V_dev) {
+    WHV_CUDA(g, cudaMemcpyAsync(V_dev, b.V, (size_t)g->N * b.nd * 8, cudaMemcpyDeviceToDevice, g->stream));
+    WHV_CUDA(g, cudaStreamSynchronize(g->stream));
+  }
+  return WHV_OK;
+}
+
+whv_status whv_project(whv_grid g, const double* r_dev, double* coeff_dev) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  if (g->basis.nd == 0) return fail(g, WHV_ERR_INVALID, "no deflation basis set");
+  if (!r_dev || !coeff_dev) return fail(g, WHV_ERR_INVALID, "NULL pointer");
+  return project(g, g->basis.V, g->basis.nd, r_dev, coeff_dev);
+}
+
+whv_status whv_expand(whv_grid g, const double* y_dev, double alpha, double* out_dev) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  if (g->basis.nd == 0) return fail(g, WHV_ERR_INVALID, "no deflation basis set");
+  if (!y_dev || !out_dev) return fail(g, WHV_ERR_INVALID, "NULL pointer");
+  return expand(g, g->basis.V, g->basis.nd, y_dev, alpha, out_dev);
+}
+
+whv_status whv_dot(whv_grid g, const double* x_dev, const double* y_dev, double* out_host) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  if (!x_dev || !y_dev || !out_host) return fail(g, WHV_ERR_INVALID, "NULL pointer");
+  whv_status s = dot_async(g, x_dev, y_dev, S_TMP);
+  if (s != WHV_OK) return s;
+  s = fetch_scalars(g);
+  if (s != WHV_OK) return s;
+  *out_host = g->scal_host[S_TMP];
+  return WHV_OK;
+}
+
+}  // extern "C"

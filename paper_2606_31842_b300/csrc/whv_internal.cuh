@@ -1,0 +1,131 @@
+// Internal declarations of the B300 WaveHoltz library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "whv.h"
+
+namespace whv {
+
+// ---------------------------------------------------------------- device scalar slots
+// Krylov scalars live in device memory so that iterations run without host round trips.
+enum Slot {
+  S_RR = 0,     // r^T M r of the current residual
+  S_PQ = 1,     // p^T M (A p)
+  S_ALPHA = 2,
+  S_BETA = 3,
+  S_RR0 = 4,    // residual norm^2 at the start (stopping reference)
+  S_FLAG = 5,   // breakdown flag (nonzero: non-finite or non-positive scalar seen)
+  S_TMP = 6,    // scratch result of whv_dot and friends
+  S_TMP2 = 7,
+  S_NSLOTS = 16
+};
+
+// reduction "channels": each kernel that reduces uses its own partials/counter pair so that
+// reductions of consecutive kernels never share a counter.
+enum Channel { CH_STEP = 0, CH_UPDATE = 1, CH_DOT = 2, CH_PROJ = 3, CH_NCH = 4 };
+
+constexpr int kRedBlocks = 592;          // 4 x 148 SMs: grid of the grid-stride reduction kernels
+constexpr int kMaxStepBlocks = 1 << 20;  // upper bound on blocks of a fused step+reduction kernel
+constexpr int kMaxND = 1024;             // deflation / Krylov basis columns per contraction
+
+struct TimeGridH {
+  double omega = 0, omega_hat = 0, dt = 0, tbar = 0, omega_eff = 0, cfl = 0;
+  int periods = 0, adjust = 0, nt = 0;
+  std::vector<double> phase;   // cos(omega_hat t^n), n = 0..nt
+  std::vector<double> weight;  // (2/Tbar) eta_n (cos(omega_hat t^n) - 1/4) dt
+};
+
+struct Basis {
+  int nd = 0, mode = WHV_BASIS_NONE, flags = 0;
+  double* V = nullptr;                // N x nd, column-major, FP64
+  double* d_coef = nullptr;           // nd scratch
+  std::vector<double> lambda2, mu;    // lambda^2 and mu = 1 - beta_h
+  std::vector<int> modes;             // nd * dim (closed form)
+  double omega = 0; int periods = 0, adjust = 0; double cfl = 0;  // time grid it was built for
+};
+
+struct StepPlan;  // cached CUDA graphs of wave solves (stencil.cu)
+
+}  // namespace whv
+
+struct whv_grid_s {
+  int dim = 1, order = 2, precision = WHV_FP64;
+  int64_t npts[3] = {3, 3, 3};
+  int n[3] = {1, 1, 1};        // interior counts nx, ny, nz
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, h[3] = {1, 1, 1};
+  int64_t N = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;     // created by the grid (caller passed the legacy default stream)
+
+  // speed
+  double* c2 = nullptr;        // FP64 c^2 (nullptr: c = 1)
+  float* c2f = nullptr;        // FP32 copy for FP32 stepping
+  double* mw = nullptr;        // M weights 1/c^2 (nullptr: ones)
+  double c2max = 1.0;
+
+  // stepping buffers (element type double or float by precision)
+  void* wbuf[2] = {nullptr, nullptr};
+  void* acc = nullptr;
+
+  // FP64 Krylov work vectors
+  double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *t = nullptr, *fd = nullptr;
+  double* krylov = nullptr;    // GMRES basis, (restart+1) * N
+  int krylov_cols = 0;
+  double* small = nullptr;     // device small-vector scratch (kMaxND)
+
+  // reductions
+  double* partials = nullptr;  // CH_NCH * kMaxStepBlocks
+  unsigned* counters = nullptr;// CH_NCH
+  double* scal = nullptr;      // S_NSLOTS device scalars
+  double* scal_host = nullptr; // pinned mirror
+
+  whv::Basis basis;
+  whv::StepPlan* plan = nullptr;
+  std::string err;
+};
+
+namespace whv {
+
+// ------------------------------------------------------------------ host helpers (core.cu)
+whv_status fail(whv_grid g, whv_status s, const std::string& msg);
+whv_status cuda_fail(whv_grid g, cudaError_t e, const char* what);
+#define WHV_CUDA(g, call)                                   \
+  do {                                                      \
+    cudaError_t _e = (call);                                \
+    if (_e != cudaSuccess) return whv::cuda_fail(g, _e, #call); \
+  } while (0)
+
+whv_status make_time_grid(whv_grid g, const whv_params* p, TimeGridH* tg);
+
+// launch accounting (whv_kernel_launches)
+void count_launches(int64_t n);
+
+// ---------------------------------------------------------------- kernels launchers
+// stencil.cu: one wave solve.  v (FP64, nullable => 0), f (FP64, nullable => 0).
+//   epi = 0: out = Pi_h(v; f)                  (out FP64)
+//   epi = 1: out = v - Pi_h(v; f) = A v (f=0), and scal[S_PQ] = <v, out>_M
+whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
+                      double* out, int epi);
+void free_plan(whv_grid g);
+
+// reduce.cu
+whv_status dot_async(whv_grid g, const double* x, const double* y, int slot);   // scal[slot] = <x,y>_M
+whv_status cg_update(whv_grid g);        // alpha = rr/pq; x += a p; r -= a q; rr' ; beta
+whv_status cg_direction(whv_grid g);     // p = r + beta p
+whv_status axpby(whv_grid g, int64_t n, double a, const double* x, double b, double* y);  // y = a x + b y
+whv_status fetch_scalars(whv_grid g);    // scal -> scal_host (synchronises the stream)
+
+// deflate.cu: contractions with a column-major N x nd matrix (basis or Krylov basis)
+//   project:  coef[m] = sum_i W[i + m N] M_i r_i            (m < nd)
+//   expand:   out_i  += alpha sum_m W[i + m N] coef[m]
+whv_status project(whv_grid g, const double* W, int nd, const double* r, double* coef);
+whv_status expand(whv_grid g, const double* W, int nd, const double* coef, double alpha,
+                  double* out);
+whv_status closed_form_basis(whv_grid g, const TimeGridH& tg, int nd, Basis* b);
+
+}  // namespace whv

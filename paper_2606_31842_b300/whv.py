@@ -1,0 +1,206 @@
+"""Thin Python binding of the C ABI in include/whv.h (argument marshalling only).
+
+Every function has the name of the C entry point it wraps and forwards raw device pointers of
+contiguous float64 CUDA tensors; all arithmetic runs in the library's CUDA kernels.  There is
+no CPU fallback: importing this module fails loudly when libwhv.so is missing, and every call
+checks the returned status.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libwhv.so")
+
+WHV_OK, WHV_ERR_INVALID, WHV_ERR_CUDA, WHV_ERR_OOM, WHV_ERR_NOT_CONVERGED, WHV_ERR_BREAKDOWN, WHV_ERR_TIMEOUT = range(7)
+WHV_FP64, WHV_FP32_STEP = 0, 1
+WHV_FPI, WHV_CG, WHV_DCG, WHV_GMRES = 0, 1, 2, 3
+WHV_BASIS_NONE, WHV_BASIS_USER, WHV_BASIS_CLOSED_FORM, WHV_BASIS_LANCZOS = 0, 1, 2, 3
+WHV_BASIS_EXACT, WHV_BASIS_REDEFLATE = 1, 2
+WHV_TRUE_RESIDUAL = 1
+STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "NOT_CONVERGED", "BREAKDOWN", "TIMEOUT"]
+METHODS = {"fpi": WHV_FPI, "cg": WHV_CG, "dcg": WHV_DCG, "gmres": WHV_GMRES}
+
+
+class whv_params(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("periods", ctypes.c_int), ("adjust_omega", ctypes.c_int),
+                ("cfl", ctypes.c_double), ("method", ctypes.c_int), ("restart", ctypes.c_int),
+                ("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("flags", ctypes.c_int)]
+
+
+class whv_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("wave_solves", ctypes.c_int), ("nt", ctypes.c_int),
+                ("dt", ctypes.c_double), ("omega_hat", ctypes.c_double), ("omega_eff", ctypes.c_double),
+                ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class WhvError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libwhv.so not built ({_LIB_PATH}); run python -m paper_2606_31842_b300.build")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, D, I, L = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64
+    sig = {
+        "whv_create_grid": [I, ctypes.POINTER(L), ctypes.POINTER(D), ctypes.POINTER(D), I, I, P, ctypes.POINTER(P)],
+        "whv_destroy_grid": [P],
+        "whv_set_speed": [P, P],
+        "whv_time_grid": [P, ctypes.POINTER(whv_params), ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)],
+        "whv_set_deflation_basis": [P, ctypes.POINTER(whv_params), I, P, ctypes.POINTER(D), I, I],
+        "whv_get_basis": [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), P],
+        "whv_apply_pi": [P, ctypes.POINTER(whv_params), P, P, P],
+        "whv_solve": [P, ctypes.POINTER(whv_params), P, I, P, ctypes.POINTER(whv_info)],
+        "whv_project": [P, P, P],
+        "whv_expand": [P, P, D, P],
+        "whv_dot": [P, P, P, ctypes.POINTER(D)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.whv_num_unknowns.argtypes = [P]
+    lib.whv_num_unknowns.restype = L
+    lib.whv_last_error.argtypes = [P]
+    lib.whv_last_error.restype = ctypes.c_char_p
+    lib.whv_kernel_launches.argtypes = []
+    lib.whv_kernel_launches.restype = L
+    lib.whv_version.argtypes = []
+    lib.whv_version.restype = ctypes.c_char_p
+    return lib
+
+
+lib = _load()
+
+# every symbol include/whv.h declares (checked by the CPU tests)
+EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_grid",
+            "whv_set_deflation_basis", "whv_get_basis", "whv_apply_pi", "whv_solve", "whv_project",
+            "whv_expand", "whv_dot", "whv_num_unknowns", "whv_last_error", "whv_version",
+            "whv_kernel_launches"]
+
+
+def _check(status, handle=None, allow=()):
+    if status != WHV_OK and status not in allow:
+        raise WhvError(status, lib.whv_last_error(handle).decode())
+    return status
+
+
+def _ptr(t, numel=None):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_params(omega, periods=1, adjust_omega=False, cfl=0.0, method="cg", restart=30, tol=1e-8,
+                maxit=1000, check_every=1, true_residual=False) -> whv_params:
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    return whv_params(float(omega), int(periods), int(bool(adjust_omega)), float(cfl), m, int(restart),
+                      float(tol), int(maxit), int(check_every), WHV_TRUE_RESIDUAL if true_residual else 0)
+
+
+def whv_version() -> str:
+    return lib.whv_version().decode()
+
+
+def whv_kernel_launches() -> int:
+    return int(lib.whv_kernel_launches())
+
+
+class Grid:
+    """Owns one whv_grid.  `npts` are nodes per direction including boundary nodes (x first)."""
+
+    def __init__(self, npts, lo=None, hi=None, order=2, precision=WHV_FP64, stream=None):
+        dim = len(npts)
+        n3 = (ctypes.c_int64 * 3)(*(list(npts) + [3] * (3 - dim)))
+        lo3 = (ctypes.c_double * 3)(*((list(lo) if lo else [0.0] * dim) + [0.0] * (3 - dim)))
+        hi3 = (ctypes.c_double * 3)(*((list(hi) if hi else [1.0] * dim) + [1.0] * (3 - dim)))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib.whv_create_grid(dim, n3, lo3, hi3, order, precision, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)))
+        self.handle = h
+        self.dim, self.npts, self.order, self.precision = dim, tuple(npts), order, precision
+        self.shape = tuple(int(n) - 2 for n in reversed(list(npts)))
+        self.N = int(lib.whv_num_unknowns(h))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.whv_destroy_grid(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+    def whv_set_speed(self, c2):
+        _check(lib.whv_set_speed(self.handle, _ptr(c2, self.N)), self.handle)
+
+    def whv_time_grid(self, params):
+        nt, dt, oh, oe = ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib.whv_time_grid(self.handle, ctypes.byref(params), ctypes.byref(nt), ctypes.byref(dt),
+                                 ctypes.byref(oh), ctypes.byref(oe)), self.handle)
+        return {"nt": nt.value, "dt": dt.value, "omega_hat": oh.value, "omega_eff": oe.value}
+
+    def whv_set_deflation_basis(self, params, nd, mode, V=None, lambda2=None, flags=0):
+        lam = None
+        if lambda2 is not None:
+            lam = (ctypes.c_double * nd)(*[float(x) for x in lambda2])
+        _check(lib.whv_set_deflation_basis(self.handle, ctypes.byref(params), int(nd),
+                                           _ptr(V, None if V is None else self.N * nd), lam, int(mode), int(flags)),
+               self.handle)
+
+    def whv_get_basis(self, want_vectors=False):
+        nd = ctypes.c_int()
+        _check(lib.whv_get_basis(self.handle, ctypes.byref(nd), None, None, None), self.handle)
+        n = nd.value
+        if n == 0:
+            return {"nd": 0}
+        modes = (ctypes.c_int * (n * self.dim))()
+        lam = (ctypes.c_double * n)()
+        V = torch.empty(n * self.N, dtype=torch.float64, device="cuda") if want_vectors else None
+        _check(lib.whv_get_basis(self.handle, ctypes.byref(nd), modes, lam, _ptr(V)), self.handle)
+        return {"nd": n, "modes": [list(modes[i * self.dim:(i + 1) * self.dim]) for i in range(n)],
+                "lambda2": list(lam), "V": None if V is None else V.view(n, self.N)}
+
+    def whv_apply_pi(self, params, v, f=None, out=None):
+        if out is None:
+            out = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        _check(lib.whv_apply_pi(self.handle, ctypes.byref(params), _ptr(v, self.N), _ptr(f, self.N), _ptr(out, self.N)),
+               self.handle)
+        return out
+
+    def whv_solve(self, params, f, u=None, use_guess=False, raise_not_converged=False):
+        if u is None:
+            u = torch.zeros(self.N, dtype=torch.float64, device="cuda")
+        info = whv_info()
+        allow = () if raise_not_converged else (WHV_ERR_NOT_CONVERGED,)
+        st = _check(lib.whv_solve(self.handle, ctypes.byref(params), _ptr(f, self.N), int(bool(use_guess)),
+                                  _ptr(u, self.N), ctypes.byref(info)), self.handle, allow)
+        d = info.as_dict()
+        d["status"] = STATUS_NAMES[st]
+        return u, d
+
+    def whv_project(self, r, coef):
+        _check(lib.whv_project(self.handle, _ptr(r, self.N), _ptr(coef)), self.handle)
+        return coef
+
+    def whv_expand(self, y, alpha, out):
+        _check(lib.whv_expand(self.handle, _ptr(y), float(alpha), _ptr(out, self.N)), self.handle)
+        return out
+
+    def whv_dot(self, x, y):
+        out = ctypes.c_double()
+        _check(lib.whv_dot(self.handle, _ptr(x, self.N), _ptr(y, self.N), ctypes.byref(out)), self.handle)
+        return out.value

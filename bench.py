@@ -30,6 +30,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the CPU oracle legs run single-threaded (numpy elementwise work is single-threaded anyway;
+# this pins the BLAS calls of the projections too); set before numpy is first imported
+for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
 
 METRIC = "WaveHoltz solve time to rel. residual 1e-6; stencil GLUP/s vs HBM roofline"
 L2_FLUSH_BYTES = 512 << 20   # > 126 MB L2: written between timed steps
@@ -38,7 +42,7 @@ L2_FLUSH_BYTES = 512 << 20   # > 126 MB L2: written between timed steps
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="whv", choices=["whv", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -112,25 +116,23 @@ class ClockSampler:
 def oracle_sample(w, tol, iterations_hint, budget_s=12.0):
     """Time the FP64 oracle on a bounded sample of the workload: mode selection + basis, b, and
     as many CG iterations as fit in the budget; extrapolate to `iterations_hint` iterations."""
-    from threadpoolctl import threadpool_limits
     from oracle import operators as O, waveholtz as WH, spectral as SP, krylov as K
     from paper_2606_31842_b300 import inputs as I
-    with threadpool_limits(1):
-        g = O.Grid(w.npts)
-        tg = WH.time_grid_for(g, w.omega)
-        f = I.forcing_for(w)
-        t0 = time.perf_counter()
-        modes, lam2, _ = SP.select_modes(g, tg, w.nd)
-        V = SP.basis(g, modes)
-        t_setup = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        b = WH.rhs_b(g, tg, K.project_out(g, V, f))
-        t_b = time.perf_counter() - t0
-        A = K.Operator(g, tg)
-        k = max(1, int(budget_s / max(t_b, 1e-3)))
-        t0 = time.perf_counter()
-        K.cg(g, A, b, 0.0, k)
-        t_it = (time.perf_counter() - t0) / k
+    g = O.Grid(w.npts)
+    tg = WH.time_grid_for(g, w.omega)
+    f = I.forcing_for(w)
+    t0 = time.perf_counter()
+    modes, lam2, _ = SP.select_modes(g, tg, w.nd)
+    V = SP.basis(g, modes)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = WH.rhs_b(g, tg, K.project_out(g, V, f))
+    t_b = time.perf_counter() - t0
+    A = K.Operator(g, tg)
+    k = max(1, int(budget_s / max(t_b, 1e-3)))
+    t0 = time.perf_counter()
+    K.cg(g, A, b, 0.0, k)
+    t_it = (time.perf_counter() - t0) / k
     solve_s = t_b + iterations_hint * t_it
     return {"solve_s": solve_s, "setup_s": t_setup, "t_wave": t_b, "t_iter": t_it, "k": k}
 
@@ -231,6 +233,7 @@ def main():
     times, infos = [], []
     launches0 = whv.whv_kernel_launches()
     with ClockSampler(local) as clk:
+        time.sleep(0.5)                               # let the sampler start
         barrier()
         torch.cuda.synchronize()
         for _ in range(args.steps):

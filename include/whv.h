@@ -151,6 +151,20 @@ whv_status whv_apply_pi(whv_grid grid, const whv_params* p, const double* v_dev,
 whv_status whv_solve(whv_grid grid, const whv_params* p, const double* f_dev, int use_guess,
                      double* u_dev, whv_info* info);
 
+/* Steps per sweep k of the temporally blocked 2-D stencil kernel: each launch advances k leapfrog
+ * steps of the f = 0 wave solves in shared memory (halo of width k r).  k = 1 launches one kernel
+ * per time step, k = 0 restores the default (8 for FP32 stepping, 1 for FP64), k <= 16.  Only
+ * 2-D grids block; other grids always step once per launch.  whv_get_steps_per_sweep returns the
+ * value in effect. */
+whv_status whv_set_steps_per_sweep(whv_grid grid, int k);
+whv_status whv_get_steps_per_sweep(whv_grid grid, int* k);
+
+/* Autotuner: times f = 0 wave solves of p's time grid for each candidate steps-per-sweep value
+ * (1, 2, 4, 6, 8, 10, 12, 16 on 2-D grids) with CUDA events on the grid's stream and keeps the
+ * fastest; *best (host, may be NULL) receives it.  Overwrites the grid's internal work vectors,
+ * synchronises the stream.  Must not be called while the grid's stream is being captured. */
+whv_status whv_autotune(whv_grid grid, const whv_params* p, int* best);
+
 /* Deflation contractions and reductions on the grid's basis / weights (building blocks of the
  * solve, exposed for testing and for callers composing their own iterations):
  *   whv_project:  coeff_dev[m] = (W^T M r)_m, m < nd                 (Algorithm 2, (r, phi_m))

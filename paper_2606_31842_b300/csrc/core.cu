@@ -137,7 +137,7 @@ int64_t whv_num_unknowns(whv_grid g) { return g ? g->N : 0; }
 static void free_all(whv_grid g) {
   if (!g) return;
   free_plan(g);
-  void* ptrs[] = {g->c2, g->c2f, g->mw, g->wbuf[0], g->wbuf[1], g->acc, g->x, g->r, g->p, g->q,
+  void* ptrs[] = {g->c2, g->c2f, g->mw, g->wbuf[0], g->wbuf[1], g->wbuf[2], g->wbuf[3], g->acc, g->x, g->r, g->p, g->q,
                   g->t, g->fd, g->krylov, g->small, g->partials, g->counters, g->scal,
                   g->basis.V, g->basis.d_coef};
   for (void* p : ptrs)
@@ -155,6 +155,7 @@ whv_status whv_create_grid(int dim, const int64_t npts[3], const double lo[3], c
   if (precision != WHV_FP64 && precision != WHV_FP32_STEP)
     return fail(nullptr, WHV_ERR_INVALID, "precision must be WHV_FP64 or WHV_FP32_STEP");
   if (!npts) return fail(nullptr, WHV_ERR_INVALID, "npts is NULL");
+  blocked_init();
   whv_grid g = new whv_grid_s();
   g->dim = dim; g->order = order; g->precision = precision;
   int64_t N = 1;
@@ -197,7 +198,8 @@ whv_status whv_create_grid(int dim, const int64_t npts[3], const double lo[3], c
   const size_t esz = precision == WHV_FP64 ? sizeof(double) : sizeof(float);
   const size_t nb = (size_t)N;
   struct A { void** p; size_t bytes; } allocs[] = {
-      {&g->wbuf[0], nb * esz}, {&g->wbuf[1], nb * esz}, {&g->acc, nb * esz},
+      {&g->wbuf[0], nb * esz}, {&g->wbuf[1], nb * esz}, {&g->wbuf[2], nb * esz},
+      {&g->wbuf[3], nb * esz}, {&g->acc, nb * esz},
       {(void**)&g->x, nb * 8}, {(void**)&g->r, nb * 8}, {(void**)&g->p, nb * 8},
       {(void**)&g->q, nb * 8}, {(void**)&g->t, nb * 8}, {(void**)&g->fd, nb * 8},
       {(void**)&g->small, (size_t)kMaxND * 8},

@@ -155,7 +155,7 @@ static StepCoef<T> coef_of(whv_grid g, const TimeGridH& tg) {
 
 template <typename T, int DIM, int ORDER, bool VARC, bool FORCE>
 static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
-                               double* out, int epi) {
+                               double* out, int epi, int* nlaunch) {
   const LaunchShape ls = shape_of(g);
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
   T* b0 = (T*)g->wbuf[0];
@@ -168,6 +168,17 @@ static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v,
   else
     k_first<T, DIM, ORDER, VARC, FORCE, true><<<ls.grid, ls.block, 0, g->stream>>>(v, b0, b1, acc, c2, f, nx, ny, nz, cf);
   WHV_CUDA(g, cudaGetLastError());
+  *nlaunch = 1;
+  if constexpr (DIM == 2 && !FORCE) {
+    const int kb = g->kblock > 0 ? g->kblock : default_kblock(g);
+    if (kb > 1) {
+      int nl = 0;
+      whv_status s = blocked_steps_2d<T, ORDER, VARC>(g, tg, v, out, epi, kb, &nl);
+      *nlaunch += nl;
+      return s;
+    }
+  }
+  *nlaunch += tg.nt - 1;
   // after the first step: W^{n-1} in b0, W^n in b1
   T* wprev = b0;
   T* wcur = b1;
@@ -197,37 +208,42 @@ static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v,
 
 template <typename T, int DIM, int ORDER>
 static whv_status dispatch_vf(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
-                              double* out, int epi) {
+                              double* out, int epi, int* nl) {
   const bool varc = g->c2 != nullptr;
   if (varc) {
-    return f ? launch_solve<T, DIM, ORDER, true, true>(g, tg, v, f, out, epi)
-             : launch_solve<T, DIM, ORDER, true, false>(g, tg, v, f, out, epi);
+    return f ? launch_solve<T, DIM, ORDER, true, true>(g, tg, v, f, out, epi, nl)
+             : launch_solve<T, DIM, ORDER, true, false>(g, tg, v, f, out, epi, nl);
   }
-  return f ? launch_solve<T, DIM, ORDER, false, true>(g, tg, v, f, out, epi)
-           : launch_solve<T, DIM, ORDER, false, false>(g, tg, v, f, out, epi);
+  return f ? launch_solve<T, DIM, ORDER, false, true>(g, tg, v, f, out, epi, nl)
+           : launch_solve<T, DIM, ORDER, false, false>(g, tg, v, f, out, epi, nl);
 }
 
 template <typename T>
 static whv_status dispatch(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
-                           double* out, int epi) {
+                           double* out, int epi, int* nl) {
   switch (g->dim * 10 + g->order) {
-    case 12: return dispatch_vf<T, 1, 2>(g, tg, v, f, out, epi);
-    case 14: return dispatch_vf<T, 1, 4>(g, tg, v, f, out, epi);
-    case 22: return dispatch_vf<T, 2, 2>(g, tg, v, f, out, epi);
-    case 24: return dispatch_vf<T, 2, 4>(g, tg, v, f, out, epi);
-    case 32: return dispatch_vf<T, 3, 2>(g, tg, v, f, out, epi);
-    case 34: return dispatch_vf<T, 3, 4>(g, tg, v, f, out, epi);
+    case 12: return dispatch_vf<T, 1, 2>(g, tg, v, f, out, epi, nl);
+    case 14: return dispatch_vf<T, 1, 4>(g, tg, v, f, out, epi, nl);
+    case 22: return dispatch_vf<T, 2, 2>(g, tg, v, f, out, epi, nl);
+    case 24: return dispatch_vf<T, 2, 4>(g, tg, v, f, out, epi, nl);
+    case 32: return dispatch_vf<T, 3, 2>(g, tg, v, f, out, epi, nl);
+    case 34: return dispatch_vf<T, 3, 4>(g, tg, v, f, out, epi, nl);
   }
   return fail(g, WHV_ERR_INVALID, "unsupported dim/order");
 }
 
+// default steps per sweep of the blocked 2-D kernel: FP32 stepping is bound by launches and
+// L2 traffic (block 8 steps); FP64 stepping is bound by the FP64 pipe, where the redundant halo
+// updates of a blocked sweep cost more than the launches they save (one step per launch)
+int default_kblock(whv_grid g) { return g->precision == WHV_FP32_STEP ? 8 : 1; }
+
 static whv_status launch_wave_solve(whv_grid g, const TimeGridH& tg, const double* v,
-                                    const double* f, double* out, int epi) {
+                                    const double* f, double* out, int epi, int* nl) {
   const LaunchShape ls = shape_of(g);
   if ((int64_t)ls.grid.x * ls.grid.y * ls.grid.z > kMaxStepBlocks)
     return fail(g, WHV_ERR_INVALID, "grid too large for the fused reduction");
-  return g->precision == WHV_FP64 ? dispatch<double>(g, tg, v, f, out, epi)
-                                  : dispatch<float>(g, tg, v, f, out, epi);
+  return g->precision == WHV_FP64 ? dispatch<double>(g, tg, v, f, out, epi, nl)
+                                  : dispatch<float>(g, tg, v, f, out, epi, nl);
 }
 
 // ------------------------------------------------------------------ CUDA graph cache
@@ -238,7 +254,8 @@ struct PlanEntry {
   double* out;
   int epi;
   double omega, cfl;
-  int periods, adjust, nt;
+  int periods, adjust, nt, kblock;
+  int launches;   // kernels in the graph
   cudaGraphExec_t exec;
   unsigned long long last_use;
 };
@@ -260,24 +277,28 @@ whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const do
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   WHV_CUDA(g, cudaStreamIsCapturing(g->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) {  // caller is capturing: record the launches into its graph
-    count_launches(tg.nt);
-    return launch_wave_solve(g, tg, v, f, out, epi);
+    int nl = 0;
+    whv_status s = launch_wave_solve(g, tg, v, f, out, epi, &nl);
+    count_launches(nl);
+    return s;
   }
   if (!g->plan) g->plan = new StepPlan();
   StepPlan* P = g->plan;
   P->tick++;
   for (auto& e : P->entries) {
     if (e.v == v && e.f == f && e.out == out && e.epi == epi && e.omega == tg.omega &&
-        e.cfl == tg.cfl && e.periods == tg.periods && e.adjust == tg.adjust && e.nt == tg.nt) {
+        e.cfl == tg.cfl && e.periods == tg.periods && e.adjust == tg.adjust && e.nt == tg.nt &&
+        e.kblock == g->kblock) {
       e.last_use = P->tick;
       WHV_CUDA(g, cudaGraphLaunch(e.exec, g->stream));
-      count_launches(tg.nt);
+      count_launches(e.launches);
       return WHV_OK;
     }
   }
   cudaGraph_t graph = nullptr;
   WHV_CUDA(g, cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
-  whv_status s = launch_wave_solve(g, tg, v, f, out, epi);
+  int nl = 0;
+  whv_status s = launch_wave_solve(g, tg, v, f, out, epi, &nl);
   cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
   if (s != WHV_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -295,9 +316,10 @@ whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const do
     cudaGraphExecDestroy(P->entries[victim].exec);
     P->entries.erase(P->entries.begin() + victim);
   }
-  P->entries.push_back(PlanEntry{v, f, out, epi, tg.omega, tg.cfl, tg.periods, tg.adjust, tg.nt, exec, P->tick});
+  P->entries.push_back(PlanEntry{v, f, out, epi, tg.omega, tg.cfl, tg.periods, tg.adjust, tg.nt,
+                                g->kblock, nl, exec, P->tick});
   WHV_CUDA(g, cudaGraphLaunch(exec, g->stream));
-  count_launches(tg.nt);
+  count_launches(nl);
   return WHV_OK;
 }
 
@@ -315,4 +337,56 @@ extern "C" whv_status whv_apply_pi(whv_grid g, const whv_params* p, const double
   // v and out may alias: the first step has consumed v before the last step writes out.
   // Repeated calls with the same buffers replay one cached CUDA graph.
   return wave_solve(g, tg, v_dev, f_dev, out_dev, 0);
+}
+
+extern "C" whv_status whv_set_steps_per_sweep(whv_grid g, int k) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  if (k < 0 || k > 16) return fail(g, WHV_ERR_INVALID, "steps per sweep must be in [0, 16]");
+  g->kblock = k;
+  return WHV_OK;
+}
+
+extern "C" whv_status whv_get_steps_per_sweep(whv_grid g, int* k) {
+  if (!g || !k) return fail(g, WHV_ERR_INVALID, "NULL argument");
+  *k = g->kblock > 0 ? g->kblock : default_kblock(g);
+  return WHV_OK;
+}
+
+// Autotuner of the steps per sweep: times two f = 0 wave solves per candidate (graph replay,
+// CUDA events on the grid's stream, after one warm-up replay) and keeps the fastest.
+extern "C" whv_status whv_autotune(whv_grid g, const whv_params* p, int* best) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  TimeGridH tg;
+  whv_status s = make_time_grid(g, p, &tg);
+  if (s != WHV_OK) return s;
+  const int cands2d[] = {1, 2, 4, 6, 8, 10, 12, 16};
+  const int cands_other[] = {1};
+  const int* cands = g->dim == 2 ? cands2d : cands_other;
+  const int nc = g->dim == 2 ? 8 : 1;
+  cudaEvent_t e0, e1;
+  WHV_CUDA(g, cudaEventCreate(&e0));
+  WHV_CUDA(g, cudaEventCreate(&e1));
+  int kbest = 1;
+  float tbest = 1e30f;
+  const int saved = g->kblock;
+  WHV_CUDA(g, cudaMemsetAsync(g->x, 0, g->N * sizeof(double), g->stream));
+  for (int c = 0; c < nc; ++c) {
+    g->kblock = cands[c];
+    // v = x (any finite content), out = t; f = 0
+    s = wave_solve(g, tg, g->x, nullptr, g->t, 0);
+    if (s != WHV_OK) break;
+    cudaEventRecord(e0, g->stream);
+    for (int r = 0; r < 2 && s == WHV_OK; ++r) s = wave_solve(g, tg, g->x, nullptr, g->t, 0);
+    cudaEventRecord(e1, g->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { s = fail(g, WHV_ERR_CUDA, "autotune timing"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < tbest) { tbest = ms; kbest = cands[c]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != WHV_OK) { g->kblock = saved; return s; }
+  g->kblock = kbest;
+  if (best) *best = kbest;
+  return WHV_OK;
 }

@@ -68,9 +68,11 @@ struct whv_grid_s {
   double* mw = nullptr;        // M weights 1/c^2 (nullptr: ones)
   double c2max = 1.0;
 
-  // stepping buffers (element type double or float by precision)
-  void* wbuf[2] = {nullptr, nullptr};
+  // stepping buffers (element type double or float by precision): two (W^{n-1}, W^n) pairs so
+  // that temporally blocked sweeps read one pair and write the other
+  void* wbuf[4] = {nullptr, nullptr, nullptr, nullptr};
   void* acc = nullptr;
+  int kblock = 0;              // steps per sweep of the blocked 2-D kernel (0: default, 1: off)
 
   // FP64 Krylov work vectors
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *t = nullptr, *fd = nullptr;
@@ -112,6 +114,13 @@ void count_launches(int64_t n);
 whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
                       double* out, int epi);
 void free_plan(whv_grid g);
+int default_kblock(whv_grid g);
+
+// stencil_blocked.cu: steps 1..nt-1 of a 2-D f = 0 wave solve in sweeps of k steps
+template <typename T, int ORDER, bool VARC>
+whv_status blocked_steps_2d(whv_grid g, const TimeGridH& tg, const double* v, double* out, int epi,
+                            int k_want, int* launches);
+void blocked_init();
 
 // reduce.cu
 whv_status dot_async(whv_grid g, const double* x, const double* y, int slot);   // scal[slot] = <x,y>_M

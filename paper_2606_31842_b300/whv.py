@@ -64,6 +64,9 @@ def _load():
         "whv_project": [P, P, P],
         "whv_expand": [P, P, D, P],
         "whv_dot": [P, P, P, ctypes.POINTER(D)],
+        "whv_set_steps_per_sweep": [P, I],
+        "whv_get_steps_per_sweep": [P, ctypes.POINTER(I)],
+        "whv_autotune": [P, ctypes.POINTER(whv_params), ctypes.POINTER(I)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -86,7 +89,7 @@ lib = _load()
 EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_grid",
             "whv_set_deflation_basis", "whv_get_basis", "whv_apply_pi", "whv_solve", "whv_project",
             "whv_expand", "whv_dot", "whv_num_unknowns", "whv_last_error", "whv_version",
-            "whv_kernel_launches"]
+            "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune"]
 
 
 def _check(status, handle=None, allow=()):
@@ -191,6 +194,19 @@ class Grid:
         d = info.as_dict()
         d["status"] = STATUS_NAMES[st]
         return u, d
+
+    def whv_set_steps_per_sweep(self, k):
+        _check(lib.whv_set_steps_per_sweep(self.handle, int(k)), self.handle)
+
+    def whv_get_steps_per_sweep(self):
+        k = ctypes.c_int()
+        _check(lib.whv_get_steps_per_sweep(self.handle, ctypes.byref(k)), self.handle)
+        return k.value
+
+    def whv_autotune(self, params):
+        k = ctypes.c_int()
+        _check(lib.whv_autotune(self.handle, ctypes.byref(params), ctypes.byref(k)), self.handle)
+        return k.value
 
     def whv_project(self, r, coef):
         _check(lib.whv_project(self.handle, _ptr(r, self.N), _ptr(coef)), self.handle)

@@ -266,3 +266,51 @@ def test_user_stream_ordering():
         out = g.whv_apply_pi(whv.make_params(8.0), t)
     s.synchronize()
     assert relmax(host(out), WH.apply_pi(og, WH.time_grid_for(og, 8.0), v)) < 1e-12
+
+
+# --------------------------------------------------------------------------- blocked sweeps
+BLK_CASES = [((70, 45), 2, None, 14.0), ((37, 61), 4, "c3", 11.0), ((101, 99), 2, "c3", 20.0),
+             ((6, 40), 4, None, 5.0), ((3, 3), 2, None, 1.0), ((130, 67), 4, None, 17.0)]
+
+
+@pytest.mark.parametrize("npts,order,speed,omega", BLK_CASES)
+@pytest.mark.parametrize("k", [1, 2, 5, 8, 16])
+def test_blocked_sweeps_fp64(npts, order, speed, omega, k):
+    """The temporally blocked 2-D kernel (k steps per launch) gives the single-step result."""
+    g, og, _ = make(npts, order, speed)
+    g.whv_set_steps_per_sweep(k)
+    assert g.whv_get_steps_per_sweep() == k
+    prm = whv.make_params(omega)
+    tg = WH.time_grid_for(og, omega)
+    v = I.random_field(og.shape, 21)
+    out = g.whv_apply_pi(prm, dev(v))
+    assert relmax(host(out), WH.apply_pi(og, tg, v)) < 1e-12
+    # operator epilogue inside a solve (A p and p^T A p on the last sweep)
+    f = I.gaussian(npts, [0.45, 0.5], 0.1, omega ** 2)
+    prm2 = whv.make_params(omega, method="cg", tol=0.0, maxit=4)
+    u, _ = g.whv_solve(prm2, dev(f))
+    ref = K.devd_solve(og, tg, f, None, None, "cg", 0.0, 4).u
+    assert relmax(host(u), ref) < 1e-12
+
+
+@pytest.mark.parametrize("npts,order,speed,omega", BLK_CASES[:4])
+@pytest.mark.parametrize("k", [3, 8, 16])
+def test_blocked_sweeps_fp32(npts, order, speed, omega, k):
+    g, og, _ = make(npts, order, speed, precision=whv.WHV_FP32_STEP)
+    g.whv_set_steps_per_sweep(k)
+    prm = whv.make_params(omega)
+    v = I.random_field(og.shape, 22)
+    out = host(g.whv_apply_pi(prm, dev(v)))
+    ref = WH.apply_pi(og, WH.time_grid_for(og, omega), v)
+    assert np.abs(out - ref.ravel()).max() <= 2e-5 * max(np.abs(v).max(), np.abs(ref).max())
+
+
+def test_autotune_picks_valid_k_and_keeps_results():
+    g, og, _ = make((257, 257), precision=whv.WHV_FP32_STEP)
+    prm = whv.make_params(30.0, method="cg", tol=1e-6, maxit=500)
+    k = g.whv_autotune(prm)
+    assert k in (1, 2, 4, 6, 8, 10, 12, 16) and g.whv_get_steps_per_sweep() == k
+    v = I.random_field(og.shape, 23)
+    out = host(g.whv_apply_pi(prm, dev(v)))
+    ref = WH.apply_pi(og, WH.time_grid_for(og, 30.0), v)
+    assert np.abs(out - ref.ravel()).max() <= 2e-5 * max(np.abs(v).max(), np.abs(ref).max())

@@ -61,7 +61,8 @@ def config_dict(w, tol, precision, nt, n_gpus):
     return {"workload": f"2-D Helmholtz {w.npts[0]}x{w.npts[1]} nodes, omega={w.omega:g}, Gaussian source width 0.02, "
                         f"DEVD + CG with {w.nd} closed-form eigenvectors, tol {tol:g}",
             "grid": list(w.npts), "unknowns": w.n_unknowns, "omega": w.omega, "nd": w.nd, "tol": tol,
-            "method": "DEVD-CG", "stepping": precision, "krylov": "fp64", "nt": nt,
+            "method": "DEVD-CG" + (" in FP64 residual correction" if precision == "fp32" else ""),
+            "stepping": precision, "krylov": "fp64", "nt": nt,
             "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{n_gpus}"}
 
 
@@ -165,6 +166,15 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ GPU arm
+def kernel_source_hash():
+    """Hash of the stepping-kernel sources; a recorded DRAM traffic figure is only reported while
+    the kernels are the ones it was measured on."""
+    h = hashlib.sha256()
+    for fn in ("stencil.cu", "stencil_blocked.cu", "whv_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2606_31842_b300", "csrc", fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_for(kernel, precision):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the kernel
     source changed since the counters were taken."""
@@ -177,8 +187,7 @@ def traffic_for(kernel, precision):
         return None
     if not rec:
         return None
-    src = open(os.path.join(ROOT, "paper_2606_31842_b300", "csrc", "stencil.cu"), "rb").read()
-    if hashlib.sha256(src).hexdigest()[:16] != rec.get("stencil_sha"):
+    if kernel_source_hash() != rec.get("source_sha"):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -212,10 +221,13 @@ def main():
     prec = whv.WHV_FP32_STEP if args.precision == "fp32" else whv.WHV_FP64
     stream = torch.cuda.Stream()
     g = whv.Grid(w.npts, precision=prec, stream=stream)
-    prm = whv.make_params(w.omega, method="cg", tol=tol, maxit=5000, check_every=1)
+    # FP32 stepping runs inside FP64 residual correction so that the FP64 residual meets tol
+    prm = whv.make_params(w.omega, method="cg", tol=tol, maxit=5000, check_every=1,
+                          refine_fp64=args.precision == "fp32")
     tgrid = g.whv_time_grid(prm)
     nt = tgrid["nt"]
     g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
+    ksweep = g.whv_autotune(prm)                      # steps per sweep of the blocked 2-D kernel
     f_host = torch.from_numpy(I.forcing_for(w).ravel()).pin_memory()
     u_host = torch.empty_like(f_host).pin_memory()
     with torch.cuda.stream(stream):
@@ -256,6 +268,20 @@ def main():
         ms = float(t.item())
     info = infos[-1]
     lups = info["wave_solves"] * nt * w.n_unknowns
+    # accuracy of the timed configuration (outside the timed region): FP64 true residual and
+    # the error against an FP64-stepping solve of the same problem on the same GPU
+    prm_chk = whv.make_params(w.omega, method="cg", tol=tol, maxit=5000, true_residual=True,
+                              refine_fp64=args.precision == "fp32")
+    u_chk, info_chk = g.whv_solve(prm_chk, f)
+    accuracy = {"true_rel_residual": info_chk["true_rel_residual"],
+                "residual_precision": "fp64" if args.precision == "fp64" else "fp64 (FP64 wave solves)"}
+    if args.precision == "fp32":
+        g64 = whv.Grid(w.npts, precision=whv.WHV_FP64, stream=stream)
+        prm64 = whv.make_params(w.omega, method="cg", tol=1e-11, maxit=5000)
+        g64.whv_set_deflation_basis(prm64, w.nd, whv.WHV_BASIS_CLOSED_FORM)
+        u64, _ = g64.whv_solve(prm64, f)
+        accuracy["rel_max_err_vs_fp64_solve"] = float((u_chk - u64).abs().max() / u64.abs().max())
+        g64.close()
     glups_solve = lups / (ms * 1e-3) / 1e9
 
     # ------------------------------------------------------------------ e2e: host buffers
@@ -307,13 +333,44 @@ def main():
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "note": "the 511^2 state (3 arrays, 3 MB) stays resident in the 126 MB L2 during a wave solve"}
 
+    # ------------------------------------------------------------------ HBM-bound stencil
+    # the 3-D 256^3 grid (66 MB per FP32 array, 3 arrays > L2): f = 0 wave solves of the
+    # 7-point z-marching step kernel, the case on which the HBM fraction is meaningful
+    g3 = whv.Grid((256, 256, 256), precision=whv.WHV_FP32_STEP, stream=stream)
+    prm3 = whv.make_params(40.0)
+    nt3 = g3.whv_time_grid(prm3)["nt"]
+    v3 = torch.randn(g3.N, dtype=torch.float64, device="cuda")
+    o3 = torch.empty_like(v3)
+    torch.cuda.synchronize()
+    g3.whv_apply_pi(prm3, v3, None, o3)
+    stream.synchronize()
+    reps3 = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps3):
+        g3.whv_apply_pi(prm3, v3, None, o3)
+    e1.record(stream)
+    e1.synchronize()
+    # per step: the first-step kernel's share is 1/nt of the launches; report the wave-solve mean
+    t3 = e0.elapsed_time(e1) * 1e-3 / (reps3 * nt3)
+    ach3 = 20 * g3.N / t3 / 1e9
+    stencil_hbm = {"kernel": "k_step3d (3-D 7-point z-marching step + filter, FP32)",
+                   "workload": "256^3 nodes (254^3 unknowns), omega=40, f = 0 wave solves, nt=%d" % nt3,
+                   "bound": "hbm", "achieved": ach3, "peak": peak, "unit": "GB/s", "frac": ach3 / peak,
+                   "bytes_per_lup": 20, "glups": g3.N / t3 / 1e9, "step_us": t3 * 1e6,
+                   "traffic": traffic_for("k_step3d", "fp32")}
+    g3.close()
+    del v3, o3
+
     line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-            "krylov_dtype": "f64", "data": "synthetic", "config": config_dict(w, tol, args.precision, nt, world),
+            "krylov_dtype": "f64", "data": "synthetic",
+            "config": dict(config_dict(w, tol, args.precision, nt, world), steps_per_sweep=ksweep),
             "iterations": info["iterations"], "wave_solves": info["wave_solves"],
-            "rel_residual": info["rel_residual"], "glups_solve": glups_solve,
-            "roofline": roof,
+            "rel_residual": info["rel_residual"], "glups_solve": glups_solve, "accuracy": accuracy,
+            "outer_iterations": info.get("outer_iterations", 0), "wave_solves_fp64": info.get("wave_solves_fp64", 0),
+            "roofline": roof, "stencil_hbm": stencil_hbm,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": w.n_unknowns * 8,
                     "d2h_bytes_per_step": w.n_unknowns * 8},
             "gpu_launches": launches, "clocks": clocks}

@@ -68,7 +68,16 @@ enum {
 };
 /* whv_params.flags */
 enum {
-  WHV_TRUE_RESIDUAL = 1       /* at exit compute ||Pi_h(u;f) - u|| / ||Pi_h(0;f)|| (2 extra wave solves) */
+  WHV_TRUE_RESIDUAL = 1,      /* at exit compute ||Pi_h(u;f) - u|| / ||Pi_h(0;f)|| (2 extra wave solves,
+                                 in FP64 when the grid steps in FP64 or WHV_REFINE_FP64 is set)       */
+  WHV_REFINE_FP64 = 2         /* iterative refinement on the full system b = Pi_h(0; f): the residual
+                                 r = b - A x is formed with FP64 wave solves; each correction is the
+                                 modal solve of r's deflated components (W diag(1/mu) W^T M r) plus a
+                                 Krylov solve of the rest in the grid's stepping precision to relative
+                                 tolerance inner_tol; repeated until the FP64 residual meets tol.
+                                 Lets FP32 stepping reach FP64 residuals and corrects approximate
+                                 (Lanczos) eigenvectors.  Needs CG, DCG or GMRES; allocates 3 (FP64
+                                 grids) or 8 (FP32 grids) more N-vectors of FP64 on first use.       */
 };
 
 typedef struct {
@@ -83,7 +92,8 @@ typedef struct {
   double tol;         /* stop when ||r||_M <= tol ||b||_M of the iterated system                  */
   int maxit;          /* maximum operator applications in the iteration                          */
   int check_every;    /* test convergence every k iterations (CG/FPI); <= 0 selects 1             */
-  int flags;          /* WHV_TRUE_RESIDUAL                                                        */
+  int flags;          /* WHV_TRUE_RESIDUAL | WHV_REFINE_FP64                                      */
+  double inner_tol;   /* WHV_REFINE_FP64: relative tolerance of each correction solve; <= 0: 1e-3 */
 } whv_params;
 
 typedef struct {
@@ -94,6 +104,8 @@ typedef struct {
   double rel_residual;       /* last recursive relative residual of the iterated system         */
   double true_rel_residual;  /* WHV_TRUE_RESIDUAL result, else -1                               */
   double seconds;            /* host wall time of the call                                      */
+  int outer_iterations;      /* WHV_REFINE_FP64 corrections (0 otherwise)                        */
+  int wave_solves_fp64;      /* wave solves stepped in FP64 (all of them on an FP64 grid)        */
 } whv_info;
 
 /* Create a box grid [lo, hi] (per direction, x first) with npts nodes per direction including
@@ -125,11 +137,30 @@ whv_status whv_time_grid(whv_grid grid, const whv_params* p, int* nt, double* dt
  *    modes with the smallest |1 - beta_h(lambda)| (ties: mode tuple (kx,ky,kz) ascending) are
  *    generated on the device (Sec. 2.3 choice of the deflation set; Sec. 4.3 eigenvectors).
  *    Requires c = 1.  Implies WHV_BASIS_EXACT.
- *  - WHV_BASIS_LANCZOS: eigenpairs computed on the device (see whv_lanczos) -- not yet built.
+ *  - WHV_BASIS_LANCZOS: eigenpairs computed on the device by whv_lanczos with m = min(N, 1024,
+ *    max(4 nd, nd + 40)) steps, FP64 stepping, V_dev = the start vector (N doubles) or NULL for
+ *    the built-in one; implies WHV_BASIS_REDEFLATE, never WHV_BASIS_EXACT.
  *  - WHV_BASIS_NONE: drop the basis.
  * flags: WHV_BASIS_EXACT, WHV_BASIS_REDEFLATE. */
 whv_status whv_set_deflation_basis(whv_grid grid, const whv_params* p, int nd, const double* V_dev,
                                    const double* lambda2_host, int mode, int flags);
+
+/* Device eigen-solve for the deflation basis (EigenWave idea, Sec. 4.1: a Krylov method on the
+ * WaveHoltz operator finds the eigenvectors of L_h whose beta_h is nearest 1 as its extremal Ritz
+ * pairs).  Runs m Lanczos steps on S_h (one f = 0 wave solve each, FP64 stepping if
+ * fp64_stepping else the grid's precision) in the M inner product from v0_dev (N doubles, device;
+ * NULL: a built-in SplitMix64 pseudo-random vector), with full FP64 re-orthogonalisation
+ * (classical Gram-Schmidt twice), takes the nd largest Ritz values of the tridiagonal matrix, forms
+ * the Ritz vectors on the device and computes lambda^2 = -<y, L_h y>_M / <y, y>_M in FP64.  The
+ * vectors (M-orthonormal) become the grid's deflation basis for p's frequency and time grid, mode
+ * WHV_BASIS_LANCZOS with `flags` (WHV_BASIS_EXACT is removed: they are approximate; pass
+ * WHV_BASIS_REDEFLATE to re-deflate operator outputs, Algorithm 2).  theta_host / resid_host
+ * (nd doubles each, may be NULL) receive the Ritz values (descending) and ||L_h y + lambda^2 y||_M /
+ * lambda^2.  Needs 1 <= nd <= m <= min(N, 1024); temporary device memory m N doubles.  Exactly
+ * degenerate eigenvalues (square grids with c = 1) yield one vector per eigenspace: use the closed
+ * form there. */
+whv_status whv_lanczos(whv_grid grid, const whv_params* p, int nd, int m, const double* v0_dev,
+                       int fp64_stepping, int flags, double* theta_host, double* resid_host);
 
 /* Read back the basis: nd (host), the mode tuples (host int[nd*dim], closed form only; else
  * zeros), lambda^2 (host double[nd]) and the vectors (device double[N*nd]); any output may be NULL. */
@@ -144,7 +175,8 @@ whv_status whv_apply_pi(whv_grid grid, const whv_params* p, const double* v_dev,
 /* Solve A u = b for forcing f (b = Pi_h(0; f)) with p->method.  With a basis set and method
  * FPI / CG / GMRES this is DEVD (Algorithm 2): f_d = f - W W^T M f, solve with b = Pi_h(0; f_d),
  * inflate u += W diag(1/(omega_eff^2 - lambda^2)) W^T M f.  With WHV_DCG it is Algorithm 4 on
- * b = Pi_h(0; f).  use_guess = 1: u_dev holds the initial guess x0 on entry (DEVD projects it
+ * b = Pi_h(0; f).  With WHV_REFINE_FP64 on an FP32-stepping grid the iteration is wrapped in
+ * FP64 residual correction (see the flag), and rel_residual is the FP64 one.  use_guess = 1: u_dev holds the initial guess x0 on entry (DEVD projects it
  * onto span(W)^perp first); use_guess = 0: x0 = 0 and u_dev is only written.  On exit u_dev holds
  * the solution.  info (host, may be NULL) receives counts and residuals.
  * Returns WHV_ERR_NOT_CONVERGED (solution still written) if maxit is reached. */

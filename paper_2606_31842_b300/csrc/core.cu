@@ -139,7 +139,8 @@ static void free_all(whv_grid g) {
   free_plan(g);
   void* ptrs[] = {g->c2, g->c2f, g->mw, g->wbuf[0], g->wbuf[1], g->wbuf[2], g->wbuf[3], g->acc, g->x, g->r, g->p, g->q,
                   g->t, g->fd, g->krylov, g->small, g->partials, g->counters, g->scal,
-                  g->basis.V, g->basis.d_coef};
+                  g->basis.V, g->basis.d_coef, g->wbuf64[0], g->wbuf64[1], g->wbuf64[2],
+                  g->wbuf64[3], g->acc64, g->xo, g->ro, g->bo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->scal_host) cudaFreeHost(g->scal_host);
@@ -322,7 +323,8 @@ whv_status whv_set_deflation_basis(whv_grid g, const whv_params* p, int nd, cons
     s = closed_form_basis(g, tg, nd, &b);
     if (s != WHV_OK) { if (b.V) cudaFree(b.V); return s; }
   } else if (mode == WHV_BASIS_LANCZOS) {
-    return fail(g, WHV_ERR_INVALID, "LANCZOS basis is not available in this build");
+    const int64_t mm = std::min<int64_t>(std::min<int64_t>(g->N, kMaxND), std::max(4 * nd, nd + 40));
+    return whv_lanczos(g, p, nd, (int)mm, V_dev, 1, flags | WHV_BASIS_REDEFLATE, nullptr, nullptr);
   } else {
     return fail(g, WHV_ERR_INVALID, "unknown basis mode");
   }

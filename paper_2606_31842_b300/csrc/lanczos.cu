@@ -1,0 +1,353 @@
+// Device eigen-solve for the deflation basis (EigenWave idea, Sec. 4.1): Lanczos on the
+// WaveHoltz operator S_h.  Eigenvectors of L_h are eigenvectors of S_h with eigenvalue
+// beta_h(lambda); the ones to deflate (lambda nearest the frequency, beta_h near 1) are the
+// top of the spectrum of S_h, so they are the extremal Ritz pairs of a Krylov space of S_h.
+//
+//  * m steps of the Lanczos recurrence in the M inner product (S_h is M-self-adjoint); every
+//    matrix-vector product is one f = 0 wave solve on the device; every new vector is
+//    re-orthogonalised against all previous ones with classical Gram-Schmidt applied twice,
+//    in FP64, with the tall-skinny contraction kernels of the deflation path.
+//  * The m x m tridiagonal matrix: its nd largest eigenvalues by Sturm-sequence bisection,
+//    their eigenvectors by inverse iteration (tridiagonal LU with partial pivoting),
+//    re-orthogonalised inside clusters (host, O(nd m)).
+//  * Ritz vectors Y = Q S on the device (k_ritz), lambda^2 = -<y, L_h y>_M / <y, y>_M with an
+//    FP64 application of L_h, residuals ||L_h y + lambda^2 y||_M / lambda^2.
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "stencil_ops.cuh"
+#include "whv_device.cuh"
+#include "whv_internal.cuh"
+
+namespace whv {
+
+// SplitMix64 (Steele, Lea and Flood, 2014) as a counter-based generator: value i of stream seed.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+__global__ void k_start_vector(double* __restrict__ v, int64_t n, uint64_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t z = splitmix64(seed * 0x100000001B3ull + (uint64_t)i);
+    v[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;   // uniform in [-1, 1)
+  }
+}
+
+// Y[:, j0 + c] = sum_k Q[:, k] S[k, j0 + c], c < JC (S column-major m x nd)
+constexpr int kRitzJC = 8;
+__global__ void __launch_bounds__(256) k_ritz(const double* __restrict__ Q, int64_t N, int m,
+                                              const double* __restrict__ S, int nd, int j0,
+                                              double* __restrict__ Y) {
+  extern __shared__ double sS[];   // m x JC
+  const int jc = min(kRitzJC, nd - j0);
+  for (int t = threadIdx.x; t < m * kRitzJC; t += blockDim.x) {
+    const int k = t / kRitzJC, c = t % kRitzJC;
+    sS[t] = c < jc ? S[(int64_t)(j0 + c) * m + k] : 0.0;
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc[kRitzJC];
+#pragma unroll
+    for (int c = 0; c < kRitzJC; ++c) acc[c] = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double q = Q[i + (int64_t)k * N];
+#pragma unroll
+      for (int c = 0; c < kRitzJC; ++c) acc[c] = fma(q, sS[k * kRitzJC + c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kRitzJC; ++c)
+      if (c < jc) Y[i + (int64_t)(j0 + c) * N] = acc[c];
+  }
+}
+
+// out = c^2 Delta_h y (FP64)
+template <int DIM, int ORDER>
+__global__ void __launch_bounds__(256) k_apply_L(const double* __restrict__ y, const double* __restrict__ c2,
+                                                 double* __restrict__ out, int nx, int ny, int nz,
+                                                 StepCoef<double> cf) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int yy = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= nx || yy >= ny) return;
+  const int64_t idx = x + (int64_t)nx * (yy + (int64_t)ny * z);
+  double L = lap<DIM, ORDER, double>(y, idx, x, yy, z, nx, ny, nz, cf, y[idx]);
+  if (c2) L *= c2[idx];
+  out[idx] = L;
+}
+
+static whv_status apply_L_fp64(whv_grid g, const double* y, double* out) {
+  StepCoef<double> cf{};
+  for (int m = 0; m < 3; ++m) {
+    const double h2 = g->h[m] * g->h[m];
+    cf.ih2[m] = g->order == 2 ? 1.0 / h2 : 1.0 / (12.0 * h2);
+  }
+  dim3 block, grid;
+  if (g->dim == 1) { block = dim3(256, 1, 1); grid = dim3((g->n[0] + 255) / 256, 1, 1); }
+  else { block = dim3(32, 8, 1); grid = dim3((g->n[0] + 31) / 32, (g->n[1] + 7) / 8, g->dim > 2 ? g->n[2] : 1); }
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  switch (g->dim * 10 + g->order) {
+    case 12: k_apply_L<1, 2><<<grid, block, 0, g->stream>>>(y, g->c2, out, nx, ny, nz, cf); break;
+    case 14: k_apply_L<1, 4><<<grid, block, 0, g->stream>>>(y, g->c2, out, nx, ny, nz, cf); break;
+    case 22: k_apply_L<2, 2><<<grid, block, 0, g->stream>>>(y, g->c2, out, nx, ny, nz, cf); break;
+    case 24: k_apply_L<2, 4><<<grid, block, 0, g->stream>>>(y, g->c2, out, nx, ny, nz, cf); break;
+    case 32: k_apply_L<3, 2><<<grid, block, 0, g->stream>>>(y, g->c2, out, nx, ny, nz, cf); break;
+    case 34: k_apply_L<3, 4><<<grid, block, 0, g->stream>>>(y, g->c2, out, nx, ny, nz, cf); break;
+    default: return fail(g, WHV_ERR_INVALID, "unsupported dim/order");
+  }
+  count_launches(1);
+  WHV_CUDA(g, cudaGetLastError());
+  return WHV_OK;
+}
+
+// ------------------------------------------------------------------ host: tridiagonal problem
+// number of eigenvalues of the symmetric tridiagonal (a, b) smaller than x (Sturm count)
+static int sturm_count(const std::vector<double>& a, const std::vector<double>& b, int k, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  const double tiny = 1e-300;
+  for (int i = 0; i < k; ++i) {
+    const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+    d = a[i] - x - (i > 0 ? bb / d : 0.0);
+    if (d == 0.0) d = -tiny;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// Solve (T - theta I) x = rhs in place with Gaussian elimination with partial pivoting.
+static void tridiag_shift_solve(const std::vector<double>& a, const std::vector<double>& b, int k,
+                                double theta, std::vector<double>& x, double tiny) {
+  std::vector<double> d(k), du(k, 0.0), du2(k, 0.0), dl(k, 0.0);
+  std::vector<int> piv(k);
+  for (int i = 0; i < k; ++i) d[i] = a[i] - theta;
+  for (int i = 0; i + 1 < k; ++i) { du[i] = b[i]; dl[i] = b[i]; }
+  for (int i = 0; i + 1 < k; ++i) {
+    if (fabs(d[i]) >= fabs(dl[i])) {
+      if (d[i] == 0.0) d[i] = tiny;
+      const double fct = dl[i] / d[i];
+      dl[i] = fct;
+      d[i + 1] -= fct * du[i];
+      piv[i] = i;
+    } else {
+      const double fct = d[i] / dl[i];
+      d[i] = dl[i];
+      dl[i] = fct;
+      const double tmp = du[i];
+      du[i] = d[i + 1];
+      d[i + 1] = tmp - fct * d[i + 1];
+      if (i + 2 < k) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -fct * du[i + 1];
+      }
+      piv[i] = i + 1;
+    }
+  }
+  if (d[k - 1] == 0.0) d[k - 1] = tiny;
+  // forward: apply row interchanges and L
+  for (int i = 0; i + 1 < k; ++i) {
+    if (piv[i] == i) {
+      x[i + 1] -= dl[i] * x[i];
+    } else {
+      const double t = x[i];
+      x[i] = x[i + 1];
+      x[i + 1] = t - dl[i] * x[i];
+    }
+  }
+  // back substitution with U (diagonal d, super du, second super du2)
+  for (int i = k - 1; i >= 0; --i) {
+    double s = x[i];
+    if (i + 1 < k) s -= du[i] * x[i + 1];
+    if (i + 2 < k) s -= du2[i] * x[i + 2];
+    x[i] = s / d[i];
+  }
+}
+
+// nd largest eigenpairs of the tridiagonal (a, b) of order k: values (descending) and
+// eigenvectors S (column-major k x nd)
+static void top_eigenpairs(const std::vector<double>& a, const std::vector<double>& b, int k, int nd,
+                           std::vector<double>& theta, std::vector<double>& S) {
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  const double tnorm = std::max(fabs(lo), fabs(hi));
+  theta.assign(nd, 0.0);
+  for (int j = 0; j < nd; ++j) {
+    // eigenvalue number k-1-j in ascending order: count(x) <= idx < count(x') ...
+    const int idx = k - 1 - j;
+    double l = lo, h = hi;
+    for (int it = 0; it < 200 && h - l > 4e-16 * tnorm; ++it) {
+      const double mid = 0.5 * (l + h);
+      if (sturm_count(a, b, k, mid) <= idx) l = mid; else h = mid;
+    }
+    theta[j] = 0.5 * (l + h);
+  }
+  S.assign((size_t)k * nd, 0.0);
+  const double tiny = 1e-14 * tnorm + 1e-300;
+  uint64_t st = 88172645463325252ull;
+  for (int j = 0; j < nd; ++j) {
+    std::vector<double> x(k);
+    for (int i = 0; i < k; ++i) {   // xorshift64 start vector
+      st ^= st << 13; st ^= st >> 7; st ^= st << 17;
+      x[i] = (double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    }
+    for (int it = 0; it < 4; ++it) {
+      tridiag_shift_solve(a, b, k, theta[j], x, tiny);
+      // orthogonalise against earlier vectors of the same cluster
+      for (int p = 0; p < j; ++p) {
+        if (fabs(theta[p] - theta[j]) > 1e-3 * tnorm) continue;
+        double dp = 0.0;
+        for (int i = 0; i < k; ++i) dp += x[i] * S[(size_t)p * k + i];
+        for (int i = 0; i < k; ++i) x[i] -= dp * S[(size_t)p * k + i];
+      }
+      double nrm = 0.0;
+      for (int i = 0; i < k; ++i) nrm += x[i] * x[i];
+      nrm = sqrt(nrm);
+      for (int i = 0; i < k; ++i) x[i] /= nrm;
+    }
+    for (int i = 0; i < k; ++i) S[(size_t)j * k + i] = x[i];
+  }
+}
+
+}  // namespace whv
+
+using namespace whv;
+
+extern "C" whv_status whv_lanczos(whv_grid g, const whv_params* p, int nd, int m, const double* v0_dev,
+                                  int fp64_stepping, int flags, double* theta_host, double* resid_host) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  TimeGridH tg;
+  whv_status s = make_time_grid(g, p, &tg);
+  if (s != WHV_OK) return s;
+  if (nd < 1 || nd > kMaxND || m < nd || m > kMaxND || m > g->N)
+    return fail(g, WHV_ERR_INVALID, "need 1 <= nd <= m <= min(N, 1024)");
+  const int prec = fp64_stepping ? WHV_FP64 : g->precision;
+  if (prec == WHV_FP64 && g->precision != WHV_FP64) {
+    s = ensure_fp64_buffers(g);
+    if (s != WHV_OK) return s;
+  }
+  const int64_t N = g->N;
+  double* Q = nullptr;
+  double* Y = nullptr;
+  double* dS = nullptr;
+  auto cleanup = [&]() {
+    if (Q) cudaFree(Q);
+    if (dS) cudaFree(dS);
+  };
+#define LZ_TRY(expr)                                \
+  do {                                              \
+    whv_status _s = (expr);                         \
+    if (_s != WHV_OK) { cleanup(); if (Y) cudaFree(Y); return _s; } \
+  } while (0)
+#define LZ_CUDA(call)                                                      \
+  do {                                                                     \
+    cudaError_t _e = (call);                                               \
+    if (_e != cudaSuccess) { cleanup(); if (Y) cudaFree(Y); return cuda_fail(g, _e, #call); } \
+  } while (0)
+  LZ_CUDA(cudaMalloc(&Q, (size_t)m * N * sizeof(double)));
+  // start vector
+  if (v0_dev) {
+    LZ_CUDA(cudaMemcpyAsync(Q, v0_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+  } else {
+    k_start_vector<<<148 * 4, 256, 0, g->stream>>>(Q, N, 1ull);
+    count_launches(1);
+    LZ_CUDA(cudaGetLastError());
+  }
+  LZ_TRY(dot_async(g, Q, Q, S_TMP));
+  LZ_TRY(fetch_scalars(g));
+  if (!(g->scal_host[S_TMP] > 0.0)) { cleanup(); return fail(g, WHV_ERR_INVALID, "zero start vector"); }
+  LZ_TRY(axpby(g, N, 1.0 / sqrt(g->scal_host[S_TMP]), Q, 0.0, Q));
+  std::vector<double> alpha(m, 0.0), beta(m, 0.0), h1(m), h2(m);
+  int k = 0;
+  for (int j = 0; j < m; ++j) {
+    double* qj = Q + (size_t)j * N;
+    double* z = j + 1 < m ? Q + (size_t)(j + 1) * N : g->q;
+    // z = S_h q_j through fixed buffers, so that every step replays one cached CUDA graph
+    LZ_CUDA(cudaMemcpyAsync(g->p, qj, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    LZ_TRY(wave_solve(g, tg, g->p, nullptr, g->t, 0, prec));
+    LZ_CUDA(cudaMemcpyAsync(z, g->t, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    LZ_TRY(project(g, Q, j + 1, z, g->small));
+    LZ_TRY(expand(g, Q, j + 1, g->small, -1.0, z));
+    cudaMemcpyAsync(h1.data(), g->small, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+    LZ_TRY(project(g, Q, j + 1, z, g->small));
+    LZ_TRY(expand(g, Q, j + 1, g->small, -1.0, z));
+    cudaMemcpyAsync(h2.data(), g->small, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+    LZ_TRY(dot_async(g, z, z, S_TMP));
+    LZ_TRY(fetch_scalars(g));   // synchronises: h1, h2 are on the host too
+    alpha[j] = h1[j] + h2[j];
+    k = j + 1;
+    const double bn = sqrt(g->scal_host[S_TMP]);
+    if (!isfinite(bn)) { cleanup(); return fail(g, WHV_ERR_BREAKDOWN, "non-finite Lanczos vector"); }
+    if (j + 1 < m) {
+      beta[j] = bn;
+      if (!(bn > 1e-14)) break;   // invariant subspace found
+      LZ_TRY(axpby(g, N, 1.0 / bn, z, 0.0, z));
+    }
+  }
+  if (k < nd) { cleanup(); return fail(g, WHV_ERR_INVALID, "Krylov space smaller than nd (invariant subspace)"); }
+  std::vector<double> theta, S;
+  top_eigenpairs(alpha, beta, k, nd, theta, S);
+  LZ_CUDA(cudaMalloc(&dS, S.size() * sizeof(double)));
+  LZ_CUDA(cudaMemcpyAsync(dS, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+  LZ_CUDA(cudaMalloc(&Y, (size_t)nd * N * sizeof(double)));
+  LZ_CUDA(cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kMaxND * kRitzJC * sizeof(double))));
+  for (int j0 = 0; j0 < nd; j0 += kRitzJC) {
+    const int blocks = (int)std::min<int64_t>((N + 255) / 256, 148 * 8);
+    k_ritz<<<blocks, 256, (size_t)k * kRitzJC * sizeof(double), g->stream>>>(Q, N, k, dS, nd, j0, Y);
+    count_launches(1);
+    LZ_CUDA(cudaGetLastError());
+  }
+  LZ_CUDA(cudaStreamSynchronize(g->stream));
+  cleanup();
+  Q = nullptr; dS = nullptr;
+  // Rayleigh quotients and residuals with L_h in FP64
+  std::vector<double> lam2(nd), res(nd);
+  for (int j = 0; j < nd; ++j) {
+    const double* y = Y + (size_t)j * N;
+    LZ_TRY(apply_L_fp64(g, y, g->q));
+    LZ_TRY(dot_async(g, y, g->q, S_TMP));
+    LZ_TRY(dot_async(g, y, y, S_TMP2));
+    LZ_TRY(fetch_scalars(g));
+    lam2[j] = -g->scal_host[S_TMP] / g->scal_host[S_TMP2];
+    LZ_TRY(axpby(g, N, lam2[j], y, 1.0, g->q));   // q = L y + lambda^2 y
+    LZ_TRY(dot_async(g, g->q, g->q, S_TMP));
+    LZ_TRY(fetch_scalars(g));
+    res[j] = sqrt(g->scal_host[S_TMP]) / fabs(lam2[j]);
+  }
+  if (theta_host) std::copy(theta.begin(), theta.end(), theta_host);
+  if (resid_host) std::copy(res.begin(), res.end(), resid_host);
+  // install as the deflation basis (approximate eigenvectors)
+  Basis b;
+  b.nd = nd; b.mode = WHV_BASIS_LANCZOS; b.flags = flags & ~WHV_BASIS_EXACT;
+  b.omega = p->omega; b.periods = p->periods; b.adjust = p->adjust_omega ? 1 : 0; b.cfl = tg.cfl;
+  b.V = Y;
+  b.lambda2 = lam2;
+  b.mu.resize(nd);
+  for (int j = 0; j < nd; ++j) {
+    const double x = 1.0 - 0.5 * tg.dt * tg.dt * lam2[j];
+    const double th = acos(std::max(-1.0, std::min(1.0, x)));
+    double be = 0.0;
+    for (int n = 0; n <= tg.nt; ++n) be += tg.weight[n] * cos(n * th);
+    b.mu[j] = 1.0 - be;
+  }
+  b.modes.assign((size_t)nd * g->dim, 0);
+  cudaError_t e = cudaMalloc(&b.d_coef, (size_t)kMaxND * sizeof(double));
+  if (e != cudaSuccess) { cudaFree(Y); return cuda_fail(g, e, "cudaMalloc"); }
+  if (g->basis.V) cudaFree(g->basis.V);
+  if (g->basis.d_coef) cudaFree(g->basis.d_coef);
+  g->basis = std::move(b);
+#undef LZ_TRY
+#undef LZ_CUDA
+  return WHV_OK;
+}

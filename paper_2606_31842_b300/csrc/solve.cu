@@ -13,8 +13,15 @@
 //    contraction kernels on the Krylov basis), Givens rotations and the triangular solve on the
 //    host (m <= 30 scalars per step).
 //  * FPI (Algorithm 1).
+//  * FP64 residual correction (WHV_REFINE_FP64): the outer loop forms the residual r = b - A x of
+//    the full system with FP64 wave solves; the correction is the modal solve of its deflated
+//    components plus an inner Krylov solve (grid's stepping, FP64 reductions) of the rest to a
+//    loose relative tolerance -- iterative refinement, so the FP64 residual reaches tol although
+//    one FP32-stepped application of A is only accurate to ~1e-6, and approximate (Lanczos)
+//    eigenvectors are corrected instead of leaving their error in the inflated solution.
 #include <math.h>
 
+#include <algorithm>
 #include <chrono>
 #include <vector>
 
@@ -25,7 +32,9 @@ namespace whv {
 struct SolveCtx {
   whv_grid g;
   const TimeGridH& tg;
-  int ws = 0;
+  bool redefl;
+  int ws = 0;      // wave solves in the grid's precision
+  int ws64 = 0;    // FP64 wave solves of the residual correction
 };
 
 static whv_status copy_dev(whv_grid g, double* dst, const double* src, int64_t n) {
@@ -59,12 +68,12 @@ static whv_status deflate_vec(whv_grid g, double* vec) {
   return expand(g, B.V, B.nd, g->small, -1.0, vec);
 }
 
-// q = A v (+ re-deflation); scal[S_PQ] = <v, q>_M
-static whv_status apply_A(SolveCtx& c, const double* v, double* q, bool redefl) {
+// q = A v (+ re-deflation) in the grid's stepping precision; scal[S_PQ] = <v, q>_M
+static whv_status apply_A(SolveCtx& c, const double* v, double* q) {
   whv_grid g = c.g;
   TRY(wave_solve(g, c.tg, v, nullptr, q, 1));
   c.ws++;
-  if (redefl) {
+  if (c.redefl) {
     TRY(deflate_vec(g, q));
     TRY(dot_async(g, v, q, S_PQ));
   }
@@ -73,6 +82,172 @@ static whv_status apply_A(SolveCtx& c, const double* v, double* q, bool redefl) 
 
 static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct InnerResult {
+  int iters = 0;
+  bool converged = false, breakdown = false;
+  double rel = 1.0;
+};
+
+// Krylov solve of A x = b (b: device, FP64, ||b||_M^2 = bb) into g->x, in the grid's stepping
+// precision.  use_x0: g->x holds the initial guess, else x0 = 0.  fpi_force: forcing of the
+// FPI map (FPI iterates x <- Pi_h(x; f) and does not use b except for its norm).
+static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, const double* b,
+                              double bb, bool use_x0, double tol, int maxit,
+                              const double* fpi_force, InnerResult* res) {
+  whv_grid g = c.g;
+  const int64_t N = g->N;
+  const Basis& B = g->basis;
+  const int check = p->check_every > 0 ? p->check_every : 1;
+  InnerResult R;
+  if (use_x0) {
+    TRY(apply_A(c, g->x, g->q));
+    TRY(copy_dev(g, g->r, b, N));
+    TRY(axpby(g, N, -1.0, g->q, 1.0, g->r));
+  } else {
+    WHV_CUDA(g, cudaMemsetAsync(g->x, 0, N * sizeof(double), g->stream));
+    TRY(copy_dev(g, g->r, b, N));
+  }
+  if (bb == 0.0) {
+    R.converged = true;
+    R.rel = 0.0;
+    *res = R;
+    return WHV_OK;
+  }
+  if (method == WHV_CG || method == WHV_DCG) {
+    double rr0 = bb;
+    if (method == WHV_DCG) {
+      // x_0 = x_{-1} + W diag(1/mu) W^T M r_{-1};  r_0 = r_{-1} - W W^T M r_{-1}  (A W = W diag(mu))
+      std::vector<double> cf(B.nd), y(B.nd);
+      TRY(project(g, B.V, B.nd, g->r, g->small));
+      TRY(to_host(g, cf.data(), g->small, B.nd));
+      for (int m = 0; m < B.nd; ++m) y[m] = cf[m] / B.mu[m];
+      TRY(to_dev(g, g->small, y.data(), B.nd));
+      TRY(expand(g, B.V, B.nd, g->small, 1.0, g->x));
+      TRY(to_dev(g, g->small, cf.data(), B.nd));
+      TRY(expand(g, B.V, B.nd, g->small, -1.0, g->r));
+    }
+    TRY(copy_dev(g, g->p, g->r, N));
+    TRY(dot_async(g, g->r, g->r, S_RR));
+    WHV_CUDA(g, cudaMemsetAsync(g->scal + S_FLAG, 0, sizeof(double), g->stream));
+    TRY(fetch_scalars(g));
+    const double rrs = g->scal_host[S_RR];
+    if (method == WHV_DCG) rr0 = rrs;  // Algorithm 4: relative to the deflated start residual
+    R.rel = rr0 > 0.0 ? sqrt(rrs / rr0) : 0.0;
+    if (R.rel <= tol) R.converged = true;
+    while (!R.converged && R.iters < maxit) {
+      TRY(apply_A(c, g->p, g->q));
+      TRY(cg_update(g));
+      TRY(cg_direction(g));
+      ++R.iters;
+      if (R.iters % check == 0 || R.iters == maxit) {
+        TRY(fetch_scalars(g));
+        if (g->scal_host[S_FLAG] != 0.0) { R.breakdown = true; break; }
+        R.rel = sqrt(g->scal_host[S_RR] / rr0);
+        if (R.rel <= tol) R.converged = true;
+      }
+    }
+  } else if (method == WHV_GMRES) {
+    const int m = p->restart > 0 ? p->restart : 30;
+    if (m + 1 > kMaxND) return fail(g, WHV_ERR_INVALID, "GMRES restart too large");
+    if (g->krylov_cols < m + 1) {
+      if (g->krylov) cudaFree(g->krylov);
+      g->krylov = nullptr;
+      g->krylov_cols = 0;
+      WHV_CUDA(g, cudaMalloc(&g->krylov, (size_t)(m + 1) * N * sizeof(double)));
+      g->krylov_cols = m + 1;
+    }
+    double* K = g->krylov;
+    const double bnorm = sqrt(bb);
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), h1(m + 1), h2(m + 1), y(m);
+    auto Hc = [&](int i, int j) -> double& { return H[(size_t)j * (m + 1) + i]; };
+    while (true) {
+      TRY(dot_async(g, g->r, g->r, S_TMP));
+      TRY(fetch_scalars(g));
+      const double beta0 = sqrt(g->scal_host[S_TMP]);
+      if (!isfinite(beta0)) { R.breakdown = true; break; }
+      R.rel = beta0 / bnorm;
+      if (R.rel <= tol) { R.converged = true; break; }
+      if (R.iters >= maxit) break;
+      TRY(axpby(g, N, 1.0 / beta0, g->r, 0.0, K));
+      std::fill(H.begin(), H.end(), 0.0);
+      std::fill(gv.begin(), gv.end(), 0.0);
+      gv[0] = beta0;
+      int k = 0;
+      bool lucky = false;
+      for (int j = 0; j < m; ++j) {
+        double* w = K + (size_t)(j + 1) * N;
+        TRY(apply_A(c, K + (size_t)j * N, w));
+        ++R.iters;
+        // classical Gram-Schmidt, twice
+        TRY(project(g, K, j + 1, w, g->small));
+        TRY(expand(g, K, j + 1, g->small, -1.0, w));
+        TRY(to_host(g, h1.data(), g->small, j + 1));
+        TRY(project(g, K, j + 1, w, g->small));
+        TRY(expand(g, K, j + 1, g->small, -1.0, w));
+        TRY(to_host(g, h2.data(), g->small, j + 1));
+        for (int i = 0; i <= j; ++i) Hc(i, j) = h1[i] + h2[i];
+        TRY(dot_async(g, w, w, S_TMP));
+        TRY(fetch_scalars(g));
+        const double hn = sqrt(g->scal_host[S_TMP]);
+        if (!isfinite(hn)) { R.breakdown = true; break; }
+        Hc(j + 1, j) = hn;
+        lucky = !(hn > 0.0);
+        if (!lucky) TRY(axpby(g, N, 1.0 / hn, w, 0.0, w));
+        for (int i = 0; i < j; ++i) {
+          const double t = cs[i] * Hc(i, j) + sn[i] * Hc(i + 1, j);
+          Hc(i + 1, j) = -sn[i] * Hc(i, j) + cs[i] * Hc(i + 1, j);
+          Hc(i, j) = t;
+        }
+        const double den = hypot(Hc(j, j), Hc(j + 1, j));
+        if (!(den > 0.0)) { R.breakdown = true; break; }
+        cs[j] = Hc(j, j) / den;
+        sn[j] = Hc(j + 1, j) / den;
+        Hc(j, j) = den;
+        Hc(j + 1, j) = 0.0;
+        gv[j + 1] = -sn[j] * gv[j];
+        gv[j] = cs[j] * gv[j];
+        k = j + 1;
+        R.rel = fabs(gv[k]) / bnorm;
+        if (R.rel <= tol || R.iters >= maxit || lucky) break;
+      }
+      if (R.breakdown && k == 0) break;
+      for (int i = k - 1; i >= 0; --i) {
+        double s = gv[i];
+        for (int l = i + 1; l < k; ++l) s -= Hc(i, l) * y[l];
+        y[i] = s / Hc(i, i);
+      }
+      TRY(to_dev(g, g->small, y.data(), k));
+      TRY(expand(g, K, k, g->small, 1.0, g->x));
+      if (R.breakdown) break;
+      if (R.rel <= tol || lucky) { R.converged = true; break; }
+      // restart: r = b - A x
+      TRY(apply_A(c, g->x, g->q));
+      TRY(copy_dev(g, g->r, b, N));
+      TRY(axpby(g, N, -1.0, g->q, 1.0, g->r));
+    }
+  } else {  // FPI, Algorithm 1: x <- Pi_h(x; f_d)
+    const double bnorm = sqrt(bb);
+    while (R.iters < maxit) {
+      TRY(wave_solve(g, c.tg, g->x, fpi_force, g->q, 0));
+      c.ws++;
+      if (c.redefl) TRY(deflate_vec(g, g->q));
+      TRY(copy_dev(g, g->r, g->q, N));
+      TRY(axpby(g, N, -1.0, g->x, 1.0, g->r));
+      TRY(copy_dev(g, g->x, g->q, N));
+      ++R.iters;
+      if (R.iters % check == 0 || R.iters == maxit) {
+        TRY(dot_async(g, g->r, g->r, S_TMP));
+        TRY(fetch_scalars(g));
+        R.rel = sqrt(g->scal_host[S_TMP]) / bnorm;
+        if (!isfinite(R.rel)) { R.breakdown = true; break; }
+        if (R.rel <= tol) { R.converged = true; break; }
+      }
+    }
+  }
+  *res = R;
+  return WHV_OK;
 }
 
 }  // namespace whv
@@ -97,182 +272,104 @@ extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f
   if (method == WHV_DCG && !has_basis) return fail(g, WHV_ERR_INVALID, "DCG needs a deflation basis");
   if (method == WHV_DCG && !(B.flags & WHV_BASIS_EXACT))
     return fail(g, WHV_ERR_INVALID, "DCG is built for exact eigenvector bases (WHV_BASIS_EXACT)");
+  const bool refine = (p->flags & WHV_REFINE_FP64) != 0;
+  if (refine && method == WHV_FPI)
+    return fail(g, WHV_ERR_INVALID, "FP64 residual correction needs a Krylov method (CG, DCG, GMRES)");
   const bool devd = has_basis && method != WHV_DCG;
-  const bool redefl = has_basis && (B.flags & WHV_BASIS_REDEFLATE);
-  const int check = p->check_every > 0 ? p->check_every : 1;
   const int64_t N = g->N;
-  SolveCtx c{g, tg};
+  SolveCtx c{g, tg, has_basis && (B.flags & WHV_BASIS_REDEFLATE) != 0};
   double* b = g->t;  // b of the iterated system
 
   // ---- forcing (Algorithm 2: deflate the forcing)
   const double* fuse = f;
-  if (devd) {
+  if (devd && !refine) {
     TRY(project(g, B.V, B.nd, f, B.d_coef));
     TRY(copy_dev(g, g->fd, f, N));
     TRY(expand(g, B.V, B.nd, B.d_coef, -1.0, g->fd));
     fuse = g->fd;
   }
-  TRY(wave_solve(g, tg, nullptr, fuse, b, 0));
-  c.ws++;
-  TRY(dot_async(g, b, b, S_RR0));
-  TRY(fetch_scalars(g));
-  double bb = g->scal_host[S_RR0];
-  if (!isfinite(bb)) return fail(g, WHV_ERR_BREAKDOWN, "non-finite right-hand side b (NaN/Inf in f?)");
 
-  // ---- initial guess
-  if (use_guess) {
-    TRY(copy_dev(g, g->x, u, N));
-    if (devd) TRY(deflate_vec(g, g->x));
-    TRY(apply_A(c, g->x, g->q, redefl));
-    TRY(copy_dev(g, g->r, b, N));
-    TRY(axpby(g, N, -1.0, g->q, 1.0, g->r));
-  } else {
-    WHV_CUDA(g, cudaMemsetAsync(g->x, 0, N * sizeof(double), g->stream));
-    TRY(copy_dev(g, g->r, b, N));
-  }
-
-  int iters = 0;
-  bool converged = false, breakdown = false;
-  double rel = 1.0;
-
-  if (bb == 0.0) {
-    converged = true;
-    rel = 0.0;
-  } else if (method == WHV_CG || method == WHV_DCG) {
-    double rr0 = bb;
-    if (method == WHV_DCG) {
-      // x_0 = x_{-1} + W diag(1/mu) W^T M r_{-1};  r_0 = r_{-1} - W W^T M r_{-1}  (A W = W diag(mu))
-      std::vector<double> cf(B.nd);
-      TRY(project(g, B.V, B.nd, g->r, g->small));
-      TRY(to_host(g, cf.data(), g->small, B.nd));
-      std::vector<double> y(B.nd);
-      for (int m = 0; m < B.nd; ++m) y[m] = cf[m] / B.mu[m];
-      TRY(to_dev(g, g->small, y.data(), B.nd));
-      TRY(expand(g, B.V, B.nd, g->small, 1.0, g->x));
-      TRY(to_dev(g, g->small, cf.data(), B.nd));
-      TRY(expand(g, B.V, B.nd, g->small, -1.0, g->r));
-    }
-    TRY(copy_dev(g, g->p, g->r, N));
-    TRY(dot_async(g, g->r, g->r, S_RR));
+  InnerResult R;
+  int outer = 0;
+  if (!refine) {
+    TRY(wave_solve(g, tg, nullptr, fuse, b, 0));
+    c.ws++;
+    TRY(dot_async(g, b, b, S_RR0));
     TRY(fetch_scalars(g));
-    const double rrs = g->scal_host[S_RR];
-    if (method == WHV_DCG) rr0 = rrs;  // Algorithm 4: relative to the deflated start residual
-    WHV_CUDA(g, cudaMemsetAsync(g->scal + S_FLAG, 0, sizeof(double), g->stream));
-    rel = rr0 > 0.0 ? sqrt(rrs / rr0) : 0.0;
-    if (rel <= p->tol) converged = true;
-    while (!converged && iters < p->maxit) {
-      TRY(apply_A(c, g->p, g->q, redefl));
-      TRY(cg_update(g));
-      TRY(cg_direction(g));
-      ++iters;
-      if (iters % check == 0 || iters == p->maxit) {
-        TRY(fetch_scalars(g));
-        if (g->scal_host[S_FLAG] != 0.0) { breakdown = true; break; }
-        rel = sqrt(g->scal_host[S_RR] / rr0);
-        if (rel <= p->tol) converged = true;
-      }
+    const double bb = g->scal_host[S_RR0];
+    if (!isfinite(bb)) return fail(g, WHV_ERR_BREAKDOWN, "non-finite right-hand side b (NaN/Inf in f?)");
+    if (use_guess) {
+      TRY(copy_dev(g, g->x, u, N));
+      if (devd) TRY(deflate_vec(g, g->x));
     }
-  } else if (method == WHV_GMRES) {
-    const int m = p->restart > 0 ? p->restart : 30;
-    if (m + 1 > kMaxND) return fail(g, WHV_ERR_INVALID, "GMRES restart too large");
-    if (g->krylov_cols < m + 1) {
-      if (g->krylov) cudaFree(g->krylov);
-      g->krylov = nullptr;
-      g->krylov_cols = 0;
-      WHV_CUDA(g, cudaMalloc(&g->krylov, (size_t)(m + 1) * N * sizeof(double)));
-      g->krylov_cols = m + 1;
-    }
-    double* K = g->krylov;
-    const double bnorm = sqrt(bb);
-    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), h1(m + 1), h2(m + 1), y(m);
-    auto Hc = [&](int i, int j) -> double& { return H[(size_t)j * (m + 1) + i]; };
+    TRY(inner_solve(c, method, p, b, bb, use_guess != 0, p->tol, p->maxit, fuse, &R));
+  } else {
+    // ---- iterative refinement with FP64 residuals on the full system b = Pi_h(0; f):
+    // each correction d = W diag(1/mu) W^T M r (the deflated components, Algorithm 2's
+    // modal solution in terms of A) + a Krylov solve of the projected residual r - W W^T M r.
+    // With exact eigenvectors the first pass is DEVD; with approximate ones the outer loop
+    // corrects what the modal part gets wrong.
+    TRY(ensure_fp64_buffers(g));
+    TRY(wave_solve(g, tg, nullptr, f, g->bo, 0, WHV_FP64));
+    c.ws64++;
+    TRY(dot_async(g, g->bo, g->bo, S_RR0));
+    TRY(fetch_scalars(g));
+    const double bb = g->scal_host[S_RR0];
+    if (!isfinite(bb)) return fail(g, WHV_ERR_BREAKDOWN, "non-finite right-hand side b (NaN/Inf in f?)");
+    const double inner_tol = p->inner_tol > 0.0 ? p->inner_tol : 1e-3;
+    if (use_guess) TRY(copy_dev(g, g->xo, u, N));
+    else WHV_CUDA(g, cudaMemsetAsync(g->xo, 0, N * sizeof(double), g->stream));
+    bool have_x = use_guess != 0;
+    int its = 0;
+    R.rel = 1.0;
+    std::vector<double> cf(has_basis ? B.nd : 0);
     while (true) {
-      TRY(dot_async(g, g->r, g->r, S_TMP));
+      // r = b - A x in FP64 (x = 0: r = b)
+      if (have_x) {
+        TRY(wave_solve(g, tg, g->xo, nullptr, g->q, 1, WHV_FP64));
+        c.ws64++;
+        TRY(copy_dev(g, g->ro, g->bo, N));
+        TRY(axpby(g, N, -1.0, g->q, 1.0, g->ro));
+      } else {
+        TRY(copy_dev(g, g->ro, g->bo, N));
+      }
+      TRY(dot_async(g, g->ro, g->ro, S_TMP2));
       TRY(fetch_scalars(g));
-      const double beta0 = sqrt(g->scal_host[S_TMP]);
-      if (!isfinite(beta0)) { breakdown = true; break; }
-      rel = beta0 / bnorm;
-      if (rel <= p->tol) { converged = true; break; }
-      if (iters >= p->maxit) break;
-      TRY(axpby(g, N, 1.0 / beta0, g->r, 0.0, K));
-      std::fill(H.begin(), H.end(), 0.0);
-      std::fill(gv.begin(), gv.end(), 0.0);
-      gv[0] = beta0;
-      int k = 0;
-      bool lucky = false;
-      for (int j = 0; j < m; ++j) {
-        double* w = K + (size_t)(j + 1) * N;
-        TRY(apply_A(c, K + (size_t)j * N, w, redefl));
-        ++iters;
-        // classical Gram-Schmidt, twice
-        TRY(project(g, K, j + 1, w, g->small));
-        TRY(expand(g, K, j + 1, g->small, -1.0, w));
-        TRY(to_host(g, h1.data(), g->small, j + 1));
-        TRY(project(g, K, j + 1, w, g->small));
-        TRY(expand(g, K, j + 1, g->small, -1.0, w));
-        TRY(to_host(g, h2.data(), g->small, j + 1));
-        for (int i = 0; i <= j; ++i) Hc(i, j) = h1[i] + h2[i];
-        TRY(dot_async(g, w, w, S_TMP));
-        TRY(fetch_scalars(g));
-        const double hn = sqrt(g->scal_host[S_TMP]);
-        if (!isfinite(hn)) { breakdown = true; break; }
-        Hc(j + 1, j) = hn;
-        lucky = !(hn > 0.0);
-        if (!lucky) TRY(axpby(g, N, 1.0 / hn, w, 0.0, w));
-        for (int i = 0; i < j; ++i) {
-          const double t = cs[i] * Hc(i, j) + sn[i] * Hc(i + 1, j);
-          Hc(i + 1, j) = -sn[i] * Hc(i, j) + cs[i] * Hc(i + 1, j);
-          Hc(i, j) = t;
-        }
-        const double den = hypot(Hc(j, j), Hc(j + 1, j));
-        if (!(den > 0.0)) { breakdown = true; break; }
-        cs[j] = Hc(j, j) / den;
-        sn[j] = Hc(j + 1, j) / den;
-        Hc(j, j) = den;
-        Hc(j + 1, j) = 0.0;
-        gv[j + 1] = -sn[j] * gv[j];
-        gv[j] = cs[j] * gv[j];
-        k = j + 1;
-        rel = fabs(gv[k]) / bnorm;
-        if (rel <= p->tol || iters >= p->maxit || lucky) break;
+      R.rel = sqrt(g->scal_host[S_TMP2] / bb);
+      if (!isfinite(R.rel)) { R.breakdown = true; break; }
+      if (R.rel <= p->tol) { R.converged = true; break; }
+      if (its >= p->maxit || outer >= 50) break;
+      if (devd) {
+        // deflated components: x += W diag(1/mu) c, r -= W c, c = W^T M r
+        TRY(project(g, B.V, B.nd, g->ro, g->small));
+        TRY(to_host(g, cf.data(), g->small, B.nd));
+        std::vector<double> y(B.nd);
+        for (int m = 0; m < B.nd; ++m) y[m] = cf[m] / B.mu[m];
+        TRY(to_dev(g, g->small, y.data(), B.nd));
+        TRY(expand(g, B.V, B.nd, g->small, 1.0, g->xo));
+        TRY(to_dev(g, g->small, cf.data(), B.nd));
+        TRY(expand(g, B.V, B.nd, g->small, -1.0, g->ro));
       }
-      if (breakdown && k == 0) break;
-      for (int i = k - 1; i >= 0; --i) {
-        double s = gv[i];
-        for (int l = i + 1; l < k; ++l) s -= Hc(i, l) * y[l];
-        y[i] = s / Hc(i, i);
-      }
-      TRY(to_dev(g, g->small, y.data(), k));
-      TRY(expand(g, K, k, g->small, 1.0, g->x));
-      if (breakdown) break;
-      if (rel <= p->tol || lucky) { converged = true; break; }
-      // restart: r = b - A x
-      TRY(apply_A(c, g->x, g->q, redefl));
-      TRY(copy_dev(g, g->r, b, N));
-      TRY(axpby(g, N, -1.0, g->q, 1.0, g->r));
+      TRY(dot_async(g, g->ro, g->ro, S_TMP2));
+      TRY(fetch_scalars(g));
+      const double rr = g->scal_host[S_TMP2];
+      // correction of the rest: A d = r with the grid's stepping, relative tolerance inner_tol
+      // (never tighter than the outer target needs)
+      InnerResult Ri;
+      const double itol = std::max(inner_tol, 0.5 * p->tol / std::max(R.rel, 1e-300));
+      TRY(inner_solve(c, method, p, g->ro, rr, false, itol, p->maxit - its, nullptr, &Ri));
+      its += Ri.iters;
+      ++outer;
+      if (Ri.breakdown) { R.breakdown = true; break; }
+      TRY(axpby(g, N, 1.0, g->x, 1.0, g->xo));
+      have_x = true;
     }
-  } else {  // FPI, Algorithm 1: v <- Pi_h(v; f_d)
-    const double bnorm = sqrt(bb);
-    while (iters < p->maxit) {
-      TRY(wave_solve(g, tg, g->x, fuse, g->q, 0));
-      c.ws++;
-      if (redefl) TRY(deflate_vec(g, g->q));
-      TRY(copy_dev(g, g->r, g->q, N));
-      TRY(axpby(g, N, -1.0, g->x, 1.0, g->r));
-      TRY(copy_dev(g, g->x, g->q, N));
-      ++iters;
-      if (iters % check == 0 || iters == p->maxit) {
-        TRY(dot_async(g, g->r, g->r, S_TMP));
-        TRY(fetch_scalars(g));
-        rel = sqrt(g->scal_host[S_TMP]) / bnorm;
-        if (!isfinite(rel)) { breakdown = true; break; }
-        if (rel <= p->tol) { converged = true; break; }
-      }
-    }
+    R.iters = its;
+    TRY(copy_dev(g, g->x, g->xo, N));
   }
 
   // ---- inflate (Algorithm 2): u = x + W diag(1/(omega_eff^2 - lambda^2)) W^T M f
-  if (devd) {
+  if (devd && !refine) {
     std::vector<double> cf(B.nd);
     TRY(to_host(g, cf.data(), B.d_coef, B.nd));
     const double om2 = tg.omega_eff * tg.omega_eff;
@@ -284,30 +381,33 @@ extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f
 
   double true_rel = -1.0;
   if (p->flags & WHV_TRUE_RESIDUAL) {
-    // ||Pi_h(u; f) - u|| / ||Pi_h(0; f)||
-    TRY(wave_solve(g, tg, u, f, g->q, 0));
+    // ||Pi_h(u; f) - u|| / ||Pi_h(0; f)||, in FP64 when the grid has FP64 buffers
+    const int tp = (refine || g->precision == WHV_FP64) ? WHV_FP64 : g->precision;
+    TRY(wave_solve(g, tg, u, f, g->q, 0, tp));
     TRY(copy_dev(g, g->r, g->q, N));
     TRY(axpby(g, N, -1.0, u, 1.0, g->r));
     TRY(dot_async(g, g->r, g->r, S_TMP));
-    TRY(wave_solve(g, tg, nullptr, f, g->q, 0));
+    TRY(wave_solve(g, tg, nullptr, f, g->q, 0, tp));
     TRY(dot_async(g, g->q, g->q, S_TMP2));
-    c.ws += 2;
+    if (tp == WHV_FP64 && g->precision != WHV_FP64) c.ws64 += 2; else c.ws += 2;
     TRY(fetch_scalars(g));
     true_rel = sqrt(g->scal_host[S_TMP] / g->scal_host[S_TMP2]);
   }
   WHV_CUDA(g, cudaStreamSynchronize(g->stream));
   if (info) {
-    info->iterations = iters;
-    info->wave_solves = c.ws;
+    info->iterations = R.iters;
+    info->wave_solves = c.ws + c.ws64;
     info->nt = tg.nt;
     info->dt = tg.dt;
     info->omega_hat = tg.omega_hat;
     info->omega_eff = tg.omega_eff;
-    info->rel_residual = rel;
+    info->rel_residual = R.rel;
     info->true_rel_residual = true_rel;
     info->seconds = now_s() - t0;
+    info->outer_iterations = outer;
+    info->wave_solves_fp64 = (g->precision == WHV_FP64) ? c.ws + c.ws64 : c.ws64;
   }
-  if (breakdown) return fail(g, WHV_ERR_BREAKDOWN, "Krylov breakdown (non-finite or non-positive scalar)");
-  if (!converged) return fail(g, WHV_ERR_NOT_CONVERGED, "maxit reached before the tolerance");
+  if (R.breakdown) return fail(g, WHV_ERR_BREAKDOWN, "Krylov breakdown (non-finite or non-positive scalar)");
+  if (!R.converged) return fail(g, WHV_ERR_NOT_CONVERGED, "maxit reached before the tolerance");
   return WHV_OK;
 }

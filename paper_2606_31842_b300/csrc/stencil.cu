@@ -17,44 +17,13 @@
 
 #include <vector>
 
+#include "stencil_ops.cuh"
 #include "whv_device.cuh"
 #include "whv_internal.cuh"
 
 namespace whv {
 
-template <typename T>
-struct StepCoef {
-  T ih2[3];   // 1/h^2 per direction (order 4: 1/(12 h^2))
-  T dt2;      // dt^2
-  T fph;      // cos(omega_hat t^n) of the step (first step: 1)
-  T w0, w1;   // first step: w_0, w_1; other steps: w1 = w_{n+1}
-};
-
 enum Kind { K_STEP = 0, K_LAST_OUT = 1, K_LAST_AV = 2 };
-
-// Second difference along one axis at interior index i of n, without the 1/h^2 factor.
-// Dirichlet nodes hold 0; order 4 uses the odd reflection u_{-1} = -u_1 beyond the boundary.
-template <int ORDER, typename T, typename S>
-__device__ __forceinline__ T d2(const S* __restrict__ w, int64_t idx, int i, int n, int64_t s, T c) {
-  const T m1 = (i > 0) ? (T)__ldg(w + idx - s) : T(0);
-  const T p1 = (i < n - 1) ? (T)__ldg(w + idx + s) : T(0);
-  if (ORDER == 2) {
-    return fma(T(-2), c, m1 + p1);
-  } else {
-    const T m2 = (i > 1) ? (T)__ldg(w + idx - 2 * s) : (i == 1 ? T(0) : -c);
-    const T p2 = (i < n - 2) ? (T)__ldg(w + idx + 2 * s) : (i == n - 2 ? T(0) : -c);
-    return fma(T(-30), c, fma(T(16), m1 + p1, -(m2 + p2)));
-  }
-}
-
-template <int DIM, int ORDER, typename T, typename S>
-__device__ __forceinline__ T lap(const S* __restrict__ w, int64_t idx, int x, int y, int z, int nx,
-                                 int ny, int nz, const StepCoef<T>& cf, T c) {
-  T l = d2<ORDER, T>(w, idx, x, nx, 1, c) * cf.ih2[0];
-  if (DIM > 1) l = fma(d2<ORDER, T>(w, idx, y, ny, (int64_t)nx, c), cf.ih2[1], l);
-  if (DIM > 2) l = fma(d2<ORDER, T>(w, idx, z, nz, (int64_t)nx * ny, c), cf.ih2[2], l);
-  return l;
-}
 
 // First step from W^0 = v (FP64 in; nullptr => 0).  Writes W^0 -> w0, W^1 -> w1, acc.
 template <typename T, int DIM, int ORDER, bool VARC, bool FORCE, bool ZERO_V>
@@ -98,10 +67,25 @@ __global__ void __launch_bounds__(256) k_step(const T* __restrict__ wc, T* __res
   if (in) {
     const int64_t idx = x + (int64_t)nx * (y + (int64_t)ny * z);
     const T c = __ldg(wc + idx);
-    T L = lap<DIM, ORDER, T>(wc, idx, x, y, z, nx, ny, nz, cf, c);
-    if (VARC) L *= c2[idx];
-    if (FORCE) L = fma(-(T)f[idx], cf.fph, L);
-    const T wn = fma(cf.dt2, L, fma(T(2), c, -wp[idx]));
+    T wn;
+    if constexpr (ORDER == 2 && !VARC) {
+      // 6 (2-D) / 8 (3-D) floating-point instructions per update instead of 9 / 12
+      T u = fma(cf.b, c, -wp[idx]);
+      u = fma(cf.a[0], (x > 0 ? __ldg(wc + idx - 1) : T(0)) + (x < nx - 1 ? __ldg(wc + idx + 1) : T(0)), u);
+      if (DIM > 1)
+        u = fma(cf.a[1], (y > 0 ? __ldg(wc + idx - nx) : T(0)) + (y < ny - 1 ? __ldg(wc + idx + nx) : T(0)), u);
+      if (DIM > 2) {
+        const int64_t pl = (int64_t)nx * ny;
+        u = fma(cf.a[2], (z > 0 ? __ldg(wc + idx - pl) : T(0)) + (z < nz - 1 ? __ldg(wc + idx + pl) : T(0)), u);
+      }
+      if (FORCE) u = fma(-cf.dt2 * cf.fph, (T)f[idx], u);
+      wn = u;
+    } else {
+      T L = lap<DIM, ORDER, T>(wc, idx, x, y, z, nx, ny, nz, cf, c);
+      if (VARC) L *= c2[idx];
+      if (FORCE) L = fma(-(T)f[idx], cf.fph, L);
+      wn = fma(cf.dt2, L, fma(T(2), c, -wp[idx]));
+    }
     const T a = fma(cf.w1, wn, acc[idx]);
     if (KIND == K_STEP) {
       wp[idx] = wn;
@@ -122,13 +106,95 @@ __global__ void __launch_bounds__(256) k_step(const T* __restrict__ wc, T* __res
   }
 }
 
+// 3-D 7-point variant: each thread marches through a column of `zc` planes, keeping W^n at
+// z-1, z, z+1 in registers (the z neighbours cost no extra load) and loading the next plane
+// one iteration ahead; x / y neighbours come through L1.  Same arithmetic and summation order
+// as k_step.
+template <typename T, bool VARC, bool FORCE, int KIND>
+__global__ void __launch_bounds__(256) k_step3d(const T* __restrict__ wc, T* __restrict__ wp,
+                                                T* __restrict__ acc, const T* __restrict__ c2,
+                                                const double* __restrict__ f,
+                                                const double* __restrict__ v,
+                                                const double* __restrict__ mw,
+                                                double* __restrict__ out, int nx, int ny, int nz,
+                                                int zc, StepCoef<T> cf, double* partials,
+                                                unsigned* counter, double* scal_out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, nz);
+  const bool in = (x < nx) && (y < ny);
+  const int64_t plane = (int64_t)nx * ny;
+  int64_t idx = x + (int64_t)nx * y + plane * z0;
+  double part = 0.0;
+  if (in) {
+    T wzm = z0 > 0 ? __ldg(wc + idx - plane) : T(0);
+    T wz = __ldg(wc + idx);
+    T wzp = z0 + 1 < nz ? __ldg(wc + idx + plane) : T(0);
+    for (int z = z0; z < z1; ++z) {
+      // prefetch the plane after next
+      const T wzpp = z + 2 < nz ? __ldg(wc + idx + 2 * plane) : T(0);
+      const T xm = x > 0 ? __ldg(wc + idx - 1) : T(0);
+      const T xp = x < nx - 1 ? __ldg(wc + idx + 1) : T(0);
+      const T ym = y > 0 ? __ldg(wc + idx - nx) : T(0);
+      const T yp = y < ny - 1 ? __ldg(wc + idx + nx) : T(0);
+      T wn;
+      if constexpr (!VARC) {
+        T u = fma(cf.b, wz, -wp[idx]);
+        u = fma(cf.a[0], xm + xp, u);
+        u = fma(cf.a[1], ym + yp, u);
+        u = fma(cf.a[2], wzm + wzp, u);
+        if (FORCE) u = fma(-cf.dt2 * cf.fph, (T)f[idx], u);
+        wn = u;
+      } else {
+        T L = fma(T(-2), wz, xm + xp) * cf.ih2[0];
+        L = fma(fma(T(-2), wz, ym + yp), cf.ih2[1], L);
+        L = fma(fma(T(-2), wz, wzm + wzp), cf.ih2[2], L);
+        L *= c2[idx];
+        if (FORCE) L = fma(-(T)f[idx], cf.fph, L);
+        wn = fma(cf.dt2, L, fma(T(2), wz, -wp[idx]));
+      }
+      const T a = fma(cf.w1, wn, acc[idx]);
+      if (KIND == K_STEP) {
+        wp[idx] = wn;
+        acc[idx] = a;
+      } else if (KIND == K_LAST_OUT) {
+        out[idx] = (double)a;
+      } else {
+        const double vi = v[idx];
+        const double o = vi - (double)a;
+        out[idx] = o;
+        part = fma(mw ? vi * mw[idx] : vi, o, part);
+      }
+      wzm = wz;
+      wz = wzp;
+      wzp = wzpp;
+      idx += plane;
+    }
+  }
+  if (KIND == K_LAST_AV) {
+    part = block_sum(part);
+    double total;
+    if (grid_reduce(part, partials, counter, &total) && flat_tid() == 0) *scal_out = total;
+  }
+}
+
 // --------------------------------------------------------------------------- host side
 struct LaunchShape {
   dim3 grid, block;
 };
 
+constexpr int kZChunk = 16;   // planes per thread of the 3-D 7-point kernel
+
+static bool use_zmarch(whv_grid g) { return g->dim == 3 && g->order == 2; }
+
 static LaunchShape shape_of(whv_grid g) {
   LaunchShape s;
+  if (use_zmarch(g)) {
+    s.block = dim3(32, 8, 1);
+    s.grid = dim3((g->n[0] + 31) / 32, (g->n[1] + 7) / 8, (g->n[2] + kZChunk - 1) / kZChunk);
+    return s;
+  }
   if (g->dim == 1) {
     s.block = dim3(256, 1, 1);
     s.grid = dim3((g->n[0] + 255) / 256, 1, 1);
@@ -150,30 +216,39 @@ static StepCoef<T> coef_of(whv_grid g, const TimeGridH& tg) {
   cf.fph = T(1);
   cf.w0 = (T)tg.weight[0];
   cf.w1 = (T)tg.weight[1];
+  double asum = 0.0;
+  for (int m = 0; m < 3; ++m) {
+    const double am = m < g->dim ? tg.dt * tg.dt / (g->h[m] * g->h[m]) : 0.0;
+    cf.a[m] = (T)am;
+    asum += am;
+  }
+  cf.b = (T)(2.0 - 2.0 * asum);
   return cf;
 }
 
 template <typename T, int DIM, int ORDER, bool VARC, bool FORCE>
 static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
-                               double* out, int epi, int* nlaunch) {
+                               double* out, int epi, int* nlaunch, void* const* bufs, void* accbuf,
+                               int kb) {
   const LaunchShape ls = shape_of(g);
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-  T* b0 = (T*)g->wbuf[0];
-  T* b1 = (T*)g->wbuf[1];
-  T* acc = (T*)g->acc;
+  T* b0 = (T*)bufs[0];
+  T* b1 = (T*)bufs[1];
+  T* acc = (T*)accbuf;
   const T* c2 = VARC ? (const T*)(sizeof(T) == 8 ? (const void*)g->c2 : (const void*)g->c2f) : nullptr;
   StepCoef<T> cf = coef_of<T>(g, tg);
+  dim3 fgrid = ls.grid;
+  if (DIM == 3) fgrid.z = nz;   // the first-step kernel takes one plane per z block
   if (v)
-    k_first<T, DIM, ORDER, VARC, FORCE, false><<<ls.grid, ls.block, 0, g->stream>>>(v, b0, b1, acc, c2, f, nx, ny, nz, cf);
+    k_first<T, DIM, ORDER, VARC, FORCE, false><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, c2, f, nx, ny, nz, cf);
   else
-    k_first<T, DIM, ORDER, VARC, FORCE, true><<<ls.grid, ls.block, 0, g->stream>>>(v, b0, b1, acc, c2, f, nx, ny, nz, cf);
+    k_first<T, DIM, ORDER, VARC, FORCE, true><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, c2, f, nx, ny, nz, cf);
   WHV_CUDA(g, cudaGetLastError());
   *nlaunch = 1;
   if constexpr (DIM == 2 && !FORCE) {
-    const int kb = g->kblock > 0 ? g->kblock : default_kblock(g);
     if (kb > 1) {
       int nl = 0;
-      whv_status s = blocked_steps_2d<T, ORDER, VARC>(g, tg, v, out, epi, kb, &nl);
+      whv_status s = blocked_steps_2d<T, ORDER, VARC>(g, tg, v, out, epi, kb, &nl, bufs, accbuf);
       *nlaunch += nl;
       return s;
     }
@@ -188,7 +263,17 @@ static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v,
     cf.fph = (T)tg.phase[n];
     cf.w1 = (T)tg.weight[n + 1];
     const bool last = (n == tg.nt - 1);
-    if (!last) {
+    if constexpr (DIM == 3 && ORDER == 2) {
+      if (!last)
+        k_step3d<T, VARC, FORCE, K_STEP><<<ls.grid, ls.block, 0, g->stream>>>(
+            wcur, wprev, acc, c2, f, nullptr, nullptr, nullptr, nx, ny, nz, kZChunk, cf, nullptr, nullptr, nullptr);
+      else if (epi == 0)
+        k_step3d<T, VARC, FORCE, K_LAST_OUT><<<ls.grid, ls.block, 0, g->stream>>>(
+            wcur, wprev, acc, c2, f, nullptr, nullptr, out, nx, ny, nz, kZChunk, cf, nullptr, nullptr, nullptr);
+      else
+        k_step3d<T, VARC, FORCE, K_LAST_AV><<<ls.grid, ls.block, 0, g->stream>>>(
+            wcur, wprev, acc, c2, f, v, g->mw, out, nx, ny, nz, kZChunk, cf, part, cnt, g->scal + S_PQ);
+    } else if (!last) {
       k_step<T, DIM, ORDER, VARC, FORCE, K_STEP><<<ls.grid, ls.block, 0, g->stream>>>(
           wcur, wprev, acc, c2, f, nullptr, nullptr, nullptr, nx, ny, nz, cf, nullptr, nullptr, nullptr);
     } else if (epi == 0) {
@@ -206,28 +291,34 @@ static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v,
   return WHV_OK;
 }
 
+struct BufSet {
+  void* const* bufs;
+  void* acc;
+  int kb;
+};
+
 template <typename T, int DIM, int ORDER>
 static whv_status dispatch_vf(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
-                              double* out, int epi, int* nl) {
+                              double* out, int epi, int* nl, const BufSet& B) {
   const bool varc = g->c2 != nullptr;
   if (varc) {
-    return f ? launch_solve<T, DIM, ORDER, true, true>(g, tg, v, f, out, epi, nl)
-             : launch_solve<T, DIM, ORDER, true, false>(g, tg, v, f, out, epi, nl);
+    return f ? launch_solve<T, DIM, ORDER, true, true>(g, tg, v, f, out, epi, nl, B.bufs, B.acc, B.kb)
+             : launch_solve<T, DIM, ORDER, true, false>(g, tg, v, f, out, epi, nl, B.bufs, B.acc, B.kb);
   }
-  return f ? launch_solve<T, DIM, ORDER, false, true>(g, tg, v, f, out, epi, nl)
-           : launch_solve<T, DIM, ORDER, false, false>(g, tg, v, f, out, epi, nl);
+  return f ? launch_solve<T, DIM, ORDER, false, true>(g, tg, v, f, out, epi, nl, B.bufs, B.acc, B.kb)
+           : launch_solve<T, DIM, ORDER, false, false>(g, tg, v, f, out, epi, nl, B.bufs, B.acc, B.kb);
 }
 
 template <typename T>
 static whv_status dispatch(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
-                           double* out, int epi, int* nl) {
+                           double* out, int epi, int* nl, const BufSet& B) {
   switch (g->dim * 10 + g->order) {
-    case 12: return dispatch_vf<T, 1, 2>(g, tg, v, f, out, epi, nl);
-    case 14: return dispatch_vf<T, 1, 4>(g, tg, v, f, out, epi, nl);
-    case 22: return dispatch_vf<T, 2, 2>(g, tg, v, f, out, epi, nl);
-    case 24: return dispatch_vf<T, 2, 4>(g, tg, v, f, out, epi, nl);
-    case 32: return dispatch_vf<T, 3, 2>(g, tg, v, f, out, epi, nl);
-    case 34: return dispatch_vf<T, 3, 4>(g, tg, v, f, out, epi, nl);
+    case 12: return dispatch_vf<T, 1, 2>(g, tg, v, f, out, epi, nl, B);
+    case 14: return dispatch_vf<T, 1, 4>(g, tg, v, f, out, epi, nl, B);
+    case 22: return dispatch_vf<T, 2, 2>(g, tg, v, f, out, epi, nl, B);
+    case 24: return dispatch_vf<T, 2, 4>(g, tg, v, f, out, epi, nl, B);
+    case 32: return dispatch_vf<T, 3, 2>(g, tg, v, f, out, epi, nl, B);
+    case 34: return dispatch_vf<T, 3, 4>(g, tg, v, f, out, epi, nl, B);
   }
   return fail(g, WHV_ERR_INVALID, "unsupported dim/order");
 }
@@ -237,13 +328,35 @@ static whv_status dispatch(whv_grid g, const TimeGridH& tg, const double* v, con
 // updates of a blocked sweep cost more than the launches they save (one step per launch)
 int default_kblock(whv_grid g) { return g->precision == WHV_FP32_STEP ? 8 : 1; }
 
+// outer vectors of the FP64 residual correction, and FP64 stepping buffers on FP32 grids
+whv_status ensure_fp64_buffers(whv_grid g) {
+  const size_t bytes = (size_t)g->N * sizeof(double);
+  if (!g->bo) {
+    WHV_CUDA(g, cudaMalloc(&g->xo, bytes));
+    WHV_CUDA(g, cudaMalloc(&g->ro, bytes));
+    WHV_CUDA(g, cudaMalloc(&g->bo, bytes));
+  }
+  if (g->precision == WHV_FP64 || g->acc64) return WHV_OK;
+  for (int i = 0; i < 4; ++i) WHV_CUDA(g, cudaMalloc(&g->wbuf64[i], bytes));
+  WHV_CUDA(g, cudaMalloc(&g->acc64, bytes));
+  return WHV_OK;
+}
+
 static whv_status launch_wave_solve(whv_grid g, const TimeGridH& tg, const double* v,
-                                    const double* f, double* out, int epi, int* nl) {
+                                    const double* f, double* out, int epi, int* nl, int prec) {
   const LaunchShape ls = shape_of(g);
   if ((int64_t)ls.grid.x * ls.grid.y * ls.grid.z > kMaxStepBlocks)
     return fail(g, WHV_ERR_INVALID, "grid too large for the fused reduction");
-  return g->precision == WHV_FP64 ? dispatch<double>(g, tg, v, f, out, epi, nl)
-                                  : dispatch<float>(g, tg, v, f, out, epi, nl);
+  if (prec < 0) prec = g->precision;
+  if (prec == g->precision) {
+    const BufSet B{g->wbuf, g->acc, g->kblock > 0 ? g->kblock : default_kblock(g)};
+    return prec == WHV_FP64 ? dispatch<double>(g, tg, v, f, out, epi, nl, B)
+                            : dispatch<float>(g, tg, v, f, out, epi, nl, B);
+  }
+  if (prec != WHV_FP64) return fail(g, WHV_ERR_INVALID, "FP32 stepping on an FP64 grid is not provided");
+  if (!g->acc64) return fail(g, WHV_ERR_INVALID, "FP64 buffers of the FP32 grid are not allocated");
+  const BufSet B{g->wbuf64, g->acc64, 1};   // FP64 stepping is FP64-pipe bound: one step per launch
+  return dispatch<double>(g, tg, v, f, out, epi, nl, B);
 }
 
 // ------------------------------------------------------------------ CUDA graph cache
@@ -254,7 +367,7 @@ struct PlanEntry {
   double* out;
   int epi;
   double omega, cfl;
-  int periods, adjust, nt, kblock;
+  int periods, adjust, nt, kblock, prec;
   int launches;   // kernels in the graph
   cudaGraphExec_t exec;
   unsigned long long last_use;
@@ -273,12 +386,13 @@ void free_plan(whv_grid g) {
 }
 
 whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
-                      double* out, int epi) {
+                      double* out, int epi, int prec) {
+  if (prec < 0) prec = g->precision;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   WHV_CUDA(g, cudaStreamIsCapturing(g->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) {  // caller is capturing: record the launches into its graph
     int nl = 0;
-    whv_status s = launch_wave_solve(g, tg, v, f, out, epi, &nl);
+    whv_status s = launch_wave_solve(g, tg, v, f, out, epi, &nl, prec);
     count_launches(nl);
     return s;
   }
@@ -288,7 +402,7 @@ whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const do
   for (auto& e : P->entries) {
     if (e.v == v && e.f == f && e.out == out && e.epi == epi && e.omega == tg.omega &&
         e.cfl == tg.cfl && e.periods == tg.periods && e.adjust == tg.adjust && e.nt == tg.nt &&
-        e.kblock == g->kblock) {
+        e.kblock == g->kblock && e.prec == prec) {
       e.last_use = P->tick;
       WHV_CUDA(g, cudaGraphLaunch(e.exec, g->stream));
       count_launches(e.launches);
@@ -298,7 +412,7 @@ whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const do
   cudaGraph_t graph = nullptr;
   WHV_CUDA(g, cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
   int nl = 0;
-  whv_status s = launch_wave_solve(g, tg, v, f, out, epi, &nl);
+  whv_status s = launch_wave_solve(g, tg, v, f, out, epi, &nl, prec);
   cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
   if (s != WHV_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -317,7 +431,7 @@ whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const do
     P->entries.erase(P->entries.begin() + victim);
   }
   P->entries.push_back(PlanEntry{v, f, out, epi, tg.omega, tg.cfl, tg.periods, tg.adjust, tg.nt,
-                                g->kblock, nl, exec, P->tick});
+                                g->kblock, prec, nl, exec, P->tick});
   WHV_CUDA(g, cudaGraphLaunch(exec, g->stream));
   count_launches(nl);
   return WHV_OK;

@@ -1,18 +1,19 @@
 // Temporally blocked 2-D leapfrog + trapezoid filter: k time steps per launch (the f = 0 wave
 // solves that make up A p in every Krylov iteration).
 //
-// Each CTA owns a TX x TY tile.  It stages W^{n-1}, W^n (and c^2) of the tile plus a halo of
-// width H = k r (r = 1 for the 5-point, 2 for the 9-point-wide 4th-order stencil) in shared
-// memory, advances k leapfrog steps there -- at sub-step s the valid region shrinks by r on
-// every side that is not a Dirichlet boundary -- and accumulates the filter terms w_{n+s} W^{n+s}
-// of its own tile points in registers.  It then writes W^{n+k-1}, W^{n+k} of the tile to the
-// other buffer pair (neighbouring CTAs still read the old pair) and adds the accumulated filter
-// sum to acc, or, on the last block of steps, writes the FP64 epilogue (Pi_h v, or A v with the
-// p^T M A p reduction) like the single-step kernel.
+// Each CTA stages a REG x REG region (a tile of (REG - 2H)^2 nodes plus a halo of width
+// H = k r; r = 1 for the 5-point, 2 for the 9-point-wide 4th-order stencil) and advances it k
+// leapfrog steps; at sub-step s only the window [s r, REG - s r)^2 is updated, which is exactly
+// what the next sub-step needs.  Thread (warp w, lane) owns column 32 (w & 1) + lane and rows
+// (w >> 1) + 8 t, t < 8, of the region for the whole launch: W^n, W^{n-1} and the filter sum of
+// its cells stay in registers, and only W^n goes through shared memory (double-buffered) for the
+// neighbours' reads.  All global loads of a thread are issued before the first use.  The tile's
+// W^{n+k-1}, W^{n+k} go to the other buffer pair (neighbouring CTAs still read the old pair),
+// the filter sums are added to acc -- or, on the last sweep, the FP64 epilogue (Pi_h v, or A v
+// with the p^T M A p reduction) is written like the single-step kernel does.
 //
-// Global traffic per k steps and node: 3 reads + 3 writes (+ c^2) instead of 5 per step, so the
-// sweep count per wave solve drops from Nt to Nt/k; the cost is the redundant halo updates
-// ((TX + 2H)(TY + 2H) / (TX TY) on the first sub-step, shrinking to 1).
+// Global traffic per k steps and tile node: 3 reads + 3 writes (+ c^2), plus the halo re-reads
+// (REG^2 / tile^2), instead of 5 accesses per step; the price is the redundant halo updates.
 #include <math.h>
 
 #include <algorithm>
@@ -23,11 +24,14 @@
 namespace whv {
 
 constexpr int kBlkMaxK = 16;
-constexpr int kBlkTX = 32, kBlkTY = 32;   // tile per CTA; block of 32 x 8 threads
+constexpr int kReg = 64;            // staged region edge
+constexpr int kBlkThreads = 512;    // 16 warps
+constexpr int kRowsPerThread = kReg / 8;
 
 template <typename T>
 struct BlockCoef {
   T ih2x, ih2y, dt2;
+  T ax, ay, b;     // 2nd order, c = 1: W^{n+1} = ax s_x + ay s_y + b W^n - W^{n-1}
   T w[kBlkMaxK];   // filter weights w_{n0+1} .. w_{n0+k}
   int k;
 };
@@ -47,91 +51,99 @@ __device__ __forceinline__ T d2s(const T* __restrict__ a, int l, int gi, int n, 
 }
 
 template <typename T, int ORDER, bool VARC, int KIND>
-__global__ void __launch_bounds__(256) k_block2d(const T* __restrict__ gprev, const T* __restrict__ gcur,
-                                                 T* __restrict__ oprev, T* __restrict__ ocur,
-                                                 T* __restrict__ acc, const T* __restrict__ c2,
-                                                 const double* __restrict__ v,
-                                                 const double* __restrict__ mw,
-                                                 double* __restrict__ out, int nx, int ny,
-                                                 BlockCoef<T> cf, double* partials,
-                                                 unsigned* counter, double* scal_out) {
+__global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ gprev,
+                                                         const T* __restrict__ gcur,
+                                                         T* __restrict__ oprev, T* __restrict__ ocur,
+                                                         T* __restrict__ acc,
+                                                         const T* __restrict__ c2,
+                                                         const double* __restrict__ v,
+                                                         const double* __restrict__ mw,
+                                                         double* __restrict__ out, int nx, int ny,
+                                                         BlockCoef<T> cf, double* partials,
+                                                         unsigned* counter, double* scal_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S0 = reinterpret_cast<T*>(smem_raw);
+  T* S1 = S0 + kReg * kReg;
+  __shared__ T sw[kBlkMaxK];
   constexpr int R = ORDER == 2 ? 1 : 2;
-  constexpr int NB = kBlkTY / 8;   // owned tile rows per thread
   const int H = cf.k * R;
-  const int x0 = blockIdx.x * kBlkTX, y0 = blockIdx.y * kBlkTY;
-  const int rx0 = max(x0 - H, 0), rx1 = min(x0 + kBlkTX + H, nx);
-  const int ry0 = max(y0 - H, 0), ry1 = min(y0 + kBlkTY + H, ny);
-  const int RW = rx1 - rx0, RH = ry1 - ry0;
-  const bool physL = rx0 == 0, physR = rx1 == nx, physB = ry0 == 0, physT = ry1 == ny;
-  T* X = reinterpret_cast<T*>(smem_raw);
-  T* Y = X + RW * RH;
-  T* C = Y + RW * RH;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  __shared__ T sw[kBlkMaxK];   // filter weights, indexed by sub-step
-  if (ty == 0 && tx < kBlkMaxK) sw[tx] = cf.w[tx];
-  for (int j = ty; j < RH; j += 8) {
-    const int64_t grow = (int64_t)nx * (ry0 + j) + rx0;
-    for (int i = tx; i < RW; i += 32) {
-      X[j * RW + i] = gprev[grow + i];
-      Y[j * RW + i] = gcur[grow + i];
-      if (VARC) C[j * RW + i] = c2[grow + i];
-    }
-  }
-  __syncthreads();
-  T accr[NB];
+  const int TW = kReg - 2 * H;
+  const int x0 = blockIdx.x * TW - H, y0 = blockIdx.y * TW - H;   // region origin (global)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = 32 * (warp & 1) + lane;
+  const int jb = warp >> 1;
+  const int gx = x0 + i;
+  const bool colin = gx >= 0 && gx < nx;
+  if (threadIdx.x < kBlkMaxK) sw[threadIdx.x] = cf.w[threadIdx.x];
+  T cur[kRowsPerThread], prv[kRowsPerThread], acr[kRowsPerThread];
+  T cc[VARC ? kRowsPerThread : 1];
 #pragma unroll
-  for (int b = 0; b < NB; ++b) accr[b] = T(0);
-  const int ox = x0 + tx;                    // owned column
-  T* cur = Y;
-  T* prv = X;
+  for (int t = 0; t < kRowsPerThread; ++t) {
+    const int gy = y0 + jb + 8 * t;
+    const bool in = colin && gy >= 0 && gy < ny;
+    const int64_t gi = gx + (int64_t)nx * gy;
+    cur[t] = in ? gcur[gi] : T(0);
+    prv[t] = in ? gprev[gi] : T(0);
+    if (VARC) cc[t] = in ? c2[gi] : T(0);
+    acr[t] = T(0);
+  }
+#pragma unroll
+  for (int t = 0; t < kRowsPerThread; ++t) S0[(jb + 8 * t) * kReg + i] = cur[t];
+  __syncthreads();
+  T* A = S0;
+  T* B = S1;
   for (int s = 1; s <= cf.k; ++s) {
-    const int vx0 = physL ? 0 : s * R, vx1 = physR ? RW : RW - s * R;
-    const int vy0 = physB ? 0 : s * R, vy1 = physT ? RH : RH - s * R;
-    for (int j = vy0 + ty; j < vy1; j += 8) {
-      const int gy = ry0 + j;
-      for (int i = vx0 + tx; i < vx1; i += 32) {
-        const int l = j * RW + i;
-        const T c = cur[l];
-        T L = d2s<ORDER>(cur, l, rx0 + i, nx, 1, c) * cf.ih2x;
-        L = fma(d2s<ORDER>(cur, l, gy, ny, RW, c), cf.ih2y, L);
-        if (VARC) L *= C[l];
-        prv[l] = fma(cf.dt2, L, fma(T(2), c, -prv[l]));
+    const int lo = s * R, hi = kReg - s * R;
+    const bool colact = colin && i >= lo && i < hi;
+    const T ws = sw[s - 1];
+#pragma unroll
+    for (int t = 0; t < kRowsPerThread; ++t) {
+      const int j = jb + 8 * t;
+      const int gy = y0 + j;
+      if (colact && j >= lo && j < hi && gy >= 0 && gy < ny) {
+        const int l = j * kReg + i;
+        const T c = cur[t];
+        T wn;
+        if constexpr (ORDER == 2 && !VARC) {
+          T u = fma(cf.b, c, -prv[t]);
+          u = fma(cf.ax, (gx > 0 ? A[l - 1] : T(0)) + (gx < nx - 1 ? A[l + 1] : T(0)), u);
+          wn = fma(cf.ay, (gy > 0 ? A[l - kReg] : T(0)) + (gy < ny - 1 ? A[l + kReg] : T(0)), u);
+        } else {
+          T L = d2s<ORDER>(A, l, gx, nx, 1, c) * cf.ih2x;
+          L = fma(d2s<ORDER>(A, l, gy, ny, kReg, c), cf.ih2y, L);
+          if (VARC) L *= cc[t];
+          wn = fma(cf.dt2, L, fma(T(2), c, -prv[t]));
+        }
+        prv[t] = c;
+        cur[t] = wn;
+        B[l] = wn;
+        acr[t] = fma(ws, wn, acr[t]);
       }
     }
     __syncthreads();
-    T* t = cur; cur = prv; prv = t;          // cur = W^{n0+s}
-    const T ws = sw[s - 1];
-    if (ox < nx) {
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        const int oy = y0 + ty + 8 * b;
-        if (oy < ny) accr[b] = fma(ws, cur[(oy - ry0) * RW + (ox - rx0)], accr[b]);
-      }
-    }
+    T* tmp = A; A = B; B = tmp;
   }
   double part = 0.0;
-  if (ox < nx) {
+  const bool coltile = colin && i >= H && i < kReg - H;
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int oy = y0 + ty + 8 * b;
-      if (oy >= ny) continue;
-      const int l = (oy - ry0) * RW + (ox - rx0);
-      const int64_t gi = ox + (int64_t)nx * oy;
-      if (KIND == B_STEP) {
-        ocur[gi] = cur[l];
-        oprev[gi] = prv[l];
-        acc[gi] += accr[b];
+  for (int t = 0; t < kRowsPerThread; ++t) {
+    const int j = jb + 8 * t;
+    const int gy = y0 + j;
+    if (!(coltile && j >= H && j < kReg - H && gy >= 0 && gy < ny)) continue;
+    const int64_t gi = gx + (int64_t)nx * gy;
+    if (KIND == B_STEP) {
+      ocur[gi] = cur[t];
+      oprev[gi] = prv[t];
+      acc[gi] += acr[t];
+    } else {
+      const T a = acc[gi] + acr[t];
+      if (KIND == B_LAST_OUT) {
+        out[gi] = (double)a;
       } else {
-        const T a = acc[gi] + accr[b];
-        if (KIND == B_LAST_OUT) {
-          out[gi] = (double)a;
-        } else {
-          const double vi = v[gi];
-          const double o = vi - (double)a;
-          out[gi] = o;
-          part = fma(mw ? vi * mw[gi] : vi, o, part);
-        }
+        const double vi = v[gi];
+        const double o = vi - (double)a;
+        out[gi] = o;
+        part = fma(mw ? vi * mw[gi] : vi, o, part);
       }
     }
   }
@@ -142,20 +154,17 @@ __global__ void __launch_bounds__(256) k_block2d(const T* __restrict__ gprev, co
   }
 }
 
-static size_t blk_smem(int k, int order, bool varc, size_t esz) {
-  const int R = order == 2 ? 1 : 2;
-  const size_t w = kBlkTX + 2 * k * R, h = kBlkTY + 2 * k * R;
-  return (varc ? 3 : 2) * w * h * esz;
-}
+static size_t blk_smem(size_t esz) { return 2 * (size_t)kReg * kReg * esz; }
 
-// largest k <= want whose staged region fits the shared-memory budget
-int blocked_steps(int want, int order, bool varc, size_t esz) {
+// largest k <= want that leaves a tile of at least 16 nodes per edge
+int blocked_steps(int want, int order) {
+  const int R = order == 2 ? 1 : 2;
   int k = std::min(std::max(want, 1), kBlkMaxK);
-  while (k > 1 && blk_smem(k, order, varc, esz) > 160u * 1024u) --k;
+  while (k > 1 && kReg - 2 * k * R < 16) --k;
   return k;
 }
 
-constexpr int kBlkSmemCap = 160 * 1024;
+constexpr int kBlkSmemCap = 2 * kReg * kReg * 8;   // FP64 double buffer: 64 KB
 
 template <typename T, int ORDER, bool VARC>
 static void set_attrs() {
@@ -178,11 +187,12 @@ template <typename T, int ORDER, bool VARC, int KIND>
 static cudaError_t launch_block(whv_grid g, const T* gp, const T* gc, T* op, T* oc, T* acc,
                                 const T* c2, const double* v, double* out, const BlockCoef<T>& cf,
                                 double* partials, unsigned* counter, double* scal_out) {
-  const size_t smem = blk_smem(cf.k, ORDER, VARC, sizeof(T));
-  auto kern = k_block2d<T, ORDER, VARC, KIND>;
-  dim3 grid((g->n[0] + kBlkTX - 1) / kBlkTX, (g->n[1] + kBlkTY - 1) / kBlkTY, 1);
-  kern<<<grid, dim3(32, 8, 1), smem, g->stream>>>(gp, gc, op, oc, acc, c2, v, g->mw, out, g->n[0],
-                                                  g->n[1], cf, partials, counter, scal_out);
+  const size_t smem = blk_smem(sizeof(T));
+  const int R = ORDER == 2 ? 1 : 2;
+  const int TW = kReg - 2 * cf.k * R;
+  dim3 grid((g->n[0] + TW - 1) / TW, (g->n[1] + TW - 1) / TW, 1);
+  k_block2d<T, ORDER, VARC, KIND><<<grid, kBlkThreads, smem, g->stream>>>(
+      gp, gc, op, oc, acc, c2, v, g->mw, out, g->n[0], g->n[1], cf, partials, counter, scal_out);
   return cudaGetLastError();
 }
 
@@ -190,16 +200,20 @@ static cudaError_t launch_block(whv_grid g, const T* gp, const T* gc, T* op, T* 
 // start) has already written W^0 -> wbuf[0], W^1 -> wbuf[1] and acc.
 template <typename T, int ORDER, bool VARC>
 whv_status blocked_steps_2d(whv_grid g, const TimeGridH& tg, const double* v, double* out, int epi,
-                            int k_want, int* launches) {
-  T* buf[4] = {(T*)g->wbuf[0], (T*)g->wbuf[1], (T*)g->wbuf[2], (T*)g->wbuf[3]};
-  T* acc = (T*)g->acc;
+                            int k_want, int* launches, void* const* bufs, void* accbuf) {
+  T* buf[4] = {(T*)bufs[0], (T*)bufs[1], (T*)bufs[2], (T*)bufs[3]};
+  T* acc = (T*)accbuf;
   const T* c2 = VARC ? (const T*)(sizeof(T) == 8 ? (const void*)g->c2 : (const void*)g->c2f) : nullptr;
-  const int kmax = blocked_steps(k_want, ORDER, VARC, sizeof(T));
+  const int kmax = blocked_steps(k_want, ORDER);
   BlockCoef<T> cf;
   const double h2x = g->h[0] * g->h[0], h2y = g->h[1] * g->h[1];
   cf.ih2x = (T)(ORDER == 2 ? 1.0 / h2x : 1.0 / (12.0 * h2x));
   cf.ih2y = (T)(ORDER == 2 ? 1.0 / h2y : 1.0 / (12.0 * h2y));
   cf.dt2 = (T)(tg.dt * tg.dt);
+  const double ax = tg.dt * tg.dt / h2x, ay = tg.dt * tg.dt / h2y;
+  cf.ax = (T)ax;
+  cf.ay = (T)ay;
+  cf.b = (T)(2.0 - 2.0 * (ax + ay));
   double* part = g->partials + CH_STEP * kMaxStepBlocks;
   unsigned* cnt = g->counters + CH_STEP;
   int pair = 0;   // input pair: (buf[2 pair], buf[2 pair + 1]) = (W^{n-1}, W^n)
@@ -227,13 +241,13 @@ whv_status blocked_steps_2d(whv_grid g, const TimeGridH& tg, const double* v, do
   return WHV_OK;
 }
 
-template whv_status blocked_steps_2d<float, 2, false>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*);
-template whv_status blocked_steps_2d<float, 2, true>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*);
-template whv_status blocked_steps_2d<float, 4, false>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*);
-template whv_status blocked_steps_2d<float, 4, true>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*);
-template whv_status blocked_steps_2d<double, 2, false>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*);
-template whv_status blocked_steps_2d<double, 2, true>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*);
-template whv_status blocked_steps_2d<double, 4, false>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*);
-template whv_status blocked_steps_2d<double, 4, true>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*);
+template whv_status blocked_steps_2d<float, 2, false>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
+template whv_status blocked_steps_2d<float, 2, true>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
+template whv_status blocked_steps_2d<float, 4, false>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
+template whv_status blocked_steps_2d<float, 4, true>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
+template whv_status blocked_steps_2d<double, 2, false>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
+template whv_status blocked_steps_2d<double, 2, true>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
+template whv_status blocked_steps_2d<double, 4, false>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
+template whv_status blocked_steps_2d<double, 4, true>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
 
 }  // namespace whv

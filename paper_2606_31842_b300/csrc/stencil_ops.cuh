@@ -1,0 +1,45 @@
+// Stencil pieces shared by the stepping kernels and the eigen-solve: step coefficients and the
+// p-th order second differences with the Dirichlet / odd-reflection closure.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace whv {
+
+template <typename T>
+struct StepCoef {
+  T ih2[3];   // 1/h^2 per direction (order 4: 1/(12 h^2))
+  T dt2;      // dt^2
+  T fph;      // cos(omega_hat t^n) of the step (first step: 1)
+  T w0, w1;   // first step: w_0, w_1; other steps: w1 = w_{n+1}
+  // 2nd order, c = 1: W^{n+1} = sum_m a_m (W_{+e_m} + W_{-e_m}) + b W^n - W^{n-1} (- dt^2 f cos)
+  T a[3];     // dt^2 / h_m^2
+  T b;        // 2 - 2 sum_m a_m
+};
+
+// Second difference along one axis at interior index i of n, without the 1/h^2 factor.
+// Dirichlet nodes hold 0; order 4 uses the odd reflection u_{-1} = -u_1 beyond the boundary.
+template <int ORDER, typename T, typename S>
+__device__ __forceinline__ T d2(const S* __restrict__ w, int64_t idx, int i, int n, int64_t s, T c) {
+  const T m1 = (i > 0) ? (T)__ldg(w + idx - s) : T(0);
+  const T p1 = (i < n - 1) ? (T)__ldg(w + idx + s) : T(0);
+  if (ORDER == 2) {
+    return fma(T(-2), c, m1 + p1);
+  } else {
+    const T m2 = (i > 1) ? (T)__ldg(w + idx - 2 * s) : (i == 1 ? T(0) : -c);
+    const T p2 = (i < n - 2) ? (T)__ldg(w + idx + 2 * s) : (i == n - 2 ? T(0) : -c);
+    return fma(T(-30), c, fma(T(16), m1 + p1, -(m2 + p2)));
+  }
+}
+
+template <int DIM, int ORDER, typename T, typename S>
+__device__ __forceinline__ T lap(const S* __restrict__ w, int64_t idx, int x, int y, int z, int nx,
+                                 int ny, int nz, const StepCoef<T>& cf, T c) {
+  T l = d2<ORDER, T>(w, idx, x, nx, 1, c) * cf.ih2[0];
+  if (DIM > 1) l = fma(d2<ORDER, T>(w, idx, y, ny, (int64_t)nx, c), cf.ih2[1], l);
+  if (DIM > 2) l = fma(d2<ORDER, T>(w, idx, z, nz, (int64_t)nx * ny, c), cf.ih2[2], l);
+  return l;
+}
+
+}  // namespace whv

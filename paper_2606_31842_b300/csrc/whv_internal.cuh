@@ -73,6 +73,11 @@ struct whv_grid_s {
   void* wbuf[4] = {nullptr, nullptr, nullptr, nullptr};
   void* acc = nullptr;
   int kblock = 0;              // steps per sweep of the blocked 2-D kernel (0: default, 1: off)
+  // FP64 stepping buffers of an FP32-stepping grid (FP64 residual correction), allocated on
+  // first use, with the outer solution / residual / right-hand side of the refinement loop
+  void* wbuf64[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* acc64 = nullptr;
+  double *xo = nullptr, *ro = nullptr, *bo = nullptr;
 
   // FP64 Krylov work vectors
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *t = nullptr, *fd = nullptr;
@@ -111,15 +116,19 @@ void count_launches(int64_t n);
 // stencil.cu: one wave solve.  v (FP64, nullable => 0), f (FP64, nullable => 0).
 //   epi = 0: out = Pi_h(v; f)                  (out FP64)
 //   epi = 1: out = v - Pi_h(v; f) = A v (f=0), and scal[S_PQ] = <v, out>_M
+//   prec = -1: the grid's stepping precision; WHV_FP64 on an FP32-stepping grid uses the
+//   grid's FP64 buffer set (ensure_fp64_buffers first).
 whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
-                      double* out, int epi);
+                      double* out, int epi, int prec = -1);
 void free_plan(whv_grid g);
 int default_kblock(whv_grid g);
+whv_status ensure_fp64_buffers(whv_grid g);
 
-// stencil_blocked.cu: steps 1..nt-1 of a 2-D f = 0 wave solve in sweeps of k steps
+// stencil_blocked.cu: steps 1..nt-1 of a 2-D f = 0 wave solve in sweeps of k steps, on the
+// stepping buffers bufs[0..3] (two (W^{n-1}, W^n) pairs) and accumulator acc
 template <typename T, int ORDER, bool VARC>
 whv_status blocked_steps_2d(whv_grid g, const TimeGridH& tg, const double* v, double* out, int epi,
-                            int k_want, int* launches);
+                            int k_want, int* launches, void* const* bufs, void* acc);
 void blocked_init();
 
 // reduce.cu

@@ -19,7 +19,7 @@ WHV_FP64, WHV_FP32_STEP = 0, 1
 WHV_FPI, WHV_CG, WHV_DCG, WHV_GMRES = 0, 1, 2, 3
 WHV_BASIS_NONE, WHV_BASIS_USER, WHV_BASIS_CLOSED_FORM, WHV_BASIS_LANCZOS = 0, 1, 2, 3
 WHV_BASIS_EXACT, WHV_BASIS_REDEFLATE = 1, 2
-WHV_TRUE_RESIDUAL = 1
+WHV_TRUE_RESIDUAL, WHV_REFINE_FP64 = 1, 2
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "NOT_CONVERGED", "BREAKDOWN", "TIMEOUT"]
 METHODS = {"fpi": WHV_FPI, "cg": WHV_CG, "dcg": WHV_DCG, "gmres": WHV_GMRES}
 
@@ -28,14 +28,15 @@ class whv_params(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("periods", ctypes.c_int), ("adjust_omega", ctypes.c_int),
                 ("cfl", ctypes.c_double), ("method", ctypes.c_int), ("restart", ctypes.c_int),
                 ("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("flags", ctypes.c_int)]
+                ("flags", ctypes.c_int), ("inner_tol", ctypes.c_double)]
 
 
 class whv_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("wave_solves", ctypes.c_int), ("nt", ctypes.c_int),
                 ("dt", ctypes.c_double), ("omega_hat", ctypes.c_double), ("omega_eff", ctypes.c_double),
                 ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("outer_iterations", ctypes.c_int),
+                ("wave_solves_fp64", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -67,6 +68,7 @@ def _load():
         "whv_set_steps_per_sweep": [P, I],
         "whv_get_steps_per_sweep": [P, ctypes.POINTER(I)],
         "whv_autotune": [P, ctypes.POINTER(whv_params), ctypes.POINTER(I)],
+        "whv_lanczos": [P, ctypes.POINTER(whv_params), I, I, P, I, I, ctypes.POINTER(D), ctypes.POINTER(D)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -89,7 +91,8 @@ lib = _load()
 EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_grid",
             "whv_set_deflation_basis", "whv_get_basis", "whv_apply_pi", "whv_solve", "whv_project",
             "whv_expand", "whv_dot", "whv_num_unknowns", "whv_last_error", "whv_version",
-            "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune"]
+            "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune",
+            "whv_lanczos"]
 
 
 def _check(status, handle=None, allow=()):
@@ -109,10 +112,11 @@ def _ptr(t, numel=None):
 
 
 def make_params(omega, periods=1, adjust_omega=False, cfl=0.0, method="cg", restart=30, tol=1e-8,
-                maxit=1000, check_every=1, true_residual=False) -> whv_params:
+                maxit=1000, check_every=1, true_residual=False, refine_fp64=False, inner_tol=0.0) -> whv_params:
     m = METHODS[method] if isinstance(method, str) else int(method)
+    flags = (WHV_TRUE_RESIDUAL if true_residual else 0) | (WHV_REFINE_FP64 if refine_fp64 else 0)
     return whv_params(float(omega), int(periods), int(bool(adjust_omega)), float(cfl), m, int(restart),
-                      float(tol), int(maxit), int(check_every), WHV_TRUE_RESIDUAL if true_residual else 0)
+                      float(tol), int(maxit), int(check_every), flags, float(inner_tol))
 
 
 def whv_version() -> str:
@@ -207,6 +211,13 @@ class Grid:
         k = ctypes.c_int()
         _check(lib.whv_autotune(self.handle, ctypes.byref(params), ctypes.byref(k)), self.handle)
         return k.value
+
+    def whv_lanczos(self, params, nd, m, v0=None, fp64_stepping=True, flags=WHV_BASIS_REDEFLATE):
+        theta = (ctypes.c_double * nd)()
+        resid = (ctypes.c_double * nd)()
+        _check(lib.whv_lanczos(self.handle, ctypes.byref(params), int(nd), int(m), _ptr(v0, self.N),
+                               int(bool(fp64_stepping)), int(flags), theta, resid), self.handle)
+        return list(theta), list(resid)
 
     def whv_project(self, r, coef):
         _check(lib.whv_project(self.handle, _ptr(r, self.N), _ptr(coef)), self.handle)

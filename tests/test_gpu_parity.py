@@ -48,6 +48,8 @@ PI_CASES = [
     ((37, 20, 11), 2, None, 8.0),     # 3-D, ragged
     ((19, 23, 17), 2, "c5", 7.0),     # 3-D variable speed
     ((14, 13, 12), 4, None, 5.0),
+    ((12, 10, 40), 2, None, 6.0),     # 3-D, several z chunks with a ragged last one
+    ((17, 13, 45), 2, "c5", 9.0),
     ((3,), 2, None, 1.0),             # a single interior node
     ((3, 3), 2, None, 1.0),
     ((4, 5), 4, None, 2.0),
@@ -69,7 +71,7 @@ def test_apply_pi_fp64(npts, order, speed, omega, forcing, adjust):
     assert relmax(host(out), ref) < 1e-12
 
 
-@pytest.mark.parametrize("npts,order,speed,omega", PI_CASES[:7])
+@pytest.mark.parametrize("npts,order,speed,omega", PI_CASES[:9])
 def test_apply_pi_fp32(npts, order, speed, omega):
     g, og, _ = make(npts, order, speed, precision=whv.WHV_FP32_STEP)
     prm = whv.make_params(omega)
@@ -201,22 +203,52 @@ def test_c2_full_size_fixed_iterations_fp64():
 
 
 @pytest.mark.parametrize("n", [129, 513])
-def test_c2_fp32_stepping_solution_error(n):
-    """FP32 stepping + FP64 Krylov reaches residual 1e-6; the solution is within 1e-5 of the
-    FP64 oracle's converged solution."""
+@pytest.mark.parametrize("method", ["cg", "dcg"])
+def test_c2_fp32_stepping_with_fp64_correction(n, method):
+    """FP32 stepping + FP64 Krylov inside FP64 residual correction: the FP64 true residual meets
+    1e-6 and the solution is within 1e-5 of the FP64 oracle's converged solution."""
     w = I.scaled(I.WORKLOADS["c2"], n) if n != 513 else I.WORKLOADS["c2"]
     g, og, _ = make(w.npts, precision=whv.WHV_FP32_STEP)
     tg = WH.time_grid_for(og, w.omega)
     f = I.forcing_for(w)
     nd = w.nd if n == 513 else 16
-    prm = whv.make_params(w.omega, method="cg", tol=1e-6, maxit=2000, true_residual=True)
+    prm = whv.make_params(w.omega, method=method, tol=1e-6, maxit=2000, true_residual=True, refine_fp64=True)
     g.whv_set_deflation_basis(prm, nd, whv.WHV_BASIS_CLOSED_FORM)
     u, info = g.whv_solve(prm, dev(f))
     modes, lam2, _ = SP.select_modes(og, tg, nd)
     ref = K.devd_solve(og, tg, f, SP.basis(og, modes), lam2, "cg", 1e-11, 3000).u
-    assert info["status"] == "OK"
-    assert info["true_rel_residual"] < 5e-6
+    assert info["status"] == "OK" and info["outer_iterations"] >= 1
+    assert info["true_rel_residual"] < 2e-6
     assert relmax(host(u), ref) < 1e-5
+
+
+def test_c2_fp32_stepping_without_correction():
+    """Plain FP32-stepping CG stops on its recursive residual; its solution error against the
+    FP64 oracle is reported by the benchmark and bounded here at the operator-error level."""
+    w = I.WORKLOADS["c2"]
+    g, og, _ = make(w.npts, precision=whv.WHV_FP32_STEP)
+    tg = WH.time_grid_for(og, w.omega)
+    f = I.forcing_for(w)
+    prm = whv.make_params(w.omega, method="cg", tol=1e-6, maxit=2000)
+    g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
+    u, info = g.whv_solve(prm, dev(f))
+    modes, lam2, _ = SP.select_modes(og, tg, w.nd)
+    ref = K.devd_solve(og, tg, f, SP.basis(og, modes), lam2, "cg", 1e-11, 3000).u
+    assert info["status"] == "OK"
+    assert relmax(host(u), ref) < 1e-4
+
+
+def test_fp32_correction_gmres_variable_speed():
+    npts = (129, 121)
+    g, og, c2 = make(npts, order=4, speed="c3", precision=whv.WHV_FP32_STEP)
+    tg = WH.time_grid_for(og, 25.0)
+    f = I.gaussian(npts, [0.45, 0.55], 1 / 25.0, 625.0)
+    prm = whv.make_params(25.0, method="gmres", restart=30, tol=1e-7, maxit=3000, true_residual=True,
+                          refine_fp64=True)
+    u, info = g.whv_solve(prm, dev(f))
+    U = IND.helmholtz_direct(npts, tg.omega_eff, f, 4, c2)
+    assert info["status"] == "OK" and info["true_rel_residual"] < 2e-7
+    assert relmax(host(u), U) < 1e-5
 
 
 # --------------------------------------------------------------------------- errors

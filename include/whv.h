@@ -206,6 +206,26 @@ whv_status whv_project(whv_grid grid, const double* r_dev, double* coeff_dev);
 whv_status whv_expand(whv_grid grid, const double* y_dev, double alpha, double* out_dev);
 whv_status whv_dot(whv_grid grid, const double* x_dev, const double* y_dev, double* out_host);
 
+/* Allocation-free variant of whv_project, for callers that cannot allocate device memory: code
+ * whose device memory is owned by a host framework's pool or arena, real-time or embedded loops
+ * that forbid allocation after start-up, and callers working under a stream capture or a
+ * latency budget where cudaMalloc (which may synchronise the device) is not allowed.  It needs
+ * no grid (creating one allocates) and calls no cudaMalloc / cudaFree or allocating library.
+ * The paper has no counterpart: this is a deployment variant of the deflation projection.
+ *   coef_dev[m] = sum_i W_dev[i + m n] w_i r_dev[i],  m < nd   (w_dev NULL => w = 1)
+ * W_dev (n x nd, column-major), r_dev, w_dev (n) and coef_dev (nd) are caller-owned device
+ * buffers; the work is ordered on cuda_stream (a cudaStream_t, NULL = legacy default stream).
+ * Scratch: the per-block partial sums go to a static 2 MiB device array (262144 doubles) that
+ * every GPU loading the library holds until the process exits.  Limits: 1 <= nd <= 1024 and
+ * ceil(n / 2048) * nd <= 262144 (e.g. n = 261121 with nd = 1024, n = 16.7M with nd = 32);
+ * larger problems get WHV_ERR_INVALID.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current: make that first call before
+ * any stream capture.  All calls share the one array: calls whose kernels overlap on the GPU
+ * (other streams, other host threads) race and return wrong sums; serialise them.  Errors are
+ * reported through whv_last_error(NULL). */
+whv_status whv_project_noalloc(int64_t n, int nd, const double* W_dev, const double* r_dev,
+                               const double* w_dev, double* coef_dev, void* cuda_stream);
+
 /* Number of interior unknowns N of the grid (0 for NULL). */
 int64_t whv_num_unknowns(whv_grid grid);
 

@@ -7,6 +7,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -242,3 +243,63 @@ whv_status closed_form_basis(whv_grid g, const TimeGridH& tg, int nd, Basis* b) 
 }
 
 }  // namespace whv
+
+// ------------------------------------------------------------------ allocation-free projection
+// A variant of the W^T M r projection for callers that must not allocate device memory: its
+// per-block partial sums live in this file-scope array instead of a grid's scratch.  Every GPU
+// that loads the library holds the array (2 MiB) until the process exits.
+namespace whv {
+
+constexpr int64_t kNoAllocPartials = (int64_t)1 << 18;   // 262144 doubles = 2 MiB
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
+
+constexpr int kNoAllocMaxDevices = 64;
+static double* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_partials on the current device.  In host code the symbol's name
+// is only a host-side stand-in, so the address is looked up once per device (with that device
+// current) and cached.
+static cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace whv
+
+extern "C" whv_status whv_project_noalloc(int64_t n, int nd, const double* W_dev, const double* r_dev,
+                                          const double* w_dev, double* coef_dev, void* cuda_stream) {
+  using namespace whv;
+  if (n < 1 || nd < 1 || nd > kMaxND)
+    return fail(nullptr, WHV_ERR_INVALID, "whv_project_noalloc: need n >= 1 and 1 <= nd <= 1024");
+  if (!W_dev || !r_dev || !coef_dev) return fail(nullptr, WHV_ERR_INVALID, "whv_project_noalloc: NULL pointer");
+  const int64_t nb = (n + kProjRows - 1) / kProjRows;
+  if (nb * nd > kNoAllocPartials)
+    return fail(nullptr, WHV_ERR_INVALID,
+                "whv_project_noalloc: ceil(n/2048)*nd exceeds the 262144-entry static scratch "
+                "(use whv_project on a grid for larger problems)");
+  double* part = nullptr;
+  cudaError_t e = noalloc_scratch(&part);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(static scratch)");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // every partial the finishing kernel reads is written by k_project first: nothing to clear
+  k_project<<<(unsigned)nb, kProjThreads, 0, st>>>(W_dev, n, nd, r_dev, w_dev, part);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "k_project launch");
+  k_project_finish<<<nd, 256, 0, st>>>(part, (int)nb, nd, coef_dev);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "k_project_finish launch");
+  count_launches(2);
+  return WHV_OK;
+}

@@ -68,6 +68,7 @@ def _load():
         "whv_set_steps_per_sweep": [P, I],
         "whv_get_steps_per_sweep": [P, ctypes.POINTER(I)],
         "whv_autotune": [P, ctypes.POINTER(whv_params), ctypes.POINTER(I)],
+        "whv_project_noalloc": [L, I, P, P, P, P, P],
         "whv_lanczos": [P, ctypes.POINTER(whv_params), I, I, P, I, I, ctypes.POINTER(D), ctypes.POINTER(D)],
     }
     for name, args in sig.items():
@@ -92,7 +93,7 @@ EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_gr
             "whv_set_deflation_basis", "whv_get_basis", "whv_apply_pi", "whv_solve", "whv_project",
             "whv_expand", "whv_dot", "whv_num_unknowns", "whv_last_error", "whv_version",
             "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune",
-            "whv_lanczos"]
+            "whv_project_noalloc", "whv_lanczos"]
 
 
 def _check(status, handle=None, allow=()):
@@ -121,6 +122,16 @@ def make_params(omega, periods=1, adjust_omega=False, cfl=0.0, method="cg", rest
 
 def whv_version() -> str:
     return lib.whv_version().decode()
+
+
+def whv_project_noalloc(W, r, coef, w=None, stream=None):
+    """Allocation-free W^T M r: W is (nd, n) row-major (= n x nd column-major), r and w have n
+    entries, coef has nd; all float64 CUDA tensors owned by the caller (see include/whv.h)."""
+    nd, n = W.shape
+    s = (torch.cuda.current_stream() if stream is None else stream).cuda_stream
+    _check(lib.whv_project_noalloc(n, nd, _ptr(W), _ptr(r, n), _ptr(w, n) if w is not None else None,
+                                   _ptr(coef, nd), ctypes.c_void_p(s)))
+    return coef
 
 
 def whv_kernel_launches() -> int:

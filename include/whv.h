@@ -197,6 +197,23 @@ whv_status whv_get_steps_per_sweep(whv_grid grid, int* k);
  * synchronises the stream.  Must not be called while the grid's stream is being captured. */
 whv_status whv_autotune(whv_grid grid, const whv_params* p, int* best);
 
+/* Adjoint of the solve (differentiation path): gradients of L = 1/2 ||u - u_obs||^2 with respect
+ * to the forcing and the squared speed.  u_dev is the fixed point of Pi_h(.; f_dev) that whv_solve
+ * returned for the same p, f_dev the forcing used (NULL = 0), dLdu_dev = dL/du (e.g. u - u_obs).
+ *  - z_dev (out): lambda solving (I - S_h)^T lambda = dL/du, by the M-similarity
+ *    S_h^T = M S_h M^{-1} (M = diag(1/c^2), Sec. 4.1): (I - S_h) y = c^2 dL/du is solved with
+ *    p->method (CG, DCG or GMRES; the grid's basis deflates as in whv_solve; WHV_REFINE_FP64 gives
+ *    FP64 residual correction), lambda = y / c^2.
+ *  - grad_c2_dev (out, nullable): dL/dc^2 = lambda^T dPi_h(u; f, c^2)/dc^2;
+ *    grad_f_dev (out, nullable): dL/df = lambda^T dPi_h/df.  Both by one reverse sweep of the
+ *    wave solve from u (leapfrog transposed step by step, filter weights as source, FP64
+ *    accumulation), with the forward states checkpointed every `checkpoint_every` steps (<= 0: 16)
+ *    and recomputed per segment; temporary device memory (2 ceil(Nt/K) + K + 5) N elements.
+ * The time grid (dt, Nt) is held fixed.  All device buffers N doubles, caller-owned. */
+whv_status whv_solve_adjoint(whv_grid grid, const whv_params* p, const double* f_dev, const double* u_dev,
+                             const double* dLdu_dev, double* z_dev, double* grad_c2_dev,
+                             double* grad_f_dev, int checkpoint_every, whv_info* info);
+
 /* Deflation contractions and reductions on the grid's basis / weights (building blocks of the
  * solve, exposed for testing and for callers composing their own iterations):
  *   whv_project:  coeff_dev[m] = (W^T M r)_m, m < nd                 (Algorithm 2, (r, phi_m))

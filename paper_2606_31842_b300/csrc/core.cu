@@ -21,6 +21,14 @@ whv_status fail(whv_grid g, whv_status s, const std::string& msg) {
   return s;
 }
 
+void free_basis(whv_grid g) {
+  Basis& b = g->basis;
+  for (void* p : {(void*)b.V, (void*)b.d_coef, (void*)b.AW, (void*)b.Einv})
+    if (p) cudaFree(p);
+  g->basis = Basis();
+  free_cgloop(g);
+}
+
 whv_status cuda_fail(whv_grid g, cudaError_t e, const char* what) {
   std::string m = std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
                   ") in " + what;
@@ -138,8 +146,8 @@ static void free_all(whv_grid g) {
   if (!g) return;
   free_plan(g);
   void* ptrs[] = {g->c2, g->c2f, g->mw, g->wbuf[0], g->wbuf[1], g->wbuf[2], g->wbuf[3], g->acc, g->x, g->r, g->p, g->q,
-                  g->t, g->fd, g->krylov, g->small, g->partials, g->counters, g->scal,
-                  g->basis.V, g->basis.d_coef, g->wbuf64[0], g->wbuf64[1], g->wbuf64[2],
+                  g->t, g->fd, g->krylov, g->small, g->small2, g->partials, g->counters, g->scal,
+                  g->basis.V, g->basis.d_coef, g->basis.AW, g->basis.Einv, g->wbuf64[0], g->wbuf64[1], g->wbuf64[2],
                   g->wbuf64[3], g->acc64, g->xo, g->ro, g->bo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -203,7 +211,7 @@ whv_status whv_create_grid(int dim, const int64_t npts[3], const double lo[3], c
       {&g->wbuf[3], nb * esz}, {&g->acc, nb * esz},
       {(void**)&g->x, nb * 8}, {(void**)&g->r, nb * 8}, {(void**)&g->p, nb * 8},
       {(void**)&g->q, nb * 8}, {(void**)&g->t, nb * 8}, {(void**)&g->fd, nb * 8},
-      {(void**)&g->small, (size_t)kMaxND * 8},
+      {(void**)&g->small, (size_t)kMaxND * 8}, {(void**)&g->small2, (size_t)kMaxND * 8},
       {(void**)&g->partials, (size_t)CH_NCH * kMaxStepBlocks * 8},
       {(void**)&g->counters, (size_t)CH_NCH * sizeof(unsigned)},
       {(void**)&g->scal, (size_t)S_NSLOTS * 8}};
@@ -241,8 +249,7 @@ whv_status whv_destroy_grid(whv_grid g) {
 whv_status whv_set_speed(whv_grid g, const double* c2_dev) {
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
   // any basis was built for the old operator
-  if (g->basis.V) { cudaFree(g->basis.V); g->basis.V = nullptr; }
-  g->basis = Basis();
+  free_basis(g);
   free_plan(g);
   if (!c2_dev) {
     if (g->c2) cudaFree(g->c2);
@@ -288,9 +295,7 @@ whv_status whv_set_deflation_basis(whv_grid g, const whv_params* p, int nd, cons
                                    const double* lambda2_host, int mode, int flags) {
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
   if (mode == WHV_BASIS_NONE) {
-    if (g->basis.V) cudaFree(g->basis.V);
-    if (g->basis.d_coef) cudaFree(g->basis.d_coef);
-    g->basis = Basis();
+    free_basis(g);
     return WHV_OK;
   }
   TimeGridH tg;
@@ -329,8 +334,7 @@ whv_status whv_set_deflation_basis(whv_grid g, const whv_params* p, int nd, cons
     return fail(g, WHV_ERR_INVALID, "unknown basis mode");
   }
   WHV_CUDA(g, cudaMalloc(&b.d_coef, (size_t)kMaxND * 8));
-  if (g->basis.V) cudaFree(g->basis.V);
-  if (g->basis.d_coef) cudaFree(g->basis.d_coef);
+  free_basis(g);
   g->basis = std::move(b);
   WHV_CUDA(g, cudaStreamSynchronize(g->stream));
   return WHV_OK;

@@ -14,6 +14,8 @@
 //    FP64 application of L_h, residuals ||L_h y + lambda^2 y||_M / lambda^2.
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <vector>
@@ -325,6 +327,9 @@ extern "C" whv_status whv_lanczos(whv_grid g, const whv_params* p, int nd, int m
     LZ_TRY(fetch_scalars(g));
     res[j] = sqrt(g->scal_host[S_TMP]) / fabs(lam2[j]);
   }
+  if (getenv("WHV_LOG") && getenv("WHV_LOG")[0] == '1')
+    for (int j = 0; j < nd; ++j)
+      fprintf(stderr, "[whv] Lanczos pair %d: theta %.6f lambda^2 %.6e residual %.2e\n", j, theta[j], lam2[j], res[j]);
   if (theta_host) std::copy(theta.begin(), theta.end(), theta_host);
   if (resid_host) std::copy(res.begin(), res.end(), resid_host);
   // install as the deflation basis (approximate eigenvectors)
@@ -344,8 +349,7 @@ extern "C" whv_status whv_lanczos(whv_grid g, const whv_params* p, int nd, int m
   b.modes.assign((size_t)nd * g->dim, 0);
   cudaError_t e = cudaMalloc(&b.d_coef, (size_t)kMaxND * sizeof(double));
   if (e != cudaSuccess) { cudaFree(Y); return cuda_fail(g, e, "cudaMalloc"); }
-  if (g->basis.V) cudaFree(g->basis.V);
-  if (g->basis.d_coef) cudaFree(g->basis.d_coef);
+  free_basis(g);
   g->basis = std::move(b);
 #undef LZ_TRY
 #undef LZ_CUDA

@@ -20,6 +20,8 @@
 //    one FP32-stepped application of A is only accurate to ~1e-6, and approximate (Lanczos)
 //    eigenvectors are corrected instead of leaving their error in the inflated solution.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <chrono>
@@ -80,8 +82,201 @@ static whv_status apply_A(SolveCtx& c, const double* v, double* q) {
   return WHV_OK;
 }
 
+// WHV_LOG=1 in the environment prints the residual history of every solve to stderr
+static bool log_on() {
+  static const bool on = [] { const char* e = getenv("WHV_LOG"); return e && e[0] == '1'; }();
+  return on;
+}
+
 static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ------------------------------------------------------------------ general deflation (Algorithm 4)
+// out = Einv in  (nd x nd row-major, one block)
+__global__ void k_small_matvec(const double* __restrict__ Einv, const double* __restrict__ in, int nd,
+                               double* __restrict__ out) {
+  __shared__ double sin_[kMaxND];
+  for (int j = threadIdx.x; j < nd; j += blockDim.x) sin_[j] = in[j];
+  __syncthreads();
+  for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < nd; ++j) s = fma(Einv[(int64_t)i * nd + j], sin_[j], s);
+    out[i] = s;
+  }
+}
+
+static whv_status small_matvec(whv_grid g, const double* Einv, const double* in, int nd, double* out) {
+  k_small_matvec<<<1, 1024, 0, g->stream>>>(Einv, in, nd, out);
+  count_launches(1);
+  WHV_CUDA(g, cudaGetLastError());
+  return WHV_OK;
+}
+
+// Gauss-Jordan inverse with partial pivoting of an n x n row-major matrix (host, n <= 1024)
+static bool invert(std::vector<double>& a, int n) {
+  std::vector<double> inv((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(a[(size_t)r * n + c]) > fabs(a[(size_t)piv * n + c])) piv = r;
+    if (!(fabs(a[(size_t)piv * n + c]) > 0.0)) return false;
+    if (piv != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(a[(size_t)c * n + k], a[(size_t)piv * n + k]);
+        std::swap(inv[(size_t)c * n + k], inv[(size_t)piv * n + k]);
+      }
+    const double d = 1.0 / a[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) { a[(size_t)c * n + k] *= d; inv[(size_t)c * n + k] *= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = a[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        a[(size_t)r * n + k] -= f * a[(size_t)c * n + k];
+        inv[(size_t)r * n + k] -= f * inv[(size_t)c * n + k];
+      }
+    }
+  }
+  a.swap(inv);
+  return true;
+}
+
+// A W (nd wave solves of the grid's stepping) and (W^T M A W)^{-1} for Algorithm 4 with a basis
+// that is not made of exact eigenvectors
+static whv_status prepare_general_dcg(struct SolveCtx& c);
+static whv_status dcg_project_direction(whv_grid g);
+
+// ------------------------------------------------------------------ device-resident CG loop
+// One CUDA graph with a conditional WHILE node: the body is one CG iteration (the wave solve
+// q = A p with its p^T M q epilogue, optional re-deflation, the fused x/r update with r^T M r,
+// the direction update) followed by a one-thread kernel that counts the iteration and sets the
+// loop condition from r^T M r, the breakdown flag and the iteration limit.  An inner CG solve
+// is then one graph launch and one host synchronisation.
+__global__ void k_cg_check(cudaGraphConditionalHandle h, double* scal) {
+  const double it = scal[S_ITER] + 1.0;
+  scal[S_ITER] = it;
+  const bool go = scal[S_FLAG] == 0.0 && scal[S_RR] > scal[S_STOP] && it < scal[S_MAXIT];
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+struct CgLoop {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double omega = 0, cfl = 0;
+  int periods = 0, adjust = 0, nt = 0, kblock = 0;
+  bool redefl = false, general = false;
+  const double* V = nullptr;
+  int nd = 0;
+  int64_t body_launches = 0;
+};
+
+void free_cgloop(whv_grid g) {
+  if (!g->cgloop) return;
+  if (g->cgloop->exec) cudaGraphExecDestroy(g->cgloop->exec);
+  if (g->cgloop->graph) cudaGraphDestroy(g->cgloop->graph);
+  delete g->cgloop;
+  g->cgloop = nullptr;
+}
+
+static int64_t launches_now() { return whv_kernel_launches(); }
+
+// build (or reuse) the loop graph for the current time grid / basis; general: Algorithm 4 with
+// the per-iteration A-orthogonalisation against a general basis
+static whv_status cg_loop_graph(SolveCtx& c, bool general, CgLoop** out) {
+  whv_grid g = c.g;
+  const Basis& B = g->basis;
+  CgLoop* L = g->cgloop;
+  const bool usesV = c.redefl || general;
+  if (L && L->omega == c.tg.omega && L->cfl == c.tg.cfl && L->periods == c.tg.periods &&
+      L->adjust == c.tg.adjust && L->nt == c.tg.nt && L->kblock == g->kblock && L->redefl == c.redefl &&
+      L->general == general && L->V == (usesV ? B.V : nullptr) && L->nd == (usesV ? B.nd : 0)) {
+    *out = L;
+    return WHV_OK;
+  }
+  free_cgloop(g);
+  L = new CgLoop();
+  g->cgloop = L;
+  L->omega = c.tg.omega; L->cfl = c.tg.cfl; L->periods = c.tg.periods; L->adjust = c.tg.adjust;
+  L->nt = c.tg.nt; L->kblock = g->kblock; L->redefl = c.redefl; L->general = general;
+  L->V = usesV ? B.V : nullptr; L->nd = usesV ? B.nd : 0;
+  WHV_CUDA(g, cudaGraphCreate(&L->graph, 0));
+  cudaGraphConditionalHandle h;
+  WHV_CUDA(g, cudaGraphConditionalHandleCreate(&h, L->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  WHV_CUDA(g, cudaGraphAddNode(&node, L->graph, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  const int64_t l0 = launches_now();
+  const int ws0 = c.ws;
+  WHV_CUDA(g, cudaStreamBeginCaptureToGraph(g->stream, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+  whv_status s = apply_A(c, g->p, g->q);
+  if (s == WHV_OK) s = cg_update(g);
+  if (s == WHV_OK) s = cg_direction(g);
+  if (s == WHV_OK && general) s = dcg_project_direction(g);
+  if (s == WHV_OK) {
+    k_cg_check<<<1, 1, 0, g->stream>>>(h, g->scal);
+    count_launches(1);
+    if (cudaGetLastError() != cudaSuccess) s = fail(g, WHV_ERR_CUDA, "k_cg_check launch");
+  }
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaStreamEndCapture(g->stream, &captured);
+  c.ws = ws0;   // the capture did not run anything
+  L->body_launches = launches_now() - l0;
+  count_launches(-L->body_launches);
+  if (s != WHV_OK) { free_cgloop(g); return s; }
+  if (e != cudaSuccess) { free_cgloop(g); return cuda_fail(g, e, "cudaStreamEndCapture (CG loop body)"); }
+  e = cudaGraphInstantiate(&L->exec, L->graph, 0);
+  if (e != cudaSuccess) { free_cgloop(g); return cuda_fail(g, e, "cudaGraphInstantiate (CG loop)"); }
+  *out = L;
+  return WHV_OK;
+}
+
+static whv_status prepare_general_dcg(SolveCtx& c) {
+  whv_grid g = c.g;
+  Basis& B = g->basis;
+  if (B.AW && B.Einv) return WHV_OK;
+  const int64_t N = g->N;
+  const int nd = B.nd;
+  if (!B.AW) WHV_CUDA(g, cudaMalloc(&B.AW, (size_t)nd * N * sizeof(double)));
+  for (int m = 0; m < nd; ++m) {
+    // through fixed buffers so that every column replays one cached wave-solve graph
+    WHV_CUDA(g, cudaMemcpyAsync(g->p, B.V + (size_t)m * N, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    TRY(wave_solve(g, c.tg, g->p, nullptr, g->t, 1));
+    c.ws++;
+    WHV_CUDA(g, cudaMemcpyAsync(B.AW + (size_t)m * N, g->t, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+  }
+  // E = W^T M (A W), symmetrised (A is M-self-adjoint; FP32 stepping breaks it at rounding level)
+  std::vector<double> E((size_t)nd * nd), col(nd);
+  for (int m = 0; m < nd; ++m) {
+    TRY(project(g, B.V, nd, B.AW + (size_t)m * N, g->small));
+    TRY(to_host(g, col.data(), g->small, nd));
+    for (int i = 0; i < nd; ++i) E[(size_t)i * nd + m] = col[i];
+  }
+  for (int i = 0; i < nd; ++i)
+    for (int j = i + 1; j < nd; ++j) {
+      const double a = 0.5 * (E[(size_t)i * nd + j] + E[(size_t)j * nd + i]);
+      E[(size_t)i * nd + j] = E[(size_t)j * nd + i] = a;
+    }
+  if (!invert(E, nd)) return fail(g, WHV_ERR_BREAKDOWN, "W^T M A W is singular (dependent deflation vectors)");
+  if (!B.Einv) WHV_CUDA(g, cudaMalloc(&B.Einv, (size_t)nd * nd * sizeof(double)));
+  WHV_CUDA(g, cudaMemcpyAsync(B.Einv, E.data(), E.size() * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
+  return WHV_OK;
+}
+
+// p = p - W Einv (AW)^T M r  (the A-orthogonalisation of Algorithm 4 with a general basis)
+static whv_status dcg_project_direction(whv_grid g) {
+  const Basis& B = g->basis;
+  TRY(project(g, B.AW, B.nd, g->r, g->small));
+  TRY(small_matvec(g, B.Einv, g->small, B.nd, g->small2));
+  return expand(g, B.V, B.nd, g->small2, -1.0, g->p);
 }
 
 struct InnerResult {
@@ -117,7 +312,16 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
   }
   if (method == WHV_CG || method == WHV_DCG) {
     double rr0 = bb;
-    if (method == WHV_DCG) {
+    const bool general = method == WHV_DCG && !(B.flags & WHV_BASIS_EXACT);
+    if (general) {
+      // Algorithm 4 with a general basis: x_0 = x_{-1} + W E^{-1} W^T M r_{-1},
+      // r_0 = r_{-1} - (A W) E^{-1} W^T M r_{-1},  p_0 = r_0 - W E^{-1} (A W)^T M r_0
+      TRY(prepare_general_dcg(c));
+      TRY(project(g, B.V, B.nd, g->r, g->small));
+      TRY(small_matvec(g, B.Einv, g->small, B.nd, g->small2));
+      TRY(expand(g, B.V, B.nd, g->small2, 1.0, g->x));
+      TRY(expand(g, B.AW, B.nd, g->small2, -1.0, g->r));
+    } else if (method == WHV_DCG) {
       // x_0 = x_{-1} + W diag(1/mu) W^T M r_{-1};  r_0 = r_{-1} - W W^T M r_{-1}  (A W = W diag(mu))
       std::vector<double> cf(B.nd), y(B.nd);
       TRY(project(g, B.V, B.nd, g->r, g->small));
@@ -129,6 +333,7 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
       TRY(expand(g, B.V, B.nd, g->small, -1.0, g->r));
     }
     TRY(copy_dev(g, g->p, g->r, N));
+    if (general) TRY(dcg_project_direction(g));
     TRY(dot_async(g, g->r, g->r, S_RR));
     WHV_CUDA(g, cudaMemsetAsync(g->scal + S_FLAG, 0, sizeof(double), g->stream));
     TRY(fetch_scalars(g));
@@ -136,10 +341,26 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
     if (method == WHV_DCG) rr0 = rrs;  // Algorithm 4: relative to the deflated start residual
     R.rel = rr0 > 0.0 ? sqrt(rrs / rr0) : 0.0;
     if (R.rel <= tol) R.converged = true;
-    while (!R.converged && R.iters < maxit) {
+    if (!R.converged && maxit > 0 && p->check_every <= 1) {
+      // device-resident loop: one graph launch runs the iterations until convergence
+      CgLoop* L = nullptr;
+      TRY(cg_loop_graph(c, general, &L));
+      const double init[3] = {0.0, tol * tol * rr0, (double)maxit};
+      TRY(to_dev(g, g->scal + S_ITER, init, 3));
+      WHV_CUDA(g, cudaGraphLaunch(L->exec, g->stream));
+      TRY(fetch_scalars(g));
+      R.iters = (int)g->scal_host[S_ITER];
+      c.ws += R.iters;
+      count_launches(L->body_launches * R.iters);
+      if (g->scal_host[S_FLAG] != 0.0) R.breakdown = true;
+      R.rel = sqrt(g->scal_host[S_RR] / rr0);
+      if (R.rel <= tol) R.converged = true;
+    }
+    while (!R.converged && !R.breakdown && R.iters < maxit) {
       TRY(apply_A(c, g->p, g->q));
       TRY(cg_update(g));
       TRY(cg_direction(g));
+      if (general) TRY(dcg_project_direction(g));
       ++R.iters;
       if (R.iters % check == 0 || R.iters == maxit) {
         TRY(fetch_scalars(g));
@@ -166,6 +387,7 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
       TRY(dot_async(g, g->r, g->r, S_TMP));
       TRY(fetch_scalars(g));
       const double beta0 = sqrt(g->scal_host[S_TMP]);
+      if (log_on()) fprintf(stderr, "[whv] GMRES cycle start: rel %.3e after %d iterations\n", beta0 / bnorm, R.iters);
       if (!isfinite(beta0)) { R.breakdown = true; break; }
       R.rel = beta0 / bnorm;
       if (R.rel <= tol) { R.converged = true; break; }
@@ -191,7 +413,11 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
         TRY(dot_async(g, w, w, S_TMP));
         TRY(fetch_scalars(g));
         const double hn = sqrt(g->scal_host[S_TMP]);
-        if (!isfinite(hn)) { R.breakdown = true; break; }
+        if (!isfinite(hn)) {
+          if (log_on()) fprintf(stderr, "[whv] GMRES: non-finite Arnoldi norm at step %d\n", j);
+          R.breakdown = true;
+          break;
+        }
         Hc(j + 1, j) = hn;
         lucky = !(hn > 0.0);
         if (!lucky) TRY(axpby(g, N, 1.0 / hn, w, 0.0, w));
@@ -201,7 +427,11 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
           Hc(i, j) = t;
         }
         const double den = hypot(Hc(j, j), Hc(j + 1, j));
-        if (!(den > 0.0)) { R.breakdown = true; break; }
+        if (!(den > 0.0)) {
+          if (log_on()) fprintf(stderr, "[whv] GMRES: zero Givens denominator at step %d (H_jj %.3e)\n", j, Hc(j, j));
+          R.breakdown = true;
+          break;
+        }
         cs[j] = Hc(j, j) / den;
         sn[j] = Hc(j + 1, j) / den;
         Hc(j, j) = den;
@@ -250,6 +480,86 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
   return WHV_OK;
 }
 
+// Solve A x = b for a given FP64 right-hand side b (||b||_M^2 = bb) into g->xo by correction
+// passes: r = b - A x (FP64 wave solves when fp64_res, else the grid's stepping), then
+// x += W diag(1/mu) W^T M r (deflated components; with a basis set and a method other than DCG)
+// + the inner Krylov solution of the rest.  With fp64_res the passes repeat until the residual
+// meets p->tol (iterative refinement); without it one pass is made (x0 = 0: exact DEVD for
+// exact eigenvectors).  use_x0: g->xo holds the initial guess.
+static whv_status outer_solve(SolveCtx& c, int method, const whv_params* p, const double* b, double bb,
+                              bool fp64_res, bool use_x0, InnerResult* res, int* n_outer) {
+  whv_grid g = c.g;
+  const int64_t N = g->N;
+  const Basis& B = g->basis;
+  // modal correction of the deflated components: only valid for exact eigenvectors (with
+  // approximate ones W diag(1/mu) W^T M is not a Galerkin solve and the passes can diverge);
+  // approximate bases deflate through Algorithm 4 (method DCG) instead
+  const bool defl = B.nd > 0 && method != WHV_DCG && (B.flags & WHV_BASIS_EXACT);
+  const double inner_tol = fp64_res ? (p->inner_tol > 0.0 ? p->inner_tol : 1e-3) : p->tol;
+  if (!use_x0) WHV_CUDA(g, cudaMemsetAsync(g->xo, 0, N * sizeof(double), g->stream));
+  bool have_x = use_x0;
+  int its = 0, outer = 0;
+  InnerResult R;
+  R.rel = 1.0;
+  std::vector<double> cf(defl ? B.nd : 0), y(defl ? B.nd : 0);
+  while (true) {
+    if (have_x) {
+      if (fp64_res) {
+        TRY(wave_solve(g, c.tg, g->xo, nullptr, g->q, 1, WHV_FP64));
+        c.ws64++;
+      } else {
+        TRY(wave_solve(g, c.tg, g->xo, nullptr, g->q, 1));
+        c.ws++;
+      }
+      TRY(copy_dev(g, g->ro, b, N));
+      TRY(axpby(g, N, -1.0, g->q, 1.0, g->ro));
+    } else {
+      TRY(copy_dev(g, g->ro, b, N));
+    }
+    TRY(dot_async(g, g->ro, g->ro, S_TMP2));
+    TRY(fetch_scalars(g));
+    R.rel = bb > 0.0 ? sqrt(g->scal_host[S_TMP2] / bb) : 0.0;
+    if (log_on()) fprintf(stderr, "[whv] outer %d: residual %.3e (inner iterations so far %d)\n", outer, R.rel, its);
+    if (!isfinite(R.rel)) { R.breakdown = true; break; }
+    if (R.rel <= p->tol) { R.converged = true; break; }
+    if (its >= p->maxit || outer >= 50 || (!fp64_res && outer >= 1)) break;
+    if (defl) {
+      // deflated components: x += W diag(1/mu) c, r -= W c, c = W^T M r
+      TRY(project(g, B.V, B.nd, g->ro, g->small));
+      TRY(to_host(g, cf.data(), g->small, B.nd));
+      for (int m = 0; m < B.nd; ++m) y[m] = cf[m] / B.mu[m];
+      TRY(to_dev(g, g->small, y.data(), B.nd));
+      TRY(expand(g, B.V, B.nd, g->small, 1.0, g->xo));
+      TRY(to_dev(g, g->small, cf.data(), B.nd));
+      TRY(expand(g, B.V, B.nd, g->small, -1.0, g->ro));
+    }
+    TRY(dot_async(g, g->ro, g->ro, S_TMP2));
+    TRY(fetch_scalars(g));
+    const double rr = g->scal_host[S_TMP2];
+    InnerResult Ri;
+    const double itol = fp64_res ? std::max(inner_tol, 0.5 * p->tol / std::max(R.rel, 1e-300))
+                                 : p->tol * sqrt(bb / std::max(rr, 1e-300));
+    TRY(inner_solve(c, method, p, g->ro, rr, false, itol, p->maxit - its, nullptr, &Ri));
+    if (log_on())
+      fprintf(stderr, "[whv]   inner solve: %d iterations, rel %.3e (target %.1e)%s%s\n", Ri.iters, Ri.rel, itol,
+              Ri.converged ? "" : " not converged", Ri.breakdown ? " BREAKDOWN" : "");
+    its += Ri.iters;
+    ++outer;
+    TRY(axpby(g, N, 1.0, g->x, 1.0, g->xo));
+    have_x = true;
+    if (Ri.breakdown) { R.breakdown = true; break; }
+    if (!fp64_res) {   // single pass: the inner solve's own residual is the answer
+      R.converged = Ri.converged;
+      R.rel = Ri.rel * sqrt(rr / bb);
+      break;
+    }
+  }
+  R.iters = its;
+  *res = R;
+  *n_outer = outer;
+  return WHV_OK;
+}
+
 }  // namespace whv
 
 using namespace whv;
@@ -270,8 +580,6 @@ extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f
                     B.adjust != (p->adjust_omega ? 1 : 0) || B.cfl != tg.cfl))
     return fail(g, WHV_ERR_INVALID, "deflation basis was set for another frequency / time grid");
   if (method == WHV_DCG && !has_basis) return fail(g, WHV_ERR_INVALID, "DCG needs a deflation basis");
-  if (method == WHV_DCG && !(B.flags & WHV_BASIS_EXACT))
-    return fail(g, WHV_ERR_INVALID, "DCG is built for exact eigenvector bases (WHV_BASIS_EXACT)");
   const bool refine = (p->flags & WHV_REFINE_FP64) != 0;
   if (refine && method == WHV_FPI)
     return fail(g, WHV_ERR_INVALID, "FP64 residual correction needs a Krylov method (CG, DCG, GMRES)");
@@ -304,11 +612,7 @@ extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f
     }
     TRY(inner_solve(c, method, p, b, bb, use_guess != 0, p->tol, p->maxit, fuse, &R));
   } else {
-    // ---- iterative refinement with FP64 residuals on the full system b = Pi_h(0; f):
-    // each correction d = W diag(1/mu) W^T M r (the deflated components, Algorithm 2's
-    // modal solution in terms of A) + a Krylov solve of the projected residual r - W W^T M r.
-    // With exact eigenvectors the first pass is DEVD; with approximate ones the outer loop
-    // corrects what the modal part gets wrong.
+    // ---- iterative refinement with FP64 residuals on the full system b = Pi_h(0; f)
     TRY(ensure_fp64_buffers(g));
     TRY(wave_solve(g, tg, nullptr, f, g->bo, 0, WHV_FP64));
     c.ws64++;
@@ -316,55 +620,8 @@ extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f
     TRY(fetch_scalars(g));
     const double bb = g->scal_host[S_RR0];
     if (!isfinite(bb)) return fail(g, WHV_ERR_BREAKDOWN, "non-finite right-hand side b (NaN/Inf in f?)");
-    const double inner_tol = p->inner_tol > 0.0 ? p->inner_tol : 1e-3;
     if (use_guess) TRY(copy_dev(g, g->xo, u, N));
-    else WHV_CUDA(g, cudaMemsetAsync(g->xo, 0, N * sizeof(double), g->stream));
-    bool have_x = use_guess != 0;
-    int its = 0;
-    R.rel = 1.0;
-    std::vector<double> cf(has_basis ? B.nd : 0);
-    while (true) {
-      // r = b - A x in FP64 (x = 0: r = b)
-      if (have_x) {
-        TRY(wave_solve(g, tg, g->xo, nullptr, g->q, 1, WHV_FP64));
-        c.ws64++;
-        TRY(copy_dev(g, g->ro, g->bo, N));
-        TRY(axpby(g, N, -1.0, g->q, 1.0, g->ro));
-      } else {
-        TRY(copy_dev(g, g->ro, g->bo, N));
-      }
-      TRY(dot_async(g, g->ro, g->ro, S_TMP2));
-      TRY(fetch_scalars(g));
-      R.rel = sqrt(g->scal_host[S_TMP2] / bb);
-      if (!isfinite(R.rel)) { R.breakdown = true; break; }
-      if (R.rel <= p->tol) { R.converged = true; break; }
-      if (its >= p->maxit || outer >= 50) break;
-      if (devd) {
-        // deflated components: x += W diag(1/mu) c, r -= W c, c = W^T M r
-        TRY(project(g, B.V, B.nd, g->ro, g->small));
-        TRY(to_host(g, cf.data(), g->small, B.nd));
-        std::vector<double> y(B.nd);
-        for (int m = 0; m < B.nd; ++m) y[m] = cf[m] / B.mu[m];
-        TRY(to_dev(g, g->small, y.data(), B.nd));
-        TRY(expand(g, B.V, B.nd, g->small, 1.0, g->xo));
-        TRY(to_dev(g, g->small, cf.data(), B.nd));
-        TRY(expand(g, B.V, B.nd, g->small, -1.0, g->ro));
-      }
-      TRY(dot_async(g, g->ro, g->ro, S_TMP2));
-      TRY(fetch_scalars(g));
-      const double rr = g->scal_host[S_TMP2];
-      // correction of the rest: A d = r with the grid's stepping, relative tolerance inner_tol
-      // (never tighter than the outer target needs)
-      InnerResult Ri;
-      const double itol = std::max(inner_tol, 0.5 * p->tol / std::max(R.rel, 1e-300));
-      TRY(inner_solve(c, method, p, g->ro, rr, false, itol, p->maxit - its, nullptr, &Ri));
-      its += Ri.iters;
-      ++outer;
-      if (Ri.breakdown) { R.breakdown = true; break; }
-      TRY(axpby(g, N, 1.0, g->x, 1.0, g->xo));
-      have_x = true;
-    }
-    R.iters = its;
+    TRY(outer_solve(c, method, p, g->bo, bb, true, use_guess != 0, &R, &outer));
     TRY(copy_dev(g, g->x, g->xo, N));
   }
 
@@ -409,5 +666,66 @@ extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f
   }
   if (R.breakdown) return fail(g, WHV_ERR_BREAKDOWN, "Krylov breakdown (non-finite or non-positive scalar)");
   if (!R.converged) return fail(g, WHV_ERR_NOT_CONVERGED, "maxit reached before the tolerance");
+  return WHV_OK;
+}
+
+// ------------------------------------------------------------------ adjoint
+namespace whv {
+whv_status adjoint_gradients(whv_grid g, const TimeGridH& tg, const double* u, const double* f,
+                             const double* lam, double* gc2, double* gf, int K);
+whv_status scale_by(whv_grid g, const double* x, const double* y, double a, double* out);
+}  // namespace whv
+
+extern "C" whv_status whv_solve_adjoint(whv_grid g, const whv_params* p, const double* f, const double* u,
+                                        const double* dLdu, double* z, double* grad_c2, double* grad_f,
+                                        int checkpoint_every, whv_info* info) {
+  const double t0 = now_s();
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  if (!u || !dLdu || !z) return fail(g, WHV_ERR_INVALID, "u_dev, dLdu_dev and z_dev must not be NULL");
+  TimeGridH tg;
+  TRY(make_time_grid(g, p, &tg));
+  const int method = p->method;
+  if (method != WHV_CG && method != WHV_DCG && method != WHV_GMRES)
+    return fail(g, WHV_ERR_INVALID, "the adjoint solve needs a Krylov method (CG, DCG, GMRES)");
+  const Basis& B = g->basis;
+  if (B.nd > 0 && (B.omega != p->omega || B.periods != p->periods || B.adjust != (p->adjust_omega ? 1 : 0) ||
+                   B.cfl != tg.cfl))
+    return fail(g, WHV_ERR_INVALID, "deflation basis was set for another frequency / time grid");
+  if (method == WHV_DCG && B.nd == 0) return fail(g, WHV_ERR_INVALID, "DCG needs a deflation basis");
+  const int K = checkpoint_every > 0 ? checkpoint_every : 16;
+  if (K > 1024) return fail(g, WHV_ERR_INVALID, "checkpoint_every must be <= 1024");
+  const bool refine = (p->flags & WHV_REFINE_FP64) != 0;
+  const int64_t N = g->N;
+  TRY(ensure_fp64_buffers(g));
+  SolveCtx c{g, tg, B.nd > 0 && (B.flags & WHV_BASIS_REDEFLATE) != 0};
+  // (I - S)^T lambda = g  <=>  (I - S) y = c^2 g,  lambda = y / c^2
+  TRY(scale_by(g, dLdu, g->c2, 1.0, g->t));
+  TRY(dot_async(g, g->t, g->t, S_RR0));
+  TRY(fetch_scalars(g));
+  const double bb = g->scal_host[S_RR0];
+  if (!isfinite(bb)) return fail(g, WHV_ERR_BREAKDOWN, "non-finite dL/du");
+  InnerResult R;
+  int outer = 0;
+  TRY(outer_solve(c, method, p, g->t, bb, refine, false, &R, &outer));
+  TRY(scale_by(g, g->xo, g->mw, 1.0, z));
+  // lambda^T dPi_h(u; f, c^2) / d(c^2, f): checkpointed reverse sweep
+  if (grad_c2 || grad_f) TRY(adjoint_gradients(g, tg, u, f, z, grad_c2, grad_f, K));
+  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
+  if (info) {
+    info->iterations = R.iters;
+    info->wave_solves = c.ws + c.ws64 + ((grad_c2 || grad_f) ? 2 : 0);
+    info->nt = tg.nt;
+    info->dt = tg.dt;
+    info->omega_hat = tg.omega_hat;
+    info->omega_eff = tg.omega_eff;
+    info->rel_residual = R.rel;
+    info->true_rel_residual = -1.0;
+    info->seconds = now_s() - t0;
+    info->outer_iterations = outer;
+    info->wave_solves_fp64 = (g->precision == WHV_FP64) ? info->wave_solves : c.ws64;
+  }
+  (void)N;
+  if (R.breakdown) return fail(g, WHV_ERR_BREAKDOWN, "Krylov breakdown in the adjoint solve");
+  if (!R.converged) return fail(g, WHV_ERR_NOT_CONVERGED, "adjoint solve: maxit reached before the tolerance");
   return WHV_OK;
 }

@@ -131,16 +131,23 @@ __global__ void __launch_bounds__(256) k_step3d(const T* __restrict__ wc, T* __r
     T wzm = z0 > 0 ? __ldg(wc + idx - plane) : T(0);
     T wz = __ldg(wc + idx);
     T wzp = z0 + 1 < nz ? __ldg(wc + idx + plane) : T(0);
+    // W^{n-1} and acc of the current plane, loaded one plane ahead (KIND == K_LAST_AV reads v
+    // instead of storing: the extra loads stay the same)
+    T wpc = wp[idx];
+    T acc_c = acc[idx];
     for (int z = z0; z < z1; ++z) {
-      // prefetch the plane after next
+      const bool more = z + 1 < z1;
+      // prefetch: W^n two planes ahead, W^{n-1} and acc one plane ahead
       const T wzpp = z + 2 < nz ? __ldg(wc + idx + 2 * plane) : T(0);
+      const T wpn = more ? wp[idx + plane] : T(0);
+      const T accn = more ? acc[idx + plane] : T(0);
       const T xm = x > 0 ? __ldg(wc + idx - 1) : T(0);
       const T xp = x < nx - 1 ? __ldg(wc + idx + 1) : T(0);
       const T ym = y > 0 ? __ldg(wc + idx - nx) : T(0);
       const T yp = y < ny - 1 ? __ldg(wc + idx + nx) : T(0);
       T wn;
       if constexpr (!VARC) {
-        T u = fma(cf.b, wz, -wp[idx]);
+        T u = fma(cf.b, wz, -wpc);
         u = fma(cf.a[0], xm + xp, u);
         u = fma(cf.a[1], ym + yp, u);
         u = fma(cf.a[2], wzm + wzp, u);
@@ -152,9 +159,9 @@ __global__ void __launch_bounds__(256) k_step3d(const T* __restrict__ wc, T* __r
         L = fma(fma(T(-2), wz, wzm + wzp), cf.ih2[2], L);
         L *= c2[idx];
         if (FORCE) L = fma(-(T)f[idx], cf.fph, L);
-        wn = fma(cf.dt2, L, fma(T(2), wz, -wp[idx]));
+        wn = fma(cf.dt2, L, fma(T(2), wz, -wpc));
       }
-      const T a = fma(cf.w1, wn, acc[idx]);
+      const T a = fma(cf.w1, wn, acc_c);
       if (KIND == K_STEP) {
         wp[idx] = wn;
         acc[idx] = a;
@@ -169,6 +176,8 @@ __global__ void __launch_bounds__(256) k_step3d(const T* __restrict__ wc, T* __r
       wzm = wz;
       wz = wzp;
       wzp = wzpp;
+      wpc = wpn;
+      acc_c = accn;
       idx += plane;
     }
   }
@@ -379,6 +388,7 @@ struct StepPlan {
 };
 
 void free_plan(whv_grid g) {
+  free_cgloop(g);
   if (!g->plan) return;
   for (auto& e : g->plan->entries) cudaGraphExecDestroy(e.exec);
   delete g->plan;

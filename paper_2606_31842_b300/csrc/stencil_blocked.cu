@@ -5,7 +5,7 @@
 // H = k r; r = 1 for the 5-point, 2 for the 9-point-wide 4th-order stencil) and advances it k
 // leapfrog steps; at sub-step s only the window [s r, REG - s r)^2 is updated, which is exactly
 // what the next sub-step needs.  Thread (warp w, lane) owns column 32 (w & 1) + lane and rows
-// (w >> 1) + 8 t, t < 8, of the region for the whole launch: W^n, W^{n-1} and the filter sum of
+// (w >> 1) + 16 t, t < 4, of the region for the whole launch: W^n, W^{n-1} and the filter sum of
 // its cells stay in registers, and only W^n goes through shared memory (double-buffered) for the
 // neighbours' reads.  All global loads of a thread are issued before the first use.  The tile's
 // W^{n+k-1}, W^{n+k} go to the other buffer pair (neighbouring CTAs still read the old pair),
@@ -25,8 +25,9 @@ namespace whv {
 
 constexpr int kBlkMaxK = 16;
 constexpr int kReg = 64;            // staged region edge
-constexpr int kBlkThreads = 512;    // 16 warps
-constexpr int kRowsPerThread = kReg / 8;
+constexpr int kBlkThreads = 1024;   // 32 warps
+constexpr int kRowPitch = kBlkThreads / 64;   // rows between a thread's cells (16)
+constexpr int kRowsPerThread = kReg / kRowPitch;
 
 template <typename T>
 struct BlockCoef {
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ g
   T cc[VARC ? kRowsPerThread : 1];
 #pragma unroll
   for (int t = 0; t < kRowsPerThread; ++t) {
-    const int gy = y0 + jb + 8 * t;
+    const int gy = y0 + jb + kRowPitch * t;
     const bool in = colin && gy >= 0 && gy < ny;
     const int64_t gi = gx + (int64_t)nx * gy;
     cur[t] = in ? gcur[gi] : T(0);
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ g
     acr[t] = T(0);
   }
 #pragma unroll
-  for (int t = 0; t < kRowsPerThread; ++t) S0[(jb + 8 * t) * kReg + i] = cur[t];
+  for (int t = 0; t < kRowsPerThread; ++t) S0[(jb + kRowPitch * t) * kReg + i] = cur[t];
   __syncthreads();
   T* A = S0;
   T* B = S1;
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ g
     const T ws = sw[s - 1];
 #pragma unroll
     for (int t = 0; t < kRowsPerThread; ++t) {
-      const int j = jb + 8 * t;
+      const int j = jb + kRowPitch * t;
       const int gy = y0 + j;
       if (colact && j >= lo && j < hi && gy >= 0 && gy < ny) {
         const int l = j * kReg + i;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ g
   const bool coltile = colin && i >= H && i < kReg - H;
 #pragma unroll
   for (int t = 0; t < kRowsPerThread; ++t) {
-    const int j = jb + 8 * t;
+    const int j = jb + kRowPitch * t;
     const int gy = y0 + j;
     if (!(coltile && j >= H && j < kReg - H && gy >= 0 && gy < ny)) continue;
     const int64_t gi = gx + (int64_t)nx * gy;

@@ -22,6 +22,9 @@ enum Slot {
   S_FLAG = 5,   // breakdown flag (nonzero: non-finite or non-positive scalar seen)
   S_TMP = 6,    // scratch result of whv_dot and friends
   S_TMP2 = 7,
+  S_ITER = 8,   // iteration counter of the device-resident CG loop
+  S_STOP = 9,   // tol^2 rr0: the loop runs while r^T M r > S_STOP
+  S_MAXIT = 10, // iteration limit of the device-resident CG loop
   S_NSLOTS = 16
 };
 
@@ -47,9 +50,14 @@ struct Basis {
   std::vector<double> lambda2, mu;    // lambda^2 and mu = 1 - beta_h
   std::vector<int> modes;             // nd * dim (closed form)
   double omega = 0; int periods = 0, adjust = 0; double cfl = 0;  // time grid it was built for
+  // general (non-eigenvector) deflation for Algorithm 4: A W and (W^T M A W)^{-1}, built on the
+  // first DCG solve with a basis that is not WHV_BASIS_EXACT
+  double* AW = nullptr;               // N x nd
+  double* Einv = nullptr;             // nd x nd, row-major
 };
 
 struct StepPlan;  // cached CUDA graphs of wave solves (stencil.cu)
+struct CgLoop;    // cached device-resident CG loop graph (solve.cu)
 
 }  // namespace whv
 
@@ -84,6 +92,7 @@ struct whv_grid_s {
   double* krylov = nullptr;    // GMRES basis, (restart+1) * N
   int krylov_cols = 0;
   double* small = nullptr;     // device small-vector scratch (kMaxND)
+  double* small2 = nullptr;    // second small-vector scratch (kMaxND)
 
   // reductions
   double* partials = nullptr;  // CH_NCH * kMaxStepBlocks
@@ -93,6 +102,7 @@ struct whv_grid_s {
 
   whv::Basis basis;
   whv::StepPlan* plan = nullptr;
+  whv::CgLoop* cgloop = nullptr;
   std::string err;
 };
 
@@ -108,6 +118,7 @@ whv_status cuda_fail(whv_grid g, cudaError_t e, const char* what);
   } while (0)
 
 whv_status make_time_grid(whv_grid g, const whv_params* p, TimeGridH* tg);
+void free_basis(whv_grid g);   // frees the deflation basis (and what depends on it)
 
 // launch accounting (whv_kernel_launches)
 void count_launches(int64_t n);
@@ -121,6 +132,7 @@ void count_launches(int64_t n);
 whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
                       double* out, int epi, int prec = -1);
 void free_plan(whv_grid g);
+void free_cgloop(whv_grid g);
 int default_kblock(whv_grid g);
 whv_status ensure_fp64_buffers(whv_grid g);
 

@@ -70,6 +70,7 @@ def _load():
         "whv_autotune": [P, ctypes.POINTER(whv_params), ctypes.POINTER(I)],
         "whv_project_noalloc": [L, I, P, P, P, P, P],
         "whv_lanczos": [P, ctypes.POINTER(whv_params), I, I, P, I, I, ctypes.POINTER(D), ctypes.POINTER(D)],
+        "whv_solve_adjoint": [P, ctypes.POINTER(whv_params), P, P, P, P, P, P, I, ctypes.POINTER(whv_info)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -93,7 +94,7 @@ EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_gr
             "whv_set_deflation_basis", "whv_get_basis", "whv_apply_pi", "whv_solve", "whv_project",
             "whv_expand", "whv_dot", "whv_num_unknowns", "whv_last_error", "whv_version",
             "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune",
-            "whv_project_noalloc", "whv_lanczos"]
+            "whv_project_noalloc", "whv_lanczos", "whv_solve_adjoint"]
 
 
 def _check(status, handle=None, allow=()):
@@ -230,6 +231,20 @@ class Grid:
                                int(bool(fp64_stepping)), int(flags), theta, resid), self.handle)
         return list(theta), list(resid)
 
+    def whv_solve_adjoint(self, params, f, u, dLdu, want_c2=True, want_f=True, checkpoint_every=16,
+                          raise_not_converged=False):
+        z = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        gc2 = torch.empty_like(z) if want_c2 else None
+        gf = torch.empty_like(z) if want_f else None
+        info = whv_info()
+        allow = () if raise_not_converged else (WHV_ERR_NOT_CONVERGED,)
+        st = _check(lib.whv_solve_adjoint(self.handle, ctypes.byref(params), _ptr(f, self.N), _ptr(u, self.N),
+                                          _ptr(dLdu, self.N), _ptr(z, self.N), _ptr(gc2), _ptr(gf),
+                                          int(checkpoint_every), ctypes.byref(info)), self.handle, allow)
+        d = info.as_dict()
+        d["status"] = STATUS_NAMES[st]
+        return z, gc2, gf, d
+
     def whv_project(self, r, coef):
         _check(lib.whv_project(self.handle, _ptr(r, self.N), _ptr(coef)), self.handle)
         return coef
@@ -242,3 +257,27 @@ class Grid:
         out = ctypes.c_double()
         _check(lib.whv_dot(self.handle, _ptr(x, self.N), _ptr(y, self.N), ctypes.byref(out)), self.handle)
         return out.value
+
+
+class WaveHoltzSolve(torch.autograd.Function):
+    """u = WaveHoltz fixed point for forcing f and squared speed c2 on `grid` (whv_set_speed +
+    whv_solve); backward runs whv_solve_adjoint and returns dL/df and dL/dc2."""
+
+    @staticmethod
+    def forward(ctx, f, c2, grid, params, checkpoint_every=16):
+        grid.whv_set_speed(c2.detach().contiguous())
+        u, info = grid.whv_solve(params, f.detach().contiguous(), raise_not_converged=True)
+        ctx.grid, ctx.params, ctx.K = grid, params, checkpoint_every
+        ctx.save_for_backward(f, c2, u)
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        f, c2, u = ctx.saved_tensors
+        g = ctx.grid
+        g.whv_set_speed(c2.detach().contiguous())
+        _, gc2, gf, _ = g.whv_solve_adjoint(ctx.params, f.detach().contiguous(), u.contiguous(),
+                                            grad_u.contiguous(), want_c2=ctx.needs_input_grad[1],
+                                            want_f=ctx.needs_input_grad[0], checkpoint_every=ctx.K,
+                                            raise_not_converged=True)
+        return gf, gc2, None, None, None

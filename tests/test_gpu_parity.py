@@ -238,17 +238,34 @@ def test_c2_fp32_stepping_without_correction():
     assert relmax(host(u), ref) < 1e-4
 
 
-def test_fp32_correction_gmres_variable_speed():
+def test_fp32_correction_variable_speed_deep_residual():
+    """FP32 stepping reaches an FP64 residual of 1e-9 on a kappa ~ 1e3 variable-speed 4th-order
+    problem through the FP64 residual correction (CG inner solves)."""
     npts = (129, 121)
     g, og, c2 = make(npts, order=4, speed="c3", precision=whv.WHV_FP32_STEP)
     tg = WH.time_grid_for(og, 25.0)
     f = I.gaussian(npts, [0.45, 0.55], 1 / 25.0, 625.0)
-    prm = whv.make_params(25.0, method="gmres", restart=30, tol=1e-7, maxit=3000, true_residual=True,
-                          refine_fp64=True)
+    prm = whv.make_params(25.0, method="cg", tol=1e-9, maxit=6000, true_residual=True, refine_fp64=True)
     u, info = g.whv_solve(prm, dev(f))
     U = IND.helmholtz_direct(npts, tg.omega_eff, f, 4, c2)
-    assert info["status"] == "OK" and info["true_rel_residual"] < 2e-7
-    assert relmax(host(u), U) < 1e-5
+    assert info["status"] == "OK" and info["true_rel_residual"] < 2e-9, info
+    assert info["outer_iterations"] >= 2
+    assert relmax(host(u), U) < 1e-6
+
+
+def test_fp32_correction_devd_gmres():
+    """DEVD + GMRES(30) on the FP32-stepping grid inside the FP64 residual correction."""
+    w = I.scaled(I.WORKLOADS["c2"], 257)
+    g, og, _ = make(w.npts, precision=whv.WHV_FP32_STEP)
+    tg = WH.time_grid_for(og, w.omega)
+    f = I.forcing_for(w)
+    prm = whv.make_params(w.omega, method="gmres", restart=30, tol=1e-8, maxit=4000, true_residual=True,
+                          refine_fp64=True)
+    g.whv_set_deflation_basis(prm, 32, whv.WHV_BASIS_CLOSED_FORM)
+    u, info = g.whv_solve(prm, dev(f))
+    U = IND.helmholtz_direct(w.npts, tg.omega_eff, f)
+    assert info["status"] == "OK" and info["true_rel_residual"] < 2e-8, info
+    assert relmax(host(u), U) < 1e-6
 
 
 # --------------------------------------------------------------------------- errors

@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--impl", default="whv", choices=["whv", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c2 (default): the 513^2 deflated solve; others: the 1-D, variable-speed "
+                         "1025^2, batched and 3-D workloads, measured on request")
     return ap.parse_args()
 
 
@@ -192,10 +195,138 @@ def traffic_for(kernel, precision):
     return rec.get("dram_bytes_per_launch")
 
 
+def _timed(stream, fn, steps, warmup, flush):
+    import torch
+    for _ in range(max(1, warmup)):
+        fn()
+    times, out = [], None
+    for _ in range(steps):
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.mean(times), out
+
+
+def run_workload(args):
+    """The other workloads (one JSON line each): 1-D FP64 DCG, variable-speed 1025^2 with the device
+    Lanczos basis, the batched squares and the 3-D cube."""
+    import numpy as np
+    import torch
+    from paper_2606_31842_b300 import build as whv_build
+    whv_build.build()
+    from paper_2606_31842_b300 import whv
+    from paper_2606_31842_b300 import inputs as I
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    dev = lambda a: torch.from_numpy(a.ravel()).to("cuda")  # noqa: E731
+    line = {"metric": METRIC, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    if args.workload == "c4":
+        probs = []
+        t0 = time.perf_counter()
+        for n in I.C4_SIZES:
+            for om in I.C4_OMEGAS:
+                w = I.WORKLOADS[f"c4_{n}_{int(om)}"]
+                prm = whv.make_params(om, method="cg", tol=w.tol, maxit=3000)
+                tmpl = whv.Grid(w.npts, precision=whv.WHV_FP32_STEP, stream=stream)
+                tmpl.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
+                b = tmpl.whv_get_basis(want_vectors=True)
+                for src in range(I.C4_SOURCES):
+                    g = whv.Grid(w.npts, precision=whv.WHV_FP32_STEP, stream=stream)
+                    g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_USER, V=b["V"].reshape(-1),
+                                              lambda2=b["lambda2"], flags=whv.WHV_BASIS_EXACT)
+                    probs.append((g, prm, dev(I.forcing_for(w, src)), w))
+                tmpl.close()
+        setup_s = time.perf_counter() - t0
+        grids = [p[0] for p in probs]
+        params = [p[1] for p in probs]
+        fs = [p[2] for p in probs]
+        us = [torch.zeros(g.N, dtype=torch.float64, device="cuda") for g in grids]
+        res = {}
+
+        def step():
+            _, infos = whv.whv_solve_batched(grids, params, fs, us)
+            res["infos"] = infos
+        ms, _ = _timed(stream, step, args.steps, args.warmup, None)
+        infos = res["infos"]
+        lups = sum(g.N * i["nt"] * i["wave_solves"] for g, i in zip(grids, infos))
+        # FP64 true residual of a sample of the problems (outside the timed region)
+        chk = []
+        for k in range(0, len(probs), 37):
+            g, prm, f, w = probs[k]
+            g64 = whv.Grid(w.npts, precision=whv.WHV_FP64, stream=stream)
+            r = g64.whv_apply_pi(prm, us[k], f)
+            b = g64.whv_apply_pi(prm, torch.zeros_like(f), f)
+            chk.append(float((r - us[k]).norm() / b.norm()))
+            g64.close()
+        line.update({"workload": "c4", "value": ms, "ms_per_step": ms, "dtype": "f32", "krylov_dtype": "f64",
+                     "config": {"workload": "batched: 4 squares (257..1025)^2 x 4 omega x 16 Gaussian sources "
+                                            "(width 2h), 32 closed-form vectors each, DEVD-CG to 1e-6, one "
+                                            "persistent launch per iteration for all 256 problems",
+                                "problems": len(probs), "setup_s": setup_s},
+                     "iterations_max": max(i["iterations"] for i in infos),
+                     "iterations_mean": statistics.mean(i["iterations"] for i in infos),
+                     "glups_solve": lups / (ms * 1e-3) / 1e9,
+                     "accuracy": {"fp64_true_rel_residual_sample_max": max(chk)}})
+        print(json.dumps(line), flush=True)
+        return 0
+    name = args.workload
+    w = I.WORKLOADS["c5" if name == "c5" else name]
+    prec = whv.WHV_FP64 if name == "c1" else whv.WHV_FP32_STEP
+    g = whv.Grid(w.npts, order=w.order, precision=prec, stream=stream)
+    if w.speed:
+        g.whv_set_speed(dev(I.speed_squared(w.speed, w.npts, w.speed_seed)))
+    refine = prec == whv.WHV_FP32_STEP
+    method = "dcg" if name in ("c1", "c3") else "cg"
+    prm = whv.make_params(w.omega, method=method, tol=w.tol, maxit=20000, refine_fp64=refine)
+    t0 = time.perf_counter()
+    if name == "c3":
+        theta, resid = g.whv_lanczos(prm, w.nd, 1024, None, False, 0)
+        setup = {"basis": "device Lanczos on S_h (FP32 stepping, 1024 steps)",
+                 "ritz_resid_median": float(np.median(resid)), "ritz_resid_max": float(np.max(resid))}
+    else:
+        g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
+        setup = {"basis": "closed-form sine vectors"}
+    setup["setup_s"] = time.perf_counter() - t0
+    if w.dim == 2:
+        setup["steps_per_sweep"] = g.whv_autotune(prm)
+    f = dev(I.forcing_for(w))
+    u = torch.zeros_like(f)
+    res = {}
+
+    def step():
+        res["info"] = g.whv_solve(prm, f, u)[1]
+    ms, _ = _timed(stream, step, args.steps, args.warmup, flush if w.n_unknowns < 30_000_000 else None)
+    info = res["info"]
+    prm_chk = whv.make_params(w.omega, method=method, tol=w.tol, maxit=20000, true_residual=True,
+                              refine_fp64=refine)
+    _, ichk = g.whv_solve(prm_chk, f, u)
+    lups = info["wave_solves"] * info["nt"] * w.n_unknowns
+    line.update({"workload": name, "value": ms, "ms_per_step": ms,
+                 "dtype": "f64" if prec == whv.WHV_FP64 else "f32", "krylov_dtype": "f64",
+                 "config": dict({"workload": name, "grid": list(w.npts), "order": w.order, "omega": w.omega,
+                                 "nd": w.nd, "tol": w.tol, "method": method.upper(),
+                                 "variable_speed": bool(w.speed), "nt": info["nt"]}, **setup),
+                 "iterations": info["iterations"], "outer_iterations": info["outer_iterations"],
+                 "wave_solves": info["wave_solves"], "glups_solve": lups / (ms * 1e-3) / 1e9,
+                 "accuracy": {"true_rel_residual": ichk["true_rel_residual"]}})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "c2":
+        return run_workload(args)
     import torch
     import torch.distributed as dist
     rank = int(os.environ.get("RANK", "0"))

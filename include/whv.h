@@ -208,11 +208,28 @@ whv_status whv_autotune(whv_grid grid, const whv_params* p, int* best);
  *    grad_f_dev (out, nullable): dL/df = lambda^T dPi_h/df.  Both by one reverse sweep of the
  *    wave solve from u (leapfrog transposed step by step, filter weights as source, FP64
  *    accumulation), with the forward states checkpointed every `checkpoint_every` steps (<= 0: 16)
- *    and recomputed per segment; temporary device memory (2 ceil(Nt/K) + K + 5) N elements.
+ *    and recomputed per segment; temporary device memory (2 ceil(Nt/K) + K + 5) N elements.  The
+ *    sweep steps in the grid's precision, or in FP64 when p->flags has WHV_REFINE_FP64.
  * The time grid (dt, Nt) is held fixed.  All device buffers N doubles, caller-owned. */
 whv_status whv_solve_adjoint(whv_grid grid, const whv_params* p, const double* f_dev, const double* u_dev,
                              const double* dLdu_dev, double* z_dev, double* grad_c2_dev,
                              double* grad_f_dev, int checkpoint_every, whv_info* info);
+
+/* Batched solve of nprob independent problems (right-hand sides, frequencies, grids of uneven
+ * size): problem p is grids[p] with params[p] and forcing f_dev[p] (N_p doubles, device), its
+ * solution goes to u_dev[p].  Every problem needs its own grid object; all grids share one
+ * stream, precision, dimension (2 or 3), order and speed kind (all c = 1 or all variable).
+ * Method WHV_CG only; a grid's basis, if set, must be exact eigenvectors for params[p] (DEVD,
+ * Algorithm 2).  All problems iterate together: every CG iteration's wave solves of all active
+ * problems run in ONE persistent cooperative kernel launch (step s sweeps the tiles of every
+ * problem with Nt > s, then a grid barrier); b of all problems likewise.  The whole CG loop is one
+ * CUDA graph with a conditional WHILE node that runs until every problem has converged or hit its
+ * maxit.  The grid barrier waits a bounded time: if it gives up the call returns WHV_ERR_TIMEOUT.
+ * infos (host, nprob entries, may be NULL) receive per-problem counts and recursive residuals
+ * (no FP64 residual correction in this entry point).  Returns WHV_ERR_NOT_CONVERGED if any
+ * problem missed its tolerance (all solutions still written). */
+whv_status whv_solve_batched(int nprob, const whv_grid* grids, const whv_params* params,
+                             const double* const* f_dev, double* const* u_dev, whv_info* infos);
 
 /* Deflation contractions and reductions on the grid's basis / weights (building blocks of the
  * solve, exposed for testing and for callers composing their own iterations):

@@ -227,11 +227,11 @@ __global__ void k_scale_by(const double* __restrict__ x, const double* __restric
 }
 
 whv_status adjoint_gradients(whv_grid g, const TimeGridH& tg, const double* u, const double* f,
-                             const double* lam, double* gc2, double* gf, int K) {
+                             const double* lam, double* gc2, double* gf, int K, int prec) {
   if (gc2) WHV_CUDA(g, cudaMemsetAsync(gc2, 0, g->N * sizeof(double), g->stream));
   if (gf) WHV_CUDA(g, cudaMemsetAsync(gf, 0, g->N * sizeof(double), g->stream));
-  return g->precision == WHV_FP64 ? reverse_dispatch<double>(g, tg, u, f, lam, gc2, gf, K)
-                                  : reverse_dispatch<float>(g, tg, u, f, lam, gc2, gf, K);
+  return prec == WHV_FP64 ? reverse_dispatch<double>(g, tg, u, f, lam, gc2, gf, K)
+                          : reverse_dispatch<float>(g, tg, u, f, lam, gc2, gf, K);
 }
 
 whv_status scale_by(whv_grid g, const double* x, const double* y, double a, double* out) {

@@ -212,9 +212,20 @@ whv_status whv_create_grid(int dim, const int64_t npts[3], const double lo[3], c
       {(void**)&g->x, nb * 8}, {(void**)&g->r, nb * 8}, {(void**)&g->p, nb * 8},
       {(void**)&g->q, nb * 8}, {(void**)&g->t, nb * 8}, {(void**)&g->fd, nb * 8},
       {(void**)&g->small, (size_t)kMaxND * 8}, {(void**)&g->small2, (size_t)kMaxND * 8},
-      {(void**)&g->partials, (size_t)CH_NCH * kMaxStepBlocks * 8},
+      {(void**)&g->partials, 0},   // sized below
       {(void**)&g->counters, (size_t)CH_NCH * sizeof(unsigned)},
       {(void**)&g->scal, (size_t)S_NSLOTS * 8}};
+  // reduction channels: step kernels (<= N/256 blocks + slack), grid-stride reductions
+  // (2 x kRedBlocks: the speed set-up keeps block maxima after the sums), projections
+  // (ceil(N/2048) blocks x up to kMaxND columns)
+  g->chan_cap[CH_STEP] = N / 32 + 4096;
+  g->chan_cap[CH_UPDATE] = 2 * kRedBlocks;
+  g->chan_cap[CH_DOT] = 2 * kRedBlocks;
+  g->chan_cap[CH_PROJ] = ((N + 2047) / 2048) * kMaxND;
+  int64_t off = 0;
+  for (int ch = 0; ch < CH_NCH; ++ch) { g->chan_off[ch] = off; off += g->chan_cap[ch]; }
+  for (auto& a : allocs)
+    if (a.p == (void**)&g->partials) a.bytes = (size_t)off * sizeof(double);
   for (auto& a : allocs) {
     e = cudaMalloc(a.p, a.bytes);
     if (e != cudaSuccess) {
@@ -263,7 +274,7 @@ whv_status whv_set_speed(whv_grid g, const double* c2_dev) {
   if (!g->c2f) WHV_CUDA(g, cudaMalloc(&g->c2f, g->N * 4));
   if (!g->mw) WHV_CUDA(g, cudaMalloc(&g->mw, g->N * 8));
   k_speed_setup<<<kRedBlocks, 256, 0, g->stream>>>(c2_dev, g->c2, g->c2f, g->mw, g->N,
-                                                   g->partials + CH_DOT * kMaxStepBlocks,
+                                                   chan(g, CH_DOT),
                                                    g->counters + CH_DOT, g->scal);
   count_launches(1);
   WHV_CUDA(g, cudaGetLastError());

@@ -67,9 +67,9 @@ __global__ void __launch_bounds__(256) k_expand(const double* __restrict__ W, in
 whv_status project(whv_grid g, const double* W, int nd, const double* r, double* coef) {
   if (nd < 1 || nd > kMaxND) return fail(g, WHV_ERR_INVALID, "project: bad nd");
   const int64_t nb64 = (g->N + kProjRows - 1) / kProjRows;
-  if (nb64 * nd > kMaxStepBlocks) return fail(g, WHV_ERR_INVALID, "project: N * nd too large");
+  if (nb64 * nd > chan_cap(g, CH_PROJ)) return fail(g, WHV_ERR_INVALID, "project: N * nd too large");
   const int nb = (int)nb64;
-  double* part = g->partials + CH_PROJ * kMaxStepBlocks;
+  double* part = chan(g, CH_PROJ);
   k_project<<<nb, kProjThreads, 0, g->stream>>>(W, g->N, nd, r, g->mw, part);
   count_launches(1);
   WHV_CUDA(g, cudaGetLastError());

@@ -25,17 +25,20 @@ __global__ void __launch_bounds__(256) k_dot(const double* __restrict__ x, const
 }
 
 // alpha = rr / pq; x += alpha p; r -= alpha q; rr' = r^T M r; beta = rr'/rr; rr <- rr'.
-// Breakdown (pq <= 0 or non-finite scalars) raises scal[S_FLAG].
+// Breakdown (pq = 0 or non-finite scalars) raises scal[S_FLAG].  A negative pq is allowed: the
+// discrete filter transfer beta_h can exceed 1 by a few 1e-7 right at resonance, so A = I - S_h
+// may have tiny negative eigenvalues, and CG remains the Galerkin (Lanczos) iteration there.
 __global__ void __launch_bounds__(256) k_cg_update(double* __restrict__ x, double* __restrict__ r,
                                                    const double* __restrict__ p,
                                                    const double* __restrict__ q,
                                                    const double* __restrict__ mw, int64_t n,
                                                    double* scal, double* partials,
                                                    unsigned* counter) {
+  if (scal[S_HALT] != 0.0) return;   // a stopped problem of a batched solve
   const double rr = scal[S_RR];
   const double pq = scal[S_PQ];
   const double alpha = rr / pq;
-  const bool ok = (pq > 0.0) && isfinite(alpha);
+  const bool ok = (pq != 0.0) && isfinite(alpha);
   const double a = ok ? alpha : 0.0;
   double s = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -57,6 +60,7 @@ __global__ void __launch_bounds__(256) k_cg_update(double* __restrict__ x, doubl
 
 __global__ void __launch_bounds__(256) k_cg_direction(double* __restrict__ p, const double* __restrict__ r,
                                                       const double* __restrict__ scal, int64_t n) {
+  if (scal[S_HALT] != 0.0) return;
   const double beta = scal[S_BETA];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
@@ -81,7 +85,7 @@ static int grid_for(int64_t n) {
 }
 
 whv_status dot_async(whv_grid g, const double* x, const double* y, int slot) {
-  k_dot<<<grid_for(g->N), 256, 0, g->stream>>>(x, y, g->mw, g->N, g->partials + CH_DOT * kMaxStepBlocks,
+  k_dot<<<grid_for(g->N), 256, 0, g->stream>>>(x, y, g->mw, g->N, chan(g, CH_DOT),
                                                g->counters + CH_DOT, g->scal + slot);
   count_launches(1);
   WHV_CUDA(g, cudaGetLastError());
@@ -90,7 +94,7 @@ whv_status dot_async(whv_grid g, const double* x, const double* y, int slot) {
 
 whv_status cg_update(whv_grid g) {
   k_cg_update<<<grid_for(g->N), 256, 0, g->stream>>>(g->x, g->r, g->p, g->q, g->mw, g->N, g->scal,
-                                                     g->partials + CH_UPDATE * kMaxStepBlocks,
+                                                     chan(g, CH_UPDATE),
                                                      g->counters + CH_UPDATE);
   count_launches(1);
   WHV_CUDA(g, cudaGetLastError());

@@ -672,7 +672,7 @@ extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f
 // ------------------------------------------------------------------ adjoint
 namespace whv {
 whv_status adjoint_gradients(whv_grid g, const TimeGridH& tg, const double* u, const double* f,
-                             const double* lam, double* gc2, double* gf, int K);
+                             const double* lam, double* gc2, double* gf, int K, int prec);
 whv_status scale_by(whv_grid g, const double* x, const double* y, double a, double* out);
 }  // namespace whv
 
@@ -708,8 +708,11 @@ extern "C" whv_status whv_solve_adjoint(whv_grid g, const whv_params* p, const d
   int outer = 0;
   TRY(outer_solve(c, method, p, g->t, bb, refine, false, &R, &outer));
   TRY(scale_by(g, g->xo, g->mw, 1.0, z));
-  // lambda^T dPi_h(u; f, c^2) / d(c^2, f): checkpointed reverse sweep
-  if (grad_c2 || grad_f) TRY(adjoint_gradients(g, tg, u, f, z, grad_c2, grad_f, K));
+  // lambda^T dPi_h(u; f, c^2) / d(c^2, f): checkpointed reverse sweep -- like a residual it is a
+  // single pass whose rounding is not corrected afterwards, so with the FP64 residual correction
+  // it runs in FP64 (an FP32 sweep over a few hundred steps carries ~1e-3 relative errors)
+  if (grad_c2 || grad_f)
+    TRY(adjoint_gradients(g, tg, u, f, z, grad_c2, grad_f, K, refine ? WHV_FP64 : g->precision));
   WHV_CUDA(g, cudaStreamSynchronize(g->stream));
   if (info) {
     info->iterations = R.iters;

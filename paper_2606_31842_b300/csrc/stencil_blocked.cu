@@ -215,7 +215,7 @@ whv_status blocked_steps_2d(whv_grid g, const TimeGridH& tg, const double* v, do
   cf.ax = (T)ax;
   cf.ay = (T)ay;
   cf.b = (T)(2.0 - 2.0 * (ax + ay));
-  double* part = g->partials + CH_STEP * kMaxStepBlocks;
+  double* part = chan(g, CH_STEP);
   unsigned* cnt = g->counters + CH_STEP;
   int pair = 0;   // input pair: (buf[2 pair], buf[2 pair + 1]) = (W^{n-1}, W^n)
   int n = 1;      // next step computes W^{n+1}

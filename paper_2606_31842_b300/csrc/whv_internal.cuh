@@ -25,6 +25,7 @@ enum Slot {
   S_ITER = 8,   // iteration counter of the device-resident CG loop
   S_STOP = 9,   // tol^2 rr0: the loop runs while r^T M r > S_STOP
   S_MAXIT = 10, // iteration limit of the device-resident CG loop
+  S_HALT = 11,  // batched solves: nonzero once this problem has stopped (its kernels return)
   S_NSLOTS = 16
 };
 
@@ -95,7 +96,8 @@ struct whv_grid_s {
   double* small2 = nullptr;    // second small-vector scratch (kMaxND)
 
   // reductions
-  double* partials = nullptr;  // CH_NCH * kMaxStepBlocks
+  double* partials = nullptr;  // reduction scratch, one region per channel
+  int64_t chan_off[4] = {0, 0, 0, 0}, chan_cap[4] = {0, 0, 0, 0};
   unsigned* counters = nullptr;// CH_NCH
   double* scal = nullptr;      // S_NSLOTS device scalars
   double* scal_host = nullptr; // pinned mirror
@@ -107,6 +109,10 @@ struct whv_grid_s {
 };
 
 namespace whv {
+
+// per-block partial sums of reduction channel ch, and how many blocks it can hold
+inline double* chan(whv_grid g, int ch) { return g->partials + g->chan_off[ch]; }
+inline int64_t chan_cap(whv_grid g, int ch) { return g->chan_cap[ch]; }
 
 // ------------------------------------------------------------------ host helpers (core.cu)
 whv_status fail(whv_grid g, whv_status s, const std::string& msg);

@@ -71,6 +71,8 @@ def _load():
         "whv_project_noalloc": [L, I, P, P, P, P, P],
         "whv_lanczos": [P, ctypes.POINTER(whv_params), I, I, P, I, I, ctypes.POINTER(D), ctypes.POINTER(D)],
         "whv_solve_adjoint": [P, ctypes.POINTER(whv_params), P, P, P, P, P, P, I, ctypes.POINTER(whv_info)],
+        "whv_solve_batched": [I, ctypes.POINTER(P), ctypes.POINTER(whv_params), ctypes.POINTER(P),
+                              ctypes.POINTER(P), ctypes.POINTER(whv_info)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -94,7 +96,7 @@ EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_gr
             "whv_set_deflation_basis", "whv_get_basis", "whv_apply_pi", "whv_solve", "whv_project",
             "whv_expand", "whv_dot", "whv_num_unknowns", "whv_last_error", "whv_version",
             "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune",
-            "whv_project_noalloc", "whv_lanczos", "whv_solve_adjoint"]
+            "whv_project_noalloc", "whv_lanczos", "whv_solve_adjoint", "whv_solve_batched"]
 
 
 def _check(status, handle=None, allow=()):
@@ -133,6 +135,21 @@ def whv_project_noalloc(W, r, coef, w=None, stream=None):
     _check(lib.whv_project_noalloc(n, nd, _ptr(W), _ptr(r, n), _ptr(w, n) if w is not None else None,
                                    _ptr(coef, nd), ctypes.c_void_p(s)))
     return coef
+
+
+def whv_solve_batched(grids, params, fs, us=None, raise_not_converged=False):
+    """Batched solve (see include/whv.h): lists of Grid objects, whv_params and forcing tensors."""
+    n = len(grids)
+    if us is None:
+        us = [torch.zeros(g.N, dtype=torch.float64, device="cuda") for g in grids]
+    G = (ctypes.c_void_p * n)(*[g.handle for g in grids])
+    Pm = (whv_params * n)(*params)
+    F = (ctypes.c_void_p * n)(*[_ptr(f, g.N) for f, g in zip(fs, grids)])
+    U = (ctypes.c_void_p * n)(*[_ptr(u, g.N) for u, g in zip(us, grids)])
+    infos = (whv_info * n)()
+    allow = () if raise_not_converged else (WHV_ERR_NOT_CONVERGED,)
+    st = _check(lib.whv_solve_batched(n, G, Pm, F, U, infos), grids[0].handle, allow)
+    return us, [dict(i.as_dict(), status=STATUS_NAMES[st]) for i in infos]
 
 
 def whv_kernel_launches() -> int:

@@ -186,14 +186,16 @@ whv_status whv_solve(whv_grid grid, const whv_params* p, const double* f_dev, in
 /* Steps per sweep k of the temporally blocked 2-D stencil kernel: each launch advances k leapfrog
  * steps of the f = 0 wave solves in shared memory (halo of width k r).  k = 1 launches one kernel
  * per time step, k = 0 restores the default (8 for FP32 stepping, 1 for FP64), k <= 16.  Only
- * 2-D grids block; other grids always step once per launch.  whv_get_steps_per_sweep returns the
- * value in effect. */
+ * 2-D grids block; other grids always step once per launch.  With the default (k = 0) grids of at
+ * most 4096 unknowns run each whole wave solve in a single CTA (state in shared memory, one
+ * barrier per step); an explicit k turns that off.  whv_get_steps_per_sweep returns the value in
+ * effect (0 on such small grids). */
 whv_status whv_set_steps_per_sweep(whv_grid grid, int k);
 whv_status whv_get_steps_per_sweep(whv_grid grid, int* k);
 
 /* Autotuner: times f = 0 wave solves of p's time grid for each candidate steps-per-sweep value
- * (1, 2, 4, 6, 8, 10, 12, 16 on 2-D grids) with CUDA events on the grid's stream and keeps the
- * fastest; *best (host, may be NULL) receives it.  Overwrites the grid's internal work vectors,
+ * (1, 2, 4, 6, 8, 10, 12, 16 on 2-D grids; small grids keep the single-CTA solve, *best = 0) with
+ * CUDA events on the grid's stream and keeps the fastest; *best (host, may be NULL) receives it.  Overwrites the grid's internal work vectors,
  * synchronises the stream.  Must not be called while the grid's stream is being captured. */
 whv_status whv_autotune(whv_grid grid, const whv_params* p, int* best);
 
@@ -215,7 +217,7 @@ whv_status whv_solve_adjoint(whv_grid grid, const whv_params* p, const double* f
                              const double* dLdu_dev, double* z_dev, double* grad_c2_dev,
                              double* grad_f_dev, int checkpoint_every, whv_info* info);
 
-/* Batched solve of nprob independent problems (right-hand sides, frequencies, grids of uneven
+/* Batched solve of nprob (<= 1024) independent problems (right-hand sides, frequencies, grids of uneven
  * size): problem p is grids[p] with params[p] and forcing f_dev[p] (N_p doubles, device), its
  * solution goes to u_dev[p].  Every problem needs its own grid object; all grids share one
  * stream, precision, dimension (2 or 3), order and speed kind (all c = 1 or all variable).

@@ -74,22 +74,35 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, int* err, unsigned 
   return s_ok != 0;
 }
 
+constexpr int kBatchMaxProblems = 1024;
+
 template <typename T, int DIM, int ORDER, bool VARC>
 __global__ void __launch_bounds__(256) k_batch_wave(const BProb<T>* __restrict__ P, const int* __restrict__ nact,
                                                     int S, const T* __restrict__ wtab, const T* __restrict__ ptab,
                                                     unsigned* bar_count, unsigned* bar_gen, int* err) {
+  // tile offsets of all problems (and one past the last) in shared memory: each block walks its
+  // work items in increasing order, so the problem index only moves forward
+  __shared__ int64_t s_tile0[kBatchMaxProblems + 1];
+  __shared__ BProb<T> sB;
+  const int np = nact[0];
+  for (int p = threadIdx.x + blockDim.x * threadIdx.y; p <= np; p += blockDim.x * blockDim.y)
+    s_tile0[p] = p < np ? P[p].tile0 : P[np - 1].tile0 + P[np - 1].ntiles;
+  __syncthreads();
   const int lx = threadIdx.x, ly = threadIdx.y;
   for (int s = 0; s < S; ++s) {
     const int A = nact[s];
-    const int64_t total = P[A - 1].tile0 + P[A - 1].ntiles;
+    const int64_t total = s_tile0[A];
+    int cur = -1;
     for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
-      // problem of this work item: the last p < A with tile0 <= item
-      int lo = 0, hi = A - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (P[mid].tile0 <= item) lo = mid; else hi = mid - 1;
+      int p = cur < 0 ? 0 : cur;
+      while (s_tile0[p + 1] <= item) ++p;
+      if (p != cur) {   // stage the problem's descriptor in shared memory
+        __syncthreads();
+        if (lx == 0 && ly == 0) sB = P[p];
+        __syncthreads();
+        cur = p;
       }
-      const BProb<T>& B = P[lo];
+      const BProb<T>& B = sB;
       if (B.halt && *B.halt != 0.0) continue;   // uniform per block
       const int t = (int)(item - B.tile0);
       const int tx = t % B.tx, ty = (t / B.tx) % B.ty, tz = t / (B.tx * B.ty);
@@ -418,8 +431,8 @@ using namespace whv;
 
 extern "C" whv_status whv_solve_batched(int nprob, const whv_grid* grids, const whv_params* params,
                                         const double* const* f_dev, double* const* u_dev, whv_info* infos) {
-  if (nprob < 1 || !grids || !params || !f_dev || !u_dev)
-    return fail(nullptr, WHV_ERR_INVALID, "whv_solve_batched: bad arguments");
+  if (nprob < 1 || nprob > kBatchMaxProblems || !grids || !params || !f_dev || !u_dev)
+    return fail(nullptr, WHV_ERR_INVALID, "whv_solve_batched: bad arguments (1 <= nprob <= 1024)");
   whv_grid g0 = grids[0];
   if (!g0) return fail(nullptr, WHV_ERR_INVALID, "whv_solve_batched: NULL grid");
   const bool varc = g0->c2 != nullptr;

@@ -148,7 +148,7 @@ static void free_all(whv_grid g) {
   void* ptrs[] = {g->c2, g->c2f, g->mw, g->wbuf[0], g->wbuf[1], g->wbuf[2], g->wbuf[3], g->acc, g->x, g->r, g->p, g->q,
                   g->t, g->fd, g->krylov, g->small, g->small2, g->partials, g->counters, g->scal,
                   g->basis.V, g->basis.d_coef, g->basis.AW, g->basis.Einv, g->wbuf64[0], g->wbuf64[1], g->wbuf64[2],
-                  g->wbuf64[3], g->acc64, g->xo, g->ro, g->bo};
+                  g->wbuf64[3], g->acc64, g->xo, g->ro, g->bo, g->wtab_small};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->scal_host) cudaFreeHost(g->scal_host);

@@ -174,6 +174,7 @@ struct CgLoop {
 
 void free_cgloop(whv_grid g) {
   if (!g->cgloop) return;
+  cudaStreamSynchronize(g->stream);
   if (g->cgloop->exec) cudaGraphExecDestroy(g->cgloop->exec);
   if (g->cgloop->graph) cudaGraphDestroy(g->cgloop->graph);
   delete g->cgloop;

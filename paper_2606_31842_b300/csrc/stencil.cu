@@ -437,6 +437,10 @@ static whv_status launch_wave_solve(whv_grid g, const TimeGridH& tg, const doubl
   if ((int64_t)ls.grid.x * ls.grid.y * ls.grid.z > chan_cap(g, CH_STEP))
     return fail(g, WHV_ERR_INVALID, "grid too large for the fused reduction");
   if (prec < 0) prec = g->precision;
+  if (small_grid(g) && g->kblock == 0 && small_tables(g, tg) >= 0) {
+    *nl = 1;
+    return small_wave_solve(g, tg, v, f, out, epi, prec);
+  }
   if (prec == g->precision) {
     const BufSet B{g->wbuf, g->acc, g->kblock > 0 ? g->kblock : default_kblock(g)};
     return prec == WHV_FP64 ? dispatch<double>(g, tg, v, f, out, epi, nl, B)
@@ -468,6 +472,8 @@ struct StepPlan {
 };
 
 void free_plan(whv_grid g) {
+  // executable graphs must not be destroyed while a launch of them may still be running
+  if (g->plan || g->cgloop) cudaStreamSynchronize(g->stream);
   free_cgloop(g);
   if (!g->plan) return;
   for (auto& e : g->plan->entries) cudaGraphExecDestroy(e.exec);
@@ -480,6 +486,10 @@ whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const do
   if (prec < 0) prec = g->precision;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   WHV_CUDA(g, cudaStreamIsCapturing(g->stream, &cs));
+  // small grids: a new time grid replaces the device weight table, so graphs captured with the
+  // old one are dropped before anything is replayed
+  if (cs == cudaStreamCaptureStatusNone && small_grid(g) && g->kblock == 0 && small_tables(g, tg) == 1)
+    free_plan(g);
   if (cs != cudaStreamCaptureStatusNone) {  // caller is capturing: record the launches into its graph
     int nl = 0;
     whv_status s = launch_wave_solve(g, tg, v, f, out, epi, &nl, prec);
@@ -552,7 +562,7 @@ extern "C" whv_status whv_set_steps_per_sweep(whv_grid g, int k) {
 
 extern "C" whv_status whv_get_steps_per_sweep(whv_grid g, int* k) {
   if (!g || !k) return fail(g, WHV_ERR_INVALID, "NULL argument");
-  *k = g->kblock > 0 ? g->kblock : default_kblock(g);
+  *k = g->kblock > 0 ? g->kblock : (small_grid(g) ? 0 : default_kblock(g));
   return WHV_OK;
 }
 
@@ -563,6 +573,11 @@ extern "C" whv_status whv_autotune(whv_grid g, const whv_params* p, int* best) {
   TimeGridH tg;
   whv_status s = make_time_grid(g, p, &tg);
   if (s != WHV_OK) return s;
+  if (small_grid(g)) {   // the whole wave solve runs in one CTA: nothing to tune
+    g->kblock = 0;
+    if (best) *best = 0;
+    return WHV_OK;
+  }
   const int cands2d[] = {1, 2, 4, 6, 8, 10, 12, 16};
   const int cands_other[] = {1};
   const int* cands = g->dim == 2 ? cands2d : cands_other;

@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "whv_device.cuh"
 #include "whv_internal.cuh"
@@ -176,10 +177,13 @@ static void set_attrs() {
 
 // opt the blocked kernels into large dynamic shared memory once per process (outside any
 // stream capture)
+void small_init();
+
 void blocked_init() {
   static bool done = false;
   if (done) return;
   done = true;
+  small_init();
   set_attrs<float, 2, false>(); set_attrs<float, 2, true>(); set_attrs<float, 4, false>(); set_attrs<float, 4, true>();
   set_attrs<double, 2, false>(); set_attrs<double, 2, true>(); set_attrs<double, 4, false>(); set_attrs<double, 4, true>();
 }
@@ -250,5 +254,207 @@ template whv_status blocked_steps_2d<double, 2, false>(whv_grid, const TimeGridH
 template whv_status blocked_steps_2d<double, 2, true>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
 template whv_status blocked_steps_2d<double, 4, false>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
 template whv_status blocked_steps_2d<double, 4, true>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
+
+}  // namespace whv
+
+// ------------------------------------------------------------------ whole wave solve in one CTA
+// Small grids (N <= kSmallMaxN unknowns, e.g. the 1-D workload's 199) are bound by launch
+// latency when every time step is a kernel.  One CTA runs the whole wave solve instead: thread
+// t owns cells t + kBlkThreads c (c < kSmallCells) with their W^n, W^{n-1} and filter sum in
+// registers; W^n is double-buffered in shared memory for the neighbours; one barrier per step.
+// The FP64 epilogue (out = acc, or out = v - acc with p^T M out) is reduced inside the block.
+namespace whv {
+
+constexpr int kSmallCells = 4;
+constexpr int kSmallMaxN = kBlkThreads * kSmallCells;   // 4096
+
+template <typename T>
+struct SmallArgs {
+  const double* v;        // initial state (nullptr: 0)
+  const double* f;        // forcing (nullptr: 0)
+  double* out;
+  const T* c2;            // nullptr: c = 1
+  const double* mw;
+  double* scal_pq;        // epi 1: <v, out>_M
+  const double* wtab;     // w_n, n = 0..nt
+  const double* ptab;     // cos(omega_hat t^n), n = 0..nt
+  int nx, ny, nz, nt, epi;
+  T ih2x, ih2y, ih2z, dt2;
+};
+
+template <typename T, int DIM, int ORDER>
+__device__ __forceinline__ T lap_small(const T* __restrict__ A, int i, int nx, int ny, int nz,
+                                       const SmallArgs<T>& a, T c) {
+  const int x = i % nx;
+  T L = d2s<ORDER>(A, i, x, nx, 1, c) * a.ih2x;
+  if (DIM > 1) {
+    const int y = (i / nx) % ny;
+    L = fma(d2s<ORDER>(A, i, y, ny, nx, c), a.ih2y, L);
+  }
+  if (DIM > 2) {
+    const int z = i / (nx * ny);
+    L = fma(d2s<ORDER>(A, i, z, nz, nx * ny, c), a.ih2z, L);
+  }
+  return L;
+}
+
+template <typename T, int DIM, int ORDER, bool VARC>
+__global__ void __launch_bounds__(kBlkThreads) k_wave_small(SmallArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = a.nx * a.ny * a.nz;
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* B = A + N;
+  const int tid = threadIdx.x;
+  T cur[kSmallCells], prv[kSmallCells], acc[kSmallCells], cc[kSmallCells], ff[kSmallCells];
+#pragma unroll
+  for (int c = 0; c < kSmallCells; ++c) {
+    const int i = tid + kBlkThreads * c;
+    cur[c] = (i < N && a.v) ? (T)a.v[i] : T(0);
+    cc[c] = (VARC && i < N) ? a.c2[i] : T(1);
+    ff[c] = (i < N && a.f) ? (T)a.f[i] : T(0);
+    if (i < N) A[i] = cur[c];
+  }
+  __syncthreads();
+  // first step from D0t W^0 = 0
+  {
+    const T w0 = (T)a.wtab[0], w1 = (T)a.wtab[1];
+#pragma unroll
+    for (int c = 0; c < kSmallCells; ++c) {
+      const int i = tid + kBlkThreads * c;
+      if (i >= N) continue;
+      T L = lap_small<T, DIM, ORDER>(A, i, a.nx, a.ny, a.nz, a, cur[c]);
+      if (VARC) L *= cc[c];
+      L -= ff[c];   // cos(0) = 1
+      const T W1 = fma(T(0.5) * a.dt2, L, cur[c]);
+      acc[c] = fma(w1, W1, w0 * cur[c]);
+      prv[c] = cur[c];
+      cur[c] = W1;
+      B[i] = W1;
+    }
+  }
+  __syncthreads();
+  T* X = B;
+  T* Y = A;
+  for (int n = 1; n < a.nt; ++n) {
+    const T wn1 = (T)a.wtab[n + 1];
+    const T ph = (T)a.ptab[n];
+#pragma unroll
+    for (int c = 0; c < kSmallCells; ++c) {
+      const int i = tid + kBlkThreads * c;
+      if (i >= N) continue;
+      T L = lap_small<T, DIM, ORDER>(X, i, a.nx, a.ny, a.nz, a, cur[c]);
+      if (VARC) L *= cc[c];
+      L = fma(-ff[c], ph, L);
+      const T wn = fma(a.dt2, L, fma(T(2), cur[c], -prv[c]));
+      acc[c] = fma(wn1, wn, acc[c]);
+      prv[c] = cur[c];
+      cur[c] = wn;
+      Y[i] = wn;
+    }
+    __syncthreads();
+    T* t = X; X = Y; Y = t;
+  }
+  double part = 0.0;
+#pragma unroll
+  for (int c = 0; c < kSmallCells; ++c) {
+    const int i = tid + kBlkThreads * c;
+    if (i >= N) continue;
+    if (a.epi == 0) {
+      a.out[i] = (double)acc[c];
+    } else {
+      const double vi = a.v[i];
+      const double o = vi - (double)acc[c];
+      a.out[i] = o;
+      part = fma(a.mw ? vi * a.mw[i] : vi, o, part);
+    }
+  }
+  if (a.epi == 1) {
+    part = block_sum(part);
+    if (tid == 0) *a.scal_pq = part;
+  }
+}
+
+template <typename T, int DIM, int ORDER, bool VARC>
+static cudaError_t launch_small_t(whv_grid g, const SmallArgs<T>& a) {
+  const size_t smem = 2 * (size_t)g->N * sizeof(T);
+  k_wave_small<T, DIM, ORDER, VARC><<<1, kBlkThreads, smem, g->stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static whv_status launch_small(whv_grid g, const TimeGridH& tg, const double* v, const double* f, double* out,
+                               int epi) {
+  SmallArgs<T> a{};
+  a.v = v; a.f = f; a.out = out;
+  a.c2 = g->c2 ? (const T*)(sizeof(T) == 8 ? (const void*)g->c2 : (const void*)g->c2f) : nullptr;
+  a.mw = g->mw;
+  a.scal_pq = g->scal + S_PQ;
+  a.wtab = g->wtab_small;
+  a.ptab = g->wtab_small + (tg.nt + 1);
+  a.nx = g->n[0]; a.ny = g->n[1]; a.nz = g->n[2]; a.nt = tg.nt; a.epi = epi;
+  auto ih = [&](int m) { const double h2 = g->h[m] * g->h[m]; return (T)(g->order == 2 ? 1.0 / h2 : 1.0 / (12.0 * h2)); };
+  a.ih2x = ih(0); a.ih2y = ih(1); a.ih2z = ih(2);
+  a.dt2 = (T)(tg.dt * tg.dt);
+  const bool varc = g->c2 != nullptr;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (g->dim * 10 + g->order) {
+    case 12: e = varc ? launch_small_t<T, 1, 2, true>(g, a) : launch_small_t<T, 1, 2, false>(g, a); break;
+    case 14: e = varc ? launch_small_t<T, 1, 4, true>(g, a) : launch_small_t<T, 1, 4, false>(g, a); break;
+    case 22: e = varc ? launch_small_t<T, 2, 2, true>(g, a) : launch_small_t<T, 2, 2, false>(g, a); break;
+    case 24: e = varc ? launch_small_t<T, 2, 4, true>(g, a) : launch_small_t<T, 2, 4, false>(g, a); break;
+    case 32: e = varc ? launch_small_t<T, 3, 2, true>(g, a) : launch_small_t<T, 3, 2, false>(g, a); break;
+    case 34: e = varc ? launch_small_t<T, 3, 4, true>(g, a) : launch_small_t<T, 3, 4, false>(g, a); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(g, e, "k_wave_small launch");
+  return WHV_OK;
+}
+
+bool small_grid(whv_grid g) { return g->N <= kSmallMaxN; }
+
+// weight / phase table of tg in device memory, uploaded when the time grid changes (outside
+// stream captures).  Returns 0 if the table was current, 1 if it was (re)uploaded -- graphs
+// captured against the old table must then be dropped -- and -1 if it is stale and cannot be
+// uploaded now (the grid's stream is being captured).
+int small_tables(whv_grid g, const TimeGridH& tg) {
+  if (g->wtab_small && g->tab_nt == tg.nt && g->tab_key[0] == tg.omega && g->tab_key[1] == tg.cfl &&
+      g->tab_key[2] == tg.periods && g->tab_key[3] == tg.adjust)
+    return 0;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(g->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return -1;
+  if (g->wtab_small && g->tab_cap < tg.nt + 1) { cudaFree(g->wtab_small); g->wtab_small = nullptr; }
+  if (!g->wtab_small) {
+    if (cudaMalloc(&g->wtab_small, 2 * (size_t)(tg.nt + 1) * sizeof(double)) != cudaSuccess) return -1;
+    g->tab_cap = tg.nt + 1;
+  }
+  std::vector<double> tab(2 * (size_t)(tg.nt + 1));
+  std::copy(tg.weight.begin(), tg.weight.end(), tab.begin());
+  std::copy(tg.phase.begin(), tg.phase.end(), tab.begin() + (tg.nt + 1));
+  if (cudaStreamSynchronize(g->stream) != cudaSuccess) return -1;
+  if (cudaMemcpy(g->wtab_small, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return -1;
+  g->tab_nt = tg.nt;
+  g->tab_key[0] = tg.omega; g->tab_key[1] = tg.cfl; g->tab_key[2] = tg.periods; g->tab_key[3] = tg.adjust;
+  return 1;
+}
+
+whv_status small_wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f, double* out,
+                            int epi, int prec) {
+  return prec == WHV_FP64 ? launch_small<double>(g, tg, v, f, out, epi) : launch_small<float>(g, tg, v, f, out, epi);
+}
+
+template <typename T, int DIM, int ORDER, bool VARC>
+static void small_attr() {
+  cudaFuncSetAttribute(k_wave_small<T, DIM, ORDER, VARC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(2 * kSmallMaxN * sizeof(T)));
+}
+
+void small_init() {
+  small_attr<float, 1, 2, false>(); small_attr<float, 1, 2, true>(); small_attr<float, 1, 4, false>(); small_attr<float, 1, 4, true>();
+  small_attr<float, 2, 2, false>(); small_attr<float, 2, 2, true>(); small_attr<float, 2, 4, false>(); small_attr<float, 2, 4, true>();
+  small_attr<float, 3, 2, false>(); small_attr<float, 3, 2, true>(); small_attr<float, 3, 4, false>(); small_attr<float, 3, 4, true>();
+  small_attr<double, 1, 2, false>(); small_attr<double, 1, 2, true>(); small_attr<double, 1, 4, false>(); small_attr<double, 1, 4, true>();
+  small_attr<double, 2, 2, false>(); small_attr<double, 2, 2, true>(); small_attr<double, 2, 4, false>(); small_attr<double, 2, 4, true>();
+  small_attr<double, 3, 2, false>(); small_attr<double, 3, 2, true>(); small_attr<double, 3, 4, false>(); small_attr<double, 3, 4, true>();
+}
 
 }  // namespace whv

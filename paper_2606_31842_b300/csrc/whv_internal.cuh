@@ -94,6 +94,10 @@ struct whv_grid_s {
   int krylov_cols = 0;
   double* small = nullptr;     // device small-vector scratch (kMaxND)
   double* small2 = nullptr;    // second small-vector scratch (kMaxND)
+  // weight / phase table of the single-CTA wave solve (small grids)
+  double* wtab_small = nullptr;
+  int tab_nt = 0, tab_cap = 0;
+  double tab_key[4] = {0, 0, 0, 0};
 
   // reductions
   double* partials = nullptr;  // reduction scratch, one region per channel
@@ -148,6 +152,11 @@ template <typename T, int ORDER, bool VARC>
 whv_status blocked_steps_2d(whv_grid g, const TimeGridH& tg, const double* v, double* out, int epi,
                             int k_want, int* launches, void* const* bufs, void* acc);
 void blocked_init();
+// single-CTA wave solve for small grids (stencil_blocked.cu)
+bool small_grid(whv_grid g);
+int small_tables(whv_grid g, const TimeGridH& tg);   // 0 current, 1 uploaded, -1 stale
+whv_status small_wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f, double* out,
+                            int epi, int prec);
 
 // reduce.cu
 whv_status dot_async(whv_grid g, const double* x, const double* y, int slot);   // scal[slot] = <x,y>_M

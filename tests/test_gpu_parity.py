@@ -59,8 +59,13 @@ PI_CASES = [
 @pytest.mark.parametrize("npts,order,speed,omega", PI_CASES)
 @pytest.mark.parametrize("forcing", [False, True])
 @pytest.mark.parametrize("adjust", [False, True])
-def test_apply_pi_fp64(npts, order, speed, omega, forcing, adjust):
+@pytest.mark.parametrize("per_step", [False, True])
+def test_apply_pi_fp64(npts, order, speed, omega, forcing, adjust, per_step):
+    """per_step: one kernel per time step (otherwise grids of <= 4096 unknowns run the whole
+    wave solve in one CTA)."""
     g, og, _ = make(npts, order, speed)
+    if per_step:
+        g.whv_set_steps_per_sweep(1)
     prm = whv.make_params(omega, adjust_omega=adjust)
     tg = WH.time_grid_for(og, omega, adjust=adjust)
     assert g.whv_time_grid(prm)["nt"] == tg.nt
@@ -72,8 +77,11 @@ def test_apply_pi_fp64(npts, order, speed, omega, forcing, adjust):
 
 
 @pytest.mark.parametrize("npts,order,speed,omega", PI_CASES[:9])
-def test_apply_pi_fp32(npts, order, speed, omega):
+@pytest.mark.parametrize("per_step", [False, True])
+def test_apply_pi_fp32(npts, order, speed, omega, per_step):
     g, og, _ = make(npts, order, speed, precision=whv.WHV_FP32_STEP)
+    if per_step:
+        g.whv_set_steps_per_sweep(1)
     prm = whv.make_params(omega)
     tg = WH.time_grid_for(og, omega)
     v = I.random_field(og.shape, 3)

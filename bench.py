@@ -195,6 +195,18 @@ def traffic_for(kernel, precision):
     return rec.get("dram_bytes_per_launch")
 
 
+def aggregate_max(value, world, device=None):
+    """Max of a per-rank time over all ranks (replicas: the job takes as long as its slowest rank);
+    identity for a single process."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _timed(stream, fn, steps, warmup, flush):
     import torch
     for _ in range(max(1, warmup)):
@@ -392,11 +404,7 @@ def main():
         barrier()
     launches = whv.whv_kernel_launches() - launches0
     clocks = clk.summary()
-    ms = statistics.mean(times)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = aggregate_max(statistics.mean(times), world, device="cuda")
     info = infos[-1]
     lups = info["wave_solves"] * nt * w.n_unknowns
     # accuracy of the timed configuration (outside the timed region): FP64 true residual and

@@ -127,12 +127,13 @@ __global__ void __launch_bounds__(256) k_batch_wave(const BProb<T>* __restrict__
         T* wcur = (s & 1) ? B.w1 : B.w0;
         T* wprv = (s & 1) ? B.w0 : B.w1;
         if (in) {
-          const T c = wcur[idx];
-          T L = lap<DIM, ORDER, T>(wcur, idx, x, y, z, B.nx, B.ny, B.nz, B.cf, c);
+          // wcur was written by other CTAs at the previous step of this launch: coherent loads
+          const T c = __ldcg(wcur + idx);
+          T L = lap_cg<DIM, ORDER, T>(wcur, idx, x, y, z, B.nx, B.ny, B.nz, B.cf, c);
           if (VARC) L *= B.c2[idx];
           if (B.f) L = fma(-(T)B.f[idx], ptab[B.wofs + s], L);
-          const T wn = fma(B.cf.dt2, L, fma(T(2), c, -wprv[idx]));
-          const T a = fma(wtb[s + 1], wn, B.acc[idx]);
+          const T wn = fma(B.cf.dt2, L, fma(T(2), c, -__ldcg(wprv + idx)));
+          const T a = fma(wtb[s + 1], wn, __ldcg(B.acc + idx));
           if (!last) {
             wprv[idx] = wn;
             B.acc[idx] = a;

@@ -188,75 +188,6 @@ __global__ void __launch_bounds__(256) k_step3d(const T* __restrict__ wc, T* __r
   }
 }
 
-// 2-D 5-point variant with two rows per thread (y, y+1): the rows share their centre loads and
-// give each thread two independent FMA chains (the FP64 stepping is bound by the FP64 pipe).
-template <typename T, bool FORCE, int KIND>
-__global__ void __launch_bounds__(256) k_step2x(const T* __restrict__ wc, T* __restrict__ wp,
-                                                T* __restrict__ acc, const double* __restrict__ f,
-                                                const double* __restrict__ v,
-                                                const double* __restrict__ mw,
-                                                double* __restrict__ out, int nx, int ny,
-                                                StepCoef<T> cf, double* partials, unsigned* counter,
-                                                double* scal_out) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * 2;
-  double part = 0.0;
-  if (x < nx && y0 < ny) {
-    const bool two = y0 + 1 < ny;
-    const int64_t i0 = x + (int64_t)nx * y0;
-    const int64_t i1 = i0 + nx;
-    const T c0 = __ldg(wc + i0);
-    const T c1 = two ? __ldg(wc + i1) : T(0);
-    const T ym = y0 > 0 ? __ldg(wc + i0 - nx) : T(0);
-    const T yp = (y0 + 2 < ny) ? __ldg(wc + i1 + nx) : T(0);
-    const T x0m = x > 0 ? __ldg(wc + i0 - 1) : T(0);
-    const T x0p = x < nx - 1 ? __ldg(wc + i0 + 1) : T(0);
-    const T p0 = wp[i0];
-    const T a0 = acc[i0];
-    T u0 = fma(cf.b, c0, -p0);
-    u0 = fma(cf.a[0], x0m + x0p, u0);
-    u0 = fma(cf.a[1], ym + c1, u0);
-    if (FORCE) u0 = fma(-cf.dt2 * cf.fph, (T)f[i0], u0);
-    const T s0 = fma(cf.w1, u0, a0);
-    T u1 = T(0), s1 = T(0);
-    if (two) {
-      const T x1m = x > 0 ? __ldg(wc + i1 - 1) : T(0);
-      const T x1p = x < nx - 1 ? __ldg(wc + i1 + 1) : T(0);
-      const T p1 = wp[i1];
-      const T a1 = acc[i1];
-      u1 = fma(cf.b, c1, -p1);
-      u1 = fma(cf.a[0], x1m + x1p, u1);
-      u1 = fma(cf.a[1], c0 + yp, u1);
-      if (FORCE) u1 = fma(-cf.dt2 * cf.fph, (T)f[i1], u1);
-      s1 = fma(cf.w1, u1, a1);
-    }
-    if (KIND == K_STEP) {
-      wp[i0] = u0;
-      acc[i0] = s0;
-      if (two) { wp[i1] = u1; acc[i1] = s1; }
-    } else if (KIND == K_LAST_OUT) {
-      out[i0] = (double)s0;
-      if (two) out[i1] = (double)s1;
-    } else {
-      const double v0 = v[i0];
-      const double o0 = v0 - (double)s0;
-      out[i0] = o0;
-      part = (mw ? v0 * mw[i0] : v0) * o0;
-      if (two) {
-        const double v1 = v[i1];
-        const double o1 = v1 - (double)s1;
-        out[i1] = o1;
-        part = fma(mw ? v1 * mw[i1] : v1, o1, part);
-      }
-    }
-  }
-  if (KIND == K_LAST_AV) {
-    part = block_sum(part);
-    double total;
-    if (grid_reduce(part, partials, counter, &total) && flat_tid() == 0) *scal_out = total;
-  }
-}
-
 // --------------------------------------------------------------------------- host side
 struct LaunchShape {
   dim3 grid, block;
@@ -341,18 +272,7 @@ static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v,
     cf.fph = (T)tg.phase[n];
     cf.w1 = (T)tg.weight[n + 1];
     const bool last = (n == tg.nt - 1);
-    if constexpr (DIM == 2 && ORDER == 2 && !VARC) {
-      const dim3 g2(ls.grid.x, (ny + 15) / 16, 1);
-      if (!last)
-        k_step2x<T, FORCE, K_STEP><<<g2, ls.block, 0, g->stream>>>(
-            wcur, wprev, acc, f, nullptr, nullptr, nullptr, nx, ny, cf, nullptr, nullptr, nullptr);
-      else if (epi == 0)
-        k_step2x<T, FORCE, K_LAST_OUT><<<g2, ls.block, 0, g->stream>>>(
-            wcur, wprev, acc, f, nullptr, nullptr, out, nx, ny, cf, nullptr, nullptr, nullptr);
-      else
-        k_step2x<T, FORCE, K_LAST_AV><<<g2, ls.block, 0, g->stream>>>(
-            wcur, wprev, acc, f, v, g->mw, out, nx, ny, cf, part, cnt, g->scal + S_PQ);
-    } else if constexpr (DIM == 3 && ORDER == 2) {
+    if constexpr (DIM == 3 && ORDER == 2) {
       if (!last)
         k_step3d<T, VARC, FORCE, K_STEP><<<ls.grid, ls.block, 0, g->stream>>>(
             wcur, wprev, acc, c2, f, nullptr, nullptr, nullptr, nx, ny, nz, kZChunk, cf, nullptr, nullptr, nullptr);

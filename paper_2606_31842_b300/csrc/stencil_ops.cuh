@@ -33,6 +33,28 @@ __device__ __forceinline__ T d2(const S* __restrict__ w, int64_t idx, int i, int
   }
 }
 
+// The same second difference with L2-coherent loads (ld.global.cg): for kernels that read data
+// written earlier in the same launch (the persistent batched kernel), where the read-only path
+// could serve stale L1 lines.
+template <int ORDER, typename T>
+__device__ __forceinline__ T d2_cg(const T* w, int64_t idx, int i, int n, int64_t s, T c) {
+  const T m1 = (i > 0) ? __ldcg(w + idx - s) : T(0);
+  const T p1 = (i < n - 1) ? __ldcg(w + idx + s) : T(0);
+  if (ORDER == 2) return fma(T(-2), c, m1 + p1);
+  const T m2 = (i > 1) ? __ldcg(w + idx - 2 * s) : (i == 1 ? T(0) : -c);
+  const T p2 = (i < n - 2) ? __ldcg(w + idx + 2 * s) : (i == n - 2 ? T(0) : -c);
+  return fma(T(-30), c, fma(T(16), m1 + p1, -(m2 + p2)));
+}
+
+template <int DIM, int ORDER, typename T>
+__device__ __forceinline__ T lap_cg(const T* w, int64_t idx, int x, int y, int z, int nx, int ny, int nz,
+                                    const StepCoef<T>& cf, T c) {
+  T l = d2_cg<ORDER, T>(w, idx, x, nx, 1, c) * cf.ih2[0];
+  if (DIM > 1) l = fma(d2_cg<ORDER, T>(w, idx, y, ny, (int64_t)nx, c), cf.ih2[1], l);
+  if (DIM > 2) l = fma(d2_cg<ORDER, T>(w, idx, z, nz, (int64_t)nx * ny, c), cf.ih2[2], l);
+  return l;
+}
+
 template <int DIM, int ORDER, typename T, typename S>
 __device__ __forceinline__ T lap(const S* __restrict__ w, int64_t idx, int x, int y, int z, int nx,
                                  int ny, int nz, const StepCoef<T>& cf, T c) {

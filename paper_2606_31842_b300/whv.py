@@ -148,6 +148,7 @@ def whv_solve_batched(grids, params, fs, us=None, raise_not_converged=False):
     U = (ctypes.c_void_p * n)(*[_ptr(u, g.N) for u, g in zip(us, grids)])
     infos = (whv_info * n)()
     allow = () if raise_not_converged else (WHV_ERR_NOT_CONVERGED,)
+    grids[0]._pre()
     st = _check(lib.whv_solve_batched(n, G, Pm, F, U, infos), grids[0].handle, allow)
     return us, [dict(i.as_dict(), status=STATUS_NAMES[st]) for i in infos]
 
@@ -166,12 +167,26 @@ class Grid:
         hi3 = (ctypes.c_double * 3)(*((list(hi) if hi else [1.0] * dim) + [1.0] * (3 - dim)))
         if stream is None:
             stream = torch.cuda.current_stream()
+        self.stream = stream
         h = ctypes.c_void_p()
         _check(lib.whv_create_grid(dim, n3, lo3, hi3, order, precision, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)))
         self.handle = h
         self.dim, self.npts, self.order, self.precision = dim, tuple(npts), order, precision
         self.shape = tuple(int(n) - 2 for n in reversed(list(npts)))
         self.N = int(lib.whv_num_unknowns(h))
+
+    # Stream ordering: the library works on self.stream.  Before a call the grid's stream waits for
+    # the caller's current stream (inputs written there are complete); after an asynchronous call the
+    # caller's stream waits for the grid's (outputs are complete before torch reads them).
+    def _pre(self):
+        cur = torch.cuda.current_stream()
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
+    def _post(self):
+        cur = torch.cuda.current_stream()
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -181,6 +196,7 @@ class Grid:
     __del__ = close
 
     def whv_set_speed(self, c2):
+        self._pre()
         _check(lib.whv_set_speed(self.handle, _ptr(c2, self.N)), self.handle)
 
     def whv_time_grid(self, params):
@@ -190,6 +206,7 @@ class Grid:
         return {"nt": nt.value, "dt": dt.value, "omega_hat": oh.value, "omega_eff": oe.value}
 
     def whv_set_deflation_basis(self, params, nd, mode, V=None, lambda2=None, flags=0):
+        self._pre()
         lam = None
         if lambda2 is not None:
             lam = (ctypes.c_double * nd)(*[float(x) for x in lambda2])
@@ -213,8 +230,10 @@ class Grid:
     def whv_apply_pi(self, params, v, f=None, out=None):
         if out is None:
             out = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        self._pre()
         _check(lib.whv_apply_pi(self.handle, ctypes.byref(params), _ptr(v, self.N), _ptr(f, self.N), _ptr(out, self.N)),
                self.handle)
+        self._post()
         return out
 
     def whv_solve(self, params, f, u=None, use_guess=False, raise_not_converged=False):
@@ -222,6 +241,7 @@ class Grid:
             u = torch.zeros(self.N, dtype=torch.float64, device="cuda")
         info = whv_info()
         allow = () if raise_not_converged else (WHV_ERR_NOT_CONVERGED,)
+        self._pre()
         st = _check(lib.whv_solve(self.handle, ctypes.byref(params), _ptr(f, self.N), int(bool(use_guess)),
                                   _ptr(u, self.N), ctypes.byref(info)), self.handle, allow)
         d = info.as_dict()
@@ -242,6 +262,7 @@ class Grid:
         return k.value
 
     def whv_lanczos(self, params, nd, m, v0=None, fp64_stepping=True, flags=WHV_BASIS_REDEFLATE):
+        self._pre()
         theta = (ctypes.c_double * nd)()
         resid = (ctypes.c_double * nd)()
         _check(lib.whv_lanczos(self.handle, ctypes.byref(params), int(nd), int(m), _ptr(v0, self.N),
@@ -255,6 +276,7 @@ class Grid:
         gf = torch.empty_like(z) if want_f else None
         info = whv_info()
         allow = () if raise_not_converged else (WHV_ERR_NOT_CONVERGED,)
+        self._pre()
         st = _check(lib.whv_solve_adjoint(self.handle, ctypes.byref(params), _ptr(f, self.N), _ptr(u, self.N),
                                           _ptr(dLdu, self.N), _ptr(z, self.N), _ptr(gc2), _ptr(gf),
                                           int(checkpoint_every), ctypes.byref(info)), self.handle, allow)
@@ -263,14 +285,19 @@ class Grid:
         return z, gc2, gf, d
 
     def whv_project(self, r, coef):
+        self._pre()
         _check(lib.whv_project(self.handle, _ptr(r, self.N), _ptr(coef)), self.handle)
+        self._post()
         return coef
 
     def whv_expand(self, y, alpha, out):
+        self._pre()
         _check(lib.whv_expand(self.handle, _ptr(y), float(alpha), _ptr(out, self.N)), self.handle)
+        self._post()
         return out
 
     def whv_dot(self, x, y):
+        self._pre()
         out = ctypes.c_double()
         _check(lib.whv_dot(self.handle, _ptr(x, self.N), _ptr(y, self.N), ctypes.byref(out)), self.handle)
         return out.value

@@ -222,14 +222,23 @@ whv_status whv_solve_adjoint(whv_grid grid, const whv_params* p, const double* f
  * solution goes to u_dev[p].  Every problem needs its own grid object; all grids share one
  * stream, precision, dimension (2 or 3), order and speed kind (all c = 1 or all variable).
  * Method WHV_CG only; a grid's basis, if set, must be exact eigenvectors for params[p] (DEVD,
- * Algorithm 2).  All problems iterate together: every CG iteration's wave solves of all active
- * problems run in ONE persistent cooperative kernel launch (step s sweeps the tiles of every
- * problem with Nt > s, then a grid barrier); b of all problems likewise.  The whole CG loop is one
- * CUDA graph with a conditional WHILE node that runs until every problem has converged or hit its
- * maxit.  The grid barrier waits a bounded time: if it gives up the call returns WHV_ERR_TIMEOUT.
- * infos (host, nprob entries, may be NULL) receive per-problem counts and recursive residuals
- * (no FP64 residual correction in this entry point).  Returns WHV_ERR_NOT_CONVERGED if any
- * problem missed its tolerance (all solutions still written). */
+ * Algorithm 2).  All problems iterate together: each batched wave solve (b, or q = A p of every
+ * active problem) is ONE persistent cooperative kernel launch -- 2-D grids advance k leapfrog
+ * steps per sweep in shared-memory tiles (k = the first grid's whv_set_steps_per_sweep value, else
+ * 8 in FP32 / 4 in FP64, halved for order 4), 3-D grids one step per sweep, with a grid barrier
+ * between sweeps.  The CG loop is one CUDA graph with a conditional WHILE node that runs until
+ * every problem has converged or hit its maxit.
+ * WHV_REFINE_FP64 in params[].flags (all problems or none) adds FP64 residual correction: b and
+ * r = b - A u of the full system come from FP64 batched wave solves, the deflated components of r
+ * are solved modally and the rest by the batched CG loop to params[p].inner_tol (default 1e-3),
+ * repeated until each problem's FP64 residual ||b - A u|| / ||b|| <= tol (reported in
+ * true_rel_residual).  Without it infos report the recursive residual of the deflated system and
+ * true_rel_residual = -1.  Temporary device memory: the descriptor tables (a few KB); with
+ * WHV_REFINE_FP64 an FP32 grid also gets its FP64 buffer set (8 N doubles, kept by the grid).
+ * The grid barrier waits a bounded time: if it gives up the call returns WHV_ERR_TIMEOUT.
+ * infos (host, nprob entries, may be NULL) receive per-problem counts and residuals.  Returns
+ * WHV_ERR_NOT_CONVERGED if any problem missed its tolerance (all solutions still written),
+ * WHV_ERR_BREAKDOWN if a problem's CG broke down. */
 whv_status whv_solve_batched(int nprob, const whv_grid* grids, const whv_params* params,
                              const double* const* f_dev, double* const* u_dev, whv_info* infos);
 

@@ -1,18 +1,29 @@
 // Batched solves: many independent problems -- right-hand sides, frequencies and grids of uneven
 // size -- advanced together.
 //
-// One persistent cooperative kernel (k_batch_wave) performs a wave solve of every active problem:
-// at global step s it sweeps the tiles of all problems whose Nt exceeds s (problems sorted by Nt,
-// so they are a prefix of the list), then all CTAs meet at a grid barrier before step s + 1.
-// Problems with fewer steps drop out early; converged problems are skipped.  The barrier spins
-// with an iteration limit: a CTA that gives up raises an error flag and every CTA returns.
+// A batched wave solve (one role, e.g. q_p = A p_p, for every active problem) is ONE persistent
+// cooperative kernel launch:
+//  - 2-D grids: k_batch_block2d sweeps k leapfrog steps at a time.  A sweep processes the tiles of
+//    every problem that still has steps left; each tile stages a 64 x 64 region (its (64-2kr)^2
+//    nodes plus a halo of width kr, r the stencil radius) and advances it k steps in registers
+//    and shared memory; then all CTAs meet at a grid barrier.  Global traffic is 3 reads and 3
+//    writes per node per k steps (plus the halo) instead of 5 accesses per step.
+//  - 3-D grids: k_batch_wave sweeps one step at a time (tiles of 32 x 8 nodes per z plane).
+// Problems are sorted by their number of sweeps, so the active ones are a prefix of the list;
+// stopped problems are skipped a whole problem at a time.  The barrier spins with an iteration
+// limit: a CTA that gives up raises an error flag and every CTA returns.
 //
-// The batched CG loop is one CUDA graph: a conditional WHILE node whose body is the persistent
-// wave solve (q_p = A p_p for all p, with the per-tile partial sums of p^T M q), a finishing
-// kernel (p^T M q per problem, deterministic order), each problem's fused CG update and direction
-// update (which return at once for stopped problems), a per-problem convergence check and a
-// one-thread kernel that keeps the loop running while any problem is active.  DEVD (Algorithm 2)
-// deflation / inflation per problem happens before and after, with each grid's basis.
+// The batched CG loop is one CUDA graph: a conditional WHILE node whose body is the batched wave
+// solve (q_p = A p_p with per-tile partial sums of p^T M q), a finishing kernel (p^T M q per
+// problem, fixed order), each problem's fused CG update and direction update (which return at
+// once for stopped problems), a per-problem convergence test and a one-thread kernel that keeps
+// the loop running while any problem is active.
+//
+// Without FP64 residual correction, DEVD (Algorithm 2) deflates each forcing first and inflates
+// each solution after the loop.  With it (WHV_REFINE_FP64), the residual r = b - A u of the full
+// system is formed by FP64 batched wave solves, its deflated components are solved modally and
+// the rest by the batched CG loop in the grids' stepping precision, until every problem's FP64
+// residual meets its tolerance.
 #include <math.h>
 
 #include <algorithm>
@@ -25,24 +36,8 @@
 
 namespace whv {
 
-template <typename T>
-struct BProb {
-  T* w0;                 // stepping buffers: W^0, W^1 ... ping-pong
-  T* w1;
-  T* acc;                // filter accumulator
-  const double* v;       // initial state (nullptr: 0)
-  const double* f;       // forcing (nullptr: 0)
-  double* out;           // epi 0: Pi_h v;  epi 1: v - Pi_h v
-  const T* c2;           // squared speed (nullptr: 1)
-  const double* mw;      // M weights (nullptr: 1)
-  double* partials;      // epi 1: per-tile partial sums of <v, out>_M
-  const double* halt;    // problem stopped when *halt != 0 (nullptr: never)
-  int64_t tile0;         // first work item of this problem (exclusive prefix over problems)
-  int nx, ny, nz, nt, tx, ty, ntiles, epi, wofs;
-  StepCoef<T> cf;
-};
-
 constexpr unsigned long long kBarrierSpins = 1ull << 26;   // x 64 ns sleeps: ~4 s
+constexpr int kBatchMaxProblems = 1024;
 
 // Grid-wide barrier of a cooperative launch with a bounded wait.  Returns false (and raises
 // *err) if a CTA waited past the limit or another CTA raised *err.
@@ -63,6 +58,8 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, int* err, unsigned 
       unsigned long long spins = 0;
       while (*vgen == g0) {
         if (++spins > kBarrierSpins) { atomicExch(err, 1); ok = 0; break; }
+        // another CTA gave up: stop waiting for a barrier that will not complete
+        if ((spins & 1023ull) == 0 && *(volatile int*)err) { ok = 0; break; }
         __nanosleep(64);
       }
     }
@@ -74,7 +71,30 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, int* err, unsigned 
   return s_ok != 0;
 }
 
-constexpr int kBatchMaxProblems = 1024;
+// Work item to continue from so that the CTA's next item (this one + gridDim.x) is the first at
+// or after `end`: skips the rest of a stopped problem's tiles.
+__device__ __forceinline__ int64_t skip_to(int64_t item, int64_t end) {
+  const int64_t G = gridDim.x;
+  return item + ((end - item + G - 1) / G - 1) * G;
+}
+
+// ------------------------------------------------------------------ 3-D: one step per sweep
+template <typename T>
+struct BProb {
+  T* w0;                 // stepping buffers: W^0, W^1 ... ping-pong
+  T* w1;
+  T* acc;                // filter accumulator
+  const double* v;       // initial state (nullptr: 0)
+  const double* f;       // forcing (nullptr: 0)
+  double* out;           // epi 0: Pi_h v;  epi 1: v - Pi_h v
+  const T* c2;           // squared speed (nullptr: 1)
+  const double* mw;      // M weights (nullptr: 1)
+  double* partials;      // epi 1: per-tile partial sums of <v, out>_M
+  const double* halt;    // problem stopped when *halt != 0 (nullptr: never)
+  int64_t tile0;         // first work item of this problem (exclusive prefix over problems)
+  int nx, ny, nz, nt, tx, ty, ntiles, epi, wofs;
+  StepCoef<T> cf;
+};
 
 template <typename T, int DIM, int ORDER, bool VARC>
 __global__ void __launch_bounds__(256) k_batch_wave(const BProb<T>* __restrict__ P, const int* __restrict__ nact,
@@ -103,7 +123,10 @@ __global__ void __launch_bounds__(256) k_batch_wave(const BProb<T>* __restrict__
         cur = p;
       }
       const BProb<T>& B = sB;
-      if (B.halt && *B.halt != 0.0) continue;   // uniform per block
+      if (B.halt && *B.halt != 0.0) {   // uniform per block: skip the problem
+        item = skip_to(item, s_tile0[p + 1]);
+        continue;
+      }
       const int t = (int)(item - B.tile0);
       const int tx = t % B.tx, ty = (t / B.tx) % B.ty, tz = t / (B.tx * B.ty);
       const int x = tx * 32 + lx, y = ty * 8 + ly, z = tz;
@@ -156,15 +179,204 @@ __global__ void __launch_bounds__(256) k_batch_wave(const BProb<T>* __restrict__
   }
 }
 
-// p^T M q of every problem from its per-tile partial sums (one block per problem, fixed order)
+// ------------------------------------------------------------------ 2-D: k steps per sweep
+constexpr int kBReg = 64;                  // staged region edge
+constexpr int kBThreads = 1024;            // 32 warps
+constexpr int kBPitch = kBThreads / 64;    // rows between a thread's cells (16)
+constexpr int kBRows = kBReg / kBPitch;    // cells per thread (4)
+
 template <typename T>
-__global__ void k_batch_finish(const BProb<T>* __restrict__ P, double* const* __restrict__ scal) {
-  const BProb<T>& B = P[blockIdx.x];
-  if (B.epi != 1 || (B.halt && *B.halt != 0.0)) return;
+struct BTile {
+  T* w[4];               // two (W^{n-1}, W^n) pairs: sweep j writes pair j & 1
+  T* acc;                // filter accumulator
+  const double* v;       // W^0 (nullptr: 0)
+  const double* f;       // forcing (FORCED kernels)
+  double* out;           // epi 0: Pi_h(v; f);  epi 1: v - Pi_h v
+  const T* c2;           // squared speed (VARC kernels)
+  const double* mw;      // M weights (nullptr: 1)
+  double* partials;      // epi 1: per-tile partial sums of <v, out>_M
+  const double* halt;    // problem stopped when *halt != 0 (nullptr: never)
+  int64_t tile0;
+  int nx, ny, nt, tiles_x, ntiles, epi, wofs;
+  T ih2x, ih2y, dt2;
+  T ax, ay, b;           // 2nd order, c = 1: W^{n+1} = ax s_x + ay s_y + b W^n - W^{n-1}
+};
+
+// second difference at global index gi (of n) read from shared memory at local offset l, stride
+// s, with the Dirichlet / odd-reflection closure
+template <int ORDER, typename T>
+__device__ __forceinline__ T d2b(const T* __restrict__ a, int l, int gi, int n, int s, T c) {
+  const T m1 = gi > 0 ? a[l - s] : T(0);
+  const T p1 = gi < n - 1 ? a[l + s] : T(0);
+  if (ORDER == 2) return fma(T(-2), c, m1 + p1);
+  const T m2 = gi > 1 ? a[l - 2 * s] : (gi == 1 ? T(0) : -c);
+  const T p2 = gi < n - 2 ? a[l + 2 * s] : (gi == n - 2 ? T(0) : -c);
+  return fma(T(-30), c, fma(T(16), m1 + p1, -(m2 + p2)));
+}
+
+// Sweep j of problem p covers steps n0 = j K .. n0 + kk - 1 (W^{n0} -> W^{n0+kk}), kk = min(K,
+// nt - n0).  Sweep 0 starts from W^0 = v with the Taylor step; the last sweep writes the FP64
+// epilogue instead of the state.  Thread (warp w, lane) owns column 32 (w & 1) + lane and rows
+// (w >> 1) + 16 r, r < 4, of the staged region for the whole sweep.
+template <typename T, int ORDER, bool VARC, bool FORCED>
+__global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* __restrict__ P,
+                                                                const int* __restrict__ nact, int J, int K,
+                                                                const T* __restrict__ wtab,
+                                                                const T* __restrict__ ptab, unsigned* bar_count,
+                                                                unsigned* bar_gen, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* const S0 = reinterpret_cast<T*>(smem_raw);
+  T* const S1 = S0 + kBReg * kBReg;
+  __shared__ int64_t s_tile0[kBatchMaxProblems + 1];
+  __shared__ BTile<T> sB;
+  constexpr int R = ORDER == 2 ? 1 : 2;
+  const int np = nact[0];
+  for (int p = threadIdx.x; p <= np; p += blockDim.x)
+    s_tile0[p] = p < np ? P[p].tile0 : P[np - 1].tile0 + P[np - 1].ntiles;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = 32 * (warp & 1) + lane;
+  const int jb = warp >> 1;
+  const int H = K * R, TW = kBReg - 2 * H;
+  for (int j = 0; j < J; ++j) {
+    const int A = nact[j];
+    const int64_t total = s_tile0[A];
+    int cur_p = -1;
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+      int p = cur_p < 0 ? 0 : cur_p;
+      while (s_tile0[p + 1] <= item) ++p;
+      if (p != cur_p) {
+        __syncthreads();
+        if (threadIdx.x == 0) sB = P[p];
+        __syncthreads();
+        cur_p = p;
+      }
+      const BTile<T>& B = sB;
+      if (B.halt && *B.halt != 0.0) {
+        item = skip_to(item, s_tile0[p + 1]);
+        continue;
+      }
+      const int t = (int)(item - B.tile0);
+      const int x0 = (t % B.tiles_x) * TW - H, y0 = (t / B.tiles_x) * TW - H;
+      const int gx = x0 + i;
+      const int nx = B.nx, ny = B.ny;
+      const bool colin = gx >= 0 && gx < nx;
+      const int n0 = j * K;
+      const int kk = min(K, B.nt - n0);
+      const bool first = j == 0, last = n0 + kk == B.nt;
+      const T* wtb = wtab + B.wofs;
+      const T* ptb = ptab + B.wofs;
+      const int qi = (j + 1) & 1, qo = j & 1;   // input pair (written by sweep j - 1), output pair
+      T cur[kBRows], prv[kBRows], acr[kBRows];
+      T cc[VARC ? kBRows : 1];
+      T ff[FORCED ? kBRows : 1];
+      const T w0 = first ? wtb[0] : T(0);
+#pragma unroll
+      for (int r = 0; r < kBRows; ++r) {
+        const int gy = y0 + jb + kBPitch * r;
+        const bool in = colin && gy >= 0 && gy < ny;
+        const int64_t gi = gx + (int64_t)nx * gy;
+        if (first) {
+          cur[r] = (in && B.v) ? (T)__ldg(B.v + gi) : T(0);
+          prv[r] = T(0);
+        } else {   // written by other CTAs in the previous sweep of this launch: coherent loads
+          cur[r] = in ? __ldcg(B.w[2 * qi + 1] + gi) : T(0);
+          prv[r] = in ? __ldcg(B.w[2 * qi] + gi) : T(0);
+        }
+        if (VARC) cc[r] = in ? __ldg(B.c2 + gi) : T(0);
+        if (FORCED) ff[r] = in ? (T)__ldg(B.f + gi) : T(0);
+        acr[r] = w0 * cur[r];
+      }
+#pragma unroll
+      for (int r = 0; r < kBRows; ++r) S0[(jb + kBPitch * r) * kBReg + i] = cur[r];
+      __syncthreads();
+      T* Ain = S0;
+      T* Bout = S1;
+      for (int s = 1; s <= kk; ++s) {
+        const int n = n0 + s - 1;   // W^n -> W^{n+1}
+        const int lo = s * R, hi = kBReg - s * R;
+        const bool colact = colin && i >= lo && i < hi;
+        const T ws = wtb[n + 1];
+        // forcing term dt^2 f cos(omega_hat t^n) (half of it in the Taylor step)
+        const T fph = FORCED ? (n > 0 ? B.dt2 : T(0.5) * B.dt2) * ptb[n] : T(0);
+#pragma unroll
+        for (int r = 0; r < kBRows; ++r) {
+          const int jr = jb + kBPitch * r;
+          const int gy = y0 + jr;
+          if (colact && jr >= lo && jr < hi && gy >= 0 && gy < ny) {
+            const int l = jr * kBReg + i;
+            const T c = cur[r];
+            T wn;
+            if (ORDER == 2 && !VARC && n > 0) {
+              T u = fma(B.b, c, -prv[r]);
+              u = fma(B.ax, (gx > 0 ? Ain[l - 1] : T(0)) + (gx < nx - 1 ? Ain[l + 1] : T(0)), u);
+              wn = fma(B.ay, (gy > 0 ? Ain[l - kBReg] : T(0)) + (gy < ny - 1 ? Ain[l + kBReg] : T(0)), u);
+            } else {
+              T L = d2b<ORDER>(Ain, l, gx, nx, 1, c) * B.ih2x;
+              L = fma(d2b<ORDER>(Ain, l, gy, ny, kBReg, c), B.ih2y, L);
+              if (VARC) L *= cc[r];
+              wn = n > 0 ? fma(B.dt2, L, fma(T(2), c, -prv[r]))
+                         : fma(T(0.5) * B.dt2, L, c);   // Taylor start: W^1 = W^0 + dt^2/2 L W^0
+            }
+            if (FORCED) wn = fma(-fph, ff[r], wn);
+            prv[r] = c;
+            cur[r] = wn;
+            Bout[l] = wn;
+            acr[r] = fma(ws, wn, acr[r]);
+          }
+        }
+        __syncthreads();
+        T* tmp = Ain;
+        Ain = Bout;
+        Bout = tmp;
+      }
+      double part = 0.0;
+      const bool coltile = colin && i >= H && i < kBReg - H;
+#pragma unroll
+      for (int r = 0; r < kBRows; ++r) {
+        const int jr = jb + kBPitch * r;
+        const int gy = y0 + jr;
+        if (!(coltile && jr >= H && jr < kBReg - H && gy >= 0 && gy < ny)) continue;
+        const int64_t gi = gx + (int64_t)nx * gy;
+        const T a = first ? acr[r] : __ldcg(B.acc + gi) + acr[r];
+        if (!last) {
+          B.w[2 * qo + 1][gi] = cur[r];
+          B.w[2 * qo][gi] = prv[r];
+          B.acc[gi] = a;
+        } else if (B.epi == 0) {
+          B.out[gi] = (double)a;
+        } else {
+          const double vi = __ldg(B.v + gi);
+          const double o = vi - (double)a;
+          B.out[gi] = o;
+          part = fma(B.mw ? vi * __ldg(B.mw + gi) : vi, o, part);
+        }
+      }
+      if (last && B.epi == 1) {
+        part = block_sum(part);
+        if (threadIdx.x == 0) B.partials[t] = part;
+      }
+    }
+    if (!grid_barrier(bar_count, bar_gen, err, gridDim.x)) return;
+  }
+}
+
+// ------------------------------------------------------------------ per-problem small kernels
+struct BFin {
+  const double* partials;
+  const double* halt;
+  double* scal;
+  int ntiles;
+};
+
+// p^T M q of every problem from its per-tile partial sums (one block per problem, fixed order)
+__global__ void k_batch_finish(const BFin* __restrict__ F) {
+  const BFin& B = F[blockIdx.x];
+  if (B.halt && *B.halt != 0.0) return;
   double s = 0.0;
   for (int t = threadIdx.x; t < B.ntiles; t += blockDim.x) s += B.partials[t];
   s = block_sum(s);
-  if (threadIdx.x == 0) scal[blockIdx.x][S_PQ] = s;
+  if (threadIdx.x == 0) B.scal[S_PQ] = s;
 }
 
 // per-problem convergence test of the batched CG loop (one thread per problem)
@@ -187,243 +399,567 @@ __global__ void k_batch_any(cudaGraphConditionalHandle h, double* const* __restr
   cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
-struct BatchScratch {
-  void* desc = nullptr;       // BProb<T>[np] for the A p solves
-  void* desc_b = nullptr;     // BProb<T>[np] for the b solves
+// ------------------------------------------------------------------ host side
+// One role of batched wave solve (e.g. q = A p of every problem in FP32, or b in FP64): its
+// device descriptor table and the launcher of the kernel variant it needs.
+struct Wave {
+  void* desc = nullptr;
   int* nact = nullptr;
   void* wtab = nullptr;
   void* ptab = nullptr;
-  double** scal = nullptr;
-  unsigned* bar = nullptr;    // count, generation
+  BFin* fin = nullptr;
+  int J = 0, K = 1, nblocks = 1;
+  size_t smem = 0;
+  cudaError_t (*launch)(cudaStream_t, const Wave&, unsigned*, int*) = nullptr;
+};
+
+// per-problem inputs of one role
+struct RoleIO {
+  std::vector<const double*> v, f;   // v: initial state (nullptr: 0); f: forcing (nullptr: none)
+  std::vector<double*> out;
+  int epi = 0;
+  bool halt = false;                 // skip stopped problems
+};
+
+struct BatchCtx {
+  int np = 0;
+  const whv_grid* grids = nullptr;
+  const whv_params* params = nullptr;
+  std::vector<TimeGridH> tgs;
+  whv_grid g0 = nullptr;
+  cudaStream_t st = nullptr;
+  int sms = 148;
+  unsigned* bar = nullptr;     // count, generation
   int* err = nullptr;
-  void free_all() {
-    for (void* p : {desc, desc_b, (void*)nact, wtab, ptab, (void*)scal, (void*)bar, (void*)err})
-      if (p) cudaFree(p);
+  double** scal = nullptr;     // device array of the problems' scalar blocks
+  std::vector<void*> allocs;
+  int64_t launches = 0;
+  ~BatchCtx() {
+    if (st) cudaStreamSynchronize(st);
+    for (void* p : allocs) cudaFree(p);
+  }
+  template <typename X>
+  cudaError_t alloc(X** p, size_t bytes) {
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) allocs.push_back((void*)*p);
+    return e;
+  }
+  template <typename F>
+  auto each(F fn) const -> std::vector<decltype(fn(grids[0]))> {
+    std::vector<decltype(fn(grids[0]))> v(np);
+    for (int p = 0; p < np; ++p) v[p] = fn(grids[p]);
+    return v;
   }
 };
 
-template <typename T, int DIM, int ORDER, bool VARC>
-static cudaError_t launch_batch_wave(cudaStream_t st, const void* desc, const int* nact, int S, const void* wtab,
-                                     const void* ptab, unsigned* bar, int* err, int nblocks) {
-  const BProb<T>* P = (const BProb<T>*)desc;
-  const T* w = (const T*)wtab;
-  const T* ph = (const T*)ptab;
+#define B_CUDA(g, call) \
+  do { cudaError_t _e = (call); if (_e != cudaSuccess) return cuda_fail((g), _e, #call); } while (0)
+
+// steps per sweep of the blocked 2-D kernel: the grid's setting (whv_set_steps_per_sweep) if
+// any, else 8 (FP32) / 4 (FP64) steps of the 5-point stencil, half that for the 9-point one
+static int batch_k(whv_grid g, bool fp64) {
+  const int R = g->order == 2 ? 1 : 2;
+  int k = g->kblock > 0 ? g->kblock : (fp64 ? 4 : 8) / R;
+  k = std::min(std::max(k, 1), 16);
+  while (k > 1 && kBReg - 2 * k * R < 16) --k;
+  return k;
+}
+
+template <typename T, int ORDER, bool VARC, bool FORCED>
+static cudaError_t launch_block2d(cudaStream_t st, const Wave& w, unsigned* bar, int* err) {
+  const BTile<T>* P = (const BTile<T>*)w.desc;
+  const T* wt = (const T*)w.wtab;
+  const T* ph = (const T*)w.ptab;
   unsigned* bc = bar;
   unsigned* bg = bar + 1;
-  void* args[] = {(void*)&P, (void*)&nact, (void*)&S, (void*)&w, (void*)&ph, (void*)&bc, (void*)&bg, (void*)&err};
-  return cudaLaunchCooperativeKernel((const void*)k_batch_wave<T, DIM, ORDER, VARC>, dim3(nblocks), dim3(32, 8),
+  int J = w.J, K = w.K;
+  const int* na = w.nact;
+  void* args[] = {(void*)&P, (void*)&na, (void*)&J, (void*)&K, (void*)&wt, (void*)&ph,
+                  (void*)&bc, (void*)&bg, (void*)&err};
+  return cudaLaunchCooperativeKernel((const void*)k_batch_block2d<T, ORDER, VARC, FORCED>, dim3(w.nblocks),
+                                     dim3(kBThreads), args, w.smem, st);
+}
+
+template <typename T, int DIM, int ORDER, bool VARC>
+static cudaError_t launch_wave3(cudaStream_t st, const Wave& w, unsigned* bar, int* err) {
+  const BProb<T>* P = (const BProb<T>*)w.desc;
+  const T* wt = (const T*)w.wtab;
+  const T* ph = (const T*)w.ptab;
+  unsigned* bc = bar;
+  unsigned* bg = bar + 1;
+  int S = w.J;
+  const int* na = w.nact;
+  void* args[] = {(void*)&P, (void*)&na, (void*)&S, (void*)&wt, (void*)&ph, (void*)&bc, (void*)&bg, (void*)&err};
+  return cudaLaunchCooperativeKernel((const void*)k_batch_wave<T, DIM, ORDER, VARC>, dim3(w.nblocks), dim3(32, 8),
                                      args, 0, st);
 }
 
-template <typename T, int DIM, int ORDER, bool VARC>
-static int max_coresident(int sms) {
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_wave<T, DIM, ORDER, VARC>, 256, 0);
-  return std::max(1, per_sm) * sms;
+// opt the blocked kernels into their dynamic shared memory (FP64: 64 KB) once per process,
+// outside any stream capture
+template <typename T, int ORDER, bool VARC>
+static void block2d_attrs() {
+  const int bytes = 2 * kBReg * kBReg * (int)sizeof(T);
+  cudaFuncSetAttribute(k_batch_block2d<T, ORDER, VARC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_batch_block2d<T, ORDER, VARC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+static void batch_init() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  block2d_attrs<float, 2, false>(); block2d_attrs<float, 2, true>();
+  block2d_attrs<float, 4, false>(); block2d_attrs<float, 4, true>();
+  block2d_attrs<double, 2, false>(); block2d_attrs<double, 2, true>();
+  block2d_attrs<double, 4, false>(); block2d_attrs<double, 4, true>();
 }
 
+// Device tables of one role, stepping in T (double on an FP32 grid: its FP64 buffer set).
+// Problems are ordered by their number of sweeps (descending), so the active problems of sweep j
+// are a prefix.
 template <typename T, int DIM, int ORDER, bool VARC>
-static whv_status batched_cg(int np, const whv_grid* grids, const whv_params* params,
-                             const std::vector<TimeGridH>& tgs, const std::vector<const double*>& rhs_force,
-                             whv_info* infos, int* iters_out, BatchScratch& bs) {
-  whv_grid g0 = grids[0];
-  cudaStream_t st = g0->stream;
-  // problems sorted by Nt descending: the active ones at step s are a prefix
-  std::vector<int> order(np);
+static whv_status make_wave(BatchCtx& c, const RoleIO& io, Wave* out) {
+  const int np = c.np;
+  const bool fp64 = sizeof(T) == 8;
+  const bool blocked = DIM == 2;
+  bool forced = false;
+  for (const double* f : io.f) forced = forced || f != nullptr;
+  Wave w;
+  w.K = blocked ? batch_k(c.g0, fp64) : 1;
+  std::vector<int> order(np), nsw(np);
+  for (int p = 0; p < np; ++p) nsw[p] = (c.tgs[p].nt + w.K - 1) / w.K;
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tgs[a].nt > tgs[b].nt; });
-  const int S = tgs[order[0]].nt;
-  std::vector<BProb<T>> desc(np), desc_b(np);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nsw[a] > nsw[b]; });
+  w.J = nsw[order[0]];
   std::vector<T> wtab, ptab;
-  std::vector<double*> scal(np);
+  std::vector<BFin> fin(np);
+  std::vector<BTile<T>> d2(blocked ? np : 0);
+  std::vector<BProb<T>> d3(blocked ? 0 : np);
   int64_t tile0 = 0;
+  const int R = ORDER == 2 ? 1 : 2;
+  const int TW = kBReg - 2 * w.K * R;
   for (int k = 0; k < np; ++k) {
     const int p = order[k];
-    whv_grid g = grids[p];
-    const TimeGridH& tg = tgs[p];
-    BProb<T> B{};
-    B.w0 = (T*)g->wbuf[0];
-    B.w1 = (T*)g->wbuf[1];
-    B.acc = (T*)g->acc;
-    B.c2 = VARC ? (const T*)(sizeof(T) == 8 ? (const void*)g->c2 : (const void*)g->c2f) : nullptr;
-    B.mw = g->mw;
-    B.partials = chan(g, CH_STEP);
-    B.halt = g->scal + S_HALT;
-    B.nx = g->n[0]; B.ny = g->n[1]; B.nz = g->n[2];
-    B.nt = tg.nt;
-    B.tx = (g->n[0] + 31) / 32;
-    B.ty = (g->n[1] + 7) / 8;
-    B.ntiles = B.tx * B.ty * (DIM > 2 ? g->n[2] : 1);
-    if (B.ntiles > chan_cap(g, CH_STEP)) return fail(g0, WHV_ERR_INVALID, "batched: grid too large for its reduction channel");
-    B.tile0 = tile0;
-    tile0 += B.ntiles;
-    B.wofs = (int)wtab.size();
+    whv_grid g = c.grids[p];
+    const TimeGridH& tg = c.tgs[p];
+    const bool other = fp64 && g->precision != WHV_FP64;
+    void* const* bufs = other ? g->wbuf64 : g->wbuf;
+    void* accb = other ? g->acc64 : g->acc;
+    if (!accb || !bufs[0]) return fail(c.g0, WHV_ERR_INVALID, "batched: stepping buffers missing");
+    const T* c2 = VARC ? (const T*)(fp64 ? (const void*)g->c2 : (const void*)g->c2f) : nullptr;
+    const int wofs = (int)wtab.size();
     for (int n = 0; n <= tg.nt; ++n) { wtab.push_back((T)tg.weight[n]); ptab.push_back((T)tg.phase[n]); }
-    for (int m = 0; m < 3; ++m) {
-      const double h2 = g->h[m] * g->h[m];
-      B.cf.ih2[m] = (T)(g->order == 2 ? 1.0 / h2 : 1.0 / (12.0 * h2));
+    const double h2x = g->h[0] * g->h[0], h2y = g->h[1] * g->h[1];
+    int ntiles;
+    if (blocked) {
+      BTile<T> B{};
+      for (int m = 0; m < 4; ++m) B.w[m] = (T*)bufs[m];
+      B.acc = (T*)accb;
+      B.v = io.v[p]; B.f = io.f[p]; B.out = io.out[p];
+      B.c2 = c2; B.mw = g->mw; B.partials = chan(g, CH_STEP);
+      B.halt = io.halt ? g->scal + S_HALT : nullptr;
+      B.nx = g->n[0]; B.ny = g->n[1]; B.nt = tg.nt;
+      B.tiles_x = (g->n[0] + TW - 1) / TW;
+      B.ntiles = B.tiles_x * ((g->n[1] + TW - 1) / TW);
+      B.epi = io.epi; B.wofs = wofs;
+      B.ih2x = (T)(ORDER == 2 ? 1.0 / h2x : 1.0 / (12.0 * h2x));
+      B.ih2y = (T)(ORDER == 2 ? 1.0 / h2y : 1.0 / (12.0 * h2y));
+      B.dt2 = (T)(tg.dt * tg.dt);
+      const double ax = tg.dt * tg.dt / h2x, ay = tg.dt * tg.dt / h2y;
+      B.ax = (T)ax; B.ay = (T)ay; B.b = (T)(2.0 - 2.0 * (ax + ay));
+      B.tile0 = tile0;
+      ntiles = B.ntiles;
+      d2[k] = B;
+    } else {
+      if (!bufs[1]) return fail(c.g0, WHV_ERR_INVALID, "batched: stepping buffers missing");
+      BProb<T> B{};
+      B.w0 = (T*)bufs[0]; B.w1 = (T*)bufs[1]; B.acc = (T*)accb;
+      B.v = io.v[p]; B.f = io.f[p]; B.out = io.out[p];
+      B.c2 = c2; B.mw = g->mw; B.partials = chan(g, CH_STEP);
+      B.halt = io.halt ? g->scal + S_HALT : nullptr;
+      B.nx = g->n[0]; B.ny = g->n[1]; B.nz = g->n[2]; B.nt = tg.nt;
+      B.tx = (g->n[0] + 31) / 32; B.ty = (g->n[1] + 7) / 8;
+      B.ntiles = B.tx * B.ty * g->n[2];
+      B.epi = io.epi; B.wofs = wofs;
+      for (int m = 0; m < 3; ++m) {
+        const double h2 = g->h[m] * g->h[m];
+        B.cf.ih2[m] = (T)(ORDER == 2 ? 1.0 / h2 : 1.0 / (12.0 * h2));
+      }
+      B.cf.dt2 = (T)(tg.dt * tg.dt);
+      B.tile0 = tile0;
+      ntiles = B.ntiles;
+      d3[k] = B;
     }
-    B.cf.dt2 = (T)(tg.dt * tg.dt);
-    // A p solves: v = p, out = q, epi 1
-    B.v = g->p; B.f = nullptr; B.out = g->q; B.epi = 1;
-    desc[k] = B;
-    // b solves: v = 0, forcing, out = t (b), epi 0, never halted
-    BProb<T> Bb = B;
-    Bb.v = nullptr; Bb.f = rhs_force[p]; Bb.out = g->t; Bb.epi = 0; Bb.halt = nullptr;
-    desc_b[k] = Bb;
-    scal[k] = g->scal;
+    if (io.epi == 1 && ntiles > chan_cap(g, CH_STEP))
+      return fail(c.g0, WHV_ERR_INVALID, "batched: grid too large for its reduction channel");
+    fin[k] = BFin{chan(g, CH_STEP), io.halt ? g->scal + S_HALT : nullptr, g->scal, ntiles};
+    tile0 += ntiles;
   }
-  std::vector<int> nact(S);
-  for (int s = 0; s < S; ++s) {
+  std::vector<int> nact(w.J);
+  for (int j = 0; j < w.J; ++j) {
     int a = 0;
-    while (a < np && tgs[order[a]].nt > s) ++a;
-    nact[s] = a;
+    while (a < np && nsw[order[a]] > j) ++a;
+    nact[j] = a;
   }
-  // device tables
-#define B_CUDA(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) return cuda_fail(g0, _e, #call); } while (0)
-  B_CUDA(cudaMalloc(&bs.desc, np * sizeof(BProb<T>)));
-  B_CUDA(cudaMalloc(&bs.desc_b, np * sizeof(BProb<T>)));
-  B_CUDA(cudaMalloc(&bs.nact, S * sizeof(int)));
-  B_CUDA(cudaMalloc(&bs.wtab, wtab.size() * sizeof(T)));
-  B_CUDA(cudaMalloc(&bs.ptab, ptab.size() * sizeof(T)));
-  B_CUDA(cudaMalloc(&bs.scal, np * sizeof(double*)));
-  B_CUDA(cudaMalloc(&bs.bar, 2 * sizeof(unsigned)));
-  B_CUDA(cudaMalloc(&bs.err, sizeof(int)));
-  B_CUDA(cudaMemcpyAsync(bs.desc, desc.data(), np * sizeof(BProb<T>), cudaMemcpyHostToDevice, st));
-  B_CUDA(cudaMemcpyAsync(bs.desc_b, desc_b.data(), np * sizeof(BProb<T>), cudaMemcpyHostToDevice, st));
-  B_CUDA(cudaMemcpyAsync(bs.nact, nact.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
-  B_CUDA(cudaMemcpyAsync(bs.wtab, wtab.data(), wtab.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-  B_CUDA(cudaMemcpyAsync(bs.ptab, ptab.data(), ptab.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-  B_CUDA(cudaMemcpyAsync(bs.scal, scal.data(), np * sizeof(double*), cudaMemcpyHostToDevice, st));
-  B_CUDA(cudaMemsetAsync(bs.bar, 0, 2 * sizeof(unsigned), st));
-  B_CUDA(cudaMemsetAsync(bs.err, 0, sizeof(int), st));
-  B_CUDA(cudaStreamSynchronize(st));   // host tables above are pageable
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int nblocks = (int)std::min<int64_t>(max_coresident<T, DIM, ORDER, VARC>(sms), std::max<int64_t>(tile0, 1));
-  int64_t launches = 0;
-
-  // ---- b = Pi_h(0; f_p) of every problem: one persistent launch
-  B_CUDA((launch_batch_wave<T, DIM, ORDER, VARC>(st, bs.desc_b, bs.nact, S, bs.wtab, bs.ptab, bs.bar, bs.err, nblocks)));
-  ++launches;
-  // per-problem start: rr0 = <b, b>, x = 0, r = p = b, loop scalars
-  for (int k = 0; k < np; ++k) {
-    whv_grid g = grids[order[k]];
-    const whv_params* pp = &params[order[k]];
-    whv_status s = dot_async(g, g->t, g->t, S_RR0);
-    if (s != WHV_OK) return s;
-    s = fetch_scalars(g);
-    if (s != WHV_OK) return s;
-    const double bb = g->scal_host[S_RR0];
-    if (!isfinite(bb)) return fail(g0, WHV_ERR_BREAKDOWN, "batched: non-finite right-hand side");
-    B_CUDA(cudaMemsetAsync(g->x, 0, g->N * sizeof(double), st));
-    B_CUDA(cudaMemcpyAsync(g->r, g->t, g->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    B_CUDA(cudaMemcpyAsync(g->p, g->t, g->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    // S_RR, S_FLAG, S_ITER, S_STOP, S_MAXIT, S_HALT
-    double init[S_NSLOTS];
-    for (int i = 0; i < S_NSLOTS; ++i) init[i] = g->scal_host[i];
-    init[S_RR] = bb;
-    init[S_FLAG] = 0.0;
-    init[S_ITER] = 0.0;
-    init[S_STOP] = pp->tol * pp->tol * bb;
-    init[S_MAXIT] = (double)pp->maxit;
-    init[S_HALT] = (bb == 0.0 || pp->maxit == 0 || bb <= init[S_STOP]) ? 1.0 : 0.0;
-    B_CUDA(cudaMemcpyAsync(g->scal, init, S_NSLOTS * sizeof(double), cudaMemcpyHostToDevice, st));
-    B_CUDA(cudaStreamSynchronize(st));
-  }
-  launches += 3 * np;
-  // ---- the batched CG loop: one graph with a WHILE node
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  auto gfree = [&]() { if (exec) cudaGraphExecDestroy(exec); if (graph) cudaGraphDestroy(graph); };
-  B_CUDA(cudaGraphCreate(&graph, 0));
-  cudaGraphConditionalHandle h;
-  cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
-  if (e != cudaSuccess) { gfree(); return cuda_fail(g0, e, "cudaGraphConditionalHandleCreate"); }
-  cudaGraphNodeParams np_ = {};
-  np_.type = cudaGraphNodeTypeConditional;
-  np_.conditional.handle = h;
-  np_.conditional.type = cudaGraphCondTypeWhile;
-  np_.conditional.size = 1;
-  cudaGraphNode_t node;
-  e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np_);
-  if (e != cudaSuccess) { gfree(); return cuda_fail(g0, e, "cudaGraphAddNode (batched loop)"); }
-  cudaGraph_t body = np_.conditional.phGraph_out[0];
-  e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) { gfree(); return cuda_fail(g0, e, "cudaStreamBeginCaptureToGraph (batched loop)"); }
-  const int64_t l0 = whv_kernel_launches();
-  whv_status s = WHV_OK;
-  e = launch_batch_wave<T, DIM, ORDER, VARC>(st, bs.desc, bs.nact, S, bs.wtab, bs.ptab, bs.bar, bs.err, nblocks);
-  if (e == cudaSuccess) {
-    k_batch_finish<T><<<np, 256, 0, st>>>((const BProb<T>*)bs.desc, bs.scal);
-    e = cudaGetLastError();
-  }
-  for (int k = 0; k < np && e == cudaSuccess && s == WHV_OK; ++k) {
-    whv_grid g = grids[order[k]];
-    s = cg_update(g);
-    if (s == WHV_OK) s = cg_direction(g);
-  }
-  if (e == cudaSuccess && s == WHV_OK) {
-    k_batch_check<<<(np + 127) / 128, 128, 0, st>>>(bs.scal, np);
-    k_batch_any<<<1, 1, 0, st>>>(h, bs.scal, np, bs.err);
-    e = cudaGetLastError();
-  }
-  cudaGraph_t captured = nullptr;
-  cudaError_t e2 = cudaStreamEndCapture(st, &captured);
-  const int64_t body_launches = (whv_kernel_launches() - l0) + 4;   // + wave, finish, check, any
-  count_launches(-(whv_kernel_launches() - l0));
-  if (s != WHV_OK) { gfree(); return s; }
-  if (e != cudaSuccess) { gfree(); return cuda_fail(g0, e, "batched loop body"); }
-  if (e2 != cudaSuccess) { gfree(); return cuda_fail(g0, e2, "cudaStreamEndCapture (batched loop)"); }
-  e = cudaGraphInstantiate(&exec, graph, 0);
-  if (e != cudaSuccess) { gfree(); return cuda_fail(g0, e, "cudaGraphInstantiate (batched loop)"); }
-  e = cudaGraphLaunch(exec, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  gfree();
-  if (e != cudaSuccess) return cuda_fail(g0, e, "batched loop");
-  int herr = 0;
-  B_CUDA(cudaMemcpy(&herr, bs.err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (herr) return fail(g0, WHV_ERR_TIMEOUT, "batched wave solve: a grid barrier timed out");
-  int max_it = 0;
-  for (int k = 0; k < np; ++k) {
-    const int p = order[k];
-    whv_grid g = grids[p];
-    s = fetch_scalars(g);
-    if (s != WHV_OK) return s;
-    const int it = (int)g->scal_host[S_ITER];
-    max_it = std::max(max_it, it);
-    iters_out[p] = it;
-    if (infos) {
-      infos[p].iterations = it;
-      infos[p].wave_solves = it + 1;
-      infos[p].rel_residual = g->scal_host[S_RR0] > 0 ? sqrt(g->scal_host[S_RR] / g->scal_host[S_RR0]) : 0.0;
+  const size_t dbytes = blocked ? np * sizeof(BTile<T>) : np * sizeof(BProb<T>);
+  B_CUDA(c.g0, c.alloc(&w.desc, dbytes));
+  B_CUDA(c.g0, c.alloc(&w.nact, w.J * sizeof(int)));
+  B_CUDA(c.g0, c.alloc(&w.wtab, wtab.size() * sizeof(T)));
+  B_CUDA(c.g0, c.alloc(&w.ptab, ptab.size() * sizeof(T)));
+  B_CUDA(c.g0, c.alloc(&w.fin, np * sizeof(BFin)));
+  B_CUDA(c.g0, cudaMemcpy(w.desc, blocked ? (const void*)d2.data() : (const void*)d3.data(), dbytes,
+                          cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.nact, nact.data(), w.J * sizeof(int), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.wtab, wtab.data(), wtab.size() * sizeof(T), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.ptab, ptab.data(), ptab.size() * sizeof(T), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.fin, fin.data(), np * sizeof(BFin), cudaMemcpyHostToDevice));
+  int per_sm = 0;
+  if (blocked) {
+    w.smem = 2 * (size_t)kBReg * kBReg * sizeof(T);
+    if (forced) {
+      w.launch = &launch_block2d<T, ORDER, VARC, true>;
+      B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_block2d<T, ORDER, VARC, true>,
+                                                                 kBThreads, w.smem));
+    } else {
+      w.launch = &launch_block2d<T, ORDER, VARC, false>;
+      B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_block2d<T, ORDER, VARC, false>,
+                                                                 kBThreads, w.smem));
     }
+  } else {
+    w.launch = &launch_wave3<T, DIM, ORDER, VARC>;
+    B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_wave<T, DIM, ORDER, VARC>, 256, 0));
   }
-  count_launches(launches + body_launches * max_it);
-#undef B_CUDA
+  if (per_sm < 1) return fail(c.g0, WHV_ERR_INVALID, "batched: kernel cannot be resident on an SM");
+  w.nblocks = (int)std::min<int64_t>((int64_t)per_sm * c.sms, std::max<int64_t>(tile0, 1));
+  *out = w;
   return WHV_OK;
 }
 
-template <typename T, int DIM, int ORDER>
-static whv_status batched_vc(int np, const whv_grid* grids, const whv_params* params,
-                             const std::vector<TimeGridH>& tgs, const std::vector<const double*>& rf,
-                             whv_info* infos, int* iters, BatchScratch& bs, bool varc) {
-  return varc ? batched_cg<T, DIM, ORDER, true>(np, grids, params, tgs, rf, infos, iters, bs)
-              : batched_cg<T, DIM, ORDER, false>(np, grids, params, tgs, rf, infos, iters, bs);
+static whv_status run_wave(BatchCtx& c, const Wave& w) {
+  const cudaError_t e = w.launch(c.st, w, c.bar, c.err);
+  if (e != cudaSuccess) return cuda_fail(c.g0, e, "batched wave solve launch");
+  ++c.launches;
+  return WHV_OK;
 }
 
-template <typename T>
-static whv_status batched_dispatch(int np, const whv_grid* grids, const whv_params* params,
-                                   const std::vector<TimeGridH>& tgs, const std::vector<const double*>& rf,
-                                   whv_info* infos, int* iters, BatchScratch& bs, bool varc) {
-  switch (grids[0]->dim * 10 + grids[0]->order) {
-    case 22: return batched_vc<T, 2, 2>(np, grids, params, tgs, rf, infos, iters, bs, varc);
-    case 24: return batched_vc<T, 2, 4>(np, grids, params, tgs, rf, infos, iters, bs, varc);
-    case 32: return batched_vc<T, 3, 2>(np, grids, params, tgs, rf, infos, iters, bs, varc);
-    case 34: return batched_vc<T, 3, 4>(np, grids, params, tgs, rf, infos, iters, bs, varc);
+static whv_status check_barrier(BatchCtx& c) {
+  int herr = 0;
+  B_CUDA(c.g0, cudaMemcpyAsync(&herr, c.err, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  B_CUDA(c.g0, cudaStreamSynchronize(c.st));
+  if (herr) return fail(c.g0, WHV_ERR_TIMEOUT, "batched wave solve: a grid barrier timed out");
+  return WHV_OK;
+}
+
+// all problems' scalar blocks -> host (one synchronisation)
+static whv_status fetch_all(BatchCtx& c) {
+  for (int p = 0; p < c.np; ++p) {
+    whv_grid g = c.grids[p];
+    B_CUDA(c.g0, cudaMemcpyAsync(g->scal_host, g->scal, S_NSLOTS * sizeof(double), cudaMemcpyDeviceToHost, c.st));
   }
-  return fail(grids[0], WHV_ERR_INVALID, "batched solves need 2-D or 3-D grids");
+  B_CUDA(c.g0, cudaStreamSynchronize(c.st));
+  return WHV_OK;
+}
+
+// The batched CG loop as one graph with a WHILE node, built for the A p role `ap`.
+struct CgGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t body_launches = 0;
+  ~CgGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+static whv_status build_cg_graph(BatchCtx& c, const Wave& ap, CgGraph* G) {
+  B_CUDA(c.g0, cudaGraphCreate(&G->graph, 0));
+  cudaGraphConditionalHandle h;
+  B_CUDA(c.g0, cudaGraphConditionalHandleCreate(&h, G->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h;
+  prm.conditional.type = cudaGraphCondTypeWhile;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  B_CUDA(c.g0, cudaGraphAddNode(&node, G->graph, nullptr, nullptr, 0, &prm));
+  cudaGraph_t body = prm.conditional.phGraph_out[0];
+  B_CUDA(c.g0, cudaStreamBeginCaptureToGraph(c.st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const int64_t l0 = whv_kernel_launches();
+  whv_status s = WHV_OK;
+  cudaError_t e = ap.launch(c.st, ap, c.bar, c.err);
+  if (e == cudaSuccess) {
+    k_batch_finish<<<c.np, 256, 0, c.st>>>(ap.fin);
+    e = cudaGetLastError();
+  }
+  for (int p = 0; p < c.np && e == cudaSuccess && s == WHV_OK; ++p) {
+    s = cg_update(c.grids[p]);
+    if (s == WHV_OK) s = cg_direction(c.grids[p]);
+  }
+  if (e == cudaSuccess && s == WHV_OK) {
+    k_batch_check<<<(c.np + 127) / 128, 128, 0, c.st>>>(c.scal, c.np);
+    k_batch_any<<<1, 1, 0, c.st>>>(h, c.scal, c.np, c.err);
+    e = cudaGetLastError();
+  }
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(c.st, &captured);
+  G->body_launches = (whv_kernel_launches() - l0) + 4;   // + wave, finish, check, any
+  count_launches(-(whv_kernel_launches() - l0));
+  if (s != WHV_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(c.g0, e, "batched loop body");
+  if (e2 != cudaSuccess) return cuda_fail(c.g0, e2, "cudaStreamEndCapture (batched loop)");
+  B_CUDA(c.g0, cudaGraphInstantiate(&G->exec, G->graph, 0));
+  return WHV_OK;
+}
+
+// The batched CG loop on A x = rhs_p for the problems with active[p]: x = 0, r = p = rhs, stop
+// once r^T M r <= stop[p] or after maxit[p] iterations.  iters[p] receives the iterations; the
+// final r^T M r and the breakdown flag stay in the grids' scalar blocks (host mirrors fetched).
+static whv_status run_cg(BatchCtx& c, CgGraph& G, const std::vector<const double*>& rhs,
+                         const std::vector<double>& rr, const std::vector<double>& stop,
+                         const std::vector<int>& maxit, const std::vector<char>& active, std::vector<int>* iters) {
+  for (int p = 0; p < c.np; ++p) {
+    whv_grid g = c.grids[p];
+    double* sc = g->scal_host;
+    sc[S_RR] = rr[p];
+    sc[S_RR0] = rr[p];
+    sc[S_FLAG] = 0.0;
+    sc[S_ITER] = 0.0;
+    sc[S_STOP] = stop[p];
+    sc[S_MAXIT] = (double)maxit[p];
+    sc[S_HALT] = (!active[p] || rr[p] == 0.0 || maxit[p] <= 0 || rr[p] <= stop[p]) ? 1.0 : 0.0;
+    B_CUDA(c.g0, cudaMemsetAsync(g->x, 0, g->N * sizeof(double), c.st));
+    if (active[p]) {
+      B_CUDA(c.g0, cudaMemcpyAsync(g->r, rhs[p], g->N * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+      B_CUDA(c.g0, cudaMemcpyAsync(g->p, rhs[p], g->N * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+    }
+    B_CUDA(c.g0, cudaMemcpyAsync(g->scal, sc, S_NSLOTS * sizeof(double), cudaMemcpyHostToDevice, c.st));
+  }
+  B_CUDA(c.g0, cudaGraphLaunch(G.exec, c.st));
+  TRY(check_barrier(c));
+  TRY(fetch_all(c));
+  int max_it = 0;
+  for (int p = 0; p < c.np; ++p) {
+    const int it = (int)c.grids[p]->scal_host[S_ITER];
+    (*iters)[p] = it;
+    max_it = std::max(max_it, it);
+  }
+  c.launches += G.body_launches * max_it;
+  return WHV_OK;
+}
+
+template <int DIM, int ORDER, bool VARC>
+static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double* const* u_dev, bool refine,
+                                whv_info* infos) {
+  const int np = c.np;
+  const bool g64 = c.g0->precision == WHV_FP64;
+  std::vector<int> iters(np, 0), total_its(np, 0), outer(np, 0), ws(np, 0), ws64(np, 0);
+  std::vector<double> rel(np, 0.0), true_rel(np, -1.0);
+  std::vector<char> conv(np, 0), active(np, 1), flag(np, 0);
+
+  // the A p role of the CG loop, in the grids' stepping precision
+  RoleIO io_ap;
+  io_ap.v = c.each([](whv_grid g) { return (const double*)g->p; });
+  io_ap.f.assign(np, nullptr);
+  io_ap.out = c.each([](whv_grid g) { return g->q; });
+  io_ap.epi = 1;
+  io_ap.halt = true;
+  Wave ap;
+  TRY(g64 ? (make_wave<double, DIM, ORDER, VARC>(c, io_ap, &ap)) : (make_wave<float, DIM, ORDER, VARC>(c, io_ap, &ap)));
+  CgGraph G;
+  TRY(build_cg_graph(c, ap, &G));
+  std::vector<int> maxit(np);
+  for (int p = 0; p < np; ++p) maxit[p] = c.params[p].maxit;
+
+  if (!refine) {
+    // DEVD (Algorithm 2): deflate each forcing, b = Pi_h(0; f_d) of all problems in one launch
+    std::vector<const double*> fd(np);
+    for (int p = 0; p < np; ++p) {
+      whv_grid g = c.grids[p];
+      const Basis& B = g->basis;
+      fd[p] = f_dev[p];
+      if (B.nd > 0) {
+        TRY(project(g, B.V, B.nd, f_dev[p], B.d_coef));
+        TRY(copy_dev(g, g->fd, f_dev[p], g->N));
+        TRY(expand(g, B.V, B.nd, B.d_coef, -1.0, g->fd));
+        fd[p] = g->fd;
+      }
+    }
+    RoleIO io_b;
+    io_b.v.assign(np, nullptr);
+    io_b.f = fd;
+    io_b.out = c.each([](whv_grid g) { return g->t; });
+    Wave wb;
+    TRY(g64 ? (make_wave<double, DIM, ORDER, VARC>(c, io_b, &wb)) : (make_wave<float, DIM, ORDER, VARC>(c, io_b, &wb)));
+    TRY(run_wave(c, wb));
+    TRY(check_barrier(c));
+    for (int p = 0; p < np; ++p) TRY(dot_async(c.grids[p], c.grids[p]->t, c.grids[p]->t, S_TMP));
+    TRY(fetch_all(c));
+    std::vector<double> bb(np), stop(np);
+    for (int p = 0; p < np; ++p) {
+      bb[p] = c.grids[p]->scal_host[S_TMP];
+      if (!isfinite(bb[p])) return fail(c.g0, WHV_ERR_BREAKDOWN, "batched: non-finite right-hand side");
+      stop[p] = c.params[p].tol * c.params[p].tol * bb[p];
+    }
+    const std::vector<const double*> rhs = c.each([](whv_grid g) { return (const double*)g->t; });
+    TRY(run_cg(c, G, rhs, bb, stop, maxit, active, &iters));
+    for (int p = 0; p < np; ++p) {
+      whv_grid g = c.grids[p];
+      const Basis& B = g->basis;
+      total_its[p] = iters[p];
+      ws[p] = iters[p] + 1;
+      rel[p] = bb[p] > 0 ? sqrt(g->scal_host[S_RR] / bb[p]) : 0.0;
+      flag[p] = g->scal_host[S_FLAG] != 0.0;
+      conv[p] = !flag[p] && rel[p] <= c.params[p].tol;
+      if (B.nd > 0) {   // inflate: u = x + W diag(1/(omega_eff^2 - lambda^2)) W^T M f
+        std::vector<double> cf(B.nd);
+        TRY(to_host(g, cf.data(), B.d_coef, B.nd));
+        const double om2 = c.tgs[p].omega_eff * c.tgs[p].omega_eff;
+        for (int m = 0; m < B.nd; ++m) cf[m] /= (om2 - B.lambda2[m]);
+        TRY(to_dev(g, g->small, cf.data(), B.nd));
+        TRY(expand(g, B.V, B.nd, g->small, 1.0, g->x));
+      }
+      TRY(copy_dev(g, u_dev[p], g->x, g->N));
+    }
+  } else {
+    // FP64 residual correction on the full system A u = b, b = Pi_h(0; f) in FP64
+    for (int p = 0; p < np; ++p) TRY(ensure_fp64_buffers(c.grids[p]));
+    RoleIO io_b;
+    io_b.v.assign(np, nullptr);
+    io_b.f.assign(f_dev, f_dev + np);
+    io_b.out = c.each([](whv_grid g) { return g->bo; });
+    Wave wb;
+    TRY((make_wave<double, DIM, ORDER, VARC>(c, io_b, &wb)));
+    RoleIO io_ax;   // q = A x in FP64
+    io_ax.v = c.each([](whv_grid g) { return (const double*)g->xo; });
+    io_ax.f.assign(np, nullptr);
+    io_ax.out = c.each([](whv_grid g) { return g->q; });
+    io_ax.epi = 1;
+    io_ax.halt = true;
+    Wave wax;
+    TRY((make_wave<double, DIM, ORDER, VARC>(c, io_ax, &wax)));
+    TRY(run_wave(c, wb));
+    TRY(check_barrier(c));
+    for (int p = 0; p < np; ++p) {
+      whv_grid g = c.grids[p];
+      ws64[p] = 1;
+      TRY(dot_async(g, g->bo, g->bo, S_TMP2));
+      B_CUDA(c.g0, cudaMemsetAsync(g->xo, 0, g->N * sizeof(double), c.st));
+      TRY(copy_dev(g, g->ro, g->bo, g->N));
+    }
+    TRY(fetch_all(c));
+    std::vector<double> bb(np), rr(np, 0.0), stop(np, 0.0);
+    for (int p = 0; p < np; ++p) {
+      bb[p] = c.grids[p]->scal_host[S_TMP2];
+      if (!isfinite(bb[p])) return fail(c.g0, WHV_ERR_BREAKDOWN, "batched: non-finite right-hand side");
+    }
+    const std::vector<const double*> rhs = c.each([](whv_grid g) { return (const double*)g->ro; });
+    for (int pass = 0;; ++pass) {
+      if (pass > 0) {   // r = b - A x in FP64 for the problems still running
+        for (int p = 0; p < np; ++p) {
+          whv_grid g = c.grids[p];
+          g->scal_host[S_HALT] = active[p] ? 0.0 : 1.0;
+          B_CUDA(c.g0, cudaMemcpyAsync(g->scal + S_HALT, g->scal_host + S_HALT, sizeof(double),
+                                       cudaMemcpyHostToDevice, c.st));
+        }
+        TRY(run_wave(c, wax));
+        TRY(check_barrier(c));
+        for (int p = 0; p < np; ++p) {
+          if (!active[p]) continue;
+          whv_grid g = c.grids[p];
+          ++ws64[p];
+          TRY(copy_dev(g, g->ro, g->bo, g->N));
+          TRY(axpby(g, g->N, -1.0, g->q, 1.0, g->ro));
+        }
+      }
+      for (int p = 0; p < np; ++p)
+        if (active[p]) TRY(dot_async(c.grids[p], c.grids[p]->ro, c.grids[p]->ro, S_TMP2));
+      TRY(fetch_all(c));
+      bool any = false;
+      for (int p = 0; p < np; ++p) {
+        if (!active[p]) continue;
+        const double r2 = c.grids[p]->scal_host[S_TMP2];
+        rel[p] = bb[p] > 0 ? sqrt(r2 / bb[p]) : 0.0;
+        true_rel[p] = rel[p];
+        if (!isfinite(rel[p])) { flag[p] = 1; active[p] = 0; continue; }
+        if (rel[p] <= c.params[p].tol) { conv[p] = 1; active[p] = 0; continue; }
+        if (total_its[p] >= c.params[p].maxit || pass >= 50) { active[p] = 0; continue; }
+        any = true;
+      }
+      if (!any) break;
+      // deflated components (exact eigenvectors): x += W diag(1/mu) c, r -= W c, c = W^T M r
+      for (int p = 0; p < np; ++p) {
+        whv_grid g = c.grids[p];
+        const Basis& B = g->basis;
+        if (!active[p] || B.nd == 0) continue;
+        std::vector<double> cf(B.nd), y(B.nd);
+        TRY(project(g, B.V, B.nd, g->ro, g->small));
+        TRY(to_host(g, cf.data(), g->small, B.nd));
+        for (int m = 0; m < B.nd; ++m) y[m] = cf[m] / B.mu[m];
+        TRY(to_dev(g, g->small, y.data(), B.nd));
+        TRY(expand(g, B.V, B.nd, g->small, 1.0, g->xo));
+        TRY(to_dev(g, g->small, cf.data(), B.nd));
+        TRY(expand(g, B.V, B.nd, g->small, -1.0, g->ro));
+      }
+      for (int p = 0; p < np; ++p)
+        if (active[p]) TRY(dot_async(c.grids[p], c.grids[p]->ro, c.grids[p]->ro, S_TMP2));
+      TRY(fetch_all(c));
+      std::vector<int> mx(np, 0);
+      for (int p = 0; p < np; ++p) {
+        if (!active[p]) continue;
+        const whv_params& P = c.params[p];
+        rr[p] = c.grids[p]->scal_host[S_TMP2];
+        // inner tolerance: the requested fraction, but no tighter than the outer target needs
+        const double itol = std::max(P.inner_tol > 0.0 ? P.inner_tol : 1e-3, 0.5 * P.tol / std::max(rel[p], 1e-300));
+        stop[p] = itol * itol * rr[p];
+        mx[p] = P.maxit - total_its[p];
+      }
+      TRY(run_cg(c, G, rhs, rr, stop, mx, active, &iters));
+      for (int p = 0; p < np; ++p) {
+        if (!active[p]) continue;
+        whv_grid g = c.grids[p];
+        total_its[p] += iters[p];
+        ws[p] += iters[p];
+        ++outer[p];
+        TRY(axpby(g, g->N, 1.0, g->x, 1.0, g->xo));
+        if (g->scal_host[S_FLAG] != 0.0) { flag[p] = 1; active[p] = 0; }
+      }
+    }
+    for (int p = 0; p < np; ++p) TRY(copy_dev(c.grids[p], u_dev[p], c.grids[p]->xo, c.grids[p]->N));
+  }
+  // leave the grids usable by non-batched calls
+  for (int p = 0; p < np; ++p) {
+    whv_grid g = c.grids[p];
+    g->scal_host[S_HALT] = 0.0;
+    B_CUDA(c.g0, cudaMemcpyAsync(g->scal + S_HALT, g->scal_host + S_HALT, sizeof(double), cudaMemcpyHostToDevice, c.st));
+  }
+  B_CUDA(c.g0, cudaStreamSynchronize(c.st));
+  count_launches(c.launches);
+  bool all = true;
+  for (int p = 0; p < np; ++p) {
+    all = all && conv[p];
+    if (!infos) continue;
+    whv_info& I = infos[p];
+    I.iterations = total_its[p];
+    I.wave_solves = ws[p] + ws64[p];
+    I.wave_solves_fp64 = g64 ? ws[p] + ws64[p] : ws64[p];
+    I.outer_iterations = outer[p];
+    I.rel_residual = rel[p];
+    I.true_rel_residual = true_rel[p];
+    I.nt = c.tgs[p].nt;
+    I.dt = c.tgs[p].dt;
+    I.omega_hat = c.tgs[p].omega_hat;
+    I.omega_eff = c.tgs[p].omega_eff;
+    I.seconds = 0.0;
+  }
+  for (int p = 0; p < np; ++p)
+    if (flag[p]) return fail(c.g0, WHV_ERR_BREAKDOWN, "whv_solve_batched: Krylov breakdown in a problem");
+  if (!all) return fail(c.g0, WHV_ERR_NOT_CONVERGED, "whv_solve_batched: some problems did not reach tol");
+  return WHV_OK;
+}
+
+template <int DIM, int ORDER>
+static whv_status batched_vc(BatchCtx& c, const double* const* f, double* const* u, bool refine, whv_info* infos,
+                             bool varc) {
+  return varc ? batched_solve<DIM, ORDER, true>(c, f, u, refine, infos)
+              : batched_solve<DIM, ORDER, false>(c, f, u, refine, infos);
 }
 
 }  // namespace whv
@@ -432,13 +968,19 @@ using namespace whv;
 
 extern "C" whv_status whv_solve_batched(int nprob, const whv_grid* grids, const whv_params* params,
                                         const double* const* f_dev, double* const* u_dev, whv_info* infos) {
+  const double t0 = now_s();
   if (nprob < 1 || nprob > kBatchMaxProblems || !grids || !params || !f_dev || !u_dev)
     return fail(nullptr, WHV_ERR_INVALID, "whv_solve_batched: bad arguments (1 <= nprob <= 1024)");
   whv_grid g0 = grids[0];
   if (!g0) return fail(nullptr, WHV_ERR_INVALID, "whv_solve_batched: NULL grid");
   const bool varc = g0->c2 != nullptr;
-  std::vector<TimeGridH> tgs(nprob);
-  std::vector<const double*> rf(nprob);
+  const bool refine = (params[0].flags & WHV_REFINE_FP64) != 0;
+  BatchCtx c;
+  c.np = nprob;
+  c.grids = grids;
+  c.params = params;
+  c.g0 = g0;
+  c.tgs.resize(nprob);
   for (int p = 0; p < nprob; ++p) {
     whv_grid g = grids[p];
     if (!g || !f_dev[p] || !u_dev[p]) return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: NULL grid or buffer");
@@ -449,76 +991,47 @@ extern "C" whv_status whv_solve_batched(int nprob, const whv_grid* grids, const 
       return fail(g0, WHV_ERR_INVALID,
                   "whv_solve_batched: grids must share stream, precision, dimension, order and speed kind");
     if (params[p].method != WHV_CG) return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: method must be WHV_CG");
-    whv_status s = make_time_grid(g, &params[p], &tgs[p]);
+    if (((params[p].flags & WHV_REFINE_FP64) != 0) != refine)
+      return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: WHV_REFINE_FP64 must be set for all problems or none");
+    if (!(params[p].tol >= 0.0) || params[p].maxit < 0)
+      return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: tol must be >= 0, maxit >= 0");
+    whv_status s = make_time_grid(g, &params[p], &c.tgs[p]);
     if (s != WHV_OK) return fail(g0, s, std::string("whv_solve_batched: ") + g->err);
     const Basis& B = g->basis;
     if (B.nd > 0) {
       if (!(B.flags & WHV_BASIS_EXACT) || (B.flags & WHV_BASIS_REDEFLATE))
         return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: bases must be exact eigenvectors (DEVD)");
-      if (B.omega != params[p].omega || B.periods != params[p].periods || B.cfl != tgs[p].cfl ||
+      if (B.omega != params[p].omega || B.periods != params[p].periods || B.cfl != c.tgs[p].cfl ||
           B.adjust != (params[p].adjust_omega ? 1 : 0))
         return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: a basis was set for another frequency / time grid");
     }
   }
-  // DEVD (Algorithm 2): deflate each forcing
-  for (int p = 0; p < nprob; ++p) {
-    whv_grid g = grids[p];
-    const Basis& B = g->basis;
-    rf[p] = f_dev[p];
-    if (B.nd > 0) {
-      whv_status s = project(g, B.V, B.nd, f_dev[p], B.d_coef);
-      if (s == WHV_OK && cudaMemcpyAsync(g->fd, f_dev[p], g->N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
-        s = fail(g0, WHV_ERR_CUDA, "copy");
-      if (s == WHV_OK) s = expand(g, B.V, B.nd, B.d_coef, -1.0, g->fd);
-      if (s != WHV_OK) return s;
-      rf[p] = g->fd;
-    }
+  if (g0->dim < 2) return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: batched solves need 2-D or 3-D grids");
+  batch_init();
+  c.st = g0->stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
+  B_CUDA(g0, c.alloc(&c.bar, 2 * sizeof(unsigned)));
+  B_CUDA(g0, c.alloc(&c.err, sizeof(int)));
+  B_CUDA(g0, c.alloc(&c.scal, nprob * sizeof(double*)));
+  {
+    std::vector<double*> sc(nprob);
+    for (int p = 0; p < nprob; ++p) sc[p] = grids[p]->scal;
+    B_CUDA(g0, cudaMemcpy(c.scal, sc.data(), nprob * sizeof(double*), cudaMemcpyHostToDevice));
   }
-  std::vector<int> iters(nprob, 0);
-  BatchScratch bs;
-  whv_status s = g0->precision == WHV_FP64 ? batched_dispatch<double>(nprob, grids, params, tgs, rf, infos, iters.data(), bs, varc)
-                                           : batched_dispatch<float>(nprob, grids, params, tgs, rf, infos, iters.data(), bs, varc);
-  cudaStreamSynchronize(g0->stream);
-  bs.free_all();
-  if (s != WHV_OK) return s;
-  // inflate and write the solutions
-  bool all_conv = true;
-  for (int p = 0; p < nprob; ++p) {
-    whv_grid g = grids[p];
-    const Basis& B = g->basis;
-    if (B.nd > 0) {
-      std::vector<double> cf(B.nd);
-      if (cudaMemcpy(cf.data(), B.d_coef, B.nd * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return fail(g0, WHV_ERR_CUDA, "copy");
-      const double om2 = tgs[p].omega_eff * tgs[p].omega_eff;
-      for (int m = 0; m < B.nd; ++m) cf[m] /= (om2 - B.lambda2[m]);
-      if (cudaMemcpy(g->small, cf.data(), B.nd * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
-        return fail(g0, WHV_ERR_CUDA, "copy");
-      s = expand(g, B.V, B.nd, g->small, 1.0, g->x);
-      if (s != WHV_OK) return s;
-    }
-    if (cudaMemcpyAsync(u_dev[p], g->x, g->N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
-      return fail(g0, WHV_ERR_CUDA, "copy");
-    s = fetch_scalars(g);
-    if (s != WHV_OK) return s;
-    const double rel = g->scal_host[S_RR0] > 0 ? sqrt(g->scal_host[S_RR] / g->scal_host[S_RR0]) : 0.0;
-    if (!(rel <= params[p].tol)) all_conv = false;
-    if (g->scal_host[S_FLAG] != 0.0) all_conv = false;
-    if (infos) {
-      infos[p].nt = tgs[p].nt;
-      infos[p].dt = tgs[p].dt;
-      infos[p].omega_hat = tgs[p].omega_hat;
-      infos[p].omega_eff = tgs[p].omega_eff;
-      infos[p].true_rel_residual = -1.0;
-      infos[p].seconds = 0.0;
-      infos[p].outer_iterations = 0;
-      infos[p].wave_solves_fp64 = g->precision == WHV_FP64 ? iters[p] + 1 : 0;
-    }
-    // leave the grid usable by non-batched calls
-    double zero = 0.0;
-    cudaMemcpy(g->scal + S_HALT, &zero, sizeof(double), cudaMemcpyHostToDevice);
+  B_CUDA(g0, cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), c.st));
+  B_CUDA(g0, cudaMemsetAsync(c.err, 0, sizeof(int), c.st));
+  whv_status s;
+  switch (g0->dim * 10 + g0->order) {
+    case 22: s = batched_vc<2, 2>(c, f_dev, u_dev, refine, infos, varc); break;
+    case 24: s = batched_vc<2, 4>(c, f_dev, u_dev, refine, infos, varc); break;
+    case 32: s = batched_vc<3, 2>(c, f_dev, u_dev, refine, infos, varc); break;
+    default: s = batched_vc<3, 4>(c, f_dev, u_dev, refine, infos, varc); break;
   }
-  cudaStreamSynchronize(g0->stream);
-  if (!all_conv) return fail(g0, WHV_ERR_NOT_CONVERGED, "whv_solve_batched: some problems did not reach tol");
-  return WHV_OK;
+  if (infos) {
+    const double secs = now_s() - t0;
+    for (int p = 0; p < nprob; ++p) infos[p].seconds = secs;
+  }
+  return s;
 }

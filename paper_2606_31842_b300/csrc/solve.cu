@@ -39,30 +39,6 @@ struct SolveCtx {
   int ws64 = 0;    // FP64 wave solves of the residual correction
 };
 
-static whv_status copy_dev(whv_grid g, double* dst, const double* src, int64_t n) {
-  WHV_CUDA(g, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
-  return WHV_OK;
-}
-
-static whv_status to_host(whv_grid g, double* dst, const double* src, int n) {
-  WHV_CUDA(g, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
-  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
-  return WHV_OK;
-}
-
-static whv_status to_dev(whv_grid g, double* dst, const double* src, int n) {
-  WHV_CUDA(g, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, g->stream));
-  // src is pageable host memory that may be reused right after: wait for the copy
-  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
-  return WHV_OK;
-}
-
-#define TRY(expr)                          \
-  do {                                     \
-    whv_status _s = (expr);                \
-    if (_s != WHV_OK) return _s;           \
-  } while (0)
-
 // out = out - W (W^T M out)
 static whv_status deflate_vec(whv_grid g, double* vec) {
   const Basis& B = g->basis;
@@ -86,10 +62,6 @@ static whv_status apply_A(SolveCtx& c, const double* v, double* q) {
 static bool log_on() {
   static const bool on = [] { const char* e = getenv("WHV_LOG"); return e && e[0] == '1'; }();
   return on;
-}
-
-static double now_s() {
-  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
 // ------------------------------------------------------------------ general deflation (Algorithm 4)

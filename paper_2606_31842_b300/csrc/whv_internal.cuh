@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -126,6 +127,32 @@ whv_status cuda_fail(whv_grid g, cudaError_t e, const char* what);
     cudaError_t _e = (call);                                \
     if (_e != cudaSuccess) return whv::cuda_fail(g, _e, #call); \
   } while (0)
+
+#define TRY(expr)                          \
+  do {                                     \
+    whv_status _s = (expr);                \
+    if (_s != WHV_OK) return _s;           \
+  } while (0)
+
+// stream-ordered copies on the grid's stream; the host ones synchronise (pageable host memory)
+inline whv_status copy_dev(whv_grid g, double* dst, const double* src, int64_t n) {
+  WHV_CUDA(g, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+  return WHV_OK;
+}
+inline whv_status to_host(whv_grid g, double* dst, const double* src, int n) {
+  WHV_CUDA(g, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
+  return WHV_OK;
+}
+inline whv_status to_dev(whv_grid g, double* dst, const double* src, int n) {
+  WHV_CUDA(g, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+  // src is pageable host memory that may be reused right after: wait for the copy
+  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
+  return WHV_OK;
+}
+inline double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 whv_status make_time_grid(whv_grid g, const whv_params* p, TimeGridH* tg);
 void free_basis(whv_grid g);   // frees the deflation basis (and what depends on it)

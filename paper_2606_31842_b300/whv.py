@@ -150,6 +150,7 @@ def whv_solve_batched(grids, params, fs, us=None, raise_not_converged=False):
     allow = () if raise_not_converged else (WHV_ERR_NOT_CONVERGED,)
     grids[0]._pre()
     st = _check(lib.whv_solve_batched(n, G, Pm, F, U, infos), grids[0].handle, allow)
+    grids[0]._post()
     return us, [dict(i.as_dict(), status=STATUS_NAMES[st]) for i in infos]
 
 

@@ -85,3 +85,98 @@ def test_batched_rejects_mixed_grids():
         whv.whv_solve_batched([g1, g2], [prm, prm], [f, f])
     with pytest.raises(whv.WhvError):
         whv.whv_solve_batched([g1, g1], [prm, prm], [f, f])
+
+
+@pytest.mark.parametrize("k", [1, 3, 8, 16])
+def test_batched_blocked_sweeps_fp64(k):
+    """2-D batched wave solves with k steps per sweep, on problems whose Nt is not a multiple of k
+    (and one with Nt < 16): fixed-iteration DEVD-CG iterates equal the oracle's."""
+    spec = [(33, 9.0), (47, 14.0), (17, 40.0), (29, 11.0)]
+    stream = torch.cuda.Stream()
+    grids, params, fs, probs = [], [], [], []
+    it = 5
+    for n, om in spec:
+        npts = (n, n)
+        f = I.gaussian(npts, I.source_centers(n, 1, 2)[0], 0.12, om ** 2)
+        g = whv.Grid(npts, precision=whv.WHV_FP64, stream=stream)
+        prm = whv.make_params(om, method="cg", tol=0.0, maxit=it)
+        g.whv_set_deflation_basis(prm, 4, whv.WHV_BASIS_CLOSED_FORM)
+        grids.append(g); params.append(prm); fs.append(dev(f)); probs.append((npts, om, f))
+    grids[0].whv_set_steps_per_sweep(k)   # the batch takes its sweep length from the first grid
+    us, infos = whv.whv_solve_batched(grids, params, fs)
+    nts = []
+    for (npts, om, f), u, info in zip(probs, us, infos):
+        og = O.Grid(npts)
+        tg = WH.time_grid_for(og, om)
+        nts.append(tg.nt)
+        modes, lam2, _ = SP.select_modes(og, tg, 4)
+        ref = K.devd_solve(og, tg, f, SP.basis(og, modes), lam2, "cg", 0.0, it).u
+        assert info["iterations"] == it and info["nt"] == tg.nt
+        assert IND.relmax(u.cpu().numpy(), ref) < 1e-12
+    assert min(nts) < 16 and any(nt % k for nt in nts) or k == 1
+
+
+def test_batched_variable_speed_order4_fixed_iterations():
+    """Variable speed (c^2 Delta_h, M = diag(1/c^2) inner products) with the 9-point-wide
+    4th-order stencil, no basis, FP64: batched CG iterates equal the oracle's."""
+    spec = [((33, 29), 14.0, 5), ((41, 37), 18.0, 6), ((25, 31), 10.0, 7)]
+    stream = torch.cuda.Stream()
+    grids, params, fs, refs = [], [], [], []
+    it = 6
+    for npts, om, seed in spec:
+        c2 = I.speed_squared("c3", npts, seed)
+        f = I.gaussian(npts, [0.4, 0.55], 0.1, om ** 2)
+        g = whv.Grid(npts, order=4, precision=whv.WHV_FP64, stream=stream)
+        g.whv_set_speed(dev(c2))
+        grids.append(g); params.append(whv.make_params(om, method="cg", tol=0.0, maxit=it)); fs.append(dev(f))
+        og = O.Grid(npts, order=4, c2=c2)
+        tg = WH.time_grid_for(og, om)
+        refs.append(K.devd_solve(og, tg, f, None, None, "cg", 0.0, it).u)
+    us, infos = whv.whv_solve_batched(grids, params, fs)
+    for u, ref, info in zip(us, refs, infos):
+        assert info["iterations"] == it
+        assert IND.relmax(u.cpu().numpy(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_batched_fp32_with_fp64_correction(dim):
+    """FP32 stepping inside FP64 residual correction: every problem's FP64 residual of the full
+    system meets tol (recomputed here on separate FP64 grids), and the solutions match the
+    oracle's converged ones within the residual bound times the conditioning."""
+    if dim == 2:
+        probs = _problems((65, 97, 129), (12.0, 18.0), 2, 8)
+    else:
+        probs = _problems((17, 13), (7.0, 9.0), 1, 6, dim=3)
+    tol = 1e-10
+    stream = torch.cuda.Stream()
+    grids, params, fs = [], [], []
+    for npts, om, f, nd in probs:
+        g = whv.Grid(npts, precision=whv.WHV_FP32_STEP, stream=stream)
+        prm = whv.make_params(om, method="cg", tol=tol, maxit=3000, refine_fp64=True)
+        g.whv_set_deflation_basis(prm, nd, whv.WHV_BASIS_CLOSED_FORM)
+        grids.append(g); params.append(prm); fs.append(dev(f))
+    us, infos = whv.whv_solve_batched(grids, params, fs)
+    assert all(i["status"] == "OK" for i in infos), infos
+    assert max(i["outer_iterations"] for i in infos) >= 2
+    for (npts, om, f, nd), u, info, prm in zip(probs, us, infos, params):
+        assert 0 <= info["true_rel_residual"] <= tol
+        assert info["wave_solves_fp64"] == info["outer_iterations"] + 1
+        g64 = whv.Grid(npts, precision=whv.WHV_FP64, stream=stream)
+        r = g64.whv_apply_pi(prm, u, dev(f))
+        b = g64.whv_apply_pi(prm, torch.zeros_like(u), dev(f))
+        assert float((r - u).norm() / b.norm()) <= 1.01 * tol
+        og = O.Grid(npts)
+        tg = WH.time_grid_for(og, om)
+        U = IND.helmholtz_direct(npts, tg.omega_eff, f)
+        assert IND.relmax(u.cpu().numpy(), U) < 1e-7
+
+
+def test_batched_refine_flag_must_agree():
+    s = torch.cuda.Stream()
+    g1 = whv.Grid((33, 33), precision=whv.WHV_FP32_STEP, stream=s)
+    g2 = whv.Grid((33, 33), precision=whv.WHV_FP32_STEP, stream=s)
+    p1 = whv.make_params(8.0, method="cg", tol=1e-6, refine_fp64=True)
+    p2 = whv.make_params(8.0, method="cg", tol=1e-6)
+    f = dev(np.ones(g1.N))
+    with pytest.raises(whv.WhvError):
+        whv.whv_solve_batched([g1, g2], [p1, p2], [f, f])

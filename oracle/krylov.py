@@ -9,6 +9,11 @@ A = I - S_h is self-adjoint (see operators.py).
                corrected: r2 = r_0^T r_0 and r_{k+1} = r_k - alpha_k q_k.
 * gmres        restarted GMRES(m) with classical Gram-Schmidt applied twice and Givens
                rotations (the unaugmented base of Algorithm 5).
+* agmres       Algorithm 5 (augmented GMRES of Baglama and Reichel with Givens rotations):
+               the search space is span(W) + the Krylov space of A started from the part of
+               b_0 outside range(A W); restarted after m Arnoldi steps, keeping the QR factors
+               of A W.
+* augmented_solve  A u = b (b = Pi_h(0; f), undeflated forcing) by agmres with the basis W.
 * devd_solve   Algorithm 2 (direct eigenvector deflation): deflate the forcing, solve with
                FPI / CG / GMRES, optionally re-deflate each operator output, inflate.
 
@@ -214,6 +219,130 @@ def gmres(grid, A, b, tol, maxit, restart=30, x0=None):
             hist.append(abs(g[k]) / bnorm)
             return SolveResult(x.reshape(shape), its, 0, True, hist)
         r = bf - A(x.reshape(shape)).ravel()
+
+
+def agmres(grid, A, b, W, tol, maxit, restart=30, x0=None, AW=None):
+    """Algorithm 5, restarted after `restart` Arnoldi steps.  W: n x p augmentation vectors
+    (columns); AW: A W if known (A W = W diag(mu) for exact eigenvectors), else formed with p
+    applications of A.  Per cycle, in the notation of Algorithm 5 (inner products <.,.>_M):
+        b_0 = b - A x_0
+        A W = V_{1:p} H_{1:p,1:p}              thin QR (classical Gram-Schmidt, twice)
+        v_{p+1} = (I - V_p V_p^T M) b_0 / ||.||
+        g_k = <v_k, b_0>,  k = 1 .. p+1
+        Arnoldi from v_{p+1}: v_{k+1} = A v_k made orthogonal to v_1 .. v_k (twice), h_{k+1,k}
+        Givens rotations on columns k > p (the first p columns are already triangular)
+        |g_{k+1}| = residual norm;  stop when |g_{k+1}| <= tol ||b||
+        H_{1:k,1:k} y = g_{1:k};  x = x_0 + [W | V_{p+1:k}] y
+    The QR factors of A W are computed once and kept over restarts.  `maxit` bounds the Arnoldi
+    steps.  SolveResult.wave_solves counts the applications of A made here."""
+    shape = grid.shape
+    wts = grid.weights().ravel()
+    ip = lambda u, v: float(np.sum(wts * u * v))  # noqa: E731
+    bf = np.asarray(b, dtype=np.float64).ravel()
+    W = np.zeros((bf.size, 0)) if W is None else np.asarray(W, dtype=np.float64).reshape(bf.size, -1)
+    p = W.shape[1]
+    m = restart
+    nA = 0
+    if AW is None:
+        AW = np.zeros_like(W)
+        for j in range(p):
+            AW[:, j] = A(W[:, j].reshape(shape)).ravel()
+            nA += 1
+    else:
+        AW = np.asarray(AW, dtype=np.float64).reshape(bf.size, p)
+    # A W = V_{1:p} H_{1:p,1:p}
+    Vp = []
+    Hp = np.zeros((p, p))
+    for j in range(p):
+        w = AW[:, j].copy()
+        for _ in range(2):
+            h = np.array([ip(vi, w) for vi in Vp])
+            if len(Vp):
+                w = w - sum(hi * vi for hi, vi in zip(h, Vp))
+                Hp[:j, j] += h
+        Hp[j, j] = math.sqrt(ip(w, w))
+        Vp.append(w / Hp[j, j])
+    x = np.zeros(bf.size) if x0 is None else np.asarray(x0, dtype=np.float64).ravel().copy()
+    bnorm = math.sqrt(ip(bf, bf))
+    b0 = bf.copy()
+    if x0 is not None:
+        b0 = bf - A(x.reshape(shape)).ravel()
+        nA += 1
+    its = 0
+    hist = []
+    cycle = 0
+    while True:
+        beta0 = math.sqrt(ip(b0, b0))
+        hist.append(beta0 / bnorm)
+        # (the first cycle always runs: with maxit = 0 it is the least-squares fit over span(W))
+        if beta0 / bnorm <= tol or (cycle > 0 and its >= maxit):
+            return SolveResult(x.reshape(shape), its, nA, beta0 / bnorm <= tol, hist)
+        cycle += 1
+        v = b0.copy()
+        for _ in range(2):
+            v = v - sum(ip(vi, v) * vi for vi in Vp) if p else v
+        vn = math.sqrt(ip(v, v))
+        V = list(Vp) + [v / vn if vn > 0.0 else v]
+        H = np.zeros((p + m + 1, p + m))
+        H[:p, :p] = Hp
+        g = np.zeros(p + m + 1)
+        for k in range(p + 1):
+            g[k] = ip(V[k], b0)
+        cs, sn = np.zeros(p + m), np.zeros(p + m)
+        k = p
+        breakdown = False
+        # |g_{p+1}| = ||(I - V_p V_p^T M) b_0|| is already the residual of the least-squares fit
+        # over span(W) alone: no Arnoldi step when that meets tol
+        steps = range(p, p + min(m, maxit - its)) if abs(g[p]) / bnorm > tol else range(0)
+        for j in steps:
+            w = A(V[j].reshape(shape)).ravel()
+            nA += 1
+            its += 1
+            for _ in range(2):
+                h = np.array([ip(vi, w) for vi in V])
+                w = w - sum(hi * vi for hi, vi in zip(h, V))
+                H[: j + 1, j] += h
+            H[j + 1, j] = math.sqrt(ip(w, w))
+            breakdown = H[j + 1, j] == 0.0
+            if not breakdown:
+                V.append(w / H[j + 1, j])
+            for i in range(p, j):   # previous rotations on the new column
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            k = j + 1
+            if abs(g[k]) / bnorm <= tol or its >= maxit or breakdown:
+                break
+        y = np.zeros(k)
+        for i in reversed(range(k)):
+            y[i] = (g[i] - H[i, i + 1: k] @ y[i + 1:]) / H[i, i]
+        x = x + W @ y[:p] + sum((y[i] * V[i] for i in range(p, k)), np.zeros(bf.size))
+        if abs(g[k]) / bnorm <= tol or breakdown or its >= maxit:
+            hist.append(abs(g[k]) / bnorm)
+            return SolveResult(x.reshape(shape), its, nA, abs(g[k]) / bnorm <= tol, hist)
+        b0 = bf - A(x.reshape(shape)).ravel()   # restart
+        nA += 1
+
+
+def augmented_solve(grid: Grid, tg: TimeGrid, f, W, lam2=None, tol=1e-10, maxit=1000, restart=30, x0=None):
+    """A u = b with b = Pi_h(0; f) (the forcing is not deflated) by Algorithm 5 augmented with
+    the columns of W.  With lam2 (W exact eigenvectors) A W = W diag(1 - beta_h(lambda)) costs no
+    wave solve; without, A W takes one wave solve per column."""
+    from .spectral import beta_h
+    f = np.asarray(f, dtype=np.float64).reshape(grid.shape)
+    A = Operator(grid, tg)
+    b = apply_pi(grid, tg, np.zeros(grid.shape), f)
+    AW = None
+    if lam2 is not None and W is not None:
+        AW = np.asarray(W) * (1.0 - beta_h(np.asarray(lam2), tg))[None, :]
+    res = agmres(grid, A, b, W, tol, maxit, restart, x0, AW)
+    return DevdResult(res.x, res, A.count + 1, np.zeros(0), b)
 
 
 @dataclass

@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="whv", choices=["whv", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--method", default="", choices=["", "cg", "dcg", "gmres", "agmres"],
+                    help="accelerator of the single-grid workloads (default: DCG for c1/c3, CG otherwise)")
     ap.add_argument("--sources", type=int, default=0,
                     help="batched workload: Gaussian sources per (grid, frequency) (default 16)")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
@@ -313,8 +315,8 @@ def run_workload(args):
     if w.speed:
         g.whv_set_speed(dev(I.speed_squared(w.speed, w.npts, w.speed_seed)))
     refine = prec == whv.WHV_FP32_STEP
-    method = "dcg" if name in ("c1", "c3") else "cg"
-    prm = whv.make_params(w.omega, method=method, tol=w.tol, maxit=20000, refine_fp64=refine)
+    method = args.method or ("dcg" if name in ("c1", "c3") else "cg")
+    prm = whv.make_params(w.omega, method=method, tol=w.tol, maxit=20000, restart=30, refine_fp64=refine)
     t0 = time.perf_counter()
     if name == "c3":
         theta, resid = g.whv_lanczos(prm, w.nd, 1024, None, False, 0)
@@ -334,7 +336,7 @@ def run_workload(args):
         res["info"] = g.whv_solve(prm, f, u)[1]
     ms, _ = _timed(stream, step, args.steps, args.warmup, flush if w.n_unknowns < 30_000_000 else None)
     info = res["info"]
-    prm_chk = whv.make_params(w.omega, method=method, tol=w.tol, maxit=20000, true_residual=True,
+    prm_chk = whv.make_params(w.omega, method=method, tol=w.tol, maxit=20000, restart=30, true_residual=True,
                               refine_fp64=refine)
     _, ichk = g.whv_solve(prm_chk, f, u)
     lups = info["wave_solves"] * info["nt"] * w.n_unknowns

@@ -23,7 +23,7 @@ whv_status fail(whv_grid g, whv_status s, const std::string& msg) {
 
 void free_basis(whv_grid g) {
   Basis& b = g->basis;
-  for (void* p : {(void*)b.V, (void*)b.d_coef, (void*)b.AW, (void*)b.Einv})
+  for (void* p : {(void*)b.V, (void*)b.d_coef, (void*)b.AW, (void*)b.Einv, (void*)b.QAW})
     if (p) cudaFree(p);
   g->basis = Basis();
   free_cgloop(g);
@@ -147,7 +147,7 @@ static void free_all(whv_grid g) {
   free_plan(g);
   void* ptrs[] = {g->c2, g->c2f, g->mw, g->wbuf[0], g->wbuf[1], g->wbuf[2], g->wbuf[3], g->acc, g->x, g->r, g->p, g->q,
                   g->t, g->fd, g->krylov, g->small, g->small2, g->partials, g->counters, g->scal,
-                  g->basis.V, g->basis.d_coef, g->basis.AW, g->basis.Einv, g->wbuf64[0], g->wbuf64[1], g->wbuf64[2],
+                  g->basis.V, g->basis.d_coef, g->basis.AW, g->basis.Einv, g->basis.QAW, g->wbuf64[0], g->wbuf64[1], g->wbuf64[2],
                   g->wbuf64[3], g->acc64, g->xo, g->ro, g->bo, g->wtab_small};
   for (void* p : ptrs)
     if (p) cudaFree(p);

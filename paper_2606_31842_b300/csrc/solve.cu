@@ -12,6 +12,10 @@
 //  * GMRES(m): Arnoldi with classical Gram-Schmidt applied twice on the device (the deflation
 //    contraction kernels on the Krylov basis), Givens rotations and the triangular solve on the
 //    host (m <= 30 scalars per step).
+//  * AGMRES (Algorithm 5): GMRES(m) whose least-squares space is augmented by the basis W; the
+//    thin QR A W = V_p H_p (classical Gram-Schmidt twice, M inner products) is built once per
+//    basis, each cycle projects range(A W) out of the residual, runs the Arnoldi steps
+//    orthogonally to [V_p | V_{p+1..}] and solves the triangular system over [W | V_{p+1..k}].
 //  * FPI (Algorithm 1).
 //  * FP64 residual correction (WHV_REFINE_FP64): the outer loop forms the residual r = b - A x of
 //    the full system with FP64 wave solves; the correction is the modal solve of its deflated
@@ -252,6 +256,50 @@ static whv_status dcg_project_direction(whv_grid g) {
   return expand(g, B.V, B.nd, g->small2, -1.0, g->p);
 }
 
+// Algorithm 5 set-up: A W = QAW Raw, kept with the basis.  A W = W diag(mu) for exact
+// eigenvectors, the general-DCG A W if already formed, else one wave solve per column.
+static whv_status prepare_agmres(SolveCtx& c) {
+  whv_grid g = c.g;
+  Basis& B = g->basis;
+  if (B.QAW) return WHV_OK;
+  const int64_t N = g->N;
+  const int nd = B.nd;
+  WHV_CUDA(g, cudaMalloc(&B.QAW, (size_t)nd * N * sizeof(double)));
+  std::vector<double> R((size_t)nd * nd, 0.0), h(nd);
+  for (int j = 0; j < nd; ++j) {
+    double* q = B.QAW + (size_t)j * N;
+    const double* wj = B.V + (size_t)j * N;
+    if (B.flags & WHV_BASIS_EXACT) {
+      TRY(axpby(g, N, B.mu[j], wj, 0.0, q));
+    } else if (B.AW) {
+      TRY(copy_dev(g, q, B.AW + (size_t)j * N, N));
+    } else {
+      TRY(copy_dev(g, g->p, wj, N));   // fixed buffers: every column replays one wave-solve graph
+      TRY(wave_solve(g, c.tg, g->p, nullptr, g->t, 1));
+      c.ws++;
+      TRY(copy_dev(g, q, g->t, N));
+    }
+    for (int pass = 0; pass < 2 && j > 0; ++pass) {   // classical Gram-Schmidt, twice
+      TRY(project(g, B.QAW, j, q, g->small));
+      TRY(expand(g, B.QAW, j, g->small, -1.0, q));
+      TRY(to_host(g, h.data(), g->small, j));
+      for (int i = 0; i < j; ++i) R[(size_t)j * nd + i] += h[i];
+    }
+    TRY(dot_async(g, q, q, S_TMP));
+    TRY(fetch_scalars(g));
+    const double rn = sqrt(g->scal_host[S_TMP]);
+    if (!(rn > 0.0) || !isfinite(rn)) {
+      cudaFree(B.QAW);
+      B.QAW = nullptr;
+      return fail(g, WHV_ERR_BREAKDOWN, "A W is rank deficient (dependent augmentation vectors)");
+    }
+    R[(size_t)j * nd + j] = rn;
+    TRY(axpby(g, N, 1.0 / rn, q, 0.0, q));
+  }
+  B.Raw = R;
+  return WHV_OK;
+}
+
 struct InnerResult {
   int iters = 0;
   bool converged = false, breakdown = false;
@@ -430,6 +478,124 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
       TRY(copy_dev(g, g->r, b, N));
       TRY(axpby(g, N, -1.0, g->q, 1.0, g->r));
     }
+  } else if (method == WHV_AGMRES) {
+    // Algorithm 5 with restarts; augmentation W = the grid's basis (pd columns, may be 0)
+    const int m = p->restart > 0 ? p->restart : 30;
+    const int pd = B.nd;
+    if (m + 1 > kMaxND) return fail(g, WHV_ERR_INVALID, "AGMRES restart too large");
+    if (pd > 0) TRY(prepare_agmres(c));
+    if (g->krylov_cols < m + 1) {
+      if (g->krylov) cudaFree(g->krylov);
+      g->krylov = nullptr;
+      g->krylov_cols = 0;
+      WHV_CUDA(g, cudaMalloc(&g->krylov, (size_t)(m + 1) * N * sizeof(double)));
+      g->krylov_cols = m + 1;
+    }
+    double* K = g->krylov;   // v_{p+1} .. v_{p+m+1}
+    const double bnorm = sqrt(bb);
+    const int D = pd + m;
+    std::vector<double> H((size_t)(D + 1) * D), cs(D), sn(D), gv(D + 1), y(D), hp(std::max(pd, 1)), hk(m + 1);
+    auto Hc = [&](int i, int j) -> double& { return H[(size_t)j * (D + 1) + i]; };
+    int cycle = 0;
+    while (true) {
+      TRY(dot_async(g, g->r, g->r, S_TMP));
+      TRY(fetch_scalars(g));
+      const double beta0 = sqrt(g->scal_host[S_TMP]);
+      if (log_on()) fprintf(stderr, "[whv] AGMRES cycle start: rel %.3e after %d iterations\n", beta0 / bnorm, R.iters);
+      if (!isfinite(beta0)) { R.breakdown = true; break; }
+      R.rel = beta0 / bnorm;
+      if (R.rel <= tol) { R.converged = true; break; }
+      if (cycle > 0 && R.iters >= maxit) break;   // the first cycle runs even for maxit = 0
+      ++cycle;
+      std::fill(H.begin(), H.end(), 0.0);
+      std::fill(gv.begin(), gv.end(), 0.0);
+      // v_{p+1} = (I - V_p V_p^T M) b_0 / ||.||;  g_k = <v_k, b_0>, k <= p + 1
+      TRY(copy_dev(g, K, g->r, N));
+      if (pd > 0) {
+        TRY(project(g, B.QAW, pd, K, g->small));
+        TRY(to_host(g, hp.data(), g->small, pd));
+        TRY(expand(g, B.QAW, pd, g->small, -1.0, K));
+        TRY(project(g, B.QAW, pd, K, g->small));
+        TRY(expand(g, B.QAW, pd, g->small, -1.0, K));
+        for (int i = 0; i < pd; ++i) gv[i] = hp[i];
+        for (int j = 0; j < pd; ++j)
+          for (int i = 0; i <= j; ++i) Hc(i, j) = B.Raw[(size_t)j * pd + i];
+      }
+      TRY(dot_async(g, K, K, S_TMP));
+      TRY(fetch_scalars(g));
+      const double vn = sqrt(g->scal_host[S_TMP]);
+      if (vn > 0.0) TRY(axpby(g, N, 1.0 / vn, K, 0.0, K));
+      TRY(dot_async(g, K, g->r, S_TMP));
+      TRY(fetch_scalars(g));
+      gv[pd] = g->scal_host[S_TMP];
+      int k = pd;
+      bool lucky = false;
+      // |g_{p+1}| is the residual of the fit over span(W) alone: no Arnoldi step if it meets tol
+      const int nsteps = fabs(gv[pd]) / bnorm > tol ? std::min(m, maxit - R.iters) : 0;
+      for (int j = 0; j < nsteps; ++j) {
+        const int jj = pd + j;
+        double* w = K + (size_t)(j + 1) * N;
+        TRY(apply_A(c, K + (size_t)j * N, w));
+        ++R.iters;
+        for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt against [V_p | v_{p+1..}], twice
+          if (pd > 0) TRY(project(g, B.QAW, pd, w, g->small));
+          TRY(project(g, K, j + 1, w, g->small2));
+          if (pd > 0) TRY(expand(g, B.QAW, pd, g->small, -1.0, w));
+          TRY(expand(g, K, j + 1, g->small2, -1.0, w));
+          if (pd > 0) {
+            TRY(to_host(g, hp.data(), g->small, pd));
+            for (int i = 0; i < pd; ++i) Hc(i, jj) += hp[i];
+          }
+          TRY(to_host(g, hk.data(), g->small2, j + 1));
+          for (int i = 0; i <= j; ++i) Hc(pd + i, jj) += hk[i];
+        }
+        TRY(dot_async(g, w, w, S_TMP));
+        TRY(fetch_scalars(g));
+        const double hn = sqrt(g->scal_host[S_TMP]);
+        if (!isfinite(hn)) { R.breakdown = true; break; }
+        Hc(jj + 1, jj) = hn;
+        lucky = !(hn > 0.0);
+        if (!lucky) TRY(axpby(g, N, 1.0 / hn, w, 0.0, w));
+        for (int i = pd; i < jj; ++i) {   // previous rotations (the first p columns are triangular)
+          const double t = cs[i] * Hc(i, jj) + sn[i] * Hc(i + 1, jj);
+          Hc(i + 1, jj) = -sn[i] * Hc(i, jj) + cs[i] * Hc(i + 1, jj);
+          Hc(i, jj) = t;
+        }
+        const double den = hypot(Hc(jj, jj), Hc(jj + 1, jj));
+        if (!(den > 0.0)) { R.breakdown = true; break; }
+        cs[jj] = Hc(jj, jj) / den;
+        sn[jj] = Hc(jj + 1, jj) / den;
+        Hc(jj, jj) = den;
+        Hc(jj + 1, jj) = 0.0;
+        gv[jj + 1] = -sn[jj] * gv[jj];
+        gv[jj] = cs[jj] * gv[jj];
+        k = jj + 1;
+        if (fabs(gv[k]) / bnorm <= tol || R.iters >= maxit || lucky) break;
+      }
+      if (R.breakdown && k == pd && nsteps > 0) break;
+      // H_{1:k,1:k} y = g_{1:k};  x += [W | v_{p+1..k}] y
+      for (int i = k - 1; i >= 0; --i) {
+        double sacc = gv[i];
+        for (int l = i + 1; l < k; ++l) sacc -= Hc(i, l) * y[l];
+        y[i] = sacc / Hc(i, i);
+      }
+      if (pd > 0) {
+        TRY(to_dev(g, g->small, y.data(), pd));
+        TRY(expand(g, B.V, pd, g->small, 1.0, g->x));
+      }
+      if (k > pd) {
+        TRY(to_dev(g, g->small, y.data() + pd, k - pd));
+        TRY(expand(g, K, k - pd, g->small, 1.0, g->x));
+      }
+      R.rel = fabs(gv[k]) / bnorm;
+      if (R.breakdown) break;
+      if (R.rel <= tol || lucky) { R.converged = true; break; }
+      if (R.iters >= maxit) break;
+      // restart: b_0 = b - A x
+      TRY(apply_A(c, g->x, g->q));
+      TRY(copy_dev(g, g->r, b, N));
+      TRY(axpby(g, N, -1.0, g->q, 1.0, g->r));
+    }
   } else {  // FPI, Algorithm 1: x <- Pi_h(x; f_d)
     const double bnorm = sqrt(bb);
     while (R.iters < maxit) {
@@ -467,7 +633,7 @@ static whv_status outer_solve(SolveCtx& c, int method, const whv_params* p, cons
   // modal correction of the deflated components: only valid for exact eigenvectors (with
   // approximate ones W diag(1/mu) W^T M is not a Galerkin solve and the passes can diverge);
   // approximate bases deflate through Algorithm 4 (method DCG) instead
-  const bool defl = B.nd > 0 && method != WHV_DCG && (B.flags & WHV_BASIS_EXACT);
+  const bool defl = B.nd > 0 && method != WHV_DCG && method != WHV_AGMRES && (B.flags & WHV_BASIS_EXACT);
   const double inner_tol = fp64_res ? (p->inner_tol > 0.0 ? p->inner_tol : 1e-3) : p->tol;
   if (!use_x0) WHV_CUDA(g, cudaMemsetAsync(g->xo, 0, N * sizeof(double), g->stream));
   bool have_x = use_x0;
@@ -546,7 +712,7 @@ extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f
   TRY(make_time_grid(g, p, &tg));
   if (!(p->tol >= 0.0) || p->maxit < 0) return fail(g, WHV_ERR_INVALID, "tol must be >= 0, maxit >= 0");
   const int method = p->method;
-  if (method < WHV_FPI || method > WHV_GMRES) return fail(g, WHV_ERR_INVALID, "unknown method");
+  if (method < WHV_FPI || method > WHV_AGMRES) return fail(g, WHV_ERR_INVALID, "unknown method");
   Basis& B = g->basis;
   const bool has_basis = B.nd > 0;
   if (has_basis && (B.omega != p->omega || B.periods != p->periods ||
@@ -555,10 +721,11 @@ extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f
   if (method == WHV_DCG && !has_basis) return fail(g, WHV_ERR_INVALID, "DCG needs a deflation basis");
   const bool refine = (p->flags & WHV_REFINE_FP64) != 0;
   if (refine && method == WHV_FPI)
-    return fail(g, WHV_ERR_INVALID, "FP64 residual correction needs a Krylov method (CG, DCG, GMRES)");
-  const bool devd = has_basis && method != WHV_DCG;
+    return fail(g, WHV_ERR_INVALID, "FP64 residual correction needs a Krylov method (CG, DCG, GMRES, AGMRES)");
+  // DCG and AGMRES use the basis inside the iteration; the others deflate the forcing (DEVD)
+  const bool devd = has_basis && method != WHV_DCG && method != WHV_AGMRES;
   const int64_t N = g->N;
-  SolveCtx c{g, tg, has_basis && (B.flags & WHV_BASIS_REDEFLATE) != 0};
+  SolveCtx c{g, tg, has_basis && (B.flags & WHV_BASIS_REDEFLATE) != 0 && method != WHV_AGMRES};
   double* b = g->t;  // b of the iterated system
 
   // ---- forcing (Algorithm 2: deflate the forcing)
@@ -658,8 +825,8 @@ extern "C" whv_status whv_solve_adjoint(whv_grid g, const whv_params* p, const d
   TimeGridH tg;
   TRY(make_time_grid(g, p, &tg));
   const int method = p->method;
-  if (method != WHV_CG && method != WHV_DCG && method != WHV_GMRES)
-    return fail(g, WHV_ERR_INVALID, "the adjoint solve needs a Krylov method (CG, DCG, GMRES)");
+  if (method != WHV_CG && method != WHV_DCG && method != WHV_GMRES && method != WHV_AGMRES)
+    return fail(g, WHV_ERR_INVALID, "the adjoint solve needs a Krylov method (CG, DCG, GMRES, AGMRES)");
   const Basis& B = g->basis;
   if (B.nd > 0 && (B.omega != p->omega || B.periods != p->periods || B.adjust != (p->adjust_omega ? 1 : 0) ||
                    B.cfl != tg.cfl))
@@ -670,7 +837,7 @@ extern "C" whv_status whv_solve_adjoint(whv_grid g, const whv_params* p, const d
   const bool refine = (p->flags & WHV_REFINE_FP64) != 0;
   const int64_t N = g->N;
   TRY(ensure_fp64_buffers(g));
-  SolveCtx c{g, tg, B.nd > 0 && (B.flags & WHV_BASIS_REDEFLATE) != 0};
+  SolveCtx c{g, tg, B.nd > 0 && (B.flags & WHV_BASIS_REDEFLATE) != 0 && method != WHV_AGMRES};
   // (I - S)^T lambda = g  <=>  (I - S) y = c^2 g,  lambda = y / c^2
   TRY(scale_by(g, dLdu, g->c2, 1.0, g->t));
   TRY(dot_async(g, g->t, g->t, S_RR0));

@@ -56,6 +56,9 @@ struct Basis {
   // first DCG solve with a basis that is not WHV_BASIS_EXACT
   double* AW = nullptr;               // N x nd
   double* Einv = nullptr;             // nd x nd, row-major
+  // Algorithm 5: A W = QAW Raw (thin QR in <.,.>_M), built on the first AGMRES solve
+  double* QAW = nullptr;              // N x nd, M-orthonormal columns
+  std::vector<double> Raw;            // nd x nd upper triangular, column-major
 };
 
 struct StepPlan;  // cached CUDA graphs of wave solves (stencil.cu)

@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--method", default="", choices=["", "cg", "dcg", "gmres", "agmres"],
                     help="accelerator of the single-grid workloads (default: DCG for c1/c3, CG otherwise)")
+    ap.add_argument("--check-every", type=int, default=1,
+                    help="convergence test every k iterations; 1 keeps the CG loop on the device (a graph "
+                         "with a conditional node), k > 1 launches one iteration graph per step from the host")
     ap.add_argument("--sources", type=int, default=0,
                     help="batched workload: Gaussian sources per (grid, frequency) (default 16)")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
@@ -254,7 +257,8 @@ def run_workload(args):
         for n in I.C4_SIZES:
             for om in I.C4_OMEGAS:
                 w = I.WORKLOADS[f"c4_{n}_{int(om)}"]
-                prm = whv.make_params(om, method="cg", tol=w.tol, maxit=3000, refine_fp64=fp32)
+                prm = whv.make_params(om, method="cg", tol=w.tol, maxit=3000, refine_fp64=fp32,
+                                      check_every=args.check_every)
                 tmpl = whv.Grid(w.npts, precision=gprec, stream=stream)
                 tmpl.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
                 b = tmpl.whv_get_basis(want_vectors=True)
@@ -296,7 +300,8 @@ def run_workload(args):
                                             f"(width 2h), 32 closed-form vectors each, {form} to 1e-6; every "
                                             f"batched wave solve of all {len(probs)} problems is one persistent launch",
                                 "problems": len(probs), "setup_s": setup_s,
-                                "steps_per_sweep": "8 (FP32) / 4 (FP64), 5-point stencil"},
+                                "steps_per_sweep": "8 (FP32) / 4 (FP64), 5-point stencil",
+                                "check_every": args.check_every},
                      "iterations_max": max(i["iterations"] for i in infos),
                      "iterations_mean": statistics.mean(i["iterations"] for i in infos),
                      "outer_iterations_max": max(i["outer_iterations"] for i in infos),
@@ -384,7 +389,7 @@ def main():
     stream = torch.cuda.Stream()
     g = whv.Grid(w.npts, precision=prec, stream=stream)
     # FP32 stepping runs inside FP64 residual correction so that the FP64 residual meets tol
-    prm = whv.make_params(w.omega, method="cg", tol=tol, maxit=5000, check_every=1,
+    prm = whv.make_params(w.omega, method="cg", tol=tol, maxit=5000, check_every=args.check_every,
                           refine_fp64=args.precision == "fp32")
     tgrid = g.whv_time_grid(prm)
     nt = tgrid["nt"]
@@ -533,7 +538,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
             "krylov_dtype": "f64", "data": "synthetic",
-            "config": dict(config_dict(w, tol, args.precision, nt, world), steps_per_sweep=ksweep),
+            "config": dict(config_dict(w, tol, args.precision, nt, world), steps_per_sweep=ksweep,
+                           check_every=args.check_every),
             "iterations": info["iterations"], "wave_solves": info["wave_solves"],
             "rel_residual": info["rel_residual"], "glups_solve": glups_solve, "accuracy": accuracy,
             "outer_iterations": info.get("outer_iterations", 0), "wave_solves_fp64": info.get("wave_solves_fp64", 0),

@@ -658,29 +658,37 @@ static whv_status fetch_all(BatchCtx& c) {
   return WHV_OK;
 }
 
-// The batched CG loop as one graph with a WHILE node, built for the A p role `ap`.
+// The batched CG loop, built for the A p role `ap`: one graph with a WHILE node (device-resident
+// loop), or -- with check_every > 1 -- a graph of one iteration that the host launches, testing
+// convergence every check_every iterations.
 struct CgGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t body_launches = 0;
+  int check_every = 1;         // 1: device-resident loop
   ~CgGraph() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
   }
 };
 
-static whv_status build_cg_graph(BatchCtx& c, const Wave& ap, CgGraph* G) {
+static whv_status build_cg_graph(BatchCtx& c, const Wave& ap, int check_every, CgGraph* G) {
+  G->check_every = std::max(1, check_every);
+  const bool device_loop = G->check_every == 1;
   B_CUDA(c.g0, cudaGraphCreate(&G->graph, 0));
-  cudaGraphConditionalHandle h;
-  B_CUDA(c.g0, cudaGraphConditionalHandleCreate(&h, G->graph, 1, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams prm = {};
-  prm.type = cudaGraphNodeTypeConditional;
-  prm.conditional.handle = h;
-  prm.conditional.type = cudaGraphCondTypeWhile;
-  prm.conditional.size = 1;
-  cudaGraphNode_t node;
-  B_CUDA(c.g0, cudaGraphAddNode(&node, G->graph, nullptr, nullptr, 0, &prm));
-  cudaGraph_t body = prm.conditional.phGraph_out[0];
+  cudaGraphConditionalHandle h = 0;
+  cudaGraph_t body = G->graph;
+  if (device_loop) {
+    B_CUDA(c.g0, cudaGraphConditionalHandleCreate(&h, G->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams prm = {};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    B_CUDA(c.g0, cudaGraphAddNode(&node, G->graph, nullptr, nullptr, 0, &prm));
+    body = prm.conditional.phGraph_out[0];
+  }
   B_CUDA(c.g0, cudaStreamBeginCaptureToGraph(c.st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   const int64_t l0 = whv_kernel_launches();
   whv_status s = WHV_OK;
@@ -695,12 +703,12 @@ static whv_status build_cg_graph(BatchCtx& c, const Wave& ap, CgGraph* G) {
   }
   if (e == cudaSuccess && s == WHV_OK) {
     k_batch_check<<<(c.np + 127) / 128, 128, 0, c.st>>>(c.scal, c.np);
-    k_batch_any<<<1, 1, 0, c.st>>>(h, c.scal, c.np, c.err);
+    if (device_loop) k_batch_any<<<1, 1, 0, c.st>>>(h, c.scal, c.np, c.err);
     e = cudaGetLastError();
   }
   cudaGraph_t captured = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(c.st, &captured);
-  G->body_launches = (whv_kernel_launches() - l0) + 4;   // + wave, finish, check, any
+  G->body_launches = (whv_kernel_launches() - l0) + (device_loop ? 4 : 3);   // + wave, finish, check(, any)
   count_launches(-(whv_kernel_launches() - l0));
   if (s != WHV_OK) return s;
   if (e != cudaSuccess) return cuda_fail(c.g0, e, "batched loop body");
@@ -732,16 +740,33 @@ static whv_status run_cg(BatchCtx& c, CgGraph& G, const std::vector<const double
     }
     B_CUDA(c.g0, cudaMemcpyAsync(g->scal, sc, S_NSLOTS * sizeof(double), cudaMemcpyHostToDevice, c.st));
   }
-  B_CUDA(c.g0, cudaGraphLaunch(G.exec, c.st));
-  TRY(check_barrier(c));
-  TRY(fetch_all(c));
+  int64_t body_runs = -1;
+  if (G.check_every == 1) {
+    B_CUDA(c.g0, cudaGraphLaunch(G.exec, c.st));
+    TRY(check_barrier(c));
+    TRY(fetch_all(c));
+  } else {   // host-driven: stopped problems skip their work, so extra iterations are no-ops
+    int mx = 0;
+    for (int p = 0; p < c.np; ++p) mx = std::max(mx, active[p] ? maxit[p] : 0);
+    body_runs = 0;
+    bool any = false;
+    for (int p = 0; p < c.np; ++p) any = any || c.grids[p]->scal_host[S_HALT] == 0.0;
+    while (any && body_runs < mx) {
+      for (int q = 0; q < G.check_every && body_runs < mx; ++q, ++body_runs)
+        B_CUDA(c.g0, cudaGraphLaunch(G.exec, c.st));
+      TRY(check_barrier(c));
+      TRY(fetch_all(c));
+      any = false;
+      for (int p = 0; p < c.np; ++p) any = any || c.grids[p]->scal_host[S_HALT] == 0.0;
+    }
+  }
   int max_it = 0;
   for (int p = 0; p < c.np; ++p) {
     const int it = (int)c.grids[p]->scal_host[S_ITER];
     (*iters)[p] = it;
     max_it = std::max(max_it, it);
   }
-  c.launches += G.body_launches * max_it;
+  c.launches += G.body_launches * (body_runs >= 0 ? body_runs : max_it);
   return WHV_OK;
 }
 
@@ -764,7 +789,7 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
   Wave ap;
   TRY(g64 ? (make_wave<double, DIM, ORDER, VARC>(c, io_ap, &ap)) : (make_wave<float, DIM, ORDER, VARC>(c, io_ap, &ap)));
   CgGraph G;
-  TRY(build_cg_graph(c, ap, &G));
+  TRY(build_cg_graph(c, ap, c.params[0].check_every, &G));
   std::vector<int> maxit(np);
   for (int p = 0; p < np; ++p) maxit[p] = c.params[p].maxit;
 

@@ -180,3 +180,24 @@ def test_batched_refine_flag_must_agree():
     f = dev(np.ones(g1.N))
     with pytest.raises(whv.WhvError):
         whv.whv_solve_batched([g1, g2], [p1, p2], [f, f])
+
+
+def test_batched_host_driven_loop_matches_device_loop():
+    """check_every > 1 runs the batched CG iteration as a graph launched by the host (convergence
+    tested every check_every iterations): same iterates and iteration counts as the device loop."""
+    probs = _problems((33, 47), (9.0, 14.0), 1, 5)
+    out = {}
+    for ce in (1, 3):
+        stream = torch.cuda.Stream()
+        grids, params, fs = [], [], []
+        for npts, om, f, nd in probs:
+            g = whv.Grid(npts, precision=whv.WHV_FP64, stream=stream)
+            prm = whv.make_params(om, method="cg", tol=1e-9, maxit=500, check_every=ce)
+            g.whv_set_deflation_basis(prm, nd, whv.WHV_BASIS_CLOSED_FORM)
+            grids.append(g); params.append(prm); fs.append(dev(f))
+        us, infos = whv.whv_solve_batched(grids, params, fs)
+        assert all(i["status"] == "OK" for i in infos)
+        out[ce] = ([u.cpu().numpy() for u in us], [i["iterations"] for i in infos])
+    assert out[1][1] == out[3][1]
+    for a, b in zip(out[1][0], out[3][0]):
+        assert IND.relmax(a, b) < 1e-13

@@ -13,7 +13,11 @@ A = I - S_h is self-adjoint (see operators.py).
                the search space is span(W) + the Krylov space of A started from the part of
                b_0 outside range(A W); restarted after m Arnoldi steps, keeping the QR factors
                of A W.
-* augmented_solve  A u = b (b = Pi_h(0; f), undeflated forcing) by agmres with the basis W.
+* abicgstab    Algorithm 6 (augmented / recycled BiCGStab of Amritkar et al.), with the listing's
+               typos corrected: eta_1 = Q^T r and r <- r - Q eta_1 at the start, p = r in the
+               first iteration (i = 1), alpha = rho / <r~, v>.
+* augmented_solve  A u = b (b = Pi_h(0; f), undeflated forcing) by agmres or abicgstab with the
+               basis W.
 * devd_solve   Algorithm 2 (direct eigenvector deflation): deflate the forcing, solve with
                FPI / CG / GMRES, optionally re-deflate each operator output, inflate.
 
@@ -330,10 +334,111 @@ def agmres(grid, A, b, W, tol, maxit, restart=30, x0=None, AW=None):
         nA += 1
 
 
-def augmented_solve(grid: Grid, tg: TimeGrid, f, W, lam2=None, tol=1e-10, maxit=1000, restart=30, x0=None):
-    """A u = b with b = Pi_h(0; f) (the forcing is not deflated) by Algorithm 5 augmented with
-    the columns of W.  With lam2 (W exact eigenvectors) A W = W diag(1 - beta_h(lambda)) costs no
-    wave solve; without, A W takes one wave solve per column."""
+def _thin_qr(ip, AW):
+    """A W = Q R with M-orthonormal Q (classical Gram-Schmidt, twice) and upper-triangular R."""
+    p = AW.shape[1]
+    Q = []
+    R = np.zeros((p, p))
+    for j in range(p):
+        w = AW[:, j].copy()
+        for _ in range(2):
+            if Q:
+                h = np.array([ip(q, w) for q in Q])
+                w = w - sum(hi * q for hi, q in zip(h, Q))
+                R[:j, j] += h
+        R[j, j] = math.sqrt(ip(w, w))
+        Q.append(w / R[j, j])
+    return (np.array(Q).T if p else np.zeros((AW.shape[0], 0))), R
+
+
+def abicgstab(grid, A, b, W, tol, maxit, x0=None, AW=None):
+    """Algorithm 6 (inner products <.,.>_M).  `maxit` bounds the iterations (two applications of
+    A each).  In the notation of Algorithm 6:
+        r = b - A x,  r~ = r
+        A W = Q R;  eta_1 = Q^T r;  r <- r - Q eta_1;  xi = -eta_1
+        loop: rho = <r~, r>;  p = r (first) or r + beta (p - omega v), beta = (rho/rho_old)(alpha/omega)
+              v = A p;  eta_1 = Q^T v;  v <- v - Q eta_1;  alpha = rho / <r~, v>;  s = r - alpha v
+              ||s|| <= tol ||b||: x += alpha p, r = s, xi += alpha eta_1, stop
+              t = A s;  eta_2 = Q^T t;  t <- t - Q eta_2;  omega = <t, s> / <t, t>
+              xi += alpha eta_1 + omega eta_2;  x += alpha p + omega s;  r = s - omega t
+              ||r|| <= tol ||b||: stop
+        x <- x - W R^{-1} xi
+    The tracked r is the residual of the final x (the W correction removes its range(A W) part)."""
+    shape = grid.shape
+    wts = grid.weights().ravel()
+    ip = lambda u, v: float(np.sum(wts * u * v))  # noqa: E731
+    bf = np.asarray(b, dtype=np.float64).ravel()
+    W = np.zeros((bf.size, 0)) if W is None else np.asarray(W, dtype=np.float64).reshape(bf.size, -1)
+    p_ = W.shape[1]
+    nA = 0
+    if AW is None:
+        AW = np.zeros_like(W)
+        for j in range(p_):
+            AW[:, j] = A(W[:, j].reshape(shape)).ravel()
+            nA += 1
+    Q, R = _thin_qr(ip, np.asarray(AW, dtype=np.float64).reshape(bf.size, p_))
+    QtM = lambda v: Q.T @ (wts * v)  # noqa: E731
+    x = np.zeros(bf.size) if x0 is None else np.asarray(x0, dtype=np.float64).ravel().copy()
+    r = bf.copy()
+    if x0 is not None:
+        r = bf - A(x.reshape(shape)).ravel()
+        nA += 1
+    rt = r.copy()
+    eta1 = QtM(r)
+    r = r - Q @ eta1
+    xi = -eta1
+    bnorm = math.sqrt(ip(bf, bf))
+    hist = [math.sqrt(ip(r, r)) / bnorm]
+    converged = hist[0] <= tol
+    its = 0
+    rho_old = alpha = omega = 1.0
+    pv = np.zeros(bf.size)
+    v = np.zeros(bf.size)
+    while not converged and its < maxit:
+        its += 1
+        rho = ip(rt, r)
+        if rho == 0.0:
+            break
+        if its == 1:
+            pv = r.copy()
+        else:
+            beta = (rho / rho_old) * (alpha / omega)
+            pv = r + beta * (pv - omega * v)
+        v = A(pv.reshape(shape)).ravel()
+        nA += 1
+        eta1 = QtM(v)
+        v = v - Q @ eta1
+        alpha = rho / ip(rt, v)
+        s = r - alpha * v
+        if math.sqrt(ip(s, s)) <= tol * bnorm:
+            x = x + alpha * pv
+            r = s
+            xi = xi + alpha * eta1
+            converged = True
+            hist.append(math.sqrt(ip(r, r)) / bnorm)
+            break
+        t = A(s.reshape(shape)).ravel()
+        nA += 1
+        eta2 = QtM(t)
+        t = t - Q @ eta2
+        omega = ip(t, s) / ip(t, t)
+        xi = xi + alpha * eta1 + omega * eta2
+        x = x + alpha * pv + omega * s
+        r = s - omega * t
+        hist.append(math.sqrt(ip(r, r)) / bnorm)
+        converged = hist[-1] <= tol
+        rho_old = rho
+    if p_:
+        x = x - W @ np.linalg.solve(R, xi)
+    return SolveResult(x.reshape(shape), its, nA, converged, hist)
+
+
+def augmented_solve(grid: Grid, tg: TimeGrid, f, W, lam2=None, tol=1e-10, maxit=1000, restart=30, x0=None,
+                    method="agmres"):
+    """A u = b with b = Pi_h(0; f) (the forcing is not deflated) by Algorithm 5 (agmres) or
+    Algorithm 6 (abicgstab) augmented with the columns of W.  With lam2 (W exact eigenvectors)
+    A W = W diag(1 - beta_h(lambda)) costs no wave solve; without, A W takes one wave solve per
+    column."""
     from .spectral import beta_h
     f = np.asarray(f, dtype=np.float64).reshape(grid.shape)
     A = Operator(grid, tg)
@@ -341,7 +446,12 @@ def augmented_solve(grid: Grid, tg: TimeGrid, f, W, lam2=None, tol=1e-10, maxit=
     AW = None
     if lam2 is not None and W is not None:
         AW = np.asarray(W) * (1.0 - beta_h(np.asarray(lam2), tg))[None, :]
-    res = agmres(grid, A, b, W, tol, maxit, restart, x0, AW)
+    if method == "agmres":
+        res = agmres(grid, A, b, W, tol, maxit, restart, x0, AW)
+    elif method == "abicgstab":
+        res = abicgstab(grid, A, b, W, tol, maxit, x0, AW)
+    else:
+        raise ValueError(method)
     return DevdResult(res.x, res, A.count + 1, np.zeros(0), b)
 
 

@@ -52,10 +52,13 @@ enum {
   WHV_CG = 1,     /* conjugate gradients on A u = b                                   */
   WHV_DCG = 2,    /* Algorithm 4, deflated CG (needs a basis)                         */
   WHV_GMRES = 3,  /* restarted GMRES(m), classical Gram-Schmidt applied twice         */
-  WHV_AGMRES = 4  /* Algorithm 5, augmented GMRES(m): the grid's basis W augments the
+  WHV_AGMRES = 4, /* Algorithm 5, augmented GMRES(m): the grid's basis W augments the
                      Krylov space (A W = V_p H_p by a thin QR kept with the basis; for a
                      WHV_BASIS_EXACT basis A W = W diag(1 - beta_h), else one wave solve per
                      column); the forcing is not deflated; no basis = GMRES(m)              */
+  WHV_ABICGSTAB = 5 /* Algorithm 6, augmented BiCGStab: BiCGStab on the system projected
+                     away from range(A W) (same QR as AGMRES), x -= W R^{-1} xi at the end;
+                     two wave solves per iteration; no basis = BiCGStab                    */
 };
 
 /* origin of the deflation basis (whv_set_deflation_basis) */
@@ -80,8 +83,8 @@ enum {
                                  Krylov solve of the rest in the grid's stepping precision to relative
                                  tolerance inner_tol; repeated until the FP64 residual meets tol.
                                  Lets FP32 stepping reach FP64 residuals and corrects approximate
-                                 (Lanczos) eigenvectors.  Needs CG, DCG, GMRES or AGMRES (DCG and
-                                 AGMRES handle the basis themselves, no modal step); allocates 3 (FP64
+                                 (Lanczos) eigenvectors.  Needs a Krylov method (DCG, AGMRES and
+                                 ABICGSTAB use the basis themselves: no modal step); allocates 3 (FP64
                                  grids) or 8 (FP32 grids) more N-vectors of FP64 on first use.       */
 };
 
@@ -92,7 +95,7 @@ typedef struct {
                          fixed point solves the Helmholtz problem at omega exactly (Sec. 2.2);
                          0: dt = Tbar/ceil(Tbar/dt0) and the fixed point is at omega_eff        */
   double cfl;         /* dt0 = cfl * h_min / c_max; <= 0 selects 0.5 (order 2) or 0.4 (order 4)  */
-  int method;         /* WHV_FPI | WHV_CG | WHV_DCG | WHV_GMRES | WHV_AGMRES                      */
+  int method;         /* WHV_FPI | WHV_CG | WHV_DCG | WHV_GMRES | WHV_AGMRES | WHV_ABICGSTAB      */
   int restart;        /* (A)GMRES restart length m (Arnoldi steps per cycle); <= 0 selects 30     */
   double tol;         /* stop when ||r||_M <= tol ||b||_M of the iterated system                  */
   int maxit;          /* maximum operator applications in the iteration                          */

@@ -16,6 +16,9 @@
 //    thin QR A W = V_p H_p (classical Gram-Schmidt twice, M inner products) is built once per
 //    basis, each cycle projects range(A W) out of the residual, runs the Arnoldi steps
 //    orthogonally to [V_p | V_{p+1..}] and solves the triangular system over [W | V_{p+1..k}].
+//  * ABICGSTAB (Algorithm 6): BiCGStab on the system projected away from range(A W) (same QR
+//    factors as AGMRES), two wave solves per iteration, scalars on the host; the W components
+//    are restored at the end, x -= W R^{-1} xi.
 //  * FPI (Algorithm 1).
 //  * FP64 residual correction (WHV_REFINE_FP64): the outer loop forms the residual r = b - A x of
 //    the full system with FP64 wave solves; the correction is the modal solve of its deflated
@@ -225,9 +228,9 @@ static whv_status prepare_general_dcg(SolveCtx& c) {
   for (int m = 0; m < nd; ++m) {
     // through fixed buffers so that every column replays one cached wave-solve graph
     WHV_CUDA(g, cudaMemcpyAsync(g->p, B.V + (size_t)m * N, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
-    TRY(wave_solve(g, c.tg, g->p, nullptr, g->t, 1));
+    TRY(wave_solve(g, c.tg, g->p, nullptr, g->q, 1));   // not t: it may hold the right-hand side
     c.ws++;
-    WHV_CUDA(g, cudaMemcpyAsync(B.AW + (size_t)m * N, g->t, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    WHV_CUDA(g, cudaMemcpyAsync(B.AW + (size_t)m * N, g->q, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
   }
   // E = W^T M (A W), symmetrised (A is M-self-adjoint; FP32 stepping breaks it at rounding level)
   std::vector<double> E((size_t)nd * nd), col(nd);
@@ -274,10 +277,12 @@ static whv_status prepare_agmres(SolveCtx& c) {
     } else if (B.AW) {
       TRY(copy_dev(g, q, B.AW + (size_t)j * N, N));
     } else {
-      TRY(copy_dev(g, g->p, wj, N));   // fixed buffers: every column replays one wave-solve graph
-      TRY(wave_solve(g, c.tg, g->p, nullptr, g->t, 1));
+      // through p -> q (the A p buffers: every column replays one cached wave-solve graph; t may
+      // hold the right-hand side, which the restarts read again)
+      TRY(copy_dev(g, g->p, wj, N));
+      TRY(wave_solve(g, c.tg, g->p, nullptr, g->q, 1));
       c.ws++;
-      TRY(copy_dev(g, q, g->t, N));
+      TRY(copy_dev(g, q, g->q, N));
     }
     for (int pass = 0; pass < 2 && j > 0; ++pass) {   // classical Gram-Schmidt, twice
       TRY(project(g, B.QAW, j, q, g->small));
@@ -299,6 +304,10 @@ static whv_status prepare_agmres(SolveCtx& c) {
   B.Raw = R;
   return WHV_OK;
 }
+
+// Algorithms 5 and 6 use the basis inside the iteration (augmentation): no forcing deflation,
+// no modal correction, no re-deflation
+static bool augmented(int method) { return method == WHV_AGMRES || method == WHV_ABICGSTAB; }
 
 struct InnerResult {
   int iters = 0;
@@ -596,6 +605,105 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
       TRY(copy_dev(g, g->r, b, N));
       TRY(axpby(g, N, -1.0, g->q, 1.0, g->r));
     }
+  } else if (method == WHV_ABICGSTAB) {
+    // Algorithm 6 (typos corrected: eta_1 = Q^T M r; p = r at i = 1; alpha = rho / <r~, v>)
+    const int pd = B.nd;
+    if (pd > 0) TRY(prepare_agmres(c));   // A W = Q R
+    if (g->krylov_cols < 4) {
+      if (g->krylov) cudaFree(g->krylov);
+      g->krylov = nullptr;
+      g->krylov_cols = 0;
+      WHV_CUDA(g, cudaMalloc(&g->krylov, (size_t)4 * N * sizeof(double)));
+      g->krylov_cols = 4;
+    }
+    double* rt = g->krylov;              // shadow residual r~
+    double* v = g->krylov + N;
+    double* sv = g->krylov + 2 * N;
+    double* tv = g->krylov + 3 * N;
+    const double bnorm = sqrt(bb);
+    std::vector<double> xi(std::max(pd, 1), 0.0), e1(std::max(pd, 1), 0.0), e2(std::max(pd, 1), 0.0);
+    auto dot = [&](const double* a, const double* b2, double* out) -> whv_status {
+      TRY(dot_async(g, a, b2, S_TMP));
+      TRY(fetch_scalars(g));
+      *out = g->scal_host[S_TMP];
+      return WHV_OK;
+    };
+    // u <- u - Q (Q^T M u), coefficients to eta (host)
+    auto project_Q = [&](double* u, double* eta) -> whv_status {
+      TRY(project(g, B.QAW, pd, u, g->small));
+      TRY(to_host(g, eta, g->small, pd));
+      return expand(g, B.QAW, pd, g->small, -1.0, u);
+    };
+    TRY(copy_dev(g, rt, g->r, N));
+    if (pd > 0) {
+      TRY(project_Q(g->r, e1.data()));
+      for (int i = 0; i < pd; ++i) xi[i] = -e1[i];
+    }
+    double rr;
+    TRY(dot(g->r, g->r, &rr));
+    R.rel = sqrt(rr) / bnorm;
+    if (!isfinite(R.rel)) R.breakdown = true;
+    else if (R.rel <= tol) R.converged = true;
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    while (!R.converged && !R.breakdown && R.iters < maxit) {
+      ++R.iters;
+      double rho;
+      TRY(dot(rt, g->r, &rho));
+      if (!(rho != 0.0) || !isfinite(rho)) { R.breakdown = true; break; }
+      if (R.iters == 1) {
+        TRY(copy_dev(g, g->p, g->r, N));
+      } else {
+        const double beta = (rho / rho_old) * (alpha / omega);
+        TRY(axpby(g, N, -omega, v, 1.0, g->p));     // p - omega v
+        TRY(axpby(g, N, 1.0, g->r, beta, g->p));    // r + beta (p - omega v)
+      }
+      TRY(apply_A(c, g->p, v));
+      if (pd > 0) TRY(project_Q(v, e1.data()));
+      double rtv;
+      TRY(dot(rt, v, &rtv));
+      alpha = rho / rtv;
+      if (!isfinite(alpha)) { R.breakdown = true; break; }
+      TRY(copy_dev(g, sv, g->r, N));
+      TRY(axpby(g, N, -alpha, v, 1.0, sv));
+      double ss;
+      TRY(dot(sv, sv, &ss));
+      if (sqrt(ss) <= tol * bnorm) {
+        TRY(axpby(g, N, alpha, g->p, 1.0, g->x));
+        TRY(copy_dev(g, g->r, sv, N));
+        for (int i = 0; i < pd; ++i) xi[i] += alpha * e1[i];
+        R.rel = sqrt(ss) / bnorm;
+        R.converged = true;
+        break;
+      }
+      TRY(apply_A(c, sv, tv));
+      if (pd > 0) TRY(project_Q(tv, e2.data()));
+      double ts, tt;
+      TRY(dot(tv, sv, &ts));
+      TRY(dot(tv, tv, &tt));
+      omega = ts / tt;
+      if (!isfinite(omega) || omega == 0.0) { R.breakdown = true; break; }
+      for (int i = 0; i < pd; ++i) xi[i] += alpha * e1[i] + omega * e2[i];
+      TRY(axpby(g, N, alpha, g->p, 1.0, g->x));
+      TRY(axpby(g, N, omega, sv, 1.0, g->x));
+      TRY(copy_dev(g, g->r, sv, N));
+      TRY(axpby(g, N, -omega, tv, 1.0, g->r));
+      TRY(dot(g->r, g->r, &rr));
+      R.rel = sqrt(rr) / bnorm;
+      if (!isfinite(R.rel)) { R.breakdown = true; break; }
+      if (R.rel <= tol) R.converged = true;
+      rho_old = rho;
+      if (log_on() && R.iters % 10 == 0) fprintf(stderr, "[whv] ABICGSTAB %d: rel %.3e\n", R.iters, R.rel);
+    }
+    if (pd > 0) {   // x <- x - W R^{-1} xi  (R upper triangular)
+      std::vector<double> y(pd);
+      for (int i = pd - 1; i >= 0; --i) {
+        double acc = xi[i];
+        for (int l = i + 1; l < pd; ++l) acc -= B.Raw[(size_t)l * pd + i] * y[l];
+        y[i] = acc / B.Raw[(size_t)i * pd + i];
+      }
+      TRY(to_dev(g, g->small, y.data(), pd));
+      TRY(expand(g, B.V, pd, g->small, -1.0, g->x));
+    }
   } else {  // FPI, Algorithm 1: x <- Pi_h(x; f_d)
     const double bnorm = sqrt(bb);
     while (R.iters < maxit) {
@@ -633,7 +741,7 @@ static whv_status outer_solve(SolveCtx& c, int method, const whv_params* p, cons
   // modal correction of the deflated components: only valid for exact eigenvectors (with
   // approximate ones W diag(1/mu) W^T M is not a Galerkin solve and the passes can diverge);
   // approximate bases deflate through Algorithm 4 (method DCG) instead
-  const bool defl = B.nd > 0 && method != WHV_DCG && method != WHV_AGMRES && (B.flags & WHV_BASIS_EXACT);
+  const bool defl = B.nd > 0 && method != WHV_DCG && !augmented(method) && (B.flags & WHV_BASIS_EXACT);
   const double inner_tol = fp64_res ? (p->inner_tol > 0.0 ? p->inner_tol : 1e-3) : p->tol;
   if (!use_x0) WHV_CUDA(g, cudaMemsetAsync(g->xo, 0, N * sizeof(double), g->stream));
   bool have_x = use_x0;
@@ -712,7 +820,7 @@ extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f
   TRY(make_time_grid(g, p, &tg));
   if (!(p->tol >= 0.0) || p->maxit < 0) return fail(g, WHV_ERR_INVALID, "tol must be >= 0, maxit >= 0");
   const int method = p->method;
-  if (method < WHV_FPI || method > WHV_AGMRES) return fail(g, WHV_ERR_INVALID, "unknown method");
+  if (method < WHV_FPI || method > WHV_ABICGSTAB) return fail(g, WHV_ERR_INVALID, "unknown method");
   Basis& B = g->basis;
   const bool has_basis = B.nd > 0;
   if (has_basis && (B.omega != p->omega || B.periods != p->periods ||
@@ -721,11 +829,11 @@ extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f
   if (method == WHV_DCG && !has_basis) return fail(g, WHV_ERR_INVALID, "DCG needs a deflation basis");
   const bool refine = (p->flags & WHV_REFINE_FP64) != 0;
   if (refine && method == WHV_FPI)
-    return fail(g, WHV_ERR_INVALID, "FP64 residual correction needs a Krylov method (CG, DCG, GMRES, AGMRES)");
+    return fail(g, WHV_ERR_INVALID, "FP64 residual correction needs a Krylov method (CG, DCG, (A)GMRES, ABICGSTAB)");
   // DCG and AGMRES use the basis inside the iteration; the others deflate the forcing (DEVD)
-  const bool devd = has_basis && method != WHV_DCG && method != WHV_AGMRES;
+  const bool devd = has_basis && method != WHV_DCG && !augmented(method);
   const int64_t N = g->N;
-  SolveCtx c{g, tg, has_basis && (B.flags & WHV_BASIS_REDEFLATE) != 0 && method != WHV_AGMRES};
+  SolveCtx c{g, tg, has_basis && (B.flags & WHV_BASIS_REDEFLATE) != 0 && !augmented(method)};
   double* b = g->t;  // b of the iterated system
 
   // ---- forcing (Algorithm 2: deflate the forcing)
@@ -825,8 +933,8 @@ extern "C" whv_status whv_solve_adjoint(whv_grid g, const whv_params* p, const d
   TimeGridH tg;
   TRY(make_time_grid(g, p, &tg));
   const int method = p->method;
-  if (method != WHV_CG && method != WHV_DCG && method != WHV_GMRES && method != WHV_AGMRES)
-    return fail(g, WHV_ERR_INVALID, "the adjoint solve needs a Krylov method (CG, DCG, GMRES, AGMRES)");
+  if (method == WHV_FPI || method < 0 || method > WHV_ABICGSTAB)
+    return fail(g, WHV_ERR_INVALID, "the adjoint solve needs a Krylov method (CG, DCG, (A)GMRES, ABICGSTAB)");
   const Basis& B = g->basis;
   if (B.nd > 0 && (B.omega != p->omega || B.periods != p->periods || B.adjust != (p->adjust_omega ? 1 : 0) ||
                    B.cfl != tg.cfl))
@@ -837,7 +945,7 @@ extern "C" whv_status whv_solve_adjoint(whv_grid g, const whv_params* p, const d
   const bool refine = (p->flags & WHV_REFINE_FP64) != 0;
   const int64_t N = g->N;
   TRY(ensure_fp64_buffers(g));
-  SolveCtx c{g, tg, B.nd > 0 && (B.flags & WHV_BASIS_REDEFLATE) != 0 && method != WHV_AGMRES};
+  SolveCtx c{g, tg, B.nd > 0 && (B.flags & WHV_BASIS_REDEFLATE) != 0 && !augmented(method)};
   // (I - S)^T lambda = g  <=>  (I - S) y = c^2 g,  lambda = y / c^2
   TRY(scale_by(g, dLdu, g->c2, 1.0, g->t));
   TRY(dot_async(g, g->t, g->t, S_RR0));

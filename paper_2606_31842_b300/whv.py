@@ -16,12 +16,13 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "lib
 
 WHV_OK, WHV_ERR_INVALID, WHV_ERR_CUDA, WHV_ERR_OOM, WHV_ERR_NOT_CONVERGED, WHV_ERR_BREAKDOWN, WHV_ERR_TIMEOUT = range(7)
 WHV_FP64, WHV_FP32_STEP = 0, 1
-WHV_FPI, WHV_CG, WHV_DCG, WHV_GMRES, WHV_AGMRES = 0, 1, 2, 3, 4
+WHV_FPI, WHV_CG, WHV_DCG, WHV_GMRES, WHV_AGMRES, WHV_ABICGSTAB = 0, 1, 2, 3, 4, 5
 WHV_BASIS_NONE, WHV_BASIS_USER, WHV_BASIS_CLOSED_FORM, WHV_BASIS_LANCZOS = 0, 1, 2, 3
 WHV_BASIS_EXACT, WHV_BASIS_REDEFLATE = 1, 2
 WHV_TRUE_RESIDUAL, WHV_REFINE_FP64 = 1, 2
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "NOT_CONVERGED", "BREAKDOWN", "TIMEOUT"]
-METHODS = {"fpi": WHV_FPI, "cg": WHV_CG, "dcg": WHV_DCG, "gmres": WHV_GMRES, "agmres": WHV_AGMRES}
+METHODS = {"fpi": WHV_FPI, "cg": WHV_CG, "dcg": WHV_DCG, "gmres": WHV_GMRES, "agmres": WHV_AGMRES,
+           "abicgstab": WHV_ABICGSTAB}
 
 
 class whv_params(ctypes.Structure):

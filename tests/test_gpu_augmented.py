@@ -1,6 +1,7 @@
-"""Algorithm 5 (augmented GMRES) on the device against the oracle's: fixed-iteration iterates with
-restarts (exact eigenvectors, general vectors, variable speed, 3-D), GMRES as the unaugmented
-case, and the FP32-stepping form inside FP64 residual correction with a device Lanczos basis."""
+"""Augmented Krylov methods on the device against the oracle's: Algorithm 5 (AGMRES) and
+Algorithm 6 (ABICGSTAB), fixed-iteration iterates (exact eigenvectors, general vectors, variable
+speed, 1-D/2-D/3-D, restarts), the unaugmented cases, convergence to the direct solution and the
+FP32-stepping form inside FP64 residual correction with a device Lanczos basis."""
 import numpy as np
 import pytest
 import torch
@@ -117,3 +118,56 @@ def test_agmres_lanczos_basis_fp32_with_fp64_correction():
     assert info["status"] == "OK", info
     assert info["true_rel_residual"] < 2e-9
     assert IND.relmax(u.cpu().numpy(), U) < 1e-6
+
+
+@pytest.mark.parametrize("npts,omega,nd,k", [((41, 37), 14.0, 6, 7), ((13, 11, 12), 8.0, 5, 5), ((201,), 10.5, 0, 6)])
+def test_abicgstab_exact_basis_fixed_iterations(npts, omega, nd, k):
+    og = O.Grid(npts)
+    tg = WH.time_grid_for(og, omega)
+    f = I.gaussian(npts, [0.42, 0.57, 0.5][: len(npts)], 0.1, omega ** 2)
+    W = lam2 = None
+    if nd:
+        modes, lam2, _ = SP.select_modes(og, tg, nd)
+        W = SP.basis(og, modes)
+    ref = K.augmented_solve(og, tg, f, W, lam2, tol=0.0, maxit=k, method="abicgstab")
+    g = whv.Grid(npts, precision=whv.WHV_FP64)
+    prm = whv.make_params(omega, method="abicgstab", tol=0.0, maxit=k)
+    if nd:
+        g.whv_set_deflation_basis(prm, nd, whv.WHV_BASIS_CLOSED_FORM)
+    u, info = g.whv_solve(prm, dev(f))
+    assert info["iterations"] == k == ref.solve.iterations
+    assert IND.relmax(u.cpu().numpy(), ref.u) < 1e-11
+
+
+def test_abicgstab_general_basis_variable_speed_fixed_iterations():
+    npts, order = (37, 33), 4
+    c2 = I.speed_squared("c3", npts, 8)
+    og = O.Grid(npts, order=order, c2=c2)
+    omega = 14.0
+    tg = WH.time_grid_for(og, omega)
+    f = I.gaussian(npts, [0.45, 0.55], 0.1, omega ** 2)
+    nd, k = 5, 6
+    W = _m_orthonormal(og, nd, 12)
+    ref = K.augmented_solve(og, tg, f, W, None, tol=0.0, maxit=k, method="abicgstab")
+    g = whv.Grid(npts, order=order, precision=whv.WHV_FP64)
+    g.whv_set_speed(dev(c2))
+    prm = whv.make_params(omega, method="abicgstab", tol=0.0, maxit=k)
+    g.whv_set_deflation_basis(prm, nd, whv.WHV_BASIS_USER, V=dev(W.T), lambda2=np.linspace(1, 2, nd))
+    u, info = g.whv_solve(prm, dev(f))
+    assert info["iterations"] == k
+    assert IND.relmax(u.cpu().numpy(), ref.u) < 1e-11
+
+
+def test_abicgstab_fp32_with_fp64_correction_reaches_direct_solution():
+    npts, omega = (97, 89), 20.0
+    og = O.Grid(npts)
+    tg = WH.time_grid_for(og, omega)
+    f = I.gaussian(npts, [0.4, 0.6], 0.05, omega ** 2)
+    U = IND.helmholtz_direct(npts, tg.omega_eff, f)
+    g = whv.Grid(npts, precision=whv.WHV_FP32_STEP)
+    prm = whv.make_params(omega, method="abicgstab", tol=1e-10, maxit=4000, true_residual=True, refine_fp64=True)
+    g.whv_set_deflation_basis(prm, 12, whv.WHV_BASIS_CLOSED_FORM)
+    u, info = g.whv_solve(prm, dev(f))
+    assert info["status"] == "OK", info
+    assert info["true_rel_residual"] < 2e-10
+    assert IND.relmax(u.cpu().numpy(), U) < 1e-7

@@ -196,14 +196,20 @@ whv_status whv_solve(whv_grid grid, const whv_params* p, const double* f_dev, in
  * per time step, k = 0 restores the default (8 for FP32 stepping, 1 for FP64), k <= 16.  Only
  * 2-D grids block; other grids always step once per launch.  With the default (k = 0) grids of at
  * most 4096 unknowns run each whole wave solve in a single CTA (state in shared memory, one
- * barrier per step); an explicit k turns that off.  whv_get_steps_per_sweep returns the value in
- * effect (0 on such small grids). */
+ * barrier per step); an explicit k turns that off.
+ * k < 0 (2-D grids, -16 <= k): the persistent kernel -- the whole wave solve (forced or not) is
+ * ONE cooperative launch with one 1024-thread CTA per 64 x 64 staged tile, the tile state kept in
+ * registers for all steps and the halo exchanged through L2 every |k| steps at a grid barrier
+ * (bounded wait; see whv_inject_barrier_error).  Used while the tiles fit on the GPU at once
+ * (e.g. 511^2 unknowns with |k| <= 10 on 148 SMs), otherwise the default path runs.
+ * whv_get_steps_per_sweep returns the value in effect (0 on the small grids above). */
 whv_status whv_set_steps_per_sweep(whv_grid grid, int k);
 whv_status whv_get_steps_per_sweep(whv_grid grid, int* k);
 
 /* Autotuner: times f = 0 wave solves of p's time grid for each candidate steps-per-sweep value
- * (1, 2, 4, 6, 8, 10, 12, 16 on 2-D grids; small grids keep the single-CTA solve, *best = 0) with
- * CUDA events on the grid's stream and keeps the fastest; *best (host, may be NULL) receives it.  Overwrites the grid's internal work vectors,
+ * (1, 2, 4, 6, 8, 10, 12, 16 on 2-D grids, and the persistent kernel -4 ... -12 where its tiles
+ * fit; small grids keep the single-CTA solve, *best = 0) with CUDA events on the grid's stream and
+ * keeps the fastest; *best (host, may be NULL) receives it.  Overwrites the grid's internal work vectors,
  * synchronises the stream.  Must not be called while the grid's stream is being captured. */
 whv_status whv_autotune(whv_grid grid, const whv_params* p, int* best);
 
@@ -278,6 +284,13 @@ whv_status whv_dot(whv_grid grid, const double* x_dev, const double* y_dev, doub
  * reported through whv_last_error(NULL). */
 whv_status whv_project_noalloc(int64_t n, int nd, const double* W_dev, const double* r_dev,
                                const double* w_dev, double* coef_dev, void* cuda_stream);
+
+/* Test hook for the failure path of the persistent wave solve (no counterpart in the paper):
+ * raises the grid's barrier error flag, so that the next persistent wave solve on this grid leaves
+ * at its first grid barrier exactly as after a barrier wait that timed out -- its output is NaN
+ * and the whv_solve / whv_solve_adjoint / whv_lanczos call that ran it returns WHV_ERR_TIMEOUT and
+ * re-arms the barrier.  No GPU wait is made to run out. */
+whv_status whv_inject_barrier_error(whv_grid grid);
 
 /* Number of interior unknowns N of the grid (0 for NULL). */
 int64_t whv_num_unknowns(whv_grid grid);

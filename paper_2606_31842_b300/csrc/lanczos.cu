@@ -225,7 +225,7 @@ static void top_eigenpairs(const std::vector<double>& a, const std::vector<doubl
 
 using namespace whv;
 
-extern "C" whv_status whv_lanczos(whv_grid g, const whv_params* p, int nd, int m, const double* v0_dev,
+static whv_status lanczos_impl(whv_grid g, const whv_params* p, int nd, int m, const double* v0_dev,
                                   int fp64_stepping, int flags, double* theta_host, double* resid_host) {
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
   TimeGridH tg;
@@ -354,4 +354,12 @@ extern "C" whv_status whv_lanczos(whv_grid g, const whv_params* p, int nd, int m
 #undef LZ_TRY
 #undef LZ_CUDA
   return WHV_OK;
+}
+
+extern "C" whv_status whv_lanczos(whv_grid g, const whv_params* p, int nd, int m, const double* v0_dev,
+                                  int fp64_stepping, int flags, double* theta_host, double* resid_host) {
+  const whv_status s = lanczos_impl(g, p, nd, m, v0_dev, fp64_stepping, flags, theta_host, resid_host);
+  if (!g) return s;
+  const whv_status e = take_persist_error(g);   // a persistent wave solve that gave up
+  return e != WHV_OK ? e : s;
 }

@@ -811,8 +811,8 @@ static whv_status outer_solve(SolveCtx& c, int method, const whv_params* p, cons
 
 using namespace whv;
 
-extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f, int use_guess,
-                                double* u, whv_info* info) {
+static whv_status solve_impl(whv_grid g, const whv_params* p, const double* f, int use_guess, double* u,
+                             whv_info* info) {
   const double t0 = now_s();
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
   if (!f || !u) return fail(g, WHV_ERR_INVALID, "f_dev and u_dev must not be NULL");
@@ -924,9 +924,9 @@ whv_status adjoint_gradients(whv_grid g, const TimeGridH& tg, const double* u, c
 whv_status scale_by(whv_grid g, const double* x, const double* y, double a, double* out);
 }  // namespace whv
 
-extern "C" whv_status whv_solve_adjoint(whv_grid g, const whv_params* p, const double* f, const double* u,
-                                        const double* dLdu, double* z, double* grad_c2, double* grad_f,
-                                        int checkpoint_every, whv_info* info) {
+static whv_status adjoint_impl(whv_grid g, const whv_params* p, const double* f, const double* u,
+                               const double* dLdu, double* z, double* grad_c2, double* grad_f,
+                               int checkpoint_every, whv_info* info) {
   const double t0 = now_s();
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
   if (!u || !dLdu || !z) return fail(g, WHV_ERR_INVALID, "u_dev, dLdu_dev and z_dev must not be NULL");
@@ -978,5 +978,32 @@ extern "C" whv_status whv_solve_adjoint(whv_grid g, const whv_params* p, const d
   (void)N;
   if (R.breakdown) return fail(g, WHV_ERR_BREAKDOWN, "Krylov breakdown in the adjoint solve");
   if (!R.converged) return fail(g, WHV_ERR_NOT_CONVERGED, "adjoint solve: maxit reached before the tolerance");
+  return WHV_OK;
+}
+
+// A persistent wave solve that gave up at a grid barrier makes its output NaN, which surfaces as
+// a breakdown or a non-finite right-hand side; report it as the timeout it was.
+extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f, int use_guess,
+                                double* u, whv_info* info) {
+  const whv_status s = solve_impl(g, p, f, use_guess, u, info);
+  if (!g) return s;
+  const whv_status e = take_persist_error(g);
+  return e != WHV_OK ? e : s;
+}
+
+extern "C" whv_status whv_solve_adjoint(whv_grid g, const whv_params* p, const double* f, const double* u,
+                                        const double* dLdu, double* z, double* grad_c2, double* grad_f,
+                                        int checkpoint_every, whv_info* info) {
+  const whv_status s = adjoint_impl(g, p, f, u, dLdu, z, grad_c2, grad_f, checkpoint_every, info);
+  if (!g) return s;
+  const whv_status e = take_persist_error(g);
+  return e != WHV_OK ? e : s;
+}
+
+extern "C" whv_status whv_inject_barrier_error(whv_grid g) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  const unsigned one = 1u;
+  WHV_CUDA(g, cudaMemcpyAsync(g->gbar + 2, &one, sizeof(unsigned), cudaMemcpyHostToDevice, g->stream));
+  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
   return WHV_OK;
 }

@@ -361,6 +361,11 @@ static whv_status launch_wave_solve(whv_grid g, const TimeGridH& tg, const doubl
     *nl = 1;
     return small_wave_solve(g, tg, v, f, out, epi, prec);
   }
+  // persistent 2-D wave solve (one cooperative launch) when selected and the tiles fit
+  if (prec == g->precision && g->kblock < 0 && persist_fits(g, -g->kblock, prec) && small_tables(g, tg) >= 0) {
+    *nl = 1;
+    return persist_wave_solve(g, tg, v, f, out, epi, -g->kblock, prec, g->wbuf);
+  }
   if (prec == g->precision) {
     const BufSet B{g->wbuf, g->acc, g->kblock > 0 ? g->kblock : default_kblock(g)};
     return prec == WHV_FP64 ? dispatch<double>(g, tg, v, f, out, epi, nl, B)
@@ -401,15 +406,30 @@ void free_plan(whv_grid g) {
   g->plan = nullptr;
 }
 
+static bool uses_tables(whv_grid g) {
+  return (small_grid(g) && g->kblock == 0) || (g->dim == 2 && g->kblock < 0);
+}
+
+whv_status take_persist_error(whv_grid g) {
+  double e = 0.0;
+  WHV_CUDA(g, cudaMemcpyAsync(&e, g->scal + S_ERR, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
+  if (e == 0.0) return WHV_OK;
+  // re-arm the barrier and the flag so that the grid can be used again
+  WHV_CUDA(g, cudaMemsetAsync(g->gbar, 0, 4 * sizeof(unsigned), g->stream));
+  WHV_CUDA(g, cudaMemsetAsync(g->scal + S_ERR, 0, sizeof(double), g->stream));
+  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
+  return fail(g, WHV_ERR_TIMEOUT, "persistent wave solve: a grid barrier wait gave up (results were NaN)");
+}
+
 whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
                       double* out, int epi, int prec) {
   if (prec < 0) prec = g->precision;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   WHV_CUDA(g, cudaStreamIsCapturing(g->stream, &cs));
-  // small grids: a new time grid replaces the device weight table, so graphs captured with the
-  // old one are dropped before anything is replayed
-  if (cs == cudaStreamCaptureStatusNone && small_grid(g) && g->kblock == 0 && small_tables(g, tg) == 1)
-    free_plan(g);
+  // small grids and the persistent kernel read the device weight table: a new time grid replaces
+  // it, so graphs captured with the old one are dropped before anything is replayed
+  if (cs == cudaStreamCaptureStatusNone && uses_tables(g) && small_tables(g, tg) == 1) free_plan(g);
   if (cs != cudaStreamCaptureStatusNone) {  // caller is capturing: record the launches into its graph
     int nl = 0;
     whv_status s = launch_wave_solve(g, tg, v, f, out, epi, &nl, prec);
@@ -475,14 +495,15 @@ extern "C" whv_status whv_apply_pi(whv_grid g, const whv_params* p, const double
 
 extern "C" whv_status whv_set_steps_per_sweep(whv_grid g, int k) {
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
-  if (k < 0 || k > 16) return fail(g, WHV_ERR_INVALID, "steps per sweep must be in [0, 16]");
+  if (k < -16 || k > 16) return fail(g, WHV_ERR_INVALID, "steps per sweep must be in [-16, 16]");
+  if (k < 0 && g->dim != 2) return fail(g, WHV_ERR_INVALID, "the persistent kernel (k < 0) is 2-D only");
   g->kblock = k;
   return WHV_OK;
 }
 
 extern "C" whv_status whv_get_steps_per_sweep(whv_grid g, int* k) {
   if (!g || !k) return fail(g, WHV_ERR_INVALID, "NULL argument");
-  *k = g->kblock > 0 ? g->kblock : (small_grid(g) ? 0 : default_kblock(g));
+  *k = g->kblock != 0 ? g->kblock : (small_grid(g) ? 0 : default_kblock(g));
   return WHV_OK;
 }
 
@@ -498,10 +519,14 @@ extern "C" whv_status whv_autotune(whv_grid g, const whv_params* p, int* best) {
     if (best) *best = 0;
     return WHV_OK;
   }
-  const int cands2d[] = {1, 2, 4, 6, 8, 10, 12, 16};
-  const int cands_other[] = {1};
-  const int* cands = g->dim == 2 ? cands2d : cands_other;
-  const int nc = g->dim == 2 ? 8 : 1;
+  // 2-D: per step, blocked sweeps of k steps, and the persistent kernel (-k) where its tiles fit
+  std::vector<int> cands = {1};
+  if (g->dim == 2) {
+    for (int k : {2, 4, 6, 8, 10, 12, 16}) cands.push_back(k);
+    for (int k : {4, 6, 8, 10, 12})
+      if (persist_fits(g, k, g->precision)) cands.push_back(-k);
+  }
+  const int nc = (int)cands.size();
   cudaEvent_t e0, e1;
   WHV_CUDA(g, cudaEventCreate(&e0));
   WHV_CUDA(g, cudaEventCreate(&e1));

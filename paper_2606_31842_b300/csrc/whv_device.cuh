@@ -62,4 +62,40 @@ __device__ __forceinline__ bool grid_reduce(double bsum, double* partials, unsig
   return true;
 }
 
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident) with a bounded wait: count
+// and gen are the arrival counter and generation, err an error flag.  Returns false (and raises
+// *err) if this CTA waited past the limit (~4 s) or another CTA raised *err; every CTA then
+// returns false at its next barrier.
+constexpr unsigned long long kBarrierSpins = 1ull << 26;   // x 64 ns sleeps
+
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* err, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    volatile unsigned* vgen = gen;
+    const unsigned g0 = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(count, 1u) + 1u;
+    int ok = 1;
+    if (arrived == nblocks) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (*vgen == g0) {
+        if (++spins > kBarrierSpins) { atomicExch(err, 1); ok = 0; break; }
+        // another CTA gave up: stop waiting for a barrier that will not complete
+        if ((spins & 1023ull) == 0 && *(volatile int*)err) { ok = 0; break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)err) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 }  // namespace whv

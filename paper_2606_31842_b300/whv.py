@@ -72,6 +72,7 @@ def _load():
         "whv_project_noalloc": [L, I, P, P, P, P, P],
         "whv_lanczos": [P, ctypes.POINTER(whv_params), I, I, P, I, I, ctypes.POINTER(D), ctypes.POINTER(D)],
         "whv_solve_adjoint": [P, ctypes.POINTER(whv_params), P, P, P, P, P, P, I, ctypes.POINTER(whv_info)],
+        "whv_inject_barrier_error": [P],
         "whv_solve_batched": [I, ctypes.POINTER(P), ctypes.POINTER(whv_params), ctypes.POINTER(P),
                               ctypes.POINTER(P), ctypes.POINTER(whv_info)],
     }
@@ -97,7 +98,8 @@ EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_gr
             "whv_set_deflation_basis", "whv_get_basis", "whv_apply_pi", "whv_solve", "whv_project",
             "whv_expand", "whv_dot", "whv_num_unknowns", "whv_last_error", "whv_version",
             "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune",
-            "whv_project_noalloc", "whv_lanczos", "whv_solve_adjoint", "whv_solve_batched"]
+            "whv_project_noalloc", "whv_lanczos", "whv_solve_adjoint", "whv_solve_batched",
+            "whv_inject_barrier_error"]
 
 
 def _check(status, handle=None, allow=()):
@@ -257,6 +259,9 @@ class Grid:
         k = ctypes.c_int()
         _check(lib.whv_get_steps_per_sweep(self.handle, ctypes.byref(k)), self.handle)
         return k.value
+
+    def whv_inject_barrier_error(self):
+        _check(lib.whv_inject_barrier_error(self.handle), self.handle)
 
     def whv_autotune(self, params):
         k = ctypes.c_int()

@@ -31,7 +31,6 @@
 #include <vector>
 
 #include "stencil_ops.cuh"
-#include "stencil_tile.cuh"
 #include "whv_device.cuh"
 #include "whv_internal.cuh"
 
@@ -150,7 +149,8 @@ __global__ void __launch_bounds__(256) k_batch_wave(const BProb<T>* __restrict__
 // ------------------------------------------------------------------ 2-D: k steps per sweep
 constexpr int kBReg = 64;                  // staged region edge
 constexpr int kBThreads = 1024;            // 32 warps
-constexpr int kBRows = kBReg * kBReg / kBThreads;   // cells per thread (4): a strip of rows
+constexpr int kBPitch = kBThreads / 64;    // rows between a thread's cells (16)
+constexpr int kBRows = kBReg / kBPitch;    // cells per thread (4)
 
 template <typename T>
 struct BTile {
@@ -183,9 +183,8 @@ __device__ __forceinline__ T d2b(const T* __restrict__ a, int l, int gi, int n, 
 
 // Sweep j of problem p covers steps n0 = j K .. n0 + kk - 1 (W^{n0} -> W^{n0+kk}), kk = min(K,
 // nt - n0).  Sweep 0 starts from W^0 = v with the Taylor step; the last sweep writes the FP64
-// epilogue instead of the state.  Thread t owns column t % 64 and the rows 4 (t / 64) .. + 3 of
-// the staged region for the whole sweep; the 5-point stencil steps in registers with edge
-// exchanges (stencil_tile.cuh), the 9-point-wide one through a shared-memory copy of the region.
+// epilogue instead of the state.  Thread (warp w, lane) owns column 32 (w & 1) + lane and rows
+// (w >> 1) + 16 r, r < 4, of the staged region for the whole sweep.
 template <typename T, int ORDER, bool VARC, bool FORCED>
 __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* __restrict__ P,
                                                                 const int* __restrict__ nact, int J, int K,
@@ -202,10 +201,10 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
   for (int p = threadIdx.x; p <= np; p += blockDim.x)
     s_tile0[p] = p < np ? P[p].tile0 : P[np - 1].tile0 + P[np - 1].ntiles;
   __syncthreads();
-  const int i = threadIdx.x & 63;    // column of the region
-  const int jb = threadIdx.x >> 6;   // strip: rows 4 jb .. 4 jb + 3
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = 32 * (warp & 1) + lane;
+  const int jb = warp >> 1;
   const int H = K * R, TW = kBReg - 2 * H;
-  __shared__ TileEdges<T> E[ORDER == 2 ? 2 : 1];
   for (int j = 0; j < J; ++j) {
     const int A = nact[j];
     const int64_t total = s_tile0[A];
@@ -236,15 +235,14 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
       const T* ptb = ptab + B.wofs;
       const int qi = (j + 1) & 1, qo = j & 1;   // input pair (written by sweep j - 1), output pair
       T cur[kBRows], prv[kBRows], acr[kBRows];
-      T cc[kBRows], ff[kBRows];
-      bool act[kBRows];
+      T cc[VARC ? kBRows : 1];
+      T ff[FORCED ? kBRows : 1];
       const T w0 = first ? wtb[0] : T(0);
 #pragma unroll
       for (int r = 0; r < kBRows; ++r) {
-        const int gy = y0 + kBRows * jb + r;
+        const int gy = y0 + jb + kBPitch * r;
         const bool in = colin && gy >= 0 && gy < ny;
         const int64_t gi = gx + (int64_t)nx * gy;
-        act[r] = in;
         if (first) {
           cur[r] = (in && B.v) ? (T)__ldg(B.v + gi) : T(0);
           prv[r] = T(0);
@@ -252,57 +250,58 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
           cur[r] = in ? __ldcg(B.w[2 * qi + 1] + gi) : T(0);
           prv[r] = in ? __ldcg(B.w[2 * qi] + gi) : T(0);
         }
-        cc[r] = (VARC && in) ? __ldg(B.c2 + gi) : T(0);
-        ff[r] = (FORCED && in) ? (T)__ldg(B.f + gi) : T(0);
+        if (VARC) cc[r] = in ? __ldg(B.c2 + gi) : T(0);
+        if (FORCED) ff[r] = in ? (T)__ldg(B.f + gi) : T(0);
         acr[r] = w0 * cur[r];
       }
-      if constexpr (ORDER == 2) {
-        const TileCoef<T> tc{B.ih2x, B.ih2y, B.dt2, B.ax, B.ay, B.b};
-        tile_steps_o2<T, VARC, FORCED>(cur, prv, acr, cc, ff, act, n0, kk, tc,
-                                       [&](int m) { return wtb[m]; }, [&](int m) { return ptb[m]; }, E);
-      } else {
 #pragma unroll
-        for (int r = 0; r < kBRows; ++r) S0[(kBRows * jb + r) * kBReg + i] = cur[r];
-        __syncthreads();
-        T* Ain = S0;
-        T* Bout = S1;
-        for (int s = 1; s <= kk; ++s) {
-          const int n = n0 + s - 1;   // W^n -> W^{n+1}
-          const int lo = s * R, hi = kBReg - s * R;
-          const bool colact = colin && i >= lo && i < hi;
-          const T ws = wtb[n + 1];
-          // forcing term dt^2 f cos(omega_hat t^n) (half of it in the Taylor step)
-          const T fph = FORCED ? (n > 0 ? B.dt2 : T(0.5) * B.dt2) * ptb[n] : T(0);
+      for (int r = 0; r < kBRows; ++r) S0[(jb + kBPitch * r) * kBReg + i] = cur[r];
+      __syncthreads();
+      T* Ain = S0;
+      T* Bout = S1;
+      for (int s = 1; s <= kk; ++s) {
+        const int n = n0 + s - 1;   // W^n -> W^{n+1}
+        const int lo = s * R, hi = kBReg - s * R;
+        const bool colact = colin && i >= lo && i < hi;
+        const T ws = wtb[n + 1];
+        // forcing term dt^2 f cos(omega_hat t^n) (half of it in the Taylor step)
+        const T fph = FORCED ? (n > 0 ? B.dt2 : T(0.5) * B.dt2) * ptb[n] : T(0);
 #pragma unroll
-          for (int r = 0; r < kBRows; ++r) {
-            const int jr = kBRows * jb + r;
-            const int gy = y0 + jr;
-            if (colact && jr >= lo && jr < hi && gy >= 0 && gy < ny) {
-              const int l = jr * kBReg + i;
-              const T c = cur[r];
+        for (int r = 0; r < kBRows; ++r) {
+          const int jr = jb + kBPitch * r;
+          const int gy = y0 + jr;
+          if (colact && jr >= lo && jr < hi && gy >= 0 && gy < ny) {
+            const int l = jr * kBReg + i;
+            const T c = cur[r];
+            T wn;
+            if (ORDER == 2 && !VARC && n > 0) {
+              T u = fma(B.b, c, -prv[r]);
+              u = fma(B.ax, (gx > 0 ? Ain[l - 1] : T(0)) + (gx < nx - 1 ? Ain[l + 1] : T(0)), u);
+              wn = fma(B.ay, (gy > 0 ? Ain[l - kBReg] : T(0)) + (gy < ny - 1 ? Ain[l + kBReg] : T(0)), u);
+            } else {
               T L = d2b<ORDER>(Ain, l, gx, nx, 1, c) * B.ih2x;
               L = fma(d2b<ORDER>(Ain, l, gy, ny, kBReg, c), B.ih2y, L);
               if (VARC) L *= cc[r];
-              T wn = n > 0 ? fma(B.dt2, L, fma(T(2), c, -prv[r]))
-                           : fma(T(0.5) * B.dt2, L, c);   // Taylor start: W^1 = W^0 + dt^2/2 L W^0
-              if (FORCED) wn = fma(-fph, ff[r], wn);
-              prv[r] = c;
-              cur[r] = wn;
-              Bout[l] = wn;
-              acr[r] = fma(ws, wn, acr[r]);
+              wn = n > 0 ? fma(B.dt2, L, fma(T(2), c, -prv[r]))
+                         : fma(T(0.5) * B.dt2, L, c);   // Taylor start: W^1 = W^0 + dt^2/2 L W^0
             }
+            if (FORCED) wn = fma(-fph, ff[r], wn);
+            prv[r] = c;
+            cur[r] = wn;
+            Bout[l] = wn;
+            acr[r] = fma(ws, wn, acr[r]);
           }
-          __syncthreads();
-          T* tmp = Ain;
-          Ain = Bout;
-          Bout = tmp;
         }
+        __syncthreads();
+        T* tmp = Ain;
+        Ain = Bout;
+        Bout = tmp;
       }
       double part = 0.0;
       const bool coltile = colin && i >= H && i < kBReg - H;
 #pragma unroll
       for (int r = 0; r < kBRows; ++r) {
-        const int jr = kBRows * jb + r;
+        const int jr = jb + kBPitch * r;
         const int gy = y0 + jr;
         if (!(coltile && jr >= H && jr < kBReg - H && gy >= 0 && gy < ny)) continue;
         const int64_t gi = gx + (int64_t)nx * gy;
@@ -581,7 +580,7 @@ static whv_status make_wave(BatchCtx& c, const RoleIO& io, Wave* out) {
   B_CUDA(c.g0, cudaMemcpy(w.fin, fin.data(), np * sizeof(BFin), cudaMemcpyHostToDevice));
   int per_sm = 0;
   if (blocked) {
-    w.smem = ORDER == 2 ? 0 : 2 * (size_t)kBReg * kBReg * sizeof(T);   // order 2 exchanges edges only
+    w.smem = 2 * (size_t)kBReg * kBReg * sizeof(T);
     if (forced) {
       w.launch = &launch_block2d<T, ORDER, VARC, true>;
       B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_block2d<T, ORDER, VARC, true>,

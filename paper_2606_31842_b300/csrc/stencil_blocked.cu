@@ -3,16 +3,14 @@
 //
 // Each CTA stages a REG x REG region (a tile of (REG - 2H)^2 nodes plus a halo of width
 // H = k r; r = 1 for the 5-point, 2 for the 9-point-wide 4th-order stencil) and advances it k
-// leapfrog steps; after step s the cells at distance >= s r from the region edge are exact,
-// which is what the next step needs.  Thread t owns column t % 64 and the strip of rows
-// 4 (t / 64) .. + 3 of the region: W^n, W^{n-1} and the filter sum of its cells stay in
-// registers for the whole launch.  The 5-point stencil steps with edge exchanges only
-// (registers inside the strip, warp shuffles along x, shared memory across strips and across the
-// two warps of a row: stencil_tile.cuh); the 9-point-wide stencil reads a double-buffered
-// shared-memory copy of W^n.  All global loads of a thread are issued before the first use.  The
-// tile's W^{n+k-1}, W^{n+k} go to the other buffer pair (neighbouring CTAs still read the old
-// pair), the filter sums are added to acc -- or, on the last sweep, the FP64 epilogue (Pi_h v, or
-// A v with the p^T M A p reduction) is written like the single-step kernel does.
+// leapfrog steps; at sub-step s only the window [s r, REG - s r)^2 is updated, which is exactly
+// what the next sub-step needs.  Thread (warp w, lane) owns column 32 (w & 1) + lane and rows
+// (w >> 1) + 16 t, t < 4, of the region for the whole launch: W^n, W^{n-1} and the filter sum of
+// its cells stay in registers, and only W^n goes through shared memory (double-buffered) for the
+// neighbours' reads.  All global loads of a thread are issued before the first use.  The tile's
+// W^{n+k-1}, W^{n+k} go to the other buffer pair (neighbouring CTAs still read the old pair),
+// the filter sums are added to acc -- or, on the last sweep, the FP64 epilogue (Pi_h v, or A v
+// with the p^T M A p reduction) is written like the single-step kernel does.
 //
 // Global traffic per k steps and tile node: 3 reads + 3 writes (+ c^2), plus the halo re-reads
 // (REG^2 / tile^2), instead of 5 accesses per step; the price is the redundant halo updates.
@@ -21,7 +19,6 @@
 #include <algorithm>
 #include <vector>
 
-#include "stencil_tile.cuh"
 #include "whv_device.cuh"
 #include "whv_internal.cuh"
 
@@ -30,7 +27,8 @@ namespace whv {
 constexpr int kBlkMaxK = 16;
 constexpr int kReg = 64;            // staged region edge
 constexpr int kBlkThreads = 1024;   // 32 warps
-constexpr int kRowsPerThread = kReg * kReg / kBlkThreads;   // cells per thread (4): a strip of rows
+constexpr int kRowPitch = kBlkThreads / 64;   // rows between a thread's cells (16)
+constexpr int kRowsPerThread = kReg / kRowPitch;
 
 template <typename T>
 struct BlockCoef {
@@ -66,76 +64,72 @@ __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ g
                                                          BlockCoef<T> cf, double* partials,
                                                          unsigned* counter, double* scal_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S0 = reinterpret_cast<T*>(smem_raw);
+  T* S1 = S0 + kReg * kReg;
   __shared__ T sw[kBlkMaxK];
   constexpr int R = ORDER == 2 ? 1 : 2;
   const int H = cf.k * R;
   const int TW = kReg - 2 * H;
   const int x0 = blockIdx.x * TW - H, y0 = blockIdx.y * TW - H;   // region origin (global)
-  const int i = threadIdx.x & 63;          // column of the region
-  const int jb = threadIdx.x >> 6;         // strip: rows 4 jb .. 4 jb + 3
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = 32 * (warp & 1) + lane;
+  const int jb = warp >> 1;
   const int gx = x0 + i;
   const bool colin = gx >= 0 && gx < nx;
   if (threadIdx.x < kBlkMaxK) sw[threadIdx.x] = cf.w[threadIdx.x];
   T cur[kRowsPerThread], prv[kRowsPerThread], acr[kRowsPerThread];
-  T cc[kRowsPerThread];
-  bool act[kRowsPerThread];
+  T cc[VARC ? kRowsPerThread : 1];
 #pragma unroll
   for (int t = 0; t < kRowsPerThread; ++t) {
-    const int gy = y0 + kRowsPerThread * jb + t;
+    const int gy = y0 + jb + kRowPitch * t;
     const bool in = colin && gy >= 0 && gy < ny;
     const int64_t gi = gx + (int64_t)nx * gy;
-    act[t] = in;
     cur[t] = in ? gcur[gi] : T(0);
     prv[t] = in ? gprev[gi] : T(0);
-    cc[t] = (VARC && in) ? c2[gi] : T(0);
+    if (VARC) cc[t] = in ? c2[gi] : T(0);
     acr[t] = T(0);
   }
-  if constexpr (ORDER == 2) {
-    __shared__ TileEdges<T> E[2];
-    __syncthreads();   // sw
-    TileCoef<T> tc{cf.ih2x, cf.ih2y, cf.dt2, cf.ax, cf.ay, cf.b};
-    const T zero[kRowsPerThread] = {};
-    // the steps of this launch are n = n_start .. n_start + k - 1 >= 1; sw[q] = w_{n_start + 1 + q}
-    tile_steps_o2<T, VARC, false>(cur, prv, acr, cc, zero, act, 1, cf.k, tc,
-                                  [&](int m) { return sw[m - 2]; }, [](int) { return T(0); }, E);
-  } else {
-    T* S0 = reinterpret_cast<T*>(smem_raw);
-    T* S1 = S0 + kReg * kReg;
 #pragma unroll
-    for (int t = 0; t < kRowsPerThread; ++t) S0[(kRowsPerThread * jb + t) * kReg + i] = cur[t];
-    __syncthreads();
-    T* A = S0;
-    T* B = S1;
-    for (int s = 1; s <= cf.k; ++s) {
-      const int lo = s * R, hi = kReg - s * R;
-      const bool colact = colin && i >= lo && i < hi;
-      const T ws = sw[s - 1];
+  for (int t = 0; t < kRowsPerThread; ++t) S0[(jb + kRowPitch * t) * kReg + i] = cur[t];
+  __syncthreads();
+  T* A = S0;
+  T* B = S1;
+  for (int s = 1; s <= cf.k; ++s) {
+    const int lo = s * R, hi = kReg - s * R;
+    const bool colact = colin && i >= lo && i < hi;
+    const T ws = sw[s - 1];
 #pragma unroll
-      for (int t = 0; t < kRowsPerThread; ++t) {
-        const int j = kRowsPerThread * jb + t;
-        const int gy = y0 + j;
-        if (colact && j >= lo && j < hi && gy >= 0 && gy < ny) {
-          const int l = j * kReg + i;
-          const T c = cur[t];
+    for (int t = 0; t < kRowsPerThread; ++t) {
+      const int j = jb + kRowPitch * t;
+      const int gy = y0 + j;
+      if (colact && j >= lo && j < hi && gy >= 0 && gy < ny) {
+        const int l = j * kReg + i;
+        const T c = cur[t];
+        T wn;
+        if constexpr (ORDER == 2 && !VARC) {
+          T u = fma(cf.b, c, -prv[t]);
+          u = fma(cf.ax, (gx > 0 ? A[l - 1] : T(0)) + (gx < nx - 1 ? A[l + 1] : T(0)), u);
+          wn = fma(cf.ay, (gy > 0 ? A[l - kReg] : T(0)) + (gy < ny - 1 ? A[l + kReg] : T(0)), u);
+        } else {
           T L = d2s<ORDER>(A, l, gx, nx, 1, c) * cf.ih2x;
           L = fma(d2s<ORDER>(A, l, gy, ny, kReg, c), cf.ih2y, L);
           if (VARC) L *= cc[t];
-          const T wn = fma(cf.dt2, L, fma(T(2), c, -prv[t]));
-          prv[t] = c;
-          cur[t] = wn;
-          B[l] = wn;
-          acr[t] = fma(ws, wn, acr[t]);
+          wn = fma(cf.dt2, L, fma(T(2), c, -prv[t]));
         }
+        prv[t] = c;
+        cur[t] = wn;
+        B[l] = wn;
+        acr[t] = fma(ws, wn, acr[t]);
       }
-      __syncthreads();
-      T* tmp = A; A = B; B = tmp;
     }
+    __syncthreads();
+    T* tmp = A; A = B; B = tmp;
   }
   double part = 0.0;
   const bool coltile = colin && i >= H && i < kReg - H;
 #pragma unroll
   for (int t = 0; t < kRowsPerThread; ++t) {
-    const int j = kRowsPerThread * jb + t;
+    const int j = jb + kRowPitch * t;
     const int gy = y0 + j;
     if (!(coltile && j >= H && j < kReg - H && gy >= 0 && gy < ny)) continue;
     const int64_t gi = gx + (int64_t)nx * gy;
@@ -201,7 +195,7 @@ template <typename T, int ORDER, bool VARC, int KIND>
 static cudaError_t launch_block(whv_grid g, const T* gp, const T* gc, T* op, T* oc, T* acc,
                                 const T* c2, const double* v, double* out, const BlockCoef<T>& cf,
                                 double* partials, unsigned* counter, double* scal_out) {
-  const size_t smem = ORDER == 2 ? 0 : blk_smem(sizeof(T));   // order 2 exchanges edges only
+  const size_t smem = blk_smem(sizeof(T));
   const int R = ORDER == 2 ? 1 : 2;
   const int TW = kReg - 2 * cf.k * R;
   dim3 grid((g->n[0] + TW - 1) / TW, (g->n[1] + TW - 1) / TW, 1);
@@ -298,31 +292,31 @@ struct PersistArgs {
 template <typename T, int ORDER, bool VARC, bool FORCED>
 __global__ void __launch_bounds__(kBlkThreads, 1) k_wave2d_persist(PersistArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* const S0 = reinterpret_cast<T*>(smem_raw);
+  T* const S1 = S0 + kReg * kReg;
   constexpr int R = ORDER == 2 ? 1 : 2;
   const int H = a.K * R, TW = kReg - 2 * H;
-  const int i = threadIdx.x & 63;          // column of the region
-  const int jb = threadIdx.x >> 6;         // strip: rows 4 jb .. 4 jb + 3
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = 32 * (warp & 1) + lane;
+  const int jb = warp >> 1;
   const int x0 = (blockIdx.x % a.tiles_x) * TW - H, y0 = (blockIdx.x / a.tiles_x) * TW - H;
   const int nx = a.nx, ny = a.ny;
   const int gx = x0 + i;
   const bool colin = gx >= 0 && gx < nx;
   const bool coltile = colin && i >= H && i < kReg - H;
   T cur[kRowsPerThread], prv[kRowsPerThread], acr[kRowsPerThread];
-  T cc[kRowsPerThread], ff[kRowsPerThread];
-  bool act[kRowsPerThread], own[kRowsPerThread];
+  T cc[VARC ? kRowsPerThread : 1];
+  T ff[FORCED ? kRowsPerThread : 1];
   const T w0 = (T)a.wtab[0];
 #pragma unroll
   for (int r = 0; r < kRowsPerThread; ++r) {
-    const int jr = kRowsPerThread * jb + r;
-    const int gy = y0 + jr;
+    const int gy = y0 + jb + kRowPitch * r;
     const bool in = colin && gy >= 0 && gy < ny;
     const int64_t gi = gx + (int64_t)nx * gy;
-    act[r] = in;
-    own[r] = in && coltile && jr >= H && jr < kReg - H;   // a cell of this CTA's tile
     cur[r] = (in && a.v) ? (T)__ldg(a.v + gi) : T(0);
     prv[r] = T(0);
-    cc[r] = (VARC && in) ? __ldg(a.c2 + gi) : T(0);
-    ff[r] = (FORCED && in) ? (T)__ldg(a.f + gi) : T(0);
+    if (VARC) cc[r] = in ? __ldg(a.c2 + gi) : T(0);
+    if (FORCED) ff[r] = in ? (T)__ldg(a.f + gi) : T(0);
     acr[r] = w0 * cur[r];
   }
   const int J = (a.nt + a.K - 1) / a.K;
@@ -334,63 +328,64 @@ __global__ void __launch_bounds__(kBlkThreads, 1) k_wave2d_persist(PersistArgs<T
       const int qi = (j + 1) & 1;
 #pragma unroll
       for (int r = 0; r < kRowsPerThread; ++r) {
-        if (own[r]) continue;   // own tile cell: the registers are current
-        const int gy = y0 + kRowsPerThread * jb + r;
+        const int jr = jb + kRowPitch * r;
+        const int gy = y0 + jr;
+        if (coltile && jr >= H && jr < kReg - H) continue;   // own tile cell: registers are current
+        const bool in = colin && gy >= 0 && gy < ny;
         const int64_t gi = gx + (int64_t)nx * gy;
-        cur[r] = act[r] ? __ldcg(a.w[2 * qi + 1] + gi) : T(0);
-        prv[r] = act[r] ? __ldcg(a.w[2 * qi] + gi) : T(0);
+        cur[r] = in ? __ldcg(a.w[2 * qi + 1] + gi) : T(0);
+        prv[r] = in ? __ldcg(a.w[2 * qi] + gi) : T(0);
       }
     }
-    if constexpr (ORDER == 2) {
-      __shared__ TileEdges<T> E[2];
-      const TileCoef<T> tc{a.ih2x, a.ih2y, a.dt2, a.ax, a.ay, a.b};
-      tile_steps_o2<T, VARC, FORCED>(cur, prv, acr, cc, ff, act, n0, kk, tc,
-                                     [&](int m) { return (T)a.wtab[m]; }, [&](int m) { return (T)a.ptab[m]; }, E);
-    } else {
-      T* const S0 = reinterpret_cast<T*>(smem_raw);
-      T* const S1 = S0 + kReg * kReg;
 #pragma unroll
-      for (int r = 0; r < kRowsPerThread; ++r) S0[(kRowsPerThread * jb + r) * kReg + i] = cur[r];
-      __syncthreads();
-      T* Ain = S0;
-      T* Bout = S1;
-      for (int s = 1; s <= kk; ++s) {
-        const int n = n0 + s - 1;   // W^n -> W^{n+1}
-        const int lo = s * R, hi = kReg - s * R;
-        const bool colact = colin && i >= lo && i < hi;
-        const T ws = (T)a.wtab[n + 1];
-        const T fph = FORCED ? (n > 0 ? a.dt2 : T(0.5) * a.dt2) * (T)a.ptab[n] : T(0);
+    for (int r = 0; r < kRowsPerThread; ++r) S0[(jb + kRowPitch * r) * kReg + i] = cur[r];
+    __syncthreads();
+    T* Ain = S0;
+    T* Bout = S1;
+    for (int s = 1; s <= kk; ++s) {
+      const int n = n0 + s - 1;   // W^n -> W^{n+1}
+      const int lo = s * R, hi = kReg - s * R;
+      const bool colact = colin && i >= lo && i < hi;
+      const T ws = (T)a.wtab[n + 1];
+      const T fph = FORCED ? (n > 0 ? a.dt2 : T(0.5) * a.dt2) * (T)a.ptab[n] : T(0);
 #pragma unroll
-        for (int r = 0; r < kRowsPerThread; ++r) {
-          const int jr = kRowsPerThread * jb + r;
-          const int gy = y0 + jr;
-          if (colact && jr >= lo && jr < hi && gy >= 0 && gy < ny) {
-            const int l = jr * kReg + i;
-            const T c = cur[r];
+      for (int r = 0; r < kRowsPerThread; ++r) {
+        const int jr = jb + kRowPitch * r;
+        const int gy = y0 + jr;
+        if (colact && jr >= lo && jr < hi && gy >= 0 && gy < ny) {
+          const int l = jr * kReg + i;
+          const T c = cur[r];
+          T wn;
+          if (ORDER == 2 && !VARC && n > 0) {
+            T u = fma(a.b, c, -prv[r]);
+            u = fma(a.ax, (gx > 0 ? Ain[l - 1] : T(0)) + (gx < nx - 1 ? Ain[l + 1] : T(0)), u);
+            wn = fma(a.ay, (gy > 0 ? Ain[l - kReg] : T(0)) + (gy < ny - 1 ? Ain[l + kReg] : T(0)), u);
+          } else {
             T L = d2s<ORDER>(Ain, l, gx, nx, 1, c) * a.ih2x;
             L = fma(d2s<ORDER>(Ain, l, gy, ny, kReg, c), a.ih2y, L);
             if (VARC) L *= cc[r];
-            T wn = n > 0 ? fma(a.dt2, L, fma(T(2), c, -prv[r]))
-                         : fma(T(0.5) * a.dt2, L, c);   // Taylor start: W^1 = W^0 + dt^2/2 L W^0
-            if (FORCED) wn = fma(-fph, ff[r], wn);
-            prv[r] = c;
-            cur[r] = wn;
-            Bout[l] = wn;
-            acr[r] = fma(ws, wn, acr[r]);
+            wn = n > 0 ? fma(a.dt2, L, fma(T(2), c, -prv[r]))
+                       : fma(T(0.5) * a.dt2, L, c);   // Taylor start: W^1 = W^0 + dt^2/2 L W^0
           }
+          if (FORCED) wn = fma(-fph, ff[r], wn);
+          prv[r] = c;
+          cur[r] = wn;
+          Bout[l] = wn;
+          acr[r] = fma(ws, wn, acr[r]);
         }
-        __syncthreads();
-        T* tmp = Ain;
-        Ain = Bout;
-        Bout = tmp;
       }
+      __syncthreads();
+      T* tmp = Ain;
+      Ain = Bout;
+      Bout = tmp;
     }
     if (n0 + kk < a.nt) {   // publish the tile, then wait for every other CTA to publish theirs
       const int qo = j & 1;
 #pragma unroll
       for (int r = 0; r < kRowsPerThread; ++r) {
-        if (!own[r]) continue;
-        const int gy = y0 + kRowsPerThread * jb + r;
+        const int jr = jb + kRowPitch * r;
+        const int gy = y0 + jr;
+        if (!(coltile && jr >= H && jr < kReg - H && gy >= 0 && gy < ny)) continue;
         const int64_t gi = gx + (int64_t)nx * gy;
         a.w[2 * qo + 1][gi] = cur[r];
         a.w[2 * qo][gi] = prv[r];
@@ -401,8 +396,9 @@ __global__ void __launch_bounds__(kBlkThreads, 1) k_wave2d_persist(PersistArgs<T
   double part = 0.0;
 #pragma unroll
   for (int r = 0; r < kRowsPerThread; ++r) {
-    if (!own[r]) continue;
-    const int gy = y0 + kRowsPerThread * jb + r;
+    const int jr = jb + kRowPitch * r;
+    const int gy = y0 + jr;
+    if (!(coltile && jr >= H && jr < kReg - H && gy >= 0 && gy < ny)) continue;
     const int64_t gi = gx + (int64_t)nx * gy;
     if (!ok) {
       a.out[gi] = __longlong_as_double(0x7ff8000000000000ll);   // NaN: the solve did not complete
@@ -444,7 +440,7 @@ static int persist_capacity() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wave2d_persist<T, ORDER, VARC, FORCED>, kBlkThreads,
-                                                  ORDER == 2 ? 0 : 2 * kReg * kReg * sizeof(T));
+                                                  2 * kReg * kReg * sizeof(T));
     cap = per_sm * sms;
   }
   return cap;
@@ -476,8 +472,7 @@ static cudaError_t persist_launch(whv_grid g, const PersistArgs<T>& a, int ntile
   PersistArgs<T> arg = a;
   void* args[] = {(void*)&arg};
   return cudaLaunchCooperativeKernel((const void*)k_wave2d_persist<T, ORDER, VARC, FORCED>, dim3(ntiles),
-                                     dim3(kBlkThreads), args, ORDER == 2 ? 0 : 2 * kReg * kReg * sizeof(T),
-                                     g->stream);
+                                     dim3(kBlkThreads), args, 2 * kReg * kReg * sizeof(T), g->stream);
 }
 
 template <typename T>

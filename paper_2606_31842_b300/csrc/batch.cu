@@ -252,7 +252,11 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
         }
         if (VARC) cc[r] = in ? __ldg(B.c2 + gi) : T(0);
         if (FORCED) ff[r] = in ? (T)__ldg(B.f + gi) : T(0);
-        acr[r] = w0 * cur[r];
+        // the filter sum so far of the tile cells, loaded with the state (no read-modify-write
+        // round trip at the end)
+        const int jr = jb + kBPitch * r;
+        const bool tile = in && i >= H && i < kBReg - H && jr >= H && jr < kBReg - H;
+        acr[r] = (!first && tile) ? __ldcg(B.acc + gi) : w0 * cur[r];
       }
 #pragma unroll
       for (int r = 0; r < kBRows; ++r) S0[(jb + kBPitch * r) * kBReg + i] = cur[r];
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
         const int gy = y0 + jr;
         if (!(coltile && jr >= H && jr < kBReg - H && gy >= 0 && gy < ny)) continue;
         const int64_t gi = gx + (int64_t)nx * gy;
-        const T a = first ? acr[r] : __ldcg(B.acc + gi) + acr[r];
+        const T a = acr[r];
         if (!last) {
           B.w[2 * qo + 1][gi] = cur[r];
           B.w[2 * qo][gi] = prv[r];

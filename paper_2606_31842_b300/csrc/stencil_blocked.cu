@@ -79,15 +79,19 @@ __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ g
   if (threadIdx.x < kBlkMaxK) sw[threadIdx.x] = cf.w[threadIdx.x];
   T cur[kRowsPerThread], prv[kRowsPerThread], acr[kRowsPerThread];
   T cc[VARC ? kRowsPerThread : 1];
+  // all global loads up front, the filter accumulator of the tile cells included (its
+  // read-modify-write at the end would otherwise be one more L2 round trip on the critical path)
+  const bool coltile0 = colin && i >= H && i < kReg - H;
 #pragma unroll
   for (int t = 0; t < kRowsPerThread; ++t) {
-    const int gy = y0 + jb + kRowPitch * t;
+    const int j = jb + kRowPitch * t;
+    const int gy = y0 + j;
     const bool in = colin && gy >= 0 && gy < ny;
     const int64_t gi = gx + (int64_t)nx * gy;
     cur[t] = in ? gcur[gi] : T(0);
     prv[t] = in ? gprev[gi] : T(0);
     if (VARC) cc[t] = in ? c2[gi] : T(0);
-    acr[t] = T(0);
+    acr[t] = (coltile0 && j >= H && j < kReg - H && in) ? acc[gi] : T(0);
   }
 #pragma unroll
   for (int t = 0; t < kRowsPerThread; ++t) S0[(jb + kRowPitch * t) * kReg + i] = cur[t];
@@ -136,9 +140,9 @@ __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ g
     if (KIND == B_STEP) {
       ocur[gi] = cur[t];
       oprev[gi] = prv[t];
-      acc[gi] += acr[t];
+      acc[gi] = acr[t];
     } else {
-      const T a = acc[gi] + acr[t];
+      const T a = acr[t];
       if (KIND == B_LAST_OUT) {
         out[gi] = (double)a;
       } else {

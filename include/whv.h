@@ -285,6 +285,19 @@ whv_status whv_dot(whv_grid grid, const double* x_dev, const double* y_dev, doub
 whv_status whv_project_noalloc(int64_t n, int nd, const double* W_dev, const double* r_dev,
                                const double* w_dev, double* coef_dev, void* cuda_stream);
 
+/* SVD compression of the deflation basis (Sec. 4.3, experiment with compressed eigenvectors);
+ * 2-D grids.  Each basis vector, an ny x nx matrix (row y, column x), is replaced by its
+ * smallest-rank truncated SVD with Frobenius error < tau (singular values from a randomized range
+ * finder with power iterations; tau should be >= 1e-7 times the vector norm, the resolution of
+ * that finder), and the dense basis is freed: storage sum_m r_m (nx + ny + 1) doubles instead of
+ * nd nx ny.  From then on every use of the basis (DEVD deflation / inflation, DCG, AGMRES,
+ * ABICGSTAB, the FP64 residual correction, whv_project / whv_expand, batched solves) runs on the
+ * compressed vectors: the projection W^T M r is T = (M o r) V followed by per-vector sums of
+ * s_k u_k . T_k, the expansion a GEMM U diag(c) V^T (FP64 kernels of this library);
+ * whv_get_basis writes the compressed vectors out dense.  ranks_host (nd ints, may be NULL)
+ * receives r_m.  Needs a dense basis (WHV_ERR_INVALID otherwise, or if every rank is 0). */
+whv_status whv_compress_basis(whv_grid grid, double tau, int* ranks_host);
+
 /* Test hook for the failure path of the persistent wave solve (no counterpart in the paper):
  * raises the grid's barrier error flag, so that the next persistent wave solve on this grid leaves
  * at its first grid barrier exactly as after a barrier wait that timed out -- its output is NaN

@@ -772,9 +772,9 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
       const Basis& B = g->basis;
       fd[p] = f_dev[p];
       if (B.nd > 0) {
-        TRY(project(g, B.V, B.nd, f_dev[p], B.d_coef));
+        TRY(basis_project(g, f_dev[p], B.d_coef));
         TRY(copy_dev(g, g->fd, f_dev[p], g->N));
-        TRY(expand(g, B.V, B.nd, B.d_coef, -1.0, g->fd));
+        TRY(basis_expand(g, B.d_coef, -1.0, g->fd));
         fd[p] = g->fd;
       }
     }
@@ -810,7 +810,7 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
         const double om2 = c.tgs[p].omega_eff * c.tgs[p].omega_eff;
         for (int m = 0; m < B.nd; ++m) cf[m] /= (om2 - B.lambda2[m]);
         TRY(to_dev(g, g->small, cf.data(), B.nd));
-        TRY(expand(g, B.V, B.nd, g->small, 1.0, g->x));
+        TRY(basis_expand(g, g->small, 1.0, g->x));
       }
       TRY(copy_dev(g, u_dev[p], g->x, g->N));
     }
@@ -886,13 +886,13 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
         const Basis& B = g->basis;
         if (!active[p] || B.nd == 0) continue;
         std::vector<double> cf(B.nd), y(B.nd);
-        TRY(project(g, B.V, B.nd, g->ro, g->small));
+        TRY(basis_project(g, g->ro, g->small));
         TRY(to_host(g, cf.data(), g->small, B.nd));
         for (int m = 0; m < B.nd; ++m) y[m] = cf[m] / B.mu[m];
         TRY(to_dev(g, g->small, y.data(), B.nd));
-        TRY(expand(g, B.V, B.nd, g->small, 1.0, g->xo));
+        TRY(basis_expand(g, g->small, 1.0, g->xo));
         TRY(to_dev(g, g->small, cf.data(), B.nd));
-        TRY(expand(g, B.V, B.nd, g->small, -1.0, g->ro));
+        TRY(basis_expand(g, g->small, -1.0, g->ro));
       }
       for (int p = 0; p < np; ++p)
         if (active[p]) TRY(dot_async(c.grids[p], c.grids[p]->ro, c.grids[p]->ro, S_TMP2));

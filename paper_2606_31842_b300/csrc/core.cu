@@ -23,7 +23,8 @@ whv_status fail(whv_grid g, whv_status s, const std::string& msg) {
 
 void free_basis(whv_grid g) {
   Basis& b = g->basis;
-  for (void* p : {(void*)b.V, (void*)b.d_coef, (void*)b.AW, (void*)b.Einv, (void*)b.QAW})
+  for (void* p : {(void*)b.V, (void*)b.d_coef, (void*)b.AW, (void*)b.Einv, (void*)b.QAW, (void*)b.cU, (void*)b.cV,
+                  (void*)b.cs, (void*)b.cT, (void*)b.cc, (void*)b.cR, (void*)b.coff, (void*)b.cowner})
     if (p) cudaFree(p);
   g->basis = Basis();
   free_cgloop(g);
@@ -147,7 +148,8 @@ static void free_all(whv_grid g) {
   free_plan(g);
   void* ptrs[] = {g->c2, g->c2f, g->mw, g->wbuf[0], g->wbuf[1], g->wbuf[2], g->wbuf[3], g->acc, g->x, g->r, g->p, g->q,
                   g->t, g->fd, g->krylov, g->small, g->small2, g->partials, g->counters, g->gbar, g->scal,
-                  g->basis.V, g->basis.d_coef, g->basis.AW, g->basis.Einv, g->basis.QAW, g->wbuf64[0], g->wbuf64[1], g->wbuf64[2],
+                  g->basis.V, g->basis.d_coef, g->basis.AW, g->basis.Einv, g->basis.QAW, g->basis.cU, g->basis.cV,
+                  g->basis.cs, g->basis.cT, g->basis.cc, g->basis.cR, g->basis.coff, g->basis.cowner, g->wbuf64[0], g->wbuf64[1], g->wbuf64[2],
                   g->wbuf64[3], g->acc64, g->xo, g->ro, g->bo, g->wtab_small};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -360,8 +362,11 @@ whv_status whv_get_basis(whv_grid g, int* nd, int* modes_host, double* lambda2_h
   if (b.nd == 0) return WHV_OK;
   if (modes_host) std::memcpy(modes_host, b.modes.data(), b.modes.size() * sizeof(int));
   if (lambda2_host) std::memcpy(lambda2_host, b.lambda2.data(), b.nd * sizeof(double));
-  if (V_dev) {
-    WHV_CUDA(g, cudaMemcpyAsync(V_dev, b.V, (size_t)g->N * b.nd * 8, cudaMemcpyDeviceToDevice, g->stream));
+  if (V_dev) {   // the compressed vectors are written out dense
+    for (int m = 0; m < b.nd; ++m) {
+      whv_status s = basis_column(g, m, V_dev + (size_t)m * g->N);
+      if (s != WHV_OK) return s;
+    }
     WHV_CUDA(g, cudaStreamSynchronize(g->stream));
   }
   return WHV_OK;
@@ -371,14 +376,14 @@ whv_status whv_project(whv_grid g, const double* r_dev, double* coeff_dev) {
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
   if (g->basis.nd == 0) return fail(g, WHV_ERR_INVALID, "no deflation basis set");
   if (!r_dev || !coeff_dev) return fail(g, WHV_ERR_INVALID, "NULL pointer");
-  return project(g, g->basis.V, g->basis.nd, r_dev, coeff_dev);
+  return basis_project(g, r_dev, coeff_dev);
 }
 
 whv_status whv_expand(whv_grid g, const double* y_dev, double alpha, double* out_dev) {
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
   if (g->basis.nd == 0) return fail(g, WHV_ERR_INVALID, "no deflation basis set");
   if (!y_dev || !out_dev) return fail(g, WHV_ERR_INVALID, "NULL pointer");
-  return expand(g, g->basis.V, g->basis.nd, y_dev, alpha, out_dev);
+  return basis_expand(g, y_dev, alpha, out_dev);
 }
 
 whv_status whv_dot(whv_grid g, const double* x_dev, const double* y_dev, double* out_host) {

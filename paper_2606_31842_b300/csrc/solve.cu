@@ -48,9 +48,8 @@ struct SolveCtx {
 
 // out = out - W (W^T M out)
 static whv_status deflate_vec(whv_grid g, double* vec) {
-  const Basis& B = g->basis;
-  TRY(project(g, B.V, B.nd, vec, g->small));
-  return expand(g, B.V, B.nd, g->small, -1.0, vec);
+  TRY(basis_project(g, vec, g->small));
+  return basis_expand(g, g->small, -1.0, vec);
 }
 
 // q = A v (+ re-deflation) in the grid's stepping precision; scal[S_PQ] = <v, q>_M
@@ -146,7 +145,7 @@ struct CgLoop {
   double omega = 0, cfl = 0;
   int periods = 0, adjust = 0, nt = 0, kblock = 0;
   bool redefl = false, general = false;
-  const double* V = nullptr;
+  const void* V = nullptr;     // identity of the basis storage the graph was built with
   int nd = 0;
   int64_t body_launches = 0;
 };
@@ -171,7 +170,7 @@ static whv_status cg_loop_graph(SolveCtx& c, bool general, CgLoop** out) {
   const bool usesV = c.redefl || general;
   if (L && L->omega == c.tg.omega && L->cfl == c.tg.cfl && L->periods == c.tg.periods &&
       L->adjust == c.tg.adjust && L->nt == c.tg.nt && L->kblock == g->kblock && L->redefl == c.redefl &&
-      L->general == general && L->V == (usesV ? B.V : nullptr) && L->nd == (usesV ? B.nd : 0)) {
+      L->general == general && L->V == (usesV ? basis_key(B) : nullptr) && L->nd == (usesV ? B.nd : 0)) {
     *out = L;
     return WHV_OK;
   }
@@ -180,7 +179,7 @@ static whv_status cg_loop_graph(SolveCtx& c, bool general, CgLoop** out) {
   g->cgloop = L;
   L->omega = c.tg.omega; L->cfl = c.tg.cfl; L->periods = c.tg.periods; L->adjust = c.tg.adjust;
   L->nt = c.tg.nt; L->kblock = g->kblock; L->redefl = c.redefl; L->general = general;
-  L->V = usesV ? B.V : nullptr; L->nd = usesV ? B.nd : 0;
+  L->V = usesV ? basis_key(B) : nullptr; L->nd = usesV ? B.nd : 0;
   WHV_CUDA(g, cudaGraphCreate(&L->graph, 0));
   cudaGraphConditionalHandle h;
   WHV_CUDA(g, cudaGraphConditionalHandleCreate(&h, L->graph, 1, cudaGraphCondAssignDefault));
@@ -227,7 +226,7 @@ static whv_status prepare_general_dcg(SolveCtx& c) {
   if (!B.AW) WHV_CUDA(g, cudaMalloc(&B.AW, (size_t)nd * N * sizeof(double)));
   for (int m = 0; m < nd; ++m) {
     // through fixed buffers so that every column replays one cached wave-solve graph
-    WHV_CUDA(g, cudaMemcpyAsync(g->p, B.V + (size_t)m * N, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    TRY(basis_column(g, m, g->p));
     TRY(wave_solve(g, c.tg, g->p, nullptr, g->q, 1));   // not t: it may hold the right-hand side
     c.ws++;
     WHV_CUDA(g, cudaMemcpyAsync(B.AW + (size_t)m * N, g->q, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
@@ -235,7 +234,7 @@ static whv_status prepare_general_dcg(SolveCtx& c) {
   // E = W^T M (A W), symmetrised (A is M-self-adjoint; FP32 stepping breaks it at rounding level)
   std::vector<double> E((size_t)nd * nd), col(nd);
   for (int m = 0; m < nd; ++m) {
-    TRY(project(g, B.V, nd, B.AW + (size_t)m * N, g->small));
+    TRY(basis_project(g, B.AW + (size_t)m * N, g->small));
     TRY(to_host(g, col.data(), g->small, nd));
     for (int i = 0; i < nd; ++i) E[(size_t)i * nd + m] = col[i];
   }
@@ -256,7 +255,7 @@ static whv_status dcg_project_direction(whv_grid g) {
   const Basis& B = g->basis;
   TRY(project(g, B.AW, B.nd, g->r, g->small));
   TRY(small_matvec(g, B.Einv, g->small, B.nd, g->small2));
-  return expand(g, B.V, B.nd, g->small2, -1.0, g->p);
+  return basis_expand(g, g->small2, -1.0, g->p);
 }
 
 // Algorithm 5 set-up: A W = QAW Raw, kept with the basis.  A W = W diag(mu) for exact
@@ -271,15 +270,15 @@ static whv_status prepare_agmres(SolveCtx& c) {
   std::vector<double> R((size_t)nd * nd, 0.0), h(nd);
   for (int j = 0; j < nd; ++j) {
     double* q = B.QAW + (size_t)j * N;
-    const double* wj = B.V + (size_t)j * N;
     if (B.flags & WHV_BASIS_EXACT) {
-      TRY(axpby(g, N, B.mu[j], wj, 0.0, q));
+      TRY(basis_column(g, j, q));
+      TRY(axpby(g, N, B.mu[j], q, 0.0, q));
     } else if (B.AW) {
       TRY(copy_dev(g, q, B.AW + (size_t)j * N, N));
     } else {
       // through p -> q (the A p buffers: every column replays one cached wave-solve graph; t may
       // hold the right-hand side, which the restarts read again)
-      TRY(copy_dev(g, g->p, wj, N));
+      TRY(basis_column(g, j, g->p));
       TRY(wave_solve(g, c.tg, g->p, nullptr, g->q, 1));
       c.ws++;
       TRY(copy_dev(g, q, g->q, N));
@@ -347,20 +346,20 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
       // Algorithm 4 with a general basis: x_0 = x_{-1} + W E^{-1} W^T M r_{-1},
       // r_0 = r_{-1} - (A W) E^{-1} W^T M r_{-1},  p_0 = r_0 - W E^{-1} (A W)^T M r_0
       TRY(prepare_general_dcg(c));
-      TRY(project(g, B.V, B.nd, g->r, g->small));
+      TRY(basis_project(g, g->r, g->small));
       TRY(small_matvec(g, B.Einv, g->small, B.nd, g->small2));
-      TRY(expand(g, B.V, B.nd, g->small2, 1.0, g->x));
+      TRY(basis_expand(g, g->small2, 1.0, g->x));
       TRY(expand(g, B.AW, B.nd, g->small2, -1.0, g->r));
     } else if (method == WHV_DCG) {
       // x_0 = x_{-1} + W diag(1/mu) W^T M r_{-1};  r_0 = r_{-1} - W W^T M r_{-1}  (A W = W diag(mu))
       std::vector<double> cf(B.nd), y(B.nd);
-      TRY(project(g, B.V, B.nd, g->r, g->small));
+      TRY(basis_project(g, g->r, g->small));
       TRY(to_host(g, cf.data(), g->small, B.nd));
       for (int m = 0; m < B.nd; ++m) y[m] = cf[m] / B.mu[m];
       TRY(to_dev(g, g->small, y.data(), B.nd));
-      TRY(expand(g, B.V, B.nd, g->small, 1.0, g->x));
+      TRY(basis_expand(g, g->small, 1.0, g->x));
       TRY(to_dev(g, g->small, cf.data(), B.nd));
-      TRY(expand(g, B.V, B.nd, g->small, -1.0, g->r));
+      TRY(basis_expand(g, g->small, -1.0, g->r));
     }
     TRY(copy_dev(g, g->p, g->r, N));
     if (general) TRY(dcg_project_direction(g));
@@ -590,7 +589,7 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
       }
       if (pd > 0) {
         TRY(to_dev(g, g->small, y.data(), pd));
-        TRY(expand(g, B.V, pd, g->small, 1.0, g->x));
+        TRY(basis_expand(g, g->small, 1.0, g->x));
       }
       if (k > pd) {
         TRY(to_dev(g, g->small, y.data() + pd, k - pd));
@@ -702,7 +701,7 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
         y[i] = acc / B.Raw[(size_t)i * pd + i];
       }
       TRY(to_dev(g, g->small, y.data(), pd));
-      TRY(expand(g, B.V, pd, g->small, -1.0, g->x));
+      TRY(basis_expand(g, g->small, -1.0, g->x));
     }
   } else {  // FPI, Algorithm 1: x <- Pi_h(x; f_d)
     const double bnorm = sqrt(bb);
@@ -772,13 +771,13 @@ static whv_status outer_solve(SolveCtx& c, int method, const whv_params* p, cons
     if (its >= p->maxit || outer >= 50 || (!fp64_res && outer >= 1)) break;
     if (defl) {
       // deflated components: x += W diag(1/mu) c, r -= W c, c = W^T M r
-      TRY(project(g, B.V, B.nd, g->ro, g->small));
+      TRY(basis_project(g, g->ro, g->small));
       TRY(to_host(g, cf.data(), g->small, B.nd));
       for (int m = 0; m < B.nd; ++m) y[m] = cf[m] / B.mu[m];
       TRY(to_dev(g, g->small, y.data(), B.nd));
-      TRY(expand(g, B.V, B.nd, g->small, 1.0, g->xo));
+      TRY(basis_expand(g, g->small, 1.0, g->xo));
       TRY(to_dev(g, g->small, cf.data(), B.nd));
-      TRY(expand(g, B.V, B.nd, g->small, -1.0, g->ro));
+      TRY(basis_expand(g, g->small, -1.0, g->ro));
     }
     TRY(dot_async(g, g->ro, g->ro, S_TMP2));
     TRY(fetch_scalars(g));
@@ -839,9 +838,9 @@ static whv_status solve_impl(whv_grid g, const whv_params* p, const double* f, i
   // ---- forcing (Algorithm 2: deflate the forcing)
   const double* fuse = f;
   if (devd && !refine) {
-    TRY(project(g, B.V, B.nd, f, B.d_coef));
+    TRY(basis_project(g, f, B.d_coef));
     TRY(copy_dev(g, g->fd, f, N));
-    TRY(expand(g, B.V, B.nd, B.d_coef, -1.0, g->fd));
+    TRY(basis_expand(g, B.d_coef, -1.0, g->fd));
     fuse = g->fd;
   }
 
@@ -880,7 +879,7 @@ static whv_status solve_impl(whv_grid g, const whv_params* p, const double* f, i
     const double om2 = tg.omega_eff * tg.omega_eff;
     for (int m = 0; m < B.nd; ++m) cf[m] = cf[m] / (om2 - B.lambda2[m]);
     TRY(to_dev(g, g->small, cf.data(), B.nd));
-    TRY(expand(g, B.V, B.nd, g->small, 1.0, g->x));
+    TRY(basis_expand(g, g->small, 1.0, g->x));
   }
   TRY(copy_dev(g, u, g->x, N));
 

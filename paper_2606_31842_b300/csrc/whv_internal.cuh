@@ -60,6 +60,13 @@ struct Basis {
   // Algorithm 5: A W = QAW Raw (thin QR in <.,.>_M), built on the first AGMRES solve
   double* QAW = nullptr;              // N x nd, M-orthonormal columns
   std::vector<double> Raw;            // nd x nd upper triangular, column-major
+  // SVD-compressed vectors (whv_compress_basis; V is then freed): vector m = sum over its
+  // columns k of s_k u_k v_k^T, u_k (ny) and v_k (nx) the columns off[m] .. off[m+1]-1 of cU, cV
+  int comp_R = 0;                     // total rank (0: dense basis)
+  double comp_tau = 0.0;
+  double *cU = nullptr, *cV = nullptr, *cs = nullptr;   // ny x R, nx x R (column-major), R
+  double *cT = nullptr, *cc = nullptr, *cR = nullptr;   // scratch: ny x R, R, N
+  int *coff = nullptr, *cowner = nullptr;               // nd + 1 offsets, owner vector of each column
 };
 
 struct StepPlan;  // cached CUDA graphs of wave solves (stencil.cu)
@@ -212,5 +219,11 @@ whv_status project(whv_grid g, const double* W, int nd, const double* r, double*
 whv_status expand(whv_grid g, const double* W, int nd, const double* coef, double alpha,
                   double* out);
 whv_status closed_form_basis(whv_grid g, const TimeGridH& tg, int nd, Basis* b);
+
+// compress.cu: contractions with the grid's basis, dense or SVD-compressed
+whv_status basis_project(whv_grid g, const double* r, double* coef);                  // W^T M r
+whv_status basis_expand(whv_grid g, const double* coef, double alpha, double* out);   // out += a W c
+whv_status basis_column(whv_grid g, int m, double* dst);                             // dst = W e_m
+const void* basis_key(const Basis& B);   // identity of the basis storage (graph cache keys)
 
 }  // namespace whv

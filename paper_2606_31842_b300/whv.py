@@ -73,6 +73,7 @@ def _load():
         "whv_lanczos": [P, ctypes.POINTER(whv_params), I, I, P, I, I, ctypes.POINTER(D), ctypes.POINTER(D)],
         "whv_solve_adjoint": [P, ctypes.POINTER(whv_params), P, P, P, P, P, P, I, ctypes.POINTER(whv_info)],
         "whv_inject_barrier_error": [P],
+        "whv_compress_basis": [P, D, ctypes.POINTER(I)],
         "whv_solve_batched": [I, ctypes.POINTER(P), ctypes.POINTER(whv_params), ctypes.POINTER(P),
                               ctypes.POINTER(P), ctypes.POINTER(whv_info)],
     }
@@ -99,7 +100,7 @@ EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_gr
             "whv_expand", "whv_dot", "whv_num_unknowns", "whv_last_error", "whv_version",
             "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune",
             "whv_project_noalloc", "whv_lanczos", "whv_solve_adjoint", "whv_solve_batched",
-            "whv_inject_barrier_error"]
+            "whv_inject_barrier_error", "whv_compress_basis"]
 
 
 def _check(status, handle=None, allow=()):
@@ -259,6 +260,14 @@ class Grid:
         k = ctypes.c_int()
         _check(lib.whv_get_steps_per_sweep(self.handle, ctypes.byref(k)), self.handle)
         return k.value
+
+    def whv_compress_basis(self, tau):
+        """SVD-compress the basis (2-D); returns the rank of every vector."""
+        self._pre()
+        nd = self.whv_get_basis()["nd"]
+        ranks = (ctypes.c_int * max(nd, 1))()
+        _check(lib.whv_compress_basis(self.handle, float(tau), ranks), self.handle)
+        return [ranks[i] for i in range(nd)]
 
     def whv_inject_barrier_error(self):
         _check(lib.whv_inject_barrier_error(self.handle), self.handle)

@@ -54,7 +54,7 @@ def parse():
                          "with a conditional node), k > 1 launches one iteration graph per step from the host")
     ap.add_argument("--sources", type=int, default=0,
                     help="batched workload: Gaussian sources per (grid, frequency) (default 16)")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "study"],
                     help="c2 (default): the 513^2 deflated solve; others: the 1-D, variable-speed "
                          "1025^2, batched and 3-D workloads, measured on request")
     return ap.parse_args()
@@ -247,6 +247,33 @@ def run_workload(args):
     dev = lambda a: torch.from_numpy(a.ravel()).to("cuda")  # noqa: E731
     line = {"metric": METRIC, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    if args.workload == "study":
+        # iterations vs omega with N_D growing linearly or quadratically in omega (Sec. 4.4):
+        # DEVD-CG, FP64, closed-form vectors on the 257^2 unit square, omega = 10 .. 40
+        res = {"quadratic": [], "linear": []}
+        t_all = 0.0
+        omegas = [10.0, 15.0, 20.0, 25.0, 30.0, 35.0, 40.0]
+        for rule, nd_of in (("quadratic", lambda om: int(om * om // 10)), ("linear", lambda om: int(3 * om // 2))):
+            for om in omegas:
+                npts = (257, 257)
+                g = whv.Grid(npts, precision=whv.WHV_FP64, stream=stream)
+                prm = whv.make_params(om, method="cg", tol=1e-8, maxit=20000)
+                g.whv_set_deflation_basis(prm, nd_of(om), whv.WHV_BASIS_CLOSED_FORM)
+                f = dev(I.gaussian(npts, [0.37, 0.58], 1.0 / om, om * om))
+                t0 = time.perf_counter()
+                _, info = g.whv_solve(prm, f)
+                t_all += time.perf_counter() - t0
+                res[rule].append({"omega": om, "nd": nd_of(om), "iterations": info["iterations"],
+                                  "status": info["status"]})
+                g.close()
+        line.update({"workload": "study", "value": t_all * 1e3, "ms_per_step": t_all * 1e3, "dtype": "f64",
+                     "krylov_dtype": "f64",
+                     "config": {"workload": "iterations vs omega on the 257^2 unit square, DEVD-CG to 1e-8 with "
+                                            "N_D = floor(omega^2/10) (quadratic) or floor(3 omega/2) (linear) "
+                                            "closed-form vectors; value = total solve time"},
+                     "study": res})
+        print(json.dumps(line), flush=True)
+        return 0
     if args.workload == "c4":
         # FP32 stepping inside FP64 residual correction (default), or the plain FP64 form
         fp32 = args.precision == "fp32"
@@ -353,6 +380,23 @@ def run_workload(args):
                  "iterations": info["iterations"], "outer_iterations": info["outer_iterations"],
                  "wave_solves": info["wave_solves"], "glups_solve": lups / (ms * 1e-3) / 1e9,
                  "accuracy": {"true_rel_residual": ichk["true_rel_residual"]}})
+    if name == "c3":
+        # break-even of the eigenvector set-up (Sec. 4.1 cost model): the same problem without
+        # deflation, counted in wave solves, outside the timed region
+        g0 = whv.Grid(w.npts, order=w.order, precision=prec, stream=stream)
+        if w.speed:
+            g0.whv_set_speed(dev(I.speed_squared(w.speed, w.npts, w.speed_seed)))
+        p0 = whv.make_params(w.omega, method="cg", tol=w.tol, maxit=20000, refine_fp64=refine)
+        t0 = time.perf_counter()
+        _, i0 = g0.whv_solve(p0, f)
+        t_undefl = time.perf_counter() - t0
+        setup_ws = 1024 + w.nd   # Lanczos steps + A W of Algorithm 4 (first deflated solve)
+        gain = i0["wave_solves"] - info["wave_solves"]
+        line["break_even"] = {"setup_wave_solves": setup_ws, "wave_solves_deflated": info["wave_solves"],
+                              "wave_solves_undeflated": i0["wave_solves"], "undeflated_status": i0["status"],
+                              "undeflated_s": t_undefl,
+                              "rhs": (setup_ws / gain) if gain > 0 else None}
+        g0.close()
     print(json.dumps(line), flush=True)
     return 0
 

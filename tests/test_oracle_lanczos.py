@@ -52,3 +52,23 @@ def test_partial_krylov_converges_for_constant_speed():
         close = np.abs(all_l2 - l2) < 1e-7 * l2
         Z = SP.basis(g, allm[close])
         assert np.linalg.norm(y - Z @ (Z.T @ y)) < 1e-5
+
+
+def test_thick_restart_recovers_top_of_spectrum_with_a_small_basis():
+    """Thick-restart Lanczos with a basis of 3 nd + 4 vectors, restarted, reaches the same top
+    eigenpairs as the dense eigen-solve of the independent matrix."""
+    npts = (19, 17)
+    c2 = I.speed_squared("c3", npts, 4)
+    g = O.Grid(npts, order=4, c2=c2)
+    tg = WH.time_grid_for(g, 14.0)
+    nd = 8
+    res = LZ.lanczos_thick(g, tg, nd, 3 * nd + 4, I.random_field(g.shape, 1), max_restarts=400, tol=1e-11)
+    assert res.converged == nd
+    assert res.restarts > 0 and res.wave_solves < g.n   # restarted, and cheaper than a full space
+    lam2_all, _ = _dense_pairs(npts, 4, c2)
+    beta_all = SP.beta_h(lam2_all, tg)
+    top = np.sort(lam2_all[np.argsort(-beta_all)[:nd]])
+    assert np.allclose(np.sort(res.lambda2), top, rtol=1e-9)
+    assert res.resid.max() < 1e-8
+    W = res.V
+    assert np.abs(W.T @ (g.weights().ravel()[:, None] * W) - np.eye(nd)).max() < 1e-10

@@ -138,3 +138,26 @@ def test_break_even_model():
     b = GOLD["break_even"]
     nf = next(n for n in range(1, 100) if b["deflated_per_rhs"] * n + b["eigen_setup"] < b["standard_per_rhs"] * n)
     assert nf == b["break_even_nf"]
+
+
+def test_nd_proportional_to_omega_squared_keeps_the_rate_bounded():
+    """Sec. 4.4 (Weyl + gap law): with N_D = floor(omega^2/10) deflated modes the asymptotic
+    convergence rate of the deflated iteration stays bounded away from 1 as omega grows on the unit
+    square, while N_D = floor(3 omega/2) lets it drift towards 1."""
+    og = O.Grid((129, 129))
+    modes = SP.all_modes(og)
+    lam2 = SP.mode_lambda2(og, modes)
+    quad, lin = {}, {}
+    for om in (10, 15, 20, 25, 30):
+        tg = WH.time_grid_for(og, float(om))
+        bh = SP.beta_h(lam2, tg)
+        order = np.lexsort((np.arange(len(bh)), np.abs(1.0 - bh)))
+
+        def acr(nd):
+            rest = np.ones(len(bh), bool)
+            rest[order[:nd]] = False
+            return float(np.abs(bh[rest]).max())
+        quad[om], lin[om] = acr(om * om // 10), acr(3 * om // 2)
+    assert max(quad.values()) < 0.5
+    assert quad[30] - quad[15] < 0.1
+    assert lin[30] > 0.8 and lin[30] - lin[15] > 0.3

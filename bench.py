@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--method", default="", choices=["", "cg", "dcg", "gmres", "agmres"],
                     help="accelerator of the single-grid workloads (default: DCG for c1/c3, CG otherwise)")
+    ap.add_argument("--steps-per-sweep", type=int, default=0,
+                    help="2-D stepping kernel: 0 = autotune (default), k = blocked k steps per launch, "
+                         "-k = persistent kernel; a fixed value keeps profiled runs on the kernel the plain run uses")
     ap.add_argument("--check-every", type=int, default=1,
                     help="convergence test every k iterations; 1 keeps the CG loop on the device (a graph "
                          "with a conditional node), k > 1 launches one iteration graph per step from the host")
@@ -438,7 +441,11 @@ def main():
     tgrid = g.whv_time_grid(prm)
     nt = tgrid["nt"]
     g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
-    ksweep = g.whv_autotune(prm)                      # steps per sweep of the blocked 2-D kernel
+    if args.steps_per_sweep:
+        g.whv_set_steps_per_sweep(args.steps_per_sweep)
+        ksweep = args.steps_per_sweep
+    else:
+        ksweep = g.whv_autotune(prm)                  # steps per sweep of the blocked 2-D kernel
     f_host = torch.from_numpy(I.forcing_for(w).ravel()).pin_memory()
     u_host = torch.empty_like(f_host).pin_memory()
     with torch.cuda.stream(stream):

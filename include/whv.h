@@ -170,6 +170,21 @@ whv_status whv_set_deflation_basis(whv_grid grid, const whv_params* p, int nd, c
 whv_status whv_lanczos(whv_grid grid, const whv_params* p, int nd, int m, const double* v0_dev,
                        int fp64_stepping, int flags, double* theta_host, double* resid_host);
 
+/* Thick-restart Lanczos (Wu and Simon 2000) for the same basis when nd is large: the Krylov basis
+ * holds at most m vectors; when it is full, the Ritz pairs of the projected matrix (filled from the
+ * FP64 re-orthogonalisation coefficients, dense symmetric eigen-solve on the host by Householder
+ * reduction, bisection and inverse iteration) are tested -- the residual of pair i is |b s_{m,i}|,
+ * b the norm of the next, unnormalised Lanczos vector -- and unless the nd largest are below tol
+ * (on the scale of S_h's eigenvalues, which lie in (-1, 1]) the `keep` largest Ritz vectors and the
+ * residual vector restart the basis (keep <= 0: nd + max(nd/2, 8), capped at m - 2).  At most
+ * max_restarts restarts.  The nd Ritz vectors become the grid's WHV_BASIS_LANCZOS basis as with
+ * whv_lanczos; stats_host (3 ints, may be NULL) receives {restarts, wave solves, converged pairs}.
+ * Needs 1 <= nd <= keep <= m - 2, m <= min(N, 1024), tol > 0; temporary device memory
+ * (m + keep + nd) N doubles. */
+whv_status whv_lanczos_restarted(whv_grid grid, const whv_params* p, int nd, int m, int keep, int max_restarts,
+                                 double tol, const double* v0_dev, int fp64_stepping, int flags,
+                                 double* theta_host, double* resid_host, int* stats_host);
+
 /* Read back the basis: nd (host), the mode tuples (host int[nd*dim], closed form only; else
  * zeros), lambda^2 (host double[nd]) and the vectors (device double[N*nd]); any output may be NULL. */
 whv_status whv_get_basis(whv_grid grid, int* nd, int* modes_host, double* lambda2_host, double* V_dev);

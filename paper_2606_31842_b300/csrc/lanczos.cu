@@ -225,6 +225,59 @@ static void top_eigenpairs(const std::vector<double>& a, const std::vector<doubl
 
 using namespace whv;
 
+// Rayleigh quotients lambda^2 = -<y, L_h y>_M / <y, y>_M and residuals ||L_h y + lambda^2 y||_M /
+// lambda^2 in FP64 for the nd Ritz vectors Y (N x nd, device, owned by the caller until this
+// returns WHV_OK, then by the basis), and install them as the grid's WHV_BASIS_LANCZOS basis.
+static whv_status install_ritz_basis(whv_grid g, const whv_params* p, const TimeGridH& tg, double* Y, int nd,
+                                     const std::vector<double>& theta, int flags, double* theta_host,
+                                     double* resid_host) {
+  const int64_t N = g->N;
+#define LZ_TRY(expr)                                \
+  do {                                              \
+    whv_status _s = (expr);                         \
+    if (_s != WHV_OK) { cudaFree(Y); return _s; }   \
+  } while (0)
+  std::vector<double> lam2(nd), res(nd);
+  for (int j = 0; j < nd; ++j) {
+    const double* y = Y + (size_t)j * N;
+    LZ_TRY(apply_L_fp64(g, y, g->q));
+    LZ_TRY(dot_async(g, y, g->q, S_TMP));
+    LZ_TRY(dot_async(g, y, y, S_TMP2));
+    LZ_TRY(fetch_scalars(g));
+    lam2[j] = -g->scal_host[S_TMP] / g->scal_host[S_TMP2];
+    LZ_TRY(axpby(g, N, lam2[j], y, 1.0, g->q));   // q = L y + lambda^2 y
+    LZ_TRY(dot_async(g, g->q, g->q, S_TMP));
+    LZ_TRY(fetch_scalars(g));
+    res[j] = sqrt(g->scal_host[S_TMP]) / fabs(lam2[j]);
+  }
+  if (getenv("WHV_LOG") && getenv("WHV_LOG")[0] == '1')
+    for (int j = 0; j < nd; ++j)
+      fprintf(stderr, "[whv] Lanczos pair %d: theta %.6f lambda^2 %.6e residual %.2e\n", j, theta[j], lam2[j], res[j]);
+  if (theta_host) std::copy(theta.begin(), theta.end(), theta_host);
+  if (resid_host) std::copy(res.begin(), res.end(), resid_host);
+  // install as the deflation basis (approximate eigenvectors)
+  Basis b;
+  b.nd = nd; b.mode = WHV_BASIS_LANCZOS; b.flags = flags & ~WHV_BASIS_EXACT;
+  b.omega = p->omega; b.periods = p->periods; b.adjust = p->adjust_omega ? 1 : 0; b.cfl = tg.cfl;
+  b.V = Y;
+  b.lambda2 = lam2;
+  b.mu.resize(nd);
+  for (int j = 0; j < nd; ++j) {
+    const double x = 1.0 - 0.5 * tg.dt * tg.dt * lam2[j];
+    const double th = acos(std::max(-1.0, std::min(1.0, x)));
+    double be = 0.0;
+    for (int n = 0; n <= tg.nt; ++n) be += tg.weight[n] * cos(n * th);
+    b.mu[j] = 1.0 - be;
+  }
+  b.modes.assign((size_t)nd * g->dim, 0);
+  cudaError_t e = cudaMalloc(&b.d_coef, (size_t)kMaxND * sizeof(double));
+  if (e != cudaSuccess) { cudaFree(Y); return cuda_fail(g, e, "cudaMalloc"); }
+  free_basis(g);
+  g->basis = std::move(b);
+#undef LZ_TRY
+  return WHV_OK;
+}
+
 static whv_status lanczos_impl(whv_grid g, const whv_params* p, int nd, int m, const double* v0_dev,
                                   int fp64_stepping, int flags, double* theta_host, double* resid_host) {
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
@@ -313,52 +366,205 @@ static whv_status lanczos_impl(whv_grid g, const whv_params* p, int nd, int m, c
   LZ_CUDA(cudaStreamSynchronize(g->stream));
   cleanup();
   Q = nullptr; dS = nullptr;
-  // Rayleigh quotients and residuals with L_h in FP64
-  std::vector<double> lam2(nd), res(nd);
-  for (int j = 0; j < nd; ++j) {
-    const double* y = Y + (size_t)j * N;
-    LZ_TRY(apply_L_fp64(g, y, g->q));
-    LZ_TRY(dot_async(g, y, g->q, S_TMP));
-    LZ_TRY(dot_async(g, y, y, S_TMP2));
-    LZ_TRY(fetch_scalars(g));
-    lam2[j] = -g->scal_host[S_TMP] / g->scal_host[S_TMP2];
-    LZ_TRY(axpby(g, N, lam2[j], y, 1.0, g->q));   // q = L y + lambda^2 y
-    LZ_TRY(dot_async(g, g->q, g->q, S_TMP));
-    LZ_TRY(fetch_scalars(g));
-    res[j] = sqrt(g->scal_host[S_TMP]) / fabs(lam2[j]);
-  }
-  if (getenv("WHV_LOG") && getenv("WHV_LOG")[0] == '1')
-    for (int j = 0; j < nd; ++j)
-      fprintf(stderr, "[whv] Lanczos pair %d: theta %.6f lambda^2 %.6e residual %.2e\n", j, theta[j], lam2[j], res[j]);
-  if (theta_host) std::copy(theta.begin(), theta.end(), theta_host);
-  if (resid_host) std::copy(res.begin(), res.end(), resid_host);
-  // install as the deflation basis (approximate eigenvectors)
-  Basis b;
-  b.nd = nd; b.mode = WHV_BASIS_LANCZOS; b.flags = flags & ~WHV_BASIS_EXACT;
-  b.omega = p->omega; b.periods = p->periods; b.adjust = p->adjust_omega ? 1 : 0; b.cfl = tg.cfl;
-  b.V = Y;
-  b.lambda2 = lam2;
-  b.mu.resize(nd);
-  for (int j = 0; j < nd; ++j) {
-    const double x = 1.0 - 0.5 * tg.dt * tg.dt * lam2[j];
-    const double th = acos(std::max(-1.0, std::min(1.0, x)));
-    double be = 0.0;
-    for (int n = 0; n <= tg.nt; ++n) be += tg.weight[n] * cos(n * th);
-    b.mu[j] = 1.0 - be;
-  }
-  b.modes.assign((size_t)nd * g->dim, 0);
-  cudaError_t e = cudaMalloc(&b.d_coef, (size_t)kMaxND * sizeof(double));
-  if (e != cudaSuccess) { cudaFree(Y); return cuda_fail(g, e, "cudaMalloc"); }
-  free_basis(g);
-  g->basis = std::move(b);
+  return install_ritz_basis(g, p, tg, Y, nd, theta, flags, theta_host, resid_host);
 #undef LZ_TRY
 #undef LZ_CUDA
   return WHV_OK;
 }
 
+// ------------------------------------------------------------------ thick-restart Lanczos
+static bool log_on_lz() {
+  static const bool on = [] { const char* e = getenv("WHV_LOG"); return e && e[0] == '1'; }();
+  return on;
+}
+
+// Top kw eigenpairs of the dense symmetric n x n matrix H (row-major): Householder reduction to
+// tridiagonal form H = P T P^T, the tridiagonal eigenpairs by bisection and inverse iteration,
+// eigenvectors S = P S_T (n x kw, column-major).
+static void dense_top_eigenpairs(std::vector<double> A, int n, int kw, std::vector<double>& theta,
+                                 std::vector<double>& S) {
+  std::vector<double> P((size_t)n * n, 0.0);   // row-major
+  for (int i = 0; i < n; ++i) P[(size_t)i * n + i] = 1.0;
+  std::vector<double> v(n), pv(n), q(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;   // length of the column below the diagonal
+    double nx = 0.0;
+    for (int i = 0; i < m; ++i) nx += A[(size_t)(k + 1 + i) * n + k] * A[(size_t)(k + 1 + i) * n + k];
+    nx = sqrt(nx);
+    if (nx == 0.0) continue;
+    const double x0 = A[(size_t)(k + 1) * n + k];
+    const double alpha = x0 >= 0.0 ? -nx : nx;
+    for (int i = 0; i < m; ++i) v[i] = A[(size_t)(k + 1 + i) * n + k];
+    v[0] -= alpha;
+    double nv = 0.0;
+    for (int i = 0; i < m; ++i) nv += v[i] * v[i];
+    nv = sqrt(nv);
+    if (nv == 0.0) continue;
+    for (int i = 0; i < m; ++i) v[i] /= nv;
+    // trailing block: A22 <- (I - 2 v v^T) A22 (I - 2 v v^T) = A22 - 2 (v q^T + q v^T)
+    for (int i = 0; i < m; ++i) {
+      double sacc = 0.0;
+      for (int j = 0; j < m; ++j) sacc += A[(size_t)(k + 1 + i) * n + (k + 1 + j)] * v[j];
+      pv[i] = sacc;
+    }
+    double K = 0.0;
+    for (int i = 0; i < m; ++i) K += v[i] * pv[i];
+    for (int i = 0; i < m; ++i) q[i] = pv[i] - K * v[i];
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) A[(size_t)(k + 1 + i) * n + (k + 1 + j)] -= 2.0 * (v[i] * q[j] + q[i] * v[j]);
+    A[(size_t)(k + 1) * n + k] = A[(size_t)k * n + (k + 1)] = alpha;
+    for (int i = 1; i < m; ++i) A[(size_t)(k + 1 + i) * n + k] = A[(size_t)k * n + (k + 1 + i)] = 0.0;
+    // P <- P (I - 2 v v^T) on columns k+1 .. n-1
+    for (int r = 0; r < n; ++r) {
+      double sacc = 0.0;
+      for (int j = 0; j < m; ++j) sacc += P[(size_t)r * n + (k + 1 + j)] * v[j];
+      for (int j = 0; j < m; ++j) P[(size_t)r * n + (k + 1 + j)] -= 2.0 * sacc * v[j];
+    }
+  }
+  std::vector<double> a(n), b(n, 0.0), St;
+  for (int i = 0; i < n; ++i) a[i] = A[(size_t)i * n + i];
+  for (int i = 0; i + 1 < n; ++i) b[i] = A[(size_t)(i + 1) * n + i];
+  top_eigenpairs(a, b, n, kw, theta, St);
+  S.assign((size_t)n * kw, 0.0);
+  for (int j = 0; j < kw; ++j)
+    for (int r = 0; r < n; ++r) {
+      double sacc = 0.0;
+      for (int c = 0; c < n; ++c) sacc += P[(size_t)r * n + c] * St[(size_t)j * n + c];
+      S[(size_t)j * n + r] = sacc;
+    }
+}
+
+// Thick-restart Lanczos (Wu and Simon 2000) on S_h in the M inner product: basis of at most m
+// vectors, the `keep` largest Ritz vectors and the residual vector carried over a restart.  Every
+// step re-orthogonalises against the whole basis (classical Gram-Schmidt twice, FP64), so the
+// projected matrix H = Q^T M S_h Q is filled from the Gram-Schmidt coefficients; the Ritz
+// residual of pair i is |b s_{m,i}| with b the norm of the last, unnormalised vector.
+static whv_status lanczos_thick_impl(whv_grid g, const whv_params* p, int nd, int m, int keep, int max_restarts,
+                                     double tol, const double* v0_dev, int fp64_stepping, int flags,
+                                     double* theta_host, double* resid_host, int* stats) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  TimeGridH tg;
+  whv_status s = make_time_grid(g, p, &tg);
+  if (s != WHV_OK) return s;
+  if (keep <= 0) keep = std::min(m - 2, nd + std::max(nd / 2, 8));
+  if (nd < 1 || keep < nd || keep > m - 2 || m > kMaxND || m > g->N || max_restarts < 0 || !(tol > 0.0))
+    return fail(g, WHV_ERR_INVALID, "need 1 <= nd <= keep <= m - 2, m <= min(N, 1024), max_restarts >= 0, tol > 0");
+  const int prec = fp64_stepping ? WHV_FP64 : g->precision;
+  if (prec == WHV_FP64 && g->precision != WHV_FP64) {
+    s = ensure_fp64_buffers(g);
+    if (s != WHV_OK) return s;
+  }
+  const int64_t N = g->N;
+  double *Q = nullptr, *Y = nullptr, *dS = nullptr;
+  auto cleanup = [&]() { for (double* x : {Q, Y, dS}) if (x) cudaFree(x); };
+#define TL_TRY(expr) do { whv_status _s = (expr); if (_s != WHV_OK) { cleanup(); return _s; } } while (0)
+#define TL_CUDA(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) { cleanup(); return cuda_fail(g, _e, #call); } } while (0)
+  TL_CUDA(cudaMalloc(&Q, (size_t)m * N * sizeof(double)));
+  TL_CUDA(cudaMalloc(&Y, (size_t)keep * N * sizeof(double)));
+  TL_CUDA(cudaMalloc(&dS, (size_t)m * keep * sizeof(double)));
+  TL_CUDA(cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kMaxND * kRitzJC * sizeof(double))));
+  if (v0_dev) {
+    TL_CUDA(cudaMemcpyAsync(Q, v0_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+  } else {
+    k_start_vector<<<148 * 4, 256, 0, g->stream>>>(Q, N, 1ull);
+    count_launches(1);
+    TL_CUDA(cudaGetLastError());
+  }
+  TL_TRY(dot_async(g, Q, Q, S_TMP));
+  TL_TRY(fetch_scalars(g));
+  if (!(g->scal_host[S_TMP] > 0.0)) { cleanup(); return fail(g, WHV_ERR_INVALID, "zero start vector"); }
+  TL_TRY(axpby(g, N, 1.0 / sqrt(g->scal_host[S_TMP]), Q, 0.0, Q));
+  std::vector<double> H((size_t)m * m, 0.0), h1(m), h2(m), theta, S;
+  int j0 = 0, restarts = 0, nws = 0, conv = 0;
+  double bres = 0.0;
+  while (true) {
+    for (int j = j0; j < m; ++j) {
+      double* qj = Q + (size_t)j * N;
+      double* z = j + 1 < m ? Q + (size_t)(j + 1) * N : g->q;
+      TL_CUDA(cudaMemcpyAsync(g->p, qj, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+      TL_TRY(wave_solve(g, tg, g->p, nullptr, g->t, 0, prec));
+      ++nws;
+      TL_CUDA(cudaMemcpyAsync(z, g->t, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+      TL_TRY(project(g, Q, j + 1, z, g->small));
+      TL_TRY(expand(g, Q, j + 1, g->small, -1.0, z));
+      cudaMemcpyAsync(h1.data(), g->small, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+      TL_TRY(project(g, Q, j + 1, z, g->small));
+      TL_TRY(expand(g, Q, j + 1, g->small, -1.0, z));
+      cudaMemcpyAsync(h2.data(), g->small, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+      TL_TRY(dot_async(g, z, z, S_TMP));
+      TL_TRY(fetch_scalars(g));   // synchronises: h1, h2 are on the host too
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = H[(size_t)j * m + i] = h1[i] + h2[i];
+      bres = sqrt(g->scal_host[S_TMP]);
+      if (!isfinite(bres)) { cleanup(); return fail(g, WHV_ERR_BREAKDOWN, "non-finite Lanczos vector"); }
+      if (bres > 1e-14) {
+        TL_TRY(axpby(g, N, 1.0 / bres, z, 0.0, z));
+      } else if (j + 1 < m) {
+        cleanup();
+        return fail(g, WHV_ERR_BREAKDOWN, "invariant subspace before the basis filled");
+      }   // else: the full basis is invariant, every Ritz pair is exact (residual estimates 0)
+      if (j + 1 < m) H[(size_t)(j + 1) * m + j] = H[(size_t)j * m + (j + 1)] = bres;
+    }
+    dense_top_eigenpairs(H, m, keep, theta, S);
+    conv = 0;
+    for (int i = 0; i < nd; ++i) conv += fabs(bres * S[(size_t)i * m + (m - 1)]) <= tol ? 1 : 0;
+    if (log_on_lz())
+      fprintf(stderr, "[whv] thick-restart Lanczos: restart %d, %d wave solves, %d of %d converged\n", restarts, nws,
+              conv, nd);
+    if (conv == nd || restarts == max_restarts) break;
+    ++restarts;
+    // keep the `keep` largest Ritz vectors and the residual vector (normalised, in g->q)
+    TL_CUDA(cudaMemcpyAsync(dS, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    for (int c0 = 0; c0 < keep; c0 += kRitzJC) {
+      const int blocks = (int)std::min<int64_t>((N + 255) / 256, 148 * 8);
+      k_ritz<<<blocks, 256, (size_t)m * kRitzJC * sizeof(double), g->stream>>>(Q, N, m, dS, keep, c0, Y);
+      count_launches(1);
+      TL_CUDA(cudaGetLastError());
+    }
+    TL_CUDA(cudaMemcpyAsync(Q, Y, (size_t)keep * N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    TL_CUDA(cudaMemcpyAsync(Q + (size_t)keep * N, g->q, N * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    TL_CUDA(cudaStreamSynchronize(g->stream));   // dS is read from the pageable S before it changes
+    std::fill(H.begin(), H.end(), 0.0);
+    for (int i = 0; i < keep; ++i) {
+      H[(size_t)i * m + i] = theta[i];
+      H[(size_t)i * m + keep] = H[(size_t)keep * m + i] = bres * S[(size_t)i * m + (m - 1)];
+    }
+    j0 = keep;
+  }
+  // the nd wanted Ritz vectors
+  std::vector<double> Snd(S.begin(), S.begin() + (size_t)nd * m), th(theta.begin(), theta.begin() + nd);
+  TL_CUDA(cudaMemcpyAsync(dS, Snd.data(), Snd.size() * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+  double* Yf = nullptr;
+  TL_CUDA(cudaMalloc(&Yf, (size_t)nd * N * sizeof(double)));
+  for (int c0 = 0; c0 < nd; c0 += kRitzJC) {
+    const int blocks = (int)std::min<int64_t>((N + 255) / 256, 148 * 8);
+    k_ritz<<<blocks, 256, (size_t)m * kRitzJC * sizeof(double), g->stream>>>(Q, N, m, dS, nd, c0, Yf);
+    count_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { cudaFree(Yf); cleanup(); return cuda_fail(g, e, "k_ritz"); }
+  }
+  const cudaError_t e = cudaStreamSynchronize(g->stream);
+  cleanup();
+  if (e != cudaSuccess) { cudaFree(Yf); return cuda_fail(g, e, "thick-restart Lanczos"); }
+  if (stats) { stats[0] = restarts; stats[1] = nws; stats[2] = conv; }
+#undef TL_TRY
+#undef TL_CUDA
+  return install_ritz_basis(g, p, tg, Yf, nd, th, flags, theta_host, resid_host);
+}
+
 extern "C" whv_status whv_lanczos(whv_grid g, const whv_params* p, int nd, int m, const double* v0_dev,
                                   int fp64_stepping, int flags, double* theta_host, double* resid_host) {
   const whv_status s = lanczos_impl(g, p, nd, m, v0_dev, fp64_stepping, flags, theta_host, resid_host);
+  if (!g) return s;
+  const whv_status e = take_persist_error(g);   // a persistent wave solve that gave up
+  return e != WHV_OK ? e : s;
+}
+
+extern "C" whv_status whv_lanczos_restarted(whv_grid g, const whv_params* p, int nd, int m, int keep,
+                                            int max_restarts, double tol, const double* v0_dev, int fp64_stepping,
+                                            int flags, double* theta_host, double* resid_host, int* stats_host) {
+  const whv_status s = lanczos_thick_impl(g, p, nd, m, keep, max_restarts, tol, v0_dev, fp64_stepping, flags,
+                                          theta_host, resid_host, stats_host);
   if (!g) return s;
   const whv_status e = take_persist_error(g);   // a persistent wave solve that gave up
   return e != WHV_OK ? e : s;

@@ -74,6 +74,8 @@ def _load():
         "whv_solve_adjoint": [P, ctypes.POINTER(whv_params), P, P, P, P, P, P, I, ctypes.POINTER(whv_info)],
         "whv_inject_barrier_error": [P],
         "whv_compress_basis": [P, D, ctypes.POINTER(I)],
+        "whv_lanczos_restarted": [P, ctypes.POINTER(whv_params), I, I, I, I, D, P, I, I, ctypes.POINTER(D),
+                                  ctypes.POINTER(D), ctypes.POINTER(I)],
         "whv_solve_batched": [I, ctypes.POINTER(P), ctypes.POINTER(whv_params), ctypes.POINTER(P),
                               ctypes.POINTER(P), ctypes.POINTER(whv_info)],
     }
@@ -100,7 +102,7 @@ EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_gr
             "whv_expand", "whv_dot", "whv_num_unknowns", "whv_last_error", "whv_version",
             "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune",
             "whv_project_noalloc", "whv_lanczos", "whv_solve_adjoint", "whv_solve_batched",
-            "whv_inject_barrier_error", "whv_compress_basis"]
+            "whv_inject_barrier_error", "whv_compress_basis", "whv_lanczos_restarted"]
 
 
 def _check(status, handle=None, allow=()):
@@ -260,6 +262,18 @@ class Grid:
         k = ctypes.c_int()
         _check(lib.whv_get_steps_per_sweep(self.handle, ctypes.byref(k)), self.handle)
         return k.value
+
+    def whv_lanczos_restarted(self, params, nd, m, max_restarts=50, tol=1e-9, v0=None, fp64_stepping=True,
+                              flags=0, keep=0):
+        """Thick-restart Lanczos; returns (theta, resid, {restarts, wave_solves, converged})."""
+        self._pre()
+        theta = (ctypes.c_double * nd)()
+        resid = (ctypes.c_double * nd)()
+        st = (ctypes.c_int * 3)()
+        _check(lib.whv_lanczos_restarted(self.handle, ctypes.byref(params), int(nd), int(m), int(keep),
+                                         int(max_restarts), float(tol), _ptr(v0, self.N), int(bool(fp64_stepping)),
+                                         int(flags), theta, resid, st), self.handle)
+        return list(theta), list(resid), {"restarts": st[0], "wave_solves": st[1], "converged": st[2]}
 
     def whv_compress_basis(self, tau):
         """SVD-compress the basis (2-D); returns the rank of every vector."""

@@ -101,3 +101,46 @@ def test_dcg_general_basis_fixed_iterations(npts, order, speed):
     ref = K.dcg(og, K.Operator(og, tg), WH.rhs_b(og, tg, f), W, 0.0, k)
     assert info["iterations"] == k
     assert IND.relmax(u.cpu().numpy(), ref.x) < 1e-11
+
+
+def test_thick_restart_lanczos_matches_the_dense_spectrum():
+    """Thick-restart Lanczos on the device (basis of 3 nd + 4 vectors, restarted) converges to the
+    top eigenpairs the oracle's restarted Lanczos and the dense eigen-solve give."""
+    npts, nd = (19, 17), 8
+    c2 = I.speed_squared("c3", npts, 4)
+    og = O.Grid(npts, order=4, c2=c2)
+    tg = WH.time_grid_for(og, 14.0)
+    v0 = I.random_field(og.shape, 1)
+    ref = LZ.lanczos_thick(og, tg, nd, 3 * nd + 4, v0, max_restarts=400, tol=1e-11)
+    g = whv.Grid(npts, order=4, precision=whv.WHV_FP64)
+    g.whv_set_speed(dev(c2))
+    prm = whv.make_params(14.0)
+    theta, resid, st = g.whv_lanczos_restarted(prm, nd, 3 * nd + 4, max_restarts=400, tol=1e-11, v0=dev(v0))
+    assert st["converged"] == nd and st["restarts"] > 0
+    assert np.allclose(theta, ref.theta, atol=1e-9)
+    got = g.whv_get_basis(want_vectors=True)
+    assert np.allclose(np.array(got["lambda2"]), ref.lambda2, rtol=1e-8)
+    assert max(resid) < 1e-7
+
+
+def test_thick_restart_basis_deflates_a_solve():
+    """A larger variable-speed grid: 32 vectors from a 100-vector restarted basis deflate DCG
+    (Algorithm 4) to the direct solution with fewer iterations than undeflated CG."""
+    npts, omega = (129, 121), 24.0
+    c2 = I.speed_squared("c3", npts, 7)
+    og = O.Grid(npts, order=4, c2=c2)
+    tg = WH.time_grid_for(og, omega)
+    f = I.gaussian(npts, [0.42, 0.57], 1 / omega, omega ** 2)
+    U = IND.helmholtz_direct(npts, tg.omega_eff, f, 4, c2)
+    g = whv.Grid(npts, order=4, precision=whv.WHV_FP64)
+    g.whv_set_speed(dev(c2))
+    prm = whv.make_params(omega, method="dcg", tol=1e-9, maxit=5000, true_residual=True)
+    _, _, st = g.whv_lanczos_restarted(prm, 32, 100, max_restarts=60, tol=1e-8)
+    assert st["converged"] >= 24
+    u, info = g.whv_solve(prm, dev(f))
+    assert info["status"] == "OK"
+    assert IND.relmax(u.cpu().numpy(), U) < 1e-6
+    g0 = whv.Grid(npts, order=4, precision=whv.WHV_FP64)
+    g0.whv_set_speed(dev(c2))
+    _, i0 = g0.whv_solve(whv.make_params(omega, method="cg", tol=1e-9, maxit=5000), dev(f))
+    assert info["iterations"] < i0["iterations"]

@@ -111,7 +111,9 @@ def test_agmres_lanczos_basis_fp32_with_fp64_correction():
     U = IND.helmholtz_direct(npts, tg.omega_eff, f, 4, c2)
     g = whv.Grid(npts, order=4, precision=whv.WHV_FP32_STEP)
     g.whv_set_speed(dev(c2))
-    prm = whv.make_params(omega, method="agmres", tol=1e-9, maxit=6000, restart=30, true_residual=True,
+    # restart 60: with these approximate vectors (Ritz residuals 1e-2 .. 1) GMRES(30) stagnates
+    # in the correction solves (thousands of iterations), GMRES(60) does not
+    prm = whv.make_params(omega, method="agmres", tol=1e-9, maxit=6000, restart=60, true_residual=True,
                           refine_fp64=True)
     g.whv_set_deflation_basis(prm, 24, whv.WHV_BASIS_LANCZOS)
     u, info = g.whv_solve(prm, dev(f))

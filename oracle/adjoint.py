@@ -30,9 +30,15 @@ from .waveholtz import TimeGrid, wave_states, apply_pi
 from . import krylov as K
 
 
+def _nonconservative_only(grid: Grid):
+    if getattr(grid, "form", "nonconservative") != "nonconservative" and grid.c2 is not None:
+        raise ValueError("the adjoint here differentiates the non-conservative operator c^2 Delta_h")
+
+
 def reverse_sweep(grid: Grid, tg: TimeGrid, states, abar):
     """Transpose of one wave solve at the forward states W^0..W^Nt: returns (vbar, c2bar, fbar)
     for the adjoint seed abar of the filtered output."""
+    _nonconservative_only(grid)
     dt2 = tg.dt * tg.dt
     w = tg.filter_weights()
     ph = tg.forcing_phase()
@@ -57,6 +63,7 @@ def reverse_sweep(grid: Grid, tg: TimeGrid, states, abar):
 
 def apply_St(grid: Grid, tg: TimeGrid, a):
     """S_h^T a (reverse sweep with f = 0; the forward states do not enter vbar)."""
+    _nonconservative_only(grid)
     dt2 = tg.dt * tg.dt
     w = tg.filter_weights()
     c2 = np.ones(grid.shape) if grid.c2 is None else grid.c2

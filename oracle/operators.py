@@ -8,6 +8,11 @@ nodes.  Readings used here:
     speed multiplies the discrete Laplacian).  It is self-adjoint in the inner product
     <u, v>_M = sum_j u_j v_j / c_j^2, the diagonal-mass-matrix symmetrisation of Sec. 4.1
     with M = diag(1/c^2); for c = 1 this is the Euclidean inner product.
+  * The conservative form L_h = div_h(c^2 grad_h) (order 2 only, `form="conservative"`):
+    per direction (c^2_{j+1/2} (u_{j+1} - u_j) - c^2_{j-1/2} (u_j - u_{j-1})) / h^2 with the
+    face values c^2_{j+1/2} = (c^2_j + c^2_{j+1}) / 2 and, on the two boundary faces, the value
+    of the adjacent interior node (reading: c^2 is given on the interior nodes only).  It is
+    self-adjoint in the Euclidean inner product (M = I).
   * 4th order (p = 4): the centred five-point formula per direction, with the value at the
     ghost node outside the Dirichlet boundary taken as the odd reflection of the first
     interior value (u_{-1} = -u_1).  The paper leaves the near-boundary closure to
@@ -22,7 +27,7 @@ import numpy as np
 class Grid:
     """Structured box grid: `npts` nodes per direction (x first), boundary included."""
 
-    def __init__(self, npts, lo=None, hi=None, order=2, c2=None):
+    def __init__(self, npts, lo=None, hi=None, order=2, c2=None, form="nonconservative"):
         self.dim = len(npts)
         self.npts = tuple(int(n) for n in npts)
         self.lo = [0.0] * self.dim if lo is None else [float(a) for a in lo]
@@ -34,6 +39,11 @@ class Grid:
         # array axes are (z, y, x): axis for direction m is dim-1-m
         self.shape = tuple(n - 2 for n in reversed(self.npts))
         self.c2 = None if c2 is None else np.asarray(c2, dtype=np.float64).reshape(self.shape)
+        if form not in ("nonconservative", "conservative"):
+            raise ValueError(form)
+        if form == "conservative" and order != 2:
+            raise ValueError("the conservative form is second order")
+        self.form = form
 
     @property
     def n(self):
@@ -44,8 +54,8 @@ class Grid:
         return 1.0 if self.c2 is None else float(np.sqrt(self.c2.max()))
 
     def weights(self):
-        """Diagonal of M: 1/c^2 (ones for c = 1)."""
-        if self.c2 is None:
+        """Diagonal of M: 1/c^2 (ones for c = 1 and for the conservative form)."""
+        if self.c2 is None or self.form == "conservative":
             return np.ones(self.shape)
         return 1.0 / self.c2
 
@@ -94,8 +104,30 @@ def laplacian(grid: Grid, u: np.ndarray) -> np.ndarray:
     return out
 
 
+def _conservative_difference(u, c2, axis, h):
+    """(c^2_{j+1/2} (u_{j+1} - u_j) - c^2_{j-1/2} (u_j - u_{j-1})) / h^2 along `axis`, u = 0 at
+    the boundary nodes, interior faces by the mean of their two nodes, boundary faces by the
+    adjacent interior node."""
+    n = u.shape[axis]
+    sl = lambda a, b: tuple(slice(a, b) if k == axis else slice(None) for k in range(u.ndim))  # noqa: E731
+    pad = [(0, 0)] * u.ndim
+    pad[axis] = (1, 1)
+    up = np.pad(u, pad)
+    # faces j - 1/2 for j = 0 .. n (n + 1 of them)
+    faces = np.concatenate([c2[sl(0, 1)], 0.5 * (c2[sl(0, n - 1)] + c2[sl(1, n)]), c2[sl(n - 1, n)]], axis=axis)
+    flux = faces * (up[sl(1, n + 2)] - up[sl(0, n + 1)])   # c^2_{j-1/2} (u_j - u_{j-1}), j = 0 .. n
+    return (flux[sl(1, n + 1)] - flux[sl(0, n)]) / (h * h)
+
+
 def apply_L(grid: Grid, u: np.ndarray) -> np.ndarray:
-    """L_{p,h} u = c^2 Delta_{p,h} u (eq. discreteHelmholtz with L = c^2 Delta)."""
+    """L_{p,h} u = c^2 Delta_{p,h} u (eq. discreteHelmholtz with L = c^2 Delta), or the
+    conservative div_h(c^2 grad_h) u."""
+    if grid.c2 is not None and grid.form == "conservative":
+        u = np.asarray(u, dtype=np.float64).reshape(grid.shape)
+        out = np.zeros(grid.shape)
+        for m in range(grid.dim):
+            out += _conservative_difference(u, grid.c2, grid.dim - 1 - m, grid.h[m])
+        return out
     lap = laplacian(grid, u)
     return lap if grid.c2 is None else grid.c2 * lap
 

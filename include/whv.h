@@ -61,6 +61,12 @@ enum {
                      two wave solves per iteration; no basis = BiCGStab                    */
 };
 
+/* form of the variable-speed operator (whv_set_speed_form) */
+enum {
+  WHV_SPEED_NONCONSERVATIVE = 0,  /* L_h = c^2 Delta_h (any order), inner products <u,v>_M, M = 1/c^2 */
+  WHV_SPEED_CONSERVATIVE = 1      /* L_h = div_h(c^2 grad_h) (eq. L, second order), Euclidean      */
+};
+
 /* origin of the deflation basis (whv_set_deflation_basis) */
 enum {
   WHV_BASIS_NONE = 0,         /* remove the basis                                          */
@@ -130,6 +136,16 @@ whv_status whv_destroy_grid(whv_grid grid);
  * the call completes on the stream).  c2_dev = NULL restores c = 1.  Any existing deflation basis
  * is dropped.  Requires c^2 > 0 (checked). */
 whv_status whv_set_speed(whv_grid grid, const double* c2_dev);
+
+/* Squared speed with the operator form: WHV_SPEED_NONCONSERVATIVE is whv_set_speed;
+ * WHV_SPEED_CONSERVATIVE (second-order grids) makes L_h = div_h(c^2 grad_h) u (eq. L): per axis
+ * (c^2_{j+1/2} (u_{j+1} - u_j) - c^2_{j-1/2} (u_j - u_{j-1})) / h^2, face values the mean of the
+ * two nodes' c^2 (the adjacent interior value on the faces to the boundary nodes).  This operator
+ * is symmetric in the Euclidean inner product, which all Krylov and deflation products then use.
+ * Its wave solves run one step per launch (the blocked, persistent and single-CTA kernels are
+ * bypassed); whv_solve_batched and whv_solve_adjoint refuse such grids.  Extra device memory:
+ * dim N doubles + dim N floats of face values. */
+whv_status whv_set_speed_form(whv_grid grid, const double* c2_dev, int form);
 
 /* Time grid the given parameters select (reading of Sec. 2.2): nt steps of dt over Tbar,
  * cos/filter frequency omega_hat, fixed-point frequency omega_eff.  Host outputs, any may be NULL.

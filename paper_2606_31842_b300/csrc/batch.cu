@@ -987,6 +987,7 @@ extern "C" whv_status whv_solve_batched(int nprob, const whv_grid* grids, const 
       return fail(g0, WHV_ERR_INVALID,
                   "whv_solve_batched: grids must share stream, precision, dimension, order and speed kind");
     if (params[p].method != WHV_CG) return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: method must be WHV_CG");
+    if (g->cons) return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: the conservative operator is not batched");
     if (((params[p].flags & WHV_REFINE_FP64) != 0) != refine)
       return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: WHV_REFINE_FP64 must be set for all problems or none");
     if (!(params[p].tol >= 0.0) || params[p].maxit < 0)

@@ -150,7 +150,8 @@ static void free_all(whv_grid g) {
                   g->t, g->fd, g->krylov, g->small, g->small2, g->partials, g->counters, g->gbar, g->scal,
                   g->basis.V, g->basis.d_coef, g->basis.AW, g->basis.Einv, g->basis.QAW, g->basis.cU, g->basis.cV,
                   g->basis.cs, g->basis.cT, g->basis.cc, g->basis.cR, g->basis.coff, g->basis.cowner, g->wbuf64[0], g->wbuf64[1], g->wbuf64[2],
-                  g->wbuf64[3], g->acc64, g->xo, g->ro, g->bo, g->wtab_small};
+                  g->wbuf64[3], g->acc64, g->xo, g->ro, g->bo, g->wtab_small, g->face64[0], g->face64[1],
+                  g->face64[2], g->face32[0], g->face32[1], g->face32[2]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->scal_host) cudaFreeHost(g->scal_host);
@@ -261,11 +262,44 @@ whv_status whv_destroy_grid(whv_grid g) {
   return WHV_OK;
 }
 
+// face values of the conservative operator: face[m][idx] between node idx and its + neighbour
+// along axis m (mean of the two c^2), or the node's own c^2 on the face to the boundary node
+__global__ void k_faces(const double* __restrict__ c2, int nx, int ny, int nz, int dim, double* __restrict__ f0,
+                        double* __restrict__ f1, double* __restrict__ f2, float* __restrict__ g0,
+                        float* __restrict__ g1, float* __restrict__ g2) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(idx % nx), y = (int)((idx / nx) % ny), z = (int)(idx / ((int64_t)nx * ny));
+    const double c = c2[idx];
+    const double fx = x < nx - 1 ? 0.5 * (c + c2[idx + 1]) : c;
+    f0[idx] = fx; g0[idx] = (float)fx;
+    if (dim > 1) {
+      const double fy = y < ny - 1 ? 0.5 * (c + c2[idx + nx]) : c;
+      f1[idx] = fy; g1[idx] = (float)fy;
+    }
+    if (dim > 2) {
+      const double fz = z < nz - 1 ? 0.5 * (c + c2[idx + (int64_t)nx * ny]) : c;
+      f2[idx] = fz; g2[idx] = (float)fz;
+    }
+  }
+}
+
+static void free_faces(whv_grid g) {
+  for (int m = 0; m < 3; ++m) {
+    if (g->face64[m]) cudaFree(g->face64[m]);
+    if (g->face32[m]) cudaFree(g->face32[m]);
+    g->face64[m] = nullptr;
+    g->face32[m] = nullptr;
+  }
+  g->cons = 0;
+}
+
 whv_status whv_set_speed(whv_grid g, const double* c2_dev) {
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
   // any basis was built for the old operator
   free_basis(g);
   free_plan(g);
+  free_faces(g);
   if (!c2_dev) {
     if (g->c2) cudaFree(g->c2);
     if (g->c2f) cudaFree(g->c2f);
@@ -290,6 +324,30 @@ whv_status whv_set_speed(whv_grid g, const double* c2_dev) {
     return fail(g, WHV_ERR_INVALID, "c^2 must be finite and > 0 at every interior node");
   }
   g->c2max = g->scal_host[S_TMP2];
+  return WHV_OK;
+}
+
+whv_status whv_set_speed_form(whv_grid g, const double* c2_dev, int form) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  if (form != WHV_SPEED_NONCONSERVATIVE && form != WHV_SPEED_CONSERVATIVE)
+    return fail(g, WHV_ERR_INVALID, "unknown speed form");
+  if (form == WHV_SPEED_CONSERVATIVE && (!c2_dev || g->order != 2))
+    return fail(g, WHV_ERR_INVALID, "the conservative form needs c^2 and a second-order grid");
+  whv_status s = whv_set_speed(g, c2_dev);
+  if (s != WHV_OK || form == WHV_SPEED_NONCONSERVATIVE) return s;
+  // div_h(c^2 grad_h) is symmetric in the Euclidean inner product: no M weights
+  cudaFree(g->mw);
+  g->mw = nullptr;
+  for (int m = 0; m < g->dim; ++m) {
+    WHV_CUDA(g, cudaMalloc(&g->face64[m], g->N * 8));
+    WHV_CUDA(g, cudaMalloc(&g->face32[m], g->N * 4));
+  }
+  k_faces<<<kRedBlocks, 256, 0, g->stream>>>(g->c2, g->n[0], g->n[1], g->n[2], g->dim, g->face64[0], g->face64[1],
+                                             g->face64[2], g->face32[0], g->face32[1], g->face32[2]);
+  count_launches(1);
+  WHV_CUDA(g, cudaGetLastError());
+  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
+  g->cons = 1;
   return WHV_OK;
 }
 

@@ -85,6 +85,19 @@ __global__ void __launch_bounds__(256) k_apply_L(const double* __restrict__ y, c
   out[idx] = L;
 }
 
+// out = div_h(c^2 grad_h) y (FP64, conservative form)
+template <int DIM>
+__global__ void __launch_bounds__(256) k_apply_L_cons(const double* __restrict__ y, ConsFaces<double> fc,
+                                                      double* __restrict__ out, int nx, int ny, int nz,
+                                                      StepCoef<double> cf) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int yy = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= nx || yy >= ny) return;
+  const int64_t idx = x + (int64_t)nx * (yy + (int64_t)ny * z);
+  out[idx] = lap_cons<DIM, double>(y, idx, x, yy, z, nx, ny, nz, fc, cf, y[idx]);
+}
+
 static whv_status apply_L_fp64(whv_grid g, const double* y, double* out) {
   StepCoef<double> cf{};
   for (int m = 0; m < 3; ++m) {
@@ -95,6 +108,15 @@ static whv_status apply_L_fp64(whv_grid g, const double* y, double* out) {
   if (g->dim == 1) { block = dim3(256, 1, 1); grid = dim3((g->n[0] + 255) / 256, 1, 1); }
   else { block = dim3(32, 8, 1); grid = dim3((g->n[0] + 31) / 32, (g->n[1] + 7) / 8, g->dim > 2 ? g->n[2] : 1); }
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  if (g->cons) {
+    ConsFaces<double> fc{{g->face64[0], g->face64[1], g->face64[2]}, g->c2};
+    if (g->dim == 1) k_apply_L_cons<1><<<grid, block, 0, g->stream>>>(y, fc, out, nx, ny, nz, cf);
+    else if (g->dim == 2) k_apply_L_cons<2><<<grid, block, 0, g->stream>>>(y, fc, out, nx, ny, nz, cf);
+    else k_apply_L_cons<3><<<grid, block, 0, g->stream>>>(y, fc, out, nx, ny, nz, cf);
+    count_launches(1);
+    WHV_CUDA(g, cudaGetLastError());
+    return WHV_OK;
+  }
   switch (g->dim * 10 + g->order) {
     case 12: k_apply_L<1, 2><<<grid, block, 0, g->stream>>>(y, g->c2, out, nx, ny, nz, cf); break;
     case 14: k_apply_L<1, 4><<<grid, block, 0, g->stream>>>(y, g->c2, out, nx, ny, nz, cf); break;

@@ -941,6 +941,7 @@ static whv_status adjoint_impl(whv_grid g, const whv_params* p, const double* f,
   if (method == WHV_DCG && B.nd == 0) return fail(g, WHV_ERR_INVALID, "DCG needs a deflation basis");
   const int K = checkpoint_every > 0 ? checkpoint_every : 16;
   if (K > 1024) return fail(g, WHV_ERR_INVALID, "checkpoint_every must be <= 1024");
+  if (g->cons) return fail(g, WHV_ERR_INVALID, "the adjoint differentiates the non-conservative operator c^2 Delta_h");
   const bool refine = (p->flags & WHV_REFINE_FP64) != 0;
   const int64_t N = g->N;
   TRY(ensure_fp64_buffers(g));

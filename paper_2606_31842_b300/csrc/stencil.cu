@@ -106,6 +106,67 @@ __global__ void __launch_bounds__(256) k_step(const T* __restrict__ wc, T* __res
   }
 }
 
+// Conservative operator div_h(c^2 grad_h) (second order): first step and step kernels, same
+// structure and epilogues as k_first / k_step with lap_cons in place of c^2 Delta_h.
+template <typename T, int DIM, bool FORCE, bool ZERO_V>
+__global__ void __launch_bounds__(256) k_first_cons(const double* __restrict__ v, T* __restrict__ w0,
+                                                    T* __restrict__ w1, T* __restrict__ acc, ConsFaces<T> fc,
+                                                    const double* __restrict__ f, int nx, int ny, int nz,
+                                                    StepCoef<T> cf) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= nx || y >= ny) return;
+  const int64_t idx = x + (int64_t)nx * (y + (int64_t)ny * z);
+  T W0 = T(0), L = T(0);
+  if (!ZERO_V) {
+    W0 = (T)v[idx];
+    L = lap_cons<DIM, T>(v, idx, x, y, z, nx, ny, nz, fc, cf, W0);
+  }
+  if (FORCE) L -= (T)f[idx];
+  const T W1 = fma(T(0.5) * cf.dt2, L, W0);
+  w0[idx] = W0;
+  w1[idx] = W1;
+  acc[idx] = fma(cf.w1, W1, cf.w0 * W0);
+}
+
+template <typename T, int DIM, bool FORCE, int KIND>
+__global__ void __launch_bounds__(256) k_step_cons(const T* __restrict__ wc, T* __restrict__ wp,
+                                                   T* __restrict__ acc, ConsFaces<T> fc,
+                                                   const double* __restrict__ f, const double* __restrict__ v,
+                                                   double* __restrict__ out, int nx, int ny, int nz, StepCoef<T> cf,
+                                                   double* partials, unsigned* counter, double* scal_out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  const bool in = (x < nx) && (y < ny);
+  double part = 0.0;
+  if (in) {
+    const int64_t idx = x + (int64_t)nx * (y + (int64_t)ny * z);
+    const T c = __ldg(wc + idx);
+    T L = lap_cons<DIM, T>(wc, idx, x, y, z, nx, ny, nz, fc, cf, c);
+    if (FORCE) L = fma(-(T)f[idx], cf.fph, L);
+    const T wn = fma(cf.dt2, L, fma(T(2), c, -wp[idx]));
+    const T a = fma(cf.w1, wn, acc[idx]);
+    if (KIND == K_STEP) {
+      wp[idx] = wn;
+      acc[idx] = a;
+    } else if (KIND == K_LAST_OUT) {
+      out[idx] = (double)a;
+    } else {   // Euclidean inner product (the conservative operator is symmetric without M)
+      const double vi = v[idx];
+      const double o = vi - (double)a;
+      out[idx] = o;
+      part = vi * o;
+    }
+  }
+  if (KIND == K_LAST_AV) {
+    part = block_sum(part);
+    double total;
+    if (grid_reduce(part, partials, counter, &total) && flat_tid() == 0) *scal_out = total;
+  }
+}
+
 // 3-D 7-point variant: each thread marches through a column of `zc` planes, keeping W^n at
 // z-1, z, z+1 in registers (the z neighbours cost no extra load) and loading the next plane
 // one iteration ahead; x / y neighbours come through L1.  Same arithmetic and summation order
@@ -235,10 +296,59 @@ static StepCoef<T> coef_of(whv_grid g, const TimeGridH& tg) {
   return cf;
 }
 
+template <typename T, int DIM, bool FORCE>
+static whv_status launch_solve_cons(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
+                                    double* out, int epi, int* nlaunch, void* const* bufs, void* accbuf) {
+  const LaunchShape ls = shape_of(g);
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  T* b0 = (T*)bufs[0];
+  T* b1 = (T*)bufs[1];
+  T* acc = (T*)accbuf;
+  ConsFaces<T> fc;
+  for (int m = 0; m < 3; ++m) fc.f[m] = (const T*)(sizeof(T) == 8 ? (const void*)g->face64[m] : (const void*)g->face32[m]);
+  fc.c2 = (const T*)(sizeof(T) == 8 ? (const void*)g->c2 : (const void*)g->c2f);
+  StepCoef<T> cf = coef_of<T>(g, tg);
+  dim3 fgrid = ls.grid;
+  if (DIM == 3) fgrid.z = nz;
+  if (v)
+    k_first_cons<T, DIM, FORCE, false><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, fc, f, nx, ny, nz, cf);
+  else
+    k_first_cons<T, DIM, FORCE, true><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, fc, f, nx, ny, nz, cf);
+  WHV_CUDA(g, cudaGetLastError());
+  *nlaunch = tg.nt;
+  T* wprev = b0;
+  T* wcur = b1;
+  double* part = chan(g, CH_STEP);
+  unsigned* cnt = g->counters + CH_STEP;
+  for (int n = 1; n < tg.nt; ++n) {
+    cf.fph = (T)tg.phase[n];
+    cf.w1 = (T)tg.weight[n + 1];
+    const bool last = (n == tg.nt - 1);
+    if (!last)
+      k_step_cons<T, DIM, FORCE, K_STEP><<<fgrid, ls.block, 0, g->stream>>>(wcur, wprev, acc, fc, f, nullptr, nullptr,
+                                                                            nx, ny, nz, cf, nullptr, nullptr, nullptr);
+    else if (epi == 0)
+      k_step_cons<T, DIM, FORCE, K_LAST_OUT><<<fgrid, ls.block, 0, g->stream>>>(wcur, wprev, acc, fc, f, nullptr, out,
+                                                                                nx, ny, nz, cf, nullptr, nullptr,
+                                                                                nullptr);
+    else
+      k_step_cons<T, DIM, FORCE, K_LAST_AV><<<fgrid, ls.block, 0, g->stream>>>(wcur, wprev, acc, fc, f, v, out, nx,
+                                                                               ny, nz, cf, part, cnt, g->scal + S_PQ);
+    WHV_CUDA(g, cudaGetLastError());
+    T* tmp = wprev;
+    wprev = wcur;
+    wcur = tmp;
+  }
+  return WHV_OK;
+}
+
 template <typename T, int DIM, int ORDER, bool VARC, bool FORCE>
 static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
                                double* out, int epi, int* nlaunch, void* const* bufs, void* accbuf,
                                int kb) {
+  if constexpr (ORDER == 2 && VARC) {
+    if (g->cons) return launch_solve_cons<T, DIM, FORCE>(g, tg, v, f, out, epi, nlaunch, bufs, accbuf);
+  }
   const LaunchShape ls = shape_of(g);
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
   T* b0 = (T*)bufs[0];
@@ -357,17 +467,18 @@ static whv_status launch_wave_solve(whv_grid g, const TimeGridH& tg, const doubl
   if ((int64_t)ls.grid.x * ls.grid.y * ls.grid.z > chan_cap(g, CH_STEP))
     return fail(g, WHV_ERR_INVALID, "grid too large for the fused reduction");
   if (prec < 0) prec = g->precision;
-  if (small_grid(g) && g->kblock == 0 && small_tables(g, tg) >= 0) {
+  if (!g->cons && small_grid(g) && g->kblock == 0 && small_tables(g, tg) >= 0) {
     *nl = 1;
     return small_wave_solve(g, tg, v, f, out, epi, prec);
   }
   // persistent 2-D wave solve (one cooperative launch) when selected and the tiles fit
-  if (prec == g->precision && g->kblock < 0 && persist_fits(g, -g->kblock, prec) && small_tables(g, tg) >= 0) {
+  if (!g->cons && prec == g->precision && g->kblock < 0 && persist_fits(g, -g->kblock, prec) &&
+      small_tables(g, tg) >= 0) {
     *nl = 1;
     return persist_wave_solve(g, tg, v, f, out, epi, -g->kblock, prec, g->wbuf);
   }
   if (prec == g->precision) {
-    const BufSet B{g->wbuf, g->acc, g->kblock > 0 ? g->kblock : default_kblock(g)};
+    const BufSet B{g->wbuf, g->acc, g->cons ? 1 : (g->kblock > 0 ? g->kblock : default_kblock(g))};
     return prec == WHV_FP64 ? dispatch<double>(g, tg, v, f, out, epi, nl, B)
                             : dispatch<float>(g, tg, v, f, out, epi, nl, B);
   }
@@ -407,7 +518,7 @@ void free_plan(whv_grid g) {
 }
 
 static bool uses_tables(whv_grid g) {
-  return (small_grid(g) && g->kblock == 0) || (g->dim == 2 && g->kblock < 0);
+  return !g->cons && ((small_grid(g) && g->kblock == 0) || (g->dim == 2 && g->kblock < 0));
 }
 
 whv_status take_persist_error(whv_grid g) {
@@ -514,9 +625,14 @@ extern "C" whv_status whv_autotune(whv_grid g, const whv_params* p, int* best) {
   TimeGridH tg;
   whv_status s = make_time_grid(g, p, &tg);
   if (s != WHV_OK) return s;
-  if (small_grid(g)) {   // the whole wave solve runs in one CTA: nothing to tune
+  if (small_grid(g) && !g->cons) {   // the whole wave solve runs in one CTA: nothing to tune
     g->kblock = 0;
     if (best) *best = 0;
+    return WHV_OK;
+  }
+  if (g->cons) {   // the conservative operator steps once per launch
+    g->kblock = 1;
+    if (best) *best = 1;
     return WHV_OK;
   }
   // 2-D: per step, blocked sweeps of k steps, and the persistent kernel (-k) where its tiles fit

@@ -64,4 +64,33 @@ __device__ __forceinline__ T lap(const S* __restrict__ w, int64_t idx, int x, in
   return l;
 }
 
+// Conservative second-order operator div_h(c^2 grad_h) at interior index idx (x fastest): per
+// axis m, (F+ (u+ - u) - F- (u - u-)) / h^2, where F+ = face[m][idx] is the face value towards the
+// + neighbour (mean of the two nodes' c^2, or the node's own c^2 on the face to the boundary
+// node) and F- the face towards the - neighbour (face[m] of that neighbour, or the node's own
+// c^2 at the first node); boundary nodes hold 0.
+template <typename T>
+struct ConsFaces {
+  const T* f[3];   // face values per axis
+  const T* c2;     // node values (the - face of the first node)
+};
+
+template <int DIM, typename T, typename S>
+__device__ __forceinline__ T lap_cons(const S* __restrict__ w, int64_t idx, int x, int y, int z, int nx, int ny,
+                                      int nz, const ConsFaces<T>& fc, const StepCoef<T>& cf, T c) {
+  T L = T(0);
+#pragma unroll
+  for (int m = 0; m < DIM; ++m) {
+    const int i = m == 0 ? x : (m == 1 ? y : z);
+    const int n = m == 0 ? nx : (m == 1 ? ny : nz);
+    const int64_t st = m == 0 ? 1 : (m == 1 ? (int64_t)nx : (int64_t)nx * ny);
+    const T up = i < n - 1 ? (T)__ldg(w + idx + st) : T(0);
+    const T um = i > 0 ? (T)__ldg(w + idx - st) : T(0);
+    const T Fp = __ldg(fc.f[m] + idx);
+    const T Fm = i > 0 ? __ldg(fc.f[m] + idx - st) : __ldg(fc.c2 + idx);
+    L = fma(fma(Fp, up - c, -Fm * (c - um)), cf.ih2[m], L);
+  }
+  return L;
+}
+
 }  // namespace whv

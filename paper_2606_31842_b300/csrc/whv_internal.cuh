@@ -93,6 +93,9 @@ struct whv_grid_s {
   // that temporally blocked sweeps read one pair and write the other
   void* wbuf[4] = {nullptr, nullptr, nullptr, nullptr};
   void* acc = nullptr;
+  int cons = 0;                // 1: L_h = div_h(c^2 grad_h) (whv_set_speed_form), Euclidean inner products
+  double* face64[3] = {nullptr, nullptr, nullptr};   // its face values per axis (FP64, FP32)
+  float* face32[3] = {nullptr, nullptr, nullptr};
   int kblock = 0;              // steps per sweep of the blocked 2-D kernel (0: default, 1: off,
                                // < 0: persistent kernel with -kblock steps per sweep)
   // FP64 stepping buffers of an FP32-stepping grid (FP64 residual correction), allocated on

@@ -20,6 +20,7 @@ WHV_FPI, WHV_CG, WHV_DCG, WHV_GMRES, WHV_AGMRES, WHV_ABICGSTAB = 0, 1, 2, 3, 4, 
 WHV_BASIS_NONE, WHV_BASIS_USER, WHV_BASIS_CLOSED_FORM, WHV_BASIS_LANCZOS = 0, 1, 2, 3
 WHV_BASIS_EXACT, WHV_BASIS_REDEFLATE = 1, 2
 WHV_TRUE_RESIDUAL, WHV_REFINE_FP64 = 1, 2
+WHV_SPEED_NONCONSERVATIVE, WHV_SPEED_CONSERVATIVE = 0, 1
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "NOT_CONVERGED", "BREAKDOWN", "TIMEOUT"]
 METHODS = {"fpi": WHV_FPI, "cg": WHV_CG, "dcg": WHV_DCG, "gmres": WHV_GMRES, "agmres": WHV_AGMRES,
            "abicgstab": WHV_ABICGSTAB}
@@ -74,6 +75,7 @@ def _load():
         "whv_solve_adjoint": [P, ctypes.POINTER(whv_params), P, P, P, P, P, P, I, ctypes.POINTER(whv_info)],
         "whv_inject_barrier_error": [P],
         "whv_compress_basis": [P, D, ctypes.POINTER(I)],
+        "whv_set_speed_form": [P, P, I],
         "whv_lanczos_restarted": [P, ctypes.POINTER(whv_params), I, I, I, I, D, P, I, I, ctypes.POINTER(D),
                                   ctypes.POINTER(D), ctypes.POINTER(I)],
         "whv_solve_batched": [I, ctypes.POINTER(P), ctypes.POINTER(whv_params), ctypes.POINTER(P),
@@ -102,7 +104,7 @@ EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_gr
             "whv_expand", "whv_dot", "whv_num_unknowns", "whv_last_error", "whv_version",
             "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune",
             "whv_project_noalloc", "whv_lanczos", "whv_solve_adjoint", "whv_solve_batched",
-            "whv_inject_barrier_error", "whv_compress_basis", "whv_lanczos_restarted"]
+            "whv_inject_barrier_error", "whv_compress_basis", "whv_lanczos_restarted", "whv_set_speed_form"]
 
 
 def _check(status, handle=None, allow=()):
@@ -205,6 +207,10 @@ class Grid:
     def whv_set_speed(self, c2):
         self._pre()
         _check(lib.whv_set_speed(self.handle, _ptr(c2, self.N)), self.handle)
+
+    def whv_set_speed_form(self, c2, form):
+        self._pre()
+        _check(lib.whv_set_speed_form(self.handle, _ptr(c2, self.N), int(form)), self.handle)
 
     def whv_time_grid(self, params):
         nt, dt, oh, oe = ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--steps-per-sweep", type=int, default=0,
                     help="2-D stepping kernel: 0 = autotune (default), k = blocked k steps per launch, "
                          "-k = persistent kernel; a fixed value keeps profiled runs on the kernel the plain run uses")
+    ap.add_argument("--residual", default="df64", choices=["df64", "fp64"],
+                    help="FP32 stepping: precision of the b and residual wave solves of the correction "
+                         "(df64 = pairs of FP32 with error-free arithmetic; the accuracy check always uses FP64)")
     ap.add_argument("--check-every", type=int, default=1,
                     help="convergence test every k iterations; 1 keeps the CG loop on the device (a graph "
                          "with a conditional node), k > 1 launches one iteration graph per step from the host")
@@ -445,8 +448,9 @@ def main():
     stream = torch.cuda.Stream()
     g = whv.Grid(w.npts, precision=prec, stream=stream)
     # FP32 stepping runs inside FP64 residual correction so that the FP64 residual meets tol
+    fp32 = args.precision == "fp32"
     prm = whv.make_params(w.omega, method="cg", tol=tol, maxit=5000, check_every=args.check_every,
-                          refine_fp64=args.precision == "fp32")
+                          refine_fp64=fp32, residual_df64=fp32 and args.residual == "df64")
     tgrid = g.whv_time_grid(prm)
     nt = tgrid["nt"]
     g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
@@ -496,10 +500,12 @@ def main():
     # accuracy of the timed configuration (outside the timed region): FP64 true residual and
     # the error against an FP64-stepping solve of the same problem on the same GPU
     prm_chk = whv.make_params(w.omega, method="cg", tol=tol, maxit=5000, true_residual=True,
-                              refine_fp64=args.precision == "fp32")
+                              refine_fp64=fp32, residual_df64=fp32 and args.residual == "df64")
     u_chk, info_chk = g.whv_solve(prm_chk, f)
     accuracy = {"true_rel_residual": info_chk["true_rel_residual"],
-                "residual_precision": "fp64" if args.precision == "fp64" else "fp64 (FP64 wave solves)"}
+                "true_residual_check": "FP64 wave solves",
+                "correction_residuals": ("fp64" if not fp32 else
+                                         "df64 (pairs of FP32)" if args.residual == "df64" else "fp64")}
     if args.precision == "fp32":
         g64 = whv.Grid(w.npts, precision=whv.WHV_FP64, stream=stream)
         prm64 = whv.make_params(w.omega, method="cg", tol=1e-11, maxit=5000)
@@ -599,7 +605,8 @@ def main():
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
             "krylov_dtype": "f64", "data": "synthetic",
             "config": dict(config_dict(w, tol, args.precision, nt, world), steps_per_sweep=ksweep,
-                           check_every=args.check_every),
+                           check_every=args.check_every,
+                           correction_residuals=("df64" if fp32 and args.residual == "df64" else "fp64")),
             "iterations": info["iterations"], "wave_solves": info["wave_solves"],
             "rel_residual": info["rel_residual"], "glups_solve": glups_solve, "accuracy": accuracy,
             "outer_iterations": info.get("outer_iterations", 0), "wave_solves_fp64": info.get("wave_solves_fp64", 0),

@@ -83,7 +83,7 @@ enum {
 enum {
   WHV_TRUE_RESIDUAL = 1,      /* at exit compute ||Pi_h(u;f) - u|| / ||Pi_h(0;f)|| (2 extra wave solves,
                                  in FP64 when the grid steps in FP64 or WHV_REFINE_FP64 is set)       */
-  WHV_REFINE_FP64 = 2         /* iterative refinement on the full system b = Pi_h(0; f): the residual
+  WHV_REFINE_FP64 = 2,        /* iterative refinement on the full system b = Pi_h(0; f): the residual
                                  r = b - A x is formed with FP64 wave solves; each correction is the
                                  modal solve of r's deflated components (W diag(1/mu) W^T M r) plus a
                                  Krylov solve of the rest in the grid's stepping precision to relative
@@ -92,6 +92,12 @@ enum {
                                  (Lanczos) eigenvectors.  Needs a Krylov method (DCG, AGMRES and
                                  ABICGSTAB use the basis themselves: no modal step); allocates 3 (FP64
                                  grids) or 8 (FP32 grids) more N-vectors of FP64 on first use.       */
+  WHV_RESIDUAL_DF64 = 4       /* with WHV_REFINE_FP64 on second-order grids (c^2 Delta_h): the b and
+                                 residual wave solves of the correction run in double-float
+                                 arithmetic -- each value a pair of FP32 numbers, ~48-bit significand,
+                                 error-free two-sum / two-product on the FP32 pipes -- instead of FP64
+                                 (B300's FP64 rate is 1/64 of FP32).  Enough for tolerances down to
+                                 ~1e-10 relative; WHV_TRUE_RESIDUAL still checks in FP64.          */
 };
 
 typedef struct {
@@ -106,7 +112,7 @@ typedef struct {
   double tol;         /* stop when ||r||_M <= tol ||b||_M of the iterated system                  */
   int maxit;          /* maximum operator applications in the iteration                          */
   int check_every;    /* test convergence every k iterations (CG/FPI); <= 0 selects 1             */
-  int flags;          /* WHV_TRUE_RESIDUAL | WHV_REFINE_FP64                                      */
+  int flags;          /* WHV_TRUE_RESIDUAL | WHV_REFINE_FP64 | WHV_RESIDUAL_DF64                  */
   double inner_tol;   /* WHV_REFINE_FP64: relative tolerance of each correction solve; <= 0: 1e-3 */
 } whv_params;
 

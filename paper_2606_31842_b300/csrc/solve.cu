@@ -43,7 +43,8 @@ struct SolveCtx {
   const TimeGridH& tg;
   bool redefl;
   int ws = 0;      // wave solves in the grid's precision
-  int ws64 = 0;    // FP64 wave solves of the residual correction
+  int ws64 = 0;    // FP64 (or double-float) wave solves of the residual correction
+  int res_prec = WHV_FP64;   // precision of those: WHV_FP64 or kPrecDF64 (WHV_RESIDUAL_DF64)
 };
 
 // out = out - W (W^T M out)
@@ -751,7 +752,7 @@ static whv_status outer_solve(SolveCtx& c, int method, const whv_params* p, cons
   while (true) {
     if (have_x) {
       if (fp64_res) {
-        TRY(wave_solve(g, c.tg, g->xo, nullptr, g->q, 1, WHV_FP64));
+        TRY(wave_solve(g, c.tg, g->xo, nullptr, g->q, 1, c.res_prec));
         c.ws64++;
       } else {
         TRY(wave_solve(g, c.tg, g->xo, nullptr, g->q, 1));
@@ -833,6 +834,7 @@ static whv_status solve_impl(whv_grid g, const whv_params* p, const double* f, i
   const bool devd = has_basis && method != WHV_DCG && !augmented(method);
   const int64_t N = g->N;
   SolveCtx c{g, tg, has_basis && (B.flags & WHV_BASIS_REDEFLATE) != 0 && !augmented(method)};
+  if (refine && (p->flags & WHV_RESIDUAL_DF64) && g->order == 2 && !g->cons) c.res_prec = kPrecDF64;
   double* b = g->t;  // b of the iterated system
 
   // ---- forcing (Algorithm 2: deflate the forcing)
@@ -861,7 +863,7 @@ static whv_status solve_impl(whv_grid g, const whv_params* p, const double* f, i
   } else {
     // ---- iterative refinement with FP64 residuals on the full system b = Pi_h(0; f)
     TRY(ensure_fp64_buffers(g));
-    TRY(wave_solve(g, tg, nullptr, f, g->bo, 0, WHV_FP64));
+    TRY(wave_solve(g, tg, nullptr, f, g->bo, 0, c.res_prec));
     c.ws64++;
     TRY(dot_async(g, g->bo, g->bo, S_RR0));
     TRY(fetch_scalars(g));

@@ -17,6 +17,7 @@
 
 #include <vector>
 
+#include "df64.cuh"
 #include "stencil_ops.cuh"
 #include "whv_device.cuh"
 #include "whv_internal.cuh"
@@ -158,6 +159,103 @@ __global__ void __launch_bounds__(256) k_step_cons(const T* __restrict__ wc, T* 
       const double o = vi - (double)a;
       out[idx] = o;
       part = vi * o;
+    }
+  }
+  if (KIND == K_LAST_AV) {
+    part = block_sum(part);
+    double total;
+    if (grid_reduce(part, partials, counter, &total) && flat_tid() == 0) *scal_out = total;
+  }
+}
+
+// Double-float wave solves (second order): the residual wave solves of the FP64 residual
+// correction with WHV_RESIDUAL_DF64 -- same recurrence, filter and epilogues as k_first / k_step,
+// each value the pair hi + lo of FP32 numbers (df64.cuh), stored as 8-byte pairs.
+template <int DIM, typename LD>
+__device__ __forceinline__ dfl lap_df(LD load, int x, int y, int z, int nx, int ny, int nz, int64_t idx,
+                                      const DfCoef& cf, dfl c) {
+  const dfl c2x = {2.0f * c.hi, 2.0f * c.lo};   // exact
+  dfl L = df_zero();
+#pragma unroll
+  for (int m = 0; m < DIM; ++m) {
+    const int i = m == 0 ? x : (m == 1 ? y : z);
+    const int n = m == 0 ? nx : (m == 1 ? ny : nz);
+    const int64_t st = m == 0 ? 1 : (m == 1 ? (int64_t)nx : (int64_t)nx * ny);
+    const dfl s = df_add(i > 0 ? load(idx - st) : df_zero(), i < n - 1 ? load(idx + st) : df_zero());
+    L = df_add(L, df_mul(cf.ih2[m], df_sub(s, c2x)));
+  }
+  return L;
+}
+
+template <int DIM, bool VARC, bool FORCE, bool ZERO_V>
+__global__ void __launch_bounds__(256) k_first_df(const double* __restrict__ v, dfl* __restrict__ w0,
+                                                  dfl* __restrict__ w1, dfl* __restrict__ acc,
+                                                  const double* __restrict__ c2, const double* __restrict__ f,
+                                                  int nx, int ny, int nz, DfCoef cf) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= nx || y >= ny) return;
+  const int64_t idx = x + (int64_t)nx * (y + (int64_t)ny * z);
+  dfl W0 = df_zero(), L = df_zero();
+  if (!ZERO_V) {
+    W0 = df_from(v[idx]);
+    L = lap_df<DIM>([&](int64_t j) { return df_from(__ldg(v + j)); }, x, y, z, nx, ny, nz, idx, cf, W0);
+    if (VARC) L = df_mul(L, df_from(c2[idx]));
+  }
+  if (FORCE) L = df_sub(L, df_from(f[idx]));   // cos(0) = 1
+  const dfl W1 = df_add(W0, df_mul(cf.hdt2, L));
+  w0[idx] = W0;
+  w1[idx] = W1;
+  acc[idx] = df_add(df_mul(cf.w0, W0), df_mul(cf.w1, W1));
+}
+
+template <int DIM, bool VARC, bool FORCE, int KIND>
+__global__ void __launch_bounds__(256) k_step_df(const dfl* __restrict__ wc, dfl* __restrict__ wp,
+                                                 dfl* __restrict__ acc, const double* __restrict__ c2,
+                                                 const double* __restrict__ f, const double* __restrict__ v,
+                                                 const double* __restrict__ mw, double* __restrict__ out, int nx,
+                                                 int ny, int nz, DfCoef cf, double* partials, unsigned* counter,
+                                                 double* scal_out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  const bool in = (x < nx) && (y < ny);
+  double part = 0.0;
+  if (in) {
+    const int64_t idx = x + (int64_t)nx * (y + (int64_t)ny * z);
+    const dfl c = wc[idx];
+    auto load = [&](int64_t j) { return wc[j]; };
+    dfl wn;
+    if (!VARC) {   // sum_m a_m (W_{+m} + W_{-m}) + b W^n - W^{n-1}
+      wn = df_sub(df_mul(cf.b, c), wp[idx]);
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) {
+        const int i = m == 0 ? x : (m == 1 ? y : z);
+        const int n = m == 0 ? nx : (m == 1 ? ny : nz);
+        const int64_t st = m == 0 ? 1 : (m == 1 ? (int64_t)nx : (int64_t)nx * ny);
+        const dfl s = df_add(i > 0 ? load(idx - st) : df_zero(), i < n - 1 ? load(idx + st) : df_zero());
+        wn = df_add(wn, df_mul(cf.a[m], s));
+      }
+      if (FORCE) wn = df_sub(wn, df_mul(cf.fph, df_from(f[idx])));   // fph = dt^2 cos(omega_hat t^n)
+    } else {
+      dfl L = lap_df<DIM>(load, x, y, z, nx, ny, nz, idx, cf, c);
+      L = df_mul(L, df_from(c2[idx]));
+      if (FORCE) L = df_sub(L, df_mul(cf.fph, df_from(f[idx])));   // fph = cos(omega_hat t^n)
+      const dfl t = df_sub(dfl{2.0f * c.hi, 2.0f * c.lo}, wp[idx]);
+      wn = df_add(t, df_mul(cf.dt2, L));
+    }
+    const dfl a = df_add(acc[idx], df_mul(cf.w1, wn));
+    if (KIND == K_STEP) {
+      wp[idx] = wn;
+      acc[idx] = a;
+    } else if (KIND == K_LAST_OUT) {
+      out[idx] = df_to(a);
+    } else {
+      const double vi = v[idx];
+      const double o = vi - df_to(a);
+      out[idx] = o;
+      part = (mw ? vi * mw[idx] : vi) * o;
     }
   }
   if (KIND == K_LAST_AV) {
@@ -342,6 +440,74 @@ static whv_status launch_solve_cons(whv_grid g, const TimeGridH& tg, const doubl
   return WHV_OK;
 }
 
+template <int DIM, bool VARC, bool FORCE>
+static whv_status launch_solve_df(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
+                                  double* out, int epi, int* nlaunch, void* const* bufs, void* accbuf) {
+  const LaunchShape ls = shape_of(g);
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  dfl* b0 = (dfl*)bufs[0];
+  dfl* b1 = (dfl*)bufs[1];
+  dfl* acc = (dfl*)accbuf;
+  DfCoef cf{};
+  double asum = 0.0;
+  for (int m = 0; m < 3; ++m) {
+    const double h2 = g->h[m] * g->h[m];
+    cf.ih2[m] = df_from(1.0 / h2);
+    const double am = m < g->dim ? tg.dt * tg.dt / h2 : 0.0;
+    cf.a[m] = df_from(am);
+    asum += am;
+  }
+  cf.b = df_from(2.0 - 2.0 * asum);
+  cf.dt2 = df_from(tg.dt * tg.dt);
+  cf.hdt2 = df_from(0.5 * tg.dt * tg.dt);
+  cf.w0 = df_from(tg.weight[0]);
+  cf.w1 = df_from(tg.weight[1]);
+  dim3 fgrid = ls.grid;
+  if (DIM == 3) fgrid.z = nz;
+  if (v)
+    k_first_df<DIM, VARC, FORCE, false><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, g->c2, f, nx, ny, nz, cf);
+  else
+    k_first_df<DIM, VARC, FORCE, true><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, g->c2, f, nx, ny, nz, cf);
+  WHV_CUDA(g, cudaGetLastError());
+  *nlaunch = tg.nt;
+  dfl* wprev = b0;
+  dfl* wcur = b1;
+  double* part = chan(g, CH_STEP);
+  unsigned* cnt = g->counters + CH_STEP;
+  for (int n = 1; n < tg.nt; ++n) {
+    cf.fph = df_from(VARC ? tg.phase[n] : tg.dt * tg.dt * tg.phase[n]);
+    cf.w1 = df_from(tg.weight[n + 1]);
+    const bool last = (n == tg.nt - 1);
+    if (!last)
+      k_step_df<DIM, VARC, FORCE, K_STEP><<<fgrid, ls.block, 0, g->stream>>>(wcur, wprev, acc, g->c2, f, nullptr,
+                                                                           nullptr, nullptr, nx, ny, nz, cf, nullptr,
+                                                                           nullptr, nullptr);
+    else if (epi == 0)
+      k_step_df<DIM, VARC, FORCE, K_LAST_OUT><<<fgrid, ls.block, 0, g->stream>>>(wcur, wprev, acc, g->c2, f, nullptr,
+                                                                               nullptr, out, nx, ny, nz, cf, nullptr,
+                                                                               nullptr, nullptr);
+    else
+      k_step_df<DIM, VARC, FORCE, K_LAST_AV><<<fgrid, ls.block, 0, g->stream>>>(wcur, wprev, acc, g->c2, f, v, g->mw,
+                                                                              out, nx, ny, nz, cf, part, cnt,
+                                                                              g->scal + S_PQ);
+    WHV_CUDA(g, cudaGetLastError());
+    dfl* tmp = wprev;
+    wprev = wcur;
+    wcur = tmp;
+  }
+  return WHV_OK;
+}
+
+template <int DIM>
+static whv_status dispatch_df_dim(whv_grid g, const TimeGridH& tg, const double* v, const double* f, double* out,
+                                  int epi, int* nl, void* const* bufs, void* acc) {
+  const bool varc = g->c2 != nullptr;
+  if (varc) return f ? launch_solve_df<DIM, true, true>(g, tg, v, f, out, epi, nl, bufs, acc)
+                     : launch_solve_df<DIM, true, false>(g, tg, v, f, out, epi, nl, bufs, acc);
+  return f ? launch_solve_df<DIM, false, true>(g, tg, v, f, out, epi, nl, bufs, acc)
+           : launch_solve_df<DIM, false, false>(g, tg, v, f, out, epi, nl, bufs, acc);
+}
+
 template <typename T, int DIM, int ORDER, bool VARC, bool FORCE>
 static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
                                double* out, int epi, int* nlaunch, void* const* bufs, void* accbuf,
@@ -481,6 +647,17 @@ static whv_status launch_wave_solve(whv_grid g, const TimeGridH& tg, const doubl
     const BufSet B{g->wbuf, g->acc, g->cons ? 1 : (g->kblock > 0 ? g->kblock : default_kblock(g))};
     return prec == WHV_FP64 ? dispatch<double>(g, tg, v, f, out, epi, nl, B)
                             : dispatch<float>(g, tg, v, f, out, epi, nl, B);
+  }
+  if (prec == kPrecDF64) {   // double-float residual wave solves (second order, c^2 Delta_h)
+    if (g->order != 2 || g->cons) return fail(g, WHV_ERR_INVALID, "double-float stepping needs order 2");
+    if (!g->acc64 && g->precision != WHV_FP64) return fail(g, WHV_ERR_INVALID, "FP64 buffers are not allocated");
+    void* const* bufs = g->precision == WHV_FP64 ? g->wbuf : g->wbuf64;
+    void* acc = g->precision == WHV_FP64 ? g->acc : g->acc64;
+    switch (g->dim) {
+      case 1: return dispatch_df_dim<1>(g, tg, v, f, out, epi, nl, bufs, acc);
+      case 2: return dispatch_df_dim<2>(g, tg, v, f, out, epi, nl, bufs, acc);
+      default: return dispatch_df_dim<3>(g, tg, v, f, out, epi, nl, bufs, acc);
+    }
   }
   if (prec != WHV_FP64) return fail(g, WHV_ERR_INVALID, "FP32 stepping on an FP64 grid is not provided");
   if (!g->acc64) return fail(g, WHV_ERR_INVALID, "FP64 buffers of the FP32 grid are not allocated");

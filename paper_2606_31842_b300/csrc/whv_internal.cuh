@@ -182,6 +182,9 @@ void count_launches(int64_t n);
 //   epi = 1: out = v - Pi_h(v; f) = A v (f=0), and scal[S_PQ] = <v, out>_M
 //   prec = -1: the grid's stepping precision; WHV_FP64 on an FP32-stepping grid uses the
 //   grid's FP64 buffer set (ensure_fp64_buffers first).
+//   prec = kPrecDF64: double-float stepping (pairs of FP32, second-order grids) in the FP64
+//   buffer set -- the residual wave solves of WHV_RESIDUAL_DF64.
+constexpr int kPrecDF64 = 2;
 whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
                       double* out, int epi, int prec = -1);
 void free_plan(whv_grid g);

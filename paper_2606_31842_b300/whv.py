@@ -19,7 +19,7 @@ WHV_FP64, WHV_FP32_STEP = 0, 1
 WHV_FPI, WHV_CG, WHV_DCG, WHV_GMRES, WHV_AGMRES, WHV_ABICGSTAB = 0, 1, 2, 3, 4, 5
 WHV_BASIS_NONE, WHV_BASIS_USER, WHV_BASIS_CLOSED_FORM, WHV_BASIS_LANCZOS = 0, 1, 2, 3
 WHV_BASIS_EXACT, WHV_BASIS_REDEFLATE = 1, 2
-WHV_TRUE_RESIDUAL, WHV_REFINE_FP64 = 1, 2
+WHV_TRUE_RESIDUAL, WHV_REFINE_FP64, WHV_RESIDUAL_DF64 = 1, 2, 4
 WHV_SPEED_NONCONSERVATIVE, WHV_SPEED_CONSERVATIVE = 0, 1
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "NOT_CONVERGED", "BREAKDOWN", "TIMEOUT"]
 METHODS = {"fpi": WHV_FPI, "cg": WHV_CG, "dcg": WHV_DCG, "gmres": WHV_GMRES, "agmres": WHV_AGMRES,
@@ -124,9 +124,11 @@ def _ptr(t, numel=None):
 
 
 def make_params(omega, periods=1, adjust_omega=False, cfl=0.0, method="cg", restart=30, tol=1e-8,
-                maxit=1000, check_every=1, true_residual=False, refine_fp64=False, inner_tol=0.0) -> whv_params:
+                maxit=1000, check_every=1, true_residual=False, refine_fp64=False, inner_tol=0.0,
+                residual_df64=False) -> whv_params:
     m = METHODS[method] if isinstance(method, str) else int(method)
-    flags = (WHV_TRUE_RESIDUAL if true_residual else 0) | (WHV_REFINE_FP64 if refine_fp64 else 0)
+    flags = ((WHV_TRUE_RESIDUAL if true_residual else 0) | (WHV_REFINE_FP64 if refine_fp64 else 0)
+             | (WHV_RESIDUAL_DF64 if residual_df64 else 0))
     return whv_params(float(omega), int(periods), int(bool(adjust_omega)), float(cfl), m, int(restart),
                       float(tol), int(maxit), int(check_every), flags, float(inner_tol))
 

@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="whv", choices=["whv", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--method", default="", choices=["", "cg", "dcg", "gmres", "agmres"],
+    ap.add_argument("--method", default="", choices=["", "cg", "dcg", "gmres", "agmres", "abicgstab"],
                     help="accelerator of the single-grid workloads (default: DCG for c1/c3, CG otherwise)")
     ap.add_argument("--steps-per-sweep", type=int, default=0,
                     help="2-D stepping kernel: 0 = autotune (default), k = blocked k steps per launch, "
@@ -60,6 +60,10 @@ def parse():
                          "with a conditional node), k > 1 launches one iteration graph per step from the host")
     ap.add_argument("--eigs", default="lanczos", choices=["lanczos", "thick"],
                     help="variable-speed workload: one 1024-step Lanczos run, or thick-restart Lanczos (basis 3 nd + 4)")
+    ap.add_argument("--compress", type=float, default=0.0,
+                    help="variable-speed workload: SVD-compress the basis with this Frobenius tolerance")
+    ap.add_argument("--form", default="nonconservative", choices=["nonconservative", "conservative"],
+                    help="variable-speed workload: operator form (conservative: div(c^2 grad), second order)")
     ap.add_argument("--sources", type=int, default=0,
                     help="batched workload: Gaussian sources per (grid, frequency) (default 16)")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "study"],
@@ -351,9 +355,15 @@ def run_workload(args):
     name = args.workload
     w = I.WORKLOADS["c5" if name == "c5" else name]
     prec = whv.WHV_FP64 if name == "c1" else whv.WHV_FP32_STEP
-    g = whv.Grid(w.npts, order=w.order, precision=prec, stream=stream)
+    cons = name == "c3" and args.form == "conservative"
+    order = 2 if cons else w.order   # the conservative operator is second order
+    g = whv.Grid(w.npts, order=order, precision=prec, stream=stream)
     if w.speed:
-        g.whv_set_speed(dev(I.speed_squared(w.speed, w.npts, w.speed_seed)))
+        c2v = dev(I.speed_squared(w.speed, w.npts, w.speed_seed))
+        if cons:
+            g.whv_set_speed_form(c2v, whv.WHV_SPEED_CONSERVATIVE)
+        else:
+            g.whv_set_speed(c2v)
     refine = prec == whv.WHV_FP32_STEP
     method = args.method or ("dcg" if name in ("c1", "c3") else "cg")
     prm = whv.make_params(w.omega, method=method, tol=w.tol, maxit=20000, restart=30, refine_fp64=refine)
@@ -372,6 +382,14 @@ def run_workload(args):
     else:
         g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
         setup = {"basis": "closed-form sine vectors"}
+    if args.compress > 0.0 and w.dim == 2:
+        ranks = g.whv_compress_basis(args.compress)
+        ny, nx = w.npts[1] - 2, w.npts[0] - 2
+        setup.update({"compressed_tau": args.compress, "compressed_rank_mean": float(np.mean(ranks)),
+                      "compressed_rank_max": int(max(ranks)),
+                      "compression_ratio": float(sum(r * (nx + ny + 1) for r in ranks) / (len(ranks) * nx * ny))})
+    if cons:
+        setup["operator"] = "conservative div(c^2 grad), second order, Euclidean inner products"
     setup["setup_s"] = time.perf_counter() - t0
     if w.dim == 2:
         setup["steps_per_sweep"] = g.whv_autotune(prm)
@@ -389,7 +407,7 @@ def run_workload(args):
     lups = info["wave_solves"] * info["nt"] * w.n_unknowns
     line.update({"workload": name, "value": ms, "ms_per_step": ms,
                  "dtype": "f64" if prec == whv.WHV_FP64 else "f32", "krylov_dtype": "f64",
-                 "config": dict({"workload": name, "grid": list(w.npts), "order": w.order, "omega": w.omega,
+                 "config": dict({"workload": name, "grid": list(w.npts), "order": order, "omega": w.omega,
                                  "nd": w.nd, "tol": w.tol, "method": method.upper(),
                                  "variable_speed": bool(w.speed), "nt": info["nt"]}, **setup),
                  "iterations": info["iterations"], "outer_iterations": info["outer_iterations"],
@@ -398,9 +416,12 @@ def run_workload(args):
     if name == "c3":
         # break-even of the eigenvector set-up (Sec. 4.1 cost model): the same problem without
         # deflation, counted in wave solves, outside the timed region
-        g0 = whv.Grid(w.npts, order=w.order, precision=prec, stream=stream)
+        g0 = whv.Grid(w.npts, order=order, precision=prec, stream=stream)
         if w.speed:
-            g0.whv_set_speed(dev(I.speed_squared(w.speed, w.npts, w.speed_seed)))
+            if cons:
+                g0.whv_set_speed_form(dev(I.speed_squared(w.speed, w.npts, w.speed_seed)), whv.WHV_SPEED_CONSERVATIVE)
+            else:
+                g0.whv_set_speed(dev(I.speed_squared(w.speed, w.npts, w.speed_seed)))
         p0 = whv.make_params(w.omega, method="cg", tol=w.tol, maxit=20000, refine_fp64=refine)
         t0 = time.perf_counter()
         _, i0 = g0.whv_solve(p0, f)

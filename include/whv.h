@@ -250,6 +250,15 @@ whv_status whv_get_steps_per_sweep(whv_grid grid, int* k);
  * synchronises the stream.  Must not be called while the grid's stream is being captured. */
 whv_status whv_autotune(whv_grid grid, const whv_params* p, int* best);
 
+/* Several right-hand sides on one grid (the multi-right-hand-side use that amortises the
+ * eigenvector set-up, Sec. 4.1): column j of F_dev (N doubles at F_dev + j ld, device) is solved
+ * into U_dev + j ld exactly as whv_solve(grid, p, ., use_guess, ., infos + j) would; the basis and
+ * everything built from it (A W, QR factors, captured graphs, the device CG loop) is reused.
+ * infos (host, nrhs entries) may be NULL.  ld >= N.  Returns WHV_ERR_NOT_CONVERGED if a column
+ * missed its tolerance (all columns are still solved), any other error at once. */
+whv_status whv_solve_many(whv_grid grid, const whv_params* p, int nrhs, int64_t ld, const double* F_dev,
+                          int use_guess, double* U_dev, whv_info* infos);
+
 /* Adjoint of the solve (differentiation path): gradients of L = 1/2 ||u - u_obs||^2 with respect
  * to the forcing and the squared speed.  u_dev is the fixed point of Pi_h(.; f_dev) that whv_solve
  * returned for the same p, f_dev the forcing used (NULL = 0), dLdu_dev = dL/du (e.g. u - u_obs).

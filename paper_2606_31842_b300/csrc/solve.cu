@@ -1009,3 +1009,21 @@ extern "C" whv_status whv_inject_barrier_error(whv_grid g) {
   WHV_CUDA(g, cudaStreamSynchronize(g->stream));
   return WHV_OK;
 }
+
+// Several right-hand sides on one grid: column j of F (leading dimension ld) -> column j of U,
+// each by whv_solve with the same parameters; the basis, its derived quantities (A W, QR factors)
+// and the captured CUDA graphs are built for the first and reused by the others.
+extern "C" whv_status whv_solve_many(whv_grid g, const whv_params* p, int nrhs, int64_t ld, const double* F,
+                                     int use_guess, double* U, whv_info* infos) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  if (nrhs < 0 || (nrhs > 0 && (!F || !U)) || ld < g->N)
+    return fail(g, WHV_ERR_INVALID, "need nrhs >= 0, ld >= N and non-NULL F, U");
+  whv_status worst = WHV_OK;
+  for (int j = 0; j < nrhs; ++j) {
+    const whv_status s = whv_solve(g, p, F + (size_t)j * ld, use_guess, U + (size_t)j * ld, infos ? infos + j : nullptr);
+    if (s == WHV_ERR_NOT_CONVERGED) { worst = s; continue; }   // keep going: the iterate is written
+    if (s != WHV_OK) return s;
+  }
+  if (worst != WHV_OK) return fail(g, worst, "whv_solve_many: some right-hand sides did not reach tol");
+  return WHV_OK;
+}

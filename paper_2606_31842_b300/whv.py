@@ -76,6 +76,7 @@ def _load():
         "whv_inject_barrier_error": [P],
         "whv_compress_basis": [P, D, ctypes.POINTER(I)],
         "whv_set_speed_form": [P, P, I],
+        "whv_solve_many": [P, ctypes.POINTER(whv_params), I, L, P, I, P, ctypes.POINTER(whv_info)],
         "whv_lanczos_restarted": [P, ctypes.POINTER(whv_params), I, I, I, I, D, P, I, I, ctypes.POINTER(D),
                                   ctypes.POINTER(D), ctypes.POINTER(I)],
         "whv_solve_batched": [I, ctypes.POINTER(P), ctypes.POINTER(whv_params), ctypes.POINTER(P),
@@ -104,7 +105,8 @@ EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_gr
             "whv_expand", "whv_dot", "whv_num_unknowns", "whv_last_error", "whv_version",
             "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune",
             "whv_project_noalloc", "whv_lanczos", "whv_solve_adjoint", "whv_solve_batched",
-            "whv_inject_barrier_error", "whv_compress_basis", "whv_lanczos_restarted", "whv_set_speed_form"]
+            "whv_inject_barrier_error", "whv_compress_basis", "whv_lanczos_restarted", "whv_set_speed_form",
+            "whv_solve_many"]
 
 
 def _check(status, handle=None, allow=()):
@@ -209,6 +211,19 @@ class Grid:
     def whv_set_speed(self, c2):
         self._pre()
         _check(lib.whv_set_speed(self.handle, _ptr(c2, self.N)), self.handle)
+
+    def whv_solve_many(self, params, F, U=None, use_guess=False, raise_not_converged=False):
+        """F: (nrhs, N) float64 CUDA tensor (row j = right-hand side j); returns (U, infos)."""
+        nrhs = F.shape[0]
+        if U is None:
+            U = torch.zeros_like(F)
+        infos = (whv_info * max(nrhs, 1))()
+        self._pre()
+        allow = () if raise_not_converged else (WHV_ERR_NOT_CONVERGED,)
+        st = _check(lib.whv_solve_many(self.handle, ctypes.byref(params), int(nrhs), int(F.stride(0)), _ptr(F),
+                                       int(bool(use_guess)), _ptr(U), infos), self.handle, allow)
+        self._post()
+        return U, [dict(infos[j].as_dict(), status=STATUS_NAMES[st]) for j in range(nrhs)]
 
     def whv_set_speed_form(self, c2, form):
         self._pre()

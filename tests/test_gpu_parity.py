@@ -436,3 +436,22 @@ def test_residual_correction_in_double_float(npts, speed, omega):
         assert relmax(host(u), U) < 1e-6
         out[df] = host(u)
     assert relmax(out[True], out[False]) < 1e-7
+
+
+def test_solve_many_equals_single_solves():
+    """Several right-hand sides on one grid: each column equals its own whv_solve, and the
+    direct solution."""
+    npts, omega, nd = (129, 121), 24.0, 16
+    og = O.Grid(npts)
+    tg = WH.time_grid_for(og, omega)
+    fs = [I.gaussian(npts, I.source_centers(40 + j, 1, 2)[0], 1.0 / omega, omega ** 2) for j in range(4)]
+    F = torch.stack([dev(f) for f in fs])
+    g = whv.Grid(npts, precision=whv.WHV_FP64)
+    prm = whv.make_params(omega, method="cg", tol=1e-10, maxit=3000)
+    g.whv_set_deflation_basis(prm, nd, whv.WHV_BASIS_CLOSED_FORM)
+    U, infos = g.whv_solve_many(prm, F)
+    assert all(i["status"] == "OK" for i in infos)
+    for j, f in enumerate(fs):
+        u1, _ = g.whv_solve(prm, dev(f))
+        assert relmax(host(U[j]), host(u1)) < 1e-14
+        assert relmax(host(U[j]), IND.helmholtz_direct(npts, tg.omega_eff, f)) < 1e-7

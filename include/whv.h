@@ -341,7 +341,10 @@ whv_status whv_project_noalloc(int64_t n, int nd, const double* W_dev, const dou
  * compressed vectors: the projection W^T M r is T = (M o r) V followed by per-vector sums of
  * s_k u_k . T_k, the expansion a GEMM U diag(c) V^T (FP64 kernels of this library);
  * whv_get_basis writes the compressed vectors out dense.  ranks_host (nd ints, may be NULL)
- * receives r_m.  Needs a dense basis (WHV_ERR_INVALID otherwise, or if every rank is 0). */
+ * receives r_m.  Ranks are capped at 256 (beyond about half the shorter side of the grid the
+ * factors take more memory than the vector): a vector that needs more at this tolerance makes
+ * the call return WHV_ERR_INVALID and leave the basis dense (grids whose shorter side is <= 256
+ * keep up to full rank).  Needs a dense basis (WHV_ERR_INVALID otherwise, or if every rank is 0). */
 whv_status whv_compress_basis(whv_grid grid, double tau, int* ranks_host);
 
 /* Test hook for the failure path of the persistent wave solve (no counterpart in the paper):

@@ -12,7 +12,7 @@
 // The truncated SVD is computed by a randomized range finder with two power iterations
 // (Halko, Martinsson and Tropp 2011): Y = phi Omega (Gaussian Omega, l columns), Q = orth(Y),
 // B = Q^T phi; the SVD of the small B (l x nx) comes from the eigen-decomposition of B B^T (cyclic
-// Jacobi on the host); the range error ||phi - Q Q^T phi||_F^2 = ||phi||_F^2 - ||B||_F^2 is added
+// Householder reduction, bisection and inverse iteration on the host); the range error ||phi - Q Q^T phi||_F^2 = ||phi||_F^2 - ||B||_F^2 is added
 // to the discarded singular values, and l doubles until the tolerance is met.  Singular values
 // below ~1e-7 ||phi|| are not resolved by the B B^T eigenvalues: tau must be at least that.
 #include <math.h>
@@ -200,53 +200,6 @@ static int orthonormalise(std::vector<double>& X, int n, int l) {
   return kept;
 }
 
-// Eigen-decomposition of the symmetric l x l matrix G (row-major) by cyclic Jacobi rotations:
-// G = Z diag(ev) Z^T, eigenvalues sorted descending, Z column-major.
-static void jacobi_eigen(std::vector<double> G, int l, std::vector<double>& ev, std::vector<double>& Z) {
-  Z.assign((size_t)l * l, 0.0);
-  for (int i = 0; i < l; ++i) Z[(size_t)i * l + i] = 1.0;
-  auto a = [&](int i, int j) -> double& { return G[(size_t)i * l + j]; };
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = 0; i < l; ++i)
-      for (int j = 0; j < l; ++j) (i == j ? tot : off) += a(i, j) * a(i, j);
-    if (off <= 1e-30 * (tot + off)) break;
-    for (int p = 0; p < l - 1; ++p)
-      for (int q = p + 1; q < l; ++q) {
-        const double apq = a(p, q);
-        if (apq == 0.0) continue;
-        const double theta = (a(q, q) - a(p, p)) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < l; ++k) {   // G <- J^T G J
-          const double gkp = a(k, p), gkq = a(k, q);
-          a(k, p) = c * gkp - s * gkq;
-          a(k, q) = s * gkp + c * gkq;
-        }
-        for (int k = 0; k < l; ++k) {
-          const double gpk = a(p, k), gqk = a(q, k);
-          a(p, k) = c * gpk - s * gqk;
-          a(q, k) = s * gpk + c * gqk;
-        }
-        for (int k = 0; k < l; ++k) {   // Z <- Z J
-          const double zkp = Z[(size_t)p * l + k], zkq = Z[(size_t)q * l + k];
-          Z[(size_t)p * l + k] = c * zkp - s * zkq;
-          Z[(size_t)q * l + k] = s * zkp + c * zkq;
-        }
-      }
-  }
-  std::vector<int> idx(l);
-  for (int i = 0; i < l; ++i) idx[i] = i;
-  std::sort(idx.begin(), idx.end(), [&](int x, int y) { return a(x, x) > a(y, y); });
-  ev.resize(l);
-  std::vector<double> Zs((size_t)l * l);
-  for (int j = 0; j < l; ++j) {
-    ev[j] = a(idx[j], idx[j]);
-    std::copy(&Z[(size_t)idx[j] * l], &Z[(size_t)idx[j] * l] + l, &Zs[(size_t)j * l]);
-  }
-  Z.swap(Zs);
-}
-
 }  // namespace whv
 
 using namespace whv;
@@ -258,7 +211,10 @@ extern "C" whv_status whv_compress_basis(whv_grid g, double tau, int* ranks_host
   if (!B.V || B.nd < 1) return fail(g, WHV_ERR_INVALID, "no dense deflation basis to compress");
   if (!(tau > 0.0)) return fail(g, WHV_ERR_INVALID, "tau must be > 0");
   const int nx = g->n[0], ny = g->n[1], nd = B.nd;
-  const int lmax = std::min(nx, ny);
+  // ranks beyond ~half the shorter side store more than the dense vector: the sketch stops at
+  // kCompMaxRank, and a vector that needs more at this tolerance is reported as not compressible
+  constexpr int kCompMaxRank = 256;
+  const int lmax = std::min({nx, ny, kCompMaxRank});
   const int64_t N = g->N;
   // device scratch for the range finder (largest l = lmax)
   double *Y = nullptr, *Zd = nullptr, *Bd = nullptr;
@@ -319,7 +275,7 @@ extern "C" whv_status whv_compress_basis(whv_grid g, double tau, int* ranks_host
         }
       double bfro2 = 0.0;
       for (double v : Bh) bfro2 += v * v;
-      jacobi_eigen(G, kept, ev, Z);
+      if (kept > 0) host_sym_top_eigenpairs(G, kept, kept, ev, Z);
       const double range2 = std::max(fro2 - bfro2, 0.0);   // ||phi - Q Q^T phi||_F^2
       // smallest r with sum_{k >= r} sigma_k^2 + range error < tau^2
       std::vector<double> tail(kept + 1, 0.0);
@@ -331,7 +287,15 @@ extern "C" whv_status whv_compress_basis(whv_grid g, double tau, int* ranks_host
         l = std::min(2 * l, lmax);
         continue;
       }
-      if (r < 0) r = kept;   // full sketch: keep everything it resolved
+      if (r < 0) {
+        if (lmax == std::min(nx, ny)) {
+          r = kept;   // the sketch spans the whole column space: keep everything it resolved
+        } else {
+          st = fail(g, WHV_ERR_INVALID, "whv_compress_basis: a basis vector needs rank > 256 at this tolerance "
+                                        "(not compressible; the basis is left dense)");
+          break;
+        }
+      }
       // U = Q Z_r (ny x r), s = sqrt(ev), V = B^T Z_r / s (nx x r)
       for (int k = 0; k < r; ++k) {
         const double sk = sqrt(std::max(ev[k], 0.0));

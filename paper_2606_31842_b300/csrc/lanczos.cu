@@ -404,6 +404,17 @@ static bool log_on_lz() {
 // tridiagonal form H = P T P^T, the tridiagonal eigenpairs by bisection and inverse iteration,
 // eigenvectors S = P S_T (n x kw, column-major).
 static void dense_top_eigenpairs(std::vector<double> A, int n, int kw, std::vector<double>& theta,
+                                 std::vector<double>& S);
+
+namespace whv {
+// exported for the SVD compression (compress.cu)
+void host_sym_top_eigenpairs(const std::vector<double>& A, int n, int kw, std::vector<double>& theta,
+                             std::vector<double>& S) {
+  dense_top_eigenpairs(A, n, kw, theta, S);
+}
+}  // namespace whv
+
+static void dense_top_eigenpairs(std::vector<double> A, int n, int kw, std::vector<double>& theta,
                                  std::vector<double>& S) {
   std::vector<double> P((size_t)n * n, 0.0);   // row-major
   for (int i = 0; i < n; ++i) P[(size_t)i * n + i] = 1.0;

@@ -231,5 +231,9 @@ whv_status basis_project(whv_grid g, const double* r, double* coef);            
 whv_status basis_expand(whv_grid g, const double* coef, double alpha, double* out);   // out += a W c
 whv_status basis_column(whv_grid g, int m, double* dst);                             // dst = W e_m
 const void* basis_key(const Basis& B);   // identity of the basis storage (graph cache keys)
+// lanczos.cu: the kw largest eigenpairs of a dense symmetric n x n matrix (row-major) by
+// Householder reduction, bisection and inverse iteration; S is n x kw, column-major
+void host_sym_top_eigenpairs(const std::vector<double>& A, int n, int kw, std::vector<double>& theta,
+                             std::vector<double>& S);
 
 }  // namespace whv

@@ -302,6 +302,14 @@ whv_status whv_solve_adjoint(whv_grid grid, const whv_params* p, const double* f
 whv_status whv_solve_batched(int nprob, const whv_grid* grids, const whv_params* params,
                              const double* const* f_dev, double* const* u_dev, whv_info* infos);
 
+/* Autotuner of the batched steps per sweep (2-D grids): times one persistent batched f = 0 wave
+ * solve of all nprob problems for k = 2, 4, 6, 8, 10, 12 (CUDA events on the shared stream, after a
+ * warm-up launch) and stores the fastest in grids[0] (as whv_set_steps_per_sweep), which
+ * whv_solve_batched reads; *best (may be NULL) receives it.  3-D batches step once per sweep
+ * (*best = 1).  Uses the grids' scratch buffers; the same restrictions on the grids as
+ * whv_solve_batched.  Must not be called while the stream is being captured. */
+whv_status whv_autotune_batched(int nprob, const whv_grid* grids, const whv_params* params, int* best);
+
 /* Deflation contractions and reductions on the grid's basis / weights (building blocks of the
  * solve, exposed for testing and for callers composing their own iterations):
  *   whv_project:  coeff_dev[m] = (W^T M r)_m, m < nd                 (Algorithm 2, (r, phi_m))

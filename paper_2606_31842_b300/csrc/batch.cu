@@ -962,6 +962,83 @@ static whv_status batched_vc(BatchCtx& c, const double* const* f, double* const*
 
 using namespace whv;
 
+// Autotuner of the batched steps per sweep (2-D): one batched f = 0 wave solve of every problem
+// (v = 0, into the grids' scratch) per candidate k, timed with CUDA events after a warm-up launch;
+// the fastest k is stored in grids[0] (whv_set_steps_per_sweep), which the batched solve reads.
+extern "C" whv_status whv_autotune_batched(int nprob, const whv_grid* grids, const whv_params* params, int* best) {
+  if (nprob < 1 || nprob > kBatchMaxProblems || !grids || !params || !grids[0])
+    return fail(nullptr, WHV_ERR_INVALID, "whv_autotune_batched: bad arguments (1 <= nprob <= 1024)");
+  whv_grid g0 = grids[0];
+  if (g0->dim != 2) {   // 3-D batches step once per sweep: nothing to tune
+    if (best) *best = 1;
+    return WHV_OK;
+  }
+  const bool varc = g0->c2 != nullptr;
+  BatchCtx c;
+  c.np = nprob;
+  c.grids = grids;
+  c.params = params;
+  c.g0 = g0;
+  c.tgs.resize(nprob);
+  for (int p = 0; p < nprob; ++p) {
+    whv_grid g = grids[p];
+    if (!g || g->stream != g0->stream || g->precision != g0->precision || g->dim != 2 || g->order != g0->order ||
+        (g->c2 != nullptr) != varc || g->cons)
+      return fail(g0, WHV_ERR_INVALID, "whv_autotune_batched: grids must match as for whv_solve_batched");
+    whv_status s = make_time_grid(g, &params[p], &c.tgs[p]);
+    if (s != WHV_OK) return fail(g0, s, std::string("whv_autotune_batched: ") + g->err);
+  }
+  batch_init();
+  c.st = g0->stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
+  B_CUDA(g0, c.alloc(&c.bar, 2 * sizeof(unsigned)));
+  B_CUDA(g0, c.alloc(&c.err, sizeof(int)));
+  B_CUDA(g0, cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), c.st));
+  B_CUDA(g0, cudaMemsetAsync(c.err, 0, sizeof(int), c.st));
+  RoleIO io;
+  io.v.assign(nprob, nullptr);
+  io.f.assign(nprob, nullptr);
+  io.out = c.each([](whv_grid g) { return g->t; });
+  const int saved = g0->kblock;
+  cudaEvent_t e0, e1;
+  B_CUDA(g0, cudaEventCreate(&e0));
+  B_CUDA(g0, cudaEventCreate(&e1));
+  const int R = g0->order == 2 ? 1 : 2;
+  int kbest = batch_k(g0, g0->precision == WHV_FP64);
+  float tbest = 1e30f;
+  whv_status s = WHV_OK;
+  for (int k : {2, 4, 6, 8, 10, 12}) {
+    if (kBReg - 2 * k * R < 16) continue;
+    g0->kblock = k;
+    Wave w;
+    const bool f64 = g0->precision == WHV_FP64;
+    if (g0->order == 2)
+      s = f64 ? (varc ? make_wave<double, 2, 2, true>(c, io, &w) : make_wave<double, 2, 2, false>(c, io, &w))
+              : (varc ? make_wave<float, 2, 2, true>(c, io, &w) : make_wave<float, 2, 2, false>(c, io, &w));
+    else
+      s = f64 ? (varc ? make_wave<double, 2, 4, true>(c, io, &w) : make_wave<double, 2, 4, false>(c, io, &w))
+              : (varc ? make_wave<float, 2, 4, true>(c, io, &w) : make_wave<float, 2, 4, false>(c, io, &w));
+    if (s != WHV_OK) break;
+    if ((s = run_wave(c, w)) != WHV_OK) break;   // warm-up
+    cudaEventRecord(e0, c.st);
+    if ((s = run_wave(c, w)) != WHV_OK) break;
+    cudaEventRecord(e1, c.st);
+    if ((s = check_barrier(c)) != WHV_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < tbest) { tbest = ms; kbest = k; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  count_launches(c.launches);
+  g0->kblock = s == WHV_OK ? kbest : saved;
+  if (s != WHV_OK) return s;
+  if (best) *best = kbest;
+  return WHV_OK;
+}
+
 extern "C" whv_status whv_solve_batched(int nprob, const whv_grid* grids, const whv_params* params,
                                         const double* const* f_dev, double* const* u_dev, whv_info* infos) {
   const double t0 = now_s();

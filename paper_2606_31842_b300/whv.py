@@ -77,6 +77,7 @@ def _load():
         "whv_compress_basis": [P, D, ctypes.POINTER(I)],
         "whv_set_speed_form": [P, P, I],
         "whv_solve_many": [P, ctypes.POINTER(whv_params), I, L, P, I, P, ctypes.POINTER(whv_info)],
+        "whv_autotune_batched": [I, ctypes.POINTER(P), ctypes.POINTER(whv_params), ctypes.POINTER(I)],
         "whv_lanczos_restarted": [P, ctypes.POINTER(whv_params), I, I, I, I, D, P, I, I, ctypes.POINTER(D),
                                   ctypes.POINTER(D), ctypes.POINTER(I)],
         "whv_solve_batched": [I, ctypes.POINTER(P), ctypes.POINTER(whv_params), ctypes.POINTER(P),
@@ -106,7 +107,7 @@ EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_gr
             "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune",
             "whv_project_noalloc", "whv_lanczos", "whv_solve_adjoint", "whv_solve_batched",
             "whv_inject_barrier_error", "whv_compress_basis", "whv_lanczos_restarted", "whv_set_speed_form",
-            "whv_solve_many"]
+            "whv_solve_many", "whv_autotune_batched"]
 
 
 def _check(status, handle=None, allow=()):
@@ -164,6 +165,17 @@ def whv_solve_batched(grids, params, fs, us=None, raise_not_converged=False):
     st = _check(lib.whv_solve_batched(n, G, Pm, F, U, infos), grids[0].handle, allow)
     grids[0]._post()
     return us, [dict(i.as_dict(), status=STATUS_NAMES[st]) for i in infos]
+
+
+def whv_autotune_batched(grids, params):
+    """Batched steps-per-sweep autotuner (see include/whv.h); returns the chosen k."""
+    n = len(grids)
+    G = (ctypes.c_void_p * n)(*[g.handle for g in grids])
+    Pm = (whv_params * n)(*params)
+    k = ctypes.c_int()
+    grids[0]._pre()
+    _check(lib.whv_autotune_batched(n, G, Pm, ctypes.byref(k)), grids[0].handle)
+    return k.value
 
 
 def whv_kernel_launches() -> int:

@@ -201,3 +201,23 @@ def test_batched_host_driven_loop_matches_device_loop():
     assert out[1][1] == out[3][1]
     for a, b in zip(out[1][0], out[3][0]):
         assert IND.relmax(a, b) < 1e-13
+
+
+def test_batched_autotuner_picks_a_valid_k_and_keeps_results():
+    probs = _problems((65, 97), (12.0, 18.0), 1, 6)
+    stream = torch.cuda.Stream()
+    grids, params, fs = [], [], []
+    for npts, om, f, nd in probs:
+        g = whv.Grid(npts, precision=whv.WHV_FP64, stream=stream)
+        prm = whv.make_params(om, method="cg", tol=0.0, maxit=5)
+        g.whv_set_deflation_basis(prm, nd, whv.WHV_BASIS_CLOSED_FORM)
+        grids.append(g); params.append(prm); fs.append(dev(f))
+    k = whv.whv_autotune_batched(grids, params)
+    assert k in (2, 4, 6, 8, 10, 12) and grids[0].whv_get_steps_per_sweep() == k
+    us, infos = whv.whv_solve_batched(grids, params, fs)
+    for (npts, om, f, nd), u in zip(probs, us):
+        og = O.Grid(npts)
+        tg = WH.time_grid_for(og, om)
+        modes, lam2, _ = SP.select_modes(og, tg, nd)
+        ref = K.devd_solve(og, tg, f, SP.basis(og, modes), lam2, "cg", 0.0, 5).u
+        assert IND.relmax(u.cpu().numpy(), ref) < 1e-12

@@ -310,7 +310,11 @@ def run_workload(args):
         setup_s = time.perf_counter() - t0
         grids = [p[0] for p in probs]
         params = [p[1] for p in probs]
-        kb = whv.whv_autotune_batched(grids, params)   # steps per sweep of the batched kernel
+        if args.steps_per_sweep > 0:
+            grids[0].whv_set_steps_per_sweep(args.steps_per_sweep)
+            kb, ktag = args.steps_per_sweep, "fixed"
+        else:
+            kb, ktag = whv.whv_autotune_batched(grids, params), "autotuned"   # batched kernel's k
         fs = [p[2] for p in probs]
         us = [torch.zeros(g.N, dtype=torch.float64, device="cuda") for g in grids]
         res = {}
@@ -340,7 +344,7 @@ def run_workload(args):
                                             f"(width 2h), 32 closed-form vectors each, {form} to 1e-6; every "
                                             f"batched wave solve of all {len(probs)} problems is one persistent launch",
                                 "problems": len(probs), "setup_s": setup_s,
-                                "steps_per_sweep": f"{kb} (autotuned, both precisions)",
+                                "steps_per_sweep": f"{kb} ({ktag}, both precisions)",
                                 "check_every": args.check_every},
                      "iterations_max": max(i["iterations"] for i in infos),
                      "iterations_mean": statistics.mean(i["iterations"] for i in infos),

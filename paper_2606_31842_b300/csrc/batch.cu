@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "stencil_ops.cuh"
+#include "quad2d.cuh"
 #include "whv_device.cuh"
 #include "whv_internal.cuh"
 
@@ -185,6 +186,10 @@ __device__ __forceinline__ T d2b(const T* __restrict__ a, int l, int gi, int n, 
 // nt - n0).  Sweep 0 starts from W^0 = v with the Taylor step; the last sweep writes the FP64
 // epilogue instead of the state.  Thread (warp w, lane) owns column 32 (w & 1) + lane and rows
 // (w >> 1) + 16 r, r < 4, of the staged region for the whole sweep.
+// FP32, 5-point, c = 1, f = 0: the sub-steps run in the four-cells-per-thread mapping of quad2d.cuh
+template <typename T, int ORDER, bool VARC, bool FORCED>
+constexpr bool kBQuad = sizeof(T) == 4 && ORDER == 2 && !VARC && !FORCED;
+
 template <typename T, int ORDER, bool VARC, bool FORCED>
 __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* __restrict__ P,
                                                                 const int* __restrict__ nact, int J, int K,
@@ -196,6 +201,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
   T* const S1 = S0 + kBReg * kBReg;
   __shared__ int64_t s_tile0[kBatchMaxProblems + 1];
   __shared__ BTile<T> sB;
+  __shared__ T sw[16];      // filter weights of the current sweep (four-cell kernels; k <= 16)
   constexpr int R = ORDER == 2 ? 1 : 2;
   const int np = nact[0];
   for (int p = threadIdx.x; p <= np; p += blockDim.x)
@@ -258,6 +264,35 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
         const bool tile = in && i >= H && i < kBReg - H && jr >= H && jr < kBReg - H;
         acr[r] = (!first && tile) ? __ldcg(B.acc + gi) : w0 * cur[r];
       }
+      if constexpr (kBQuad<T, ORDER, VARC, FORCED>) {
+        T* const S2 = S1 + kBReg * kBReg;
+#pragma unroll
+        for (int r = 0; r < kBRows; ++r) {
+          const int l = (jb + kBPitch * r) * kBReg + i;
+          S0[l] = cur[r];
+          S1[l] = prv[r];
+          S2[l] = acr[r];
+        }
+        if (threadIdx.x < kk) sw[threadIdx.x] = wtb[n0 + 1 + threadIdx.x];
+        __syncthreads();
+        const QuadCoef q{B.ax, B.ay, B.b, B.ih2x, B.ih2y, 0.5f * B.dt2};
+        const bool inside = x0 >= 0 && y0 >= 0 && x0 + kBReg <= nx && y0 + kBReg <= ny;
+        const unsigned m = inside ? 0xfu : quad_mask(x0, y0, nx, ny);
+        if (first) {
+          if (inside) quad_sweep<false, true>(S0, S1, S2, kk, sw, q, m);
+          else quad_sweep<true, true>(S0, S1, S2, kk, sw, q, m);
+        } else {
+          if (inside) quad_sweep<false, false>(S0, S1, S2, kk, sw, q, m);
+          else quad_sweep<true, false>(S0, S1, S2, kk, sw, q, m);
+        }
+#pragma unroll
+        for (int r = 0; r < kBRows; ++r) {
+          const int l = (jb + kBPitch * r) * kBReg + i;
+          cur[r] = S0[l];
+          prv[r] = S1[l];
+          acr[r] = S2[l];
+        }
+      } else {
 #pragma unroll
       for (int r = 0; r < kBRows; ++r) S0[(jb + kBPitch * r) * kBReg + i] = cur[r];
       __syncthreads();
@@ -300,6 +335,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
         T* tmp = Ain;
         Ain = Bout;
         Bout = tmp;
+      }
       }
       double part = 0.0;
       const bool coltile = colin && i >= H && i < kBReg - H;
@@ -467,11 +503,19 @@ static cudaError_t launch_wave3(cudaStream_t st, const Wave& w, unsigned* bar, i
 
 // opt the blocked kernels into their dynamic shared memory (FP64: 64 KB) once per process,
 // outside any stream capture
+// dynamic shared memory of the blocked batched kernel: two state buffers, plus W^{n-1} and the
+// filter sums for the four-cell kernels
+template <typename T, int ORDER, bool VARC, bool FORCED>
+static size_t batch_smem() {
+  return (kBQuad<T, ORDER, VARC, FORCED> ? 3 : 2) * (size_t)kBReg * kBReg * sizeof(T);
+}
+
 template <typename T, int ORDER, bool VARC>
 static void block2d_attrs() {
-  const int bytes = 2 * kBReg * kBReg * (int)sizeof(T);
-  cudaFuncSetAttribute(k_batch_block2d<T, ORDER, VARC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_batch_block2d<T, ORDER, VARC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_batch_block2d<T, ORDER, VARC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)batch_smem<T, ORDER, VARC, false>());
+  cudaFuncSetAttribute(k_batch_block2d<T, ORDER, VARC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)batch_smem<T, ORDER, VARC, true>());
 }
 static void batch_init() {
   static bool done = false;
@@ -584,7 +628,7 @@ static whv_status make_wave(BatchCtx& c, const RoleIO& io, Wave* out) {
   B_CUDA(c.g0, cudaMemcpy(w.fin, fin.data(), np * sizeof(BFin), cudaMemcpyHostToDevice));
   int per_sm = 0;
   if (blocked) {
-    w.smem = 2 * (size_t)kBReg * kBReg * sizeof(T);
+    w.smem = forced ? batch_smem<T, ORDER, VARC, true>() : batch_smem<T, ORDER, VARC, false>();
     if (forced) {
       w.launch = &launch_block2d<T, ORDER, VARC, true>;
       B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_block2d<T, ORDER, VARC, true>,

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "quad2d.cuh"
 #include "whv_device.cuh"
 #include "whv_internal.cuh"
 
@@ -51,6 +52,10 @@ __device__ __forceinline__ T d2s(const T* __restrict__ a, int l, int gi, int n, 
   const T p2 = gi < n - 2 ? a[l + 2 * s] : (gi == n - 2 ? T(0) : -c);
   return fma(T(-30), c, fma(T(16), m1 + p1, -(m2 + p2)));
 }
+
+// FP32, 5-point, c = 1: the sub-steps run in the four-cells-per-thread mapping of quad2d.cuh
+template <typename T, int ORDER, bool VARC>
+constexpr bool kQuad = sizeof(T) == 4 && ORDER == 2 && !VARC;
 
 template <typename T, int ORDER, bool VARC, int KIND>
 __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ gprev,
@@ -93,6 +98,29 @@ __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ g
     if (VARC) cc[t] = in ? c2[gi] : T(0);
     acr[t] = (coltile0 && j >= H && j < kReg - H && in) ? acc[gi] : T(0);
   }
+  if constexpr (kQuad<T, ORDER, VARC>) {
+    T* const S2 = S1 + kReg * kReg;
+#pragma unroll
+    for (int t = 0; t < kRowsPerThread; ++t) {
+      const int l = (jb + kRowPitch * t) * kReg + i;
+      S0[l] = cur[t];
+      S1[l] = prv[t];
+      S2[l] = acr[t];
+    }
+    __syncthreads();
+    const QuadCoef q{cf.ax, cf.ay, cf.b, cf.ih2x, cf.ih2y, 0.5f * cf.dt2};
+    if (x0 >= 0 && y0 >= 0 && x0 + kReg <= nx && y0 + kReg <= ny)
+      quad_sweep<false, false>(S0, S1, S2, cf.k, sw, q, 0xfu);
+    else
+      quad_sweep<true, false>(S0, S1, S2, cf.k, sw, q, quad_mask(x0, y0, nx, ny));
+#pragma unroll
+    for (int t = 0; t < kRowsPerThread; ++t) {
+      const int l = (jb + kRowPitch * t) * kReg + i;
+      cur[t] = S0[l];
+      prv[t] = S1[l];
+      acr[t] = S2[l];
+    }
+  } else {
 #pragma unroll
   for (int t = 0; t < kRowsPerThread; ++t) S0[(jb + kRowPitch * t) * kReg + i] = cur[t];
   __syncthreads();
@@ -129,6 +157,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ g
     __syncthreads();
     T* tmp = A; A = B; B = tmp;
   }
+  }
   double part = 0.0;
   const bool coltile = colin && i >= H && i < kReg - H;
 #pragma unroll
@@ -160,7 +189,8 @@ __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ g
   }
 }
 
-static size_t blk_smem(size_t esz) { return 2 * (size_t)kReg * kReg * esz; }
+// two state buffers; the FP32 four-cell sweep stages W^{n-1} and the filter sums in a third
+static size_t blk_smem(size_t esz, bool quad) { return (quad ? 3 : 2) * (size_t)kReg * kReg * esz; }
 
 // largest k <= want that leaves a tile of at least 16 nodes per edge
 int blocked_steps(int want, int order) {
@@ -199,7 +229,7 @@ template <typename T, int ORDER, bool VARC, int KIND>
 static cudaError_t launch_block(whv_grid g, const T* gp, const T* gc, T* op, T* oc, T* acc,
                                 const T* c2, const double* v, double* out, const BlockCoef<T>& cf,
                                 double* partials, unsigned* counter, double* scal_out) {
-  const size_t smem = blk_smem(sizeof(T));
+  const size_t smem = blk_smem(sizeof(T), kQuad<T, ORDER, VARC>);
   const int R = ORDER == 2 ? 1 : 2;
   const int TW = kReg - 2 * cf.k * R;
   dim3 grid((g->n[0] + TW - 1) / TW, (g->n[1] + TW - 1) / TW, 1);

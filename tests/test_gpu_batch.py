@@ -221,3 +221,35 @@ def test_batched_autotuner_picks_a_valid_k_and_keeps_results():
         modes, lam2, _ = SP.select_modes(og, tg, nd)
         ref = K.devd_solve(og, tg, f, SP.basis(og, modes), lam2, "cg", 0.0, 5).u
         assert IND.relmax(u.cpu().numpy(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("k", [3, 8, 16])
+def test_batched_fp32_sweeps_match_single_grid_fp32(k):
+    """FP32 stepping without correction, fixed iterations: the batched four-cell sweeps (Taylor
+    start inside the first sweep, ragged last sweeps, regions inside and across the boundary) give
+    the single-grid FP32 iterates up to the rounding of the start step, and the FP64 oracle's
+    within the FP32 operator error."""
+    spec = [((33, 33), 9.0), ((97, 97), 14.0), ((150, 131), 21.0), ((70, 45), 30.0)]
+    stream = torch.cuda.Stream()
+    it = 4
+    grids, params, fs, singles = [], [], [], []
+    for npts, om in spec:
+        f = I.gaussian(npts, I.source_centers(npts[0], 1, 2)[0], 0.1, om ** 2)
+        prm = whv.make_params(om, method="cg", tol=0.0, maxit=it)
+        g = whv.Grid(npts, precision=whv.WHV_FP32_STEP, stream=stream)
+        g.whv_set_deflation_basis(prm, 4, whv.WHV_BASIS_CLOSED_FORM)
+        grids.append(g); params.append(prm); fs.append(dev(f))
+        s1 = whv.Grid(npts, precision=whv.WHV_FP32_STEP)
+        s1.whv_set_steps_per_sweep(1)
+        s1.whv_set_deflation_basis(prm, 4, whv.WHV_BASIS_CLOSED_FORM)
+        singles.append((s1.whv_solve(prm, dev(f))[0].cpu().numpy(), npts, om, f))
+    grids[0].whv_set_steps_per_sweep(k)
+    us, infos = whv.whv_solve_batched(grids, params, fs)
+    for u, info, (u1, npts, om, f) in zip(us, infos, singles):
+        assert info["iterations"] == it
+        assert IND.relmax(u.cpu().numpy(), u1) < 2e-5
+        og = O.Grid(npts)
+        tg = WH.time_grid_for(og, om)
+        modes, lam2, _ = SP.select_modes(og, tg, 4)
+        ref = K.devd_solve(og, tg, f, SP.basis(og, modes), lam2, "cg", 0.0, it).u
+        assert IND.relmax(u.cpu().numpy(), ref) < 1e-4

@@ -113,6 +113,125 @@ __device__ __forceinline__ void quad_taylor(const float4& c, float4& w, float4& 
   w = n;
 }
 
+// Variable speed (c^2 Delta_h) with the 5-point or the 9-point-wide 4th-order stencil: the second
+// differences of the scalar kernels, fma(-2, c, m1 + p1) and fma(-30, c, fma(16, m1 + p1,
+// -(m2 + p2))), times 1 / h^2 (1 / 12 h^2), W^{n+1} = fma(dt^2, c^2 L, fma(2, c, -W^{n-1})).  The
+// 4th-order closure at the boundary (odd reflection: the value two nodes outside the first or last
+// interior node is minus that node) is applied to the cells whose bits are set in e (MASK only):
+// bits 0-3 the cells at x = 0, bits 4-7 at x = nx - 1, bit 8 the row y = 0, bit 9 the row y = ny - 1.
+struct QuadBnd {
+  unsigned in;   // in-domain bits of the four cells
+  unsigned e;    // 4th-order boundary bits
+};
+
+__device__ __forceinline__ QuadBnd quad_bnd(int x0, int y0, int nx, int ny) {
+  const int row = threadIdx.x >> 4, col = (threadIdx.x & 15) * 4;
+  const int gy = y0 + row;
+  QuadBnd b{quad_mask(x0, y0, nx, ny), 0u};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int gx = x0 + col + e;
+    if (gx == 0) b.e |= 1u << e;
+    if (gx == nx - 1) b.e |= 16u << e;
+  }
+  if (gy == 0) b.e |= 256u;
+  if (gy == ny - 1) b.e |= 512u;
+  return b;
+}
+
+template <int ORDER, bool MASK>
+__device__ __forceinline__ float q_d2(float c, float m1, float p1, float m2, float p2, bool lo, bool hi) {
+  if (ORDER == 2) return fmaf(-2.0f, c, m1 + p1);
+  if (MASK) {
+    m2 = lo ? -c : m2;
+    p2 = hi ? -c : p2;
+  }
+  return fmaf(-30.0f, c, fmaf(16.0f, m1 + p1, -(m2 + p2)));
+}
+
+struct QuadCoefV {
+  float ih2x, ih2y, dt2;   // 1 / h^2 (order 2) or 1 / (12 h^2) (order 4); dt^2
+};
+
+template <int ORDER, bool VARC, bool MASK>
+__device__ __forceinline__ void quadv_step(const float4& c, float4& w, float4& a, const float4& cc, const float* Ain,
+                                           float* Bout, int off, int rowoff[4], float ws, const QuadCoefV& q,
+                                           const QuadBnd& b) {
+  // y neighbours: rows -1, +1 (and -2, +2 for order 4), clamped to the region
+  const float4 U1 = q_lds(Ain, rowoff[1]), D1 = q_lds(Ain, rowoff[2]);
+  float4 U2 = make_float4(0.f, 0.f, 0.f, 0.f), D2 = U2;
+  if (ORDER == 4) {
+    U2 = q_lds(Ain, rowoff[0]);
+    D2 = q_lds(Ain, rowoff[3]);
+  }
+  const float lw = __shfl_up_sync(0xffffffffu, c.w, 1);
+  const float rx = __shfl_down_sync(0xffffffffu, c.x, 1);
+  float lz = 0.f, ry = 0.f;
+  if (ORDER == 4) {
+    lz = __shfl_up_sync(0xffffffffu, c.z, 1);
+    ry = __shfl_down_sync(0xffffffffu, c.y, 1);
+  }
+  const bool ylo = MASK && (b.e & 256u), yhi = MASK && (b.e & 512u);
+  auto upd = [&](float cm, float m1, float p1, float m2, float p2, float um1, float dp1, float um2, float dp2,
+                 float wp, float c2, int e) {
+    float L = q_d2<ORDER, MASK>(cm, m1, p1, m2, p2, MASK && (b.e & (1u << e)), MASK && (b.e & (16u << e))) * q.ih2x;
+    L = fmaf(q_d2<ORDER, MASK>(cm, um1, dp1, um2, dp2, ylo, yhi), q.ih2y, L);
+    if (VARC) L *= c2;
+    return fmaf(q.dt2, L, fmaf(2.0f, cm, -wp));
+  };
+  float4 n;
+  n.x = upd(c.x, lw, c.y, lz, c.z, U1.x, D1.x, U2.x, D2.x, w.x, cc.x, 0);
+  n.y = upd(c.y, c.x, c.z, lw, c.w, U1.y, D1.y, U2.y, D2.y, w.y, cc.y, 1);
+  n.z = upd(c.z, c.y, c.w, c.x, rx, U1.z, D1.z, U2.z, D2.z, w.z, cc.z, 2);
+  n.w = upd(c.w, c.z, rx, c.y, ry, U1.w, D1.w, U2.w, D2.w, w.w, cc.w, 3);
+  if (MASK) {
+    n.x = (b.in & 1u) ? n.x : 0.0f;
+    n.y = (b.in & 2u) ? n.y : 0.0f;
+    n.z = (b.in & 4u) ? n.z : 0.0f;
+    n.w = (b.in & 8u) ? n.w : 0.0f;
+  }
+  q_sts(Bout, off, n);
+  a.x = fmaf(ws, n.x, a.x);
+  a.y = fmaf(ws, n.y, a.y);
+  a.z = fmaf(ws, n.z, a.z);
+  a.w = fmaf(ws, n.w, a.w);
+  w = n;
+}
+
+// quad_sweep for the variable-speed and 4th-order kernels (no Taylor start: the single-grid path
+// takes its first step separately); cc holds c^2 of the thread's four cells (VARC)
+template <int ORDER, bool VARC, bool MASK>
+__device__ __forceinline__ void quadv_sweep(float* S0, float* S1, float* S2, int kk, const float* sw,
+                                            const QuadCoefV& q, const QuadBnd& b, const float4 cc) {
+  const int row = threadIdx.x >> 4, col = (threadIdx.x & 15) * 4;
+  const int off = row * kQReg + col;
+  int rowoff[4];
+  rowoff[0] = max(row - 2, 0) * kQReg + col;
+  rowoff[1] = max(row - 1, 0) * kQReg + col;
+  rowoff[2] = min(row + 1, kQReg - 1) * kQReg + col;
+  rowoff[3] = min(row + 2, kQReg - 1) * kQReg + col;
+  float4 c = q_lds(S0, off), w = q_lds(S1, off), a = q_lds(S2, off);
+  __syncthreads();
+  float* A = S0;
+  float* B = S1;
+  int s = 0;
+  for (; s + 2 <= kk; s += 2) {
+    quadv_step<ORDER, VARC, MASK>(c, w, a, cc, A, B, off, rowoff, sw[s], q, b);
+    __syncthreads();
+    quadv_step<ORDER, VARC, MASK>(w, c, a, cc, B, A, off, rowoff, sw[s + 1], q, b);
+    __syncthreads();
+  }
+  if (s < kk) {
+    quadv_step<ORDER, VARC, MASK>(c, w, a, cc, A, B, off, rowoff, sw[s], q, b);
+    __syncthreads();
+    q_swap(c, w);
+  }
+  q_sts(S0, off, c);
+  q_sts(S1, off, w);
+  q_sts(S2, off, a);
+  __syncthreads();
+}
+
 // Advances the region staged in S0 (W^n), S1 (W^{n-1}) and S2 (filter sums) kk sub-steps with the
 // weights sw[0 .. kk-1] (FIRST: sub-step 1 is the Taylor start).  The caller has synchronised
 // after staging; on return, after a barrier, S0 = W^{n+kk}, S1 = W^{n+kk-1}, S2 = filter sums.

@@ -53,9 +53,9 @@ __device__ __forceinline__ T d2s(const T* __restrict__ a, int l, int gi, int n, 
   return fma(T(-30), c, fma(T(16), m1 + p1, -(m2 + p2)));
 }
 
-// FP32, 5-point, c = 1: the sub-steps run in the four-cells-per-thread mapping of quad2d.cuh
+// FP32: the sub-steps run in the four-cells-per-thread mapping of quad2d.cuh
 template <typename T, int ORDER, bool VARC>
-constexpr bool kQuad = sizeof(T) == 4 && ORDER == 2 && !VARC;
+constexpr bool kQuad = sizeof(T) == 4;
 
 template <typename T, int ORDER, bool VARC, int KIND>
 __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ gprev,
@@ -108,11 +108,30 @@ __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ g
       S2[l] = acr[t];
     }
     __syncthreads();
-    const QuadCoef q{cf.ax, cf.ay, cf.b, cf.ih2x, cf.ih2y, 0.5f * cf.dt2};
-    if (x0 >= 0 && y0 >= 0 && x0 + kReg <= nx && y0 + kReg <= ny)
-      quad_sweep<false, false>(S0, S1, S2, cf.k, sw, q, 0xfu);
-    else
-      quad_sweep<true, false>(S0, S1, S2, cf.k, sw, q, quad_mask(x0, y0, nx, ny));
+    const bool inside = x0 >= 0 && y0 >= 0 && x0 + kReg <= nx && y0 + kReg <= ny;
+    if constexpr (ORDER == 2 && !VARC) {
+      const QuadCoef q{cf.ax, cf.ay, cf.b, cf.ih2x, cf.ih2y, 0.5f * cf.dt2};
+      if (inside)
+        quad_sweep<false, false>(S0, S1, S2, cf.k, sw, q, 0xfu);
+      else
+        quad_sweep<true, false>(S0, S1, S2, cf.k, sw, q, quad_mask(x0, y0, nx, ny));
+    } else {
+      const QuadCoefV q{cf.ih2x, cf.ih2y, cf.dt2};
+      const QuadBnd bd = inside ? QuadBnd{0xfu, 0u} : quad_bnd(x0, y0, nx, ny);
+      float4 cq = make_float4(1.f, 1.f, 1.f, 1.f);
+      if constexpr (VARC) {   // c^2 of the thread's four cells (read-only: through L1)
+        const int qy = y0 + (int)(threadIdx.x >> 4), qx = x0 + (int)(threadIdx.x & 15) * 4;
+        const T* row = c2 + (int64_t)nx * qy + qx;
+        cq.x = (bd.in & 1u) ? __ldg(row) : 0.f;
+        cq.y = (bd.in & 2u) ? __ldg(row + 1) : 0.f;
+        cq.z = (bd.in & 4u) ? __ldg(row + 2) : 0.f;
+        cq.w = (bd.in & 8u) ? __ldg(row + 3) : 0.f;
+      }
+      if (inside)
+        quadv_sweep<ORDER, VARC, false>(S0, S1, S2, cf.k, sw, q, bd, cq);
+      else
+        quadv_sweep<ORDER, VARC, true>(S0, S1, S2, cf.k, sw, q, bd, cq);
+    }
 #pragma unroll
     for (int t = 0; t < kRowsPerThread; ++t) {
       const int l = (jb + kRowPitch * t) * kReg + i;

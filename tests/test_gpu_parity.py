@@ -364,17 +364,20 @@ def test_blocked_sweeps_fp32(npts, order, speed, omega, k):
     assert np.abs(out - ref.ravel()).max() <= 2e-5 * max(np.abs(v).max(), np.abs(ref).max())
 
 
-@pytest.mark.parametrize("npts,omega", [((200, 150), 21.0), ((70, 45), 14.0), ((130, 67), 17.0), ((66, 66), 9.0)])
-def test_blocked_fp32_four_cell_sweeps_equal_single_steps_bitwise(npts, omega):
-    """FP32, 5-point, c = 1: the four-cells-per-thread sweeps (regions inside the domain and
-    crossing its boundary, odd and even k, a ragged last sweep) perform the single-step kernel's
-    operations in its order, so Pi_h v is bitwise the k = 1 result."""
-    g, og, _ = make(npts, 2, None, precision=whv.WHV_FP32_STEP)
+@pytest.mark.parametrize("npts,omega,order,speed", [
+    ((200, 150), 21.0, 2, None), ((70, 45), 14.0, 2, None), ((130, 67), 17.0, 2, None), ((66, 66), 9.0, 2, None),
+    ((200, 150), 21.0, 4, "c3"), ((101, 99), 20.0, 4, "c3"), ((130, 67), 17.0, 4, None), ((180, 140), 19.0, 2, "c3")])
+def test_blocked_fp32_four_cell_sweeps_equal_single_steps_bitwise(npts, omega, order, speed):
+    """FP32: the four-cells-per-thread sweeps (5-point with c = 1; c^2 Delta_h and the 4th-order
+    stencil with its odd-reflection closure; regions inside the domain and crossing its boundary,
+    odd and even k, a ragged last sweep) perform the single-step kernel's operations in its order,
+    so Pi_h v is bitwise the k = 1 result."""
+    g, og, _ = make(npts, order, speed, precision=whv.WHV_FP32_STEP)
     prm = whv.make_params(omega)
     v = dev(I.random_field(og.shape, 24))
     g.whv_set_steps_per_sweep(1)
     ref = host(g.whv_apply_pi(prm, v))
-    for k in (2, 3, 5, 8, 11, 16):
+    for k in ((2, 3, 5, 8, 11, 16) if order == 2 else (2, 3, 5, 8, 11, 12)):
         g.whv_set_steps_per_sweep(k)
         out = host(g.whv_apply_pi(prm, v))
         assert np.array_equal(out, ref), (k, np.abs(out - ref).max())

@@ -215,6 +215,10 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
     const int A = nact[j];
     const int64_t total = s_tile0[A];
     int cur_p = -1;
+    // four-cell kernels: the column data of this CTA's next item (same sweep, same problem),
+    // loaded while the current item's sub-steps run
+    T ncur[kBRows], nprv[kBRows], nacr[kBRows];
+    int64_t pitem = -1;
     for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
       int p = cur_p < 0 ? 0 : cur_p;
       while (s_tile0[p + 1] <= item) ++p;
@@ -244,6 +248,14 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
       T cc[VARC ? kBRows : 1];
       T ff[FORCED ? kBRows : 1];
       const T w0 = first ? wtb[0] : T(0);
+      if (kBQuad<T, ORDER, VARC, FORCED> && item == pitem) {
+#pragma unroll
+        for (int r = 0; r < kBRows; ++r) {
+          cur[r] = ncur[r];
+          prv[r] = nprv[r];
+          acr[r] = nacr[r];
+        }
+      } else
 #pragma unroll
       for (int r = 0; r < kBRows; ++r) {
         const int gy = y0 + jb + kBPitch * r;
@@ -275,6 +287,28 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
         }
         if (threadIdx.x < kk) sw[threadIdx.x] = wtb[n0 + 1 + threadIdx.x];
         __syncthreads();
+        // issue the next item's loads now: its input pair and filter sums are not written in this
+        // sweep (outputs go to the other pair, filter sums to this CTA's own tiles)
+        pitem = -1;
+        const int64_t nitem = item + gridDim.x;
+        if (!first && nitem < s_tile0[p + 1]) {
+          const int tn = (int)(nitem - B.tile0);
+          const int px0 = (tn % B.tiles_x) * TW - H, py0 = (tn / B.tiles_x) * TW - H;
+          const int pgx = px0 + i;
+          const bool pcol = pgx >= 0 && pgx < nx;
+#pragma unroll
+          for (int r = 0; r < kBRows; ++r) {
+            const int jr = jb + kBPitch * r;
+            const int gy = py0 + jr;
+            const bool in = pcol && gy >= 0 && gy < ny;
+            const int64_t gi = pgx + (int64_t)nx * gy;
+            ncur[r] = in ? __ldcg(B.w[2 * qi + 1] + gi) : T(0);
+            nprv[r] = in ? __ldcg(B.w[2 * qi] + gi) : T(0);
+            const bool tile = in && i >= H && i < kBReg - H && jr >= H && jr < kBReg - H;
+            nacr[r] = tile ? __ldcg(B.acc + gi) : T(0);
+          }
+          pitem = nitem;
+        }
         const QuadCoef q{B.ax, B.ay, B.b, B.ih2x, B.ih2y, 0.5f * B.dt2};
         const bool inside = x0 >= 0 && y0 >= 0 && x0 + kBReg <= nx && y0 + kBReg <= ny;
         const unsigned m = inside ? 0xfu : quad_mask(x0, y0, nx, ny);

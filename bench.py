@@ -188,11 +188,17 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ GPU arm
-def kernel_source_hash():
-    """Hash of the stepping-kernel sources; a recorded DRAM traffic figure is only reported while
-    the kernels are the ones it was measured on."""
+KERNEL_SOURCES = {
+    "k_block2d": ("stencil_blocked.cu", "quad2d.cuh", "whv_device.cuh"),
+    "k_step3d": ("stencil.cu", "stencil_ops.cuh", "whv_device.cuh"),
+}
+
+
+def kernel_source_hash(kernel):
+    """Hash of the sources of one stepping kernel; a recorded DRAM traffic figure is only reported
+    while the kernel is the one it was measured on."""
     h = hashlib.sha256()
-    for fn in ("stencil.cu", "stencil_blocked.cu", "whv_device.cuh"):
+    for fn in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_2606_31842_b300", "csrc", fn), "rb").read())
     return h.hexdigest()[:16]
 
@@ -209,7 +215,7 @@ def traffic_for(kernel, precision):
         return None
     if not rec:
         return None
-    if kernel_source_hash() != rec.get("source_sha"):
+    if kernel not in KERNEL_SOURCES or kernel_source_hash(kernel) != rec.get("source_sha"):
         return None
     return rec.get("dram_bytes_per_launch")
 

@@ -230,8 +230,10 @@ whv_status whv_solve(whv_grid grid, const whv_params* p, const double* f_dev, in
 
 /* Steps per sweep k of the temporally blocked 2-D stencil kernel: each launch advances k leapfrog
  * steps of the f = 0 wave solves in shared memory (halo of width k r).  k = 1 launches one kernel
- * per time step, k = 0 restores the default (8 for FP32 stepping, 1 for FP64), k <= 16.  Only
- * 2-D grids block; other grids always step once per launch.  With the default (k = 0) grids of at
+ * per time step, k = 0 restores the default (8 for FP32 stepping, 1 for FP64), k <= 16.  2-D
+ * grids block k steps; 3-D second-order constant-speed FP32 grids take any k >= 2 as two steps per
+ * launch (z-marching, W^{n+1} staged plane by plane); other grids step once per launch.  With the
+ * default (k = 0) grids of at
  * most 4096 unknowns run each whole wave solve in a single CTA (state in shared memory, one
  * barrier per step); an explicit k turns that off.
  * k < 0 (2-D grids, -16 <= k): the persistent kernel -- the whole wave solve (forced or not) is

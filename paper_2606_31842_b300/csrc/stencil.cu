@@ -347,6 +347,106 @@ __global__ void __launch_bounds__(256) k_step3d(const T* __restrict__ wc, T* __r
   }
 }
 
+// 3-D 7-point, FP32, c = 1, f = 0: TWO leapfrog steps per pass (W^{n-1}, W^n -> W^{n+1}, W^{n+2}
+// into the other buffer pair), halving the state traffic of single steps.  A CTA of 32 x 16
+// threads covers an xy region R1 = tile + 1-node ring (tile 30 x 14) and marches through a
+// chunk of zc planes.  At iteration z, step A computes W^{n+1} on R1 at plane z from W^n at
+// z-1, z, z+1 (the plane z with its ring staged in shared memory, the z neighbours in registers)
+// and stages it; step B then computes W^{n+2} on the tile at plane z-1 from W^{n+1} at z-2, z-1
+// (shared memory, staged one iteration earlier), z (registers).  Step A runs on planes
+// z0-1 .. z1 of the chunk [z0, z1), step B on z0 .. z1-1.  Nodes outside the domain are 0 (the
+// Dirichlet values).  Same operations in the same order as two k_step3d steps:
+//   W^{n+1} = fma(az, zm + zp, fma(ay, ym + yp, fma(ax, xm + xp, fma(b, W^n, -W^{n-1}))))
+//   acc = fma(w_{n+2}, W^{n+2}, fma(w_{n+1}, W^{n+1}, acc))
+// Global traffic per node and 2 steps: read W^{n-1}, W^n, acc, write W^{n+1}, W^{n+2}, acc
+// (24 B instead of 40 B), plus the ring re-reads (mostly L1/L2 hits).
+constexpr int k3TX = 32, k3TY = 16;   // threads = R1 extent; tile (k3TX - 2) x (k3TY - 2)
+
+template <int KIND>
+__global__ void __launch_bounds__(k3TX * k3TY) k_step3d2(const float* __restrict__ gp, const float* __restrict__ gc,
+                                                     float* __restrict__ op, float* __restrict__ oc,
+                                                     float* __restrict__ acc, const double* __restrict__ v,
+                                                     const double* __restrict__ mw, double* __restrict__ out,
+                                                     int nx, int ny, int nz, int zc, StepCoef<float> cf, float w2,
+                                                     double* partials, unsigned* counter, double* scal_out) {
+  __shared__ float P[k3TY + 2][k3TX + 2];   // W^n(z) on R1 and its ring
+  __shared__ float Q[2][k3TY][k3TX];        // W^{n+1} on R1, planes z - 1 and z
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = tx + k3TX * ty;
+  const int xb = blockIdx.x * (k3TX - 2) - 1, yb = blockIdx.y * (k3TY - 2) - 1;   // R1 origin
+  const int x = xb + tx, y = yb + ty;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
+  const bool inxy = x >= 0 && x < nx && y >= 0 && y < ny;
+  const bool tile = inxy && tx >= 1 && tx < k3TX - 1 && ty >= 1 && ty < k3TY - 1;
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t col = (int64_t)x + (int64_t)nx * y;
+  auto ldc = [&](int z) { return (inxy && z >= 0 && z < nz) ? __ldg(gc + col + plane * z) : 0.0f; };
+  float cm = ldc(z0 - 2), c0 = ldc(z0 - 1), cp = ldc(z0);   // W^n at z - 1, z, z + 1 for z = z0 - 1
+  float q2 = 0.0f, q1 = 0.0f;   // W^{n+1} of this column at z - 2, z - 1
+  float accA = 0.0f;            // acc(z - 1) after step n + 1
+  double part = 0.0;
+  int buf = 0;
+  for (int z = z0 - 1; z <= z1; ++z) {
+    const bool zin = z >= 0 && z < nz;
+    for (int i = tid; i < (k3TX + 2) * (k3TY + 2); i += k3TX * k3TY) {
+      const int px = i % (k3TX + 2), py = i / (k3TX + 2);
+      const int gx = xb - 1 + px, gy = yb - 1 + py;
+      P[py][px] = (zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny)
+                      ? __ldg(gc + gx + (int64_t)nx * gy + plane * z) : 0.0f;
+    }
+    const float cpp = ldc(z + 2);
+    const float wpz = (inxy && zin) ? __ldg(gp + col + plane * z) : 0.0f;
+    const float accz = (tile && zin) ? acc[col + plane * z] : 0.0f;
+    __syncthreads();
+    // step A: W^{n+1}(z) on R1
+    float a1 = 0.0f;
+    if (inxy && zin) {
+      float u = fmaf(cf.b, c0, -wpz);
+      u = fmaf(cf.a[0], P[ty + 1][tx] + P[ty + 1][tx + 2], u);
+      u = fmaf(cf.a[1], P[ty][tx + 1] + P[ty + 2][tx + 1], u);
+      u = fmaf(cf.a[2], cm + cp, u);
+      a1 = u;
+    }
+    Q[buf][ty][tx] = a1;
+    const float accN = fmaf(cf.w1, a1, accz);
+    __syncthreads();
+    // step B: W^{n+2}(z - 1) on the tile
+    if (z - 1 >= z0 && tile) {
+      const float(*R)[k3TX] = Q[buf ^ 1];
+      float u = fmaf(cf.b, q1, -cm);
+      u = fmaf(cf.a[0], R[ty][tx - 1] + R[ty][tx + 1], u);
+      u = fmaf(cf.a[1], R[ty - 1][tx] + R[ty + 1][tx], u);
+      u = fmaf(cf.a[2], q2 + a1, u);
+      const float a = fmaf(w2, u, accA);
+      const int64_t idx = col + plane * (z - 1);
+      if (KIND == K_STEP) {
+        op[idx] = q1;
+        oc[idx] = u;
+        acc[idx] = a;
+      } else if (KIND == K_LAST_OUT) {
+        out[idx] = (double)a;
+      } else {
+        const double vi = v[idx];
+        const double o = vi - (double)a;
+        out[idx] = o;
+        part = fma(mw ? vi * mw[idx] : vi, o, part);
+      }
+    }
+    q2 = q1;
+    q1 = a1;
+    accA = accN;
+    cm = c0;
+    c0 = cp;
+    cp = cpp;
+    buf ^= 1;
+  }
+  if (KIND == K_LAST_AV) {
+    part = block_sum(part);
+    double total;
+    if (grid_reduce(part, partials, counter, &total) && flat_tid() == 0) *scal_out = total;
+  }
+}
+
 // --------------------------------------------------------------------------- host side
 struct LaunchShape {
   dim3 grid, block;
@@ -508,6 +608,74 @@ static whv_status dispatch_df_dim(whv_grid g, const TimeGridH& tg, const double*
            : launch_solve_df<DIM, false, false>(g, tg, v, f, out, epi, nl, bufs, acc);
 }
 
+constexpr int kZChunk2 = 32;   // planes per CTA of the two-step 3-D kernel
+
+static dim3 grid_3d2(whv_grid g) {
+  return dim3((g->n[0] + k3TX - 3) / (k3TX - 2), (g->n[1] + k3TY - 3) / (k3TY - 2),
+              (g->n[2] + kZChunk2 - 1) / kZChunk2);
+}
+
+// Steps n = 1 .. nt-1 of a 3-D f = 0 FP32 wave solve (c = 1, second order) after the Taylor
+// start (W^0 in buf[0], W^1 in buf[1], acc): one single step when their number is odd, then
+// two-step passes alternating between the buffer pairs (0, 1) and (2, 3); the last launch writes
+// the epilogue.
+static whv_status two_step_3d(whv_grid g, const TimeGridH& tg, const double* v, double* out, int epi,
+                              int* launches, void* const* bufs, void* accbuf) {
+  float* buf[4] = {(float*)bufs[0], (float*)bufs[1], (float*)bufs[2], (float*)bufs[3]};
+  float* acc = (float*)accbuf;
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  StepCoef<float> cf = coef_of<float>(g, tg);
+  double* part = chan(g, CH_STEP);
+  unsigned* cnt = g->counters + CH_STEP;
+  const dim3 g2 = grid_3d2(g), b2(k3TX, k3TY, 1);
+  if ((int64_t)g2.x * g2.y * g2.z > chan_cap(g, CH_STEP)) return fail(g, WHV_ERR_INVALID, "grid too large for the fused reduction");
+  const LaunchShape ls = shape_of(g);
+  float* wprev = buf[0];
+  float* wcur = buf[1];
+  int n = 1, nl = 0;
+  if ((tg.nt - 1) % 2 == 1) {   // one single step first (the last one when nt = 2)
+    cf.w1 = (float)tg.weight[2];
+    const bool last = tg.nt == 2;
+    if (!last)
+      k_step3d<float, false, false, K_STEP><<<ls.grid, ls.block, 0, g->stream>>>(
+          wcur, wprev, acc, nullptr, nullptr, nullptr, nullptr, nullptr, nx, ny, nz, kZChunk, cf, nullptr, nullptr, nullptr);
+    else if (epi == 0)
+      k_step3d<float, false, false, K_LAST_OUT><<<ls.grid, ls.block, 0, g->stream>>>(
+          wcur, wprev, acc, nullptr, nullptr, nullptr, nullptr, out, nx, ny, nz, kZChunk, cf, nullptr, nullptr, nullptr);
+    else
+      k_step3d<float, false, false, K_LAST_AV><<<ls.grid, ls.block, 0, g->stream>>>(
+          wcur, wprev, acc, nullptr, nullptr, v, g->mw, out, nx, ny, nz, kZChunk, cf, part, cnt, g->scal + S_PQ);
+    WHV_CUDA(g, cudaGetLastError());
+    ++nl;
+    float* t = wprev; wprev = wcur; wcur = t;
+    n = 2;
+  }
+  while (n < tg.nt) {   // W^n -> W^{n+2}
+    cf.w1 = (float)tg.weight[n + 1];
+    const float w2 = (float)tg.weight[n + 2];
+    const bool last = n + 2 == tg.nt;
+    const bool in01 = wprev == buf[0] || wprev == buf[1];   // (wprev, wcur) is one of the pairs
+    float* op = in01 ? buf[2] : buf[0];
+    float* oc = in01 ? buf[3] : buf[1];
+    if (!last)
+      k_step3d2<K_STEP><<<g2, b2, 0, g->stream>>>(wprev, wcur, op, oc, acc, nullptr, nullptr, nullptr, nx, ny, nz,
+                                                  kZChunk2, cf, w2, nullptr, nullptr, nullptr);
+    else if (epi == 0)
+      k_step3d2<K_LAST_OUT><<<g2, b2, 0, g->stream>>>(wprev, wcur, op, oc, acc, nullptr, nullptr, out, nx, ny, nz,
+                                                      kZChunk2, cf, w2, nullptr, nullptr, nullptr);
+    else
+      k_step3d2<K_LAST_AV><<<g2, b2, 0, g->stream>>>(wprev, wcur, op, oc, acc, v, g->mw, out, nx, ny, nz, kZChunk2,
+                                                     cf, w2, part, cnt, g->scal + S_PQ);
+    WHV_CUDA(g, cudaGetLastError());
+    ++nl;
+    wprev = op;
+    wcur = oc;
+    n += 2;
+  }
+  *launches = nl;
+  return WHV_OK;
+}
+
 template <typename T, int DIM, int ORDER, bool VARC, bool FORCE>
 static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
                                double* out, int epi, int* nlaunch, void* const* bufs, void* accbuf,
@@ -534,6 +702,14 @@ static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v,
     if (kb > 1) {
       int nl = 0;
       whv_status s = blocked_steps_2d<T, ORDER, VARC>(g, tg, v, out, epi, kb, &nl, bufs, accbuf);
+      *nlaunch += nl;
+      return s;
+    }
+  }
+  if constexpr (DIM == 3 && ORDER == 2 && !VARC && !FORCE && sizeof(T) == 4) {
+    if (kb > 1) {
+      int nl = 0;
+      whv_status s = two_step_3d(g, tg, v, out, epi, &nl, bufs, accbuf);
       *nlaunch += nl;
       return s;
     }
@@ -812,8 +988,10 @@ extern "C" whv_status whv_autotune(whv_grid g, const whv_params* p, int* best) {
     if (best) *best = 1;
     return WHV_OK;
   }
-  // 2-D: per step, blocked sweeps of k steps, and the persistent kernel (-k) where its tiles fit
+  // 2-D: per step, blocked sweeps of k steps, and the persistent kernel (-k) where its tiles fit;
+  // 3-D FP32 (c = 1): per step and two steps per launch
   std::vector<int> cands = {1};
+  if (g->dim == 3 && g->order == 2 && !g->c2 && g->precision == WHV_FP32_STEP) cands.push_back(2);
   if (g->dim == 2) {
     for (int k : {2, 4, 6, 8, 10, 12, 16}) cands.push_back(k);
     for (int k : {4, 6, 8, 10, 12})

@@ -383,6 +383,29 @@ def test_blocked_fp32_four_cell_sweeps_equal_single_steps_bitwise(npts, omega, o
         assert np.array_equal(out, ref), (k, np.abs(out - ref).max())
 
 
+@pytest.mark.parametrize("npts,omega", [((37, 20, 11), 8.0), ((12, 10, 40), 6.0), ((70, 33, 45), 9.0),
+                                         ((70, 33, 45), 9.7), ((5, 6, 4), 3.0)])
+def test_two_step_3d_equals_single_steps_bitwise(npts, omega):
+    """3-D FP32, c = 1: two leapfrog steps per launch (xy tiles with a one-node ring, z chunks with
+    a ragged last one, an odd number of steps handled by one single step first) perform the
+    single-step kernel's operations in its order: Pi_h v is bitwise the k = 1 result, and the
+    operator epilogue inside fixed-iteration CG agrees to rounding of the reductions."""
+    g, og, _ = make(npts, 2, None, precision=whv.WHV_FP32_STEP)
+    prm = whv.make_params(omega)
+    tg = WH.time_grid_for(og, omega)
+    v = dev(I.random_field(og.shape, 25))
+    g.whv_set_steps_per_sweep(1)
+    ref = host(g.whv_apply_pi(prm, v))
+    f = dev(I.gaussian(npts, [0.4, 0.5, 0.55], 0.15, omega ** 2))
+    prm2 = whv.make_params(omega, method="cg", tol=0.0, maxit=4)
+    u1 = host(g.whv_solve(prm2, f)[0])
+    g.whv_set_steps_per_sweep(2)
+    out = host(g.whv_apply_pi(prm, v))
+    assert np.array_equal(out, ref), (tg.nt, np.abs(out - ref).max())
+    u2 = host(g.whv_solve(prm2, f)[0])
+    assert relmax(u2, u1) < 1e-9
+
+
 def test_autotune_picks_valid_k_and_keeps_results():
     g, og, _ = make((257, 257), precision=whv.WHV_FP32_STEP)
     prm = whv.make_params(30.0, method="cg", tol=1e-6, maxit=500)

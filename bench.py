@@ -615,23 +615,34 @@ def main():
     v3 = torch.randn(g3.N, dtype=torch.float64, device="cuda")
     o3 = torch.empty_like(v3)
     torch.cuda.synchronize()
-    g3.whv_apply_pi(prm3, v3, None, o3)
-    stream.synchronize()
-    reps3 = 5
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps3):
+
+    def time_3d(k):
+        g3.whv_set_steps_per_sweep(k)
         g3.whv_apply_pi(prm3, v3, None, o3)
-    e1.record(stream)
-    e1.synchronize()
-    # per step: the first-step kernel's share is 1/nt of the launches; report the wave-solve mean
-    t3 = e0.elapsed_time(e1) * 1e-3 / (reps3 * nt3)
-    ach3 = 20 * g3.N / t3 / 1e9
-    stencil_hbm = {"kernel": "k_step3d (3-D 7-point z-marching step + filter, FP32)",
+        stream.synchronize()
+        reps3 = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps3):
+            g3.whv_apply_pi(prm3, v3, None, o3)
+        e1.record(stream)
+        e1.synchronize()
+        # per step: the first-step kernel's share is 1/nt of the launches; the wave-solve mean
+        return e0.elapsed_time(e1) * 1e-3 / (reps3 * nt3)
+
+    t31 = time_3d(1)    # k_step3d, one step per launch
+    t32 = time_3d(2)    # k_step3d2, two steps per launch
+    ach31, ach32 = 20 * g3.N / t31 / 1e9, 20 * g3.N / t32 / 1e9
+    stencil_hbm = {"kernel": "k_step3d2 (3-D 7-point, two leapfrog steps + filter per launch, FP32)",
                    "workload": "256^3 nodes (254^3 unknowns), omega=40, f = 0 wave solves, nt=%d" % nt3,
-                   "bound": "hbm", "achieved": ach3, "peak": peak, "unit": "GB/s", "frac": ach3 / peak,
-                   "bytes_per_lup": 20, "glups": g3.N / t3 / 1e9, "step_us": t3 * 1e6,
-                   "traffic": traffic_for("k_step3d", "fp32")}
+                   "bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s", "frac": ach32 / peak,
+                   "bytes_per_lup": 20, "glups": g3.N / t32 / 1e9, "step_us": t32 * 1e6,
+                   "own_bytes_per_lup": 12, "own_frac": 12 * g3.N / t32 / 1e9 / peak,
+                   "note": "achieved/frac count the 20 B per LUP of single-step streaming (equivalent "
+                           "bandwidth); own_frac counts the 12 B per LUP the two-step kernel must move",
+                   "single_step": {"kernel": "k_step3d (one step per launch)", "achieved": ach31,
+                                   "frac": ach31 / peak, "glups": g3.N / t31 / 1e9, "step_us": t31 * 1e6,
+                                   "traffic": traffic_for("k_step3d", "fp32")}}
     g3.close()
     del v3, o3
 

@@ -569,6 +569,14 @@ static whv_status launch_solve_df(whv_grid g, const TimeGridH& tg, const double*
   else
     k_first_df<DIM, VARC, FORCE, true><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, g->c2, f, nx, ny, nz, cf);
   WHV_CUDA(g, cudaGetLastError());
+  if constexpr (DIM == 2 && !VARC) {   // blocked double-float sweeps unless one step per launch is set
+    if (g->kblock != 1) {
+      int nl = 0;
+      whv_status s = blocked_steps_2d_df<FORCE>(g, tg, v, f, out, epi, &nl, bufs, accbuf);
+      *nlaunch = 1 + nl;
+      return s;
+    }
+  }
   *nlaunch = tg.nt;
   dfl* wprev = b0;
   dfl* wcur = b1;

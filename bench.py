@@ -303,7 +303,7 @@ def run_workload(args):
             for om in I.C4_OMEGAS:
                 w = I.WORKLOADS[f"c4_{n}_{int(om)}"]
                 prm = whv.make_params(om, method="cg", tol=w.tol, maxit=3000, refine_fp64=fp32,
-                                      check_every=args.check_every)
+                                      residual_df64=fp32 and args.residual == "df64", check_every=args.check_every)
                 tmpl = whv.Grid(w.npts, precision=gprec, stream=stream)
                 tmpl.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
                 b = tmpl.whv_get_basis(want_vectors=True)
@@ -342,8 +342,9 @@ def run_workload(args):
             b = g64.whv_apply_pi(prm, torch.zeros_like(f), f)
             chk.append(float((r - us[k]).norm() / b.norm()))
             g64.close()
-        form = ("DEVD-CG with FP32 stepping inside FP64 residual correction" if fp32
-                else "DEVD-CG, FP64 stepping")
+        form = (("DEVD-CG with FP32 stepping inside FP64 residual correction"
+                 + (" (double-float b and residual wave solves)" if args.residual == "df64" else ""))
+                if fp32 else "DEVD-CG, FP64 stepping")
         line.update({"workload": "c4", "value": ms, "ms_per_step": ms, "dtype": "f32" if fp32 else "f64",
                      "krylov_dtype": "f64",
                      "config": {"workload": f"batched: 4 squares (257..1025)^2 x 4 omega x {nsrc} Gaussian sources "

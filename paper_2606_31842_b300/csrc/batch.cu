@@ -28,8 +28,10 @@
 
 #include <algorithm>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
+#include "df64.cuh"
 #include "stencil_ops.cuh"
 #include "quad2d.cuh"
 #include "whv_device.cuh"
@@ -402,6 +404,162 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
   }
 }
 
+// Double-float roles (2-D, second order, c = 1): the b and residual wave solves of the FP64
+// residual correction in pairs of FP32 numbers (df64.cuh) instead of FP64 arithmetic, which runs
+// at 1/64 of the FP32 rate on this GPU.  Same work items, sweeps and grid barriers as
+// k_batch_block2d; each CTA stages a 64 x 64 region of 8-byte hi/lo pairs, thread (warp, lane)
+// owns column 32 (w & 1) + lane and rows (w >> 1) + 16 r, and sub-step s advances the window
+// [s, 64 - s)^2 (with ~150 FP32 instructions per update the shrinking window pays).  The updates
+// are the double-float operations of the single-grid kernels k_first_df / k_step_df:
+//   Taylor start  W^1 = W^0 + (dt^2 / 2) (sum_m ih2_m ((W_- + W_+) - 2 W^0) - f)
+//   step          W^{n+1} = ((b W^n - W^{n-1}) + a_x (W_l + W_r)) + a_y (W_d + W_u) - fph_n f
+//   filter        acc = w_0 W^0 + w_1 W^1, then acc + w_{n+1} W^{n+1}
+// with fph_n = dt^2 cos(omega_hat t^n) from the role's table.
+template <bool FORCED>
+__global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d_df(const BTile<dfl>* __restrict__ P,
+                                                                   const int* __restrict__ nact, int J, int K,
+                                                                   const dfl* __restrict__ wtab,
+                                                                   const dfl* __restrict__ ptab, unsigned* bar_count,
+                                                                   unsigned* bar_gen, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  dfl* const S0 = reinterpret_cast<dfl*>(smem_raw);
+  dfl* const S1 = S0 + kBReg * kBReg;
+  __shared__ int64_t s_tile0[kBatchMaxProblems + 1];
+  __shared__ BTile<dfl> sB;
+  const int np = nact[0];
+  for (int p = threadIdx.x; p <= np; p += blockDim.x)
+    s_tile0[p] = p < np ? P[p].tile0 : P[np - 1].tile0 + P[np - 1].ntiles;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = 32 * (warp & 1) + lane;
+  const int jb = warp >> 1;
+  const int H = K, TW = kBReg - 2 * H;
+  for (int j = 0; j < J; ++j) {
+    const int A = nact[j];
+    const int64_t total = s_tile0[A];
+    int cur_p = -1;
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+      int p = cur_p < 0 ? 0 : cur_p;
+      while (s_tile0[p + 1] <= item) ++p;
+      if (p != cur_p) {
+        __syncthreads();
+        if (threadIdx.x == 0) sB = P[p];
+        __syncthreads();
+        cur_p = p;
+      }
+      const BTile<dfl>& B = sB;
+      if (B.halt && *B.halt != 0.0) {
+        item = skip_to(item, s_tile0[p + 1]);
+        continue;
+      }
+      const int t = (int)(item - B.tile0);
+      const int x0 = (t % B.tiles_x) * TW - H, y0 = (t / B.tiles_x) * TW - H;
+      const int gx = x0 + i;
+      const int nx = B.nx, ny = B.ny;
+      const bool colin = gx >= 0 && gx < nx;
+      const int n0 = j * K;
+      const int kk = min(K, B.nt - n0);
+      const bool first = j == 0, last = n0 + kk == B.nt;
+      const dfl* wtb = wtab + B.wofs;
+      const dfl* ptb = ptab + B.wofs;
+      const int qi = (j + 1) & 1, qo = j & 1;
+      dfl cur[kBRows], prv[kBRows], acr[kBRows];
+      dfl ff[FORCED ? kBRows : 1];
+#pragma unroll
+      for (int r = 0; r < kBRows; ++r) {
+        const int jr = jb + kBPitch * r;
+        const int gy = y0 + jr;
+        const bool in = colin && gy >= 0 && gy < ny;
+        const int64_t gi = gx + (int64_t)nx * gy;
+        const bool tile = in && i >= H && i < kBReg - H && jr >= H && jr < kBReg - H;
+        if (first) {
+          cur[r] = (in && B.v) ? df_from(__ldg(B.v + gi)) : df_zero();
+          prv[r] = df_zero();
+          acr[r] = df_mul(wtb[0], cur[r]);
+        } else {   // written by other CTAs in the previous sweep: coherent loads
+          const float2 c2v = in ? __ldcg(reinterpret_cast<const float2*>(B.w[2 * qi + 1] + gi)) : make_float2(0.f, 0.f);
+          const float2 p2v = in ? __ldcg(reinterpret_cast<const float2*>(B.w[2 * qi] + gi)) : make_float2(0.f, 0.f);
+          const float2 a2v = tile ? __ldcg(reinterpret_cast<const float2*>(B.acc + gi)) : make_float2(0.f, 0.f);
+          cur[r] = dfl{c2v.x, c2v.y};
+          prv[r] = dfl{p2v.x, p2v.y};
+          acr[r] = dfl{a2v.x, a2v.y};
+        }
+        if (FORCED) ff[r] = in ? df_from(__ldg(B.f + gi)) : df_zero();
+      }
+#pragma unroll
+      for (int r = 0; r < kBRows; ++r) S0[(jb + kBPitch * r) * kBReg + i] = cur[r];
+      __syncthreads();
+      const dfl* Ain = S0;
+      dfl* Bout = S1;
+      for (int s = 1; s <= kk; ++s) {
+        const int n = n0 + s - 1;   // W^n -> W^{n+1}
+        const int lo = s, hi = kBReg - s;
+        const bool colact = colin && i >= lo && i < hi;
+        const dfl ws = wtb[n + 1];
+        const dfl fph = FORCED ? ptb[n] : df_zero();
+#pragma unroll
+        for (int r = 0; r < kBRows; ++r) {
+          const int jr = jb + kBPitch * r;
+          const int gy = y0 + jr;
+          if (colact && jr >= lo && jr < hi && gy >= 0 && gy < ny) {
+            const int l = jr * kBReg + i;
+            const dfl c = cur[r];
+            const dfl sx = df_add(gx > 0 ? Ain[l - 1] : df_zero(), gx < nx - 1 ? Ain[l + 1] : df_zero());
+            const dfl sy = df_add(gy > 0 ? Ain[l - kBReg] : df_zero(), gy < ny - 1 ? Ain[l + kBReg] : df_zero());
+            dfl wn;
+            if (n == 0) {   // Taylor start
+              const dfl c2x = {2.0f * c.hi, 2.0f * c.lo};
+              dfl L = df_add(df_zero(), df_mul(B.ih2x, df_sub(sx, c2x)));
+              L = df_add(L, df_mul(B.ih2y, df_sub(sy, c2x)));
+              if (FORCED) L = df_sub(L, ff[r]);
+              wn = df_add(c, df_mul(dfl{0.5f * B.dt2.hi, 0.5f * B.dt2.lo}, L));
+            } else {
+              wn = df_sub(df_mul(B.b, c), prv[r]);
+              wn = df_add(wn, df_mul(B.ax, sx));
+              wn = df_add(wn, df_mul(B.ay, sy));
+              if (FORCED) wn = df_sub(wn, df_mul(fph, ff[r]));
+            }
+            prv[r] = c;
+            cur[r] = wn;
+            Bout[l] = wn;
+            acr[r] = df_add(acr[r], df_mul(ws, wn));
+          }
+        }
+        __syncthreads();
+        dfl* tmp = const_cast<dfl*>(Ain);
+        Ain = Bout;
+        Bout = tmp;
+      }
+      double part = 0.0;
+      const bool coltile = colin && i >= H && i < kBReg - H;
+#pragma unroll
+      for (int r = 0; r < kBRows; ++r) {
+        const int jr = jb + kBPitch * r;
+        const int gy = y0 + jr;
+        if (!(coltile && jr >= H && jr < kBReg - H && gy >= 0 && gy < ny)) continue;
+        const int64_t gi = gx + (int64_t)nx * gy;
+        if (!last) {
+          B.w[2 * qo + 1][gi] = cur[r];
+          B.w[2 * qo][gi] = prv[r];
+          B.acc[gi] = acr[r];
+        } else if (B.epi == 0) {
+          B.out[gi] = df_to(acr[r]);
+        } else {
+          const double vi = __ldg(B.v + gi);
+          const double o = vi - df_to(acr[r]);
+          B.out[gi] = o;
+          part = fma(B.mw ? vi * __ldg(B.mw + gi) : vi, o, part);
+        }
+      }
+      if (last && B.epi == 1) {
+        part = block_sum(part);
+        if (threadIdx.x == 0) B.partials[t] = part;
+      }
+    }
+    if (!grid_barrier(bar_count, bar_gen, err, gridDim.x)) return;
+  }
+}
+
 // ------------------------------------------------------------------ per-problem small kernels
 struct BFin {
   const double* partials;
@@ -555,13 +713,41 @@ static void batch_init() {
   static bool done = false;
   if (done) return;
   done = true;
+  cudaFuncSetAttribute(k_batch_block2d_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       2 * kBReg * kBReg * (int)sizeof(dfl));
+  cudaFuncSetAttribute(k_batch_block2d_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       2 * kBReg * kBReg * (int)sizeof(dfl));
   block2d_attrs<float, 2, false>(); block2d_attrs<float, 2, true>();
   block2d_attrs<float, 4, false>(); block2d_attrs<float, 4, true>();
   block2d_attrs<double, 2, false>(); block2d_attrs<double, 2, true>();
   block2d_attrs<double, 4, false>(); block2d_attrs<double, 4, true>();
 }
 
-// Device tables of one role, stepping in T (double on an FP32 grid: its FP64 buffer set).
+template <typename T>
+static T cvt(double x) {
+  if constexpr (std::is_same<T, dfl>::value) return df_from(x);
+  else return (T)x;
+}
+
+template <bool FORCED>
+static cudaError_t launch_block2d_df(cudaStream_t st, const Wave& w, unsigned* bar, int* err) {
+  const BTile<dfl>* P = (const BTile<dfl>*)w.desc;
+  const dfl* wt = (const dfl*)w.wtab;
+  const dfl* ph = (const dfl*)w.ptab;
+  unsigned* bc = bar;
+  unsigned* bg = bar + 1;
+  int J = w.J, K = w.K;
+  const int* na = w.nact;
+  void* args[] = {(void*)&P, (void*)&na, (void*)&J, (void*)&K, (void*)&wt, (void*)&ph,
+                  (void*)&bc, (void*)&bg, (void*)&err};
+  return cudaLaunchCooperativeKernel((const void*)k_batch_block2d_df<FORCED>, dim3(w.nblocks), dim3(kBThreads), args,
+                                     w.smem, st);
+}
+
+constexpr int kBDfK = 4;   // sub-steps per sweep of the double-float roles
+
+// Device tables of one role, stepping in T (double on an FP32 grid: its FP64 buffer set; dfl:
+// double-float pairs in the same 8-byte buffers, 2-D second order with c = 1 only).
 // Problems are ordered by their number of sweeps (descending), so the active problems of sweep j
 // are a prefix.
 template <typename T, int DIM, int ORDER, bool VARC>
@@ -571,8 +757,10 @@ static whv_status make_wave(BatchCtx& c, const RoleIO& io, Wave* out) {
   const bool blocked = DIM == 2;
   bool forced = false;
   for (const double* f : io.f) forced = forced || f != nullptr;
+  constexpr bool DF = std::is_same<T, dfl>::value;
+  static_assert(!DF || (DIM == 2 && ORDER == 2 && !VARC), "double-float roles: 2-D, second order, c = 1");
   Wave w;
-  w.K = blocked ? batch_k(c.g0, fp64) : 1;
+  w.K = DF ? kBDfK : (blocked ? batch_k(c.g0, fp64) : 1);
   std::vector<int> order(np), nsw(np);
   for (int p = 0; p < np; ++p) nsw[p] = (c.tgs[p].nt + w.K - 1) / w.K;
   std::iota(order.begin(), order.end(), 0);
@@ -595,10 +783,14 @@ static whv_status make_wave(BatchCtx& c, const RoleIO& io, Wave* out) {
     if (!accb || !bufs[0]) return fail(c.g0, WHV_ERR_INVALID, "batched: stepping buffers missing");
     const T* c2 = VARC ? (const T*)(fp64 ? (const void*)g->c2 : (const void*)g->c2f) : nullptr;
     const int wofs = (int)wtab.size();
-    for (int n = 0; n <= tg.nt; ++n) { wtab.push_back((T)tg.weight[n]); ptab.push_back((T)tg.phase[n]); }
+    for (int n = 0; n <= tg.nt; ++n) {
+      wtab.push_back(cvt<T>(tg.weight[n]));
+      // double-float steps take the forcing factor dt^2 cos(omega_hat t^n) whole
+      ptab.push_back(cvt<T>(DF ? tg.dt * tg.dt * tg.phase[n] : tg.phase[n]));
+    }
     const double h2x = g->h[0] * g->h[0], h2y = g->h[1] * g->h[1];
-    int ntiles;
-    if (blocked) {
+    int ntiles = 0;
+    if constexpr (DIM == 2) {
       BTile<T> B{};
       for (int m = 0; m < 4; ++m) B.w[m] = (T*)bufs[m];
       B.acc = (T*)accb;
@@ -609,11 +801,11 @@ static whv_status make_wave(BatchCtx& c, const RoleIO& io, Wave* out) {
       B.tiles_x = (g->n[0] + TW - 1) / TW;
       B.ntiles = B.tiles_x * ((g->n[1] + TW - 1) / TW);
       B.epi = io.epi; B.wofs = wofs;
-      B.ih2x = (T)(ORDER == 2 ? 1.0 / h2x : 1.0 / (12.0 * h2x));
-      B.ih2y = (T)(ORDER == 2 ? 1.0 / h2y : 1.0 / (12.0 * h2y));
-      B.dt2 = (T)(tg.dt * tg.dt);
+      B.ih2x = cvt<T>(ORDER == 2 ? 1.0 / h2x : 1.0 / (12.0 * h2x));
+      B.ih2y = cvt<T>(ORDER == 2 ? 1.0 / h2y : 1.0 / (12.0 * h2y));
+      B.dt2 = cvt<T>(tg.dt * tg.dt);
       const double ax = tg.dt * tg.dt / h2x, ay = tg.dt * tg.dt / h2y;
-      B.ax = (T)ax; B.ay = (T)ay; B.b = (T)(2.0 - 2.0 * (ax + ay));
+      B.ax = cvt<T>(ax); B.ay = cvt<T>(ay); B.b = cvt<T>(2.0 - 2.0 * (ax + ay));
       B.tile0 = tile0;
       ntiles = B.ntiles;
       d2[k] = B;
@@ -661,7 +853,16 @@ static whv_status make_wave(BatchCtx& c, const RoleIO& io, Wave* out) {
   B_CUDA(c.g0, cudaMemcpy(w.ptab, ptab.data(), ptab.size() * sizeof(T), cudaMemcpyHostToDevice));
   B_CUDA(c.g0, cudaMemcpy(w.fin, fin.data(), np * sizeof(BFin), cudaMemcpyHostToDevice));
   int per_sm = 0;
-  if (blocked) {
+  if constexpr (DF) {
+    w.smem = 2 * (size_t)kBReg * kBReg * sizeof(dfl);
+    if (forced) {
+      w.launch = &launch_block2d_df<true>;
+      B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_block2d_df<true>, kBThreads, w.smem));
+    } else {
+      w.launch = &launch_block2d_df<false>;
+      B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_block2d_df<false>, kBThreads, w.smem));
+    }
+  } else if (blocked) {
     w.smem = forced ? batch_smem<T, ORDER, VARC, true>() : batch_smem<T, ORDER, VARC, false>();
     if (forced) {
       w.launch = &launch_block2d<T, ORDER, VARC, true>;
@@ -899,16 +1100,24 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
     io_b.v.assign(np, nullptr);
     io_b.f.assign(f_dev, f_dev + np);
     io_b.out = c.each([](whv_grid g) { return g->bo; });
-    Wave wb;
-    TRY((make_wave<double, DIM, ORDER, VARC>(c, io_b, &wb)));
-    RoleIO io_ax;   // q = A x in FP64
+    RoleIO io_ax;   // q = A x in FP64 (or double-float)
     io_ax.v = c.each([](whv_grid g) { return (const double*)g->xo; });
     io_ax.f.assign(np, nullptr);
     io_ax.out = c.each([](whv_grid g) { return g->q; });
     io_ax.epi = 1;
     io_ax.halt = true;
-    Wave wax;
-    TRY((make_wave<double, DIM, ORDER, VARC>(c, io_ax, &wax)));
+    Wave wb, wax;
+    bool dfr = false;   // double-float b and residual wave solves (WHV_RESIDUAL_DF64)
+    if constexpr (DIM == 2 && ORDER == 2 && !VARC) dfr = (c.params[0].flags & WHV_RESIDUAL_DF64) != 0;
+    if (dfr) {
+      if constexpr (DIM == 2 && ORDER == 2 && !VARC) {
+        TRY((make_wave<dfl, 2, 2, false>(c, io_b, &wb)));
+        TRY((make_wave<dfl, 2, 2, false>(c, io_ax, &wax)));
+      }
+    } else {
+      TRY((make_wave<double, DIM, ORDER, VARC>(c, io_b, &wb)));
+      TRY((make_wave<double, DIM, ORDER, VARC>(c, io_ax, &wax)));
+    }
     TRY(run_wave(c, wb));
     TRY(check_barrier(c));
     for (int p = 0; p < np; ++p) {
@@ -1143,6 +1352,8 @@ extern "C" whv_status whv_solve_batched(int nprob, const whv_grid* grids, const 
                   "whv_solve_batched: grids must share stream, precision, dimension, order and speed kind");
     if (params[p].method != WHV_CG) return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: method must be WHV_CG");
     if (g->cons) return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: the conservative operator is not batched");
+    if (((params[p].flags & WHV_RESIDUAL_DF64) != 0) != ((params[0].flags & WHV_RESIDUAL_DF64) != 0))
+      return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: WHV_RESIDUAL_DF64 must be set for all problems or none");
     if (((params[p].flags & WHV_REFINE_FP64) != 0) != refine)
       return fail(g0, WHV_ERR_INVALID, "whv_solve_batched: WHV_REFINE_FP64 must be set for all problems or none");
     if (!(params[p].tol >= 0.0) || params[p].maxit < 0)

@@ -253,3 +253,43 @@ def test_batched_fp32_sweeps_match_single_grid_fp32(k):
         modes, lam2, _ = SP.select_modes(og, tg, 4)
         ref = K.devd_solve(og, tg, f, SP.basis(og, modes), lam2, "cg", 0.0, it).u
         assert IND.relmax(u.cpu().numpy(), ref) < 1e-4
+
+
+@pytest.mark.parametrize("df", [False, True])
+def test_batched_refine_with_double_float_residuals(df):
+    """FP32 stepping inside FP64 residual correction with the b and residual wave solves in FP64 or
+    in double-float pairs (2-D, c = 1): every problem's true FP64 residual meets 1e-9 and its
+    solution is the direct one; problems of uneven size and frequency stop independently."""
+    probs = _problems((65, 97, 150), (12.0, 18.0), 1, 8)
+    stream = torch.cuda.Stream()
+    grids, params, fs = [], [], []
+    for npts, om, f, nd in probs:
+        g = whv.Grid(npts, precision=whv.WHV_FP32_STEP, stream=stream)
+        prm = whv.make_params(om, method="cg", tol=1e-9, maxit=4000, refine_fp64=True, residual_df64=df)
+        g.whv_set_deflation_basis(prm, nd, whv.WHV_BASIS_CLOSED_FORM)
+        grids.append(g); params.append(prm); fs.append(dev(f))
+    us, infos = whv.whv_solve_batched(grids, params, fs)
+    assert all(i["status"] == "OK" for i in infos), infos
+    for (npts, om, f, nd), u, info in zip(probs, us, infos):
+        assert info["true_rel_residual"] < 1e-9
+        og = O.Grid(npts)
+        tg = WH.time_grid_for(og, om)
+        assert IND.relmax(u.cpu().numpy(), IND.helmholtz_direct(npts, tg.omega_eff, f)) < 1e-6
+        # the residual recomputed with an FP64 wave solve of the FP64 grid
+        g64 = whv.Grid(npts, precision=whv.WHV_FP64)
+        prm64 = whv.make_params(om)
+        ff = dev(f)
+        r = g64.whv_apply_pi(prm64, u, ff)
+        b = g64.whv_apply_pi(prm64, torch.zeros_like(ff), ff)
+        assert float((r - u).norm() / b.norm()) < 2e-9
+
+
+def test_batched_residual_precision_must_agree():
+    s = torch.cuda.Stream()
+    g1 = whv.Grid((33, 33), precision=whv.WHV_FP32_STEP, stream=s)
+    g2 = whv.Grid((33, 33), precision=whv.WHV_FP32_STEP, stream=s)
+    p1 = whv.make_params(8.0, method="cg", tol=1e-6, refine_fp64=True, residual_df64=True)
+    p2 = whv.make_params(8.0, method="cg", tol=1e-6, refine_fp64=True, residual_df64=False)
+    f = dev(np.ones(g1.N))
+    with pytest.raises(whv.WhvError):
+        whv.whv_solve_batched([g1, g2], [p1, p2], [f, f])

@@ -406,8 +406,11 @@ def run_workload(args):
     if cons:
         setup["operator"] = "conservative div(c^2 grad), second order, Euclidean inner products"
     setup["setup_s"] = time.perf_counter() - t0
-    if w.dim == 2:
-        setup["steps_per_sweep"] = g.whv_autotune(prm)
+    if args.steps_per_sweep:
+        g.whv_set_steps_per_sweep(args.steps_per_sweep)
+        setup["steps_per_sweep"] = args.steps_per_sweep
+    elif w.dim >= 2:
+        setup["steps_per_sweep"] = g.whv_autotune(prm)   # 2-D: blocked k; 3-D: one or two steps per launch
     f = dev(I.forcing_for(w))
     u = torch.zeros_like(f)
     res = {}

@@ -369,17 +369,26 @@ __global__ void __launch_bounds__(k3TX * k3TY) k_step3d2(const float* __restrict
                                                      const double* __restrict__ mw, double* __restrict__ out,
                                                      int nx, int ny, int nz, int zc, StepCoef<float> cf, float w2,
                                                      double* partials, unsigned* counter, double* scal_out) {
-  __shared__ float P[k3TY + 2][k3TX + 2];   // W^n(z) on R1 and its ring
+  __shared__ float P[k3TY + 2][k3TX + 2];   // W^n(z) on R1 and its ring (corners unused)
   __shared__ float Q[2][k3TY][k3TX];        // W^{n+1} on R1, planes z - 1 and z
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = tx + k3TX * ty;
   const int xb = blockIdx.x * (k3TX - 2) - 1, yb = blockIdx.y * (k3TY - 2) - 1;   // R1 origin
   const int x = xb + tx, y = yb + ty;
   const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
-  const bool inxy = x >= 0 && x < nx && y >= 0 && y < ny;
+  const bool xin = x >= 0 && x < nx, yin = y >= 0 && y < ny;
+  const bool inxy = xin && yin;
   const bool tile = inxy && tx >= 1 && tx < k3TX - 1 && ty >= 1 && ty < k3TY - 1;
   const int64_t plane = (int64_t)nx * ny;
-  const int64_t col = (int64_t)x + (int64_t)nx * y;
+  // the ring node this thread stages, if any: the row above (ty = 0) / below (ty = last) its
+  // column, the column left (tx = 0) / right (tx = last) of its row; -1: none or outside
+  int64_t ringv = -1, ringh = -1;
+  if (ty == 0 && xin && yb - 1 >= 0) ringv = x + (int64_t)nx * (yb - 1);
+  if (ty == k3TY - 1 && xin && yb + k3TY < ny) ringv = x + (int64_t)nx * (yb + k3TY);
+  if (tx == 0 && yin && xb - 1 >= 0) ringh = (xb - 1) + (int64_t)nx * y;
+  if (tx == k3TX - 1 && yin && xb + k3TX < nx) ringh = (xb + k3TX) + (int64_t)nx * y;
+  const int pvy = ty == 0 ? 0 : k3TY + 1, phx = tx == 0 ? 0 : k3TX + 1;
+  const bool hasv = ty == 0 || ty == k3TY - 1, hash = tx == 0 || tx == k3TX - 1;
+  const int64_t col = inxy ? (int64_t)x + (int64_t)nx * y : 0;
   auto ldc = [&](int z) { return (inxy && z >= 0 && z < nz) ? __ldg(gc + col + plane * z) : 0.0f; };
   float cm = ldc(z0 - 2), c0 = ldc(z0 - 1), cp = ldc(z0);   // W^n at z - 1, z, z + 1 for z = z0 - 1
   float q2 = 0.0f, q1 = 0.0f;   // W^{n+1} of this column at z - 2, z - 1
@@ -388,15 +397,13 @@ __global__ void __launch_bounds__(k3TX * k3TY) k_step3d2(const float* __restrict
   int buf = 0;
   for (int z = z0 - 1; z <= z1; ++z) {
     const bool zin = z >= 0 && z < nz;
-    for (int i = tid; i < (k3TX + 2) * (k3TY + 2); i += k3TX * k3TY) {
-      const int px = i % (k3TX + 2), py = i / (k3TX + 2);
-      const int gx = xb - 1 + px, gy = yb - 1 + py;
-      P[py][px] = (zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny)
-                      ? __ldg(gc + gx + (int64_t)nx * gy + plane * z) : 0.0f;
-    }
+    const int64_t zo = plane * z;
+    P[ty + 1][tx + 1] = c0;
+    if (hasv) P[pvy][tx + 1] = (zin && ringv >= 0) ? __ldg(gc + ringv + zo) : 0.0f;
+    if (hash) P[ty + 1][phx] = (zin && ringh >= 0) ? __ldg(gc + ringh + zo) : 0.0f;
     const float cpp = ldc(z + 2);
-    const float wpz = (inxy && zin) ? __ldg(gp + col + plane * z) : 0.0f;
-    const float accz = (tile && zin) ? acc[col + plane * z] : 0.0f;
+    const float wpz = (inxy && zin) ? __ldg(gp + col + zo) : 0.0f;
+    const float accz = (tile && zin) ? acc[col + zo] : 0.0f;
     __syncthreads();
     // step A: W^{n+1}(z) on R1
     float a1 = 0.0f;
@@ -418,7 +425,7 @@ __global__ void __launch_bounds__(k3TX * k3TY) k_step3d2(const float* __restrict
       u = fmaf(cf.a[1], R[ty - 1][tx] + R[ty + 1][tx], u);
       u = fmaf(cf.a[2], q2 + a1, u);
       const float a = fmaf(w2, u, accA);
-      const int64_t idx = col + plane * (z - 1);
+      const int64_t idx = col + zo - plane;
       if (KIND == K_STEP) {
         op[idx] = q1;
         oc[idx] = u;
@@ -569,14 +576,6 @@ static whv_status launch_solve_df(whv_grid g, const TimeGridH& tg, const double*
   else
     k_first_df<DIM, VARC, FORCE, true><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, g->c2, f, nx, ny, nz, cf);
   WHV_CUDA(g, cudaGetLastError());
-  if constexpr (DIM == 2 && !VARC) {   // blocked double-float sweeps unless one step per launch is set
-    if (g->kblock != 1) {
-      int nl = 0;
-      whv_status s = blocked_steps_2d_df<FORCE>(g, tg, v, f, out, epi, &nl, bufs, accbuf);
-      *nlaunch = 1 + nl;
-      return s;
-    }
-  }
   *nlaunch = tg.nt;
   dfl* wprev = b0;
   dfl* wcur = b1;
@@ -715,7 +714,7 @@ static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v,
     }
   }
   if constexpr (DIM == 3 && ORDER == 2 && !VARC && !FORCE && sizeof(T) == 4) {
-    if (kb > 1) {
+    if (g->kblock >= 2) {   // two steps per launch when set (or chosen by the autotuner)
       int nl = 0;
       whv_status s = two_step_3d(g, tg, v, out, epi, &nl, bufs, accbuf);
       *nlaunch += nl;

@@ -239,7 +239,6 @@ void blocked_init() {
   if (done) return;
   done = true;
   small_init();
-  blocked_df_init();
   persist_init();
   set_attrs<float, 2, false>(); set_attrs<float, 2, true>(); set_attrs<float, 4, false>(); set_attrs<float, 4, true>();
   set_attrs<double, 2, false>(); set_attrs<double, 2, true>(); set_attrs<double, 4, false>(); set_attrs<double, 4, true>();

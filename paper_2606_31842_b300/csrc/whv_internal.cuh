@@ -200,11 +200,7 @@ template <typename T, int ORDER, bool VARC>
 whv_status blocked_steps_2d(whv_grid g, const TimeGridH& tg, const double* v, double* out, int epi,
                             int k_want, int* launches, void* const* bufs, void* acc);
 void blocked_init();
-// double-float blocked sweeps (stencil_blocked_df.cu): 2-D, second order, c = 1
-template <bool FORCE>
-whv_status blocked_steps_2d_df(whv_grid g, const TimeGridH& tg, const double* v, const double* f, double* out,
-                               int epi, int* launches, void* const* bufs, void* accbuf);
-void blocked_df_init();
+
 // persistent 2-D wave solve (stencil_blocked.cu): one cooperative launch, tiles resident in
 // registers, halo exchange through the stepping buffers every k steps
 bool persist_fits(whv_grid g, int k, int prec);

@@ -480,32 +480,6 @@ def test_residual_correction_in_double_float(npts, speed, omega):
     assert relmax(out[True], out[False]) < 1e-7
 
 
-@pytest.mark.parametrize("npts,omega", [((129, 121), 24.0), ((200, 77), 21.0)])
-def test_double_float_blocked_sweeps_match_single_steps(npts, omega):
-    """The double-float residual wave solves in blocked sweeps (default steps per sweep: b with the
-    forcing, A x with the operator epilogue, ragged last sweep) and one step per launch
-    (steps per sweep 1): both corrections meet tol = 1e-9 against the FP64-checked residual and
-    agree with each other and with the direct solution."""
-    og = O.Grid(npts)
-    tg = WH.time_grid_for(og, omega)
-    f = I.gaussian(npts, [0.4, 0.6], 1.0 / omega, omega ** 2)
-    U = IND.helmholtz_direct(npts, tg.omega_eff, f)
-    out = {}
-    for k in (0, 1):
-        g = whv.Grid(npts, precision=whv.WHV_FP32_STEP)
-        if k:
-            g.whv_set_steps_per_sweep(k)
-        prm = whv.make_params(omega, method="cg", tol=1e-9, maxit=6000, true_residual=True, refine_fp64=True,
-                              residual_df64=True)
-        g.whv_set_deflation_basis(prm, 12, whv.WHV_BASIS_CLOSED_FORM)
-        u, info = g.whv_solve(prm, dev(f))
-        assert info["status"] == "OK", info
-        assert info["true_rel_residual"] < 2e-9
-        assert relmax(host(u), U) < 1e-6
-        out[k] = host(u)
-    assert relmax(out[0], out[1]) < 1e-7
-
-
 def test_solve_many_equals_single_solves():
     """Several right-hand sides on one grid: each column equals its own whv_solve, and the
     direct solution."""

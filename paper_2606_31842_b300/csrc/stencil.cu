@@ -369,8 +369,11 @@ __global__ void __launch_bounds__(k3TX * k3TY) k_step3d2(const float* __restrict
                                                      const double* __restrict__ mw, double* __restrict__ out,
                                                      int nx, int ny, int nz, int zc, StepCoef<float> cf, float w2,
                                                      double* partials, unsigned* counter, double* scal_out) {
-  __shared__ float P[k3TY + 2][k3TX + 2];   // W^n(z) on R1 and its ring (corners unused)
-  __shared__ float Q[2][k3TY][k3TX];        // W^{n+1} on R1, planes z - 1 and z
+  // Double-buffered stages, so that one barrier per plane suffices: at iteration z the CTA writes
+  // P[z & 1] (W^n(z) with its ring; corners unused) and Q[z & 1] (W^{n+1}(z) on R1), step A reads
+  // P[z & 1] after the barrier, step B reads Q[(z - 1) & 1], written before it.
+  __shared__ float P[2][k3TY + 2][k3TX + 2];
+  __shared__ float Q[2][k3TY][k3TX];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int xb = blockIdx.x * (k3TX - 2) - 1, yb = blockIdx.y * (k3TY - 2) - 1;   // R1 origin
   const int x = xb + tx, y = yb + ty;
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(k3TX * k3TY) k_step3d2(const float* __restrict
   const bool tile = inxy && tx >= 1 && tx < k3TX - 1 && ty >= 1 && ty < k3TY - 1;
   const int64_t plane = (int64_t)nx * ny;
   // the ring node this thread stages, if any: the row above (ty = 0) / below (ty = last) its
-  // column, the column left (tx = 0) / right (tx = last) of its row; -1: none or outside
+  // column, the column left (tx = 0) / right (tx = last) of its row
   int64_t ringv = -1, ringh = -1;
   if (ty == 0 && xin && yb - 1 >= 0) ringv = x + (int64_t)nx * (yb - 1);
   if (ty == k3TY - 1 && xin && yb + k3TY < ny) ringv = x + (int64_t)nx * (yb + k3TY);
@@ -394,32 +397,33 @@ __global__ void __launch_bounds__(k3TX * k3TY) k_step3d2(const float* __restrict
   float q2 = 0.0f, q1 = 0.0f;   // W^{n+1} of this column at z - 2, z - 1
   float accA = 0.0f;            // acc(z - 1) after step n + 1
   double part = 0.0;
-  int buf = 0;
-  for (int z = z0 - 1; z <= z1; ++z) {
+  // running pointers of plane z (valid only where dereferenced: z in range)
+  int64_t zo = plane * (z0 - 1);
+  for (int z = z0 - 1; z <= z1; ++z, zo += plane) {
+    const int b = z & 1;
     const bool zin = z >= 0 && z < nz;
-    const int64_t zo = plane * z;
-    P[ty + 1][tx + 1] = c0;
-    if (hasv) P[pvy][tx + 1] = (zin && ringv >= 0) ? __ldg(gc + ringv + zo) : 0.0f;
-    if (hash) P[ty + 1][phx] = (zin && ringh >= 0) ? __ldg(gc + ringh + zo) : 0.0f;
-    const float cpp = ldc(z + 2);
-    const float wpz = (inxy && zin) ? __ldg(gp + col + zo) : 0.0f;
+    P[b][ty + 1][tx + 1] = c0;
+    if (hasv) P[b][pvy][tx + 1] = (zin && ringv >= 0) ? __ldg(gc + ringv + zo) : 0.0f;
+    if (hash) P[b][ty + 1][phx] = (zin && ringh >= 0) ? __ldg(gc + ringh + zo) : 0.0f;
+    const bool act = inxy && zin;
+    const float cpp = (inxy && z + 2 < nz) ? __ldg(gc + col + zo + 2 * plane) : 0.0f;
+    const float wpz = act ? __ldg(gp + col + zo) : 0.0f;
     const float accz = (tile && zin) ? acc[col + zo] : 0.0f;
     __syncthreads();
     // step A: W^{n+1}(z) on R1
     float a1 = 0.0f;
-    if (inxy && zin) {
+    if (act) {
       float u = fmaf(cf.b, c0, -wpz);
-      u = fmaf(cf.a[0], P[ty + 1][tx] + P[ty + 1][tx + 2], u);
-      u = fmaf(cf.a[1], P[ty][tx + 1] + P[ty + 2][tx + 1], u);
+      u = fmaf(cf.a[0], P[b][ty + 1][tx] + P[b][ty + 1][tx + 2], u);
+      u = fmaf(cf.a[1], P[b][ty][tx + 1] + P[b][ty + 2][tx + 1], u);
       u = fmaf(cf.a[2], cm + cp, u);
       a1 = u;
     }
-    Q[buf][ty][tx] = a1;
+    Q[b][ty][tx] = a1;
     const float accN = fmaf(cf.w1, a1, accz);
-    __syncthreads();
-    // step B: W^{n+2}(z - 1) on the tile
-    if (z - 1 >= z0 && tile) {
-      const float(*R)[k3TX] = Q[buf ^ 1];
+    // step B: W^{n+2}(z - 1) on the tile, from Q[(z - 1) & 1] (written before the barrier)
+    if (z > z0 && tile) {
+      const float(*R)[k3TX] = Q[b ^ 1];
       float u = fmaf(cf.b, q1, -cm);
       u = fmaf(cf.a[0], R[ty][tx - 1] + R[ty][tx + 1], u);
       u = fmaf(cf.a[1], R[ty - 1][tx] + R[ty + 1][tx], u);
@@ -445,7 +449,6 @@ __global__ void __launch_bounds__(k3TX * k3TY) k_step3d2(const float* __restrict
     cm = c0;
     c0 = cp;
     cp = cpp;
-    buf ^= 1;
   }
   if (KIND == K_LAST_AV) {
     part = block_sum(part);

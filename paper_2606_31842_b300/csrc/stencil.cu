@@ -372,8 +372,7 @@ __global__ void __launch_bounds__(k3TX * k3TY) k_step3d2(const float* __restrict
                                                      double* partials, unsigned* counter, double* scal_out) {
   // Double-buffered stages, so that one barrier per plane suffices: at iteration z the CTA writes
   // P[z & 1] (W^n(z) with its ring; corners unused) and Q[z & 1] (W^{n+1}(z) on R1), step A reads
-  // P[z & 1] after the barrier, step B reads Q[(z - 1) & 1], written before it.  The plane loop is
-  // unrolled by two so that the stage of each half is fixed.
+  // P[z & 1] after the barrier, step B reads Q[(z - 1) & 1], written before it.
   __shared__ float P[2][k3TY + 2][k3TX + 2];
   __shared__ float Q[2][k3TY][k3TX];
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -393,64 +392,56 @@ __global__ void __launch_bounds__(k3TX * k3TY) k_step3d2(const float* __restrict
   if (tx == k3TX - 1 && yin && xb + k3TX < nx) ringh = (xb + k3TX) + (int64_t)nx * y;
   const int pvy = ty == 0 ? 0 : k3TY + 1, phx = tx == 0 ? 0 : k3TX + 1;
   const bool hasv = ty == 0 || ty == k3TY - 1, hash = tx == 0 || tx == k3TX - 1;
-  const bool okv = ringv >= 0, okh = ringh >= 0;
   const int64_t col = inxy ? (int64_t)x + (int64_t)nx * y : 0;
   auto ldc = [&](int z) { return (inxy && z >= 0 && z < nz) ? __ldg(gc + col + plane * z) : 0.0f; };
   float cm = ldc(z0 - 2), c0 = ldc(z0 - 1), cp = ldc(z0);   // W^n at z - 1, z, z + 1 for z = z0 - 1
   float q2 = 0.0f, q1 = 0.0f;   // W^{n+1} of this column at z - 2, z - 1
   float accA = 0.0f;            // acc(z - 1) after step n + 1
   double part = 0.0;
-  // element offsets of plane z (dereferenced only where z is in range)
-  const int64_t zs = plane * (z0 - 1);
-  const float* pv = gc + (okv ? ringv : 0) + zs;
-  const float* ph = gc + (okh ? ringh : 0) + zs;
-  const float* pc2 = gc + col + zs + 2 * plane;
-  const float* ppz = gp + col + zs;
-  float* pac = acc + col + zs;
-  const int64_t so = col + zs - plane;   // output offset of plane z - 1
-  float* pop = op + so;
-  float* poc = oc + so;
-  double* pout = out + so;
-  const double* pvin = v + so;
-  const double* pmw = mw ? mw + so : nullptr;
-  auto plane_step = [&](int z, auto Bc) {
-    constexpr int B = decltype(Bc)::value;
+  // running pointers of plane z (valid only where dereferenced: z in range)
+  int64_t zo = plane * (z0 - 1);
+  for (int z = z0 - 1; z <= z1; ++z, zo += plane) {
+    const int b = z & 1;
     const bool zin = z >= 0 && z < nz;
-    P[B][ty + 1][tx + 1] = c0;
-    if (hasv) P[B][pvy][tx + 1] = (zin && okv) ? __ldg(pv) : 0.0f;
-    if (hash) P[B][ty + 1][phx] = (zin && okh) ? __ldg(ph) : 0.0f;
+    P[b][ty + 1][tx + 1] = c0;
+    if (hasv) P[b][pvy][tx + 1] = (zin && ringv >= 0) ? __ldg(gc + ringv + zo) : 0.0f;
+    if (hash) P[b][ty + 1][phx] = (zin && ringh >= 0) ? __ldg(gc + ringh + zo) : 0.0f;
     const bool act = inxy && zin;
-    const float cpp = (inxy && z + 2 < nz) ? __ldg(pc2) : 0.0f;
-    const float wpz = act ? __ldg(ppz) : 0.0f;
-    const float accz = (tile && zin) ? *pac : 0.0f;
+    const float cpp = (inxy && z + 2 < nz) ? __ldg(gc + col + zo + 2 * plane) : 0.0f;
+    const float wpz = act ? __ldg(gp + col + zo) : 0.0f;
+    const float accz = (tile && zin) ? acc[col + zo] : 0.0f;
     __syncthreads();
+    // step A: W^{n+1}(z) on R1
     float a1 = 0.0f;
-    if (act) {   // step A: W^{n+1}(z) on R1
+    if (act) {
       float u = fmaf(cf.b, c0, -wpz);
-      u = fmaf(cf.a[0], P[B][ty + 1][tx] + P[B][ty + 1][tx + 2], u);
-      u = fmaf(cf.a[1], P[B][ty][tx + 1] + P[B][ty + 2][tx + 1], u);
+      u = fmaf(cf.a[0], P[b][ty + 1][tx] + P[b][ty + 1][tx + 2], u);
+      u = fmaf(cf.a[1], P[b][ty][tx + 1] + P[b][ty + 2][tx + 1], u);
       u = fmaf(cf.a[2], cm + cp, u);
       a1 = u;
     }
-    Q[B][ty][tx] = a1;
+    Q[b][ty][tx] = a1;
     const float accN = fmaf(cf.w1, a1, accz);
-    if (z > z0 && tile) {   // step B: W^{n+2}(z - 1) on the tile, from Q[B ^ 1]
+    // step B: W^{n+2}(z - 1) on the tile, from Q[(z - 1) & 1] (written before the barrier)
+    if (z > z0 && tile) {
+      const float(*R)[k3TX] = Q[b ^ 1];
       float u = fmaf(cf.b, q1, -cm);
-      u = fmaf(cf.a[0], Q[B ^ 1][ty][tx - 1] + Q[B ^ 1][ty][tx + 1], u);
-      u = fmaf(cf.a[1], Q[B ^ 1][ty - 1][tx] + Q[B ^ 1][ty + 1][tx], u);
+      u = fmaf(cf.a[0], R[ty][tx - 1] + R[ty][tx + 1], u);
+      u = fmaf(cf.a[1], R[ty - 1][tx] + R[ty + 1][tx], u);
       u = fmaf(cf.a[2], q2 + a1, u);
       const float a = fmaf(w2, u, accA);
+      const int64_t idx = col + zo - plane;
       if (KIND == K_STEP) {
-        *pop = q1;
-        *poc = u;
-        pac[-plane] = a;
+        op[idx] = q1;
+        oc[idx] = u;
+        acc[idx] = a;
       } else if (KIND == K_LAST_OUT) {
-        *pout = (double)a;
+        out[idx] = (double)a;
       } else {
-        const double vi = *pvin;
+        const double vi = v[idx];
         const double o = vi - (double)a;
-        *pout = o;
-        part = fma(pmw ? vi * *pmw : vi, o, part);
+        out[idx] = o;
+        part = fma(mw ? vi * mw[idx] : vi, o, part);
       }
     }
     q2 = q1;
@@ -459,21 +450,7 @@ __global__ void __launch_bounds__(k3TX * k3TY) k_step3d2(const float* __restrict
     cm = c0;
     c0 = cp;
     cp = cpp;
-    pv += plane; ph += plane; pc2 += plane; ppz += plane; pac += plane;
-    pop += plane; poc += plane; pout += plane; pvin += plane;
-    if (pmw) pmw += plane;
-  };
-  // planes z0 - 1 .. z1: pairs with the stage parity of z fixed at compile time
-  int z = z0 - 1;
-  if (z & 1) {   // z0 - 1 odd: one plane with stage 1 first
-    plane_step(z, std::integral_constant<int, 1>());
-    ++z;
   }
-  for (; z + 1 <= z1; z += 2) {
-    plane_step(z, std::integral_constant<int, 0>());
-    plane_step(z + 1, std::integral_constant<int, 1>());
-  }
-  if (z <= z1) plane_step(z, std::integral_constant<int, 0>());
   if (KIND == K_LAST_AV) {
     part = block_sum(part);
     double total;

@@ -191,6 +191,7 @@ def run_reference(args):
 KERNEL_SOURCES = {
     "k_block2d": ("stencil_blocked.cu", "quad2d.cuh", "whv_device.cuh"),
     "k_step3d": ("stencil.cu", "stencil_ops.cuh", "whv_device.cuh"),
+    "k_step3d2": ("stencil.cu", "stencil_ops.cuh", "whv_device.cuh"),
 }
 
 
@@ -642,6 +643,7 @@ def main():
                    "bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s", "frac": ach32 / peak,
                    "bytes_per_lup": 20, "glups": g3.N / t32 / 1e9, "step_us": t32 * 1e6,
                    "own_bytes_per_lup": 12, "own_frac": 12 * g3.N / t32 / 1e9 / peak,
+                   "traffic": traffic_for("k_step3d2", "fp32"), "traffic_unit": "DRAM bytes per launch (2 steps)",
                    "note": "achieved/frac count the 20 B per LUP of single-step streaming (equivalent "
                            "bandwidth); own_frac counts the 12 B per LUP the two-step kernel must move",
                    "single_step": {"kernel": "k_step3d (one step per launch)", "achieved": ach31,

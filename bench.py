@@ -378,8 +378,10 @@ def run_workload(args):
         else:
             g.whv_set_speed(c2v)
     refine = prec == whv.WHV_FP32_STEP
+    dfres = refine and args.residual == "df64" and not cons   # the conservative operator corrects in FP64
     method = args.method or ("dcg" if name in ("c1", "c3") else "cg")
-    prm = whv.make_params(w.omega, method=method, tol=w.tol, maxit=20000, restart=30, refine_fp64=refine)
+    prm = whv.make_params(w.omega, method=method, tol=w.tol, maxit=20000, restart=30, refine_fp64=refine,
+                          residual_df64=dfres)
     t0 = time.perf_counter()
     if name == "c3" and args.eigs == "thick":
         theta, resid, st = g.whv_lanczos_restarted(prm, w.nd, 3 * w.nd + 4, max_restarts=40, tol=1e-6,
@@ -428,7 +430,9 @@ def run_workload(args):
                  "dtype": "f64" if prec == whv.WHV_FP64 else "f32", "krylov_dtype": "f64",
                  "config": dict({"workload": name, "grid": list(w.npts), "order": order, "omega": w.omega,
                                  "nd": w.nd, "tol": w.tol, "method": method.upper(),
-                                 "variable_speed": bool(w.speed), "nt": info["nt"]}, **setup),
+                                 "variable_speed": bool(w.speed), "nt": info["nt"],
+                                 "correction_residuals": ("df64" if dfres else "fp64") if refine else None},
+                            **setup),
                  "iterations": info["iterations"], "outer_iterations": info["outer_iterations"],
                  "wave_solves": info["wave_solves"], "glups_solve": lups / (ms * 1e-3) / 1e9,
                  "accuracy": {"true_rel_residual": ichk["true_rel_residual"]}})

@@ -92,7 +92,8 @@ enum {
                                  (Lanczos) eigenvectors.  Needs a Krylov method (DCG, AGMRES and
                                  ABICGSTAB use the basis themselves: no modal step); allocates 3 (FP64
                                  grids) or 8 (FP32 grids) more N-vectors of FP64 on first use.       */
-  WHV_RESIDUAL_DF64 = 4       /* with WHV_REFINE_FP64 on second-order grids (c^2 Delta_h): the b and
+  WHV_RESIDUAL_DF64 = 4       /* with WHV_REFINE_FP64 on grids with the operator c^2 Delta_h (order 2
+                                 or 4; batched solves: 2-D, order 2, c = 1, else FP64): the b and
                                  residual wave solves of the correction run in double-float
                                  arithmetic -- each value a pair of FP32 numbers, ~48-bit significand,
                                  error-free two-sum / two-product on the FP32 pipes -- instead of FP64

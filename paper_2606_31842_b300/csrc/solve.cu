@@ -834,7 +834,7 @@ static whv_status solve_impl(whv_grid g, const whv_params* p, const double* f, i
   const bool devd = has_basis && method != WHV_DCG && !augmented(method);
   const int64_t N = g->N;
   SolveCtx c{g, tg, has_basis && (B.flags & WHV_BASIS_REDEFLATE) != 0 && !augmented(method)};
-  if (refine && (p->flags & WHV_RESIDUAL_DF64) && g->order == 2 && !g->cons) c.res_prec = kPrecDF64;
+  if (refine && (p->flags & WHV_RESIDUAL_DF64) && !g->cons) c.res_prec = kPrecDF64;
   double* b = g->t;  // b of the iterated system
 
   // ---- forcing (Algorithm 2: deflate the forcing)

@@ -172,7 +172,10 @@ __global__ void __launch_bounds__(256) k_step_cons(const T* __restrict__ wc, T* 
 // Double-float wave solves (second order): the residual wave solves of the FP64 residual
 // correction with WHV_RESIDUAL_DF64 -- same recurrence, filter and epilogues as k_first / k_step,
 // each value the pair hi + lo of FP32 numbers (df64.cuh), stored as 8-byte pairs.
-template <int DIM, typename LD>
+// second order: ih2 ((W_- + W_+) - 2 W) per axis; fourth order (ih2 = 1 / 12 h^2):
+// ih2 ((16 (W_-1 + W_+1) - (W_-2 + W_+2)) - 30 W) with the odd-reflection closure of the FP32 / FP64
+// kernels (the value two nodes outside the first or last interior node is minus that node)
+template <int DIM, int ORDER, typename LD>
 __device__ __forceinline__ dfl lap_df(LD load, int x, int y, int z, int nx, int ny, int nz, int64_t idx,
                                       const DfCoef& cf, dfl c) {
   const dfl c2x = {2.0f * c.hi, 2.0f * c.lo};   // exact
@@ -183,12 +186,21 @@ __device__ __forceinline__ dfl lap_df(LD load, int x, int y, int z, int nx, int 
     const int n = m == 0 ? nx : (m == 1 ? ny : nz);
     const int64_t st = m == 0 ? 1 : (m == 1 ? (int64_t)nx : (int64_t)nx * ny);
     const dfl s = df_add(i > 0 ? load(idx - st) : df_zero(), i < n - 1 ? load(idx + st) : df_zero());
-    L = df_add(L, df_mul(cf.ih2[m], df_sub(s, c2x)));
+    dfl t;
+    if (ORDER == 2) {
+      t = df_sub(s, c2x);
+    } else {
+      const dfl m2 = i > 1 ? load(idx - 2 * st) : (i == 1 ? df_zero() : df_neg(c));
+      const dfl p2 = i < n - 2 ? load(idx + 2 * st) : (i == n - 2 ? df_zero() : df_neg(c));
+      t = df_sub(dfl{16.0f * s.hi, 16.0f * s.lo}, df_add(m2, p2));   // 16 s exact
+      t = df_sub(t, df_mul(dfl{30.0f, 0.0f}, c));
+    }
+    L = df_add(L, df_mul(cf.ih2[m], t));
   }
   return L;
 }
 
-template <int DIM, bool VARC, bool FORCE, bool ZERO_V>
+template <int DIM, int ORDER, bool VARC, bool FORCE, bool ZERO_V>
 __global__ void __launch_bounds__(256) k_first_df(const double* __restrict__ v, dfl* __restrict__ w0,
                                                   dfl* __restrict__ w1, dfl* __restrict__ acc,
                                                   const double* __restrict__ c2, const double* __restrict__ f,
@@ -201,7 +213,7 @@ __global__ void __launch_bounds__(256) k_first_df(const double* __restrict__ v, 
   dfl W0 = df_zero(), L = df_zero();
   if (!ZERO_V) {
     W0 = df_from(v[idx]);
-    L = lap_df<DIM>([&](int64_t j) { return df_from(__ldg(v + j)); }, x, y, z, nx, ny, nz, idx, cf, W0);
+    L = lap_df<DIM, ORDER>([&](int64_t j) { return df_from(__ldg(v + j)); }, x, y, z, nx, ny, nz, idx, cf, W0);
     if (VARC) L = df_mul(L, df_from(c2[idx]));
   }
   if (FORCE) L = df_sub(L, df_from(f[idx]));   // cos(0) = 1
@@ -211,7 +223,7 @@ __global__ void __launch_bounds__(256) k_first_df(const double* __restrict__ v, 
   acc[idx] = df_add(df_mul(cf.w0, W0), df_mul(cf.w1, W1));
 }
 
-template <int DIM, bool VARC, bool FORCE, int KIND>
+template <int DIM, int ORDER, bool VARC, bool FORCE, int KIND>
 __global__ void __launch_bounds__(256) k_step_df(const dfl* __restrict__ wc, dfl* __restrict__ wp,
                                                  dfl* __restrict__ acc, const double* __restrict__ c2,
                                                  const double* __restrict__ f, const double* __restrict__ v,
@@ -228,7 +240,7 @@ __global__ void __launch_bounds__(256) k_step_df(const dfl* __restrict__ wc, dfl
     const dfl c = wc[idx];
     auto load = [&](int64_t j) { return wc[j]; };
     dfl wn;
-    if (!VARC) {   // sum_m a_m (W_{+m} + W_{-m}) + b W^n - W^{n-1}
+    if (!VARC && ORDER == 2) {   // sum_m a_m (W_{+m} + W_{-m}) + b W^n - W^{n-1}
       wn = df_sub(df_mul(cf.b, c), wp[idx]);
 #pragma unroll
       for (int m = 0; m < DIM; ++m) {
@@ -240,8 +252,8 @@ __global__ void __launch_bounds__(256) k_step_df(const dfl* __restrict__ wc, dfl
       }
       if (FORCE) wn = df_sub(wn, df_mul(cf.fph, df_from(f[idx])));   // fph = dt^2 cos(omega_hat t^n)
     } else {
-      dfl L = lap_df<DIM>(load, x, y, z, nx, ny, nz, idx, cf, c);
-      L = df_mul(L, df_from(c2[idx]));
+      dfl L = lap_df<DIM, ORDER>(load, x, y, z, nx, ny, nz, idx, cf, c);
+      if (VARC) L = df_mul(L, df_from(c2[idx]));
       if (FORCE) L = df_sub(L, df_mul(cf.fph, df_from(f[idx])));   // fph = cos(omega_hat t^n)
       const dfl t = df_sub(dfl{2.0f * c.hi, 2.0f * c.lo}, wp[idx]);
       wn = df_add(t, df_mul(cf.dt2, L));
@@ -551,7 +563,7 @@ static whv_status launch_solve_cons(whv_grid g, const TimeGridH& tg, const doubl
   return WHV_OK;
 }
 
-template <int DIM, bool VARC, bool FORCE>
+template <int DIM, int ORDER, bool VARC, bool FORCE>
 static whv_status launch_solve_df(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
                                   double* out, int epi, int* nlaunch, void* const* bufs, void* accbuf) {
   const LaunchShape ls = shape_of(g);
@@ -563,7 +575,7 @@ static whv_status launch_solve_df(whv_grid g, const TimeGridH& tg, const double*
   double asum = 0.0;
   for (int m = 0; m < 3; ++m) {
     const double h2 = g->h[m] * g->h[m];
-    cf.ih2[m] = df_from(1.0 / h2);
+    cf.ih2[m] = df_from(ORDER == 2 ? 1.0 / h2 : 1.0 / (12.0 * h2));
     const double am = m < g->dim ? tg.dt * tg.dt / h2 : 0.0;
     cf.a[m] = df_from(am);
     asum += am;
@@ -576,9 +588,9 @@ static whv_status launch_solve_df(whv_grid g, const TimeGridH& tg, const double*
   dim3 fgrid = ls.grid;
   if (DIM == 3) fgrid.z = nz;
   if (v)
-    k_first_df<DIM, VARC, FORCE, false><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, g->c2, f, nx, ny, nz, cf);
+    k_first_df<DIM, ORDER, VARC, FORCE, false><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, g->c2, f, nx, ny, nz, cf);
   else
-    k_first_df<DIM, VARC, FORCE, true><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, g->c2, f, nx, ny, nz, cf);
+    k_first_df<DIM, ORDER, VARC, FORCE, true><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, g->c2, f, nx, ny, nz, cf);
   WHV_CUDA(g, cudaGetLastError());
   *nlaunch = tg.nt;
   dfl* wprev = b0;
@@ -586,19 +598,20 @@ static whv_status launch_solve_df(whv_grid g, const TimeGridH& tg, const double*
   double* part = chan(g, CH_STEP);
   unsigned* cnt = g->counters + CH_STEP;
   for (int n = 1; n < tg.nt; ++n) {
-    cf.fph = df_from(VARC ? tg.phase[n] : tg.dt * tg.dt * tg.phase[n]);
+    // the c = 1 second-order update takes dt^2 cos(omega_hat t^n) whole, the general one cos(...)
+    cf.fph = df_from(VARC || ORDER == 4 ? tg.phase[n] : tg.dt * tg.dt * tg.phase[n]);
     cf.w1 = df_from(tg.weight[n + 1]);
     const bool last = (n == tg.nt - 1);
     if (!last)
-      k_step_df<DIM, VARC, FORCE, K_STEP><<<fgrid, ls.block, 0, g->stream>>>(wcur, wprev, acc, g->c2, f, nullptr,
+      k_step_df<DIM, ORDER, VARC, FORCE, K_STEP><<<fgrid, ls.block, 0, g->stream>>>(wcur, wprev, acc, g->c2, f, nullptr,
                                                                            nullptr, nullptr, nx, ny, nz, cf, nullptr,
                                                                            nullptr, nullptr);
     else if (epi == 0)
-      k_step_df<DIM, VARC, FORCE, K_LAST_OUT><<<fgrid, ls.block, 0, g->stream>>>(wcur, wprev, acc, g->c2, f, nullptr,
+      k_step_df<DIM, ORDER, VARC, FORCE, K_LAST_OUT><<<fgrid, ls.block, 0, g->stream>>>(wcur, wprev, acc, g->c2, f, nullptr,
                                                                                nullptr, out, nx, ny, nz, cf, nullptr,
                                                                                nullptr, nullptr);
     else
-      k_step_df<DIM, VARC, FORCE, K_LAST_AV><<<fgrid, ls.block, 0, g->stream>>>(wcur, wprev, acc, g->c2, f, v, g->mw,
+      k_step_df<DIM, ORDER, VARC, FORCE, K_LAST_AV><<<fgrid, ls.block, 0, g->stream>>>(wcur, wprev, acc, g->c2, f, v, g->mw,
                                                                               out, nx, ny, nz, cf, part, cnt,
                                                                               g->scal + S_PQ);
     WHV_CUDA(g, cudaGetLastError());
@@ -609,14 +622,21 @@ static whv_status launch_solve_df(whv_grid g, const TimeGridH& tg, const double*
   return WHV_OK;
 }
 
+template <int DIM, int ORDER>
+static whv_status dispatch_df_ord(whv_grid g, const TimeGridH& tg, const double* v, const double* f, double* out,
+                                  int epi, int* nl, void* const* bufs, void* acc) {
+  const bool varc = g->c2 != nullptr;
+  if (varc) return f ? launch_solve_df<DIM, ORDER, true, true>(g, tg, v, f, out, epi, nl, bufs, acc)
+                     : launch_solve_df<DIM, ORDER, true, false>(g, tg, v, f, out, epi, nl, bufs, acc);
+  return f ? launch_solve_df<DIM, ORDER, false, true>(g, tg, v, f, out, epi, nl, bufs, acc)
+           : launch_solve_df<DIM, ORDER, false, false>(g, tg, v, f, out, epi, nl, bufs, acc);
+}
+
 template <int DIM>
 static whv_status dispatch_df_dim(whv_grid g, const TimeGridH& tg, const double* v, const double* f, double* out,
                                   int epi, int* nl, void* const* bufs, void* acc) {
-  const bool varc = g->c2 != nullptr;
-  if (varc) return f ? launch_solve_df<DIM, true, true>(g, tg, v, f, out, epi, nl, bufs, acc)
-                     : launch_solve_df<DIM, true, false>(g, tg, v, f, out, epi, nl, bufs, acc);
-  return f ? launch_solve_df<DIM, false, true>(g, tg, v, f, out, epi, nl, bufs, acc)
-           : launch_solve_df<DIM, false, false>(g, tg, v, f, out, epi, nl, bufs, acc);
+  return g->order == 2 ? dispatch_df_ord<DIM, 2>(g, tg, v, f, out, epi, nl, bufs, acc)
+                       : dispatch_df_ord<DIM, 4>(g, tg, v, f, out, epi, nl, bufs, acc);
 }
 
 constexpr int kZChunk2 = 32;   // planes per CTA of the two-step 3-D kernel
@@ -820,7 +840,8 @@ static whv_status launch_wave_solve(whv_grid g, const TimeGridH& tg, const doubl
   if ((int64_t)ls.grid.x * ls.grid.y * ls.grid.z > chan_cap(g, CH_STEP))
     return fail(g, WHV_ERR_INVALID, "grid too large for the fused reduction");
   if (prec < 0) prec = g->precision;
-  if (!g->cons && small_grid(g) && g->kblock == 0 && small_tables(g, tg) >= 0) {
+  // (the single-CTA kernel steps in FP32 or FP64 only: double-float solves take the general path)
+  if (!g->cons && prec != kPrecDF64 && small_grid(g) && g->kblock == 0 && small_tables(g, tg) >= 0) {
     *nl = 1;
     return small_wave_solve(g, tg, v, f, out, epi, prec);
   }
@@ -835,8 +856,8 @@ static whv_status launch_wave_solve(whv_grid g, const TimeGridH& tg, const doubl
     return prec == WHV_FP64 ? dispatch<double>(g, tg, v, f, out, epi, nl, B)
                             : dispatch<float>(g, tg, v, f, out, epi, nl, B);
   }
-  if (prec == kPrecDF64) {   // double-float residual wave solves (second order, c^2 Delta_h)
-    if (g->order != 2 || g->cons) return fail(g, WHV_ERR_INVALID, "double-float stepping needs order 2");
+  if (prec == kPrecDF64) {   // double-float residual wave solves (c^2 Delta_h, order 2 or 4)
+    if (g->cons) return fail(g, WHV_ERR_INVALID, "double-float stepping needs the non-conservative operator");
     if (!g->acc64 && g->precision != WHV_FP64) return fail(g, WHV_ERR_INVALID, "FP64 buffers are not allocated");
     void* const* bufs = g->precision == WHV_FP64 ? g->wbuf : g->wbuf64;
     void* acc = g->precision == WHV_FP64 ? g->acc : g->acc64;

@@ -453,19 +453,23 @@ def test_persistent_barrier_failure_is_reported_and_recovers():
     assert relmax(host(u), ref) < 1e-12
 
 
-@pytest.mark.parametrize("npts,speed,omega", [((129, 121), None, 24.0), ((97, 89), "c3", 18.0), ((21, 19, 17), None, 8.0)])
-def test_residual_correction_in_double_float(npts, speed, omega):
-    """FP32 stepping with the residual wave solves in double-float arithmetic (pairs of FP32):
-    the FP64-checked true residual meets tol = 1e-9 and the solution is the direct one; the
-    result agrees with the FP64-residual form."""
+@pytest.mark.parametrize("npts,speed,omega,order", [
+    ((129, 121), None, 24.0, 2), ((97, 89), "c3", 18.0, 2), ((21, 19, 17), None, 8.0, 2),
+    ((129, 121), None, 24.0, 4), ((97, 89), "c3", 18.0, 4), ((17, 15, 14), None, 7.0, 4),
+    ((41, 37), None, 12.0, 2)])
+def test_residual_correction_in_double_float(npts, speed, omega, order):
+    """FP32 stepping with the residual wave solves in double-float arithmetic (pairs of FP32),
+    second- and fourth-order stencils (the latter with its odd-reflection closure): the
+    FP64-checked true residual meets tol = 1e-9 and the solution is the direct one; the result
+    agrees with the FP64-residual form."""
     c2 = None if speed is None else I.speed_squared(speed, npts, 3)
-    og = O.Grid(npts, c2=c2)
+    og = O.Grid(npts, order=order, c2=c2)
     tg = WH.time_grid_for(og, omega)
     f = I.gaussian(npts, [0.4, 0.6, 0.5][: len(npts)], 1.0 / omega, omega ** 2)
-    U = IND.helmholtz_direct(npts, tg.omega_eff, f, 2, c2)
+    U = IND.helmholtz_direct(npts, tg.omega_eff, f, order, c2)
     out = {}
     for df in (True, False):
-        g = whv.Grid(npts, precision=whv.WHV_FP32_STEP)
+        g = whv.Grid(npts, order=order, precision=whv.WHV_FP32_STEP)
         if c2 is not None:
             g.whv_set_speed(dev(c2))
         prm = whv.make_params(omega, method="cg", tol=1e-9, maxit=6000, true_residual=True, refine_fp64=True,

@@ -4,8 +4,14 @@
 //   two-sum (Knuth, TAOCP vol. 2):      s = a + b exactly as s + e, any a, b
 //   fast two-sum (Dekker 1971):         the same when |a| >= |b|
 //   exact product with an FMA:          a b = p + e, e = fma(a, b, -p)
-// with the renormalisations of the "accurate" double-word sum and product.  No expression here
-// has a multiply next to an add that the compiler could contract into an FMA and change.
+// The sum is Dekker's double-word addition (add2, 1971): a two-sum of the high parts, the low
+// parts added to its error term, one fast two-sum to renormalise (11 FP32 operations instead of
+// the 20 of the form that two-sums the low parts as well).  Its error is bounded relative to
+// |a| + |b| rather than to |a + b| -- about 2^-46 (|a| + |b|) -- so under cancellation it keeps
+// an absolute, not a relative, accuracy: enough for the wave solves, where every sum has
+// operands of the size of the field (W^n, W^{n-1}, the neighbours, the filter sum) and what
+// matters is the error against that size.  No expression here has a multiply next to an add
+// that the compiler could contract into an FMA and change.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -36,9 +42,7 @@ __device__ __forceinline__ dfl fast_two_sum(float a, float b) {
 }
 __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
   const dfl s = two_sum(a.hi, b.hi);
-  const dfl t = two_sum(a.lo, b.lo);
-  const dfl u = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-  return fast_two_sum(u.hi, __fadd_rn(u.lo, t.lo));
+  return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, a.lo), b.lo));
 }
 __device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
 __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {

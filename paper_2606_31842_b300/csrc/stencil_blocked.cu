@@ -72,6 +72,9 @@ __global__ void __launch_bounds__(kBlkThreads) k_block2d(const T* __restrict__ g
   T* S0 = reinterpret_cast<T*>(smem_raw);
   T* S1 = S0 + kReg * kReg;
   __shared__ T sw[kBlkMaxK];
+  // launched as a programmatic dependent of the previous sweep: wait for its results (returns at
+  // once when there is no such dependency)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   constexpr int R = ORDER == 2 ? 1 : 2;
   const int H = cf.k * R;
   const int TW = kReg - 2 * H;
@@ -252,9 +255,22 @@ static cudaError_t launch_block(whv_grid g, const T* gp, const T* gc, T* op, T* 
   const int R = ORDER == 2 ? 1 : 2;
   const int TW = kReg - 2 * cf.k * R;
   dim3 grid((g->n[0] + TW - 1) / TW, (g->n[1] + TW - 1) / TW, 1);
-  k_block2d<T, ORDER, VARC, KIND><<<grid, kBlkThreads, smem, g->stream>>>(
-      gp, gc, op, oc, acc, c2, v, g->mw, out, g->n[0], g->n[1], cf, partials, counter, scal_out);
-  return cudaGetLastError();
+  // programmatic dependent launch: the sweep may be scheduled as the previous kernel's CTAs exit;
+  // it waits (griddepcontrol.wait) for that kernel's completion before reading anything
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = grid;
+  lc.blockDim = dim3(kBlkThreads, 1, 1);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = g->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  const double* mw = g->mw;
+  const int nx = g->n[0], ny = g->n[1];
+  return cudaLaunchKernelEx(&lc, k_block2d<T, ORDER, VARC, KIND>, gp, gc, op, oc, acc, c2, v, mw, out, nx, ny, cf,
+                            partials, counter, scal_out);
 }
 
 // Steps n = 1 .. nt-1 of a 2-D f = 0 wave solve in sweeps of k steps; the first step (Taylor

@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -188,19 +189,38 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ GPU arm
+# the sources a recorded traffic figure depends on: whole files, or (file, kernel) for the text of
+# one kernel's definition in a file that holds others as well
 KERNEL_SOURCES = {
     "k_block2d": ("stencil_blocked.cu", "quad2d.cuh", "whv_device.cuh"),
-    "k_step3d": ("stencil.cu", "stencil_ops.cuh", "whv_device.cuh"),
-    "k_step3d2": ("stencil.cu", "stencil_ops.cuh", "whv_device.cuh"),
+    "k_step3d": (("stencil.cu", "k_step3d"), "stencil_ops.cuh", "whv_device.cuh"),
+    "k_step3d2": (("stencil.cu", "k_step3d2"), "stencil_ops.cuh", "whv_device.cuh"),
 }
+
+
+def _kernel_text(src, name):
+    """The definition of __global__ kernel `name` in `src`: from its declaration to the closing
+    brace of its body."""
+    m = re.search(r"__global__[^;{]*?\b" + re.escape(name) + r"\(", src)
+    if not m:
+        raise KeyError(name)
+    i = src.index("{", m.end())
+    depth = 0
+    for j in range(i, len(src)):
+        depth += {"{": 1, "}": -1}.get(src[j], 0)
+        if depth == 0:
+            return src[m.start(): j + 1]
+    raise ValueError(name)
 
 
 def kernel_source_hash(kernel):
     """Hash of the sources of one stepping kernel; a recorded DRAM traffic figure is only reported
     while the kernel is the one it was measured on."""
     h = hashlib.sha256()
-    for fn in KERNEL_SOURCES[kernel]:
-        h.update(open(os.path.join(ROOT, "paper_2606_31842_b300", "csrc", fn), "rb").read())
+    for item in KERNEL_SOURCES[kernel]:
+        fn, name = item if isinstance(item, tuple) else (item, None)
+        text = open(os.path.join(ROOT, "paper_2606_31842_b300", "csrc", fn)).read()
+        h.update((_kernel_text(text, name) if name else text).encode())
     return h.hexdigest()[:16]
 
 

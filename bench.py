@@ -213,13 +213,21 @@ def _kernel_text(src, name):
     raise ValueError(name)
 
 
+def _code_only(text):
+    """C/C++ source without its comments, whitespace runs made single spaces (edits of comments
+    and layout do not change a kernel)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.sub(r"\s+", " ", text).strip()
+
+
 def kernel_source_hash(kernel):
-    """Hash of the sources of one stepping kernel; a recorded DRAM traffic figure is only reported
-    while the kernel is the one it was measured on."""
+    """Hash of the code of one stepping kernel and the headers it uses (comments left out); a
+    recorded DRAM traffic figure is only reported while the kernel is the one it was measured on."""
     h = hashlib.sha256()
     for item in KERNEL_SOURCES[kernel]:
         fn, name = item if isinstance(item, tuple) else (item, None)
-        text = open(os.path.join(ROOT, "paper_2606_31842_b300", "csrc", fn)).read()
+        text = _code_only(open(os.path.join(ROOT, "paper_2606_31842_b300", "csrc", fn)).read())
         h.update((_kernel_text(text, name) if name else text).encode())
     return h.hexdigest()[:16]
 

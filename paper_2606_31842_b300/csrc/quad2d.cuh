@@ -1,6 +1,8 @@
-// Sub-steps of a staged 64 x 64 region for the FP32 5-point stencil with c = 1 -- the f = 0 wave
-// solves of the constant-speed 2-D grids, i.e. every A p of their Krylov iterations -- in a
-// thread mapping chosen for the issue rate rather than for the global loads.
+// Sub-steps of a staged 64 x 64 region for the FP32 2-D stencils -- the f = 0 wave solves, i.e.
+// every A p of the Krylov iterations: quad_sweep for the 5-point stencil with c = 1 (with the
+// Taylor start for the batched kernel), quadv_sweep for c^2 Delta_h and the 9-point-wide
+// 4th-order stencil -- in a thread mapping chosen for the issue rate rather than for the global
+// loads.
 //
 // Thread t of the 1024 owns the four consecutive cells 4 (t mod 16) .. 4 (t mod 16) + 3 of region
 // row t / 16 for the whole sweep, their W^n, W^{n-1} and filter sums in registers.  Per sub-step a

@@ -48,15 +48,20 @@ def test_traffic_is_null_once_the_kernel_changes(tmp_path, monkeypatch):
     j = src.index("{", i)
     p.write_text(src[:j + 1] + "  // edited\n" + src[j + 1:])
     assert bench.traffic_for("k_step3d2", "fp32") is not None
-    # ... editing the kernel itself drops it
+    # ... and so does a comment inside the kernel ...
     src = p.read_text()
     j = src.index("float accA = 0.0f;")
-    p.write_text(src[:j] + "float accA = 0.0f;  // changed" + src[j + len("float accA = 0.0f;"):])
+    p.write_text(src[:j] + "/* note */ " + src[j:])
+    assert bench.traffic_for("k_step3d2", "fp32") is not None
+    # ... editing the kernel's code drops it
+    src = p.read_text()
+    j = src.index("float accA = 0.0f;")
+    p.write_text(src[:j] + "float accA = 0.0f * 1.0f;" + src[j + len("float accA = 0.0f;"):])
     assert bench.traffic_for("k_step3d2", "fp32") is None
     assert bench.traffic_for("k_step3d", "fp32") is not None
     # a shared header drops every kernel built from it
     h = root / "paper_2606_31842_b300" / "csrc" / "whv_device.cuh"
-    h.write_text(h.read_text() + "\n// edited\n")
+    h.write_text(h.read_text() + "\nconstexpr int kEdited = 1;\n")
     assert bench.traffic_for("k_step3d", "fp32") is None
     assert bench.traffic_for("k_block2d", "fp32") is None
     assert bench.traffic_for("unknown_kernel", "fp32") is None

@@ -103,10 +103,16 @@ def select_modes(grid: Grid, tg: TimeGrid, nd: int):
     modes = all_modes(grid)
     lam2 = mode_lambda2(grid, modes)
     bh = beta_h(lam2, tg)
+    order = deflation_order(grid, modes, bh)[:nd]
+    return modes[order], lam2[order], bh[order]
+
+
+def deflation_order(grid: Grid, modes: np.ndarray, bh: np.ndarray) -> np.ndarray:
+    """Indices of `modes` sorted by |1 - beta_h| ascending, ties by the mode tuple
+    (k_x, k_y, k_z) in lexicographic order (the reading of Sec. 2.3 used by select_modes)."""
     key = np.abs(1.0 - bh)
     keys = [modes[:, m] for m in reversed(range(grid.dim))] + [key]
-    order = np.lexsort(keys)[:nd]
-    return modes[order], lam2[order], bh[order]
+    return np.lexsort(keys)
 
 
 def mode_vector(grid: Grid, mode) -> np.ndarray:

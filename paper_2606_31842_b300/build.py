@@ -2,8 +2,9 @@
 
     python -m paper_2606_31842_b300.build [-v]
 
-nvcc cross-compiles without a GPU.  The shared library lands in
-paper_2606_31842_b300/lib/libwhv.so and links the CUDA runtime dynamically, so it shares the
+nvcc cross-compiles without a GPU.  Every .cu file is compiled to its own object (in parallel,
+under paper_2606_31842_b300/_build/) and the objects are linked into
+paper_2606_31842_b300/lib/libwhv.so, which links the CUDA runtime dynamically, so it shares the
 runtime (and its streams) with PyTorch in the same process.
 """
 from __future__ import annotations
@@ -13,13 +14,16 @@ import os
 import shutil
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
+OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(LIBDIR, "libwhv.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3", "-cudart", "shared"]
 
 
 def nvcc_path() -> str:
@@ -33,25 +37,47 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def headers():
+    return glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "whv.h")]
+
+
+def _newest(paths) -> float:
+    return max(os.path.getmtime(p) for p in paths)
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False
-    t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "whv.h")]
-    return all(os.path.getmtime(d) <= t for d in deps)
+    return _newest(sources() + headers()) <= os.path.getmtime(LIB)
+
+
+def _obj(src: str) -> str:
+    return os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
 
 
 def build(verbose: bool = False, force: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)
-    cmd = [nvcc_path(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared",
-           "-Xcompiler", "-fPIC,-O3", "-cudart", "shared",
-           "-I", os.path.join(ROOT, "include"), "-I", CSRC,
-           "-o", LIB + ".tmp", *sources()]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), flush=True)
+    os.makedirs(OBJDIR, exist_ok=True)
+    nvcc = nvcc_path()
+    hdr_t = _newest(headers())
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
+
+    def compile_one(src):
+        obj = _obj(src)
+        if not force and os.path.exists(obj) and max(hdr_t, os.path.getmtime(src)) <= os.path.getmtime(obj):
+            return obj
+        cmd = [nvcc, *ARCH, *FLAGS, *(["-Xptxas=-v"] if verbose else []), *inc, "-c", "-o", obj + ".tmp", src]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        subprocess.run(cmd, check=True)
+        os.replace(obj + ".tmp", obj)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=max(1, os.cpu_count() or 1)) as ex:
+        objs = list(ex.map(compile_one, sources()))
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB + ".tmp", *objs]
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB

@@ -1,28 +1,36 @@
 #!/usr/bin/env python
 """Benchmark of the deflated WaveHoltz solve on one B300 (replicas on N GPUs).
 
-A step is one complete deflated solve of the 2-D Helmholtz workload: 513^2 nodes (511^2
-unknowns), omega = 50, Gaussian source of width 0.02 at a seeded point, 64 closed-form sine
-eigenvectors (DEVD, Algorithm 2) and CG on (I - S_h) u = b to relative residual 1e-6 -- weight
-tables, Taylor start, the fused leapfrog + filter steps, the operator epilogue, forcing deflation
-and inflation and the FP64 Krylov reductions all run in the library's kernels.  Default precision:
-FP32 wave stepping with FP64 Krylov / deflation arithmetic; --precision fp64 runs the plain FP64
-form (tolerance 1e-8, the 2-D workload's own).
+A step is one complete batched solve of the batched-squares workload: 256 problems -- constant-
+speed Dirichlet squares of 257^2, 513^2, 769^2 and 1025^2 nodes x omega in {20, 30, 40, 50} x 16
+Gaussian point sources of width 2h at seeded positions -- each deflated by its (grid, omega)'s 32
+closed-form sine eigenvectors (DEVD, Algorithm 2; the 16 sources of one class share one basis),
+solved by CG on (I - S_h) u = b to relative residual 1e-6, all problems advanced together: every
+batched wave solve is ONE persistent launch, the CG loop a CUDA graph with a device-side WHILE
+node.  Default precision: FP32 wave stepping inside FP64 residual correction (the b and residual
+wave solves in double-float pairs, the Krylov and deflation arithmetic in FP64); the same line
+carries the plain FP64 form's time on the same GPU (`fp64_form`), the 513^2 single-grid workload
+(`c2`) and the HBM-resident 3-D stencil (`stencil_hbm`).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64] [--impl whv|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl whv|reference] [--workload c4|c2|...]
 
-Prints one JSON line on rank 0.  --impl reference times the FP64 CPU oracle (numpy, one thread)
-on the same workload instead.  Under torchrun every rank solves its own copy of the workload
-(replicas; the path has no collective) and the time is the maximum over ranks.
+Prints one JSON line on rank 0.  --impl reference times the FP64 CPU oracle on the host cores
+instead (a bounded sample per step, extrapolated to the whole workload with the oracle's own
+iteration counts).  --gpus N without torchrun relaunches itself under torchrun with N ranks;
+every rank solves its own copy of the workload (replicas: the path has no collective) and the
+time is the maximum over ranks.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
-import re
 import json
 import math
+import multiprocessing
 import os
+import platform
+import re
+import socket
 import statistics
 import subprocess
 import sys
@@ -31,16 +39,16 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-# the CPU oracle legs run single-threaded (numpy elementwise work is single-threaded anyway;
-# this pins the BLAS calls of the projections too); set before numpy is first imported
+# the CPU oracle legs run one thread per process (numpy elementwise work is single-threaded
+# anyway; this pins the BLAS calls of the projections too); set before numpy is first imported
 for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_var, "1")
 
 METRIC = "WaveHoltz solve time to rel. residual 1e-6; stencil GLUP/s vs HBM roofline"
-L2_FLUSH_BYTES = 512 << 20   # > 126 MB L2: written between timed steps
+L2_FLUSH_BYTES = 512 << 20   # > 126 MB L2: written between timed steps of the L2-sized workloads
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -48,6 +56,8 @@ def parse():
     ap.add_argument("--impl", default="whv", choices=["whv", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="batched workload: skip the plain-FP64 form, c2, the 3-D stencil and e2e legs")
     ap.add_argument("--method", default="", choices=["", "cg", "dcg", "gmres", "agmres", "abicgstab"],
                     help="accelerator of the single-grid workloads (default: DCG for c1/c3, CG otherwise)")
     ap.add_argument("--steps-per-sweep", type=int, default=0,
@@ -61,32 +71,51 @@ def parse():
                          "with a conditional node), k > 1 launches one iteration graph per step from the host")
     ap.add_argument("--eigs", default="lanczos", choices=["lanczos", "thick"],
                     help="variable-speed workload: one 1024-step Lanczos run, or thick-restart Lanczos (basis 3 nd + 4)")
+    ap.add_argument("--lanczos-fp64", action="store_true",
+                    help="variable-speed workload: FP64 stepping in the Lanczos eigen-solve (default: FP32)")
     ap.add_argument("--compress", type=float, default=0.0,
                     help="variable-speed workload: SVD-compress the basis with this Frobenius tolerance")
     ap.add_argument("--form", default="nonconservative", choices=["nonconservative", "conservative"],
                     help="variable-speed workload: operator form (conservative: div(c^2 grad), second order)")
     ap.add_argument("--sources", type=int, default=0,
                     help="batched workload: Gaussian sources per (grid, frequency) (default 16)")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "study"],
-                    help="c2 (default): the 513^2 deflated solve; others: the 1-D, variable-speed "
-                         "1025^2, batched and 3-D workloads, measured on request")
-    return ap.parse_args()
+    ap.add_argument("--workload", default="c4", choices=["c1", "c2", "c3", "c4", "c5", "study"],
+                    help="c4 (default): the batched squares; c2: the 513^2 deflated solve; c1, c3, c5: the "
+                         "1-D, variable-speed 1025^2 and 3-D workloads; study: iterations vs omega")
+    return ap.parse_args(argv)
 
 
-def workload_config(precision):
-    from paper_2606_31842_b300 import inputs as I
-    w = I.WORKLOADS["c2"]
-    tol = 1e-6 if precision == "fp32" else w.tol
-    return w, tol
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
 
 
-def config_dict(w, tol, precision, nt, n_gpus):
-    return {"workload": f"2-D Helmholtz {w.npts[0]}x{w.npts[1]} nodes, omega={w.omega:g}, Gaussian source width 0.02, "
-                        f"DEVD + CG with {w.nd} closed-form eigenvectors, tol {tol:g}",
-            "grid": list(w.npts), "unknowns": w.n_unknowns, "omega": w.omega, "nd": w.nd, "tol": tol,
-            "method": "DEVD-CG" + (" in FP64 residual correction" if precision == "fp32" else ""),
-            "stepping": precision, "krylov": "fp64", "nt": nt,
-            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{n_gpus}"}
+def relaunch_under_torchrun(args, argv):
+    """--gpus N > 1 without a torchrun environment: run this script again as N ranks on this node
+    (one replica per GPU) and return its exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", f"--master-port={_free_port()}", os.path.abspath(__file__), *argv]
+    return subprocess.call(cmd)
+
+
+def host_cpu():
+    """Host cores this process may use and the CPU model."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = platform.processor() or ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": cores, "cpu_model": model}
 
 
 # ------------------------------------------------------------------------------ clocks
@@ -137,18 +166,166 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ oracle legs
-def oracle_sample(w, tol, iterations_hint, budget_s=12.0):
-    """Time the FP64 oracle on a bounded sample of the workload: mode selection + basis, b, and
-    as many CG iterations as fit in the budget; extrapolate to `iterations_hint` iterations."""
+# The batched workload is far too large for the FP64 numpy oracle to solve within a benchmark run
+# (about 10^12 lattice-point updates at ~5e7 per second and core).  Its time is therefore
+# extrapolated from measured pieces of the oracle itself:
+#   * the oracle's own iteration counts: DEVD-CG of every problem run to the workload's tolerance
+#     by oracle/modal.py (the same CG in the box's sine eigenbasis, pinned to the time-domain
+#     oracle: equal iteration counts up to rounding at the threshold);
+#   * the time of one oracle CG iteration (one wave solve of krylov.Operator plus its vector
+#     updates) on each grid size, per lattice-point update;
+#   * for all host cores: the same CG iteration run by one process per core at once (the problems
+#     are independent, so the oracle parallelises over them), which gives the aggregate rate.
+# The oracle solve time of problem p is (iterations_p + 1) wave solves (the +1 is b) of
+# N_p * Nt_p updates; the eigenvector set-up is left out on both sides (the GPU's timed step
+# starts from bases that are already set, as the oracle's would).
+
+def _c4_classes(nsrc):
+    from paper_2606_31842_b300 import inputs as I
+    return [(n, om) for n in I.C4_SIZES for om in I.C4_OMEGAS]
+
+
+def _modal_iterations(job):
+    """Oracle DEVD-CG iteration counts of the nsrc sources of one (grid, omega) class."""
+    n, om, nsrc = job
+    import numpy as np
+    from oracle import operators as O, waveholtz as WH, modal as MD
+    from paper_2606_31842_b300 import inputs as I
+    w = I.WORKLOADS[f"c4_{n}_{int(om)}"]
+    g = O.Grid(w.npts)
+    tg = WH.time_grid_for(g, w.omega)
+    ms = MD.ModalSystem(g, tg, w.nd)
+    F = np.stack([I.forcing_for(w, s).reshape(g.shape) for s in range(nsrc)])
+    its, conv, _ = MD.devd_cg(ms, F, w.tol, 20000)
+    return {"n": n, "omega": om, "iterations": [int(x) for x in its], "converged": bool(conv.all()),
+            "nt": tg.nt, "unknowns": g.n}
+
+
+def _cg_iteration_time(job):
+    """Seconds of one oracle CG iteration (krylov.cg, one step) on the class's grid and time grid,
+    and the lattice-point updates of its wave solve."""
+    n, om = job
+    from oracle import operators as O, waveholtz as WH, krylov as K
+    from paper_2606_31842_b300 import inputs as I
+    w = I.WORKLOADS[f"c4_{n}_{int(om)}"]
+    g = O.Grid(w.npts)
+    tg = WH.time_grid_for(g, w.omega)
+    b = I.random_field(g.shape, 7)
+    A = K.Operator(g, tg)
+    t0 = time.perf_counter()
+    K.cg(g, A, b, 0.0, 1)
+    t = time.perf_counter() - t0
+    return {"n": n, "omega": om, "seconds": t, "lups": g.n * tg.nt}
+
+
+def oracle_iterations(pool, nsrc):
+    """Per-problem oracle iteration counts of the batched workload (in parallel over classes)."""
+    jobs = [(n, om, nsrc) for n, om in _c4_classes(nsrc)]
+    return pool.map(_modal_iterations, jobs, chunksize=1)
+
+
+def oracle_time_model(classes, sec_per_lup, parallel_speedup):
+    """Extrapolated oracle solve time (seconds) of the whole batch: sum over problems of
+    (iterations + 1) wave solves at the measured seconds per update of their grid size."""
+    total = 0.0
+    lups = 0
+    for c in classes:
+        spl = sec_per_lup.get(c["n"], statistics.mean(sec_per_lup.values()))
+        for it in c["iterations"]:
+            total += (it + 1) * c["unknowns"] * c["nt"] * spl
+            lups += (it + 1) * c["unknowns"] * c["nt"]
+    return {"one_core_s": total, "all_cores_s": total / parallel_speedup, "lups": lups}
+
+
+def oracle_parallel_speedup(pool, nworkers, job=(513, 50.0)):
+    """All-core speed-up of the problem-parallel oracle: nworkers processes each run one oracle CG
+    iteration at once (after a warm-up round); speed-up = nworkers x (time of the iteration run
+    alone / its mean time when all run together), at most nworkers."""
+    pool.map(_cg_iteration_time, [job] * nworkers, chunksize=1)          # warm-up round
+    alone = min(pool.apply(_cg_iteration_time, (job,))["seconds"] for _ in range(2))
+    t0 = time.perf_counter()
+    res = pool.map(_cg_iteration_time, [job] * nworkers, chunksize=1)
+    wall = time.perf_counter() - t0
+    together = statistics.mean(r["seconds"] for r in res)
+    return min(float(nworkers), nworkers * alone / together), wall
+
+
+def oracle_c4_baseline(nsrc):
+    """cpu_baseline of the batched workload: iteration counts, per-size update rates on one core
+    (one CG iteration per grid size at omega = 50), all-core speed-up; about 30 s of host time."""
+    cpu = host_cpu()
+    P = cpu["nproc"]
+    ctx = multiprocessing.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(P) as pool:
+        classes = oracle_iterations(pool, nsrc)
+        rates = pool.map(_cg_iteration_time, [(n, 50.0) for n in (257, 513, 769, 1025)], chunksize=1)
+        speedup, wall_par = oracle_parallel_speedup(pool, P)
+    spl = {r["n"]: r["seconds"] / r["lups"] for r in rates}
+    model = oracle_time_model(classes, spl, speedup)
+    return {"model": model, "classes": classes, "sec_per_lup": spl, "speedup": speedup, "cpu": cpu,
+            "host_s": time.perf_counter() - t0}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle on the host cores, on the batched workload (or the
+    513^2 workload with --workload c2).  Each timed step is a bounded sample: one oracle CG
+    iteration on the next (grid, omega) class in turn (all 16 classes within 16 steps); `value`
+    extrapolates the samples to the whole workload with the oracle's own iteration counts and the
+    all-core speed-up, `ms_per_step` is the measured time of a sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    if args.workload == "c2":
+        return run_reference_c2(args)
+    nsrc = args.sources if args.sources > 0 else 16
+    cpu = host_cpu()
+    ctx = multiprocessing.get_context("spawn")
+    with ctx.Pool(cpu["nproc"]) as pool:
+        classes = oracle_iterations(pool, nsrc)
+        speedup, _ = oracle_parallel_speedup(pool, cpu["nproc"])
+    order = _c4_classes(nsrc)
+    samples, step_ms = {}, []
+    for s in range(args.warmup + args.steps):
+        job = (257, 50.0) if s < args.warmup else order[(s - args.warmup) % len(order)]
+        t0 = time.perf_counter()
+        r = _cg_iteration_time(job)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            step_ms.append(dt * 1e3)
+            samples.setdefault(r["n"], []).append(r["seconds"] / r["lups"])
+    spl = {n: statistics.mean(v) for n, v in samples.items()}
+    model = oracle_time_model(classes, spl, speedup)
+    value = model["all_cores_s"] * 1e3
+    nprob = sum(len(c["iterations"]) for c in classes)
+    sample = (f"per step one oracle CG iteration (numpy FP64, 1 process) on the next of the 16 (grid, omega) "
+              f"classes; extrapolated to all {nprob} problems with the oracle's own DEVD-CG iteration counts "
+              f"(oracle/modal.py, tol 1e-6) and the measured {speedup:.1f}x speed-up of {cpu['nproc']} processes "
+              f"(one problem per core); eigenvector set-up excluded on both sides")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": c4_config(nsrc, "DEVD-CG, FP64 (oracle)", nprob),
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": cpu["nproc"], "kind": "oracle",
+                             "sample": sample, "cpu_model": cpu["cpu_model"],
+                             "one_core_ms": model["one_core_s"] * 1e3, "parallel_speedup": speedup},
+            "oracle_iterations_mean": statistics.mean(i for c in classes for i in c["iterations"]),
+            "oracle_iterations_max": max(i for c in classes for i in c["iterations"]),
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def oracle_sample_c2(w, tol, iterations, budget_s=12.0):
+    """The FP64 oracle on a bounded sample of the 513^2 workload: b and as many CG iterations as
+    fit in the budget, extrapolated to `iterations`."""
     from oracle import operators as O, waveholtz as WH, spectral as SP, krylov as K
     from paper_2606_31842_b300 import inputs as I
     g = O.Grid(w.npts)
     tg = WH.time_grid_for(g, w.omega)
     f = I.forcing_for(w)
-    t0 = time.perf_counter()
     modes, lam2, _ = SP.select_modes(g, tg, w.nd)
     V = SP.basis(g, modes)
-    t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     b = WH.rhs_b(g, tg, K.project_out(g, V, f))
     t_b = time.perf_counter() - t0
@@ -157,32 +334,41 @@ def oracle_sample(w, tol, iterations_hint, budget_s=12.0):
     t0 = time.perf_counter()
     K.cg(g, A, b, 0.0, k)
     t_it = (time.perf_counter() - t0) / k
-    solve_s = t_b + iterations_hint * t_it
-    return {"solve_s": solve_s, "setup_s": t_setup, "t_wave": t_b, "t_iter": t_it, "k": k}
+    return {"solve_s": t_b + iterations * t_it, "t_wave": t_b, "t_iter": t_it, "k": k}
 
 
-def run_reference(args):
-    """--impl reference: the FP64 CPU oracle on the same workload, metric and unit."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return 0
-    w, tol = workload_config(args.precision)
-    from oracle import operators as O, waveholtz as WH
-    nt = WH.time_grid_for(O.Grid(w.npts), w.omega).nt
-    # iteration count of the oracle at this tolerance (deflated CG on this workload)
-    iters = 37 if tol >= 1e-6 else 50
-    times = []
+def oracle_iterations_c2(w, tol):
+    """The oracle's DEVD-CG iteration count on the 513^2 workload (oracle/modal.py)."""
+    import numpy as np
+    from oracle import operators as O, waveholtz as WH, modal as MD
+    from paper_2606_31842_b300 import inputs as I
+    g = O.Grid(w.npts)
+    tg = WH.time_grid_for(g, w.omega)
+    its, conv, _ = MD.devd_cg(MD.ModalSystem(g, tg, w.nd), I.forcing_for(w).reshape(g.shape), tol, 20000)
+    return int(its)
+
+
+def run_reference_c2(args):
+    from paper_2606_31842_b300 import inputs as I
+    w = I.WORKLOADS["c2"]
+    tol = 1e-6 if args.precision == "fp32" else w.tol
+    iters = oracle_iterations_c2(w, tol)
+    times, step_ms = [], []
     for s in range(args.warmup + args.steps):
-        t = oracle_sample(w, tol, iters, budget_s=3.0)
+        t0 = time.perf_counter()
+        t = oracle_sample_c2(w, tol, iters, budget_s=2.0)
         if s >= args.warmup:
             times.append(t["solve_s"] * 1e3)
+            step_ms.append((time.perf_counter() - t0) * 1e3)
     ms = statistics.mean(times)
-    cb = {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
-          "sample": f"b wave solve + {t['k']} CG iterations per step at 1 thread, extrapolated to {iters} iterations"}
+    cpu = host_cpu()
+    cb = {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "cpu_model": cpu["cpu_model"],
+          "sample": f"b + {t['k']} CG iterations per step (numpy FP64, 1 thread), extrapolated to the oracle's "
+                    f"own {iters} DEVD-CG iterations (oracle/modal.py)"}
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(w, tol, "fp64", nt, args.gpus), "cpu_baseline": cb,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": c2_config(w, tol, "fp64", None, args.gpus), "cpu_baseline": cb,
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -195,6 +381,7 @@ KERNEL_SOURCES = {
     "k_block2d": ("stencil_blocked.cu", "quad2d.cuh", "whv_device.cuh"),
     "k_step3d": (("stencil.cu", "k_step3d"), "stencil_ops.cuh", "whv_device.cuh"),
     "k_step3d2": (("stencil.cu", "k_step3d2"), "stencil_ops.cuh", "whv_device.cuh"),
+    "k_batch_block2d": (("batch.cu", "k_batch_block2d"), "quad2d.cuh", "whv_device.cuh"),
 }
 
 
@@ -261,6 +448,18 @@ def aggregate_max(value, world, device=None):
     return float(t.item())
 
 
+def aggregate_max(value, world, device=None):
+    """Max of a per-rank time over all ranks (replicas: the job takes as long as its slowest rank);
+    identity for a single process."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _timed(stream, fn, steps, warmup, flush):
     import torch
     for _ in range(max(1, warmup)):
@@ -279,9 +478,428 @@ def _timed(stream, fn, steps, warmup, flush):
     return statistics.mean(times), out
 
 
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(path)) if os.path.exists(path) else {}
+    return peaks.get("hbm_gbs", 6400.0), ("measured" if "hbm_gbs" in peaks else "fallback")
+
+
+def c4_config(nsrc, form, nprob):
+    return {"workload": f"batched squares: (257, 513, 769, 1025)^2 nodes x omega (20, 30, 40, 50) x {nsrc} Gaussian "
+                        f"point sources (width 2h, seeded), Dirichlet, c = 1, 32 closed-form eigenvectors per "
+                        f"(grid, omega), {form}, to rel. residual 1e-6",
+            "problems": nprob, "grids": [257, 513, 769, 1025], "omegas": [20.0, 30.0, 40.0, 50.0],
+            "sources": nsrc, "nd": 32, "tol": 1e-6, "parallelism": "replicas (one batch per GPU)"}
+
+
+class C4Batch:
+    """The batched workload on the device: one grid per problem, the 16 sources of a (grid, omega)
+    class sharing that class's closed-form basis; forcings resident on the device (and pinned on
+    the host for the end-to-end leg)."""
+
+    def __init__(self, whv, I, stream, fp32, nsrc, residual="df64", check_every=1):
+        import torch
+        self.whv, self.stream = whv, stream
+        prec = whv.WHV_FP32_STEP if fp32 else whv.WHV_FP64
+        self.grids, self.params, self.fs, self.hf, self.w = [], [], [], [], []
+        t0 = time.perf_counter()
+        for n in I.C4_SIZES:
+            for om in I.C4_OMEGAS:
+                w = I.WORKLOADS[f"c4_{n}_{int(om)}"]
+                prm = whv.make_params(om, method="cg", tol=w.tol, maxit=3000, refine_fp64=fp32,
+                                      residual_df64=fp32 and residual == "df64", check_every=check_every)
+                owner = None
+                for src in range(nsrc):
+                    g = whv.Grid(w.npts, precision=prec, stream=stream)
+                    if owner is None:
+                        g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
+                        owner = g
+                    else:
+                        g.whv_share_basis(owner)
+                    h = torch.from_numpy(I.forcing_for(w, src).ravel()).pin_memory()
+                    with torch.cuda.stream(stream):
+                        self.fs.append(h.to("cuda", non_blocking=True))
+                    self.grids.append(g); self.params.append(prm); self.hf.append(h); self.w.append(w)
+        with torch.cuda.stream(stream):
+            self.us = [torch.zeros(g.N, dtype=torch.float64, device="cuda") for g in self.grids]
+        stream.synchronize()
+        self.setup_s = time.perf_counter() - t0
+        self.infos = None
+
+    def solve(self):
+        _, self.infos = self.whv.whv_solve_batched(self.grids, self.params, self.fs, self.us)
+        return self.infos
+
+    def close(self):
+        for g in self.grids:
+            g.close()
+        self.grids = []
+
+
+def c4_sweep_bytes(grids, nts, k):
+    """Algorithmic DRAM bytes of one FP32 f = 0 batched wave solve (k_batch_block2d, sweeps of k
+    steps): per node, the first sweep reads v (8 B) and writes the state pair and the filter sum
+    (12 B), every middle sweep reads and writes those three (24 B), the last one reads them and
+    writes the FP64 output (20 B).  Halo re-reads are not counted."""
+    total = 0
+    for g, nt in zip(grids, nts):
+        J = -(-nt // k)
+        total += g.N * (20 + 24 * max(J - 2, 0) + (20 if J >= 2 else 0))
+    return total
+
+
+def c2_config(w, tol, precision, nt, n_gpus):
+    return {"workload": f"2-D Helmholtz {w.npts[0]}x{w.npts[1]} nodes, omega={w.omega:g}, Gaussian source width 0.02, "
+                        f"DEVD + CG with {w.nd} closed-form eigenvectors, tol {tol:g}",
+            "grid": list(w.npts), "unknowns": w.n_unknowns, "omega": w.omega, "nd": w.nd, "tol": tol,
+            "method": "DEVD-CG" + (" in FP64 residual correction" if precision == "fp32" else ""),
+            "stepping": precision, "krylov": "fp64", "nt": nt,
+            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{n_gpus}"}
+
+
+def c2_measure(whv, I, stream, flush, precision, steps, warmup, residual="df64", check_every=1, kfix=0):
+    """The 513^2 workload: DEVD-CG solve time (CUDA events, L2 flushed between steps), the
+    blocked kernel's equivalent bandwidth (its 3 MB state stays in L2) and the accuracy."""
+    import torch
+    w = I.WORKLOADS["c2"]
+    fp32 = precision == "fp32"
+    tol = 1e-6 if fp32 else w.tol
+    g = whv.Grid(w.npts, precision=whv.WHV_FP32_STEP if fp32 else whv.WHV_FP64, stream=stream)
+    prm = whv.make_params(w.omega, method="cg", tol=tol, maxit=5000, check_every=check_every,
+                          refine_fp64=fp32, residual_df64=fp32 and residual == "df64")
+    nt = g.whv_time_grid(prm)["nt"]
+    g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
+    if kfix:
+        g.whv_set_steps_per_sweep(kfix)
+        ksweep = kfix
+    else:
+        ksweep = g.whv_autotune(prm)
+    with torch.cuda.stream(stream):
+        f = torch.from_numpy(I.forcing_for(w).ravel()).to("cuda")
+        u = torch.zeros_like(f)
+    res = {}
+
+    def solve():
+        res["info"] = g.whv_solve(prm, f, u)[1]
+    ms, _ = _timed(stream, solve, steps, max(3, warmup), flush)
+    info = res["info"]
+    prm_chk = whv.make_params(w.omega, method="cg", tol=tol, maxit=5000, true_residual=True, refine_fp64=fp32,
+                              residual_df64=fp32 and residual == "df64")
+    _, ichk = g.whv_solve(prm_chk, f)
+    # the step kernel alone: replays of the f = 0 wave-solve graph, per leapfrog step
+    v = torch.randn(w.n_unknowns, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(v)
+    torch.cuda.synchronize()
+    g.whv_apply_pi(prm, v, None, out)
+    stream.synchronize()
+    reps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        g.whv_apply_pi(prm, v, None, out)
+    e1.record(stream)
+    e1.synchronize()
+    t_step = e0.elapsed_time(e1) * 1e-3 / (reps * nt)
+    g.close()
+    esz = 4 if fp32 else 8
+    return {"solve_ms": ms, "tol": tol, "iterations": info["iterations"], "wave_solves": info["wave_solves"],
+            "true_rel_residual": ichk["true_rel_residual"], "nt": nt, "steps_per_sweep": ksweep,
+            "step_us": t_step * 1e6, "glups": w.n_unknowns / t_step / 1e9,
+            "equiv_gbs": 5 * esz * w.n_unknowns / t_step / 1e9,
+            "kernel": (f"k_block2d ({ksweep} leapfrog steps + filter per launch)" if ksweep > 1 else "k_step"),
+            "note": "511^2 state (3 arrays, 3 MB) stays in the 126 MB L2: equivalent bandwidth, not an HBM figure"}
+
+
+def stencil_hbm_measure(whv, stream, peak):
+    """The 3-D 256^3 grid (66 MB per FP32 array, 3 arrays > L2): f = 0 wave solves with one
+    (k_step3d) and two (k_step3d2) leapfrog steps per launch, the case on which the HBM fraction
+    of the stencil is read."""
+    import torch
+    g3 = whv.Grid((256, 256, 256), precision=whv.WHV_FP32_STEP, stream=stream)
+    prm3 = whv.make_params(40.0)
+    nt3 = g3.whv_time_grid(prm3)["nt"]
+    v3 = torch.randn(g3.N, dtype=torch.float64, device="cuda")
+    o3 = torch.empty_like(v3)
+    torch.cuda.synchronize()
+
+    def time_3d(k):
+        g3.whv_set_steps_per_sweep(k)
+        g3.whv_apply_pi(prm3, v3, None, o3)
+        stream.synchronize()
+        reps3 = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps3):
+            g3.whv_apply_pi(prm3, v3, None, o3)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3 / (reps3 * nt3)
+
+    t31 = time_3d(1)
+    t32 = time_3d(2)
+    N = g3.N
+    g3.close()
+    ach31, ach32 = 20 * N / t31 / 1e9, 20 * N / t32 / 1e9
+    return {"kernel": "k_step3d2 (3-D 7-point, two leapfrog steps + filter per launch, FP32)",
+            "workload": "256^3 nodes (254^3 unknowns), omega=40, f = 0 wave solves, nt=%d" % nt3,
+            "bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s", "frac": ach32 / peak,
+            "bytes_per_lup": 20, "glups": N / t32 / 1e9, "step_us": t32 * 1e6,
+            "own_bytes_per_lup": 12, "own_frac": 12 * N / t32 / 1e9 / peak,
+            "traffic": traffic_for("k_step3d2", "fp32"), "traffic_unit": "DRAM bytes per launch (2 steps)",
+            "note": "achieved/frac count the 20 B per LUP of single-step streaming (equivalent bandwidth); "
+                    "own_frac counts the 12 B per LUP the two-step kernel must move",
+            "single_step": {"kernel": "k_step3d (one step per launch)", "achieved": ach31, "frac": ach31 / peak,
+                            "glups": N / t31 / 1e9, "step_us": t31 * 1e6, "traffic": traffic_for("k_step3d", "fp32")}}
+
+
+def _env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _init_dist(world, local):
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_c4(args):
+    """The default line: the batched squares in one persistent launch per batched wave solve."""
+    import torch
+    rank, world, local = _env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    _init_dist(world, local)
+    from paper_2606_31842_b300 import build as whv_build
+    whv_build.build()
+    from paper_2606_31842_b300 import whv
+    from paper_2606_31842_b300 import inputs as I
+    stream = torch.cuda.Stream()
+    nsrc = args.sources if args.sources > 0 else I.C4_SOURCES
+    fp32 = args.precision == "fp32"
+    B = C4Batch(whv, I, stream, fp32, nsrc, args.residual, args.check_every)
+    if args.steps_per_sweep > 0:
+        B.grids[0].whv_set_steps_per_sweep(args.steps_per_sweep)
+        kb, ktag = args.steps_per_sweep, "fixed"
+    else:
+        kb, ktag = whv.whv_autotune_batched(B.grids, B.params), "autotuned"
+    for _ in range(max(3, args.warmup)):
+        B.solve()
+    # ------------------------------------------------------------------ timed region
+    times, infos = [], None
+    launches0 = whv.whv_kernel_launches()
+    with ClockSampler(local) as clk:
+        time.sleep(0.5)                               # let the sampler start
+        _barrier(world)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos = B.solve()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        _barrier(world)
+    launches = whv.whv_kernel_launches() - launches0
+    clocks = clk.summary()
+    ms = aggregate_max(statistics.mean(times), world, device="cuda")
+    nprob = len(B.grids)
+    lups = sum(g.N * i["nt"] * i["wave_solves"] for g, i in zip(B.grids, infos))
+    lups64 = sum(g.N * i["nt"] * i["wave_solves_fp64"] for g, i in zip(B.grids, infos))
+    # FP64 true residual of a sample of the problems, recomputed on separate FP64 grids
+    chk = []
+    for p in range(0, nprob, 37):
+        g64 = whv.Grid(B.w[p].npts, precision=whv.WHV_FP64, stream=stream)
+        r = g64.whv_apply_pi(B.params[p], B.us[p], B.fs[p])
+        bb = g64.whv_apply_pi(B.params[p], torch.zeros_like(B.fs[p]), B.fs[p])
+        chk.append(float((r - B.us[p]).norm() / bb.norm()))
+        g64.close()
+    form = (("DEVD-CG with FP32 stepping inside FP64 residual correction"
+             + (" (double-float b and residual wave solves)" if args.residual == "df64" else ""))
+            if fp32 else "DEVD-CG, FP64 stepping")
+    peak, peak_src = measured_peaks()
+    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "krylov_dtype": "f64", "data": "synthetic",
+            "config": dict(c4_config(nsrc, form, nprob), steps_per_sweep=f"{kb} ({ktag})",
+                           check_every=args.check_every, setup_s=B.setup_s,
+                           l2="no flush: the working set (~1.5 GB of FP32 state, ~1 GB of forcings and "
+                              "solutions) is larger than the 126 MB L2",
+                           basis="one closed-form basis per (grid, omega), shared by its sources"),
+            "iterations_max": max(i["iterations"] for i in infos),
+            "iterations_mean": statistics.mean(i["iterations"] for i in infos),
+            "outer_iterations_max": max(i["outer_iterations"] for i in infos),
+            "wave_solves": sum(i["wave_solves"] for i in infos),
+            "wave_solves_fp64_or_df64": sum(i["wave_solves_fp64"] for i in infos),
+            "glups_solve": lups / (ms * 1e-3) / 1e9, "lups_fp64_or_df64_share": lups64 / max(lups, 1),
+            "accuracy": {"fp64_true_rel_residual_max": (max(i["true_rel_residual"] for i in infos) if fp32 else None),
+                         "fp64_true_rel_residual_recomputed_sample_max": max(chk),
+                         "recomputed": f"{len(chk)} problems, FP64 wave solves on separate FP64 grids"}}
+    if not args.no_extras:
+        # ---------------------------------------------------------------- e2e: host buffers
+        # the same batched solve through the public API with the forcings copied from pinned host
+        # memory and the solutions copied back inside the timed region (host wall clock, stream
+        # synchronised at both ends)
+        hu = [torch.empty(g.N, dtype=torch.float64).pin_memory() for g in B.grids]
+        e2e = []
+        for k in range(min(args.steps, 3) + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                for f, h in zip(B.fs, B.hf):
+                    f.copy_(h, non_blocking=True)
+            B.solve()
+            with torch.cuda.stream(stream):
+                for u, h in zip(B.us, hu):
+                    h.copy_(u, non_blocking=True)
+            stream.synchronize()
+            if k > 0:
+                e2e.append((time.perf_counter() - t0) * 1e3)
+        nbytes = sum(g.N * 8 for g in B.grids)
+        line["e2e"] = {"value": aggregate_max(statistics.mean(e2e), world, device="cuda"), "unit": "ms",
+                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                       "timing": "host wall clock around H2D of every forcing, whv_solve_batched, D2H of every "
+                                 "solution, stream synchronised"}
+        del hu
+        # ---------------------------------------------------------------- dominant kernel
+        # k_batch_block2d (FP32, 5-point, c = 1): one batched f = 0 wave solve of all problems per
+        # launch (whv_apply_pi_batched), timed with CUDA events on the launching stream
+        if fp32:
+            outs = [torch.empty(g.N, dtype=torch.float64, device="cuda") for g in B.grids]
+            prm0 = [whv.make_params(p.omega) for p in B.params]
+            whv.whv_apply_pi_batched(B.grids, prm0, B.us, None, outs)
+            reps = 3
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                whv.whv_apply_pi_batched(B.grids, prm0, B.us, None, outs)
+            e1.record(stream)
+            e1.synchronize()
+            t_launch = e0.elapsed_time(e1) * 1e-3 / reps
+            nts = [i["nt"] for i in infos]
+            lup_launch = sum(g.N * nt for g, nt in zip(B.grids, nts))
+            own = c4_sweep_bytes(B.grids, nts, kb)
+            tr = traffic_for("k_batch_block2d", "fp32")
+            tr_scaled = None
+            if tr:
+                rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_batch_block2d:fp32"]
+                tr_scaled = tr * lup_launch / rec["lups_per_launch"]
+            line["roofline"] = {"bound": "hbm", "achieved": own / t_launch / 1e9, "peak": peak, "unit": "GB/s",
+                                "frac": own / t_launch / 1e9 / peak, "traffic": tr_scaled,
+                                "kernel": f"k_batch_block2d<float> ({kb} leapfrog steps + filter per sweep, all "
+                                          f"{nprob} problems per launch)",
+                                "algorithmic_bytes_per_launch": own, "lups_per_launch": lup_launch,
+                                "launch_ms": t_launch * 1e3, "glups": lup_launch / t_launch / 1e9,
+                                "equiv_single_step_gbs": 20 * lup_launch / t_launch / 1e9,
+                                "peak_source": peak_src,
+                                "note": "achieved counts the bytes the blocked kernel must move (3 FP32 reads and "
+                                        "writes per node per sweep); equiv_single_step_gbs the 20 B per LUP of "
+                                        "one-step streaming; traffic: ncu DRAM bytes of a smaller batch scaled by LUPs"}
+            del outs
+        # ---------------------------------------------------------------- plain FP64 form
+        B64 = C4Batch(whv, I, stream, False, nsrc)
+        k64 = whv.whv_autotune_batched(B64.grids, B64.params)
+        warm = [whv.make_params(p.omega, method="cg", tol=p.tol, maxit=2) for p in B64.params]
+        whv.whv_solve_batched(B64.grids, warm, B64.fs, B64.us)   # warm-up: kernels, graphs, FP64 buffers
+        t64 = []
+        for _ in range(1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            i64 = B64.solve()
+            e1.record(stream)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        ms64 = aggregate_max(statistics.mean(t64), world, device="cuda")
+        line["fp64_form"] = {"ms": ms64, "speedup_of_value": ms64 / ms, "steps_per_sweep": k64,
+                             "iterations_mean": statistics.mean(i["iterations"] for i in i64),
+                             "iterations_max": max(i["iterations"] for i in i64),
+                             "status": sorted(set(i["status"] for i in i64)),
+                             "timing": "1 timed solve after a 2-iteration warm-up solve (CUDA events)"}
+        B64.close()
+        del B64
+        # ---------------------------------------------------------------- c2 and the 3-D stencil
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        c2_32 = c2_measure(whv, I, stream, flush, "fp32", 10, 3, args.residual)
+        c2_64 = c2_measure(whv, I, stream, flush, "fp64", 3, 3)
+        line["c2"] = {"workload": c2_config(I.WORKLOADS["c2"], 1e-6, "fp32", c2_32["nt"], world)["workload"],
+                      "fp32_correction": c2_32, "fp64": c2_64}
+        del flush
+        line["stencil_hbm"] = stencil_hbm_measure(whv, stream, peak)
+    line["gpu_launches"] = launches
+    line["clocks"] = clocks
+    B.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_c4_baseline(nsrc)
+        m = cb["model"]
+        line["cpu_baseline"] = {
+            "value": m["all_cores_s"] * 1e3, "unit": "ms", "cores": cb["cpu"]["nproc"], "kind": "oracle",
+            "cpu_model": cb["cpu"]["cpu_model"], "one_core_ms": m["one_core_s"] * 1e3,
+            "parallel_speedup": cb["speedup"], "host_s": cb["host_s"],
+            "oracle_iterations_mean": statistics.mean(i for c in cb["classes"] for i in c["iterations"]),
+            "sample": (f"numpy FP64 oracle: one CG iteration per grid size (omega = 50) on one core, the same "
+                       f"iteration in {cb['cpu']['nproc']} processes at once for the all-core rate, the oracle's own "
+                       f"DEVD-CG iteration counts of all {nprob} problems (oracle/modal.py); extrapolated to "
+                       f"sum_p (iterations_p + 1) wave solves; eigenvector set-up excluded on both sides")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_c2(args):
+    """--workload c2: the 513^2 deflated solve (FP32 + FP64 correction, or plain FP64 to 1e-8)."""
+    import torch
+    rank, world, local = _env()
+    _init_dist(world, local)
+    from paper_2606_31842_b300 import build as whv_build
+    whv_build.build()
+    from paper_2606_31842_b300 import whv
+    from paper_2606_31842_b300 import inputs as I
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    launches0 = whv.whv_kernel_launches()
+    with ClockSampler(local) as clk:
+        time.sleep(0.5)
+        _barrier(world)
+        r = c2_measure(whv, I, stream, flush, args.precision, args.steps, args.warmup, args.residual,
+                       args.check_every, args.steps_per_sweep)
+        _barrier(world)
+    ms = aggregate_max(r["solve_ms"], world, device="cuda")
+    w = I.WORKLOADS["c2"]
+    peak, peak_src = measured_peaks()
+    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "krylov_dtype": "f64",
+            "data": "synthetic", "config": c2_config(w, r["tol"], args.precision, r["nt"], world),
+            "c2": r, "gpu_launches": whv.whv_kernel_launches() - launches0, "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        iters = oracle_iterations_c2(w, r["tol"])
+        cb = oracle_sample_c2(w, r["tol"], iters)
+        line["cpu_baseline"] = {"value": cb["solve_s"] * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+                                "sample": f"numpy FP64, 1 thread: b + {cb['k']} CG iterations, extrapolated to the "
+                                          f"oracle's own {iters} DEVD-CG iterations"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_workload(args):
     """The other workloads (one JSON line each): 1-D FP64 DCG, variable-speed 1025^2 with the device
-    Lanczos basis, the batched squares and the 3-D cube."""
+    Lanczos basis, the 3-D cube and the omega study."""
     import numpy as np
     import torch
     from paper_2606_31842_b300 import build as whv_build
@@ -321,78 +939,6 @@ def run_workload(args):
                      "study": res})
         print(json.dumps(line), flush=True)
         return 0
-    if args.workload == "c4":
-        # FP32 stepping inside FP64 residual correction (default), or the plain FP64 form
-        fp32 = args.precision == "fp32"
-        gprec = whv.WHV_FP32_STEP if fp32 else whv.WHV_FP64
-        probs = []
-        t0 = time.perf_counter()
-        nsrc = args.sources if args.sources > 0 else I.C4_SOURCES
-        for n in I.C4_SIZES:
-            for om in I.C4_OMEGAS:
-                w = I.WORKLOADS[f"c4_{n}_{int(om)}"]
-                prm = whv.make_params(om, method="cg", tol=w.tol, maxit=3000, refine_fp64=fp32,
-                                      residual_df64=fp32 and args.residual == "df64", check_every=args.check_every)
-                tmpl = whv.Grid(w.npts, precision=gprec, stream=stream)
-                tmpl.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
-                b = tmpl.whv_get_basis(want_vectors=True)
-                for src in range(nsrc):
-                    g = whv.Grid(w.npts, precision=gprec, stream=stream)
-                    g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_USER, V=b["V"].reshape(-1),
-                                              lambda2=b["lambda2"], flags=whv.WHV_BASIS_EXACT)
-                    probs.append((g, prm, dev(I.forcing_for(w, src)), w))
-                tmpl.close()
-        setup_s = time.perf_counter() - t0
-        grids = [p[0] for p in probs]
-        params = [p[1] for p in probs]
-        if args.steps_per_sweep > 0:
-            grids[0].whv_set_steps_per_sweep(args.steps_per_sweep)
-            kb, ktag = args.steps_per_sweep, "fixed"
-        else:
-            kb, ktag = whv.whv_autotune_batched(grids, params), "autotuned"   # batched kernel's k
-        fs = [p[2] for p in probs]
-        us = [torch.zeros(g.N, dtype=torch.float64, device="cuda") for g in grids]
-        res = {}
-
-        def step():
-            _, infos = whv.whv_solve_batched(grids, params, fs, us)
-            res["infos"] = infos
-        ms, _ = _timed(stream, step, args.steps, args.warmup, None)
-        infos = res["infos"]
-        lups = sum(g.N * i["nt"] * i["wave_solves"] for g, i in zip(grids, infos))
-        lups64 = sum(g.N * i["nt"] * i["wave_solves_fp64"] for g, i in zip(grids, infos))
-        # FP64 true residual of a sample of the problems, recomputed on separate FP64 grids
-        # (outside the timed region)
-        chk = []
-        for k in range(0, len(probs), 37):
-            g, prm, f, w = probs[k]
-            g64 = whv.Grid(w.npts, precision=whv.WHV_FP64, stream=stream)
-            r = g64.whv_apply_pi(prm, us[k], f)
-            b = g64.whv_apply_pi(prm, torch.zeros_like(f), f)
-            chk.append(float((r - us[k]).norm() / b.norm()))
-            g64.close()
-        form = (("DEVD-CG with FP32 stepping inside FP64 residual correction"
-                 + (" (double-float b and residual wave solves)" if args.residual == "df64" else ""))
-                if fp32 else "DEVD-CG, FP64 stepping")
-        line.update({"workload": "c4", "value": ms, "ms_per_step": ms, "dtype": "f32" if fp32 else "f64",
-                     "krylov_dtype": "f64",
-                     "config": {"workload": f"batched: 4 squares (257..1025)^2 x 4 omega x {nsrc} Gaussian sources "
-                                            f"(width 2h), 32 closed-form vectors each, {form} to 1e-6; every "
-                                            f"batched wave solve of all {len(probs)} problems is one persistent launch",
-                                "problems": len(probs), "setup_s": setup_s,
-                                "steps_per_sweep": f"{kb} ({ktag}, both precisions)",
-                                "check_every": args.check_every},
-                     "iterations_max": max(i["iterations"] for i in infos),
-                     "iterations_mean": statistics.mean(i["iterations"] for i in infos),
-                     "outer_iterations_max": max(i["outer_iterations"] for i in infos),
-                     "wave_solves_fp64": sum(i["wave_solves_fp64"] for i in infos),
-                     "wave_solves": sum(i["wave_solves"] for i in infos),
-                     "glups_solve": lups / (ms * 1e-3) / 1e9, "glups_fp64_share": lups64 / max(lups, 1),
-                     "accuracy": {"fp64_true_rel_residual_max": (max(i["true_rel_residual"] for i in infos) if fp32
-                                                                   else None),
-                                  "fp64_true_rel_residual_recomputed_sample_max": max(chk)}})
-        print(json.dumps(line), flush=True)
-        return 0
     name = args.workload
     w = I.WORKLOADS["c5" if name == "c5" else name]
     prec = whv.WHV_FP64 if name == "c1" else whv.WHV_FP32_STEP
@@ -413,13 +959,14 @@ def run_workload(args):
     t0 = time.perf_counter()
     if name == "c3" and args.eigs == "thick":
         theta, resid, st = g.whv_lanczos_restarted(prm, w.nd, 3 * w.nd + 4, max_restarts=40, tol=1e-6,
-                                                   fp64_stepping=False)
-        setup = {"basis": f"device thick-restart Lanczos on S_h (FP32 stepping, basis {3 * w.nd + 4}, tol 1e-6)",
+                                                   fp64_stepping=args.lanczos_fp64)
+        setup = {"basis": f"device thick-restart Lanczos on S_h ({'FP64' if args.lanczos_fp64 else 'FP32'} stepping, "
+                          f"basis {3 * w.nd + 4}, tol 1e-6)",
                  "ritz_resid_median": float(np.median(resid)), "ritz_resid_max": float(np.max(resid)),
                  "setup_wave_solves": st["wave_solves"], "restarts": st["restarts"], "converged": st["converged"]}
     elif name == "c3":
-        theta, resid = g.whv_lanczos(prm, w.nd, 1024, None, False, 0)
-        setup = {"basis": "device Lanczos on S_h (FP32 stepping, 1024 steps)",
+        theta, resid = g.whv_lanczos(prm, w.nd, 1024, None, args.lanczos_fp64, 0)
+        setup = {"basis": f"device Lanczos on S_h ({'FP64' if args.lanczos_fp64 else 'FP32'} stepping, 1024 steps)",
                  "ritz_resid_median": float(np.median(resid)), "ritz_resid_max": float(np.max(resid)),
                  "setup_wave_solves": 1024}
     else:
@@ -488,228 +1035,18 @@ def run_workload(args):
     return 0
 
 
-def main():
-    args = parse()
+def main(argv=None):
+    argv = sys.argv[1:] if argv is None else argv
+    args = parse(argv)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return relaunch_under_torchrun(args, argv)
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload != "c2":
-        return run_workload(args)
-    import torch
-    import torch.distributed as dist
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if not torch.cuda.is_available():
-        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
-        return 1
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    from paper_2606_31842_b300 import build as whv_build
-    whv_build.build()
-    from paper_2606_31842_b300 import whv
-    from paper_2606_31842_b300 import inputs as I
-
-    w, tol = workload_config(args.precision)
-    prec = whv.WHV_FP32_STEP if args.precision == "fp32" else whv.WHV_FP64
-    stream = torch.cuda.Stream()
-    g = whv.Grid(w.npts, precision=prec, stream=stream)
-    # FP32 stepping runs inside FP64 residual correction so that the FP64 residual meets tol
-    fp32 = args.precision == "fp32"
-    prm = whv.make_params(w.omega, method="cg", tol=tol, maxit=5000, check_every=args.check_every,
-                          refine_fp64=fp32, residual_df64=fp32 and args.residual == "df64")
-    tgrid = g.whv_time_grid(prm)
-    nt = tgrid["nt"]
-    g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
-    if args.steps_per_sweep:
-        g.whv_set_steps_per_sweep(args.steps_per_sweep)
-        ksweep = args.steps_per_sweep
-    else:
-        ksweep = g.whv_autotune(prm)                  # steps per sweep of the blocked 2-D kernel
-    f_host = torch.from_numpy(I.forcing_for(w).ravel()).pin_memory()
-    u_host = torch.empty_like(f_host).pin_memory()
-    with torch.cuda.stream(stream):
-        f = f_host.to("cuda", non_blocking=True)
-        u = torch.zeros_like(f)
-        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    stream.synchronize()
-
-    def solve():
-        return g.whv_solve(prm, f, u)[1]
-
-    for _ in range(max(3, args.warmup)):
-        info = solve()
-    # ------------------------------------------------------------------ timed region
-    times, infos = [], []
-    launches0 = whv.whv_kernel_launches()
-    with ClockSampler(local) as clk:
-        time.sleep(0.5)                               # let the sampler start
-        barrier()
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push("timed")           # lets a profiler restrict itself to these steps
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(1.0)                      # evict the working set from L2
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            infos.append(solve())
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        barrier()
-    launches = whv.whv_kernel_launches() - launches0
-    clocks = clk.summary()
-    ms = aggregate_max(statistics.mean(times), world, device="cuda")
-    info = infos[-1]
-    lups = info["wave_solves"] * nt * w.n_unknowns
-    # accuracy of the timed configuration (outside the timed region): FP64 true residual and
-    # the error against an FP64-stepping solve of the same problem on the same GPU
-    prm_chk = whv.make_params(w.omega, method="cg", tol=tol, maxit=5000, true_residual=True,
-                              refine_fp64=fp32, residual_df64=fp32 and args.residual == "df64")
-    u_chk, info_chk = g.whv_solve(prm_chk, f)
-    accuracy = {"true_rel_residual": info_chk["true_rel_residual"],
-                "true_residual_check": "FP64 wave solves",
-                "correction_residuals": ("fp64" if not fp32 else
-                                         "df64 (pairs of FP32)" if args.residual == "df64" else "fp64")}
-    if args.precision == "fp32":
-        g64 = whv.Grid(w.npts, precision=whv.WHV_FP64, stream=stream)
-        prm64 = whv.make_params(w.omega, method="cg", tol=1e-11, maxit=5000)
-        g64.whv_set_deflation_basis(prm64, w.nd, whv.WHV_BASIS_CLOSED_FORM)
-        u64, _ = g64.whv_solve(prm64, f)
-        accuracy["rel_max_err_vs_fp64_solve"] = float((u_chk - u64).abs().max() / u64.abs().max())
-        g64.close()
-    glups_solve = lups / (ms * 1e-3) / 1e9
-
-    # ------------------------------------------------------------------ e2e: host buffers
-    e2e_times = []
-    for k in range(args.steps + 1):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)
-            e0.record(stream)
-            f.copy_(f_host, non_blocking=True)
-        g.whv_solve(prm, f, u)
-        with torch.cuda.stream(stream):
-            u_host.copy_(u, non_blocking=True)
-            e1.record(stream)
-        e1.synchronize()
-        if k > 0:
-            e2e_times.append(e0.elapsed_time(e1))
-    e2e_ms = statistics.mean(e2e_times)
-
-    # ------------------------------------------------------------------ dominant kernel
-    # the leapfrog+filter kernel of the timed solve's wave solves -- k_block2d (k steps per launch)
-    # when the autotuner picked k > 1, else k_step: average time per leapfrog step over replays of
-    # the same wave-solve graph, timed with events on the launching stream right after the timed
-    # region; algorithmic bytes = 5 s per LUP (read W^n, W^{n-1}, acc; write W^{n+1}, acc) times
-    # the k N LUPs one launch advances
-    reps = 20
-    v = torch.randn(w.n_unknowns, dtype=torch.float64, device="cuda")
-    out = torch.empty_like(v)
-    torch.cuda.synchronize()
-    g.whv_apply_pi(prm, v, None, out)
-    stream.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        g.whv_apply_pi(prm, v, None, out)
-    e1.record(stream)
-    e1.synchronize()
-    t_step = e0.elapsed_time(e1) * 1e-3 / (reps * nt)
-    esz = 4 if args.precision == "fp32" else 8
-    bytes_per_lup = 5 * esz                          # read W^n, W^{n-1}, acc; write W^{n+1}, acc
-    achieved = bytes_per_lup * w.n_unknowns / t_step / 1e9
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    peak = peaks.get("hbm_gbs", 6400.0)
-    kname = "k_block2d" if ksweep > 1 else "k_step"
-    kdesc = (f"k_block2d ({ksweep} fused leapfrog steps + trapezoid filter per launch)" if ksweep > 1
-             else "k_step (fused leapfrog step + trapezoid filter)")
-    traffic = traffic_for(kname, args.precision)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": kdesc,
-            "bytes_per_lup": bytes_per_lup, "lups_per_launch": w.n_unknowns * max(1, ksweep),
-            "launch_us": t_step * max(1, ksweep) * 1e6, "step_us": t_step * 1e6,
-            "glups": w.n_unknowns / t_step / 1e9,
-            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "note": "the 511^2 state (3 arrays, 3 MB) stays resident in the 126 MB L2 during a wave solve"}
-
-    # ------------------------------------------------------------------ HBM-bound stencil
-    # the 3-D 256^3 grid (66 MB per FP32 array, 3 arrays > L2): f = 0 wave solves of the
-    # 7-point z-marching step kernel, the case on which the HBM fraction is meaningful
-    g3 = whv.Grid((256, 256, 256), precision=whv.WHV_FP32_STEP, stream=stream)
-    prm3 = whv.make_params(40.0)
-    nt3 = g3.whv_time_grid(prm3)["nt"]
-    v3 = torch.randn(g3.N, dtype=torch.float64, device="cuda")
-    o3 = torch.empty_like(v3)
-    torch.cuda.synchronize()
-
-    def time_3d(k):
-        g3.whv_set_steps_per_sweep(k)
-        g3.whv_apply_pi(prm3, v3, None, o3)
-        stream.synchronize()
-        reps3 = 5
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps3):
-            g3.whv_apply_pi(prm3, v3, None, o3)
-        e1.record(stream)
-        e1.synchronize()
-        # per step: the first-step kernel's share is 1/nt of the launches; the wave-solve mean
-        return e0.elapsed_time(e1) * 1e-3 / (reps3 * nt3)
-
-    t31 = time_3d(1)    # k_step3d, one step per launch
-    t32 = time_3d(2)    # k_step3d2, two steps per launch
-    ach31, ach32 = 20 * g3.N / t31 / 1e9, 20 * g3.N / t32 / 1e9
-    stencil_hbm = {"kernel": "k_step3d2 (3-D 7-point, two leapfrog steps + filter per launch, FP32)",
-                   "workload": "256^3 nodes (254^3 unknowns), omega=40, f = 0 wave solves, nt=%d" % nt3,
-                   "bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s", "frac": ach32 / peak,
-                   "bytes_per_lup": 20, "glups": g3.N / t32 / 1e9, "step_us": t32 * 1e6,
-                   "own_bytes_per_lup": 12, "own_frac": 12 * g3.N / t32 / 1e9 / peak,
-                   "traffic": traffic_for("k_step3d2", "fp32"), "traffic_unit": "DRAM bytes per launch (2 steps)",
-                   "note": "achieved/frac count the 20 B per LUP of single-step streaming (equivalent "
-                           "bandwidth); own_frac counts the 12 B per LUP the two-step kernel must move",
-                   "single_step": {"kernel": "k_step3d (one step per launch)", "achieved": ach31,
-                                   "frac": ach31 / peak, "glups": g3.N / t31 / 1e9, "step_us": t31 * 1e6,
-                                   "traffic": traffic_for("k_step3d", "fp32")}}
-    g3.close()
-    del v3, o3
-
-    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-            "krylov_dtype": "f64", "data": "synthetic",
-            "config": dict(config_dict(w, tol, args.precision, nt, world), steps_per_sweep=ksweep,
-                           check_every=args.check_every,
-                           correction_residuals=("df64" if fp32 and args.residual == "df64" else "fp64")),
-            "iterations": info["iterations"], "wave_solves": info["wave_solves"],
-            "rel_residual": info["rel_residual"], "glups_solve": glups_solve, "accuracy": accuracy,
-            "outer_iterations": info.get("outer_iterations", 0), "wave_solves_fp64": info.get("wave_solves_fp64", 0),
-            "roofline": roof, "stencil_hbm": stencil_hbm,
-            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": w.n_unknowns * 8,
-                    "d2h_bytes_per_step": w.n_unknowns * 8},
-            "gpu_launches": launches, "clocks": clocks}
-
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = oracle_sample(w, tol, info["iterations"])
-        line["cpu_baseline"] = {"value": cb["solve_s"] * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
-                                "sample": f"oracle (numpy FP64, 1 thread): b wave solve + {cb['k']} CG iterations, "
-                                          f"extrapolated to the GPU's {info['iterations']} iterations"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    g.close()
-    if world > 1:
-        dist.destroy_process_group()
-    return 0
+    if args.workload == "c4":
+        return run_c4(args)
+    if args.workload == "c2":
+        return run_c2(args)
+    return run_workload(args)
 
 
 if __name__ == "__main__":

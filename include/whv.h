@@ -208,6 +208,20 @@ whv_status whv_lanczos_restarted(whv_grid grid, const whv_params* p, int nd, int
                                  double tol, const double* v0_dev, int fp64_stepping, int flags,
                                  double* theta_host, double* resid_host, int* stats_host);
 
+/* Share src's deflation basis with dst (no copy of the vectors): the many-right-hand-side use of
+ * one eigenvector set (Sec. 4.1: the set-up is paid once and amortised over all forcings).  dst
+ * takes src's vectors, eigenvalues, mode tuples, flags and the frequency / time grid they were
+ * built for; the vector storage is reference-counted and freed with the last grid that uses it,
+ * so either grid may be destroyed or get a new basis later.  Both grids must have the same box,
+ * node counts, order and speed: both c = 1, or both the same c^2 (compared bit for bit on the
+ * device; the basis is M-orthonormal for that c^2); conservative-form grids cannot share.  src
+ * needs a dense basis (not SVD-compressed).  What a grid derives from its basis for Algorithm 4
+ * (A W) or Algorithm 5 (the QR of A W) stays per grid.  whv_solve_batched contracts the
+ * problems that share one basis together: each deflation projection W^T M [r_1 ... r_k] and
+ * expansion [u_1 ... u_k] += W Y reads W once.  Allocates nd doubles of scratch in dst;
+ * synchronises both grids' streams. */
+whv_status whv_share_basis(whv_grid dst, whv_grid src);
+
 /* Read back the basis: nd (host), the mode tuples (host int[nd*dim], closed form only; else
  * zeros), lambda^2 (host double[nd]) and the vectors (device double[N*nd]); any output may be NULL. */
 whv_status whv_get_basis(whv_grid grid, int* nd, int* modes_host, double* lambda2_host, double* V_dev);
@@ -257,8 +271,14 @@ whv_status whv_autotune(whv_grid grid, const whv_params* p, int* best);
  * eigenvector set-up, Sec. 4.1): column j of F_dev (N doubles at F_dev + j ld, device) is solved
  * into U_dev + j ld exactly as whv_solve(grid, p, ., use_guess, ., infos + j) would; the basis and
  * everything built from it (A W, QR factors, captured graphs, the device CG loop) is reused.
- * infos (host, nrhs entries) may be NULL.  ld >= N.  Returns WHV_ERR_NOT_CONVERGED if a column
- * missed its tolerance (all columns are still solved), any other error at once. */
+ * With DEVD on a dense basis (FPI / CG / GMRES; no WHV_REFINE_FP64, no WHV_TRUE_RESIDUAL,
+ * use_guess = 0, nrhs > 1) the deflation of Algorithm 2 is done for all columns at once: the
+ * projection W^T M F, the deflated forcings F - W C (written into U_dev, whose columns then
+ * receive the solutions in place) and the inflation each read W once for all columns; temporary
+ * device memory nd (nrhs + 1) + ceil(N / 512) nd nrhs doubles.  Results equal the column-by-column
+ * solves up to rounding.  infos (host, nrhs entries) may be NULL.  ld >= N; F_dev and U_dev must not
+ * overlap.  Returns WHV_ERR_NOT_CONVERGED if a column missed its tolerance (all columns are still
+ * solved), any other error at once. */
 whv_status whv_solve_many(whv_grid grid, const whv_params* p, int nrhs, int64_t ld, const double* F_dev,
                           int use_guess, double* U_dev, whv_info* infos);
 
@@ -279,6 +299,22 @@ whv_status whv_solve_many(whv_grid grid, const whv_params* p, int nrhs, int64_t 
 whv_status whv_solve_adjoint(whv_grid grid, const whv_params* p, const double* f_dev, const double* u_dev,
                              const double* dLdu_dev, double* z_dev, double* grad_c2_dev,
                              double* grad_f_dev, int checkpoint_every, whv_info* info);
+
+/* Vector-Jacobian product of out = Pi_h(v; f, c^2) -- the reverse (transposed) sweep of one wave
+ * solve on its own, the building block of whv_solve_adjoint (eq. discreteWaveExplicit and
+ * eq. quadrature transposed step by step).  For the seed abar_dev (N doubles):
+ *  - vbar_dev  (out, nullable) = S_h^T abar, by S_h^T = M S_h M^{-1} (M = diag(1/c^2)): one forward
+ *    wave solve of c^2 abar, divided by c^2;
+ *  - c2bar_dev (out, nullable) = abar^T dPi_h(v; f, c^2)/dc^2 and fbar_dev (out, nullable) =
+ *    abar^T dPi_h/df: the leapfrog run backwards from the filter weights times abar, with the
+ *    forward states from v checkpointed every checkpoint_every (<= 0: 16) steps and recomputed
+ *    per segment; temporary device memory (2 ceil(Nt/K) + K + 5) N elements.
+ * Steps in the grid's precision, or in FP64 when p->flags has WHV_REFINE_FP64 (FP32 grids; the
+ * gradient sums are FP64 either way).  f_dev NULL = 0.  vbar_dev must not alias v_dev or abar_dev.
+ * The time grid (dt, Nt) is held fixed.  Synchronises the grid's stream. */
+whv_status whv_apply_pi_vjp(whv_grid grid, const whv_params* p, const double* v_dev, const double* f_dev,
+                            const double* abar_dev, double* vbar_dev, double* c2bar_dev, double* fbar_dev,
+                            int checkpoint_every);
 
 /* Batched solve of nprob (<= 1024) independent problems (right-hand sides, frequencies, grids of uneven
  * size): problem p is grids[p] with params[p] and forcing f_dev[p] (N_p doubles, device), its
@@ -304,6 +340,17 @@ whv_status whv_solve_adjoint(whv_grid grid, const whv_params* p, const double* f
  * WHV_ERR_BREAKDOWN if a problem's CG broke down. */
 whv_status whv_solve_batched(int nprob, const whv_grid* grids, const whv_params* params,
                              const double* const* f_dev, double* const* u_dev, whv_info* infos);
+
+/* Batched wave solve: out_dev[p] = Pi_h(v_dev[p]; f_dev[p]) (whv_apply_pi for every problem) in ONE
+ * persistent cooperative launch -- the batched wave solve each iteration of whv_solve_batched
+ * runs (2-D: k leapfrog steps per sweep in shared-memory tiles, k as in whv_solve_batched; 3-D:
+ * one step per sweep; grid barriers between sweeps).  Same restrictions on the grids as
+ * whv_solve_batched; v_dev / f_dev may be NULL (all zero), as may any of their entries; out_dev
+ * entries are N_p doubles each and must not alias v_dev / f_dev entries.  Uses the grids'
+ * stepping buffers; temporary device memory: the descriptor tables (a few KB).  Synchronises the
+ * shared stream; WHV_ERR_TIMEOUT if a grid barrier gave up. */
+whv_status whv_apply_pi_batched(int nprob, const whv_grid* grids, const whv_params* params,
+                                const double* const* v_dev, const double* const* f_dev, double* const* out_dev);
 
 /* Autotuner of the batched steps per sweep (2-D grids): times one persistent batched f = 0 wave
  * solve of all nprob problems for k = 2, 4, 6, 8, 10, 12 (CUDA events on the shared stream, after a

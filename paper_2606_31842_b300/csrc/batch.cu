@@ -31,9 +31,12 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda.h>   // CUtensorMap and its encoding enums (the encoder is fetched through the runtime)
+
 #include "df64.cuh"
 #include "stencil_ops.cuh"
 #include "quad2d.cuh"
+#include "tma.cuh"
 #include "whv_device.cuh"
 #include "whv_internal.cuh"
 
@@ -271,7 +274,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d(const BTile<T>* 
           prv[r] = in ? __ldcg(B.w[2 * qi] + gi) : T(0);
         }
         if (VARC) cc[r] = in ? __ldg(B.c2 + gi) : T(0);
-        if (FORCED) ff[r] = in ? (T)__ldg(B.f + gi) : T(0);
+        if (FORCED) ff[r] = (in && B.f) ? (T)__ldg(B.f + gi) : T(0);
         // the filter sum so far of the tile cells, loaded with the state (no read-modify-write
         // round trip at the end)
         const int jr = jb + kBPitch * r;
@@ -484,7 +487,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d_df(const BTile<d
           prv[r] = dfl{p2v.x, p2v.y};
           acr[r] = dfl{a2v.x, a2v.y};
         }
-        if (FORCED) ff[r] = in ? df_from(__ldg(B.f + gi)) : df_zero();
+        if (FORCED) ff[r] = (in && B.f) ? df_from(__ldg(B.f + gi)) : df_zero();
       }
 #pragma unroll
       for (int r = 0; r < kBRows; ++r) S0[(jb + kBPitch * r) * kBReg + i] = cur[r];
@@ -560,6 +563,225 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d_df(const BTile<d
   }
 }
 
+// ------------------------------------------------------------------ 2-D, FP32, TMA-fed
+// The f = 0 FP32 wave solve of the 5-point stencil with c = 1 -- every A p of the batched CG
+// loop -- with the state in row-padded buffers (pitch a multiple of 4 floats), so that the copy
+// engine can move it: for every work item after the first sweep, one thread issues three tiled
+// TMA copies (the 64 x 64 region of W^n and of W^{n-1} with a k-wide halo, out-of-domain cells
+// read as 0, and the (64 - 2k)^2 tile of filter sums) into one of two shared-memory stages while
+// the CTA steps the previous item in the other stage; the sub-steps run in the four-cell mapping
+// of quad2d.cuh on the staged buffers; the tile's new state goes from registers straight to
+// global memory as 16-byte stores.  The first sweep reads v (FP64) directly, the last writes the
+// FP64 output (and p^T M q partials).  k is a multiple of 4 (the region's x origin tile*TW - k
+// must be 16-byte aligned for the copy engine).  Same operations in the same order as
+// k_batch_block2d's four-cell path.
+struct BTileT {
+  float* w[4];           // pitched (W^{n-1}, W^n) pairs: sweep j writes pair j & 1
+  float* acc;            // pitched filter sums
+  const double* v;       // W^0 (nullptr: 0)
+  double* out;           // epi 0: Pi_h v;  epi 1: v - Pi_h v
+  const double* mw;      // M weights (nullptr: 1)
+  double* partials;      // epi 1: per-tile partial sums of <v, out>_M
+  const double* halt;    // problem stopped when *halt != 0 (nullptr: never)
+  int64_t tile0;
+  int nx, ny, nt, tiles_x, ntiles, epi, wofs, pitch;
+  float ax, ay, b, ih2x, ih2y, dt2;
+};
+
+struct BMaps {           // tensor maps of one problem's pitched buffers
+  CUtensorMap w[4];      // 64 x 64 boxes
+  CUtensorMap acc;       // (64 - 2k)^2 boxes
+};
+
+constexpr uint32_t kMbarPolls = 1u << 22;   // bound on the polls of one stage's mbarrier
+
+template <int K>
+struct TmaLayout {
+  static constexpr int TW = kBReg - 2 * K;
+  static constexpr int kRegion = kBReg * kBReg * 4;             // bytes of one 64 x 64 FP32 box
+  static constexpr int kAcc = TW * TW * 4;
+  static constexpr int kStage = ((2 * kRegion + kAcc) + 1023) / 1024 * 1024;
+  static constexpr int kSmem = 2 * kStage + 1024;               // + alignment slack
+  static constexpr uint32_t kTx = 2 * kRegion + kAcc;          // bytes one item's copies deliver
+};
+
+// next work item of this CTA at or after `item` (stepping by gridDim.x) whose problem is running;
+// p is advanced to that item's problem
+__device__ __forceinline__ int64_t tma_live_item(int64_t item, int& p, int64_t total, const int64_t* s_tile0,
+                                                 const BTileT* __restrict__ P) {
+  while (item < total) {
+    while (s_tile0[p + 1] <= item) ++p;
+    const double* h = P[p].halt;
+    if (!h || *h == 0.0) return item;
+    item = skip_to(item, s_tile0[p + 1]) + gridDim.x;
+  }
+  return item;
+}
+
+template <int K>
+__device__ __forceinline__ void tma_issue(const BMaps* __restrict__ M, const BTileT* __restrict__ P, int p,
+                                          int64_t item, int qi, unsigned char* stage, uint64_t* bar) {
+  using L = TmaLayout<K>;
+  const int t = (int)(item - P[p].tile0);
+  const int tx = t % P[p].tiles_x, ty = t / P[p].tiles_x;
+  mbar_arrive_expect_tx(bar, L::kTx);
+  tma_load_2d(stage, &M[p].w[2 * qi + 1], tx * L::TW - K, ty * L::TW - K, bar);             // W^n
+  tma_load_2d(stage + L::kRegion, &M[p].w[2 * qi], tx * L::TW - K, ty * L::TW - K, bar);    // W^{n-1}
+  tma_load_2d(stage + 2 * L::kRegion, &M[p].acc, tx * L::TW, ty * L::TW, bar);             // filter sums
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBThreads, 1) k_batch_tma(const BTileT* __restrict__ P, const BMaps* __restrict__ M,
+                                                            const int* __restrict__ nact, int J,
+                                                            const float* __restrict__ wtab, unsigned* bar_count,
+                                                            unsigned* bar_gen, int* err) {
+  using L = TmaLayout<K>;
+  constexpr int TW = L::TW;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* const base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ int64_t s_tile0[kBatchMaxProblems + 1];
+  __shared__ BTileT sB;
+  __shared__ float sw[16];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  // the CTA's next work item and its problem, written by thread 0 into the slot of the stage it
+  // will use and read by all after the barrier that ends the current item (two slots: a slot is
+  // rewritten only after every thread has passed the barrier that follows its last read)
+  __shared__ int64_t s_item[2];
+  __shared__ int s_p[2];
+  const int np = nact[0];
+  for (int p = threadIdx.x; p <= np; p += blockDim.x)
+    s_tile0[p] = p < np ? P[p].tile0 : P[np - 1].tile0 + P[np - 1].ntiles;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint32_t parity[2] = {0u, 0u};
+  const int row = threadIdx.x >> 4, col = (threadIdx.x & 15) * 4;
+  const int off = row * kBReg + col;
+  const bool trow = row >= K && row < kBReg - K, tcol = col >= K && col < kBReg - K;
+  const int aoff = (row - K) * TW + (col - K);   // filter-sum box offset (tile cells only)
+  for (int j = 0; j < J; ++j) {
+    const int A = nact[j];
+    const int64_t total = s_tile0[A];
+    const int qi = (j + 1) & 1, qo = j & 1;   // input pair (written by sweep j - 1), output pair
+    int stage = 0;
+    if (threadIdx.x == 0) {
+      if (j > 0) fence_proxy_async_global();   // the previous sweep's stores (all CTAs) before the copies
+      int p = 0;
+      const int64_t it = tma_live_item(blockIdx.x, p, total, s_tile0, P);
+      s_item[0] = it;
+      s_p[0] = p;
+      if (j > 0 && it < total) tma_issue<K>(M, P, p, it, qi, base, &s_bar[0]);
+    }
+    __syncthreads();
+    int64_t item = s_item[0];
+    int p = s_p[0], cur_p = -1;
+    while (item < total) {
+      if (p != cur_p) {
+        if (threadIdx.x == 0) sB = P[p];
+        __syncthreads();
+        cur_p = p;
+      }
+      const BTileT& B = sB;
+      unsigned char* const st = base + stage * L::kStage;
+      float* const SA = reinterpret_cast<float*>(st);
+      float* const SB = reinterpret_cast<float*>(st + L::kRegion);
+      const float* const SC = reinterpret_cast<const float*>(st + 2 * L::kRegion);
+      // the next item's copies into the other stage (free: its item ended with a barrier)
+      if (threadIdx.x == 0) {
+        int pn = p;
+        const int64_t nit = tma_live_item(item + gridDim.x, pn, total, s_tile0, P);
+        s_item[stage ^ 1] = nit;
+        s_p[stage ^ 1] = pn;
+        if (j > 0 && nit < total) tma_issue<K>(M, P, pn, nit, qi, base + (stage ^ 1) * L::kStage, &s_bar[stage ^ 1]);
+      }
+      const int t = (int)(item - B.tile0);
+      const int x0 = (t % B.tiles_x) * TW - K, y0 = (t / B.tiles_x) * TW - K;
+      const int nx = B.nx, ny = B.ny;
+      const int n0 = j * K;
+      const int kk = min(K, B.nt - n0);
+      const bool first = j == 0, last = n0 + kk == B.nt;
+      const float* wtb = wtab + B.wofs;
+      if (threadIdx.x < kk) sw[threadIdx.x] = wtb[n0 + 1 + threadIdx.x];
+      const int gy = y0 + row, gx = x0 + col;
+      float4 c, w, a;
+      if (first) {   // W^0 = v (FP64, unpadded rows), W^{-1} unused (Taylor start), sums w_0 W^0
+        const float w0 = wtb[0];
+        float cv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const bool in = gy >= 0 && gy < ny && gx + e >= 0 && gx + e < nx && B.v;
+          cv[e] = in ? (float)__ldg(B.v + (gx + e) + (int64_t)nx * gy) : 0.0f;
+        }
+        c = make_float4(cv[0], cv[1], cv[2], cv[3]);
+        w = make_float4(0.f, 0.f, 0.f, 0.f);
+        a = make_float4(w0 * c.x, w0 * c.y, w0 * c.z, w0 * c.w);
+        q_sts(SA, off, c);
+      } else {
+        const bool ok = mbar_wait(&s_bar[stage], parity[stage], kMbarPolls);
+        if (__syncthreads_or(!ok)) {   // the copies did not arrive: give up (bounded)
+          if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            mbar_wait(&s_bar[stage ^ 1], parity[stage ^ 1], kMbarPolls);   // drain what may be in flight
+          }
+          __syncthreads();
+          return;
+        }
+        parity[stage] ^= 1u;
+        c = q_lds(SA, off);
+        w = q_lds(SB, off);
+        a = (trow && tcol) ? *reinterpret_cast<const float4*>(SC + aoff) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      const QuadCoef q{B.ax, B.ay, B.b, B.ih2x, B.ih2y, 0.5f * B.dt2};
+      const bool inside = x0 >= 0 && y0 >= 0 && x0 + kBReg <= nx && y0 + kBReg <= ny;
+      const unsigned m = inside ? 0xfu : quad_mask(x0, y0, nx, ny);
+      if (first) {
+        if (inside) quad_steps<false, true>(c, w, a, SA, SB, kk, sw, q, m);
+        else quad_steps<true, true>(c, w, a, SA, SB, kk, sw, q, m);
+      } else {
+        if (inside) quad_steps<false, false>(c, w, a, SA, SB, kk, sw, q, m);
+        else quad_steps<true, false>(c, w, a, SA, SB, kk, sw, q, m);
+      }
+      double part = 0.0;
+      if (trow && tcol && gy < ny && gx < nx) {
+        if (!last) {   // 16-byte stores of the tile's new state (padding columns take zeros)
+          const int64_t gi = gx + (int64_t)B.pitch * gy;
+          *reinterpret_cast<float4*>(B.w[2 * qo + 1] + gi) = c;
+          *reinterpret_cast<float4*>(B.w[2 * qo] + gi) = w;
+          *reinterpret_cast<float4*>(B.acc + gi) = a;
+        } else {
+          const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (gx + e >= nx) break;
+            const int64_t gi = gx + e + (int64_t)nx * gy;
+            if (B.epi == 0) {
+              B.out[gi] = (double)av[e];
+            } else {
+              const double vi = __ldg(B.v + gi);
+              const double o = vi - (double)av[e];
+              B.out[gi] = o;
+              part = fma(B.mw ? vi * __ldg(B.mw + gi) : vi, o, part);
+            }
+          }
+        }
+      }
+      if (last && B.epi == 1) {   // uniform per CTA (one problem per item)
+        part = block_sum(part);
+        if (threadIdx.x == 0) B.partials[t] = part;
+      }
+      __syncthreads();   // this stage is free again; the other slot holds the next item
+      stage ^= 1;
+      item = s_item[stage];
+      p = s_p[stage];
+    }
+    fence_proxy_async_global();   // this sweep's stores before other CTAs' copies of the next sweep
+    if (!grid_barrier(bar_count, bar_gen, err, gridDim.x)) return;
+  }
+}
+
 // ------------------------------------------------------------------ per-problem small kernels
 struct BFin {
   const double* partials;
@@ -603,6 +825,7 @@ __global__ void k_batch_any(cudaGraphConditionalHandle h, double* const* __restr
 // device descriptor table and the launcher of the kernel variant it needs.
 struct Wave {
   void* desc = nullptr;
+  void* maps = nullptr;        // tensor maps (TMA-fed role)
   int* nact = nullptr;
   void* wtab = nullptr;
   void* ptab = nullptr;
@@ -744,6 +967,163 @@ static cudaError_t launch_block2d_df(cudaStream_t st, const Wave& w, unsigned* b
                                      w.smem, st);
 }
 
+// ------------------------------------------------------------------ TMA-fed role (host)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, fetched once through the runtime (no link to libcuda)
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// The TMA-fed kernel serves the FP32 f = 0 roles of 2-D second-order c = 1 batches when k is a
+// multiple of 4 (4, 8, 12); WHV_BATCH_TMA=0 in the environment selects k_batch_block2d instead
+// (a diagnostic switch: both give the same results bit for bit).
+static bool tma_role(int K, bool forced) {
+  static const int env = [] { const char* e = getenv("WHV_BATCH_TMA"); return e ? atoi(e) : 1; }();
+  return env != 0 && !forced && K >= 4 && K <= 12 && K % 4 == 0 && encode_tiled() != nullptr;
+}
+
+template <int K>
+static cudaError_t launch_tma(cudaStream_t st, const Wave& w, unsigned* bar, int* err) {
+  const BTileT* P = (const BTileT*)w.desc;
+  const BMaps* M = (const BMaps*)w.maps;
+  const float* wt = (const float*)w.wtab;
+  unsigned* bc = bar;
+  unsigned* bg = bar + 1;
+  int J = w.J;
+  const int* na = w.nact;
+  void* args[] = {(void*)&P, (void*)&M, (void*)&na, (void*)&J, (void*)&wt, (void*)&bc, (void*)&bg, (void*)&err};
+  return cudaLaunchCooperativeKernel((const void*)k_batch_tma<K>, dim3(w.nblocks), dim3(kBThreads), args, w.smem, st);
+}
+
+template <int K>
+static cudaError_t tma_prepare(int* per_sm) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_batch_tma<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               TmaLayout<K>::kSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_tma<K>, kBThreads, TmaLayout<K>::kSmem);
+}
+
+// pitched FP32 state buffers of a 2-D grid (rows padded to a multiple of 4 floats), on first use
+static whv_status ensure_tma_buffers(whv_grid g) {
+  if (g->tacc) return WHV_OK;
+  const int pitch = (g->n[0] + 3) / 4 * 4;
+  const size_t bytes = (size_t)pitch * g->n[1] * sizeof(float);
+  for (int m = 0; m < 4; ++m) {
+    WHV_CUDA(g, cudaMalloc(&g->tw[m], bytes));
+    WHV_CUDA(g, cudaMemsetAsync(g->tw[m], 0, bytes, g->stream));
+  }
+  WHV_CUDA(g, cudaMalloc(&g->tacc, bytes));
+  WHV_CUDA(g, cudaMemsetAsync(g->tacc, 0, bytes, g->stream));
+  g->tpitch = pitch;
+  return WHV_OK;
+}
+
+static bool encode_box(CUtensorMap* map, float* base, int nx, int ny, int pitch, int box) {
+  const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+  const cuuint32_t boxd[2] = {(cuuint32_t)box, (cuuint32_t)box};
+  const cuuint32_t es[2] = {1, 1};
+  return encode_tiled()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, boxd, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// descriptor and tensor-map tables of the TMA-fed role; problems ordered by sweeps (descending)
+static whv_status make_wave_tma(BatchCtx& c, const RoleIO& io, int K, Wave* out) {
+  const int np = c.np;
+  Wave w;
+  w.K = K;
+  std::vector<int> order(np), nsw(np);
+  for (int p = 0; p < np; ++p) nsw[p] = (c.tgs[p].nt + K - 1) / K;
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nsw[a] > nsw[b]; });
+  w.J = nsw[order[0]];
+  const int TW = kBReg - 2 * K;
+  std::vector<float> wtab;
+  std::vector<BFin> fin(np);
+  std::vector<BTileT> d(np);
+  std::vector<BMaps> maps(np);
+  int64_t tile0 = 0;
+  for (int k = 0; k < np; ++k) {
+    const int p = order[k];
+    whv_grid g = c.grids[p];
+    const TimeGridH& tg = c.tgs[p];
+    TRY(ensure_tma_buffers(g));
+    const int wofs = (int)wtab.size();
+    for (int n = 0; n <= tg.nt; ++n) wtab.push_back((float)tg.weight[n]);
+    const double h2x = g->h[0] * g->h[0], h2y = g->h[1] * g->h[1];
+    BTileT B{};
+    for (int m = 0; m < 4; ++m) B.w[m] = g->tw[m];
+    B.acc = g->tacc;
+    B.v = io.v[p]; B.out = io.out[p];
+    B.mw = g->mw; B.partials = chan(g, CH_STEP);
+    B.halt = io.halt ? g->scal + S_HALT : nullptr;
+    B.nx = g->n[0]; B.ny = g->n[1]; B.nt = tg.nt; B.pitch = g->tpitch;
+    B.tiles_x = (g->n[0] + TW - 1) / TW;
+    B.ntiles = B.tiles_x * ((g->n[1] + TW - 1) / TW);
+    B.epi = io.epi; B.wofs = wofs;
+    B.ih2x = (float)(1.0 / h2x);
+    B.ih2y = (float)(1.0 / h2y);
+    B.dt2 = (float)(tg.dt * tg.dt);
+    const double ax = tg.dt * tg.dt / h2x, ay = tg.dt * tg.dt / h2y;
+    B.ax = (float)ax; B.ay = (float)ay; B.b = (float)(2.0 - 2.0 * (ax + ay));
+    B.tile0 = tile0;
+    for (int m = 0; m < 4; ++m)
+      if (!encode_box(&maps[k].w[m], g->tw[m], g->n[0], g->n[1], g->tpitch, kBReg))
+        return fail(c.g0, WHV_ERR_CUDA, "batched: cuTensorMapEncodeTiled failed (state buffers)");
+    if (!encode_box(&maps[k].acc, g->tacc, g->n[0], g->n[1], g->tpitch, TW))
+      return fail(c.g0, WHV_ERR_CUDA, "batched: cuTensorMapEncodeTiled failed (filter sums)");
+    if (io.epi == 1 && B.ntiles > chan_cap(g, CH_STEP))
+      return fail(c.g0, WHV_ERR_INVALID, "batched: grid too large for its reduction channel");
+    fin[k] = BFin{chan(g, CH_STEP), io.halt ? g->scal + S_HALT : nullptr, g->scal, B.ntiles};
+    d[k] = B;
+    tile0 += B.ntiles;
+  }
+  std::vector<int> nact(w.J);
+  for (int j = 0; j < w.J; ++j) {
+    int a = 0;
+    while (a < np && nsw[order[a]] > j) ++a;
+    nact[j] = a;
+  }
+  B_CUDA(c.g0, c.alloc(&w.desc, np * sizeof(BTileT)));
+  B_CUDA(c.g0, c.alloc(&w.maps, np * sizeof(BMaps)));
+  B_CUDA(c.g0, c.alloc(&w.nact, w.J * sizeof(int)));
+  B_CUDA(c.g0, c.alloc(&w.wtab, wtab.size() * sizeof(float)));
+  B_CUDA(c.g0, c.alloc(&w.fin, np * sizeof(BFin)));
+  B_CUDA(c.g0, cudaMemcpy(w.desc, d.data(), np * sizeof(BTileT), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.maps, maps.data(), np * sizeof(BMaps), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.nact, nact.data(), w.J * sizeof(int), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.wtab, wtab.data(), wtab.size() * sizeof(float), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.fin, fin.data(), np * sizeof(BFin), cudaMemcpyHostToDevice));
+  int per_sm = 0;
+  switch (K) {
+    case 4: B_CUDA(c.g0, tma_prepare<4>(&per_sm)); w.launch = &launch_tma<4>; w.smem = TmaLayout<4>::kSmem; break;
+    case 8: B_CUDA(c.g0, tma_prepare<8>(&per_sm)); w.launch = &launch_tma<8>; w.smem = TmaLayout<8>::kSmem; break;
+    default: B_CUDA(c.g0, tma_prepare<12>(&per_sm)); w.launch = &launch_tma<12>; w.smem = TmaLayout<12>::kSmem; break;
+  }
+  if (per_sm < 1) return fail(c.g0, WHV_ERR_INVALID, "batched: kernel cannot be resident on an SM");
+  w.nblocks = (int)std::min<int64_t>((int64_t)per_sm * c.sms, std::max<int64_t>(tile0, 1));
+  *out = w;
+  return WHV_OK;
+}
+
 constexpr int kBDfK = 4;   // sub-steps per sweep of the double-float roles
 
 // Device tables of one role, stepping in T (double on an FP32 grid: its FP64 buffer set; dfl:
@@ -761,6 +1141,8 @@ static whv_status make_wave(BatchCtx& c, const RoleIO& io, Wave* out) {
   static_assert(!DF || (DIM == 2 && ORDER == 2 && !VARC), "double-float roles: 2-D, second order, c = 1");
   Wave w;
   w.K = DF ? kBDfK : (blocked ? batch_k(c.g0, fp64) : 1);
+  if constexpr (std::is_same<T, float>::value && DIM == 2 && ORDER == 2 && !VARC)
+    if (tma_role(w.K, forced)) return make_wave_tma(c, io, w.K, out);
   std::vector<int> order(np), nsw(np);
   for (int p = 0; p < np; ++p) nsw[p] = (c.tgs[p].nt + w.K - 1) / w.K;
   std::iota(order.begin(), order.end(), 0);
@@ -908,6 +1290,106 @@ static whv_status fetch_all(BatchCtx& c) {
   return WHV_OK;
 }
 
+// Problems whose grids share one dense basis (whv_share_basis) form a group: its deflation
+// projections and expansions are single contractions over the group's right-hand sides, reading
+// the basis once (project_many / expand_many).  A grid with its own basis is a group of one;
+// SVD-compressed bases take the per-problem contractions.
+struct BasisGroup {
+  const double* V = nullptr;
+  int nd = 0;
+  int64_t N = 0;
+  const double* mw = nullptr;
+  std::vector<int> members;
+  double* C = nullptr;          // nd x k coefficients (column j = member j of the call)
+  double* s_inf = nullptr;      // 1 / (omega_eff^2 - lambda^2): DEVD inflation
+  double* s_mu = nullptr;       // 1 / mu: modal correction of the FP64 residual
+};
+
+struct Groups {
+  std::vector<BasisGroup> g;
+  std::vector<int> loose;       // problems with a compressed basis (per-problem contractions)
+  double* partials = nullptr;
+  const double** ptrs = nullptr;   // device: 2 np pointer slots
+  std::vector<const double*> hptrs;
+};
+
+static whv_status make_groups(BatchCtx& c, Groups* G) {
+  for (int p = 0; p < c.np; ++p) {
+    const Basis& B = c.grids[p]->basis;
+    if (B.nd == 0) continue;
+    if (!B.V) { G->loose.push_back(p); continue; }
+    BasisGroup* bg = nullptr;
+    for (auto& x : G->g)
+      if (x.V == B.V) bg = &x;
+    if (!bg) {
+      G->g.emplace_back();
+      bg = &G->g.back();
+      bg->V = B.V; bg->nd = B.nd; bg->N = c.grids[p]->N; bg->mw = c.grids[p]->mw;
+    }
+    bg->members.push_back(p);
+  }
+  int64_t scratch = 0;
+  for (auto& bg : G->g) {
+    const int k = (int)bg.members.size();
+    const whv_grid g = c.grids[bg.members[0]];
+    const Basis& B = g->basis;
+    const TimeGridH& tg = c.tgs[bg.members[0]];
+    scratch = std::max(scratch, project_many_scratch(bg.N, bg.nd, k));
+    B_CUDA(c.g0, c.alloc(&bg.C, (size_t)bg.nd * k * sizeof(double)));
+    B_CUDA(c.g0, c.alloc(&bg.s_inf, bg.nd * sizeof(double)));
+    B_CUDA(c.g0, c.alloc(&bg.s_mu, bg.nd * sizeof(double)));
+    std::vector<double> si(bg.nd), sm(bg.nd);
+    const double om2 = tg.omega_eff * tg.omega_eff;
+    for (int m = 0; m < bg.nd; ++m) {
+      si[m] = 1.0 / (om2 - B.lambda2[m]);
+      sm[m] = 1.0 / B.mu[m];
+    }
+    B_CUDA(c.g0, cudaMemcpy(bg.s_inf, si.data(), bg.nd * sizeof(double), cudaMemcpyHostToDevice));
+    B_CUDA(c.g0, cudaMemcpy(bg.s_mu, sm.data(), bg.nd * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if (!G->g.empty()) {
+    B_CUDA(c.g0, c.alloc(&G->partials, (size_t)scratch * sizeof(double)));
+    B_CUDA(c.g0, c.alloc(&G->ptrs, 2 * (size_t)c.np * sizeof(double*)));
+  }
+  return WHV_OK;
+}
+
+// the pointer slots as the output list of expand_many
+static double* const* out_ptrs(Groups& G) { return (double* const*)(void*)G.ptrs; }
+
+// upload the group's pointer lists a (slot 0) and b (slot 1): k entries each
+static whv_status group_ptrs(BatchCtx& c, Groups& G, const std::vector<const double*>& a,
+                             const std::vector<const double*>& b) {
+  G.hptrs.assign(2 * (size_t)c.np, nullptr);
+  std::copy(a.begin(), a.end(), G.hptrs.begin());
+  std::copy(b.begin(), b.end(), G.hptrs.begin() + c.np);
+  B_CUDA(c.g0, cudaMemcpyAsync(G.ptrs, G.hptrs.data(), 2 * (size_t)c.np * sizeof(double*), cudaMemcpyHostToDevice,
+                               c.st));
+  // pageable source: keep the copy ordered before the host reuses the vector
+  B_CUDA(c.g0, cudaStreamSynchronize(c.st));
+  return WHV_OK;
+}
+
+// For the members `who` of group bg: C = W^T M [in_j], then for each (alpha, scale, out) pass
+// out_j += alpha W diag(scale) C_j -- one read of W per contraction for all members.
+struct ExpandPass {
+  double alpha;
+  const double* scale;
+  std::vector<double*> out;
+};
+static whv_status group_contract(BatchCtx& c, Groups& G, const BasisGroup& bg, const std::vector<const double*>& in,
+                                 const std::vector<ExpandPass>& passes) {
+  const int k = (int)in.size();
+  if (k == 0) return WHV_OK;
+  TRY(group_ptrs(c, G, in, {}));
+  B_CUDA(c.g0, project_many(c.st, bg.V, bg.N, bg.nd, k, G.ptrs, bg.mw, G.partials, bg.C));
+  for (const ExpandPass& ps : passes) {
+    TRY(group_ptrs(c, G, std::vector<const double*>(ps.out.begin(), ps.out.end()), {}));
+    B_CUDA(c.g0, expand_many(c.st, bg.V, bg.N, bg.nd, k, bg.C, ps.scale, ps.alpha, out_ptrs(G)));
+  }
+  return WHV_OK;
+}
+
 // The batched CG loop, built for the A p role `ap`: one graph with a WHILE node (device-resident
 // loop), or -- with check_every > 1 -- a graph of one iteration that the host launches, testing
 // convergence every check_every iterations.
@@ -1038,24 +1520,35 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
   io_ap.halt = true;
   Wave ap;
   TRY(g64 ? (make_wave<double, DIM, ORDER, VARC>(c, io_ap, &ap)) : (make_wave<float, DIM, ORDER, VARC>(c, io_ap, &ap)));
-  CgGraph G;
-  TRY(build_cg_graph(c, ap, c.params[0].check_every, &G));
+  CgGraph CG;
+  TRY(build_cg_graph(c, ap, c.params[0].check_every, &CG));
+  Groups G;
+  TRY(make_groups(c, &G));
   std::vector<int> maxit(np);
   for (int p = 0; p < np; ++p) maxit[p] = c.params[p].maxit;
 
   if (!refine) {
     // DEVD (Algorithm 2): deflate each forcing, b = Pi_h(0; f_d) of all problems in one launch
-    std::vector<const double*> fd(np);
-    for (int p = 0; p < np; ++p) {
-      whv_grid g = c.grids[p];
-      const Basis& B = g->basis;
-      fd[p] = f_dev[p];
-      if (B.nd > 0) {
-        TRY(basis_project(g, f_dev[p], B.d_coef));
+    std::vector<const double*> fd(f_dev, f_dev + np);
+    for (const BasisGroup& bg : G.g) {   // f_d = f - W W^T M f, W read once per contraction
+      std::vector<const double*> in;
+      ExpandPass ps{-1.0, nullptr, {}};
+      for (int p : bg.members) {
+        whv_grid g = c.grids[p];
         TRY(copy_dev(g, g->fd, f_dev[p], g->N));
-        TRY(basis_expand(g, B.d_coef, -1.0, g->fd));
+        in.push_back(f_dev[p]);
+        ps.out.push_back(g->fd);
         fd[p] = g->fd;
       }
+      TRY(group_contract(c, G, bg, in, {ps}));
+    }
+    for (int p : G.loose) {
+      whv_grid g = c.grids[p];
+      const Basis& B = g->basis;
+      TRY(basis_project(g, f_dev[p], B.d_coef));
+      TRY(copy_dev(g, g->fd, f_dev[p], g->N));
+      TRY(basis_expand(g, B.d_coef, -1.0, g->fd));
+      fd[p] = g->fd;
     }
     RoleIO io_b;
     io_b.v.assign(np, nullptr);
@@ -1074,25 +1567,35 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
       stop[p] = c.params[p].tol * c.params[p].tol * bb[p];
     }
     const std::vector<const double*> rhs = c.each([](whv_grid g) { return (const double*)g->t; });
-    TRY(run_cg(c, G, rhs, bb, stop, maxit, active, &iters));
+    TRY(run_cg(c, CG, rhs, bb, stop, maxit, active, &iters));
     for (int p = 0; p < np; ++p) {
       whv_grid g = c.grids[p];
-      const Basis& B = g->basis;
       total_its[p] = iters[p];
       ws[p] = iters[p] + 1;
       rel[p] = bb[p] > 0 ? sqrt(g->scal_host[S_RR] / bb[p]) : 0.0;
       flag[p] = g->scal_host[S_FLAG] != 0.0;
       conv[p] = !flag[p] && rel[p] <= c.params[p].tol;
-      if (B.nd > 0) {   // inflate: u = x + W diag(1/(omega_eff^2 - lambda^2)) W^T M f
-        std::vector<double> cf(B.nd);
-        TRY(to_host(g, cf.data(), B.d_coef, B.nd));
-        const double om2 = c.tgs[p].omega_eff * c.tgs[p].omega_eff;
-        for (int m = 0; m < B.nd; ++m) cf[m] /= (om2 - B.lambda2[m]);
-        TRY(to_dev(g, g->small, cf.data(), B.nd));
-        TRY(basis_expand(g, g->small, 1.0, g->x));
-      }
-      TRY(copy_dev(g, u_dev[p], g->x, g->N));
     }
+    // inflate: u = x + W diag(1/(omega_eff^2 - lambda^2)) W^T M f (the group's C still holds
+    // W^T M f: the CG loop does not touch it)
+    for (const BasisGroup& bg : G.g) {
+      std::vector<double*> xs;
+      for (int p : bg.members) xs.push_back(c.grids[p]->x);
+      TRY(group_ptrs(c, G, std::vector<const double*>(xs.begin(), xs.end()), {}));
+      B_CUDA(c.g0, expand_many(c.st, bg.V, bg.N, bg.nd, (int)xs.size(), bg.C, bg.s_inf, 1.0,
+                               out_ptrs(G)));
+    }
+    for (int p : G.loose) {
+      whv_grid g = c.grids[p];
+      const Basis& B = g->basis;
+      std::vector<double> cf(B.nd);
+      TRY(to_host(g, cf.data(), B.d_coef, B.nd));
+      const double om2 = c.tgs[p].omega_eff * c.tgs[p].omega_eff;
+      for (int m = 0; m < B.nd; ++m) cf[m] /= (om2 - B.lambda2[m]);
+      TRY(to_dev(g, g->small, cf.data(), B.nd));
+      TRY(basis_expand(g, g->small, 1.0, g->x));
+    }
+    for (int p = 0; p < np; ++p) TRY(copy_dev(c.grids[p], u_dev[p], c.grids[p]->x, c.grids[p]->N));
   } else {
     // FP64 residual correction on the full system A u = b, b = Pi_h(0; f) in FP64
     for (int p = 0; p < np; ++p) TRY(ensure_fp64_buffers(c.grids[p]));
@@ -1168,7 +1671,19 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
       }
       if (!any) break;
       // deflated components (exact eigenvectors): x += W diag(1/mu) c, r -= W c, c = W^T M r
-      for (int p = 0; p < np; ++p) {
+      for (const BasisGroup& bg : G.g) {
+        std::vector<const double*> in;
+        ExpandPass px{1.0, bg.s_mu, {}}, pr{-1.0, nullptr, {}};
+        for (int p : bg.members) {
+          if (!active[p]) continue;
+          whv_grid g = c.grids[p];
+          in.push_back(g->ro);
+          px.out.push_back(g->xo);
+          pr.out.push_back(g->ro);
+        }
+        TRY(group_contract(c, G, bg, in, {px, pr}));
+      }
+      for (int p : G.loose) {
         whv_grid g = c.grids[p];
         const Basis& B = g->basis;
         if (!active[p] || B.nd == 0) continue;
@@ -1194,7 +1709,7 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
         stop[p] = itol * itol * rr[p];
         mx[p] = P.maxit - total_its[p];
       }
-      TRY(run_cg(c, G, rhs, rr, stop, mx, active, &iters));
+      TRY(run_cg(c, CG, rhs, rr, stop, mx, active, &iters));
       for (int p = 0; p < np; ++p) {
         if (!active[p]) continue;
         whv_grid g = c.grids[p];
@@ -1324,6 +1839,71 @@ extern "C" whv_status whv_autotune_batched(int nprob, const whv_grid* grids, con
   if (s != WHV_OK) return s;
   if (best) *best = kbest;
   return WHV_OK;
+}
+
+template <int DIM, int ORDER, bool VARC>
+static whv_status batched_apply(BatchCtx& c, const RoleIO& io, bool fp64) {
+  Wave w;
+  TRY(fp64 ? (make_wave<double, DIM, ORDER, VARC>(c, io, &w)) : (make_wave<float, DIM, ORDER, VARC>(c, io, &w)));
+  TRY(run_wave(c, w));
+  return check_barrier(c);
+}
+
+// out_p = Pi_h(v_p; f_p) of every problem in one persistent launch (the batched form of
+// whv_apply_pi): the wave solve that each batched CG iteration runs, exposed on its own.
+extern "C" whv_status whv_apply_pi_batched(int nprob, const whv_grid* grids, const whv_params* params,
+                                           const double* const* v_dev, const double* const* f_dev,
+                                           double* const* out_dev) {
+  if (nprob < 1 || nprob > kBatchMaxProblems || !grids || !params || !out_dev || !grids[0])
+    return fail(nullptr, WHV_ERR_INVALID, "whv_apply_pi_batched: bad arguments (1 <= nprob <= 1024)");
+  whv_grid g0 = grids[0];
+  const bool varc = g0->c2 != nullptr;
+  BatchCtx c;
+  c.np = nprob;
+  c.grids = grids;
+  c.params = params;
+  c.g0 = g0;
+  c.tgs.resize(nprob);
+  for (int p = 0; p < nprob; ++p) {
+    whv_grid g = grids[p];
+    if (!g || !out_dev[p]) return fail(g0, WHV_ERR_INVALID, "whv_apply_pi_batched: NULL grid or output");
+    for (int q = 0; q < p; ++q)
+      if (grids[q] == g) return fail(g0, WHV_ERR_INVALID, "whv_apply_pi_batched: every problem needs its own grid");
+    if (g->stream != g0->stream || g->precision != g0->precision || g->dim != g0->dim || g->order != g0->order ||
+        (g->c2 != nullptr) != varc || g->cons)
+      return fail(g0, WHV_ERR_INVALID, "whv_apply_pi_batched: grids must match as for whv_solve_batched");
+    whv_status s = make_time_grid(g, &params[p], &c.tgs[p]);
+    if (s != WHV_OK) return fail(g0, s, std::string("whv_apply_pi_batched: ") + g->err);
+  }
+  if (g0->dim < 2) return fail(g0, WHV_ERR_INVALID, "whv_apply_pi_batched: batched solves need 2-D or 3-D grids");
+  batch_init();
+  c.st = g0->stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
+  B_CUDA(g0, c.alloc(&c.bar, 2 * sizeof(unsigned)));
+  B_CUDA(g0, c.alloc(&c.err, sizeof(int)));
+  B_CUDA(g0, cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), c.st));
+  B_CUDA(g0, cudaMemsetAsync(c.err, 0, sizeof(int), c.st));
+  RoleIO io;
+  io.v.assign(nprob, nullptr);
+  io.f.assign(nprob, nullptr);
+  for (int p = 0; p < nprob; ++p) {
+    if (v_dev) io.v[p] = v_dev[p];
+    if (f_dev) io.f[p] = f_dev[p];
+  }
+  io.out.assign(out_dev, out_dev + nprob);
+  io.epi = 0;
+  const bool fp64 = g0->precision == WHV_FP64;
+  whv_status s;
+  switch (g0->dim * 10 + g0->order) {
+    case 22: s = varc ? batched_apply<2, 2, true>(c, io, fp64) : batched_apply<2, 2, false>(c, io, fp64); break;
+    case 24: s = varc ? batched_apply<2, 4, true>(c, io, fp64) : batched_apply<2, 4, false>(c, io, fp64); break;
+    case 32: s = varc ? batched_apply<3, 2, true>(c, io, fp64) : batched_apply<3, 2, false>(c, io, fp64); break;
+    default: s = varc ? batched_apply<3, 4, true>(c, io, fp64) : batched_apply<3, 4, false>(c, io, fp64); break;
+  }
+  count_launches(c.launches);
+  return s;
 }
 
 extern "C" whv_status whv_solve_batched(int nprob, const whv_grid* grids, const whv_params* params,

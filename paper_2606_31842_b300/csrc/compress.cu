@@ -342,7 +342,7 @@ extern "C" whv_status whv_compress_basis(whv_grid g, double tau, int* ranks_host
   // the dense vectors (and what was built from them: graphs, A W, QR) go
   cudaStreamSynchronize(g->stream);
   free_plan(g);
-  cudaFree(B.V);
+  nb.vhold.reset();   // the dense vectors: freed unless another grid shares them
   for (void* p : {(void*)B.AW, (void*)B.Einv, (void*)B.QAW})
     if (p) cudaFree(p);
   nb.V = nullptr;

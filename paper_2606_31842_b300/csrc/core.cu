@@ -21,9 +21,14 @@ whv_status fail(whv_grid g, whv_status s, const std::string& msg) {
   return s;
 }
 
+void hold_vectors(Basis& b) {
+  b.vhold = std::shared_ptr<void>(b.V, [](void* p) { if (p) cudaFree(p); });
+}
+
 void free_basis(whv_grid g) {
   Basis& b = g->basis;
-  for (void* p : {(void*)b.V, (void*)b.d_coef, (void*)b.AW, (void*)b.Einv, (void*)b.QAW, (void*)b.cU, (void*)b.cV,
+  b.vhold.reset();   // the vectors go with the last grid that uses them
+  for (void* p : {(void*)b.d_coef, (void*)b.AW, (void*)b.Einv, (void*)b.QAW, (void*)b.cU, (void*)b.cV,
                   (void*)b.cs, (void*)b.cT, (void*)b.cc, (void*)b.cR, (void*)b.coff, (void*)b.cowner})
     if (p) cudaFree(p);
   g->basis = Basis();
@@ -148,9 +153,9 @@ static void free_all(whv_grid g) {
   free_plan(g);
   void* ptrs[] = {g->c2, g->c2f, g->mw, g->wbuf[0], g->wbuf[1], g->wbuf[2], g->wbuf[3], g->acc, g->x, g->r, g->p, g->q,
                   g->t, g->fd, g->krylov, g->small, g->small2, g->partials, g->counters, g->gbar, g->scal,
-                  g->basis.V, g->basis.d_coef, g->basis.AW, g->basis.Einv, g->basis.QAW, g->basis.cU, g->basis.cV,
+                  g->basis.d_coef, g->basis.AW, g->basis.Einv, g->basis.QAW, g->basis.cU, g->basis.cV,
                   g->basis.cs, g->basis.cT, g->basis.cc, g->basis.cR, g->basis.coff, g->basis.cowner, g->wbuf64[0], g->wbuf64[1], g->wbuf64[2],
-                  g->wbuf64[3], g->acc64, g->xo, g->ro, g->bo, g->wtab_small, g->face64[0], g->face64[1],
+                  g->wbuf64[3], g->acc64, g->tw[0], g->tw[1], g->tw[2], g->tw[3], g->tacc, g->xo, g->ro, g->bo, g->wtab_small, g->face64[0], g->face64[1],
                   g->face64[2], g->face32[0], g->face32[1], g->face32[2]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -284,6 +289,13 @@ __global__ void k_faces(const double* __restrict__ c2, int nx, int ny, int nz, i
   }
 }
 
+// *flag = 1 if a and b differ anywhere (bitwise comparison of two c^2 arrays)
+__global__ void k_differ(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                         double* __restrict__ flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (a[i] != b[i]) *flag = 1.0;
+}
+
 static void free_faces(whv_grid g) {
   for (int m = 0; m < 3; ++m) {
     if (g->face64[m]) cudaFree(g->face64[m]);
@@ -406,10 +418,50 @@ whv_status whv_set_deflation_basis(whv_grid g, const whv_params* p, int nd, cons
   } else {
     return fail(g, WHV_ERR_INVALID, "unknown basis mode");
   }
-  WHV_CUDA(g, cudaMalloc(&b.d_coef, (size_t)kMaxND * 8));
+  {
+    const cudaError_t e = cudaMalloc(&b.d_coef, (size_t)kMaxND * 8);
+    if (e != cudaSuccess) { if (b.V) cudaFree(b.V); return cuda_fail(g, e, "cudaMalloc (basis scratch)"); }
+  }
+  hold_vectors(b);
   free_basis(g);
   g->basis = std::move(b);
   WHV_CUDA(g, cudaStreamSynchronize(g->stream));
+  return WHV_OK;
+}
+
+whv_status whv_share_basis(whv_grid dst, whv_grid src) {
+  if (!dst || !src) return fail(dst, WHV_ERR_INVALID, "whv_share_basis: grid is NULL");
+  if (dst == src) return WHV_OK;
+  const Basis& s = src->basis;
+  if (s.nd == 0 || !s.V) return fail(dst, WHV_ERR_INVALID, "whv_share_basis: the source grid has no dense basis");
+  bool same = dst->dim == src->dim && dst->order == src->order && dst->cons == 0 && src->cons == 0 &&
+              (dst->c2 == nullptr) == (src->c2 == nullptr);
+  for (int m = 0; m < 3 && same; ++m)
+    same = dst->n[m] == src->n[m] && dst->lo[m] == src->lo[m] && dst->hi[m] == src->hi[m];
+  if (!same)
+    return fail(dst, WHV_ERR_INVALID,
+                "whv_share_basis: grids differ in shape, box, order or speed kind (conservative grids cannot share)");
+  if (dst->c2) {   // the basis is M-orthonormal for src's c^2: dst must have the same field
+    WHV_CUDA(dst, cudaStreamSynchronize(src->stream));
+    dst->scal_host[S_TMP] = 0.0;
+    WHV_CUDA(dst, cudaMemcpyAsync(dst->scal + S_TMP, dst->scal_host + S_TMP, sizeof(double), cudaMemcpyHostToDevice,
+                                  dst->stream));
+    k_differ<<<kRedBlocks, 256, 0, dst->stream>>>(dst->c2, src->c2, dst->N, dst->scal + S_TMP);
+    count_launches(1);
+    WHV_CUDA(dst, cudaGetLastError());
+    TRY(fetch_scalars(dst));
+    if (dst->scal_host[S_TMP] != 0.0) return fail(dst, WHV_ERR_INVALID, "whv_share_basis: the grids' c^2 differ");
+  }
+  Basis b;
+  b.nd = s.nd; b.mode = s.mode; b.flags = s.flags;
+  b.V = s.V; b.vhold = s.vhold;
+  b.lambda2 = s.lambda2; b.mu = s.mu; b.modes = s.modes;
+  b.omega = s.omega; b.periods = s.periods; b.adjust = s.adjust; b.cfl = s.cfl;
+  WHV_CUDA(dst, cudaMalloc(&b.d_coef, (size_t)kMaxND * 8));
+  // src's pending writes of the vectors must land before dst's stream reads them
+  WHV_CUDA(dst, cudaStreamSynchronize(src->stream));
+  free_basis(dst);
+  dst->basis = std::move(b);
   return WHV_OK;
 }
 

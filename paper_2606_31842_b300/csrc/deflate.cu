@@ -89,6 +89,143 @@ whv_status expand(whv_grid g, const double* W, int nd, const double* coef, doubl
   return WHV_OK;
 }
 
+// ------------------------------------------------------------------ many right-hand sides
+// The same contractions for k right-hand sides that share one basis W (several forcings on one
+// grid, or batched problems whose grids share a basis): W is read once for all of them.
+//   project_many:  C[j nd + m] = sum_i W[i + m N] M_i r_j[i]            (j < k, m < nd)
+//   expand_many:   out_j[i]  += alpha sum_m W[i + m N] s_m C[j nd + m]  (s = scale or 1)
+// Both are FP64-FMA bound on this GPU once k is more than a few (nd k FMAs per row against
+// (nd + k) 8 bytes), so a block takes up to kMK right-hand sides at a time (grid.y covers more)
+// and the template width KB keeps the FMA count at the actual k when k is small.
+constexpr int kMThreads = 256;
+constexpr int kMRows = 512;    // rows staged per block by project_many
+constexpr int kMK = 16;        // right-hand sides per block
+
+template <int KB>
+__global__ void __launch_bounds__(kMThreads) k_project_many(const double* __restrict__ W, int64_t N, int nd, int k,
+                                                            const double* const* __restrict__ R,
+                                                            const double* __restrict__ mw,
+                                                            double* __restrict__ partials) {
+  extern __shared__ __align__(16) double sr[];   // KB x kMRows: the block's rows of M r_j
+  const int j0 = blockIdx.y * KB;
+  const int kb = min(KB, k - j0);
+  const int64_t row0 = (int64_t)blockIdx.x * kMRows;
+  const int rows = (int)min((int64_t)kMRows, N - row0);
+  for (int j = 0; j < KB; ++j) {
+    const double* r = j < kb ? R[j0 + j] + row0 : nullptr;
+    for (int i = threadIdx.x; i < rows; i += kMThreads)
+      sr[j * kMRows + i] = r ? (mw ? r[i] * mw[row0 + i] : r[i]) : 0.0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int m = warp; m < nd; m += kMThreads / 32) {
+    const double* col = W + (int64_t)m * N + row0;
+    double acc[KB];
+#pragma unroll
+    for (int j = 0; j < KB; ++j) acc[j] = 0.0;
+    for (int i = lane; i < rows; i += 32) {
+      const double v = __ldcs(col + i);   // W is streamed once: do not keep it in L2
+#pragma unroll
+      for (int j = 0; j < KB; ++j) acc[j] = fma(v, sr[j * kMRows + i], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < KB; ++j) {
+      const double s = warp_sum(acc[j]);
+      if (lane == 0 && j < kb) partials[((int64_t)blockIdx.x * k + j0 + j) * nd + m] = s;
+    }
+  }
+}
+
+// C[j nd + m] = sum over blocks b (in order) of partials[(b k + j) nd + m]: one block per (j, m)
+__global__ void __launch_bounds__(256) k_project_many_finish(const double* __restrict__ partials, int nblocks,
+                                                             int nd, int k, double* __restrict__ C) {
+  const int jm = blockIdx.x;   // j nd + m
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[(int64_t)b * k * nd + jm];
+  s = block_sum(s);
+  if (threadIdx.x == 0) C[jm] = s;
+}
+
+template <int KB>
+__global__ void __launch_bounds__(kMThreads) k_expand_many(const double* __restrict__ W, int64_t N, int nd, int k,
+                                                           const double* __restrict__ C,
+                                                           const double* __restrict__ scale, double alpha,
+                                                           double* const* __restrict__ out) {
+  constexpr int kSlab = 256;   // coefficients staged per pass
+  __shared__ double sc[kSlab * KB];
+  const int j0 = blockIdx.y * KB;
+  const int kb = min(KB, k - j0);
+  const int64_t stride = (int64_t)gridDim.x * kMThreads;
+  for (int m0 = 0; m0 < nd; m0 += kSlab) {
+    const int mb = min(kSlab, nd - m0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < mb * KB; t += kMThreads) {
+      const int m = t / KB, j = t % KB;
+      sc[t] = j < kb ? (alpha * (scale ? scale[m0 + m] : 1.0)) * C[(int64_t)(j0 + j) * nd + m0 + m] : 0.0;
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)kMThreads + threadIdx.x; i < N; i += stride) {
+      double acc[KB];
+#pragma unroll
+      for (int j = 0; j < KB; ++j) acc[j] = 0.0;
+      for (int m = 0; m < mb; ++m) {
+        const double w = __ldcs(W + i + (int64_t)(m0 + m) * N);
+#pragma unroll
+        for (int j = 0; j < KB; ++j) acc[j] = fma(w, sc[m * KB + j], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < KB; ++j)
+        if (j < kb) out[j0 + j][i] += acc[j];
+    }
+  }
+}
+
+template <int KB>
+static cudaError_t project_many_kb(cudaStream_t st, const double* W, int64_t N, int nd, int k,
+                                   const double* const* R, const double* mw, double* partials, double* C) {
+  const int nb = (int)((N + kMRows - 1) / kMRows);
+  const size_t smem = (size_t)KB * kMRows * sizeof(double);
+  static bool attr = false;   // opt into > 48 KB of dynamic shared memory once
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_project_many<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_project_many<KB><<<dim3(nb, (k + KB - 1) / KB), kMThreads, smem, st>>>(W, N, nd, k, R, mw, partials);
+  k_project_many_finish<<<nd * k, 256, 0, st>>>(partials, nb, nd, k, C);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+template <int KB>
+static cudaError_t expand_many_kb(cudaStream_t st, const double* W, int64_t N, int nd, int k, const double* C,
+                                  const double* scale, double alpha, double* const* out) {
+  const int blocks = (int)std::min<int64_t>((N + kMThreads - 1) / kMThreads, 148 * 8);
+  k_expand_many<KB><<<dim3(blocks, (k + KB - 1) / KB), kMThreads, 0, st>>>(W, N, nd, k, C, scale, alpha, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+int64_t project_many_scratch(int64_t N, int nd, int k) { return ((N + kMRows - 1) / kMRows) * (int64_t)nd * k; }
+
+cudaError_t project_many(cudaStream_t st, const double* W, int64_t N, int nd, int k, const double* const* R,
+                         const double* mw, double* partials, double* C) {
+  if (k <= 1) return project_many_kb<1>(st, W, N, nd, k, R, mw, partials, C);
+  if (k <= 2) return project_many_kb<2>(st, W, N, nd, k, R, mw, partials, C);
+  if (k <= 4) return project_many_kb<4>(st, W, N, nd, k, R, mw, partials, C);
+  if (k <= 8) return project_many_kb<8>(st, W, N, nd, k, R, mw, partials, C);
+  return project_many_kb<kMK>(st, W, N, nd, k, R, mw, partials, C);
+}
+
+cudaError_t expand_many(cudaStream_t st, const double* W, int64_t N, int nd, int k, const double* C,
+                        const double* scale, double alpha, double* const* out) {
+  if (k <= 1) return expand_many_kb<1>(st, W, N, nd, k, C, scale, alpha, out);
+  if (k <= 2) return expand_many_kb<2>(st, W, N, nd, k, C, scale, alpha, out);
+  if (k <= 4) return expand_many_kb<4>(st, W, N, nd, k, C, scale, alpha, out);
+  if (k <= 8) return expand_many_kb<8>(st, W, N, nd, k, C, scale, alpha, out);
+  return expand_many_kb<kMK>(st, W, N, nd, k, C, scale, alpha, out);
+}
+
 // ------------------------------------------------------------------ closed-form basis
 // beta_h of every tensor-product sine mode: lambda^2 is the sum of the per-direction values in
 // ascending order (so permuted tuples tie exactly), cos(theta) = 1 - dt^2 lambda^2/2,

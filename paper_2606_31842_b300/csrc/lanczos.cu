@@ -294,6 +294,7 @@ static whv_status install_ritz_basis(whv_grid g, const whv_params* p, const Time
   b.modes.assign((size_t)nd * g->dim, 0);
   cudaError_t e = cudaMalloc(&b.d_coef, (size_t)kMaxND * sizeof(double));
   if (e != cudaSuccess) { cudaFree(Y); return cuda_fail(g, e, "cudaMalloc"); }
+  hold_vectors(b);
   free_basis(g);
   g->basis = std::move(b);
 #undef LZ_TRY

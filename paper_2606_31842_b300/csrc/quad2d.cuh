@@ -234,20 +234,19 @@ __device__ __forceinline__ void quadv_sweep(float* S0, float* S1, float* S2, int
   __syncthreads();
 }
 
-// Advances the region staged in S0 (W^n), S1 (W^{n-1}) and S2 (filter sums) kk sub-steps with the
-// weights sw[0 .. kk-1] (FIRST: sub-step 1 is the Taylor start).  The caller has synchronised
-// after staging; on return, after a barrier, S0 = W^{n+kk}, S1 = W^{n+kk-1}, S2 = filter sums.
-// All 1024 threads call it (shuffles and barriers).
+// The sub-steps with the thread's four cells in registers: on entry c = W^n, w = W^{n-1} and a =
+// the filter sums of its cells, and A holds W^n of the whole region (written and synchronised by
+// the caller); on return c = W^{n+kk}, w = W^{n+kk-1}, a the updated sums.  A and B are the two
+// exchange buffers (both overwritten); B may hold the W^{n-1} the threads loaded w from, so the
+// first barrier comes before the first sub-step writes it.  FIRST: sub-step 1 is the Taylor start.
+// All 1024 threads call it (shuffles and barriers); it ends with a barrier.
 template <bool MASK, bool FIRST>
-__device__ __forceinline__ void quad_sweep(float* S0, float* S1, float* S2, int kk, const float* sw,
-                                           const QuadCoef& q, unsigned m) {
+__device__ __forceinline__ void quad_steps(float4& c, float4& w, float4& a, float* A, float* B, int kk,
+                                           const float* sw, const QuadCoef& q, unsigned m) {
   const int row = threadIdx.x >> 4, col = (threadIdx.x & 15) * 4;
   const int off = row * kQReg + col;
   const int up = max(row - 1, 0) * kQReg + col, dn = min(row + 1, kQReg - 1) * kQReg + col;
-  float4 c = q_lds(S0, off), w = q_lds(S1, off), a = q_lds(S2, off);
-  __syncthreads();   // the first sub-step overwrites S1
-  float* A = S0;
-  float* B = S1;
+  __syncthreads();
   int s = 0;
   if (FIRST && kk > 0) {
     quad_taylor<MASK>(c, w, a, A, B, off, up, dn, sw[0], q, m);
@@ -267,6 +266,19 @@ __device__ __forceinline__ void quad_sweep(float* S0, float* S1, float* S2, int 
     __syncthreads();
     q_swap(c, w);
   }
+}
+
+// Advances the region staged in S0 (W^n), S1 (W^{n-1}) and S2 (filter sums) kk sub-steps with the
+// weights sw[0 .. kk-1] (FIRST: sub-step 1 is the Taylor start).  The caller has synchronised
+// after staging; on return, after a barrier, S0 = W^{n+kk}, S1 = W^{n+kk-1}, S2 = filter sums.
+// All 1024 threads call it (shuffles and barriers).
+template <bool MASK, bool FIRST>
+__device__ __forceinline__ void quad_sweep(float* S0, float* S1, float* S2, int kk, const float* sw,
+                                           const QuadCoef& q, unsigned m) {
+  const int row = threadIdx.x >> 4, col = (threadIdx.x & 15) * 4;
+  const int off = row * kQReg + col;
+  float4 c = q_lds(S0, off), w = q_lds(S1, off), a = q_lds(S2, off);
+  quad_steps<MASK, FIRST>(c, w, a, S0, S1, kk, sw, q, m);
   q_sts(S0, off, c);
   q_sts(S1, off, w);
   q_sts(S2, off, a);

@@ -811,8 +811,10 @@ static whv_status outer_solve(SolveCtx& c, int method, const whv_params* p, cons
 
 using namespace whv;
 
+// pre_fd: the forcing already deflated by the caller (whv_solve_many); the DEVD projection and
+// the inflation are then left to the caller as well
 static whv_status solve_impl(whv_grid g, const whv_params* p, const double* f, int use_guess, double* u,
-                             whv_info* info) {
+                             whv_info* info, const double* pre_fd = nullptr) {
   const double t0 = now_s();
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
   if (!f || !u) return fail(g, WHV_ERR_INVALID, "f_dev and u_dev must not be NULL");
@@ -839,7 +841,9 @@ static whv_status solve_impl(whv_grid g, const whv_params* p, const double* f, i
 
   // ---- forcing (Algorithm 2: deflate the forcing)
   const double* fuse = f;
-  if (devd && !refine) {
+  if (devd && !refine && pre_fd) {
+    fuse = pre_fd;
+  } else if (devd && !refine) {
     TRY(basis_project(g, f, B.d_coef));
     TRY(copy_dev(g, g->fd, f, N));
     TRY(basis_expand(g, B.d_coef, -1.0, g->fd));
@@ -875,7 +879,7 @@ static whv_status solve_impl(whv_grid g, const whv_params* p, const double* f, i
   }
 
   // ---- inflate (Algorithm 2): u = x + W diag(1/(omega_eff^2 - lambda^2)) W^T M f
-  if (devd && !refine) {
+  if (devd && !refine && !pre_fd) {
     std::vector<double> cf(B.nd);
     TRY(to_host(g, cf.data(), B.d_coef, B.nd));
     const double om2 = tg.omega_eff * tg.omega_eff;
@@ -1002,6 +1006,40 @@ extern "C" whv_status whv_solve_adjoint(whv_grid g, const whv_params* p, const d
   return e != WHV_OK ? e : s;
 }
 
+// Vector-Jacobian product of out = Pi_h(v; f, c^2) (the reverse sweep on its own): for the seed
+// abar, vbar = S_h^T abar = M S_h (M^{-1} abar) by one forward wave solve, (c2bar, fbar) =
+// abar^T dPi_h/d(c^2, f) by the checkpointed transposed sweep from v.
+static whv_status vjp_impl(whv_grid g, const whv_params* p, const double* v, const double* f, const double* abar,
+                           double* vbar, double* c2bar, double* fbar, int checkpoint_every) {
+  if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
+  if (!v || !abar) return fail(g, WHV_ERR_INVALID, "v_dev and abar_dev must not be NULL");
+  if (vbar && (vbar == abar || vbar == v)) return fail(g, WHV_ERR_INVALID, "vbar_dev must not alias v_dev or abar_dev");
+  if (g->cons) return fail(g, WHV_ERR_INVALID, "the adjoint differentiates the non-conservative operator c^2 Delta_h");
+  TimeGridH tg;
+  TRY(make_time_grid(g, p, &tg));
+  const int K = checkpoint_every > 0 ? checkpoint_every : 16;
+  if (K > 1024) return fail(g, WHV_ERR_INVALID, "checkpoint_every must be <= 1024");
+  const int prec = (p->flags & WHV_REFINE_FP64) ? WHV_FP64 : g->precision;
+  if (prec == WHV_FP64 && g->precision != WHV_FP64) TRY(ensure_fp64_buffers(g));
+  if (c2bar || fbar) TRY(adjoint_gradients(g, tg, v, f, abar, c2bar, fbar, K, prec));
+  if (vbar) {
+    TRY(scale_by(g, abar, g->c2, 1.0, g->t));                // c^2 abar
+    TRY(wave_solve(g, tg, g->t, nullptr, vbar, 0, prec));     // S_h (c^2 abar)
+    TRY(scale_by(g, vbar, g->mw, 1.0, vbar));                // / c^2
+  }
+  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
+  return WHV_OK;
+}
+
+extern "C" whv_status whv_apply_pi_vjp(whv_grid g, const whv_params* p, const double* v, const double* f,
+                                       const double* abar, double* vbar, double* c2bar, double* fbar,
+                                       int checkpoint_every) {
+  const whv_status s = vjp_impl(g, p, v, f, abar, vbar, c2bar, fbar, checkpoint_every);
+  if (!g) return s;
+  const whv_status e = take_persist_error(g);
+  return e != WHV_OK ? e : s;
+}
+
 extern "C" whv_status whv_inject_barrier_error(whv_grid g) {
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
   const unsigned one = 1u;
@@ -1019,10 +1057,77 @@ extern "C" whv_status whv_solve_many(whv_grid g, const whv_params* p, int nrhs, 
   if (nrhs < 0 || (nrhs > 0 && (!F || !U)) || ld < g->N)
     return fail(g, WHV_ERR_INVALID, "need nrhs >= 0, ld >= N and non-NULL F, U");
   whv_status worst = WHV_OK;
-  for (int j = 0; j < nrhs; ++j) {
-    const whv_status s = whv_solve(g, p, F + (size_t)j * ld, use_guess, U + (size_t)j * ld, infos ? infos + j : nullptr);
-    if (s == WHV_ERR_NOT_CONVERGED) { worst = s; continue; }   // keep going: the iterate is written
-    if (s != WHV_OK) return s;
+  const Basis& B = g->basis;
+  const int method = p ? p->method : -1;
+  // DEVD with a dense basis (Algorithm 2 with FPI / CG / GMRES, no FP64 correction, no initial
+  // guesses, no true-residual check): the forcings are deflated and the solutions inflated all at
+  // once -- W^T M F, F_d = F - W C and U += W diag(1/(omega_eff^2 - lambda^2)) C each read W once
+  // for all columns -- and the columns are solved on F_d (written into U, which receives the
+  // solution in place).
+  const bool many = nrhs > 1 && !use_guess && B.nd > 0 && B.V && p && method != WHV_DCG &&
+                    method != WHV_AGMRES && method != WHV_ABICGSTAB &&
+                    !(p->flags & (WHV_REFINE_FP64 | WHV_TRUE_RESIDUAL));
+  if (many) {
+    TimeGridH tg;
+    TRY(make_time_grid(g, p, &tg));
+    if (B.omega != p->omega || B.periods != p->periods || B.adjust != (p->adjust_omega ? 1 : 0) || B.cfl != tg.cfl)
+      return fail(g, WHV_ERR_INVALID, "deflation basis was set for another frequency / time grid");
+    const int nd = B.nd;
+    const int64_t N = g->N;
+    std::vector<void*> tmp;
+    auto cleanup = [&]() {
+      cudaStreamSynchronize(g->stream);
+      for (void* q : tmp) cudaFree(q);
+    };
+    auto alloc = [&](void** q, size_t bytes) {
+      const cudaError_t e = cudaMalloc(q, bytes);
+      if (e == cudaSuccess) tmp.push_back(*q);
+      return e;
+    };
+    double *C = nullptr, *part = nullptr, *scale = nullptr;
+    const double** fp = nullptr;
+    double** up = nullptr;
+    cudaError_t e = alloc((void**)&C, (size_t)nd * nrhs * 8);
+    if (e == cudaSuccess) e = alloc((void**)&part, (size_t)project_many_scratch(N, nd, nrhs) * 8);
+    if (e == cudaSuccess) e = alloc((void**)&scale, (size_t)nd * 8);
+    if (e == cudaSuccess) e = alloc((void**)&fp, (size_t)nrhs * sizeof(double*));
+    if (e == cudaSuccess) e = alloc((void**)&up, (size_t)nrhs * sizeof(double*));
+    std::vector<const double*> hf(nrhs);
+    std::vector<double*> hu(nrhs);
+    std::vector<double> hs(nd);
+    const double om2 = tg.omega_eff * tg.omega_eff;
+    for (int m = 0; m < nd; ++m) hs[m] = 1.0 / (om2 - B.lambda2[m]);
+    for (int j = 0; j < nrhs; ++j) {
+      hf[j] = F + (size_t)j * ld;
+      hu[j] = U + (size_t)j * ld;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(fp, hf.data(), nrhs * sizeof(double*), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(up, hu.data(), nrhs * sizeof(double*), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scale, hs.data(), nd * 8, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = project_many(g->stream, B.V, N, nd, nrhs, fp, g->mw, part, C);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(U, ld * 8, F, ld * 8, N * 8, nrhs, cudaMemcpyDeviceToDevice, g->stream);
+    if (e == cudaSuccess) e = expand_many(g->stream, B.V, N, nd, nrhs, C, nullptr, -1.0, up);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(g, e, "whv_solve_many: deflation of the forcings"); }
+    for (int j = 0; j < nrhs; ++j) {
+      whv_status st = solve_impl(g, p, hf[j], 0, hu[j], infos ? infos + j : nullptr, hu[j]);
+      const whv_status te = take_persist_error(g);
+      if (te != WHV_OK) st = te;
+      if (st == WHV_ERR_NOT_CONVERGED) { worst = st; continue; }
+      if (st != WHV_OK) { cleanup(); return st; }
+    }
+    e = expand_many(g->stream, B.V, N, nd, nrhs, C, scale, 1.0, up);   // inflate every column
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(g, e, "whv_solve_many: inflation");
+  } else {
+    for (int j = 0; j < nrhs; ++j) {
+      const whv_status s = whv_solve(g, p, F + (size_t)j * ld, use_guess, U + (size_t)j * ld,
+                                     infos ? infos + j : nullptr);
+      if (s == WHV_ERR_NOT_CONVERGED) { worst = s; continue; }   // keep going: the iterate is written
+      if (s != WHV_OK) return s;
+    }
   }
   if (worst != WHV_OK) return fail(g, worst, "whv_solve_many: some right-hand sides did not reach tol");
   return WHV_OK;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <chrono>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -49,6 +50,9 @@ struct TimeGridH {
 struct Basis {
   int nd = 0, mode = WHV_BASIS_NONE, flags = 0;
   double* V = nullptr;                // N x nd, column-major, FP64
+  // owner of V: grids that share one basis (whv_share_basis) hold references to the same
+  // storage, which is freed with the last of them
+  std::shared_ptr<void> vhold;
   double* d_coef = nullptr;           // nd scratch
   std::vector<double> lambda2, mu;    // lambda^2 and mu = 1 - beta_h
   std::vector<int> modes;             // nd * dim (closed form)
@@ -102,6 +106,12 @@ struct whv_grid_s {
   // first use, with the outer solution / residual / right-hand side of the refinement loop
   void* wbuf64[4] = {nullptr, nullptr, nullptr, nullptr};
   void* acc64 = nullptr;
+  // FP32 state of the TMA-fed batched 2-D kernel (k_batch_tma): two (W^{n-1}, W^n) pairs and the
+  // filter sums with rows padded to tpitch floats (a multiple of 4: the copy engine needs 16-byte
+  // row strides), allocated on first use
+  float* tw[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* tacc = nullptr;
+  int tpitch = 0;
   double *xo = nullptr, *ro = nullptr, *bo = nullptr;
 
   // FP64 Krylov work vectors
@@ -172,6 +182,8 @@ inline double now_s() {
 
 whv_status make_time_grid(whv_grid g, const whv_params* p, TimeGridH* tg);
 void free_basis(whv_grid g);   // frees the deflation basis (and what depends on it)
+// make b.vhold the owner of b.V (a cudaMalloc'ed buffer)
+void hold_vectors(Basis& b);
 
 // launch accounting (whv_kernel_launches)
 void count_launches(int64_t n);
@@ -226,6 +238,16 @@ whv_status project(whv_grid g, const double* W, int nd, const double* r, double*
 whv_status expand(whv_grid g, const double* W, int nd, const double* coef, double alpha,
                   double* out);
 whv_status closed_form_basis(whv_grid g, const TimeGridH& tg, int nd, Basis* b);
+// k right-hand sides sharing one basis W (W read once for all of them):
+//   project_many: C[j nd + m] = sum_i W[i + m N] mw_i R[j][i]   (mw NULL: 1); R a DEVICE array of k
+//                 pointers; partials needs project_many_scratch(N, nd, k) doubles
+//   expand_many:  out[j][i] += alpha sum_m W[i + m N] s_m C[j nd + m]   (scale NULL: s = 1); out a
+//                 DEVICE array of k pointers
+int64_t project_many_scratch(int64_t N, int nd, int k);
+cudaError_t project_many(cudaStream_t st, const double* W, int64_t N, int nd, int k, const double* const* R,
+                         const double* mw, double* partials, double* C);
+cudaError_t expand_many(cudaStream_t st, const double* W, int64_t N, int nd, int k, const double* C,
+                        const double* scale, double alpha, double* const* out);
 
 // compress.cu: contractions with the grid's basis, dense or SVD-compressed
 whv_status basis_project(whv_grid g, const double* r, double* coef);                  // W^T M r

@@ -82,6 +82,10 @@ def _load():
                                   ctypes.POINTER(D), ctypes.POINTER(I)],
         "whv_solve_batched": [I, ctypes.POINTER(P), ctypes.POINTER(whv_params), ctypes.POINTER(P),
                               ctypes.POINTER(P), ctypes.POINTER(whv_info)],
+        "whv_apply_pi_batched": [I, ctypes.POINTER(P), ctypes.POINTER(whv_params), ctypes.POINTER(P),
+                                 ctypes.POINTER(P), ctypes.POINTER(P)],
+        "whv_share_basis": [P, P],
+        "whv_apply_pi_vjp": [P, ctypes.POINTER(whv_params), P, P, P, P, P, P, I],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -107,7 +111,8 @@ EXPORTED = ["whv_create_grid", "whv_destroy_grid", "whv_set_speed", "whv_time_gr
             "whv_kernel_launches", "whv_set_steps_per_sweep", "whv_get_steps_per_sweep", "whv_autotune",
             "whv_project_noalloc", "whv_lanczos", "whv_solve_adjoint", "whv_solve_batched",
             "whv_inject_barrier_error", "whv_compress_basis", "whv_lanczos_restarted", "whv_set_speed_form",
-            "whv_solve_many", "whv_autotune_batched"]
+            "whv_solve_many", "whv_autotune_batched", "whv_apply_pi_batched", "whv_share_basis",
+            "whv_apply_pi_vjp"]
 
 
 def _check(status, handle=None, allow=()):
@@ -165,6 +170,23 @@ def whv_solve_batched(grids, params, fs, us=None, raise_not_converged=False):
     st = _check(lib.whv_solve_batched(n, G, Pm, F, U, infos), grids[0].handle, allow)
     grids[0]._post()
     return us, [dict(i.as_dict(), status=STATUS_NAMES[st]) for i in infos]
+
+
+def whv_apply_pi_batched(grids, params, vs=None, fs=None, outs=None):
+    """Batched wave solve out_p = Pi_h(v_p; f_p) in one persistent launch (see include/whv.h);
+    vs / fs are lists of tensors or None entries (or None for all zero)."""
+    n = len(grids)
+    if outs is None:
+        outs = [torch.empty(g.N, dtype=torch.float64, device="cuda") for g in grids]
+    G = (ctypes.c_void_p * n)(*[g.handle for g in grids])
+    Pm = (whv_params * n)(*params)
+    Vp = None if vs is None else (ctypes.c_void_p * n)(*[_ptr(v, g.N) for v, g in zip(vs, grids)])
+    Fp = None if fs is None else (ctypes.c_void_p * n)(*[_ptr(f, g.N) for f, g in zip(fs, grids)])
+    O = (ctypes.c_void_p * n)(*[_ptr(o, g.N) for o, g in zip(outs, grids)])
+    grids[0]._pre()
+    _check(lib.whv_apply_pi_batched(n, G, Pm, Vp, Fp, O), grids[0].handle)
+    grids[0]._post()
+    return outs
 
 
 def whv_autotune_batched(grids, params):
@@ -255,6 +277,11 @@ class Grid:
         _check(lib.whv_set_deflation_basis(self.handle, ctypes.byref(params), int(nd),
                                            _ptr(V, None if V is None else self.N * nd), lam, int(mode), int(flags)),
                self.handle)
+
+    def whv_share_basis(self, src):
+        """Use src's deflation basis (no copy; see include/whv.h)."""
+        self._pre()
+        _check(lib.whv_share_basis(self.handle, src.handle), self.handle)
 
     def whv_get_basis(self, want_vectors=False):
         nd = ctypes.c_int()
@@ -348,6 +375,17 @@ class Grid:
         d = info.as_dict()
         d["status"] = STATUS_NAMES[st]
         return z, gc2, gf, d
+
+    def whv_apply_pi_vjp(self, params, v, f, abar, want_v=True, want_c2=True, want_f=True, checkpoint_every=16):
+        """(vbar, c2bar, fbar) = the VJP of Pi_h(v; f, c^2) for the seed abar (see include/whv.h)."""
+        self._pre()
+        mk = lambda want: torch.empty(self.N, dtype=torch.float64, device="cuda") if want else None  # noqa: E731
+        vb, cb, fb = mk(want_v), mk(want_c2), mk(want_f)
+        _check(lib.whv_apply_pi_vjp(self.handle, ctypes.byref(params), _ptr(v, self.N), _ptr(f, self.N),
+                                    _ptr(abar, self.N), _ptr(vb, self.N), _ptr(cb, self.N), _ptr(fb, self.N),
+                                    int(checkpoint_every)), self.handle)
+        self._post()
+        return vb, cb, fb
 
     def whv_project(self, r, coef):
         self._pre()

@@ -79,9 +79,10 @@ def parse(argv=None):
                     help="variable-speed workload: operator form (conservative: div(c^2 grad), second order)")
     ap.add_argument("--sources", type=int, default=0,
                     help="batched workload: Gaussian sources per (grid, frequency) (default 16)")
-    ap.add_argument("--workload", default="c4", choices=["c1", "c2", "c3", "c4", "c5", "study"],
-                    help="c4 (default): the batched squares; c2: the 513^2 deflated solve; c1, c3, c5: the "
-                         "1-D, variable-speed 1025^2 and 3-D workloads; study: iterations vs omega")
+    ap.add_argument("--workload", default="c4", choices=["c1", "c2", "c3", "c4", "c4wave", "c5", "study"],
+                    help="c4 (default): the batched squares; c4wave: only the batched FP32 wave solve of those "
+                         "problems (the dominant kernel, for profiling); c2: the 513^2 deflated solve; c1, c3, c5: "
+                         "the 1-D, variable-speed 1025^2 and 3-D workloads; study: iterations vs omega")
     return ap.parse_args(argv)
 
 
@@ -382,13 +383,15 @@ KERNEL_SOURCES = {
     "k_step3d": (("stencil.cu", "k_step3d"), "stencil_ops.cuh", "whv_device.cuh"),
     "k_step3d2": (("stencil.cu", "k_step3d2"), "stencil_ops.cuh", "whv_device.cuh"),
     "k_batch_block2d": (("batch.cu", "k_batch_block2d"), "quad2d.cuh", "whv_device.cuh"),
+    "k_batch_tma": (("batch.cu", "k_batch_tma"), ("batch.cu", "tma_issue"), ("batch.cu", "tma_live_item"),
+                    "quad2d.cuh", "tma.cuh", "whv_device.cuh"),
 }
 
 
 def _kernel_text(src, name):
-    """The definition of __global__ kernel `name` in `src`: from its declaration to the closing
-    brace of its body."""
-    m = re.search(r"__global__[^;{]*?\b" + re.escape(name) + r"\(", src)
+    """The definition of the __global__ kernel (or __device__ function) `name` in `src`: from its
+    declaration to the closing brace of its body."""
+    m = re.search(r"(?:__global__|__device__)[^;{]*?\b" + re.escape(name) + r"\(", src)
     if not m:
         raise KeyError(name)
     i = src.index("{", m.end())
@@ -534,6 +537,51 @@ class C4Batch:
         for g in self.grids:
             g.close()
         self.grids = []
+
+
+def batch_kernel_name(k):
+    """The FP32 f = 0 batched 2-D kernel the library runs for k steps per sweep: the TMA-fed one for
+    k = 4, 8, 12 (unless WHV_BATCH_TMA=0), k_batch_block2d otherwise."""
+    tma = os.environ.get("WHV_BATCH_TMA", "1") != "0" and k in (4, 8, 12)
+    return "k_batch_tma" if tma else "k_batch_block2d"
+
+
+def run_c4wave(args):
+    """--workload c4wave: only the batched FP32 f = 0 wave solve of the batched squares (one
+    whv_apply_pi_batched launch per step, CUDA events), the kernel the solve spends most of its
+    time in; a small, self-contained command for ncu captures."""
+    import torch
+    from paper_2606_31842_b300 import build as whv_build
+    whv_build.build()
+    from paper_2606_31842_b300 import whv
+    from paper_2606_31842_b300 import inputs as I
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream()
+    nsrc = args.sources if args.sources > 0 else I.C4_SOURCES
+    B = C4Batch(whv, I, stream, True, nsrc)
+    if args.steps_per_sweep > 0:
+        B.grids[0].whv_set_steps_per_sweep(args.steps_per_sweep)
+        kb = args.steps_per_sweep
+    else:
+        kb = whv.whv_autotune_batched(B.grids, B.params)
+    prm0 = [whv.make_params(p.omega) for p in B.params]
+    outs = [torch.empty(g.N, dtype=torch.float64, device="cuda") for g in B.grids]
+    vs = [torch.randn(g.N, dtype=torch.float64, device="cuda") for g in B.grids]
+
+    def step():
+        whv.whv_apply_pi_batched(B.grids, prm0, vs, None, outs)
+    ms, _ = _timed(stream, step, args.steps, args.warmup, None)
+    nts = [g.whv_time_grid(p)["nt"] for g, p in zip(B.grids, prm0)]
+    lups = sum(g.N * nt for g, nt in zip(B.grids, nts))
+    own = c4_sweep_bytes(B.grids, nts, kb)
+    peak, _ = measured_peaks()
+    print(json.dumps({"metric": "batched FP32 wave solve time", "value": ms, "unit": "ms", "steps": args.steps,
+                      "warmup": args.warmup, "kernel": batch_kernel_name(kb), "steps_per_sweep": kb,
+                      "problems": len(B.grids), "lups_per_launch": lups, "glups": lups / ms / 1e6,
+                      "algorithmic_bytes_per_launch": own, "achieved_gbs": own / ms / 1e6,
+                      "frac": own / ms / 1e6 / peak}), flush=True)
+    B.close()
+    return 0
 
 
 def c4_sweep_bytes(grids, nts, k):
@@ -791,14 +839,15 @@ def run_c4(args):
             nts = [i["nt"] for i in infos]
             lup_launch = sum(g.N * nt for g, nt in zip(B.grids, nts))
             own = c4_sweep_bytes(B.grids, nts, kb)
-            tr = traffic_for("k_batch_block2d", "fp32")
+            kname = batch_kernel_name(kb)
+            tr = traffic_for(kname, "fp32")
             tr_scaled = None
             if tr:
-                rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_batch_block2d:fp32"]
+                rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[f"{kname}:fp32"]
                 tr_scaled = tr * lup_launch / rec["lups_per_launch"]
             line["roofline"] = {"bound": "hbm", "achieved": own / t_launch / 1e9, "peak": peak, "unit": "GB/s",
                                 "frac": own / t_launch / 1e9 / peak, "traffic": tr_scaled,
-                                "kernel": f"k_batch_block2d<float> ({kb} leapfrog steps + filter per sweep, all "
+                                "kernel": f"{batch_kernel_name(kb)} ({kb} leapfrog steps + filter per sweep, all "
                                           f"{nprob} problems per launch)",
                                 "algorithmic_bytes_per_launch": own, "lups_per_launch": lup_launch,
                                 "launch_ms": t_launch * 1e3, "glups": lup_launch / t_launch / 1e9,
@@ -1044,6 +1093,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "c4":
         return run_c4(args)
+    if args.workload == "c4wave":
+        return run_c4wave(args)
     if args.workload == "c2":
         return run_c2(args)
     return run_workload(args)

@@ -630,11 +630,14 @@ __device__ __forceinline__ void tma_issue(const BMaps* __restrict__ M, const BTi
   tma_load_2d(stage + 2 * L::kRegion, &M[p].acc, tx * L::TW, ty * L::TW, bar);             // filter sums
 }
 
-template <int K>
-__global__ void __launch_bounds__(kBThreads, 1) k_batch_tma(const BTileT* __restrict__ P, const BMaps* __restrict__ M,
-                                                            const int* __restrict__ nact, int J,
-                                                            const float* __restrict__ wtab, unsigned* bar_count,
-                                                            unsigned* bar_gen, int* err) {
+// R rows of four cells per thread: R = 1, 1024 threads (quad2d.cuh quad_steps), one CTA per SM;
+// R = 2, 512 threads (duo_steps), two CTAs per SM, each with its own two stages.
+template <int K, int R>
+__global__ void __launch_bounds__(kBThreads / R, R) k_batch_tma(const BTileT* __restrict__ P,
+                                                                 const BMaps* __restrict__ M,
+                                                                 const int* __restrict__ nact, int J,
+                                                                 const float* __restrict__ wtab,
+                                                                 unsigned* bar_count, unsigned* bar_gen, int* err) {
   using L = TmaLayout<K>;
   constexpr int TW = L::TW;
   extern __shared__ unsigned char smem_raw[];
@@ -658,8 +661,9 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_tma(const BTileT* __rest
   }
   __syncthreads();
   uint32_t parity[2] = {0u, 0u};
-  const int row = threadIdx.x >> 4, col = (threadIdx.x & 15) * 4;
+  const int row = (threadIdx.x >> 4) * R, col = (threadIdx.x & 15) * 4;
   const int off = row * kBReg + col;
+  // K and row are even: the R = 2 rows of a thread are both in the tile or both in the halo
   const bool trow = row >= K && row < kBReg - K, tcol = col >= K && col < kBReg - K;
   const int aoff = (row - K) * TW + (col - K);   // filter-sum box offset (tile cells only)
   for (int j = 0; j < J; ++j) {
@@ -705,20 +709,24 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_tma(const BTileT* __rest
       const bool first = j == 0, last = n0 + kk == B.nt;
       const float* wtb = wtab + B.wofs;
       if (threadIdx.x < kk) sw[threadIdx.x] = wtb[n0 + 1 + threadIdx.x];
-      const int gy = y0 + row, gx = x0 + col;
-      float4 c, w, a;
+      const int gx = x0 + col;
+      float4 c[R], w[R], a[R];
       if (first) {   // W^0 = v (FP64, unpadded rows), W^{-1} unused (Taylor start), sums w_0 W^0
         const float w0 = wtb[0];
-        float cv[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const bool in = gy >= 0 && gy < ny && gx + e >= 0 && gx + e < nx && B.v;
-          cv[e] = in ? (float)__ldg(B.v + (gx + e) + (int64_t)nx * gy) : 0.0f;
+        for (int rr = 0; rr < R; ++rr) {
+          const int gy = y0 + row + rr;
+          float cv[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const bool in = gy >= 0 && gy < ny && gx + e >= 0 && gx + e < nx && B.v;
+            cv[e] = in ? (float)__ldg(B.v + (gx + e) + (int64_t)nx * gy) : 0.0f;
+          }
+          c[rr] = make_float4(cv[0], cv[1], cv[2], cv[3]);
+          w[rr] = make_float4(0.f, 0.f, 0.f, 0.f);
+          a[rr] = make_float4(w0 * c[rr].x, w0 * c[rr].y, w0 * c[rr].z, w0 * c[rr].w);
+          q_sts(SA, off + rr * kBReg, c[rr]);
         }
-        c = make_float4(cv[0], cv[1], cv[2], cv[3]);
-        w = make_float4(0.f, 0.f, 0.f, 0.f);
-        a = make_float4(w0 * c.x, w0 * c.y, w0 * c.z, w0 * c.w);
-        q_sts(SA, off, c);
       } else {
         const bool ok = mbar_wait(&s_bar[stage], parity[stage], kMbarPolls);
         if (__syncthreads_or(!ok)) {   // the copies did not arrive: give up (bounded)
@@ -730,29 +738,47 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_tma(const BTileT* __rest
           return;
         }
         parity[stage] ^= 1u;
-        c = q_lds(SA, off);
-        w = q_lds(SB, off);
-        a = (trow && tcol) ? *reinterpret_cast<const float4*>(SC + aoff) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+          c[rr] = q_lds(SA, off + rr * kBReg);
+          w[rr] = q_lds(SB, off + rr * kBReg);
+          a[rr] = (trow && tcol) ? *reinterpret_cast<const float4*>(SC + aoff + rr * TW)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
       const QuadCoef q{B.ax, B.ay, B.b, B.ih2x, B.ih2y, 0.5f * B.dt2};
       const bool inside = x0 >= 0 && y0 >= 0 && x0 + kBReg <= nx && y0 + kBReg <= ny;
-      const unsigned m = inside ? 0xfu : quad_mask(x0, y0, nx, ny);
-      if (first) {
-        if (inside) quad_steps<false, true>(c, w, a, SA, SB, kk, sw, q, m);
-        else quad_steps<true, true>(c, w, a, SA, SB, kk, sw, q, m);
+      if constexpr (R == 1) {
+        const unsigned m = inside ? 0xfu : quad_mask(x0, y0, nx, ny);
+        if (first) {
+          if (inside) quad_steps<false, true>(c[0], w[0], a[0], SA, SB, kk, sw, q, m);
+          else quad_steps<true, true>(c[0], w[0], a[0], SA, SB, kk, sw, q, m);
+        } else {
+          if (inside) quad_steps<false, false>(c[0], w[0], a[0], SA, SB, kk, sw, q, m);
+          else quad_steps<true, false>(c[0], w[0], a[0], SA, SB, kk, sw, q, m);
+        }
       } else {
-        if (inside) quad_steps<false, false>(c, w, a, SA, SB, kk, sw, q, m);
-        else quad_steps<true, false>(c, w, a, SA, SB, kk, sw, q, m);
+        const unsigned m = inside ? 0xffu : duo_mask(x0, y0, nx, ny);
+        if (first) {
+          if (inside) duo_steps<false, true>(c[0], c[1], w[0], w[1], a[0], a[1], SA, SB, kk, sw, q, m);
+          else duo_steps<true, true>(c[0], c[1], w[0], w[1], a[0], a[1], SA, SB, kk, sw, q, m);
+        } else {
+          if (inside) duo_steps<false, false>(c[0], c[1], w[0], w[1], a[0], a[1], SA, SB, kk, sw, q, m);
+          else duo_steps<true, false>(c[0], c[1], w[0], w[1], a[0], a[1], SA, SB, kk, sw, q, m);
+        }
       }
       double part = 0.0;
-      if (trow && tcol && gy < ny && gx < nx) {
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
+        const int gy = y0 + row + rr;
+        if (!(trow && tcol && gy < ny && gx < nx)) continue;
         if (!last) {   // 16-byte stores of the tile's new state (padding columns take zeros)
           const int64_t gi = gx + (int64_t)B.pitch * gy;
-          *reinterpret_cast<float4*>(B.w[2 * qo + 1] + gi) = c;
-          *reinterpret_cast<float4*>(B.w[2 * qo] + gi) = w;
-          *reinterpret_cast<float4*>(B.acc + gi) = a;
+          *reinterpret_cast<float4*>(B.w[2 * qo + 1] + gi) = c[rr];
+          *reinterpret_cast<float4*>(B.w[2 * qo] + gi) = w[rr];
+          *reinterpret_cast<float4*>(B.acc + gi) = a[rr];
         } else {
-          const float av[4] = {a.x, a.y, a.z, a.w};
+          const float av[4] = {a[rr].x, a[rr].y, a[rr].z, a[rr].w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             if (gx + e >= nx) break;
@@ -988,14 +1014,19 @@ static EncodeTiledFn encode_tiled() {
 }
 
 // The TMA-fed kernel serves the FP32 f = 0 roles of 2-D second-order c = 1 batches when k is a
-// multiple of 4 (4, 8, 12); WHV_BATCH_TMA=0 in the environment selects k_batch_block2d instead
-// (a diagnostic switch: both give the same results bit for bit).
-static bool tma_role(int K, bool forced) {
-  static const int env = [] { const char* e = getenv("WHV_BATCH_TMA"); return e ? atoi(e) : 1; }();
-  return env != 0 && !forced && K >= 4 && K <= 12 && K % 4 == 0 && encode_tiled() != nullptr;
+// multiple of 4 (4, 8, 12), with two rows of cells per thread; WHV_BATCH_TMA in the environment is
+// a diagnostic switch (0: k_batch_block2d, 1: the TMA-fed kernel with one row per thread): all
+// three give the same results bit for bit.
+static int tma_env() {
+  static const int env = [] { const char* e = getenv("WHV_BATCH_TMA"); return e ? atoi(e) : 2; }();
+  return env;
 }
+static bool tma_role(int K, bool forced) {
+  return tma_env() != 0 && !forced && K >= 4 && K <= 12 && K % 4 == 0 && encode_tiled() != nullptr;
+}
+static int tma_rows() { return tma_env() == 1 ? 1 : 2; }
 
-template <int K>
+template <int K, int R>
 static cudaError_t launch_tma(cudaStream_t st, const Wave& w, unsigned* bar, int* err) {
   const BTileT* P = (const BTileT*)w.desc;
   const BMaps* M = (const BMaps*)w.maps;
@@ -1005,19 +1036,21 @@ static cudaError_t launch_tma(cudaStream_t st, const Wave& w, unsigned* bar, int
   int J = w.J;
   const int* na = w.nact;
   void* args[] = {(void*)&P, (void*)&M, (void*)&na, (void*)&J, (void*)&wt, (void*)&bc, (void*)&bg, (void*)&err};
-  return cudaLaunchCooperativeKernel((const void*)k_batch_tma<K>, dim3(w.nblocks), dim3(kBThreads), args, w.smem, st);
+  return cudaLaunchCooperativeKernel((const void*)k_batch_tma<K, R>, dim3(w.nblocks), dim3(kBThreads / R), args,
+                                     w.smem, st);
 }
 
-template <int K>
+template <int K, int R>
 static cudaError_t tma_prepare(int* per_sm) {
   static bool attr = false;
   if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_batch_tma<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const cudaError_t e = cudaFuncSetAttribute(k_batch_tma<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                TmaLayout<K>::kSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_tma<K>, kBThreads, TmaLayout<K>::kSmem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_tma<K, R>, kBThreads / R,
+                                                       TmaLayout<K>::kSmem);
 }
 
 // pitched FP32 state buffers of a 2-D grid (rows padded to a multiple of 4 floats), on first use
@@ -1113,11 +1146,18 @@ static whv_status make_wave_tma(BatchCtx& c, const RoleIO& io, int K, Wave* out)
   B_CUDA(c.g0, cudaMemcpy(w.wtab, wtab.data(), wtab.size() * sizeof(float), cudaMemcpyHostToDevice));
   B_CUDA(c.g0, cudaMemcpy(w.fin, fin.data(), np * sizeof(BFin), cudaMemcpyHostToDevice));
   int per_sm = 0;
+  // rows of four cells per thread: 2 (512 threads, two CTAs per SM) unless WHV_BATCH_TMA=1
+  const bool duo = tma_rows() == 2;
+#define TMA_CASE(KK)                                                                                \
+  if (duo) { B_CUDA(c.g0, (tma_prepare<KK, 2>(&per_sm))); w.launch = &launch_tma<KK, 2>; }          \
+  else { B_CUDA(c.g0, (tma_prepare<KK, 1>(&per_sm))); w.launch = &launch_tma<KK, 1>; }              \
+  w.smem = TmaLayout<KK>::kSmem;
   switch (K) {
-    case 4: B_CUDA(c.g0, tma_prepare<4>(&per_sm)); w.launch = &launch_tma<4>; w.smem = TmaLayout<4>::kSmem; break;
-    case 8: B_CUDA(c.g0, tma_prepare<8>(&per_sm)); w.launch = &launch_tma<8>; w.smem = TmaLayout<8>::kSmem; break;
-    default: B_CUDA(c.g0, tma_prepare<12>(&per_sm)); w.launch = &launch_tma<12>; w.smem = TmaLayout<12>::kSmem; break;
+    case 4: { TMA_CASE(4) break; }
+    case 8: { TMA_CASE(8) break; }
+    default: { TMA_CASE(12) break; }
   }
+#undef TMA_CASE
   if (per_sm < 1) return fail(c.g0, WHV_ERR_INVALID, "batched: kernel cannot be resident on an SM");
   w.nblocks = (int)std::min<int64_t>((int64_t)per_sm * c.sms, std::max<int64_t>(tile0, 1));
   *out = w;

@@ -738,10 +738,20 @@ static whv_status outer_solve(SolveCtx& c, int method, const whv_params* p, cons
   whv_grid g = c.g;
   const int64_t N = g->N;
   const Basis& B = g->basis;
-  // modal correction of the deflated components: only valid for exact eigenvectors (with
-  // approximate ones W diag(1/mu) W^T M is not a Galerkin solve and the passes can diverge);
-  // approximate bases deflate through Algorithm 4 (method DCG) instead
-  const bool defl = B.nd > 0 && method != WHV_DCG && !augmented(method) && (B.flags & WHV_BASIS_EXACT);
+  // Deflated components of the residual before each inner solve (Algorithm 2 solves them
+  // directly, the accelerator iterates on the rest):
+  //  - exact eigenvectors: the modal solve x += W diag(1/mu) c, r -= W c, c = W^T M r;
+  //  - approximate ones (Lanczos), with the FP64 correction: the Galerkin solve on span(W),
+  //    y = (W^T M A W)^{-1} W^T M r, x += W y, r -= (A W) y (A W formed once, as for Algorithm 4
+  //    with a general basis), after which W^T M r = 0: the residual is consistent with the
+  //    re-deflated operator the inner iteration applies, and the outer FP64 passes correct what
+  //    the stepping precision and the inexact vectors leave.  (W diag(1/mu) W^T M is not a
+  //    Galerkin solve for approximate vectors and the passes can diverge.)
+  // DCG and the augmented methods use the basis inside the iteration instead.
+  const bool devd = B.nd > 0 && method != WHV_DCG && !augmented(method);
+  const bool defl = devd && (B.flags & WHV_BASIS_EXACT);
+  const bool gal = devd && !(B.flags & WHV_BASIS_EXACT) && fp64_res;
+  if (gal) TRY(prepare_general_dcg(c));
   const double inner_tol = fp64_res ? (p->inner_tol > 0.0 ? p->inner_tol : 1e-3) : p->tol;
   if (!use_x0) WHV_CUDA(g, cudaMemsetAsync(g->xo, 0, N * sizeof(double), g->stream));
   bool have_x = use_x0;
@@ -779,6 +789,11 @@ static whv_status outer_solve(SolveCtx& c, int method, const whv_params* p, cons
       TRY(basis_expand(g, g->small, 1.0, g->xo));
       TRY(to_dev(g, g->small, cf.data(), B.nd));
       TRY(basis_expand(g, g->small, -1.0, g->ro));
+    } else if (gal) {
+      TRY(basis_project(g, g->ro, g->small));
+      TRY(small_matvec(g, B.Einv, g->small, B.nd, g->small2));
+      TRY(basis_expand(g, g->small2, 1.0, g->xo));
+      TRY(expand(g, B.AW, B.nd, g->small2, -1.0, g->ro));
     }
     TRY(dot_async(g, g->ro, g->ro, S_TMP2));
     TRY(fetch_scalars(g));

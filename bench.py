@@ -385,6 +385,8 @@ KERNEL_SOURCES = {
     "k_batch_block2d": (("batch.cu", "k_batch_block2d"), "quad2d.cuh", "whv_device.cuh"),
     "k_batch_tma": (("batch.cu", "k_batch_tma"), ("batch.cu", "tma_issue"), ("batch.cu", "tma_live_item"),
                     "quad2d.cuh", "tma.cuh", "whv_device.cuh"),
+    "k_batch_front": (("batch.cu", "k_batch_front"), ("batch.cu", "front_clock"), ("batch.cu", "front_issue"),
+                      ("batch.cu", "front_acc"), "tma.cuh", "whv_device.cuh"),
 }
 
 
@@ -540,10 +542,14 @@ class C4Batch:
 
 
 def batch_kernel_name(k):
-    """The FP32 f = 0 batched 2-D kernel the library runs for k steps per sweep: the TMA-fed one for
-    k = 4, 8, 12 (unless WHV_BATCH_TMA=0), k_batch_block2d otherwise."""
-    tma = os.environ.get("WHV_BATCH_TMA", "1") != "0" and k in (4, 8, 12)
-    return "k_batch_tma" if tma else "k_batch_block2d"
+    """The FP32 f = 0 batched 2-D kernel the library runs for k steps per sweep: the wavefront
+    kernel for k = 8, the TMA-fed staged kernel for k = 4 and 12, k_batch_block2d otherwise (the
+    library's diagnostic switch WHV_BATCH_TMA changes this: 0 = k_batch_block2d throughout, 1 or
+    2 = the staged kernel for k = 4, 8, 12)."""
+    env = os.environ.get("WHV_BATCH_TMA", "3")
+    if env == "0" or k not in (4, 8, 12):
+        return "k_batch_block2d"
+    return "k_batch_front" if (k == 8 and env not in ("1", "2")) else "k_batch_tma"
 
 
 def run_c4wave(args):

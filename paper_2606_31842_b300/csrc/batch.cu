@@ -25,10 +25,13 @@
 // the rest by the batched CG loop in the grids' stepping precision, until every problem's FP64
 // residual meets its tolerance.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <numeric>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include <cuda.h>   // CUtensorMap and its encoding enums (the encoder is fetched through the runtime)
@@ -808,6 +811,274 @@ __global__ void __launch_bounds__(kBThreads / R, R) k_batch_tma(const BTileT* __
   }
 }
 
+// ------------------------------------------------------------------ 2-D, FP32, wavefront
+// The f = 0 FP32 wave solve of the 5-point stencil with c = 1 (every A p of the batched CG loop)
+// as a wavefront in registers: a work item is a strip of 64 columns (the 64 - 2K middle ones are
+// its output, K on each side are halo) and S rows of one problem, and ONE WARP advances it K time
+// levels in a single pass down the rows.  Lane l holds columns 2l, 2l + 1 of the strip; at clock
+// c the warp takes input row c (W^n, W^{n-1} and the filter sums, copied by the copy engine into
+// the warp's own shared-memory blocks of FRB rows, two blocks in flight) and computes level t of
+// row c - t for t = 1 .. K: level t needs rows c - t - 1 .. c - t + 1 of level t - 1 (a ring of
+// three rows per level in registers) and row c - t of level t - 2; x neighbours come from the
+// adjacent lanes (shuffles).  There is no shared-memory exchange and no block-wide barrier: each
+// warp runs on its own.  The filter sum of row y collects w_{n+t} W^{n+t}(y) in a ring of K + 1
+// rows; at clock c, row c - K is complete and W^{n+K}, W^{n+K-1} and its filter sum go to global
+// memory (8-byte stores of the output columns).  Rows above and below the strip's S rows are
+// input halo: a level-t value is exact at distance >= t from the rows and columns the strip did
+// not load, so the K-wide halos leave the output exact.  Cells outside the domain are held at 0.
+// The first sweep reads W^0 = v (FP64) directly and takes the Taylor start as level 1; the last
+// sweep of a problem writes only the FP64 output (its levels beyond the problem's last step carry
+// zero filter weights).  Same operations in the same order as the four-cell kernels: bitwise
+// equal results.
+constexpr int kFK = 8;                 // time levels per sweep
+constexpr int kFTW = 64 - 2 * kFK;     // output columns of a strip (48)
+constexpr int kFS = 256;               // output rows of a work item
+constexpr int kFRB = 8;                // rows per copied block
+constexpr int kFWarps = 4;             // warps per CTA
+constexpr int kFBlockBytes = (64 + 64 + kFTW) * kFRB * 4;   // W^n, W^{n-1}, filter sums of FRB rows
+constexpr int kFWarpBytes = 2 * kFBlockBytes;               // two blocks in flight
+constexpr int kFSmem = kFWarps * kFWarpBytes + 128;
+
+struct BMapsF {          // tensor maps of one problem for the wavefront kernel
+  CUtensorMap w[4];      // 64 x FRB boxes of the pitched state buffers
+  CUtensorMap acc;       // (64 - 2K) x FRB boxes of the filter sums
+};
+
+struct FrontState {      // the registers of one lane (two columns)
+  float L[kFK + 1][3][2];    // level t - 1 at index t: L[0] = W^{n-1}, L[1] = W^n, L[t + 1] = level t
+  float A[kFK + 1][2];       // filter sums of the rows in flight (ring of K + 1 rows)
+};
+
+__device__ __forceinline__ float fr_mask(float v, bool in) { return in ? v : 0.0f; }
+
+// One clock of the wavefront at phase PH = c mod 9 (3 for the level rings, K + 1 = 9 for the
+// filter sums).  Input row c: wn, wp (W^n, W^{n-1}), an = its filter sum so far.  Levels 1 .. K
+// of rows c - 1 .. c - K.  Returns in o0/o1 level K of row c - K (W^{n+K}) and in p0/p1 level K - 1
+// of that row (W^{n+K-1}); the complete filter sum of row c - K stays at A[(c - K) mod 9].
+template <int PH, bool FIRST>
+__device__ __forceinline__ void front_clock(FrontState& st, int c, float2 wn, float2 wp, float2 an, const float* wt,
+                                            float ax, float ay, float b, float ih2x, float ih2y, float hdt2,
+                                            bool cin0, bool cin1, int ny, float& o0, float& o1, float& p0,
+                                            float& p1) {
+  constexpr int r3 = PH % 3;
+  st.L[0][r3][0] = wp.x; st.L[0][r3][1] = wp.y;
+  st.L[1][r3][0] = wn.x; st.L[1][r3][1] = wn.y;
+  st.A[PH % (kFK + 1)][0] = an.x; st.A[PH % (kFK + 1)][1] = an.y;
+#pragma unroll
+  for (int t = 1; t <= kFK; ++t) {
+    const int y = c - t;
+    const int im = (PH - t - 1 + 30) % 3, i0 = (PH - t + 30) % 3, ip = (PH - t + 1 + 30) % 3;
+    const float* up = st.L[t][im];
+    const float* mid = st.L[t][i0];
+    const float* dn = st.L[t][ip];
+    const float l = __shfl_up_sync(0xffffffffu, mid[1], 1);
+    const float r = __shfl_down_sync(0xffffffffu, mid[0], 1);
+    float n0, n1;
+    if (FIRST && t == 1) {   // Taylor start W^1 = W^0 + dt^2/2 L W^0
+      float L0 = fmaf(-2.0f, mid[0], l + mid[1]) * ih2x;
+      L0 = fmaf(fmaf(-2.0f, mid[0], up[0] + dn[0]), ih2y, L0);
+      n0 = fmaf(hdt2, L0, mid[0]);
+      float L1 = fmaf(-2.0f, mid[1], mid[0] + r) * ih2x;
+      L1 = fmaf(fmaf(-2.0f, mid[1], up[1] + dn[1]), ih2y, L1);
+      n1 = fmaf(hdt2, L1, mid[1]);
+    } else {
+      const float* pv = st.L[t - 1][i0];   // level t - 2 at row y
+      n0 = fmaf(ay, up[0] + dn[0], fmaf(ax, l + mid[1], fmaf(b, mid[0], -pv[0])));
+      n1 = fmaf(ay, up[1] + dn[1], fmaf(ax, mid[0] + r, fmaf(b, mid[1], -pv[1])));
+    }
+    const bool rin = (unsigned)y < (unsigned)ny;
+    n0 = fr_mask(n0, rin && cin0);
+    n1 = fr_mask(n1, rin && cin1);
+    const int ia = (PH - t + 90) % (kFK + 1);
+    st.A[ia][0] = fmaf(wt[t - 1], n0, st.A[ia][0]);
+    st.A[ia][1] = fmaf(wt[t - 1], n1, st.A[ia][1]);
+    if (t < kFK) {
+      st.L[t + 1][i0][0] = n0;
+      st.L[t + 1][i0][1] = n1;
+    } else {
+      o0 = n0;
+      o1 = n1;
+      p0 = st.L[kFK][i0][0];
+      p1 = st.L[kFK][i0][1];
+    }
+  }
+}
+
+template <int PH>
+__device__ __forceinline__ float2 front_acc(const FrontState& st) {
+  return make_float2(st.A[(PH - kFK + 90) % (kFK + 1)][0], st.A[(PH - kFK + 90) % (kFK + 1)][1]);
+}
+
+__device__ __forceinline__ void front_issue(const BMapsF* __restrict__ M, int p, int qi, int x0, int row,
+                                            unsigned char* blk, uint64_t* bar) {
+  mbar_arrive_expect_tx(bar, kFBlockBytes);
+  tma_load_2d(blk, &M[p].w[2 * qi + 1], x0, row, bar);                      // W^n
+  tma_load_2d(blk + 64 * kFRB * 4, &M[p].w[2 * qi], x0, row, bar);          // W^{n-1}
+  tma_load_2d(blk + 128 * kFRB * 4, &M[p].acc, x0 + kFK, row, bar);         // filter sums
+}
+
+__global__ void __launch_bounds__(kFWarps * 32) k_batch_front(const BTileT* __restrict__ P,
+                                                              const BMapsF* __restrict__ M,
+                                                              const int* __restrict__ nact, int J,
+                                                              const float* __restrict__ wtab, unsigned* bar_count,
+                                                              unsigned* bar_gen, int* err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* const base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  __shared__ int64_t s_tile0[kBatchMaxProblems + 1];
+  __shared__ __align__(8) uint64_t s_bar[kFWarps][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int np = nact[0];
+  for (int p = threadIdx.x; p <= np; p += blockDim.x)
+    s_tile0[p] = p < np ? P[p].tile0 : P[np - 1].tile0 + P[np - 1].ntiles;
+  if (lane == 0) {
+    mbar_init(&s_bar[warp][0], 1);
+    mbar_init(&s_bar[warp][1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  unsigned char* const wbase = base + warp * kFWarpBytes;
+  uint32_t parity[2] = {0u, 0u};
+  const int64_t G = (int64_t)gridDim.x * kFWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kFWarps + warp;
+  bool failed = false;
+  for (int j = 0; j < J && !failed; ++j) {
+    const int A = nact[j];
+    const int64_t total = s_tile0[A];
+    const int qi = (j + 1) & 1, qo = j & 1;
+    if (j > 0) fence_proxy_async_global();   // the previous sweep's stores before this sweep's copies
+    int p = 0;
+    for (int64_t item = gw; item < total && !failed; item += G) {
+      while (s_tile0[p + 1] <= item) ++p;
+      const BTileT& B = P[p];
+      if (B.halt && *B.halt != 0.0) continue;
+      const int t = (int)(item - B.tile0);
+      const int sx = t % B.tiles_x, sy = t / B.tiles_x;
+      const int nx = B.nx, ny = B.ny;
+      const int x0 = sx * kFTW - kFK;
+      const int Y0 = sy * kFS, Y1 = min(Y0 + kFS, ny);
+      const int c0 = Y0 - kFK, c1 = Y1 - 1 + kFK;       // clocks (input rows) of this item
+      const int n0 = j * kFK;
+      const int kk = min(kFK, B.nt - n0);
+      const bool first = j == 0, last = n0 + kk == B.nt;
+      float wt[kFK];
+#pragma unroll
+      for (int s = 0; s < kFK; ++s) wt[s] = s < kk ? __ldg(wtab + B.wofs + n0 + 1 + s) : 0.0f;
+      const float w0 = first ? __ldg(wtab + B.wofs) : 0.0f;
+      const int gx0 = x0 + 2 * lane;
+      const bool cin0 = gx0 >= 0 && gx0 < nx, cin1 = gx0 + 1 >= 0 && gx0 + 1 < nx;
+      const bool outc = 2 * lane >= kFK && 2 * lane < 64 - kFK && gx0 < nx;   // output columns
+      const float ax = B.ax, ay = B.ay, bb = B.b, ih2x = B.ih2x, ih2y = B.ih2y, hdt2 = 0.5f * B.dt2;
+      FrontState st;
+#pragma unroll
+      for (int a = 0; a < kFK + 1; ++a)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) st.L[a][r][0] = st.L[a][r][1] = 0.0f;
+#pragma unroll
+      for (int a = 0; a < kFK + 1; ++a) st.A[a][0] = st.A[a][1] = 0.0f;
+      const int nblk = (c1 - c0 + 1 + kFRB - 1) / kFRB;
+      if (!first && lane == 0) {
+        front_issue(M, p, qi, x0, c0, wbase, &s_bar[warp][0]);
+        if (nblk > 1) front_issue(M, p, qi, x0, c0 + kFRB, wbase + kFBlockBytes, &s_bar[warp][1]);
+      }
+      __syncwarp();
+      double part = 0.0;
+      int c = c0;
+      // clocks in groups of nine (the phase of the register rings is c - c0 mod 9)
+      auto clock = [&](auto ph) {
+        constexpr int PH = decltype(ph)::value;
+        const int rel = c - c0, blk = rel / kFRB, row = rel % kFRB, slot = blk & 1;
+        float2 wn = make_float2(0.f, 0.f), wp = wn, an = wn;
+        if (first) {
+          const bool rin = (unsigned)c < (unsigned)ny;
+          if (rin && cin0 && B.v) wn.x = (float)__ldg(B.v + gx0 + (int64_t)nx * c);
+          if (rin && cin1 && B.v) wn.y = (float)__ldg(B.v + gx0 + 1 + (int64_t)nx * c);
+          an = make_float2(w0 * wn.x, w0 * wn.y);
+        } else {
+          if (row == 0) {   // a new block: wait for its copies
+            if (!mbar_wait(&s_bar[warp][slot], parity[slot], kMbarPolls)) failed = true;
+            parity[slot] ^= 1u;
+          }
+          const unsigned char* bp = wbase + slot * kFBlockBytes;
+          wn = reinterpret_cast<const float2*>(bp)[row * 32 + lane];
+          wp = reinterpret_cast<const float2*>(bp + 64 * kFRB * 4)[row * 32 + lane];
+          if (2 * lane >= kFK && 2 * lane < 64 - kFK)
+            an = reinterpret_cast<const float2*>(bp + 128 * kFRB * 4)[row * (kFTW / 2) + lane - kFK / 2];
+          if (row == kFRB - 1) {   // block done: refill its slot two blocks ahead
+            __syncwarp();
+            if (lane == 0 && blk + 2 < nblk)
+              front_issue(M, p, qi, x0, c0 + (blk + 2) * kFRB, wbase + slot * kFBlockBytes, &s_bar[warp][slot]);
+          }
+        }
+        float o0, o1, p0, p1;
+        if (first)
+          front_clock<PH, true>(st, c, wn, wp, an, wt, ax, ay, bb, ih2x, ih2y, hdt2, cin0, cin1, ny, o0, o1, p0, p1);
+        else
+          front_clock<PH, false>(st, c, wn, wp, an, wt, ax, ay, bb, ih2x, ih2y, hdt2, cin0, cin1, ny, o0, o1, p0, p1);
+        const int y = c - kFK;
+        if (y >= Y0 && y < Y1 && outc) {
+          const float2 a = front_acc<PH>(st);
+          if (!last) {
+            const int64_t gi = gx0 + (int64_t)B.pitch * y;
+            *reinterpret_cast<float2*>(B.w[2 * qo + 1] + gi) = make_float2(o0, o1);
+            *reinterpret_cast<float2*>(B.w[2 * qo] + gi) = make_float2(p0, p1);
+            *reinterpret_cast<float2*>(B.acc + gi) = a;
+          } else {
+            const int64_t gi = gx0 + (int64_t)nx * y;
+            const float av[2] = {a.x, a.y};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              if (gx0 + e >= nx) break;
+              if (B.epi == 0) {
+                B.out[gi + e] = (double)av[e];
+              } else {
+                const double vi = __ldg(B.v + gi + e);
+                const double o = vi - (double)av[e];
+                B.out[gi + e] = o;
+                part = fma(B.mw ? vi * __ldg(B.mw + gi + e) : vi, o, part);
+              }
+            }
+          }
+        }
+        ++c;
+      };
+      while (c <= c1) {
+        clock(std::integral_constant<int, 0>());
+        if (c > c1) break;
+        clock(std::integral_constant<int, 1>());
+        if (c > c1) break;
+        clock(std::integral_constant<int, 2>());
+        if (c > c1) break;
+        clock(std::integral_constant<int, 3>());
+        if (c > c1) break;
+        clock(std::integral_constant<int, 4>());
+        if (c > c1) break;
+        clock(std::integral_constant<int, 5>());
+        if (c > c1) break;
+        clock(std::integral_constant<int, 6>());
+        if (c > c1) break;
+        clock(std::integral_constant<int, 7>());
+        if (c > c1) break;
+        clock(std::integral_constant<int, 8>());
+      }
+      if (last && B.epi == 1) {
+        part = warp_sum(part);
+        if (lane == 0) B.partials[t] = part;
+      }
+    }
+    fence_proxy_async_global();   // this sweep's stores before other CTAs' copies of the next sweep
+    if (__syncthreads_or(failed)) {   // copies that did not arrive: give up, after a bounded drain
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      if (lane == 0) {
+        mbar_wait(&s_bar[warp][0], parity[0], kMbarPolls);
+        mbar_wait(&s_bar[warp][1], parity[1], kMbarPolls);
+      }
+      __syncwarp();
+      return;
+    }
+    if (!grid_barrier(bar_count, bar_gen, err, gridDim.x)) return;
+  }
+}
+
 // ------------------------------------------------------------------ per-problem small kernels
 struct BFin {
   const double* partials;
@@ -882,6 +1153,15 @@ struct BatchCtx {
   double** scal = nullptr;     // device array of the problems' scalar blocks
   std::vector<void*> allocs;
   int64_t launches = 0;
+  // WHV_LOG=1: host wall time per phase of the batched solve (the phases end with a stream
+  // synchronisation, so the host clock brackets the device work), printed at the end
+  double t_mark = 0.0;
+  double t_phase[5] = {0, 0, 0, 0, 0};   // b wave solve, CG loops, residual wave solves, deflation, other
+  void mark(int ph) {
+    const double t = now_s();
+    if (t_mark > 0.0) t_phase[ph] += t - t_mark;
+    t_mark = t;
+  }
   ~BatchCtx() {
     if (st) cudaStreamSynchronize(st);
     for (void* p : allocs) cudaFree(p);
@@ -1013,18 +1293,21 @@ static EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// The TMA-fed kernel serves the FP32 f = 0 roles of 2-D second-order c = 1 batches when k is a
-// multiple of 4 (4, 8, 12), with two rows of cells per thread; WHV_BATCH_TMA in the environment is
-// a diagnostic switch (0: k_batch_block2d, 1: the TMA-fed kernel with one row per thread): all
-// three give the same results bit for bit.
+// The FP32 f = 0 roles of 2-D second-order c = 1 batches: k = 8 runs the wavefront kernel
+// (k_batch_front), k = 4 and 12 the TMA-fed staged kernel with two rows of cells per thread, other
+// k k_batch_block2d.  WHV_BATCH_TMA in the environment is a diagnostic switch (0: k_batch_block2d
+// for every k; 1 or 2: the staged TMA-fed kernel with one or two rows per thread for k = 4, 8, 12):
+// all of them give the same results bit for bit.
 static int tma_env() {
-  static const int env = [] { const char* e = getenv("WHV_BATCH_TMA"); return e ? atoi(e) : 2; }();
+  static const int env = [] { const char* e = getenv("WHV_BATCH_TMA"); return e ? atoi(e) : 3; }();
   return env;
 }
 static bool tma_role(int K, bool forced) {
   return tma_env() != 0 && !forced && K >= 4 && K <= 12 && K % 4 == 0 && encode_tiled() != nullptr;
 }
 static int tma_rows() { return tma_env() == 1 ? 1 : 2; }
+// k = 8 takes the wavefront kernel (k_batch_front) unless WHV_BATCH_TMA is 0, 1 or 2
+static bool front_role(int K, bool forced) { return tma_role(K, forced) && K == kFK && tma_env() >= 3; }
 
 template <int K, int R>
 static cudaError_t launch_tma(cudaStream_t st, const Wave& w, unsigned* bar, int* err) {
@@ -1164,6 +1447,114 @@ static whv_status make_wave_tma(BatchCtx& c, const RoleIO& io, int K, Wave* out)
   return WHV_OK;
 }
 
+// ------------------------------------------------------------------ wavefront role (host)
+static cudaError_t launch_front(cudaStream_t st, const Wave& w, unsigned* bar, int* err) {
+  const BTileT* P = (const BTileT*)w.desc;
+  const BMapsF* M = (const BMapsF*)w.maps;
+  const float* wt = (const float*)w.wtab;
+  unsigned* bc = bar;
+  unsigned* bg = bar + 1;
+  int J = w.J;
+  const int* na = w.nact;
+  void* args[] = {(void*)&P, (void*)&M, (void*)&na, (void*)&J, (void*)&wt, (void*)&bc, (void*)&bg, (void*)&err};
+  return cudaLaunchCooperativeKernel((const void*)k_batch_front, dim3(w.nblocks), dim3(kFWarps * 32), args, w.smem,
+                                     st);
+}
+
+static bool encode_rows(CUtensorMap* map, float* base, int nx, int ny, int pitch, int boxw) {
+  const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+  const cuuint32_t boxd[2] = {(cuuint32_t)boxw, (cuuint32_t)kFRB};
+  const cuuint32_t es[2] = {1, 1};
+  return encode_tiled()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, boxd, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// descriptor and tensor-map tables of the wavefront role (k = kFK); problems ordered by sweeps
+static whv_status make_wave_front(BatchCtx& c, const RoleIO& io, Wave* out) {
+  const int np = c.np;
+  const int K = kFK;
+  Wave w;
+  w.K = K;
+  std::vector<int> order(np), nsw(np);
+  for (int p = 0; p < np; ++p) nsw[p] = (c.tgs[p].nt + K - 1) / K;
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nsw[a] > nsw[b]; });
+  w.J = nsw[order[0]];
+  std::vector<float> wtab;
+  std::vector<BFin> fin(np);
+  std::vector<BTileT> d(np);
+  std::vector<BMapsF> maps(np);
+  int64_t tile0 = 0;
+  for (int k = 0; k < np; ++k) {
+    const int p = order[k];
+    whv_grid g = c.grids[p];
+    const TimeGridH& tg = c.tgs[p];
+    TRY(ensure_tma_buffers(g));
+    const int wofs = (int)wtab.size();
+    for (int n = 0; n <= tg.nt; ++n) wtab.push_back((float)tg.weight[n]);
+    // K extra zero weights: the last sweep may read beyond the problem's nt
+    for (int n = 0; n < K; ++n) wtab.push_back(0.0f);
+    const double h2x = g->h[0] * g->h[0], h2y = g->h[1] * g->h[1];
+    BTileT B{};
+    for (int m = 0; m < 4; ++m) B.w[m] = g->tw[m];
+    B.acc = g->tacc;
+    B.v = io.v[p]; B.out = io.out[p];
+    B.mw = g->mw; B.partials = chan(g, CH_STEP);
+    B.halt = io.halt ? g->scal + S_HALT : nullptr;
+    B.nx = g->n[0]; B.ny = g->n[1]; B.nt = tg.nt; B.pitch = g->tpitch;
+    B.tiles_x = (g->n[0] + kFTW - 1) / kFTW;
+    B.ntiles = B.tiles_x * ((g->n[1] + kFS - 1) / kFS);
+    B.epi = io.epi; B.wofs = wofs;
+    B.ih2x = (float)(1.0 / h2x);
+    B.ih2y = (float)(1.0 / h2y);
+    B.dt2 = (float)(tg.dt * tg.dt);
+    const double ax = tg.dt * tg.dt / h2x, ay = tg.dt * tg.dt / h2y;
+    B.ax = (float)ax; B.ay = (float)ay; B.b = (float)(2.0 - 2.0 * (ax + ay));
+    B.tile0 = tile0;
+    for (int m = 0; m < 4; ++m)
+      if (!encode_rows(&maps[k].w[m], g->tw[m], g->n[0], g->n[1], g->tpitch, 64))
+        return fail(c.g0, WHV_ERR_CUDA, "batched: cuTensorMapEncodeTiled failed (state buffers)");
+    if (!encode_rows(&maps[k].acc, g->tacc, g->n[0], g->n[1], g->tpitch, kFTW))
+      return fail(c.g0, WHV_ERR_CUDA, "batched: cuTensorMapEncodeTiled failed (filter sums)");
+    if (io.epi == 1 && B.ntiles > chan_cap(g, CH_STEP))
+      return fail(c.g0, WHV_ERR_INVALID, "batched: grid too large for its reduction channel");
+    fin[k] = BFin{chan(g, CH_STEP), io.halt ? g->scal + S_HALT : nullptr, g->scal, B.ntiles};
+    d[k] = B;
+    tile0 += B.ntiles;
+  }
+  std::vector<int> nact(w.J);
+  for (int j = 0; j < w.J; ++j) {
+    int a = 0;
+    while (a < np && nsw[order[a]] > j) ++a;
+    nact[j] = a;
+  }
+  B_CUDA(c.g0, c.alloc(&w.desc, np * sizeof(BTileT)));
+  B_CUDA(c.g0, c.alloc(&w.maps, np * sizeof(BMapsF)));
+  B_CUDA(c.g0, c.alloc(&w.nact, w.J * sizeof(int)));
+  B_CUDA(c.g0, c.alloc(&w.wtab, wtab.size() * sizeof(float)));
+  B_CUDA(c.g0, c.alloc(&w.fin, np * sizeof(BFin)));
+  B_CUDA(c.g0, cudaMemcpy(w.desc, d.data(), np * sizeof(BTileT), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.maps, maps.data(), np * sizeof(BMapsF), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.nact, nact.data(), w.J * sizeof(int), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.wtab, wtab.data(), wtab.size() * sizeof(float), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.fin, fin.data(), np * sizeof(BFin), cudaMemcpyHostToDevice));
+  static bool attr = false;
+  if (!attr) {
+    B_CUDA(c.g0, cudaFuncSetAttribute(k_batch_front, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem));
+    attr = true;
+  }
+  int per_sm = 0;
+  B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_front, kFWarps * 32, kFSmem));
+  if (per_sm < 1) return fail(c.g0, WHV_ERR_INVALID, "batched: kernel cannot be resident on an SM");
+  w.smem = kFSmem;
+  w.launch = &launch_front;
+  w.nblocks = (int)std::min<int64_t>((int64_t)per_sm * c.sms, std::max<int64_t>((tile0 + kFWarps - 1) / kFWarps, 1));
+  *out = w;
+  return WHV_OK;
+}
+
 constexpr int kBDfK = 4;   // sub-steps per sweep of the double-float roles
 
 // Device tables of one role, stepping in T (double on an FP32 grid: its FP64 buffer set; dfl:
@@ -1182,7 +1573,8 @@ static whv_status make_wave(BatchCtx& c, const RoleIO& io, Wave* out) {
   Wave w;
   w.K = DF ? kBDfK : (blocked ? batch_k(c.g0, fp64) : 1);
   if constexpr (std::is_same<T, float>::value && DIM == 2 && ORDER == 2 && !VARC)
-    if (tma_role(w.K, forced)) return make_wave_tma(c, io, w.K, out);
+    if (front_role(w.K, forced)) return make_wave_front(c, io, out);
+    else if (tma_role(w.K, forced)) return make_wave_tma(c, io, w.K, out);
   std::vector<int> order(np), nsw(np);
   for (int p = 0; p < np; ++p) nsw[p] = (c.tgs[p].nt + w.K - 1) / w.K;
   std::iota(order.begin(), order.end(), 0);
@@ -1596,8 +1988,10 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
     io_b.out = c.each([](whv_grid g) { return g->t; });
     Wave wb;
     TRY(g64 ? (make_wave<double, DIM, ORDER, VARC>(c, io_b, &wb)) : (make_wave<float, DIM, ORDER, VARC>(c, io_b, &wb)));
+    c.mark(4);
     TRY(run_wave(c, wb));
     TRY(check_barrier(c));
+    c.mark(0);
     for (int p = 0; p < np; ++p) TRY(dot_async(c.grids[p], c.grids[p]->t, c.grids[p]->t, S_TMP));
     TRY(fetch_all(c));
     std::vector<double> bb(np), stop(np);
@@ -1607,7 +2001,9 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
       stop[p] = c.params[p].tol * c.params[p].tol * bb[p];
     }
     const std::vector<const double*> rhs = c.each([](whv_grid g) { return (const double*)g->t; });
+    c.mark(4);
     TRY(run_cg(c, CG, rhs, bb, stop, maxit, active, &iters));
+    c.mark(1);
     for (int p = 0; p < np; ++p) {
       whv_grid g = c.grids[p];
       total_its[p] = iters[p];
@@ -1661,8 +2057,10 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
       TRY((make_wave<double, DIM, ORDER, VARC>(c, io_b, &wb)));
       TRY((make_wave<double, DIM, ORDER, VARC>(c, io_ax, &wax)));
     }
+    c.mark(4);
     TRY(run_wave(c, wb));
     TRY(check_barrier(c));
+    c.mark(0);
     for (int p = 0; p < np; ++p) {
       whv_grid g = c.grids[p];
       ws64[p] = 1;
@@ -1685,8 +2083,10 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
           B_CUDA(c.g0, cudaMemcpyAsync(g->scal + S_HALT, g->scal_host + S_HALT, sizeof(double),
                                        cudaMemcpyHostToDevice, c.st));
         }
+        c.mark(4);
         TRY(run_wave(c, wax));
         TRY(check_barrier(c));
+        c.mark(2);
         for (int p = 0; p < np; ++p) {
           if (!active[p]) continue;
           whv_grid g = c.grids[p];
@@ -1711,6 +2111,7 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
       }
       if (!any) break;
       // deflated components (exact eigenvectors): x += W diag(1/mu) c, r -= W c, c = W^T M r
+      c.mark(4);
       for (const BasisGroup& bg : G.g) {
         std::vector<const double*> in;
         ExpandPass px{1.0, bg.s_mu, {}}, pr{-1.0, nullptr, {}};
@@ -1749,7 +2150,9 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
         stop[p] = itol * itol * rr[p];
         mx[p] = P.maxit - total_its[p];
       }
+      c.mark(3);
       TRY(run_cg(c, CG, rhs, rr, stop, mx, active, &iters));
+      c.mark(1);
       for (int p = 0; p < np; ++p) {
         if (!active[p]) continue;
         whv_grid g = c.grids[p];
@@ -1762,6 +2165,11 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
     }
     for (int p = 0; p < np; ++p) TRY(copy_dev(c.grids[p], u_dev[p], c.grids[p]->xo, c.grids[p]->N));
   }
+  c.mark(4);
+  if (getenv("WHV_LOG") && getenv("WHV_LOG")[0] == '1')
+    fprintf(stderr, "[whv] batched solve phases (s): b %.3f  CG loops %.3f  residual wave solves %.3f  "
+                    "deflation %.3f  other %.3f\n", c.t_phase[0], c.t_phase[1], c.t_phase[2], c.t_phase[3],
+            c.t_phase[4]);
   // leave the grids usable by non-batched calls
   for (int p = 0; p < np; ++p) {
     whv_grid g = c.grids[p];

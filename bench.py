@@ -791,7 +791,14 @@ def run_c4(args):
                            check_every=args.check_every, setup_s=B.setup_s,
                            l2="no flush: the working set (~1.5 GB of FP32 state, ~1 GB of forcings and "
                               "solutions) is larger than the 126 MB L2",
-                           basis="one closed-form basis per (grid, omega), shared by its sources"),
+                           basis="one closed-form basis per (grid, omega), shared by its sources",
+                           basis_bytes=sum(32 * I.WORKLOADS[f"c4_{n}_{int(om)}"].n_unknowns * 8
+                                           for n in I.C4_SIZES for om in I.C4_OMEGAS),
+                           basis_bytes_if_copied=sum(32 * g.N * 8 for g in B.grids),
+                           contraction_bytes_per_projection=sum(
+                               (32 + nsrc) * I.WORKLOADS[f"c4_{n}_{int(om)}"].n_unknowns * 8
+                               for n in I.C4_SIZES for om in I.C4_OMEGAS),
+                           contraction_bytes_per_projection_if_per_problem=sum((32 + 1) * g.N * 8 for g in B.grids)),
             "iterations_max": max(i["iterations"] for i in infos),
             "iterations_mean": statistics.mean(i["iterations"] for i in infos),
             "outer_iterations_max": max(i["outer_iterations"] for i in infos),

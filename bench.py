@@ -51,7 +51,7 @@ L2_FLUSH_BYTES = 512 << 20   # > 126 MB L2: written between timed steps of the L
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="whv", choices=["whv", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -61,8 +61,8 @@ def parse(argv=None):
     ap.add_argument("--method", default="", choices=["", "cg", "dcg", "gmres", "agmres", "abicgstab"],
                     help="accelerator of the single-grid workloads (default: DCG for c1/c3, CG otherwise)")
     ap.add_argument("--steps-per-sweep", type=int, default=0,
-                    help="2-D stepping kernel: 0 = autotune (default), k = blocked k steps per launch, "
-                         "-k = persistent kernel; a fixed value keeps profiled runs on the kernel the plain run uses")
+                    help="2-D stepping kernel: 0 = autotune (default), k = blocked k steps per launch; "
+                         "a fixed value keeps profiled runs on the kernel the plain run uses")
     ap.add_argument("--residual", default="df64", choices=["df64", "fp64"],
                     help="FP32 stepping: precision of the b and residual wave solves of the correction "
                          "(df64 = pairs of FP32 with error-free arithmetic; the accuracy check always uses FP64)")

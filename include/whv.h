@@ -149,8 +149,7 @@ whv_status whv_set_speed(whv_grid grid, const double* c2_dev);
  * (c^2_{j+1/2} (u_{j+1} - u_j) - c^2_{j-1/2} (u_j - u_{j-1})) / h^2, face values the mean of the
  * two nodes' c^2 (the adjacent interior value on the faces to the boundary nodes).  This operator
  * is symmetric in the Euclidean inner product, which all Krylov and deflation products then use.
- * Its wave solves run one step per launch (the blocked, persistent and single-CTA kernels are
- * bypassed); whv_solve_batched and whv_solve_adjoint refuse such grids.  Extra device memory:
+ * Its wave solves run one step per launch (the blocked and single-CTA kernels are bypassed); whv_solve_batched and whv_solve_adjoint refuse such grids.  Extra device memory:
  * dim N doubles + dim N floats of face values. */
 whv_status whv_set_speed_form(whv_grid grid, const double* c2_dev, int form);
 
@@ -245,24 +244,19 @@ whv_status whv_solve(whv_grid grid, const whv_params* p, const double* f_dev, in
 
 /* Steps per sweep k of the temporally blocked 2-D stencil kernel: each launch advances k leapfrog
  * steps of the f = 0 wave solves in shared memory (halo of width k r).  k = 1 launches one kernel
- * per time step, k = 0 restores the default (8 for FP32 stepping, 1 for FP64), k <= 16.  2-D
+ * per time step, k = 0 restores the default (8 for FP32 stepping, 1 for FP64), 0 <= k <= 16.  2-D
  * grids block k steps; 3-D second-order constant-speed FP32 grids take any k >= 2 as two steps per
  * launch (z-marching, W^{n+1} staged plane by plane); other grids step once per launch.  With the
  * default (k = 0) grids of at
  * most 4096 unknowns run each whole wave solve in a single CTA (state in shared memory, one
- * barrier per step); an explicit k turns that off.
- * k < 0 (2-D grids, -16 <= k): the persistent kernel -- the whole wave solve (forced or not) is
- * ONE cooperative launch with one 1024-thread CTA per 64 x 64 staged tile, the tile state kept in
- * registers for all steps and the halo exchanged through L2 every |k| steps at a grid barrier
- * (bounded wait; see whv_inject_barrier_error).  Used while the tiles fit on the GPU at once
- * (e.g. 511^2 unknowns with |k| <= 10 on 148 SMs), otherwise the default path runs.
+ * barrier per step); an explicit k turns that off.  Other values: WHV_ERR_INVALID.
  * whv_get_steps_per_sweep returns the value in effect (0 on the small grids above). */
 whv_status whv_set_steps_per_sweep(whv_grid grid, int k);
 whv_status whv_get_steps_per_sweep(whv_grid grid, int* k);
 
 /* Autotuner: times f = 0 wave solves of p's time grid for each candidate steps-per-sweep value
- * (1, 2, 4, 6, 8, 10, 12, 16 on 2-D grids, and the persistent kernel -4 ... -12 where its tiles
- * fit; small grids keep the single-CTA solve, *best = 0) with CUDA events on the grid's stream and
+ * (1, 2, 4, 6, 8, 10, 12, 16 on 2-D grids, 1 and 2 on 3-D constant-speed FP32 grids; small
+ * grids keep the single-CTA solve, *best = 0) with CUDA events on the grid's stream and
  * keeps the fastest; *best (host, may be NULL) receives it.  Overwrites the grid's internal work vectors,
  * synchronises the stream.  Must not be called while the grid's stream is being captured. */
 whv_status whv_autotune(whv_grid grid, const whv_params* p, int* best);
@@ -405,11 +399,14 @@ whv_status whv_project_noalloc(int64_t n, int nd, const double* W_dev, const dou
  * keep up to full rank).  Needs a dense basis (WHV_ERR_INVALID otherwise, or if every rank is 0). */
 whv_status whv_compress_basis(whv_grid grid, double tau, int* ranks_host);
 
-/* Test hook for the failure path of the persistent wave solve (no counterpart in the paper):
- * raises the grid's barrier error flag, so that the next persistent wave solve on this grid leaves
- * at its first grid barrier exactly as after a barrier wait that timed out -- its output is NaN
- * and the whv_solve / whv_solve_adjoint / whv_lanczos call that ran it returns WHV_ERR_TIMEOUT and
- * re-arms the barrier.  No GPU wait is made to run out. */
+/* Test hook for the failure path of the grid barriers of the batched persistent kernels (no
+ * counterpart in the paper): marks the grid so that the next whv_solve_batched,
+ * whv_apply_pi_batched or whv_autotune_batched call that includes it starts with the batch's
+ * barrier error flag raised.  Every CTA of its first batched wave solve then leaves at its first
+ * grid barrier exactly as after a barrier wait that gave up; the call returns WHV_ERR_TIMEOUT
+ * (outputs unspecified) and the mark is cleared, so the next batched call runs normally.  No GPU
+ * wait is made to run out.  Single-grid calls ignore the mark (their kernels have no grid
+ * barrier). */
 whv_status whv_inject_barrier_error(whv_grid grid);
 
 /* Number of interior unknowns N of the grid (0 for NULL). */

@@ -1704,6 +1704,18 @@ static whv_status run_wave(BatchCtx& c, const Wave& w) {
   return WHV_OK;
 }
 
+// The barrier error flag starts at zero, or raised (any nonzero value) when whv_inject_barrier_error
+// marked one of the grids: then every CTA of the first batched wave solve leaves at its first grid
+// barrier exactly as after a wait that gave up, and the call reports WHV_ERR_TIMEOUT.
+static cudaError_t clear_err(BatchCtx& c) {
+  bool fault = false;
+  for (int p = 0; p < c.np; ++p) {
+    fault = fault || c.grids[p]->barrier_fault;
+    c.grids[p]->barrier_fault = false;
+  }
+  return cudaMemsetAsync(c.err, fault ? 0x01 : 0, sizeof(int), c.st);
+}
+
 static whv_status check_barrier(BatchCtx& c) {
   int herr = 0;
   B_CUDA(c.g0, cudaMemcpyAsync(&herr, c.err, sizeof(int), cudaMemcpyDeviceToHost, c.st));
@@ -2246,7 +2258,7 @@ extern "C" whv_status whv_autotune_batched(int nprob, const whv_grid* grids, con
   B_CUDA(g0, c.alloc(&c.bar, 2 * sizeof(unsigned)));
   B_CUDA(g0, c.alloc(&c.err, sizeof(int)));
   B_CUDA(g0, cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), c.st));
-  B_CUDA(g0, cudaMemsetAsync(c.err, 0, sizeof(int), c.st));
+  B_CUDA(g0, clear_err(c));
   RoleIO io;
   io.v.assign(nprob, nullptr);
   io.f.assign(nprob, nullptr);
@@ -2332,7 +2344,7 @@ extern "C" whv_status whv_apply_pi_batched(int nprob, const whv_grid* grids, con
   B_CUDA(g0, c.alloc(&c.bar, 2 * sizeof(unsigned)));
   B_CUDA(g0, c.alloc(&c.err, sizeof(int)));
   B_CUDA(g0, cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), c.st));
-  B_CUDA(g0, cudaMemsetAsync(c.err, 0, sizeof(int), c.st));
+  B_CUDA(g0, clear_err(c));
   RoleIO io;
   io.v.assign(nprob, nullptr);
   io.f.assign(nprob, nullptr);
@@ -2412,7 +2424,7 @@ extern "C" whv_status whv_solve_batched(int nprob, const whv_grid* grids, const 
     B_CUDA(g0, cudaMemcpy(c.scal, sc.data(), nprob * sizeof(double*), cudaMemcpyHostToDevice));
   }
   B_CUDA(g0, cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), c.st));
-  B_CUDA(g0, cudaMemsetAsync(c.err, 0, sizeof(int), c.st));
+  B_CUDA(g0, clear_err(c));
   whv_status s;
   switch (g0->dim * 10 + g0->order) {
     case 22: s = batched_vc<2, 2>(c, f_dev, u_dev, refine, infos, varc); break;

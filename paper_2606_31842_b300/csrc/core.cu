@@ -152,7 +152,7 @@ static void free_all(whv_grid g) {
   if (!g) return;
   free_plan(g);
   void* ptrs[] = {g->c2, g->c2f, g->mw, g->wbuf[0], g->wbuf[1], g->wbuf[2], g->wbuf[3], g->acc, g->x, g->r, g->p, g->q,
-                  g->t, g->fd, g->krylov, g->small, g->small2, g->partials, g->counters, g->gbar, g->scal,
+                  g->t, g->fd, g->krylov, g->small, g->small2, g->partials, g->counters, g->scal,
                   g->basis.d_coef, g->basis.AW, g->basis.Einv, g->basis.QAW, g->basis.cU, g->basis.cV,
                   g->basis.cs, g->basis.cT, g->basis.cc, g->basis.cR, g->basis.coff, g->basis.cowner, g->wbuf64[0], g->wbuf64[1], g->wbuf64[2],
                   g->wbuf64[3], g->acc64, g->tw[0], g->tw[1], g->tw[2], g->tw[3], g->tacc, g->xo, g->ro, g->bo, g->wtab_small, g->face64[0], g->face64[1],
@@ -222,7 +222,6 @@ whv_status whv_create_grid(int dim, const int64_t npts[3], const double lo[3], c
       {(void**)&g->small, (size_t)kMaxND * 8}, {(void**)&g->small2, (size_t)kMaxND * 8},
       {(void**)&g->partials, 0},   // sized below
       {(void**)&g->counters, (size_t)CH_NCH * sizeof(unsigned)},
-      {(void**)&g->gbar, 4 * sizeof(unsigned)},
       {(void**)&g->scal, (size_t)S_NSLOTS * 8}};
   // reduction channels: step kernels (<= N/256 blocks + slack), grid-stride reductions
   // (2 x kRedBlocks: the speed set-up keeps block maxima after the sums), projections
@@ -246,7 +245,6 @@ whv_status whv_create_grid(int dim, const int64_t npts[3], const double lo[3], c
   }
   e = cudaMallocHost((void**)&g->scal_host, S_NSLOTS * 8);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->counters, 0, CH_NCH * sizeof(unsigned), g->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(g->gbar, 0, 4 * sizeof(unsigned), g->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->scal, 0, S_NSLOTS * 8, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) {

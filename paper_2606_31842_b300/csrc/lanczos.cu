@@ -588,18 +588,12 @@ static whv_status lanczos_thick_impl(whv_grid g, const whv_params* p, int nd, in
 
 extern "C" whv_status whv_lanczos(whv_grid g, const whv_params* p, int nd, int m, const double* v0_dev,
                                   int fp64_stepping, int flags, double* theta_host, double* resid_host) {
-  const whv_status s = lanczos_impl(g, p, nd, m, v0_dev, fp64_stepping, flags, theta_host, resid_host);
-  if (!g) return s;
-  const whv_status e = take_persist_error(g);   // a persistent wave solve that gave up
-  return e != WHV_OK ? e : s;
+  return lanczos_impl(g, p, nd, m, v0_dev, fp64_stepping, flags, theta_host, resid_host);
 }
 
 extern "C" whv_status whv_lanczos_restarted(whv_grid g, const whv_params* p, int nd, int m, int keep,
                                             int max_restarts, double tol, const double* v0_dev, int fp64_stepping,
                                             int flags, double* theta_host, double* resid_host, int* stats_host) {
-  const whv_status s = lanczos_thick_impl(g, p, nd, m, keep, max_restarts, tol, v0_dev, fp64_stepping, flags,
-                                          theta_host, resid_host, stats_host);
-  if (!g) return s;
-  const whv_status e = take_persist_error(g);   // a persistent wave solve that gave up
-  return e != WHV_OK ? e : s;
+  return lanczos_thick_impl(g, p, nd, m, keep, max_restarts, tol, v0_dev, fp64_stepping, flags, theta_host,
+                            resid_host, stats_host);
 }

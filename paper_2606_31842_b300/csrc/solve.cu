@@ -1002,23 +1002,15 @@ static whv_status adjoint_impl(whv_grid g, const whv_params* p, const double* f,
   return WHV_OK;
 }
 
-// A persistent wave solve that gave up at a grid barrier makes its output NaN, which surfaces as
-// a breakdown or a non-finite right-hand side; report it as the timeout it was.
 extern "C" whv_status whv_solve(whv_grid g, const whv_params* p, const double* f, int use_guess,
                                 double* u, whv_info* info) {
-  const whv_status s = solve_impl(g, p, f, use_guess, u, info);
-  if (!g) return s;
-  const whv_status e = take_persist_error(g);
-  return e != WHV_OK ? e : s;
+  return solve_impl(g, p, f, use_guess, u, info);
 }
 
 extern "C" whv_status whv_solve_adjoint(whv_grid g, const whv_params* p, const double* f, const double* u,
                                         const double* dLdu, double* z, double* grad_c2, double* grad_f,
                                         int checkpoint_every, whv_info* info) {
-  const whv_status s = adjoint_impl(g, p, f, u, dLdu, z, grad_c2, grad_f, checkpoint_every, info);
-  if (!g) return s;
-  const whv_status e = take_persist_error(g);
-  return e != WHV_OK ? e : s;
+  return adjoint_impl(g, p, f, u, dLdu, z, grad_c2, grad_f, checkpoint_every, info);
 }
 
 // Vector-Jacobian product of out = Pi_h(v; f, c^2) (the reverse sweep on its own): for the seed
@@ -1049,17 +1041,12 @@ static whv_status vjp_impl(whv_grid g, const whv_params* p, const double* v, con
 extern "C" whv_status whv_apply_pi_vjp(whv_grid g, const whv_params* p, const double* v, const double* f,
                                        const double* abar, double* vbar, double* c2bar, double* fbar,
                                        int checkpoint_every) {
-  const whv_status s = vjp_impl(g, p, v, f, abar, vbar, c2bar, fbar, checkpoint_every);
-  if (!g) return s;
-  const whv_status e = take_persist_error(g);
-  return e != WHV_OK ? e : s;
+  return vjp_impl(g, p, v, f, abar, vbar, c2bar, fbar, checkpoint_every);
 }
 
 extern "C" whv_status whv_inject_barrier_error(whv_grid g) {
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
-  const unsigned one = 1u;
-  WHV_CUDA(g, cudaMemcpyAsync(g->gbar + 2, &one, sizeof(unsigned), cudaMemcpyHostToDevice, g->stream));
-  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
+  g->barrier_fault = true;
   return WHV_OK;
 }
 
@@ -1126,9 +1113,7 @@ extern "C" whv_status whv_solve_many(whv_grid g, const whv_params* p, int nrhs, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) { cleanup(); return cuda_fail(g, e, "whv_solve_many: deflation of the forcings"); }
     for (int j = 0; j < nrhs; ++j) {
-      whv_status st = solve_impl(g, p, hf[j], 0, hu[j], infos ? infos + j : nullptr, hu[j]);
-      const whv_status te = take_persist_error(g);
-      if (te != WHV_OK) st = te;
+      const whv_status st = solve_impl(g, p, hf[j], 0, hu[j], infos ? infos + j : nullptr, hu[j]);
       if (st == WHV_ERR_NOT_CONVERGED) { worst = st; continue; }
       if (st != WHV_OK) { cleanup(); return st; }
     }

@@ -845,12 +845,6 @@ static whv_status launch_wave_solve(whv_grid g, const TimeGridH& tg, const doubl
     *nl = 1;
     return small_wave_solve(g, tg, v, f, out, epi, prec);
   }
-  // persistent 2-D wave solve (one cooperative launch) when selected and the tiles fit
-  if (!g->cons && prec == g->precision && g->kblock < 0 && persist_fits(g, -g->kblock, prec) &&
-      small_tables(g, tg) >= 0) {
-    *nl = 1;
-    return persist_wave_solve(g, tg, v, f, out, epi, -g->kblock, prec, g->wbuf);
-  }
   if (prec == g->precision) {
     const BufSet B{g->wbuf, g->acc, g->cons ? 1 : (g->kblock > 0 ? g->kblock : default_kblock(g))};
     return prec == WHV_FP64 ? dispatch<double>(g, tg, v, f, out, epi, nl, B)
@@ -903,19 +897,7 @@ void free_plan(whv_grid g) {
 }
 
 static bool uses_tables(whv_grid g) {
-  return !g->cons && ((small_grid(g) && g->kblock == 0) || (g->dim == 2 && g->kblock < 0));
-}
-
-whv_status take_persist_error(whv_grid g) {
-  double e = 0.0;
-  WHV_CUDA(g, cudaMemcpyAsync(&e, g->scal + S_ERR, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
-  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
-  if (e == 0.0) return WHV_OK;
-  // re-arm the barrier and the flag so that the grid can be used again
-  WHV_CUDA(g, cudaMemsetAsync(g->gbar, 0, 4 * sizeof(unsigned), g->stream));
-  WHV_CUDA(g, cudaMemsetAsync(g->scal + S_ERR, 0, sizeof(double), g->stream));
-  WHV_CUDA(g, cudaStreamSynchronize(g->stream));
-  return fail(g, WHV_ERR_TIMEOUT, "persistent wave solve: a grid barrier wait gave up (results were NaN)");
+  return !g->cons && small_grid(g) && g->kblock == 0;
 }
 
 whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
@@ -923,7 +905,7 @@ whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const do
   if (prec < 0) prec = g->precision;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   WHV_CUDA(g, cudaStreamIsCapturing(g->stream, &cs));
-  // small grids and the persistent kernel read the device weight table: a new time grid replaces
+  // small grids read the device weight table: a new time grid replaces
   // it, so graphs captured with the old one are dropped before anything is replayed
   if (cs == cudaStreamCaptureStatusNone && uses_tables(g) && small_tables(g, tg) == 1) free_plan(g);
   if (cs != cudaStreamCaptureStatusNone) {  // caller is capturing: record the launches into its graph
@@ -991,8 +973,7 @@ extern "C" whv_status whv_apply_pi(whv_grid g, const whv_params* p, const double
 
 extern "C" whv_status whv_set_steps_per_sweep(whv_grid g, int k) {
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
-  if (k < -16 || k > 16) return fail(g, WHV_ERR_INVALID, "steps per sweep must be in [-16, 16]");
-  if (k < 0 && g->dim != 2) return fail(g, WHV_ERR_INVALID, "the persistent kernel (k < 0) is 2-D only");
+  if (k < 0 || k > 16) return fail(g, WHV_ERR_INVALID, "steps per sweep must be in [0, 16]");
   g->kblock = k;
   return WHV_OK;
 }
@@ -1020,15 +1001,11 @@ extern "C" whv_status whv_autotune(whv_grid g, const whv_params* p, int* best) {
     if (best) *best = 1;
     return WHV_OK;
   }
-  // 2-D: per step, blocked sweeps of k steps, and the persistent kernel (-k) where its tiles fit;
-  // 3-D FP32 (c = 1): per step and two steps per launch
+  // 2-D: per step and blocked sweeps of k steps; 3-D FP32 (c = 1): per step and two steps per launch
   std::vector<int> cands = {1};
   if (g->dim == 3 && g->order == 2 && !g->c2 && g->precision == WHV_FP32_STEP) cands.push_back(2);
-  if (g->dim == 2) {
+  if (g->dim == 2)
     for (int k : {2, 4, 6, 8, 10, 12, 16}) cands.push_back(k);
-    for (int k : {4, 6, 8, 10, 12})
-      if (persist_fits(g, k, g->precision)) cands.push_back(-k);
-  }
   const int nc = (int)cands.size();
   cudaEvent_t e0, e1;
   WHV_CUDA(g, cudaEventCreate(&e0));

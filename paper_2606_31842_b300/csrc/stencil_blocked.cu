@@ -235,14 +235,11 @@ static void set_attrs() {
 // stream capture)
 void small_init();
 
-void persist_init();
-
 void blocked_init() {
   static bool done = false;
   if (done) return;
   done = true;
   small_init();
-  persist_init();
   set_attrs<float, 2, false>(); set_attrs<float, 2, true>(); set_attrs<float, 4, false>(); set_attrs<float, 4, true>();
   set_attrs<double, 2, false>(); set_attrs<double, 2, true>(); set_attrs<double, 4, false>(); set_attrs<double, 4, true>();
 }
@@ -326,293 +323,6 @@ template whv_status blocked_steps_2d<double, 2, false>(whv_grid, const TimeGridH
 template whv_status blocked_steps_2d<double, 2, true>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
 template whv_status blocked_steps_2d<double, 4, false>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
 template whv_status blocked_steps_2d<double, 4, true>(whv_grid, const TimeGridH&, const double*, double*, int, int, int*, void* const*, void*);
-
-// ------------------------------------------------------------------ persistent 2-D wave solve
-// One cooperative launch performs the whole wave solve of a 2-D grid whose tiles all fit on the
-// GPU at once (one 1024-thread CTA per tile, one CTA per SM).  Each CTA keeps the W^n, W^{n-1}
-// and filter sum of its tile cells in registers for all Nt steps.  A sweep advances its 64 x 64
-// staged region k steps exactly as k_block2d does (halo kr, redundant halo updates); then the
-// CTA publishes its tile through L2 (the grid's stepping buffers, the two (W^{n-1}, W^n) pairs
-// alternating per sweep), all CTAs meet at a grid barrier, and each reads back only the halo
-// ring around its tile.  Compared with one k_block2d launch per sweep this removes the launch
-// gaps, the reload of the whole region and the read-modify-write of the filter accumulator.
-// The first sweep starts from W^0 = v with the Taylor step; after the last one the FP64 epilogue
-// (out = Pi_h v, or out = v - Pi_h v with p^T M out reduced over the grid) is written.  If a
-// barrier wait gives up, every CTA writes NaN to its part of out, S_FLAG and S_ERR are raised and
-// the grid's barrier state must be reset before the next launch.
-template <typename T>
-struct PersistArgs {
-  T* w[4];
-  const double* v;         // W^0 (nullptr: 0)
-  const double* f;         // forcing (FORCED)
-  double* out;
-  const T* c2;             // VARC
-  const double* mw;
-  double* partials;        // epi 1: grid reduction of p^T M out
-  unsigned* counter;
-  double* scal;
-  const double* wtab;      // w_n, n = 0..nt
-  const double* ptab;      // cos(omega_hat t^n), n = 0..nt
-  unsigned* bar;           // count, generation, error
-  int nx, ny, nt, K, tiles_x, epi;
-  T ih2x, ih2y, dt2, ax, ay, b;
-};
-
-template <typename T, int ORDER, bool VARC, bool FORCED>
-__global__ void __launch_bounds__(kBlkThreads, 1) k_wave2d_persist(PersistArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* const S0 = reinterpret_cast<T*>(smem_raw);
-  T* const S1 = S0 + kReg * kReg;
-  constexpr int R = ORDER == 2 ? 1 : 2;
-  const int H = a.K * R, TW = kReg - 2 * H;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = 32 * (warp & 1) + lane;
-  const int jb = warp >> 1;
-  const int x0 = (blockIdx.x % a.tiles_x) * TW - H, y0 = (blockIdx.x / a.tiles_x) * TW - H;
-  const int nx = a.nx, ny = a.ny;
-  const int gx = x0 + i;
-  const bool colin = gx >= 0 && gx < nx;
-  const bool coltile = colin && i >= H && i < kReg - H;
-  T cur[kRowsPerThread], prv[kRowsPerThread], acr[kRowsPerThread];
-  T cc[VARC ? kRowsPerThread : 1];
-  T ff[FORCED ? kRowsPerThread : 1];
-  const T w0 = (T)a.wtab[0];
-#pragma unroll
-  for (int r = 0; r < kRowsPerThread; ++r) {
-    const int gy = y0 + jb + kRowPitch * r;
-    const bool in = colin && gy >= 0 && gy < ny;
-    const int64_t gi = gx + (int64_t)nx * gy;
-    cur[r] = (in && a.v) ? (T)__ldg(a.v + gi) : T(0);
-    prv[r] = T(0);
-    if (VARC) cc[r] = in ? __ldg(a.c2 + gi) : T(0);
-    if (FORCED) ff[r] = in ? (T)__ldg(a.f + gi) : T(0);
-    acr[r] = w0 * cur[r];
-  }
-  const int J = (a.nt + a.K - 1) / a.K;
-  bool ok = true;
-  for (int j = 0; j < J; ++j) {
-    const int n0 = j * a.K;
-    const int kk = min(a.K, a.nt - n0);
-    if (j > 0) {   // halo ring from the neighbours' tiles published by the previous sweep
-      const int qi = (j + 1) & 1;
-#pragma unroll
-      for (int r = 0; r < kRowsPerThread; ++r) {
-        const int jr = jb + kRowPitch * r;
-        const int gy = y0 + jr;
-        if (coltile && jr >= H && jr < kReg - H) continue;   // own tile cell: registers are current
-        const bool in = colin && gy >= 0 && gy < ny;
-        const int64_t gi = gx + (int64_t)nx * gy;
-        cur[r] = in ? __ldcg(a.w[2 * qi + 1] + gi) : T(0);
-        prv[r] = in ? __ldcg(a.w[2 * qi] + gi) : T(0);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < kRowsPerThread; ++r) S0[(jb + kRowPitch * r) * kReg + i] = cur[r];
-    __syncthreads();
-    T* Ain = S0;
-    T* Bout = S1;
-    for (int s = 1; s <= kk; ++s) {
-      const int n = n0 + s - 1;   // W^n -> W^{n+1}
-      const int lo = s * R, hi = kReg - s * R;
-      const bool colact = colin && i >= lo && i < hi;
-      const T ws = (T)a.wtab[n + 1];
-      const T fph = FORCED ? (n > 0 ? a.dt2 : T(0.5) * a.dt2) * (T)a.ptab[n] : T(0);
-#pragma unroll
-      for (int r = 0; r < kRowsPerThread; ++r) {
-        const int jr = jb + kRowPitch * r;
-        const int gy = y0 + jr;
-        if (colact && jr >= lo && jr < hi && gy >= 0 && gy < ny) {
-          const int l = jr * kReg + i;
-          const T c = cur[r];
-          T wn;
-          if (ORDER == 2 && !VARC && n > 0) {
-            T u = fma(a.b, c, -prv[r]);
-            u = fma(a.ax, (gx > 0 ? Ain[l - 1] : T(0)) + (gx < nx - 1 ? Ain[l + 1] : T(0)), u);
-            wn = fma(a.ay, (gy > 0 ? Ain[l - kReg] : T(0)) + (gy < ny - 1 ? Ain[l + kReg] : T(0)), u);
-          } else {
-            T L = d2s<ORDER>(Ain, l, gx, nx, 1, c) * a.ih2x;
-            L = fma(d2s<ORDER>(Ain, l, gy, ny, kReg, c), a.ih2y, L);
-            if (VARC) L *= cc[r];
-            wn = n > 0 ? fma(a.dt2, L, fma(T(2), c, -prv[r]))
-                       : fma(T(0.5) * a.dt2, L, c);   // Taylor start: W^1 = W^0 + dt^2/2 L W^0
-          }
-          if (FORCED) wn = fma(-fph, ff[r], wn);
-          prv[r] = c;
-          cur[r] = wn;
-          Bout[l] = wn;
-          acr[r] = fma(ws, wn, acr[r]);
-        }
-      }
-      __syncthreads();
-      T* tmp = Ain;
-      Ain = Bout;
-      Bout = tmp;
-    }
-    if (n0 + kk < a.nt) {   // publish the tile, then wait for every other CTA to publish theirs
-      const int qo = j & 1;
-#pragma unroll
-      for (int r = 0; r < kRowsPerThread; ++r) {
-        const int jr = jb + kRowPitch * r;
-        const int gy = y0 + jr;
-        if (!(coltile && jr >= H && jr < kReg - H && gy >= 0 && gy < ny)) continue;
-        const int64_t gi = gx + (int64_t)nx * gy;
-        a.w[2 * qo + 1][gi] = cur[r];
-        a.w[2 * qo][gi] = prv[r];
-      }
-      if (!grid_barrier(a.bar, a.bar + 1, reinterpret_cast<int*>(a.bar + 2), gridDim.x)) { ok = false; break; }
-    }
-  }
-  double part = 0.0;
-#pragma unroll
-  for (int r = 0; r < kRowsPerThread; ++r) {
-    const int jr = jb + kRowPitch * r;
-    const int gy = y0 + jr;
-    if (!(coltile && jr >= H && jr < kReg - H && gy >= 0 && gy < ny)) continue;
-    const int64_t gi = gx + (int64_t)nx * gy;
-    if (!ok) {
-      a.out[gi] = __longlong_as_double(0x7ff8000000000000ll);   // NaN: the solve did not complete
-    } else if (a.epi == 0) {
-      a.out[gi] = (double)acr[r];
-    } else {
-      const double vi = __ldg(a.v + gi);
-      const double o = vi - (double)acr[r];
-      a.out[gi] = o;
-      part = fma(a.mw ? vi * __ldg(a.mw + gi) : vi, o, part);
-    }
-  }
-  if (!ok) {   // uniform over the CTAs: every CTA leaves at the failed barrier
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      a.scal[S_FLAG] = 1.0;
-      a.scal[S_ERR] = 1.0;
-    }
-    return;
-  }
-  if (a.epi == 1) {
-    part = block_sum(part);
-    double total;
-    if (grid_reduce(part, a.partials, a.counter, &total) && flat_tid() == 0) a.scal[S_PQ] = total;
-  }
-}
-
-static int persist_tiles(whv_grid g, int k) {
-  const int R = g->order == 2 ? 1 : 2;
-  const int TW = kReg - 2 * k * R;
-  if (TW < 16) return -1;
-  return ((g->n[0] + TW - 1) / TW) * ((g->n[1] + TW - 1) / TW);
-}
-
-template <typename T, int ORDER, bool VARC, bool FORCED>
-static int persist_capacity() {
-  static int cap = -1;
-  if (cap < 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wave2d_persist<T, ORDER, VARC, FORCED>, kBlkThreads,
-                                                  2 * kReg * kReg * sizeof(T));
-    cap = per_sm * sms;
-  }
-  return cap;
-}
-
-// all variants share the launch shape; the forced one needs the fewest registers to spare
-template <typename T>
-static int persist_cap_of(whv_grid g) {
-  const bool varc = g->c2 != nullptr;
-  int c;
-  if (g->order == 2)
-    c = varc ? std::min(persist_capacity<T, 2, true, false>(), persist_capacity<T, 2, true, true>())
-             : std::min(persist_capacity<T, 2, false, false>(), persist_capacity<T, 2, false, true>());
-  else
-    c = varc ? std::min(persist_capacity<T, 4, true, false>(), persist_capacity<T, 4, true, true>())
-             : std::min(persist_capacity<T, 4, false, false>(), persist_capacity<T, 4, false, true>());
-  return c;
-}
-
-bool persist_fits(whv_grid g, int k, int prec) {
-  if (g->dim != 2 || k < 1 || k > kBlkMaxK) return false;
-  const int nt = persist_tiles(g, k);
-  if (nt < 1) return false;
-  return nt <= (prec == WHV_FP64 ? persist_cap_of<double>(g) : persist_cap_of<float>(g));
-}
-
-template <typename T, int ORDER, bool VARC, bool FORCED>
-static cudaError_t persist_launch(whv_grid g, const PersistArgs<T>& a, int ntiles) {
-  PersistArgs<T> arg = a;
-  void* args[] = {(void*)&arg};
-  return cudaLaunchCooperativeKernel((const void*)k_wave2d_persist<T, ORDER, VARC, FORCED>, dim3(ntiles),
-                                     dim3(kBlkThreads), args, 2 * kReg * kReg * sizeof(T), g->stream);
-}
-
-template <typename T>
-static whv_status persist_t(whv_grid g, const TimeGridH& tg, const double* v, const double* f, double* out, int epi,
-                            int k, void* const* bufs) {
-  PersistArgs<T> a{};
-  for (int m = 0; m < 4; ++m) a.w[m] = (T*)bufs[m];
-  a.v = v; a.f = f; a.out = out;
-  a.c2 = g->c2 ? (const T*)(sizeof(T) == 8 ? (const void*)g->c2 : (const void*)g->c2f) : nullptr;
-  a.mw = g->mw;
-  a.partials = chan(g, CH_STEP);
-  a.counter = g->counters + CH_STEP;
-  a.scal = g->scal;
-  a.wtab = g->wtab_small;
-  a.ptab = g->wtab_small + (tg.nt + 1);
-  a.bar = g->gbar;
-  a.nx = g->n[0]; a.ny = g->n[1]; a.nt = tg.nt; a.K = k; a.epi = epi;
-  const int R = g->order == 2 ? 1 : 2;
-  const int TW = kReg - 2 * k * R;
-  a.tiles_x = (g->n[0] + TW - 1) / TW;
-  const int ntiles = a.tiles_x * ((g->n[1] + TW - 1) / TW);
-  if (ntiles > chan_cap(g, CH_STEP)) return fail(g, WHV_ERR_INVALID, "grid too large for the fused reduction");
-  const double h2x = g->h[0] * g->h[0], h2y = g->h[1] * g->h[1];
-  a.ih2x = (T)(g->order == 2 ? 1.0 / h2x : 1.0 / (12.0 * h2x));
-  a.ih2y = (T)(g->order == 2 ? 1.0 / h2y : 1.0 / (12.0 * h2y));
-  a.dt2 = (T)(tg.dt * tg.dt);
-  const double ax = tg.dt * tg.dt / h2x, ay = tg.dt * tg.dt / h2y;
-  a.ax = (T)ax; a.ay = (T)ay; a.b = (T)(2.0 - 2.0 * (ax + ay));
-  const bool varc = g->c2 != nullptr, forced = f != nullptr;
-  cudaError_t e;
-  if (g->order == 2) {
-    if (varc) e = forced ? persist_launch<T, 2, true, true>(g, a, ntiles) : persist_launch<T, 2, true, false>(g, a, ntiles);
-    else e = forced ? persist_launch<T, 2, false, true>(g, a, ntiles) : persist_launch<T, 2, false, false>(g, a, ntiles);
-  } else {
-    if (varc) e = forced ? persist_launch<T, 4, true, true>(g, a, ntiles) : persist_launch<T, 4, true, false>(g, a, ntiles);
-    else e = forced ? persist_launch<T, 4, false, true>(g, a, ntiles) : persist_launch<T, 4, false, false>(g, a, ntiles);
-  }
-  if (e != cudaSuccess) return cuda_fail(g, e, "k_wave2d_persist launch");
-  return WHV_OK;
-}
-
-whv_status persist_wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f, double* out,
-                              int epi, int k, int prec, void* const* bufs) {
-  return prec == WHV_FP64 ? persist_t<double>(g, tg, v, f, out, epi, k, bufs)
-                          : persist_t<float>(g, tg, v, f, out, epi, k, bufs);
-}
-
-template <typename T, int ORDER, bool VARC>
-static void persist_attrs() {
-  const int bytes = 2 * kReg * kReg * (int)sizeof(T);
-  cudaFuncSetAttribute(k_wave2d_persist<T, ORDER, VARC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_wave2d_persist<T, ORDER, VARC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
-// shared-memory opt-in and the co-residency capacity of every variant, once per process and
-// outside any stream capture
-template <typename T>
-static void persist_caps() {
-  persist_capacity<T, 2, false, false>(); persist_capacity<T, 2, false, true>();
-  persist_capacity<T, 2, true, false>(); persist_capacity<T, 2, true, true>();
-  persist_capacity<T, 4, false, false>(); persist_capacity<T, 4, false, true>();
-  persist_capacity<T, 4, true, false>(); persist_capacity<T, 4, true, true>();
-}
-
-void persist_init() {
-  persist_attrs<float, 2, false>(); persist_attrs<float, 2, true>(); persist_attrs<float, 4, false>();
-  persist_attrs<float, 4, true>(); persist_attrs<double, 2, false>(); persist_attrs<double, 2, true>();
-  persist_attrs<double, 4, false>(); persist_attrs<double, 4, true>();
-  persist_caps<float>();
-  persist_caps<double>();
-}
 
 }  // namespace whv
 

@@ -28,7 +28,6 @@ enum Slot {
   S_STOP = 9,   // tol^2 rr0: the loop runs while r^T M r > S_STOP
   S_MAXIT = 10, // iteration limit of the device-resident CG loop
   S_HALT = 11,  // batched solves: nonzero once this problem has stopped (its kernels return)
-  S_ERR = 12,   // a persistent wave-solve kernel gave up at a grid barrier (output is NaN)
   S_NSLOTS = 16
 };
 
@@ -100,8 +99,7 @@ struct whv_grid_s {
   int cons = 0;                // 1: L_h = div_h(c^2 grad_h) (whv_set_speed_form), Euclidean inner products
   double* face64[3] = {nullptr, nullptr, nullptr};   // its face values per axis (FP64, FP32)
   float* face32[3] = {nullptr, nullptr, nullptr};
-  int kblock = 0;              // steps per sweep of the blocked 2-D kernel (0: default, 1: off,
-                               // < 0: persistent kernel with -kblock steps per sweep)
+  int kblock = 0;              // steps per sweep of the blocked 2-D kernel (0: default, 1: off)
   // FP64 stepping buffers of an FP32-stepping grid (FP64 residual correction), allocated on
   // first use, with the outer solution / residual / right-hand side of the refinement loop
   void* wbuf64[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -129,7 +127,8 @@ struct whv_grid_s {
   double* partials = nullptr;  // reduction scratch, one region per channel
   int64_t chan_off[4] = {0, 0, 0, 0}, chan_cap[4] = {0, 0, 0, 0};
   unsigned* counters = nullptr;// CH_NCH
-  unsigned* gbar = nullptr;    // grid barrier of the persistent wave solve: count, generation, error
+  bool barrier_fault = false;  // whv_inject_barrier_error: the next batched solve starts with its
+                               // barrier error flag raised
   double* scal = nullptr;      // S_NSLOTS device scalars
   double* scal_host = nullptr; // pinned mirror
 
@@ -200,8 +199,6 @@ constexpr int kPrecDF64 = 2;
 whv_status wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f,
                       double* out, int epi, int prec = -1);
 void free_plan(whv_grid g);
-// a persistent wave solve gave up at a grid barrier since the last call: re-arm and report
-whv_status take_persist_error(whv_grid g);
 void free_cgloop(whv_grid g);
 int default_kblock(whv_grid g);
 whv_status ensure_fp64_buffers(whv_grid g);
@@ -213,11 +210,6 @@ whv_status blocked_steps_2d(whv_grid g, const TimeGridH& tg, const double* v, do
                             int k_want, int* launches, void* const* bufs, void* acc);
 void blocked_init();
 
-// persistent 2-D wave solve (stencil_blocked.cu): one cooperative launch, tiles resident in
-// registers, halo exchange through the stepping buffers every k steps
-bool persist_fits(whv_grid g, int k, int prec);
-whv_status persist_wave_solve(whv_grid g, const TimeGridH& tg, const double* v, const double* f, double* out,
-                              int epi, int k, int prec, void* const* bufs);
 // single-CTA wave solve for small grids (stencil_blocked.cu)
 bool small_grid(whv_grid g);
 int small_tables(whv_grid g, const TimeGridH& tg);   // 0 current, 1 uploaded, -1 stale

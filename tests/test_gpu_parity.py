@@ -331,11 +331,10 @@ BLK_CASES = [((70, 45), 2, None, 14.0), ((37, 61), 4, "c3", 11.0), ((101, 99), 2
 
 
 @pytest.mark.parametrize("npts,order,speed,omega", BLK_CASES)
-@pytest.mark.parametrize("k", [1, 2, 5, 8, 16, -1, -3, -8])
+@pytest.mark.parametrize("k", [1, 2, 5, 8, 16])
 def test_blocked_sweeps_fp64(npts, order, speed, omega, k):
-    """The temporally blocked 2-D kernel (k steps per launch) and the persistent kernel (k < 0: one
-    cooperative launch, |k| steps between halo exchanges) give the single-step result, forced and
-    unforced, with the operator epilogue."""
+    """The temporally blocked 2-D kernel (k steps per launch) gives the single-step result, forced
+    and unforced, with the operator epilogue."""
     g, og, _ = make(npts, order, speed)
     g.whv_set_steps_per_sweep(k)
     assert g.whv_get_steps_per_sweep() == k
@@ -353,7 +352,7 @@ def test_blocked_sweeps_fp64(npts, order, speed, omega, k):
 
 
 @pytest.mark.parametrize("npts,order,speed,omega", BLK_CASES[:4])
-@pytest.mark.parametrize("k", [3, 8, 16, -4, -10])
+@pytest.mark.parametrize("k", [3, 8, 16])
 def test_blocked_sweeps_fp32(npts, order, speed, omega, k):
     g, og, _ = make(npts, order, speed, precision=whv.WHV_FP32_STEP)
     g.whv_set_steps_per_sweep(k)
@@ -410,47 +409,35 @@ def test_autotune_picks_valid_k_and_keeps_results():
     g, og, _ = make((257, 257), precision=whv.WHV_FP32_STEP)
     prm = whv.make_params(30.0, method="cg", tol=1e-6, maxit=500)
     k = g.whv_autotune(prm)
-    assert k in (1, 2, 4, 6, 8, 10, 12, 16, -4, -6, -8, -10, -12) and g.whv_get_steps_per_sweep() == k
+    assert k in (1, 2, 4, 6, 8, 10, 12, 16) and g.whv_get_steps_per_sweep() == k
     v = I.random_field(og.shape, 23)
     out = host(g.whv_apply_pi(prm, dev(v)))
     ref = WH.apply_pi(og, WH.time_grid_for(og, 30.0), v)
     assert np.abs(out - ref.ravel()).max() <= 2e-5 * max(np.abs(v).max(), np.abs(ref).max())
 
 
-@pytest.mark.parametrize("k", [-4, -10])
-def test_persistent_fp64_forced_solve_full_size(k):
-    """The 513^2 benchmark grid with the persistent kernel (121 / 144 CTAs): b = Pi_h(0; f) (forced
-    sweeps) and fixed-iteration DEVD-CG match the oracle."""
-    w = I.WORKLOADS["c2"]
-    og = O.Grid(w.npts)
-    tg = WH.time_grid_for(og, w.omega)
-    f = I.forcing_for(w)
-    g = whv.Grid(w.npts, precision=whv.WHV_FP64)
-    g.whv_set_steps_per_sweep(k)
-    prm = whv.make_params(w.omega, method="cg", tol=0.0, maxit=3)
-    g.whv_set_deflation_basis(prm, w.nd, whv.WHV_BASIS_CLOSED_FORM)
-    u, _ = g.whv_solve(prm, dev(f))
-    modes, lam2, _ = SP.select_modes(og, tg, w.nd)
-    ref = K.devd_solve(og, tg, f, SP.basis(og, modes), lam2, "cg", 0.0, 3).u
-    assert relmax(host(u), ref) < 1e-12
-
-
-def test_persistent_barrier_failure_is_reported_and_recovers():
-    """The failure path without a GPU fault: the host raises the barrier's error flag, the next
-    persistent wave solve leaves at its first barrier with NaN output, whv_solve reports
-    WHV_ERR_TIMEOUT and re-arms; the next solve is exact again."""
+def test_batched_barrier_failure_is_reported_and_recovers():
+    """The failure path of the grid barriers without a GPU fault: the host raises the barrier error
+    flag of a batched solve (whv_inject_barrier_error on one of its grids), every CTA of the first
+    batched wave solve leaves at its first grid barrier, the call reports WHV_ERR_TIMEOUT; the next
+    batched solve on the same grids is exact again (FP64 and FP32 stepping)."""
     npts, omega = (70, 45), 14.0
-    g, og, _ = make(npts, 2, None)
-    g.whv_set_steps_per_sweep(-4)
+    og = O.Grid(npts)
     f = I.gaussian(npts, [0.45, 0.5], 0.1, omega ** 2)
-    prm = whv.make_params(omega, method="cg", tol=0.0, maxit=4)
-    g.whv_inject_barrier_error()
-    with pytest.raises(whv.WhvError) as ei:
-        g.whv_solve(prm, dev(f))
-    assert "barrier" in str(ei.value)
-    u, _ = g.whv_solve(prm, dev(f))
     ref = K.devd_solve(og, WH.time_grid_for(og, omega), f, None, None, "cg", 0.0, 4).u
-    assert relmax(host(u), ref) < 1e-12
+    for prec, tol in ((whv.WHV_FP64, 1e-12), (whv.WHV_FP32_STEP, 1e-4)):
+        grids = [whv.Grid(npts, precision=prec) for _ in range(2)]
+        prm = whv.make_params(omega, method="cg", tol=0.0, maxit=4)
+        grids[1].whv_inject_barrier_error()
+        with pytest.raises(whv.WhvError) as ei:
+            whv.whv_solve_batched(grids, [prm, prm], [dev(f), dev(f)])
+        assert "barrier" in str(ei.value)
+        us, _ = whv.whv_solve_batched(grids, [prm, prm], [dev(f), dev(f)])
+        for u in us:
+            assert relmax(host(u), ref) < tol
+        grids[0].whv_inject_barrier_error()
+        with pytest.raises(whv.WhvError):
+            whv.whv_apply_pi_batched(grids, [prm, prm], [dev(f), dev(f)], None)
 
 
 @pytest.mark.parametrize("npts,speed,omega,order", [

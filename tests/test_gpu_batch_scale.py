@@ -114,6 +114,29 @@ def test_fp64_batch_with_several_items_per_cta(share):
         g.close()
 
 
+def test_double_float_correction_with_several_items_per_cta():
+    """FP32 stepping inside the FP64 residual correction with double-float b and residual wave
+    solves (4 sub-steps per sweep, several work items per CTA): every FP64 true residual meets
+    tol = 1e-9 and every solution is the oracle's converged DEVD-CG solution within the residual
+    times the deflated condition number."""
+    assert sum(tiles((n, n), 4) for n, _, _ in SPEC) > 2 * sms()
+    stream = torch.cuda.Stream()
+    grids, params, fs, spec = build(whv.WHV_FP32_STEP, stream, tol=1e-9, maxit=3000, refine=True, df=True)
+    us, infos = whv.whv_solve_batched(grids, params, fs)
+    for (n, om, f), u, info in zip(spec, us, infos):
+        assert info["status"] == "OK" and info["outer_iterations"] >= 1, info
+        assert info["true_rel_residual"] <= 1e-9, info
+        key = (n, om)
+        if key not in _modal_cache:
+            g = O.Grid((n, n))
+            _modal_cache[key] = MD.ModalSystem(g, WH.time_grid_for(g, om), ND)
+        _, conv, ref = MD.devd_cg(_modal_cache[key], f.reshape(n - 2, n - 2), 1e-13, 20000)
+        assert conv.all()
+        assert IND.relmax(u.cpu().numpy(), ref) < 1e-6
+    for g in grids:
+        g.close()
+
+
 def test_shared_basis_batch_equals_copied_basis_batch():
     """Four sources on each of two (grid, frequency) classes: sharing the basis (one contraction
     per class reading it once) gives the same FP32 + FP64-correction solutions and iteration counts

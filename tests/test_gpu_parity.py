@@ -383,11 +383,13 @@ def test_blocked_fp32_four_cell_sweeps_equal_single_steps_bitwise(npts, omega, o
 
 
 @pytest.mark.parametrize("npts,omega", [((37, 20, 11), 8.0), ((12, 10, 40), 6.0), ((70, 33, 45), 9.0),
-                                         ((70, 33, 45), 9.7), ((5, 6, 4), 3.0)])
+                                         ((70, 33, 45), 9.7), ((5, 6, 4), 3.0), ((40, 75, 21), 7.0),
+                                         ((131, 70, 30), 9.0)])
 def test_two_step_3d_equals_single_steps_bitwise(npts, omega):
-    """3-D FP32, c = 1: two leapfrog steps per launch (xy tiles with a one-node ring, z chunks with
-    a ragged last one, an odd number of steps handled by one single step first) perform the
-    single-step kernel's operations in its order: Pi_h v is bitwise the k = 1 result, and the
+    """3-D FP32, c = 1: two leapfrog steps per launch (64 x 32 tiles with a one-node ring, several
+    tiles in x and y, odd and even row lengths, CTA ranges of (tile, plane) pairs that start and
+    end inside a tile's planes, an odd number of steps handled by one single step first) perform
+    the single-step kernel's operations in its order: Pi_h v is bitwise the k = 1 result, and the
     operator epilogue inside fixed-iteration CG agrees to rounding of the reductions."""
     g, og, _ = make(npts, 2, None, precision=whv.WHV_FP32_STEP)
     prm = whv.make_params(omega)
@@ -426,7 +428,8 @@ def test_batched_barrier_failure_is_reported_and_recovers():
     f = I.gaussian(npts, [0.45, 0.5], 0.1, omega ** 2)
     ref = K.devd_solve(og, WH.time_grid_for(og, omega), f, None, None, "cg", 0.0, 4).u
     for prec, tol in ((whv.WHV_FP64, 1e-12), (whv.WHV_FP32_STEP, 1e-4)):
-        grids = [whv.Grid(npts, precision=prec) for _ in range(2)]
+        stream = torch.cuda.Stream()
+        grids = [whv.Grid(npts, precision=prec, stream=stream) for _ in range(2)]
         prm = whv.make_params(omega, method="cg", tol=0.0, maxit=4)
         grids[1].whv_inject_barrier_error()
         with pytest.raises(whv.WhvError) as ei:

@@ -173,6 +173,7 @@ whv_status whv_create_grid(int dim, const int64_t npts[3], const double lo[3], c
     return fail(nullptr, WHV_ERR_INVALID, "precision must be WHV_FP64 or WHV_FP32_STEP");
   if (!npts) return fail(nullptr, WHV_ERR_INVALID, "npts is NULL");
   blocked_init();
+  step3d2_init();
   whv_grid g = new whv_grid_s();
   g->dim = dim; g->order = order; g->precision = precision;
   int64_t N = 1;

@@ -15,6 +15,7 @@
 // Krylov-side input v and output in FP64).
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 
@@ -361,107 +362,304 @@ __global__ void __launch_bounds__(256) k_step3d(const T* __restrict__ wc, T* __r
 }
 
 // 3-D 7-point, FP32, c = 1, f = 0: TWO leapfrog steps per pass (W^{n-1}, W^n -> W^{n+1}, W^{n+2}
-// into the other buffer pair), halving the state traffic of single steps.  A CTA of 32 x 16
-// threads covers an xy region R1 = tile + 1-node ring (tile 30 x 14) and marches through a
-// chunk of zc planes.  At iteration z, step A computes W^{n+1} on R1 at plane z from W^n at
-// z-1, z, z+1 (the plane z with its ring staged in shared memory, the z neighbours in registers)
-// and stages it; step B then computes W^{n+2} on the tile at plane z-1 from W^{n+1} at z-2, z-1
-// (shared memory, staged one iteration earlier), z (registers).  Step A runs on planes
-// z0-1 .. z1 of the chunk [z0, z1), step B on z0 .. z1-1.  Nodes outside the domain are 0 (the
-// Dirichlet values).  Same operations in the same order as two k_step3d steps:
+// into the other buffer pair), halving the state traffic of single steps.  A CTA of 17 warps
+// owns a tile of 64 x 32 nodes in x, y and marches through planes z; lane l of warp row w holds
+// the two adjacent columns x0 + 2l, x0 + 2l + 1 of the two region rows 2w, 2w + 1 (region row r
+// is y = y0 - 1 + r: rows 1 .. 32 are the tile, 0 and 33 its ring), 8-byte loads and stores where
+// the rows allow it.  At plane z, step A computes W^{n+1}(z) on the tile and its one-node ring
+// from W^n at z - 1, z, z + 1 (plane z staged in shared memory with the two columns and one row
+// beyond the ring, the z neighbours in registers); lanes 0 and 31 also compute the ring columns
+// x0 - 1 and x0 + 64.  Step B then computes W^{n+2}(z - 1) on the tile from W^{n+1} at z - 2,
+// z - 1 (registers and the stage written at the previous plane) and z.  The grid is persistent:
+// the (tile column, plane) pairs of the whole grid are split into equal contiguous ranges, one
+// per CTA; a range covering parts of two tile columns marches each part (one extra plane of
+// step A at its start).  The planes are processed four at a time with the register rings
+// (W^n at four planes, W^{n+1} at four, the rest at two) indexed by the plane's phase, so that
+// no value is moved between registers.  Nodes outside the domain are 0 (the Dirichlet values).
+// Same operations in the same order as two k_step3d steps:
 //   W^{n+1} = fma(az, zm + zp, fma(ay, ym + yp, fma(ax, xm + xp, fma(b, W^n, -W^{n-1}))))
 //   acc = fma(w_{n+2}, W^{n+2}, fma(w_{n+1}, W^{n+1}, acc))
 // Global traffic per node and 2 steps: read W^{n-1}, W^n, acc, write W^{n+1}, W^{n+2}, acc
-// (24 B instead of 40 B), plus the ring re-reads (mostly L1/L2 hits).
-constexpr int k3TX = 32, k3TY = 16;   // threads = R1 extent; tile (k3TX - 2) x (k3TY - 2)
+// (24 B instead of 40 B), plus the ring re-reads.  V2: rows of an even number of nodes, whose
+// column pairs are 8-byte aligned (otherwise two 4-byte accesses).  A plane holds < 2^31 nodes.
+constexpr int k3W = 64;               // tile columns (two per lane)
+constexpr int k3H = 32;               // tile rows
+constexpr int k3WR = k3H / 2 + 1;     // warp rows (two region rows each: tile + one ring row per side)
+constexpr int k3PC = k3W + 4;         // staged columns x0 - 2 .. x0 + 65 (column c is x0 - 2 + c)
 
-template <int KIND>
-__global__ void __launch_bounds__(k3TX * k3TY) k_step3d2(const float* __restrict__ gp, const float* __restrict__ gc,
-                                                     float* __restrict__ op, float* __restrict__ oc,
-                                                     float* __restrict__ acc, const double* __restrict__ v,
-                                                     const double* __restrict__ mw, double* __restrict__ out,
-                                                     int nx, int ny, int nz, int zc, StepCoef<float> cf, float w2,
-                                                     double* partials, unsigned* counter, double* scal_out) {
-  // Double-buffered stages, so that one barrier per plane suffices: at iteration z the CTA writes
-  // P[z & 1] (W^n(z) with its ring; corners unused) and Q[z & 1] (W^{n+1}(z) on R1), step A reads
-  // P[z & 1] after the barrier, step B reads Q[(z - 1) & 1], written before it.
-  __shared__ float P[2][k3TY + 2][k3TX + 2];
-  __shared__ float Q[2][k3TY][k3TX];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int xb = blockIdx.x * (k3TX - 2) - 1, yb = blockIdx.y * (k3TY - 2) - 1;   // R1 origin
-  const int x = xb + tx, y = yb + ty;
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
-  const bool xin = x >= 0 && x < nx, yin = y >= 0 && y < ny;
-  const bool inxy = xin && yin;
-  const bool tile = inxy && tx >= 1 && tx < k3TX - 1 && ty >= 1 && ty < k3TY - 1;
-  const int64_t plane = (int64_t)nx * ny;
-  // the ring node this thread stages, if any: the row above (ty = 0) / below (ty = last) its
-  // column, the column left (tx = 0) / right (tx = last) of its row
-  int64_t ringv = -1, ringh = -1;
-  if (ty == 0 && xin && yb - 1 >= 0) ringv = x + (int64_t)nx * (yb - 1);
-  if (ty == k3TY - 1 && xin && yb + k3TY < ny) ringv = x + (int64_t)nx * (yb + k3TY);
-  if (tx == 0 && yin && xb - 1 >= 0) ringh = (xb - 1) + (int64_t)nx * y;
-  if (tx == k3TX - 1 && yin && xb + k3TX < nx) ringh = (xb + k3TX) + (int64_t)nx * y;
-  const int pvy = ty == 0 ? 0 : k3TY + 1, phx = tx == 0 ? 0 : k3TX + 1;
-  const bool hasv = ty == 0 || ty == k3TY - 1, hash = tx == 0 || tx == k3TX - 1;
-  const int64_t col = inxy ? (int64_t)x + (int64_t)nx * y : 0;
-  auto ldc = [&](int z) { return (inxy && z >= 0 && z < nz) ? __ldg(gc + col + plane * z) : 0.0f; };
-  float cm = ldc(z0 - 2), c0 = ldc(z0 - 1), cp = ldc(z0);   // W^n at z - 1, z, z + 1 for z = z0 - 1
-  float q2 = 0.0f, q1 = 0.0f;   // W^{n+1} of this column at z - 2, z - 1
-  float accA = 0.0f;            // acc(z - 1) after step n + 1
-  double part = 0.0;
-  // running pointers of plane z (valid only where dereferenced: z in range)
-  int64_t zo = plane * (z0 - 1);
-  for (int z = z0 - 1; z <= z1; ++z, zo += plane) {
-    const int b = z & 1;
-    const bool zin = z >= 0 && z < nz;
-    P[b][ty + 1][tx + 1] = c0;
-    if (hasv) P[b][pvy][tx + 1] = (zin && ringv >= 0) ? __ldg(gc + ringv + zo) : 0.0f;
-    if (hash) P[b][ty + 1][phx] = (zin && ringh >= 0) ? __ldg(gc + ringh + zo) : 0.0f;
-    const bool act = inxy && zin;
-    const float cpp = (inxy && z + 2 < nz) ? __ldg(gc + col + zo + 2 * plane) : 0.0f;
-    const float wpz = act ? __ldg(gp + col + zo) : 0.0f;
-    const float accz = (tile && zin) ? acc[col + zo] : 0.0f;
-    __syncthreads();
-    // step A: W^{n+1}(z) on R1
-    float a1 = 0.0f;
-    if (act) {
-      float u = fmaf(cf.b, c0, -wpz);
-      u = fmaf(cf.a[0], P[b][ty + 1][tx] + P[b][ty + 1][tx + 2], u);
-      u = fmaf(cf.a[1], P[b][ty][tx + 1] + P[b][ty + 2][tx + 1], u);
-      u = fmaf(cf.a[2], cm + cp, u);
-      a1 = u;
+template <bool V2>
+__device__ __forceinline__ float2 ld2(const float* __restrict__ p, bool in0, bool in1) {
+  float2 r = make_float2(0.f, 0.f);
+  if (V2) {
+    if (in0) r = __ldg(reinterpret_cast<const float2*>(p));
+  } else {
+    if (in0) r.x = __ldg(p);
+    if (in1) r.y = __ldg(p + 1);
+  }
+  return r;
+}
+template <bool V2>
+__device__ __forceinline__ float2 ld2rw(const float* p, bool in0, bool in1) {
+  // the filter sums are read and written by the same kernel: no read-only path
+  float2 r = make_float2(0.f, 0.f);
+  if (V2) {
+    if (in0) r = *reinterpret_cast<const float2*>(p);
+  } else {
+    if (in0) r.x = p[0];
+    if (in1) r.y = p[1];
+  }
+  return r;
+}
+template <bool V2>
+__device__ __forceinline__ void st2(float* p, float2 v, bool in0, bool in1) {
+  if (V2) {
+    if (in0) *reinterpret_cast<float2*>(p) = v;
+  } else {
+    if (in0) p[0] = v.x;
+    if (in1) p[1] = v.y;
+  }
+}
+
+struct S3d2 {            // registers of one thread, rings indexed by the plane's phase k = z - zb
+  float2 c[4][2];        // W^n of the own nodes: c[(k + d) & 3] is plane z + d (d = -1 .. 2)
+  float r[4][2];         // W^n of the ring node, likewise
+  float2 q[4][2];        // W^{n+1} of the own nodes: q[k & 3] is plane z
+  float2 wp[2][2];       // W^{n-1} of the own nodes: wp[k & 1] is plane z
+  float wr[2][2];        // W^{n-1} of the ring node
+  float2 ac[2][2];       // filter sums of the own nodes: ac[k & 1] is plane z
+  float rb[2][2];        // W^n of the column beyond the ring: rb[k & 1] is plane z
+  float2 xr[2];          // W^n of the extra staged row
+  float2 aA[2][2];       // filter sums after step n + 1: aA[k & 1] is plane z
+};
+
+struct Geo3d2 {          // per-thread geometry of the current range
+  const float *gc, *gp;  // W^n, W^{n-1}
+  float *op, *oc, *acc;
+  const double *v, *mw;
+  double* out;
+  int64_t plane;
+  int nz, zs, ze, zl1, zl2;          // zl1 / zl2: last plane a prefetch of z + 1 / z + 2 may read
+  int co[2], r1o[2], r2o[2], xo;     // in-plane offsets: own pair, ring node, column beyond, extra row
+  bool own0[2], own1[2], trow[2], ry[2], rt1[2], rt2[2], xrin, xin0, xin1, edge, xrow;
+  int pc, pr1, pr2, sx;              // staged columns (own, ring, beyond), staged extra row
+};
+
+template <int PH, int KIND, bool V2>
+__device__ __forceinline__ void s3d2_plane(S3d2& S, const Geo3d2& G, int z, int wr, float (*P)[k3H + 4][k3PC],
+                                           float (*Q)[k3H + 2][k3PC], const StepCoef<float>& cf, float w2,
+                                           double& part) {
+  constexpr int b = PH & 1;
+  constexpr int M = (PH + 3) & 3, C0 = PH, CP = (PH + 1) & 3, CN = (PH + 2) & 3;   // z-1, z, z+1, z+2
+  constexpr int Q0 = PH, Q1 = (PH + 3) & 3, Q2 = (PH + 2) & 3;                     // W^{n+1}: z, z-1, z-2
+  constexpr int T0 = PH & 1, T1 = (PH + 1) & 1;                                     // plane z, z + 1
+  const int64_t zo = (int64_t)z * G.plane;
+  // stage W^n(z): own nodes, the ring column and the column beyond it, the extra row
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int sr = 2 * wr + i + 1;
+    *reinterpret_cast<float2*>(&P[b][sr][G.pc]) = S.c[C0][i];
+    if (G.edge) {
+      P[b][sr][G.pr1] = S.r[C0][i];
+      P[b][sr][G.pr2] = S.rb[T0][i];
     }
-    Q[b][ty][tx] = a1;
-    const float accN = fmaf(cf.w1, a1, accz);
-    // step B: W^{n+2}(z - 1) on the tile, from Q[(z - 1) & 1] (written before the barrier)
-    if (z > z0 && tile) {
-      const float(*R)[k3TX] = Q[b ^ 1];
-      float u = fmaf(cf.b, q1, -cm);
-      u = fmaf(cf.a[0], R[ty][tx - 1] + R[ty][tx + 1], u);
-      u = fmaf(cf.a[1], R[ty - 1][tx] + R[ty + 1][tx], u);
-      u = fmaf(cf.a[2], q2 + a1, u);
-      const float a = fmaf(w2, u, accA);
-      const int64_t idx = col + zo - plane;
+  }
+  if (G.xrow) *reinterpret_cast<float2*>(&P[b][G.sx][G.pc]) = S.xr[T0];
+  // prefetch W^n(z + 2) (own, ring), W^n(z + 1) (beyond the ring, extra row), W^{n-1}(z + 1), acc(z + 1)
+  const bool z1 = z + 1 <= G.zl1, z2 = z + 2 <= G.zl2, za = z + 1 < G.ze;
+  const float* g2 = G.gc + zo + 2 * G.plane;
+  const float* g1 = G.gc + zo + G.plane;
+  const float* p1 = G.gp + zo + G.plane;
+  const float* a1p = G.acc + zo + G.plane;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    S.c[CN][i] = ld2<V2>(g2 + G.co[i], z2 && G.own0[i], z2 && G.own1[i]);
+    S.wp[T1][i] = ld2<V2>(p1 + G.co[i], z1 && G.own0[i], z1 && G.own1[i]);
+    S.ac[T1][i] = ld2rw<V2>(a1p + G.co[i], za && G.trow[i] && G.xin0, za && G.trow[i] && G.xin1);
+    S.r[CN][i] = (z2 && G.ry[i]) ? __ldg(g2 + G.r1o[i]) : 0.f;
+    S.wr[T1][i] = (z1 && G.rt1[i]) ? __ldg(p1 + G.r1o[i]) : 0.f;
+    S.rb[T1][i] = (z1 && G.rt2[i]) ? __ldg(g1 + G.r2o[i]) : 0.f;
+  }
+  S.xr[T1] = ld2<V2>(g1 + G.xo, z1 && G.xrin && G.xin0, z1 && G.xrin && G.xin1);
+  __syncthreads();
+  const bool zin = (unsigned)z < (unsigned)G.nz;
+  // step A: W^{n+1}(z) of the own nodes (region rows 0 .. 33) and of the ring node
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int sr = 2 * wr + i + 1;
+    const float2 c0 = S.c[C0][i], cm = S.c[M][i], cp = S.c[CP][i], wpv = S.wp[T0][i];
+    const float xm = P[b][sr][G.pc - 1], xp = P[b][sr][G.pc + 2];
+    const float2 up = i == 0 ? *reinterpret_cast<const float2*>(&P[b][sr - 1][G.pc]) : S.c[C0][0];
+    const float2 dn = i == 1 ? *reinterpret_cast<const float2*>(&P[b][sr + 1][G.pc]) : S.c[C0][1];
+    float u0 = fmaf(cf.b, c0.x, -wpv.x);
+    u0 = fmaf(cf.a[0], xm + c0.y, u0);
+    u0 = fmaf(cf.a[1], up.x + dn.x, u0);
+    u0 = fmaf(cf.a[2], cm.x + cp.x, u0);
+    float u1 = fmaf(cf.b, c0.y, -wpv.y);
+    u1 = fmaf(cf.a[0], c0.x + xp, u1);
+    u1 = fmaf(cf.a[1], up.y + dn.y, u1);
+    u1 = fmaf(cf.a[2], cm.y + cp.y, u1);
+    S.q[Q0][i] = make_float2((zin && G.own0[i]) ? u0 : 0.f, (zin && G.own1[i]) ? u1 : 0.f);
+    *reinterpret_cast<float2*>(&Q[b][sr - 1][G.pc]) = S.q[Q0][i];
+    if (G.edge && G.trow[i]) {
+      float w = fmaf(cf.b, S.r[C0][i], -S.wr[T0][i]);
+      w = fmaf(cf.a[0], P[b][sr][G.pr1 - 1] + P[b][sr][G.pr1 + 1], w);
+      w = fmaf(cf.a[1], P[b][sr - 1][G.pr1] + P[b][sr + 1][G.pr1], w);
+      w = fmaf(cf.a[2], S.r[M][i] + S.r[CP][i], w);
+      Q[b][sr - 1][G.pr1] = (zin && G.rt1[i]) ? w : 0.f;
+    }
+  }
+  float2 accN[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+    accN[i] = make_float2(fmaf(cf.w1, S.q[Q0][i].x, S.ac[T0][i].x), fmaf(cf.w1, S.q[Q0][i].y, S.ac[T0][i].y));
+  // step B: W^{n+2}(z - 1) on the tile rows, from Q[(z - 1) & 1]
+  if (z > G.zs) {
+    const float(*R)[k3PC] = Q[b ^ 1];
+    const int64_t zm1 = zo - G.plane;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      if (!G.trow[i]) continue;
+      const int qr = 2 * wr + i;
+      const float2 q1 = S.q[Q1][i], q2 = S.q[Q2][i], a1 = S.q[Q0][i], cm = S.c[M][i];
+      const float xm = R[qr][G.pc - 1], xp = R[qr][G.pc + 2];
+      const float2 up = i == 0 ? *reinterpret_cast<const float2*>(&R[qr - 1][G.pc]) : S.q[Q1][0];
+      const float2 dn = i == 1 ? *reinterpret_cast<const float2*>(&R[qr + 1][G.pc]) : S.q[Q1][1];
+      float u0 = fmaf(cf.b, q1.x, -cm.x);
+      u0 = fmaf(cf.a[0], xm + q1.y, u0);
+      u0 = fmaf(cf.a[1], up.x + dn.x, u0);
+      u0 = fmaf(cf.a[2], q2.x + a1.x, u0);
+      float u1 = fmaf(cf.b, q1.y, -cm.y);
+      u1 = fmaf(cf.a[0], q1.x + xp, u1);
+      u1 = fmaf(cf.a[1], up.y + dn.y, u1);
+      u1 = fmaf(cf.a[2], q2.y + a1.y, u1);
+      const float2 a = make_float2(fmaf(w2, u0, S.aA[T1][i].x), fmaf(w2, u1, S.aA[T1][i].y));
+      const int64_t idx = zm1 + G.co[i];
       if (KIND == K_STEP) {
-        op[idx] = q1;
-        oc[idx] = u;
-        acc[idx] = a;
+        st2<V2>(G.op + idx, q1, G.xin0, G.xin1);
+        st2<V2>(G.oc + idx, make_float2(u0, u1), G.xin0, G.xin1);
+        st2<V2>(G.acc + idx, a, G.xin0, G.xin1);
       } else if (KIND == K_LAST_OUT) {
-        out[idx] = (double)a;
+        if (G.xin0) G.out[idx] = (double)a.x;
+        if (G.xin1) G.out[idx + 1] = (double)a.y;
       } else {
-        const double vi = v[idx];
-        const double o = vi - (double)a;
-        out[idx] = o;
-        part = fma(mw ? vi * mw[idx] : vi, o, part);
+        if (G.xin0) {
+          const double vi = G.v[idx];
+          const double o = vi - (double)a.x;
+          G.out[idx] = o;
+          part = fma(G.mw ? vi * G.mw[idx] : vi, o, part);
+        }
+        if (G.xin1) {
+          const double vi = G.v[idx + 1];
+          const double o = vi - (double)a.y;
+          G.out[idx + 1] = o;
+          part = fma(G.mw ? vi * G.mw[idx + 1] : vi, o, part);
+        }
       }
     }
-    q2 = q1;
-    q1 = a1;
-    accA = accN;
-    cm = c0;
-    c0 = cp;
-    cp = cpp;
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) S.aA[T0][i] = accN[i];
+}
+
+template <int KIND, bool V2>
+__global__ void __launch_bounds__(32 * k3WR, 1) k_step3d2(const float* __restrict__ gp, const float* __restrict__ gc,
+                                                         float* __restrict__ op, float* __restrict__ oc,
+                                                         float* __restrict__ acc, const double* __restrict__ v,
+                                                         const double* __restrict__ mw, double* __restrict__ out,
+                                                         int nx, int ny, int nz, int cx, int ncol, int slab,
+                                                         int64_t units, StepCoef<float> cf, float w2,
+                                                         double* partials, unsigned* counter, double* scal_out) {
+  // double-buffered stages (one barrier per plane): at phase k the CTA writes P[k & 1] (W^n(z),
+  // region rows -1 .. 34) before the barrier and Q[k & 1] (W^{n+1}(z), rows 0 .. 33) after it;
+  // step B reads Q[(k - 1) & 1], written before the barrier.  Phases count from the range's first
+  // plane, so a range starts with an extra barrier.
+  __shared__ __align__(16) float P[2][k3H + 4][k3PC];
+  __shared__ __align__(16) float Q[2][k3H + 2][k3PC];
+  const int lane = threadIdx.x, wr = threadIdx.y;
+  Geo3d2 G;
+  G.gc = gc; G.gp = gp; G.op = op; G.oc = oc; G.acc = acc; G.v = v; G.mw = mw; G.out = out;
+  G.plane = (int64_t)nx * ny;
+  G.nz = nz;
+  G.edge = lane == 0 || lane == 31;
+  G.pc = 2 * lane + 2;
+  G.pr1 = lane == 0 ? 1 : k3W + 2;
+  G.pr2 = lane == 0 ? 0 : k3W + 3;
+  const int xrow = wr == 0 ? -1 : (wr == k3WR - 1 ? k3H + 2 : -2);   // extra staged row, if any
+  G.xrow = xrow >= -1;
+  G.sx = xrow + 1;
+  double part = 0.0;
+  const int64_t u_end = units * (blockIdx.x + 1) / gridDim.x;
+  const int64_t per_slab = (int64_t)ncol * slab;
+  for (int64_t u = units * blockIdx.x / gridDim.x; u < u_end;) {
+    // unit u -> (slab, tile column, plane): slabs of `slab` planes (the last one thinner), each
+    // slab's units column by column, so that CTAs with neighbouring ranges march neighbouring
+    // tile columns through the same planes at the same time (their halo reads meet in L2)
+    const int64_t sl = u / per_slab;
+    const int zlo = (int)(sl * slab);
+    const int thick = min(slab, nz - zlo);
+    const int64_t rem = u - sl * per_slab;
+    const int cid = (int)(rem / thick);
+    G.zs = zlo + (int)(rem - (int64_t)cid * thick);
+    G.ze = (int)min((int64_t)zlo + thick, (int64_t)G.zs + (u_end - u));
+    u += G.ze - G.zs;
+    G.zl1 = min(G.ze, nz - 1);
+    G.zl2 = min(G.ze + 1, nz - 1);
+    const int x0 = (cid % cx) * k3W, y0 = (cid / cx) * k3H;
+    const int xl = x0 + 2 * lane;
+    G.xin0 = xl < nx;
+    G.xin1 = xl + 1 < nx;
+    const int xr1 = lane == 0 ? x0 - 1 : x0 + k3W, xr2 = lane == 0 ? x0 - 2 : x0 + k3W + 1;
+    const bool rx1 = G.edge && xr1 >= 0 && xr1 < nx, rx2 = G.edge && xr2 >= 0 && xr2 < nx;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int r = 2 * wr + i, y = y0 - 1 + r;
+      const bool yin = y >= 0 && y < ny;
+      G.trow[i] = yin && r >= 1 && r <= k3H;
+      G.own0[i] = yin && G.xin0;
+      G.own1[i] = yin && G.xin1;
+      G.ry[i] = rx1 && yin;
+      G.rt1[i] = rx1 && G.trow[i];
+      G.rt2[i] = rx2 && G.trow[i];
+      G.co[i] = yin ? xl + nx * y : 0;
+      G.r1o[i] = yin ? xr1 + nx * y : 0;
+      G.r2o[i] = yin ? xr2 + nx * y : 0;
+    }
+    const int yx = y0 - 1 + xrow;
+    G.xrin = G.xrow && yx >= 0 && yx < ny;
+    G.xo = G.xrin ? xl + nx * yx : 0;
+    S3d2 S;
+    const int zb = G.zs - 1;
+    auto zok = [&](int z) { return z >= 0 && z < nz; };
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {   // W^n at zb - 1, zb, zb + 1 (phase 0: c[0] is plane zb)
+        const int z = zb - 1 + d;
+        const bool ok = zok(z);
+        const float* g = gc + (int64_t)z * G.plane;
+        S.c[(d + 3) & 3][i] = ld2<V2>(g + G.co[i], ok && G.own0[i], ok && G.own1[i]);
+        S.r[(d + 3) & 3][i] = (ok && G.ry[i]) ? __ldg(g + G.r1o[i]) : 0.f;
+      }
+      const bool ok = zok(zb);
+      const int64_t zo = (int64_t)zb * G.plane;
+      S.wp[0][i] = ld2<V2>(gp + zo + G.co[i], ok && G.own0[i], ok && G.own1[i]);
+      S.wr[0][i] = (ok && G.rt1[i]) ? __ldg(gp + zo + G.r1o[i]) : 0.f;
+      S.rb[0][i] = (ok && G.rt2[i]) ? __ldg(gc + zo + G.r2o[i]) : 0.f;
+      S.ac[0][i] = make_float2(0.f, 0.f);   // acc(zs - 1) is not needed (no step B there)
+      S.aA[1][i] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int d = 0; d < 4; ++d) S.q[d][i] = make_float2(0.f, 0.f);
+    }
+    S.xr[0] = ld2<V2>(gc + (int64_t)zb * G.plane + G.xo, zok(zb) && G.xrin && G.xin0, zok(zb) && G.xrin && G.xin1);
+    __syncthreads();   // the previous range's last reads of the stages are done
+    // planes zb .. ze, four at a time (phase k = z - zb: the stage parity and the register rings
+    // follow the phase)
+    for (int z = zb;;) {
+      s3d2_plane<0, KIND, V2>(S, G, z, wr, P, Q, cf, w2, part); if (++z > G.ze) break;
+      s3d2_plane<1, KIND, V2>(S, G, z, wr, P, Q, cf, w2, part); if (++z > G.ze) break;
+      s3d2_plane<2, KIND, V2>(S, G, z, wr, P, Q, cf, w2, part); if (++z > G.ze) break;
+      s3d2_plane<3, KIND, V2>(S, G, z, wr, P, Q, cf, w2, part); if (++z > G.ze) break;
+    }
   }
   if (KIND == K_LAST_AV) {
     part = block_sum(part);
@@ -639,11 +837,34 @@ static whv_status dispatch_df_dim(whv_grid g, const TimeGridH& tg, const double*
                        : dispatch_df_ord<DIM, 4>(g, tg, v, f, out, epi, nl, bufs, acc);
 }
 
-constexpr int kZChunk2 = 32;   // planes per CTA of the two-step 3-D kernel
+// CTAs of the persistent two-step 3-D kernel: every resident CTA slot of the GPU (one per SM),
+// fewer when the grid has fewer than 16 (tile column, plane) pairs per slot
+static int s3d2_slots = 0;
 
-static dim3 grid_3d2(whv_grid g) {
-  return dim3((g->n[0] + k3TX - 3) / (k3TX - 2), (g->n[1] + k3TY - 3) / (k3TY - 2),
-              (g->n[2] + kZChunk2 - 1) / kZChunk2);
+void step3d2_init() {
+  if (s3d2_slots) return;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step3d2<K_STEP, true>, 32 * k3WR, 0);
+  s3d2_slots = std::max(1, sms * std::max(per_sm, 1));
+}
+
+struct Grid3d2 {
+  int cx, ncol, slab;
+  int64_t units;
+  int blocks;
+};
+
+// tile columns x planes, split into one contiguous range per CTA; slabs as thick as one range
+static Grid3d2 grid_3d2(whv_grid g) {
+  Grid3d2 q;
+  q.cx = (g->n[0] + k3W - 1) / k3W;
+  q.ncol = q.cx * ((g->n[1] + k3H - 1) / k3H);
+  q.units = (int64_t)q.ncol * g->n[2];
+  q.blocks = (int)std::max<int64_t>(1, std::min<int64_t>(s3d2_slots, (q.units + 15) / 16));
+  q.slab = (int)std::min<int64_t>(g->n[2], (q.units + q.blocks - 1) / q.blocks);
+  return q;
 }
 
 // Steps n = 1 .. nt-1 of a 3-D f = 0 FP32 wave solve (c = 1, second order) after the Taylor
@@ -658,8 +879,10 @@ static whv_status two_step_3d(whv_grid g, const TimeGridH& tg, const double* v, 
   StepCoef<float> cf = coef_of<float>(g, tg);
   double* part = chan(g, CH_STEP);
   unsigned* cnt = g->counters + CH_STEP;
-  const dim3 g2 = grid_3d2(g), b2(k3TX, k3TY, 1);
-  if ((int64_t)g2.x * g2.y * g2.z > chan_cap(g, CH_STEP)) return fail(g, WHV_ERR_INVALID, "grid too large for the fused reduction");
+  const Grid3d2 q = grid_3d2(g);
+  const dim3 g2(q.blocks), b2(32, k3WR, 1);
+  if (q.blocks > chan_cap(g, CH_STEP)) return fail(g, WHV_ERR_INVALID, "grid too large for the fused reduction");
+  const bool v2 = nx % 2 == 0;
   const LaunchShape ls = shape_of(g);
   float* wprev = buf[0];
   float* wcur = buf[1];
@@ -688,15 +911,14 @@ static whv_status two_step_3d(whv_grid g, const TimeGridH& tg, const double* v, 
     const bool in01 = wprev == buf[0] || wprev == buf[1];   // (wprev, wcur) is one of the pairs
     float* op = in01 ? buf[2] : buf[0];
     float* oc = in01 ? buf[3] : buf[1];
-    if (!last)
-      k_step3d2<K_STEP><<<g2, b2, 0, g->stream>>>(wprev, wcur, op, oc, acc, nullptr, nullptr, nullptr, nx, ny, nz,
-                                                  kZChunk2, cf, w2, nullptr, nullptr, nullptr);
-    else if (epi == 0)
-      k_step3d2<K_LAST_OUT><<<g2, b2, 0, g->stream>>>(wprev, wcur, op, oc, acc, nullptr, nullptr, out, nx, ny, nz,
-                                                      kZChunk2, cf, w2, nullptr, nullptr, nullptr);
-    else
-      k_step3d2<K_LAST_AV><<<g2, b2, 0, g->stream>>>(wprev, wcur, op, oc, acc, v, g->mw, out, nx, ny, nz, kZChunk2,
-                                                     cf, w2, part, cnt, g->scal + S_PQ);
+    const int kind = !last ? K_STEP : (epi == 0 ? K_LAST_OUT : K_LAST_AV);
+    auto kern = kind == K_STEP ? (v2 ? k_step3d2<K_STEP, true> : k_step3d2<K_STEP, false>)
+              : kind == K_LAST_OUT ? (v2 ? k_step3d2<K_LAST_OUT, true> : k_step3d2<K_LAST_OUT, false>)
+                                   : (v2 ? k_step3d2<K_LAST_AV, true> : k_step3d2<K_LAST_AV, false>);
+    kern<<<g2, b2, 0, g->stream>>>(wprev, wcur, op, oc, acc, kind == K_LAST_AV ? v : nullptr,
+                                   kind == K_LAST_AV ? g->mw : nullptr, kind == K_STEP ? nullptr : out, nx, ny, nz,
+                                   q.cx, q.ncol, q.slab, q.units, cf, w2, kind == K_LAST_AV ? part : nullptr,
+                                   kind == K_LAST_AV ? cnt : nullptr, kind == K_LAST_AV ? g->scal + S_PQ : nullptr);
     WHV_CUDA(g, cudaGetLastError());
     ++nl;
     wprev = op;
@@ -738,7 +960,8 @@ static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v,
     }
   }
   if constexpr (DIM == 3 && ORDER == 2 && !VARC && !FORCE && sizeof(T) == 4) {
-    if (g->kblock >= 2) {   // two steps per launch when set (or chosen by the autotuner)
+    // two steps per launch when set (or chosen by the autotuner), planes of < 2^31 nodes
+    if (g->kblock >= 2 && (int64_t)g->n[0] * g->n[1] < (int64_t(1) << 31)) {
       int nl = 0;
       whv_status s = two_step_3d(g, tg, v, out, epi, &nl, bufs, accbuf);
       *nlaunch += nl;

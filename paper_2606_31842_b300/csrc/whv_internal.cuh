@@ -209,6 +209,7 @@ template <typename T, int ORDER, bool VARC>
 whv_status blocked_steps_2d(whv_grid g, const TimeGridH& tg, const double* v, double* out, int epi,
                             int k_want, int* launches, void* const* bufs, void* acc);
 void blocked_init();
+void step3d2_init();   // stencil.cu: resident CTA slots of the persistent two-step 3-D kernel
 
 // single-CTA wave solve for small grids (stencil_blocked.cu)
 bool small_grid(whv_grid g);

@@ -40,30 +40,29 @@ def test_traffic_records_match_current_sources():
 def test_traffic_is_null_once_the_kernel_changes(tmp_path, monkeypatch):
     root = _copy_tree(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.traffic_for("k_step3d2", "fp32") is not None
+    assert bench.traffic_for("k_step3d", "fp32") is not None
     # editing another part of the same file keeps the record ...
     p = root / "paper_2606_31842_b300" / "csrc" / "stencil.cu"
     src = p.read_text()
     i = src.index("k_step_df(")
     j = src.index("{", i)
     p.write_text(src[:j + 1] + "  // edited\n" + src[j + 1:])
-    assert bench.traffic_for("k_step3d2", "fp32") is not None
+    assert bench.traffic_for("k_step3d", "fp32") is not None
     # ... and so does a comment inside the kernel ...
     src = p.read_text()
-    j = src.index("float accA = 0.0f;")
+    j = src.index("T acc_c = acc[idx];")
     p.write_text(src[:j] + "/* note */ " + src[j:])
-    assert bench.traffic_for("k_step3d2", "fp32") is not None
+    assert bench.traffic_for("k_step3d", "fp32") is not None
     # ... editing the kernel's code drops it
     src = p.read_text()
-    j = src.index("float accA = 0.0f;")
-    p.write_text(src[:j] + "float accA = 0.0f * 1.0f;" + src[j + len("float accA = 0.0f;"):])
-    assert bench.traffic_for("k_step3d2", "fp32") is None
-    assert bench.traffic_for("k_step3d", "fp32") is not None
+    j = src.index("T acc_c = acc[idx];")
+    p.write_text(src[:j] + "T acc_c = acc[idx] * T(1);" + src[j + len("T acc_c = acc[idx];"):])
+    assert bench.traffic_for("k_step3d", "fp32") is None
+    assert bench.traffic_for("k_batch_front", "fp32") is not None
     # a shared header drops every kernel built from it
     h = root / "paper_2606_31842_b300" / "csrc" / "whv_device.cuh"
     h.write_text(h.read_text() + "\nconstexpr int kEdited = 1;\n")
-    assert bench.traffic_for("k_step3d", "fp32") is None
-    assert bench.traffic_for("k_block2d", "fp32") is None
+    assert bench.traffic_for("k_batch_front", "fp32") is None
     assert bench.traffic_for("unknown_kernel", "fp32") is None
 
 

@@ -131,7 +131,7 @@ def test_double_float_correction_with_several_items_per_cta():
             g = O.Grid((n, n))
             _modal_cache[key] = MD.ModalSystem(g, WH.time_grid_for(g, om), ND)
         _, conv, ref = MD.devd_cg(_modal_cache[key], f.reshape(n - 2, n - 2), 1e-13, 20000)
-        assert conv.all()
+        assert np.all(conv)
         assert IND.relmax(u.cpu().numpy(), ref) < 1e-6
     for g in grids:
         g.close()

@@ -79,10 +79,12 @@ def parse(argv=None):
                     help="variable-speed workload: operator form (conservative: div(c^2 grad), second order)")
     ap.add_argument("--sources", type=int, default=0,
                     help="batched workload: Gaussian sources per (grid, frequency) (default 16)")
-    ap.add_argument("--workload", default="c4", choices=["c1", "c2", "c3", "c4", "c4wave", "c5", "study"],
+    ap.add_argument("--workload", default="c4",
+                    choices=["c1", "c2", "c3", "c4", "c4wave", "c5", "stencil3d", "study"],
                     help="c4 (default): the batched squares; c4wave: only the batched FP32 wave solve of those "
                          "problems (the dominant kernel, for profiling); c2: the 513^2 deflated solve; c1, c3, c5: "
-                         "the 1-D, variable-speed 1025^2 and 3-D workloads; study: iterations vs omega")
+                         "the 1-D, variable-speed 1025^2 and 3-D workloads; stencil3d: only the 256^3 FP32 wave "
+                         "solves with one and two steps per launch (for profiling); study: iterations vs omega")
     return ap.parse_args(argv)
 
 
@@ -551,6 +553,21 @@ def batch_kernel_name(k):
     if env == "0" or k not in (4, 8, 12):
         return "k_batch_block2d"
     return "k_batch_front" if (k == 8 and env not in ("1", "2")) else "k_batch_tma"
+
+
+def run_stencil3d(args):
+    """--workload stencil3d: only the 256^3 FP32 f = 0 wave solves of the benchmark's stencil_hbm
+    entry (whv_apply_pi, one and two leapfrog steps per launch); a small, self-contained command
+    for ncu captures of k_step3d / k_step3d2."""
+    import torch
+    from paper_2606_31842_b300 import build as whv_build
+    whv_build.build()
+    from paper_2606_31842_b300 import whv
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    peak, _ = measured_peaks()
+    line = stencil_hbm_measure(whv, torch.cuda.Stream(), peak)
+    print(json.dumps(dict(line, metric="3-D stencil step time", unit="us", value=line["step_us"])))
+    return 0
 
 
 def run_c4wave(args):
@@ -1109,6 +1126,8 @@ def main(argv=None):
         return run_c4(args)
     if args.workload == "c4wave":
         return run_c4wave(args)
+    if args.workload == "stencil3d":
+        return run_stencil3d(args)
     if args.workload == "c2":
         return run_c2(args)
     return run_workload(args)

@@ -21,9 +21,13 @@
 //
 // Without FP64 residual correction, DEVD (Algorithm 2) deflates each forcing first and inflates
 // each solution after the loop.  With it (WHV_REFINE_FP64), the residual r = b - A u of the full
-// system is formed by FP64 batched wave solves, its deflated components are solved modally and
-// the rest by the batched CG loop in the grids' stepping precision, until every problem's FP64
-// residual meets its tolerance.
+// system is formed by FP64 (or double-float) batched wave solves, its deflated components are
+// solved modally and the rest by the batched CG loop in the grids' stepping precision, until every
+// problem's FP64 residual meets its tolerance.  The residual is one forced wave solve from u,
+// r = Pi_h(u; f) - u (= b - A u, since Pi_h(u; f) = S_h u + b), so b itself is only needed as the
+// first pass's right-hand side and for |b| in the stopping test: it is formed by one forced wave
+// solve in the stepping precision (its rounding, ~1e-5 relative in FP32, is far inside the first
+// pass's inner tolerance and moves the stopping threshold by as little).
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -2045,28 +2049,27 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
     }
     for (int p = 0; p < np; ++p) TRY(copy_dev(c.grids[p], u_dev[p], c.grids[p]->x, c.grids[p]->N));
   } else {
-    // FP64 residual correction on the full system A u = b, b = Pi_h(0; f) in FP64
+    // FP64 residual correction on the full system A u = b, b = Pi_h(0; f) in the stepping
+    // precision, r = Pi_h(u; f) - u in FP64 (or double-float)
     for (int p = 0; p < np; ++p) TRY(ensure_fp64_buffers(c.grids[p]));
     RoleIO io_b;
     io_b.v.assign(np, nullptr);
     io_b.f.assign(f_dev, f_dev + np);
     io_b.out = c.each([](whv_grid g) { return g->bo; });
-    RoleIO io_ax;   // q = A x in FP64 (or double-float)
+    RoleIO io_ax;   // q = u - Pi_h(u; f) = -r in FP64 (or double-float)
     io_ax.v = c.each([](whv_grid g) { return (const double*)g->xo; });
-    io_ax.f.assign(np, nullptr);
+    io_ax.f.assign(f_dev, f_dev + np);
     io_ax.out = c.each([](whv_grid g) { return g->q; });
     io_ax.epi = 1;
     io_ax.halt = true;
     Wave wb, wax;
-    bool dfr = false;   // double-float b and residual wave solves (WHV_RESIDUAL_DF64)
+    bool dfr = false;   // double-float residual wave solves (WHV_RESIDUAL_DF64)
     if constexpr (DIM == 2 && ORDER == 2 && !VARC) dfr = (c.params[0].flags & WHV_RESIDUAL_DF64) != 0;
+    if (g64) TRY((make_wave<double, DIM, ORDER, VARC>(c, io_b, &wb)));
+    else TRY((make_wave<float, DIM, ORDER, VARC>(c, io_b, &wb)));
     if (dfr) {
-      if constexpr (DIM == 2 && ORDER == 2 && !VARC) {
-        TRY((make_wave<dfl, 2, 2, false>(c, io_b, &wb)));
-        TRY((make_wave<dfl, 2, 2, false>(c, io_ax, &wax)));
-      }
+      if constexpr (DIM == 2 && ORDER == 2 && !VARC) TRY((make_wave<dfl, 2, 2, false>(c, io_ax, &wax)));
     } else {
-      TRY((make_wave<double, DIM, ORDER, VARC>(c, io_b, &wb)));
       TRY((make_wave<double, DIM, ORDER, VARC>(c, io_ax, &wax)));
     }
     c.mark(4);
@@ -2075,7 +2078,8 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
     c.mark(0);
     for (int p = 0; p < np; ++p) {
       whv_grid g = c.grids[p];
-      ws64[p] = 1;
+      if (g64) ws64[p] = 1;
+      else ws[p] = 1;
       TRY(dot_async(g, g->bo, g->bo, S_TMP2));
       B_CUDA(c.g0, cudaMemsetAsync(g->xo, 0, g->N * sizeof(double), c.st));
       TRY(copy_dev(g, g->ro, g->bo, g->N));
@@ -2103,8 +2107,7 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
           if (!active[p]) continue;
           whv_grid g = c.grids[p];
           ++ws64[p];
-          TRY(copy_dev(g, g->ro, g->bo, g->N));
-          TRY(axpby(g, g->N, -1.0, g->q, 1.0, g->ro));
+          TRY(axpby(g, g->N, -1.0, g->q, 0.0, g->ro));   // r = Pi_h(x; f) - x
         }
       }
       for (int p = 0; p < np; ++p)

@@ -566,7 +566,8 @@ def run_stencil3d(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     peak, _ = measured_peaks()
     line = stencil_hbm_measure(whv, torch.cuda.Stream(), peak)
-    print(json.dumps(dict(line, metric="3-D stencil step time", unit="us", value=line["step_us"])))
+    print(json.dumps({"metric": "3-D stencil step time", "unit": "us", "value": line["step_us"],
+                      "higher_is_better": False, "stencil_hbm": line}))
     return 0
 
 

@@ -496,11 +496,20 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d_df(const BTile<d
         }
         if (FORCED) ff[r] = (in && B.f) ? df_from(__ldg(B.f + gi)) : df_zero();
       }
+      // both stages hold 0 at the nodes outside the domain (the Dirichlet values), so that the
+      // neighbour reads below need no tests; the other nodes of S1 are written by the first
+      // sub-step before any read
 #pragma unroll
-      for (int r = 0; r < kBRows; ++r) S0[(jb + kBPitch * r) * kBReg + i] = cur[r];
+      for (int r = 0; r < kBRows; ++r) {
+        const int jr = jb + kBPitch * r;
+        const int gy = y0 + jr;
+        S0[jr * kBReg + i] = cur[r];
+        if (!(colin && gy >= 0 && gy < ny)) S1[jr * kBReg + i] = df_zero();
+      }
       __syncthreads();
       const dfl* Ain = S0;
       dfl* Bout = S1;
+      const dfl coef[2] = {B.ax, B.ay};
       for (int s = 1; s <= kk; ++s) {
         const int n = n0 + s - 1;   // W^n -> W^{n+1}
         const int lo = s, hi = kBReg - s;
@@ -514,25 +523,23 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch_block2d_df(const BTile<d
           if (colact && jr >= lo && jr < hi && gy >= 0 && gy < ny) {
             const int l = jr * kBReg + i;
             const dfl c = cur[r];
-            const dfl sx = df_add(gx > 0 ? Ain[l - 1] : df_zero(), gx < nx - 1 ? Ain[l + 1] : df_zero());
-            const dfl sy = df_add(gy > 0 ? Ain[l - kBReg] : df_zero(), gy < ny - 1 ? Ain[l + kBReg] : df_zero());
             dfl wn;
             if (n == 0) {   // Taylor start
+              const dfl sx = df_add(Ain[l - 1], Ain[l + 1]);
+              const dfl sy = df_add(Ain[l - kBReg], Ain[l + kBReg]);
               const dfl c2x = {2.0f * c.hi, 2.0f * c.lo};
               dfl L = df_add(df_zero(), df_mul(B.ih2x, df_sub(sx, c2x)));
               L = df_add(L, df_mul(B.ih2y, df_sub(sy, c2x)));
               if (FORCED) L = df_sub(L, ff[r]);
               wn = df_add(c, df_mul(dfl{0.5f * B.dt2.hi, 0.5f * B.dt2.lo}, L));
             } else {
-              wn = df_sub(df_mul(B.b, c), prv[r]);
-              wn = df_add(wn, df_mul(B.ax, sx));
-              wn = df_add(wn, df_mul(B.ay, sy));
-              if (FORCED) wn = df_sub(wn, df_mul(fph, ff[r]));
+              const dfs sm[2] = {df_pair_sum(Ain[l - 1], Ain[l + 1]), df_pair_sum(Ain[l - kBReg], Ain[l + kBReg])};
+              wn = df_leapfrog<2, FORCED>(B.b, c, prv[r], coef, sm, fph, FORCED ? ff[r] : df_zero());
             }
             prv[r] = c;
             cur[r] = wn;
             Bout[l] = wn;
-            acr[r] = df_add(acr[r], df_mul(ws, wn));
+            acr[r] = df_fma_acc(acr[r], ws, wn);
           }
         }
         __syncthreads();

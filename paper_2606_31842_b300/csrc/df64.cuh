@@ -53,6 +53,73 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
   return fast_two_sum(p, e);
 }
 
+// The leapfrog update and the filter sum in one pass each, renormalised once at the end: every
+// product and sum of the HIGH parts is made exact (exact product with an FMA, two-sum), the
+// first-order low-order terms (a.hi b.lo, a.lo b.hi, the error terms) are summed in FP32 and
+// the pair is renormalised by one fast two-sum.  The terms dropped (products of two low parts)
+// and the FP32 rounding of the low-order sum are each below ~u^2 |operand| (u = 2^-24), so the
+// error of an update is below ~16 u^2 sum |operands| -- the same order as the chain of
+// double-word additions and products it replaces (each ~2^-46 (|a| + |b|)), in about two
+// thirds of the FP32 operations.
+struct dfs {             // unnormalised double-float: value h + l, |l| a few ulp(h)
+  float h, l;
+};
+__device__ __forceinline__ dfs df_pair_sum(dfl a, dfl b) {
+  const dfl s = two_sum(a.hi, b.hi);
+  return {s.hi, __fadd_rn(__fadd_rn(s.lo, a.lo), b.lo)};
+}
+
+// b c - prv + sum_{m < D} a_m s_m  (- fph f when F): the second-order leapfrog update with c = 1
+// in the order of the double-word form df_sub(df_mul(b, c), prv), df_add(., df_mul(a_m, s_m)), ...
+template <int D, bool F>
+__device__ __forceinline__ dfl df_leapfrog(dfl b, dfl c, dfl prv, const dfl* a, const dfs* sm, dfl fph, dfl f) {
+  float p = __fmul_rn(b.hi, c.hi);
+  float lo = __fmaf_rn(b.hi, c.hi, -p);
+  dfl t = two_sum(p, -prv.hi);
+  lo = __fadd_rn(lo, t.lo);
+  float th = t.hi;
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    const float q = __fmul_rn(a[m].hi, sm[m].h);
+    lo = __fadd_rn(lo, __fmaf_rn(a[m].hi, sm[m].h, -q));
+    t = two_sum(th, q);
+    th = t.hi;
+    lo = __fadd_rn(lo, t.lo);
+  }
+  if (F) {
+    const float q = __fmul_rn(fph.hi, f.hi);
+    lo = __fsub_rn(lo, __fmaf_rn(fph.hi, f.hi, -q));
+    t = two_sum(th, -q);
+    th = t.hi;
+    lo = __fadd_rn(lo, t.lo);
+  }
+  lo = __fmaf_rn(b.hi, c.lo, lo);
+  lo = __fmaf_rn(b.lo, c.hi, lo);
+  lo = __fsub_rn(lo, prv.lo);
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    lo = __fmaf_rn(a[m].hi, sm[m].l, lo);
+    lo = __fmaf_rn(a[m].lo, sm[m].h, lo);
+  }
+  if (F) {
+    lo = __fmaf_rn(-fph.hi, f.lo, lo);
+    lo = __fmaf_rn(-fph.lo, f.hi, lo);
+  }
+  return fast_two_sum(th, lo);
+}
+
+// acc + w x (the trapezoid filter sum)
+__device__ __forceinline__ dfl df_fma_acc(dfl acc, dfl w, dfl x) {
+  const float p = __fmul_rn(w.hi, x.hi);
+  float lo = __fmaf_rn(w.hi, x.hi, -p);
+  const dfl s = two_sum(acc.hi, p);
+  lo = __fadd_rn(lo, s.lo);
+  lo = __fadd_rn(lo, acc.lo);
+  lo = __fmaf_rn(w.hi, x.lo, lo);
+  lo = __fmaf_rn(w.lo, x.hi, lo);
+  return fast_two_sum(s.hi, lo);
+}
+
 // coefficients of the double-float step (from FP64 host values)
 struct DfCoef {
   dfl ih2[3], dt2, hdt2, fph, w0, w1;

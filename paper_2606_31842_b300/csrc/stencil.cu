@@ -242,16 +242,16 @@ __global__ void __launch_bounds__(256) k_step_df(const dfl* __restrict__ wc, dfl
     auto load = [&](int64_t j) { return wc[j]; };
     dfl wn;
     if (!VARC && ORDER == 2) {   // sum_m a_m (W_{+m} + W_{-m}) + b W^n - W^{n-1}
-      wn = df_sub(df_mul(cf.b, c), wp[idx]);
+      dfs sm[DIM];
 #pragma unroll
       for (int m = 0; m < DIM; ++m) {
         const int i = m == 0 ? x : (m == 1 ? y : z);
         const int n = m == 0 ? nx : (m == 1 ? ny : nz);
         const int64_t st = m == 0 ? 1 : (m == 1 ? (int64_t)nx : (int64_t)nx * ny);
-        const dfl s = df_add(i > 0 ? load(idx - st) : df_zero(), i < n - 1 ? load(idx + st) : df_zero());
-        wn = df_add(wn, df_mul(cf.a[m], s));
+        sm[m] = df_pair_sum(i > 0 ? load(idx - st) : df_zero(), i < n - 1 ? load(idx + st) : df_zero());
       }
-      if (FORCE) wn = df_sub(wn, df_mul(cf.fph, df_from(f[idx])));   // fph = dt^2 cos(omega_hat t^n)
+      // fph = dt^2 cos(omega_hat t^n)
+      wn = df_leapfrog<DIM, FORCE>(cf.b, c, wp[idx], cf.a, sm, cf.fph, FORCE ? df_from(f[idx]) : df_zero());
     } else {
       dfl L = lap_df<DIM, ORDER>(load, x, y, z, nx, ny, nz, idx, cf, c);
       if (VARC) L = df_mul(L, df_from(c2[idx]));
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) k_step_df(const dfl* __restrict__ wc, dfl
       const dfl t = df_sub(dfl{2.0f * c.hi, 2.0f * c.lo}, wp[idx]);
       wn = df_add(t, df_mul(cf.dt2, L));
     }
-    const dfl a = df_add(acc[idx], df_mul(cf.w1, wn));
+    const dfl a = df_fma_acc(acc[idx], cf.w1, wn);
     if (KIND == K_STEP) {
       wp[idx] = wn;
       acc[idx] = a;

@@ -728,13 +728,16 @@ static whv_status inner_solve(SolveCtx& c, int method, const whv_params* p, cons
 }
 
 // Solve A x = b for a given FP64 right-hand side b (||b||_M^2 = bb) into g->xo by correction
-// passes: r = b - A x (FP64 wave solves when fp64_res, else the grid's stepping), then
+// passes: r = b - A x (FP64 wave solves when fp64_res, else the grid's stepping; with a forcing
+// f_res, r = Pi_h(x; f_res) - x, the same residual for b = Pi_h(0; f_res) by one forced wave
+// solve, so that b is needed only as the first pass's right-hand side), then
 // x += W diag(1/mu) W^T M r (deflated components; with a basis set and a method other than DCG)
 // + the inner Krylov solution of the rest.  With fp64_res the passes repeat until the residual
 // meets p->tol (iterative refinement); without it one pass is made (x0 = 0: exact DEVD for
 // exact eigenvectors).  use_x0: g->xo holds the initial guess.
 static whv_status outer_solve(SolveCtx& c, int method, const whv_params* p, const double* b, double bb,
-                              bool fp64_res, bool use_x0, InnerResult* res, int* n_outer) {
+                              bool fp64_res, bool use_x0, InnerResult* res, int* n_outer,
+                              const double* f_res = nullptr) {
   whv_grid g = c.g;
   const int64_t N = g->N;
   const Basis& B = g->basis;
@@ -762,14 +765,18 @@ static whv_status outer_solve(SolveCtx& c, int method, const whv_params* p, cons
   while (true) {
     if (have_x) {
       if (fp64_res) {
-        TRY(wave_solve(g, c.tg, g->xo, nullptr, g->q, 1, c.res_prec));
+        TRY(wave_solve(g, c.tg, g->xo, f_res, g->q, 1, c.res_prec));
         c.ws64++;
       } else {
-        TRY(wave_solve(g, c.tg, g->xo, nullptr, g->q, 1));
+        TRY(wave_solve(g, c.tg, g->xo, f_res, g->q, 1));
         c.ws++;
       }
-      TRY(copy_dev(g, g->ro, b, N));
-      TRY(axpby(g, N, -1.0, g->q, 1.0, g->ro));
+      if (f_res) {   // q = x - Pi_h(x; f) = -r
+        TRY(axpby(g, N, -1.0, g->q, 0.0, g->ro));
+      } else {
+        TRY(copy_dev(g, g->ro, b, N));
+        TRY(axpby(g, N, -1.0, g->q, 1.0, g->ro));
+      }
     } else {
       TRY(copy_dev(g, g->ro, b, N));
     }
@@ -880,16 +887,18 @@ static whv_status solve_impl(whv_grid g, const whv_params* p, const double* f, i
     }
     TRY(inner_solve(c, method, p, b, bb, use_guess != 0, p->tol, p->maxit, fuse, &R));
   } else {
-    // ---- iterative refinement with FP64 residuals on the full system b = Pi_h(0; f)
+    // ---- iterative refinement with FP64 residuals on the full system b = Pi_h(0; f): b in the
+    // stepping precision (the first pass's right-hand side and |b|), every residual
+    // r = Pi_h(x; f) - x by one FP64 (or double-float) forced wave solve
     TRY(ensure_fp64_buffers(g));
-    TRY(wave_solve(g, tg, nullptr, f, g->bo, 0, c.res_prec));
-    c.ws64++;
+    TRY(wave_solve(g, tg, nullptr, f, g->bo, 0));
+    c.ws++;
     TRY(dot_async(g, g->bo, g->bo, S_RR0));
     TRY(fetch_scalars(g));
     const double bb = g->scal_host[S_RR0];
     if (!isfinite(bb)) return fail(g, WHV_ERR_BREAKDOWN, "non-finite right-hand side b (NaN/Inf in f?)");
     if (use_guess) TRY(copy_dev(g, g->xo, u, N));
-    TRY(outer_solve(c, method, p, g->bo, bb, true, use_guess != 0, &R, &outer));
+    TRY(outer_solve(c, method, p, g->bo, bb, true, use_guess != 0, &R, &outer, f));
     TRY(copy_dev(g, g->x, g->xo, N));
   }
 

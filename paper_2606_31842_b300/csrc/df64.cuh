@@ -59,8 +59,9 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
 // the pair is renormalised by one fast two-sum.  The terms dropped (products of two low parts)
 // and the FP32 rounding of the low-order sum are each below ~u^2 |operand| (u = 2^-24), so the
 // error of an update is below ~16 u^2 sum |operands| -- the same order as the chain of
-// double-word additions and products it replaces (each ~2^-46 (|a| + |b|)), in about two
-// thirds of the FP32 operations.
+// double-word additions and products it replaces (each ~2^-46 (|a| + |b|)), in about 70 % of
+// its FP32 operations (forced 5-point update with its neighbour sums: 67 against 94; filter
+// sum: 15 against 18).
 struct dfs {             // unnormalised double-float: value h + l, |l| a few ulp(h)
   float h, l;
 };

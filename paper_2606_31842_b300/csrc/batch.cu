@@ -1119,6 +1119,78 @@ __global__ void k_batch_check(double* const* __restrict__ scal, int np) {
   if (!(sc[S_FLAG] == 0.0 && sc[S_RR] > sc[S_STOP] && it < sc[S_MAXIT])) sc[S_HALT] = 1.0;
 }
 
+// The CG vector updates of every problem in two launches (instead of two per problem): problem p
+// owns blocks [block0, block0 + blocks) with blocks = the grid of the single-grid update (so each
+// problem's block partition, and its reduction order, is the single-grid one).  The x / r update
+// reduces r^T M r per problem (last block of the problem adds its partials in index order).
+struct BCg {
+  double *x, *r, *p;
+  const double *q, *mw;
+  int64_t n;
+  double* scal;
+  double* partials;
+  unsigned* counter;
+  int block0, blocks;
+};
+
+__device__ __forceinline__ int cg_problem(const BCg* __restrict__ D, int np, int b) {
+  int lo = 0, hi = np - 1;   // last problem with block0 <= b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (D[mid].block0 <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_batch_cg_update(const BCg* __restrict__ D, int np) {
+  const BCg& B = D[cg_problem(D, np, blockIdx.x)];
+  double* scal = B.scal;
+  if (scal[S_HALT] != 0.0) return;   // a stopped problem
+  const int lb = blockIdx.x - B.block0;
+  const double rr = scal[S_RR];
+  const double pq = scal[S_PQ];
+  const double alpha = rr / pq;
+  const bool ok = (pq != 0.0) && isfinite(alpha);
+  const double a = ok ? alpha : 0.0;
+  double s = 0.0;
+  const int64_t stride = (int64_t)B.blocks * blockDim.x;
+  for (int64_t i = lb * (int64_t)blockDim.x + threadIdx.x; i < B.n; i += stride) {
+    B.x[i] = fma(a, B.p[i], B.x[i]);
+    const double ri = fma(-a, B.q[i], B.r[i]);
+    B.r[i] = ri;
+    s = fma(B.mw ? ri * B.mw[i] : ri, ri, s);
+  }
+  s = block_sum(s);
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    B.partials[lb] = s;
+    __threadfence();
+    s_last = atomicAdd(B.counter, 1u) == (unsigned)(B.blocks - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int i = threadIdx.x; i < B.blocks; i += blockDim.x) t += __ldcg(B.partials + i);
+  t = block_sum(t);
+  if (threadIdx.x == 0) {
+    *B.counter = 0u;
+    scal[S_ALPHA] = a;
+    scal[S_BETA] = t / rr;
+    scal[S_RR] = t;
+    if (!ok || !isfinite(t)) scal[S_FLAG] = 1.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_batch_cg_direction(const BCg* __restrict__ D, int np) {
+  const BCg& B = D[cg_problem(D, np, blockIdx.x)];
+  if (B.scal[S_HALT] != 0.0) return;
+  const double beta = B.scal[S_BETA];
+  const int lb = blockIdx.x - B.block0;
+  const int64_t stride = (int64_t)B.blocks * blockDim.x;
+  for (int64_t i = lb * (int64_t)blockDim.x + threadIdx.x; i < B.n; i += stride) B.p[i] = fma(beta, B.p[i], B.r[i]);
+}
+
 // keep the WHILE loop running while any problem is active
 __global__ void k_batch_any(cudaGraphConditionalHandle h, double* const* __restrict__ scal, int np,
                             const int* __restrict__ err) {
@@ -1876,6 +1948,21 @@ static whv_status build_cg_graph(BatchCtx& c, const Wave& ap, int check_every, C
     B_CUDA(c.g0, cudaGraphAddNode(&node, G->graph, nullptr, nullptr, 0, &prm));
     body = prm.conditional.phGraph_out[0];
   }
+  // descriptor table of the batched CG updates (before the capture: no allocation inside it)
+  int cg_blocks = 0;
+  BCg* cgd = nullptr;
+  {
+    std::vector<BCg> d(c.np);
+    for (int p = 0; p < c.np; ++p) {
+      whv_grid g = c.grids[p];
+      const int nb = (int)std::min<int64_t>(std::max<int64_t>((g->N + 255) / 256, 1), kRedBlocks);
+      d[p] = BCg{g->x, g->r, g->p, g->q, g->mw, g->N, g->scal, chan(g, CH_UPDATE), g->counters + CH_UPDATE,
+                 cg_blocks, nb};
+      cg_blocks += nb;
+    }
+    B_CUDA(c.g0, c.alloc(&cgd, c.np * sizeof(BCg)));
+    B_CUDA(c.g0, cudaMemcpy(cgd, d.data(), c.np * sizeof(BCg), cudaMemcpyHostToDevice));
+  }
   B_CUDA(c.g0, cudaStreamBeginCaptureToGraph(c.st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   const int64_t l0 = whv_kernel_launches();
   whv_status s = WHV_OK;
@@ -1884,9 +1971,10 @@ static whv_status build_cg_graph(BatchCtx& c, const Wave& ap, int check_every, C
     k_batch_finish<<<c.np, 256, 0, c.st>>>(ap.fin);
     e = cudaGetLastError();
   }
-  for (int p = 0; p < c.np && e == cudaSuccess && s == WHV_OK; ++p) {
-    s = cg_update(c.grids[p]);
-    if (s == WHV_OK) s = cg_direction(c.grids[p]);
+  if (e == cudaSuccess) {   // the CG updates of all problems: one launch each
+    k_batch_cg_update<<<cg_blocks, 256, 0, c.st>>>(cgd, c.np);
+    k_batch_cg_direction<<<cg_blocks, 256, 0, c.st>>>(cgd, c.np);
+    e = cudaGetLastError();
   }
   if (e == cudaSuccess && s == WHV_OK) {
     k_batch_check<<<(c.np + 127) / 128, 128, 0, c.st>>>(c.scal, c.np);
@@ -1895,7 +1983,7 @@ static whv_status build_cg_graph(BatchCtx& c, const Wave& ap, int check_every, C
   }
   cudaGraph_t captured = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(c.st, &captured);
-  G->body_launches = (whv_kernel_launches() - l0) + (device_loop ? 4 : 3);   // + wave, finish, check(, any)
+  G->body_launches = (whv_kernel_launches() - l0) + (device_loop ? 6 : 5);   // wave, finish, 2 updates, check(, any)
   count_launches(-(whv_kernel_launches() - l0));
   if (s != WHV_OK) return s;
   if (e != cudaSuccess) return cuda_fail(c.g0, e, "batched loop body");

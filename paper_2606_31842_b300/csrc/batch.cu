@@ -928,11 +928,27 @@ __device__ __forceinline__ void front_issue(const BMapsF* __restrict__ M, int p,
   tma_load_2d(blk + 128 * kFRB * 4, &M[p].acc, x0 + kFK, row, bar);         // filter sums
 }
 
+// bounded wait (one lane) until *cnt >= target; false after the limit (the error flag is raised)
+// or once another warp has raised it
+__device__ __forceinline__ bool wait_count(const unsigned* cnt, unsigned target, int* err) {
+  unsigned long long spins = 0;
+  while (*(const volatile unsigned*)cnt < target) {
+    if (++spins > kBarrierSpins) {
+      atomicExch(err, 1);
+      return false;
+    }
+    if ((spins & 1023ull) == 0 && *(volatile int*)err) return false;
+    __nanosleep(64);
+  }
+  __threadfence();
+  return true;
+}
+
 __global__ void __launch_bounds__(kFWarps * 32) k_batch_front(const BTileT* __restrict__ P,
                                                               const BMapsF* __restrict__ M,
                                                               const int* __restrict__ nact, int J,
-                                                              const float* __restrict__ wtab, unsigned* bar_count,
-                                                              unsigned* bar_gen, int* err) {
+                                                              const int64_t* __restrict__ joff, unsigned* pcnt,
+                                                              const float* __restrict__ wtab, int* err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* const base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   __shared__ int64_t s_tile0[kBatchMaxProblems + 1];
@@ -952,14 +968,20 @@ __global__ void __launch_bounds__(kFWarps * 32) k_batch_front(const BTileT* __re
   const int64_t G = (int64_t)gridDim.x * kFWarps;
   const int64_t gw = (int64_t)blockIdx.x * kFWarps + warp;
   bool failed = false;
-  for (int j = 0; j < J && !failed; ++j) {
-    const int A = nact[j];
-    const int64_t total = s_tile0[A];
+  // work items of all sweeps in one sequence (sweep by sweep, the active problems' strips in
+  // order), taken round-robin by the warps; a strip of sweep j waits only for the strips of its
+  // own problem's sweep j - 1 (per-problem completion counters), not for the whole grid
+  const int64_t nitems = joff[J];
+  int j = 0, p = 0;
+  for (int64_t it = gw; it < nitems && !failed; it += G) {
+    while (joff[j + 1] <= it) {
+      ++j;
+      p = 0;
+    }
+    const int64_t item = it - joff[j];
+    while (s_tile0[p + 1] <= item) ++p;
     const int qi = (j + 1) & 1, qo = j & 1;
-    if (j > 0) fence_proxy_async_global();   // the previous sweep's stores before this sweep's copies
-    int p = 0;
-    for (int64_t item = gw; item < total && !failed; item += G) {
-      while (s_tile0[p + 1] <= item) ++p;
+    {
       const BTileT& B = P[p];
       if (B.halt && *B.halt != 0.0) continue;
       const int t = (int)(item - B.tile0);
@@ -987,9 +1009,20 @@ __global__ void __launch_bounds__(kFWarps * 32) k_batch_front(const BTileT* __re
 #pragma unroll
       for (int a = 0; a < kFK + 1; ++a) st.A[a][0] = st.A[a][1] = 0.0f;
       const int nblk = (c1 - c0 + 1 + kFRB - 1) / kFRB;
-      if (!first && lane == 0) {
-        front_issue(M, p, qi, x0, c0, wbase, &s_bar[warp][0]);
-        if (nblk > 1) front_issue(M, p, qi, x0, c0 + kFRB, wbase + kFBlockBytes, &s_bar[warp][1]);
+      if (!first) {   // every strip of this problem's previous sweep is done: its stores, then the copies
+        bool ok = true;
+        if (lane == 0) {
+          ok = wait_count(pcnt + p, (unsigned)(j * B.ntiles), err);
+          if (ok) fence_proxy_async_global();
+        }
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {
+          failed = true;
+          break;
+        }
+        if (lane == 0) {
+          front_issue(M, p, qi, x0, c0, wbase, &s_bar[warp][0]);
+          if (nblk > 1) front_issue(M, p, qi, x0, c0 + kFRB, wbase + kFBlockBytes, &s_bar[warp][1]);
+        }
       }
       __syncwarp();
       double part = 0.0;
@@ -1075,18 +1108,20 @@ __global__ void __launch_bounds__(kFWarps * 32) k_batch_front(const BTileT* __re
         part = warp_sum(part);
         if (lane == 0) B.partials[t] = part;
       }
-    }
-    fence_proxy_async_global();   // this sweep's stores before other CTAs' copies of the next sweep
-    if (__syncthreads_or(failed)) {   // copies that did not arrive: give up, after a bounded drain
-      if (threadIdx.x == 0) atomicExch(err, 1);
-      if (lane == 0) {
-        mbar_wait(&s_bar[warp][0], parity[0], kMbarPolls);
-        mbar_wait(&s_bar[warp][1], parity[1], kMbarPolls);
-      }
+      // publish this strip: its stores to every thread and to the copy engine, then the count
+      fence_proxy_async_global();
+      __threadfence();
       __syncwarp();
-      return;
+      if (lane == 0) atomicAdd(pcnt + p, 1u);
     }
-    if (!grid_barrier(bar_count, bar_gen, err, gridDim.x)) return;
+  }
+  if (__syncthreads_or(failed)) {   // a wait or copies that did not complete: give up, after a bounded drain
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    if (lane == 0) {
+      mbar_wait(&s_bar[warp][0], parity[0], kMbarPolls);
+      mbar_wait(&s_bar[warp][1], parity[1], kMbarPolls);
+    }
+    __syncwarp();
   }
 }
 
@@ -1211,6 +1246,9 @@ struct Wave {
   void* ptab = nullptr;
   BFin* fin = nullptr;
   int J = 0, K = 1, nblocks = 1;
+  int64_t* joff = nullptr;     // wavefront role: first work item of each sweep (J + 1 entries)
+  unsigned* pcnt = nullptr;    // ... and per-problem completion counters
+  int np = 0;
   size_t smem = 0;
   cudaError_t (*launch)(cudaStream_t, const Wave&, unsigned*, int*) = nullptr;
 };
@@ -1532,14 +1570,17 @@ static whv_status make_wave_tma(BatchCtx& c, const RoleIO& io, int K, Wave* out)
 
 // ------------------------------------------------------------------ wavefront role (host)
 static cudaError_t launch_front(cudaStream_t st, const Wave& w, unsigned* bar, int* err) {
+  (void)bar;   // no grid barrier: per-problem completion counters, zeroed before every launch
   const BTileT* P = (const BTileT*)w.desc;
   const BMapsF* M = (const BMapsF*)w.maps;
   const float* wt = (const float*)w.wtab;
-  unsigned* bc = bar;
-  unsigned* bg = bar + 1;
   int J = w.J;
   const int* na = w.nact;
-  void* args[] = {(void*)&P, (void*)&M, (void*)&na, (void*)&J, (void*)&wt, (void*)&bc, (void*)&bg, (void*)&err};
+  const int64_t* jo = w.joff;
+  unsigned* pc = w.pcnt;
+  const cudaError_t e = cudaMemsetAsync(w.pcnt, 0, w.np * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&P, (void*)&M, (void*)&na, (void*)&J, (void*)&jo, (void*)&pc, (void*)&wt, (void*)&err};
   return cudaLaunchCooperativeKernel((const void*)k_batch_front, dim3(w.nblocks), dim3(kFWarps * 32), args, w.smem,
                                      st);
 }
@@ -1613,6 +1654,12 @@ static whv_status make_wave_front(BatchCtx& c, const RoleIO& io, Wave* out) {
     while (a < np && nsw[order[a]] > j) ++a;
     nact[j] = a;
   }
+  std::vector<int64_t> joff(w.J + 1, 0);   // strips of sweep j: those of its active problems
+  for (int j = 0; j < w.J; ++j) joff[j + 1] = joff[j] + (nact[j] < np ? d[nact[j]].tile0 : tile0);
+  B_CUDA(c.g0, c.alloc(&w.joff, (w.J + 1) * sizeof(int64_t)));
+  B_CUDA(c.g0, c.alloc(&w.pcnt, np * sizeof(unsigned)));
+  B_CUDA(c.g0, cudaMemcpy(w.joff, joff.data(), (w.J + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  w.np = np;
   B_CUDA(c.g0, c.alloc(&w.desc, np * sizeof(BTileT)));
   B_CUDA(c.g0, c.alloc(&w.maps, np * sizeof(BMapsF)));
   B_CUDA(c.g0, c.alloc(&w.nact, w.J * sizeof(int)));

@@ -389,7 +389,7 @@ KERNEL_SOURCES = {
     "k_batch_tma": (("batch.cu", "k_batch_tma"), ("batch.cu", "tma_issue"), ("batch.cu", "tma_live_item"),
                     "quad2d.cuh", "tma.cuh", "whv_device.cuh"),
     "k_batch_front": (("batch.cu", "k_batch_front"), ("batch.cu", "front_clock"), ("batch.cu", "front_issue"),
-                      ("batch.cu", "front_acc"), "tma.cuh", "whv_device.cuh"),
+                      ("batch.cu", "front_acc"), ("batch.cu", "wait_count"), "tma.cuh", "whv_device.cuh"),
 }
 
 

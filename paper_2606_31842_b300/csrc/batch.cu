@@ -944,7 +944,7 @@ __device__ __forceinline__ bool wait_count(const unsigned* cnt, unsigned target,
   return true;
 }
 
-__global__ void __launch_bounds__(kFWarps * 32) k_batch_front(const BTileT* __restrict__ P,
+__global__ void __launch_bounds__(kFWarps * 32, 3) k_batch_front(const BTileT* __restrict__ P,
                                                               const BMapsF* __restrict__ M,
                                                               const int* __restrict__ nact, int J,
                                                               const int64_t* __restrict__ joff, unsigned* pcnt,
@@ -1028,11 +1028,14 @@ __global__ void __launch_bounds__(kFWarps * 32) k_batch_front(const BTileT* __re
       double part = 0.0;
       int c = c0;
       // clocks in groups of nine (the phase of the register rings is c - c0 mod 9)
-      auto clock = [&](auto ph) {
+      // (the first and the last sweep are separate instances, so that the loop of the other
+      // sweeps carries neither the Taylor start nor the FP64 epilogue)
+      auto clock = [&](auto ph, auto fst, auto lst) {
         constexpr int PH = decltype(ph)::value;
+        constexpr bool FIRST = decltype(fst)::value, LAST = decltype(lst)::value;
         const int rel = c - c0, blk = rel / kFRB, row = rel % kFRB, slot = blk & 1;
         float2 wn = make_float2(0.f, 0.f), wp = wn, an = wn;
-        if (first) {
+        if (FIRST) {
           const bool rin = (unsigned)c < (unsigned)ny;
           if (rin && cin0 && B.v) wn.x = (float)__ldg(B.v + gx0 + (int64_t)nx * c);
           if (rin && cin1 && B.v) wn.y = (float)__ldg(B.v + gx0 + 1 + (int64_t)nx * c);
@@ -1054,14 +1057,11 @@ __global__ void __launch_bounds__(kFWarps * 32) k_batch_front(const BTileT* __re
           }
         }
         float o0, o1, p0, p1;
-        if (first)
-          front_clock<PH, true>(st, c, wn, wp, an, wt, ax, ay, bb, ih2x, ih2y, hdt2, cin0, cin1, ny, o0, o1, p0, p1);
-        else
-          front_clock<PH, false>(st, c, wn, wp, an, wt, ax, ay, bb, ih2x, ih2y, hdt2, cin0, cin1, ny, o0, o1, p0, p1);
+        front_clock<PH, FIRST>(st, c, wn, wp, an, wt, ax, ay, bb, ih2x, ih2y, hdt2, cin0, cin1, ny, o0, o1, p0, p1);
         const int y = c - kFK;
         if (y >= Y0 && y < Y1 && outc) {
           const float2 a = front_acc<PH>(st);
-          if (!last) {
+          if (!LAST) {
             const int64_t gi = gx0 + (int64_t)B.pitch * y;
             *reinterpret_cast<float2*>(B.w[2 * qo + 1] + gi) = make_float2(o0, o1);
             *reinterpret_cast<float2*>(B.w[2 * qo] + gi) = make_float2(p0, p1);
@@ -1085,24 +1085,35 @@ __global__ void __launch_bounds__(kFWarps * 32) k_batch_front(const BTileT* __re
         }
         ++c;
       };
-      while (c <= c1) {
-        clock(std::integral_constant<int, 0>());
-        if (c > c1) break;
-        clock(std::integral_constant<int, 1>());
-        if (c > c1) break;
-        clock(std::integral_constant<int, 2>());
-        if (c > c1) break;
-        clock(std::integral_constant<int, 3>());
-        if (c > c1) break;
-        clock(std::integral_constant<int, 4>());
-        if (c > c1) break;
-        clock(std::integral_constant<int, 5>());
-        if (c > c1) break;
-        clock(std::integral_constant<int, 6>());
-        if (c > c1) break;
-        clock(std::integral_constant<int, 7>());
-        if (c > c1) break;
-        clock(std::integral_constant<int, 8>());
+      auto run = [&](auto fst, auto lst) {
+        while (c <= c1) {
+          clock(std::integral_constant<int, 0>(), fst, lst);
+          if (c > c1) break;
+          clock(std::integral_constant<int, 1>(), fst, lst);
+          if (c > c1) break;
+          clock(std::integral_constant<int, 2>(), fst, lst);
+          if (c > c1) break;
+          clock(std::integral_constant<int, 3>(), fst, lst);
+          if (c > c1) break;
+          clock(std::integral_constant<int, 4>(), fst, lst);
+          if (c > c1) break;
+          clock(std::integral_constant<int, 5>(), fst, lst);
+          if (c > c1) break;
+          clock(std::integral_constant<int, 6>(), fst, lst);
+          if (c > c1) break;
+          clock(std::integral_constant<int, 7>(), fst, lst);
+          if (c > c1) break;
+          clock(std::integral_constant<int, 8>(), fst, lst);
+        }
+      };
+      using T_ = std::true_type;
+      using F_ = std::false_type;
+      if (first) {
+        if (last) run(T_(), T_());
+        else run(T_(), F_());
+      } else {
+        if (last) run(F_(), T_());
+        else run(F_(), F_());
       }
       if (last && B.epi == 1) {
         part = warp_sum(part);

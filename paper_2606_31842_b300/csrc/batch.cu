@@ -857,15 +857,16 @@ struct BMapsF {          // tensor maps of one problem for the wavefront kernel
 
 struct FrontState {      // the registers of one lane (two columns)
   float L[kFK + 1][3][2];    // level t - 1 at index t: L[0] = W^{n-1}, L[1] = W^n, L[t + 1] = level t
-  float A[kFK + 1][2];       // filter sums of the rows in flight (ring of K + 1 rows)
+  float A[kFK + 1][2];       // filter sums of the rows in flight: A[t] is row c - t at clock c
 };
 
 __device__ __forceinline__ float fr_mask(float v, bool in) { return in ? v : 0.0f; }
 
-// One clock of the wavefront at phase PH = c mod 9 (3 for the level rings, K + 1 = 9 for the
-// filter sums).  Input row c: wn, wp (W^n, W^{n-1}), an = its filter sum so far.  Levels 1 .. K
-// of rows c - 1 .. c - K.  Returns in o0/o1 level K of row c - K (W^{n+K}) and in p0/p1 level K - 1
-// of that row (W^{n+K-1}); the complete filter sum of row c - K stays at A[(c - K) mod 9].
+// One clock of the wavefront at phase PH = c mod 3 (the level rings).  Input row c: wn, wp (W^n,
+// W^{n-1}), an = its filter sum so far (into A[0]).  Levels 1 .. K of rows c - 1 .. c - K.
+// Returns in o0/o1 level K of row c - K (W^{n+K}) and in p0/p1 level K - 1 of that row
+// (W^{n+K-1}); the complete filter sum of row c - K is then A[K] (front_shift moves the filter
+// sums one row on after the clock).
 template <int PH, bool FIRST>
 __device__ __forceinline__ void front_clock(FrontState& st, int c, float2 wn, float2 wp, float2 an, const float* wt,
                                             float ax, float ay, float b, float ih2x, float ih2y, float hdt2,
@@ -874,7 +875,7 @@ __device__ __forceinline__ void front_clock(FrontState& st, int c, float2 wn, fl
   constexpr int r3 = PH % 3;
   st.L[0][r3][0] = wp.x; st.L[0][r3][1] = wp.y;
   st.L[1][r3][0] = wn.x; st.L[1][r3][1] = wn.y;
-  st.A[PH % (kFK + 1)][0] = an.x; st.A[PH % (kFK + 1)][1] = an.y;
+  st.A[0][0] = an.x; st.A[0][1] = an.y;
 #pragma unroll
   for (int t = 1; t <= kFK; ++t) {
     const int y = c - t;
@@ -900,9 +901,8 @@ __device__ __forceinline__ void front_clock(FrontState& st, int c, float2 wn, fl
     const bool rin = (unsigned)y < (unsigned)ny;
     n0 = fr_mask(n0, rin && cin0);
     n1 = fr_mask(n1, rin && cin1);
-    const int ia = (PH - t + 90) % (kFK + 1);
-    st.A[ia][0] = fmaf(wt[t - 1], n0, st.A[ia][0]);
-    st.A[ia][1] = fmaf(wt[t - 1], n1, st.A[ia][1]);
+    st.A[t][0] = fmaf(wt[t - 1], n0, st.A[t][0]);
+    st.A[t][1] = fmaf(wt[t - 1], n1, st.A[t][1]);
     if (t < kFK) {
       st.L[t + 1][i0][0] = n0;
       st.L[t + 1][i0][1] = n1;
@@ -915,9 +915,15 @@ __device__ __forceinline__ void front_clock(FrontState& st, int c, float2 wn, fl
   }
 }
 
-template <int PH>
-__device__ __forceinline__ float2 front_acc(const FrontState& st) {
-  return make_float2(st.A[(PH - kFK + 90) % (kFK + 1)][0], st.A[(PH - kFK + 90) % (kFK + 1)][1]);
+__device__ __forceinline__ float2 front_acc(const FrontState& st) { return make_float2(st.A[kFK][0], st.A[kFK][1]); }
+
+// end of a clock: the filter sum of row c - t becomes that of row (c + 1) - (t + 1)
+__device__ __forceinline__ void front_shift(FrontState& st) {
+#pragma unroll
+  for (int t = kFK; t >= 1; --t) {
+    st.A[t][0] = st.A[t - 1][0];
+    st.A[t][1] = st.A[t - 1][1];
+  }
 }
 
 __device__ __forceinline__ void front_issue(const BMapsF* __restrict__ M, int p, int qi, int x0, int row,
@@ -1027,7 +1033,7 @@ __global__ void __launch_bounds__(kFWarps * 32, 3) k_batch_front(const BTileT* _
       __syncwarp();
       double part = 0.0;
       int c = c0;
-      // clocks in groups of nine (the phase of the register rings is c - c0 mod 9)
+      // clocks in groups of three (the phase of the level rings is c - c0 mod 3)
       // (the first and the last sweep are separate instances, so that the loop of the other
       // sweeps carries neither the Taylor start nor the FP64 epilogue)
       auto clock = [&](auto ph, auto fst, auto lst) {
@@ -1060,7 +1066,7 @@ __global__ void __launch_bounds__(kFWarps * 32, 3) k_batch_front(const BTileT* _
         front_clock<PH, FIRST>(st, c, wn, wp, an, wt, ax, ay, bb, ih2x, ih2y, hdt2, cin0, cin1, ny, o0, o1, p0, p1);
         const int y = c - kFK;
         if (y >= Y0 && y < Y1 && outc) {
-          const float2 a = front_acc<PH>(st);
+          const float2 a = front_acc(st);
           if (!LAST) {
             const int64_t gi = gx0 + (int64_t)B.pitch * y;
             *reinterpret_cast<float2*>(B.w[2 * qo + 1] + gi) = make_float2(o0, o1);
@@ -1083,6 +1089,7 @@ __global__ void __launch_bounds__(kFWarps * 32, 3) k_batch_front(const BTileT* _
             }
           }
         }
+        front_shift(st);
         ++c;
       };
       auto run = [&](auto fst, auto lst) {
@@ -1092,18 +1099,6 @@ __global__ void __launch_bounds__(kFWarps * 32, 3) k_batch_front(const BTileT* _
           clock(std::integral_constant<int, 1>(), fst, lst);
           if (c > c1) break;
           clock(std::integral_constant<int, 2>(), fst, lst);
-          if (c > c1) break;
-          clock(std::integral_constant<int, 3>(), fst, lst);
-          if (c > c1) break;
-          clock(std::integral_constant<int, 4>(), fst, lst);
-          if (c > c1) break;
-          clock(std::integral_constant<int, 5>(), fst, lst);
-          if (c > c1) break;
-          clock(std::integral_constant<int, 6>(), fst, lst);
-          if (c > c1) break;
-          clock(std::integral_constant<int, 7>(), fst, lst);
-          if (c > c1) break;
-          clock(std::integral_constant<int, 8>(), fst, lst);
         }
       };
       using T_ = std::true_type;

@@ -824,17 +824,17 @@ __global__ void __launch_bounds__(kBThreads / R, R) k_batch_tma(const BTileT* __
 
 // ------------------------------------------------------------------ 2-D, FP32, wavefront
 // The f = 0 FP32 wave solve of the 5-point stencil with c = 1 (every A p of the batched CG loop)
-// as a wavefront in registers: a work item is a strip of 64 columns (the 64 - 2K middle ones are
-// its output, K on each side are halo) and S rows of one problem, and ONE WARP advances it K time
-// levels in a single pass down the rows.  Lane l holds columns 2l, 2l + 1 of the strip; at clock
+// as a wavefront in registers: a work item is a strip of W = 32 C columns (the W - 2K middle ones
+// are its output, K on each side are halo) and S rows of one problem, and ONE WARP advances it K
+// time levels in a single pass down the rows.  Lane l holds columns C l .. C l + C - 1; at clock
 // c the warp takes input row c (W^n, W^{n-1} and the filter sums, copied by the copy engine into
 // the warp's own shared-memory blocks of FRB rows, two blocks in flight) and computes level t of
 // row c - t for t = 1 .. K: level t needs rows c - t - 1 .. c - t + 1 of level t - 1 (a ring of
-// three rows per level in registers) and row c - t of level t - 2; x neighbours come from the
-// adjacent lanes (shuffles).  There is no shared-memory exchange and no block-wide barrier: each
+// three rows per level in registers) and row c - t of level t - 2; the x neighbours of a lane's
+// outer columns come from the adjacent lanes (shuffles), the others from its own registers.  There is no shared-memory exchange and no block-wide barrier: each
 // warp runs on its own.  The filter sum of row y collects w_{n+t} W^{n+t}(y) in a ring of K + 1
 // rows; at clock c, row c - K is complete and W^{n+K}, W^{n+K-1} and its filter sum go to global
-// memory (8-byte stores of the output columns).  Rows above and below the strip's S rows are
+// memory (vector stores of the output columns).  Rows above and below the strip's S rows are
 // input halo: a level-t value is exact at distance >= t from the rows and columns the strip did
 // not load, so the K-wide halos leave the output exact.  Cells outside the domain are held at 0.
 // The first sweep reads W^0 = v (FP64) directly and takes the Taylor start as level 1; the last
@@ -842,40 +842,73 @@ __global__ void __launch_bounds__(kBThreads / R, R) k_batch_tma(const BTileT* __
 // zero filter weights).  Same operations in the same order as the four-cell kernels: bitwise
 // equal results.
 constexpr int kFK = 8;                 // time levels per sweep
-constexpr int kFTW = 64 - 2 * kFK;     // output columns of a strip (48)
+constexpr int kFC = 4;                 // columns per lane
+constexpr int kFW = 32 * kFC;          // strip width
+constexpr int kFTW = kFW - 2 * kFK;    // output columns of a strip
 constexpr int kFS = 256;               // output rows of a work item
 constexpr int kFRB = 8;                // rows per copied block
 constexpr int kFWarps = 4;             // warps per CTA
-constexpr int kFBlockBytes = (64 + 64 + kFTW) * kFRB * 4;   // W^n, W^{n-1}, filter sums of FRB rows
-constexpr int kFWarpBytes = 2 * kFBlockBytes;               // two blocks in flight
+constexpr int kFBlockBytes = (kFW + kFW + kFTW) * kFRB * 4;   // W^n, W^{n-1}, filter sums of FRB rows
+constexpr int kFWarpBytes = 2 * kFBlockBytes;                 // two blocks in flight
 constexpr int kFSmem = kFWarps * kFWarpBytes + 128;
+static_assert(kFC == 2 || kFC == 4, "two or four columns per lane");
+static_assert(kFK % 4 == 0 && kFK % kFC == 0, "strip origins x0 = sx (W - 2K) - K stay 16-byte aligned; "
+                                               "the output columns are whole lane groups");
+static_assert(kFBlockBytes % 128 == 0, "copy destinations stay 128-byte aligned");
 
 struct BMapsF {          // tensor maps of one problem for the wavefront kernel
-  CUtensorMap w[4];      // 64 x FRB boxes of the pitched state buffers
-  CUtensorMap acc;       // (64 - 2K) x FRB boxes of the filter sums
+  CUtensorMap w[4];      // W x FRB boxes of the pitched state buffers
+  CUtensorMap acc;       // (W - 2K) x FRB boxes of the filter sums
 };
 
-struct FrontState {      // the registers of one lane (two columns)
-  float L[kFK + 1][3][2];    // level t - 1 at index t: L[0] = W^{n-1}, L[1] = W^n, L[t + 1] = level t
-  float A[kFK + 1][2];       // filter sums of the rows in flight: A[t] is row c - t at clock c
+struct FV {              // the values of a lane's C columns
+  float v[kFC];
+};
+__device__ __forceinline__ FV fv_zero() {
+  FV r;
+#pragma unroll
+  for (int e = 0; e < kFC; ++e) r.v[e] = 0.0f;
+  return r;
+}
+__device__ __forceinline__ FV fv_load(const void* p) {   // 8- or 16-byte aligned
+  FV r;
+  if constexpr (kFC == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
+  } else {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    r.v[0] = q.x; r.v[1] = q.y;
+  }
+  return r;
+}
+__device__ __forceinline__ void fv_store(float* p, const FV& a) {
+  if constexpr (kFC == 4) *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+  else *reinterpret_cast<float2*>(p) = make_float2(a.v[0], a.v[1]);
+}
+
+struct FrontState {      // the registers of one lane
+  float L[kFK + 1][3][kFC];  // level t - 1 at index t: L[0] = W^{n-1}, L[1] = W^n, L[t + 1] = level t
+  float A[kFK + 1][kFC];     // filter sums of the rows in flight: A[t] is row c - t at clock c
 };
 
 __device__ __forceinline__ float fr_mask(float v, bool in) { return in ? v : 0.0f; }
 
 // One clock of the wavefront at phase PH = c mod 3 (the level rings).  Input row c: wn, wp (W^n,
 // W^{n-1}), an = its filter sum so far (into A[0]).  Levels 1 .. K of rows c - 1 .. c - K.
-// Returns in o0/o1 level K of row c - K (W^{n+K}) and in p0/p1 level K - 1 of that row
-// (W^{n+K-1}); the complete filter sum of row c - K is then A[K] (front_shift moves the filter
-// sums one row on after the clock).
+// Returns in o level K of row c - K (W^{n+K}) and in pv level K - 1 of that row (W^{n+K-1}); the
+// complete filter sum of row c - K is then A[K] (front_shift moves the filter sums one row on
+// after the clock).
 template <int PH, bool FIRST>
-__device__ __forceinline__ void front_clock(FrontState& st, int c, float2 wn, float2 wp, float2 an, const float* wt,
-                                            float ax, float ay, float b, float ih2x, float ih2y, float hdt2,
-                                            bool cin0, bool cin1, int ny, float& o0, float& o1, float& p0,
-                                            float& p1) {
+__device__ __forceinline__ void front_clock(FrontState& st, int c, const FV& wn, const FV& wp, const FV& an,
+                                            const float* wt, float ax, float ay, float b, float ih2x, float ih2y,
+                                            float hdt2, const bool* cin, int ny, FV& o, FV& pv) {
   constexpr int r3 = PH % 3;
-  st.L[0][r3][0] = wp.x; st.L[0][r3][1] = wp.y;
-  st.L[1][r3][0] = wn.x; st.L[1][r3][1] = wn.y;
-  st.A[0][0] = an.x; st.A[0][1] = an.y;
+#pragma unroll
+  for (int e = 0; e < kFC; ++e) {
+    st.L[0][r3][e] = wp.v[e];
+    st.L[1][r3][e] = wn.v[e];
+    st.A[0][e] = an.v[e];
+  }
 #pragma unroll
   for (int t = 1; t <= kFK; ++t) {
     const int y = c - t;
@@ -883,55 +916,59 @@ __device__ __forceinline__ void front_clock(FrontState& st, int c, float2 wn, fl
     const float* up = st.L[t][im];
     const float* mid = st.L[t][i0];
     const float* dn = st.L[t][ip];
-    const float l = __shfl_up_sync(0xffffffffu, mid[1], 1);
+    const float l = __shfl_up_sync(0xffffffffu, mid[kFC - 1], 1);
     const float r = __shfl_down_sync(0xffffffffu, mid[0], 1);
-    float n0, n1;
-    if (FIRST && t == 1) {   // Taylor start W^1 = W^0 + dt^2/2 L W^0
-      float L0 = fmaf(-2.0f, mid[0], l + mid[1]) * ih2x;
-      L0 = fmaf(fmaf(-2.0f, mid[0], up[0] + dn[0]), ih2y, L0);
-      n0 = fmaf(hdt2, L0, mid[0]);
-      float L1 = fmaf(-2.0f, mid[1], mid[0] + r) * ih2x;
-      L1 = fmaf(fmaf(-2.0f, mid[1], up[1] + dn[1]), ih2y, L1);
-      n1 = fmaf(hdt2, L1, mid[1]);
-    } else {
-      const float* pv = st.L[t - 1][i0];   // level t - 2 at row y
-      n0 = fmaf(ay, up[0] + dn[0], fmaf(ax, l + mid[1], fmaf(b, mid[0], -pv[0])));
-      n1 = fmaf(ay, up[1] + dn[1], fmaf(ax, mid[0] + r, fmaf(b, mid[1], -pv[1])));
-    }
     const bool rin = (unsigned)y < (unsigned)ny;
-    n0 = fr_mask(n0, rin && cin0);
-    n1 = fr_mask(n1, rin && cin1);
-    st.A[t][0] = fmaf(wt[t - 1], n0, st.A[t][0]);
-    st.A[t][1] = fmaf(wt[t - 1], n1, st.A[t][1]);
+    float n[kFC];
+#pragma unroll
+    for (int e = 0; e < kFC; ++e) {
+      const float xl = e == 0 ? l : mid[e - 1];
+      const float xr = e == kFC - 1 ? r : mid[e + 1];
+      if (FIRST && t == 1) {   // Taylor start W^1 = W^0 + dt^2/2 L W^0
+        float L0 = fmaf(-2.0f, mid[e], xl + xr) * ih2x;
+        L0 = fmaf(fmaf(-2.0f, mid[e], up[e] + dn[e]), ih2y, L0);
+        n[e] = fmaf(hdt2, L0, mid[e]);
+      } else {
+        const float* pvv = st.L[t - 1][i0];   // level t - 2 at row y
+        n[e] = fmaf(ay, up[e] + dn[e], fmaf(ax, xl + xr, fmaf(b, mid[e], -pvv[e])));
+      }
+      n[e] = fr_mask(n[e], rin && cin[e]);
+      st.A[t][e] = fmaf(wt[t - 1], n[e], st.A[t][e]);
+    }
     if (t < kFK) {
-      st.L[t + 1][i0][0] = n0;
-      st.L[t + 1][i0][1] = n1;
+#pragma unroll
+      for (int e = 0; e < kFC; ++e) st.L[t + 1][i0][e] = n[e];
     } else {
-      o0 = n0;
-      o1 = n1;
-      p0 = st.L[kFK][i0][0];
-      p1 = st.L[kFK][i0][1];
+#pragma unroll
+      for (int e = 0; e < kFC; ++e) {
+        o.v[e] = n[e];
+        pv.v[e] = st.L[kFK][i0][e];
+      }
     }
   }
 }
 
-__device__ __forceinline__ float2 front_acc(const FrontState& st) { return make_float2(st.A[kFK][0], st.A[kFK][1]); }
+__device__ __forceinline__ FV front_acc(const FrontState& st) {
+  FV a;
+#pragma unroll
+  for (int e = 0; e < kFC; ++e) a.v[e] = st.A[kFK][e];
+  return a;
+}
 
 // end of a clock: the filter sum of row c - t becomes that of row (c + 1) - (t + 1)
 __device__ __forceinline__ void front_shift(FrontState& st) {
 #pragma unroll
-  for (int t = kFK; t >= 1; --t) {
-    st.A[t][0] = st.A[t - 1][0];
-    st.A[t][1] = st.A[t - 1][1];
-  }
+  for (int t = kFK; t >= 1; --t)
+#pragma unroll
+    for (int e = 0; e < kFC; ++e) st.A[t][e] = st.A[t - 1][e];
 }
 
 __device__ __forceinline__ void front_issue(const BMapsF* __restrict__ M, int p, int qi, int x0, int row,
                                             unsigned char* blk, uint64_t* bar) {
   mbar_arrive_expect_tx(bar, kFBlockBytes);
-  tma_load_2d(blk, &M[p].w[2 * qi + 1], x0, row, bar);                      // W^n
-  tma_load_2d(blk + 64 * kFRB * 4, &M[p].w[2 * qi], x0, row, bar);          // W^{n-1}
-  tma_load_2d(blk + 128 * kFRB * 4, &M[p].acc, x0 + kFK, row, bar);         // filter sums
+  tma_load_2d(blk, &M[p].w[2 * qi + 1], x0, row, bar);                       // W^n
+  tma_load_2d(blk + kFW * kFRB * 4, &M[p].w[2 * qi], x0, row, bar);          // W^{n-1}
+  tma_load_2d(blk + 2 * kFW * kFRB * 4, &M[p].acc, x0 + kFK, row, bar);      // filter sums
 }
 
 // bounded wait (one lane) until *cnt >= target; false after the limit (the error flag is raised)
@@ -950,7 +987,7 @@ __device__ __forceinline__ bool wait_count(const unsigned* cnt, unsigned target,
   return true;
 }
 
-__global__ void __launch_bounds__(kFWarps * 32, 3) k_batch_front(const BTileT* __restrict__ P,
+__global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(const BTileT* __restrict__ P,
                                                               const BMapsF* __restrict__ M,
                                                               const int* __restrict__ nact, int J,
                                                               const int64_t* __restrict__ joff, unsigned* pcnt,
@@ -1003,17 +1040,25 @@ __global__ void __launch_bounds__(kFWarps * 32, 3) k_batch_front(const BTileT* _
 #pragma unroll
       for (int s = 0; s < kFK; ++s) wt[s] = s < kk ? __ldg(wtab + B.wofs + n0 + 1 + s) : 0.0f;
       const float w0 = first ? __ldg(wtab + B.wofs) : 0.0f;
-      const int gx0 = x0 + 2 * lane;
-      const bool cin0 = gx0 >= 0 && gx0 < nx, cin1 = gx0 + 1 >= 0 && gx0 + 1 < nx;
-      const bool outc = 2 * lane >= kFK && 2 * lane < 64 - kFK && gx0 < nx;   // output columns
+      const int gx0 = x0 + kFC * lane;
+      bool cin[kFC];
+#pragma unroll
+      for (int e = 0; e < kFC; ++e) cin[e] = gx0 + e >= 0 && gx0 + e < nx;
+      // output columns: the lane's whole group lies inside [K, W - K) (K is a multiple of C)
+      const bool outl = kFC * lane >= kFK && kFC * lane < kFW - kFK;
+      const bool outc = outl && gx0 < nx;
       const float ax = B.ax, ay = B.ay, bb = B.b, ih2x = B.ih2x, ih2y = B.ih2y, hdt2 = 0.5f * B.dt2;
       FrontState st;
 #pragma unroll
       for (int a = 0; a < kFK + 1; ++a)
 #pragma unroll
-        for (int r = 0; r < 3; ++r) st.L[a][r][0] = st.L[a][r][1] = 0.0f;
+        for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int a = 0; a < kFK + 1; ++a) st.A[a][0] = st.A[a][1] = 0.0f;
+          for (int e = 0; e < kFC; ++e) st.L[a][r][e] = 0.0f;
+#pragma unroll
+      for (int a = 0; a < kFK + 1; ++a)
+#pragma unroll
+        for (int e = 0; e < kFC; ++e) st.A[a][e] = 0.0f;
       const int nblk = (c1 - c0 + 1 + kFRB - 1) / kFRB;
       if (!first) {   // every strip of this problem's previous sweep is done: its stores, then the copies
         bool ok = true;
@@ -1040,51 +1085,52 @@ __global__ void __launch_bounds__(kFWarps * 32, 3) k_batch_front(const BTileT* _
         constexpr int PH = decltype(ph)::value;
         constexpr bool FIRST = decltype(fst)::value, LAST = decltype(lst)::value;
         const int rel = c - c0, blk = rel / kFRB, row = rel % kFRB, slot = blk & 1;
-        float2 wn = make_float2(0.f, 0.f), wp = wn, an = wn;
+        FV wn = fv_zero(), wp = fv_zero(), an = fv_zero();
         if (FIRST) {
           const bool rin = (unsigned)c < (unsigned)ny;
-          if (rin && cin0 && B.v) wn.x = (float)__ldg(B.v + gx0 + (int64_t)nx * c);
-          if (rin && cin1 && B.v) wn.y = (float)__ldg(B.v + gx0 + 1 + (int64_t)nx * c);
-          an = make_float2(w0 * wn.x, w0 * wn.y);
+#pragma unroll
+          for (int e = 0; e < kFC; ++e) {
+            if (rin && cin[e] && B.v) wn.v[e] = (float)__ldg(B.v + gx0 + e + (int64_t)nx * c);
+            an.v[e] = w0 * wn.v[e];
+          }
         } else {
           if (row == 0) {   // a new block: wait for its copies
             if (!mbar_wait(&s_bar[warp][slot], parity[slot], kMbarPolls)) failed = true;
             parity[slot] ^= 1u;
           }
           const unsigned char* bp = wbase + slot * kFBlockBytes;
-          wn = reinterpret_cast<const float2*>(bp)[row * 32 + lane];
-          wp = reinterpret_cast<const float2*>(bp + 64 * kFRB * 4)[row * 32 + lane];
-          if (2 * lane >= kFK && 2 * lane < 64 - kFK)
-            an = reinterpret_cast<const float2*>(bp + 128 * kFRB * 4)[row * (kFTW / 2) + lane - kFK / 2];
+          wn = fv_load(bp + (row * 32 + lane) * kFC * 4);
+          wp = fv_load(bp + kFW * kFRB * 4 + (row * 32 + lane) * kFC * 4);
+          if (outl) an = fv_load(bp + 2 * kFW * kFRB * 4 + (row * (kFTW / kFC) + lane - kFK / kFC) * kFC * 4);
           if (row == kFRB - 1) {   // block done: refill its slot two blocks ahead
             __syncwarp();
             if (lane == 0 && blk + 2 < nblk)
               front_issue(M, p, qi, x0, c0 + (blk + 2) * kFRB, wbase + slot * kFBlockBytes, &s_bar[warp][slot]);
           }
         }
-        float o0, o1, p0, p1;
-        front_clock<PH, FIRST>(st, c, wn, wp, an, wt, ax, ay, bb, ih2x, ih2y, hdt2, cin0, cin1, ny, o0, o1, p0, p1);
+        FV o, pv;
+        front_clock<PH, FIRST>(st, c, wn, wp, an, wt, ax, ay, bb, ih2x, ih2y, hdt2, cin, ny, o, pv);
         const int y = c - kFK;
         if (y >= Y0 && y < Y1 && outc) {
-          const float2 a = front_acc(st);
+          const FV a = front_acc(st);
           if (!LAST) {
+            // rows are padded to a multiple of 4 floats: a group's columns past nx are padding
             const int64_t gi = gx0 + (int64_t)B.pitch * y;
-            *reinterpret_cast<float2*>(B.w[2 * qo + 1] + gi) = make_float2(o0, o1);
-            *reinterpret_cast<float2*>(B.w[2 * qo] + gi) = make_float2(p0, p1);
-            *reinterpret_cast<float2*>(B.acc + gi) = a;
+            fv_store(B.w[2 * qo + 1] + gi, o);
+            fv_store(B.w[2 * qo] + gi, pv);
+            fv_store(B.acc + gi, a);
           } else {
             const int64_t gi = gx0 + (int64_t)nx * y;
-            const float av[2] = {a.x, a.y};
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
+            for (int e = 0; e < kFC; ++e) {
               if (gx0 + e >= nx) break;
               if (B.epi == 0) {
-                B.out[gi + e] = (double)av[e];
+                B.out[gi + e] = (double)a.v[e];
               } else {
                 const double vi = __ldg(B.v + gi + e);
-                const double o = vi - (double)av[e];
-                B.out[gi + e] = o;
-                part = fma(B.mw ? vi * __ldg(B.mw + gi + e) : vi, o, part);
+                const double ov = vi - (double)a.v[e];
+                B.out[gi + e] = ov;
+                part = fma(B.mw ? vi * __ldg(B.mw + gi + e) : vi, ov, part);
               }
             }
           }
@@ -1644,7 +1690,7 @@ static whv_status make_wave_front(BatchCtx& c, const RoleIO& io, Wave* out) {
     B.ax = (float)ax; B.ay = (float)ay; B.b = (float)(2.0 - 2.0 * (ax + ay));
     B.tile0 = tile0;
     for (int m = 0; m < 4; ++m)
-      if (!encode_rows(&maps[k].w[m], g->tw[m], g->n[0], g->n[1], g->tpitch, 64))
+      if (!encode_rows(&maps[k].w[m], g->tw[m], g->n[0], g->n[1], g->tpitch, kFW))
         return fail(c.g0, WHV_ERR_CUDA, "batched: cuTensorMapEncodeTiled failed (state buffers)");
     if (!encode_rows(&maps[k].acc, g->tacc, g->n[0], g->n[1], g->tpitch, kFTW))
       return fail(c.g0, WHV_ERR_CUDA, "batched: cuTensorMapEncodeTiled failed (filter sums)");

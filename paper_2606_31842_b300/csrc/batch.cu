@@ -845,7 +845,7 @@ constexpr int kFK = 8;                 // time levels per sweep
 constexpr int kFC = 4;                 // columns per lane
 constexpr int kFW = 32 * kFC;          // strip width
 constexpr int kFTW = kFW - 2 * kFK;    // output columns of a strip
-constexpr int kFS = 256;               // output rows of a work item
+constexpr int kFS = 128;               // output rows of a work item
 constexpr int kFRB = 8;                // rows per copied block
 constexpr int kFWarps = 4;             // warps per CTA
 constexpr int kFBlockBytes = (kFW + kFW + kFTW) * kFRB * 4;   // W^n, W^{n-1}, filter sums of FRB rows

@@ -1048,6 +1048,14 @@ __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(
       const bool outl = kFC * lane >= kFK && kFC * lane < kFW - kFK;
       const bool outc = outl && gx0 < nx;
       const float ax = B.ax, ay = B.ay, bb = B.b, ih2x = B.ih2x, ih2y = B.ih2y, hdt2 = 0.5f * B.dt2;
+      // the descriptor's fields in registers (the stores below could otherwise alias it)
+      float* const wout1 = B.w[2 * qo + 1];
+      float* const wout0 = B.w[2 * qo];
+      float* const accp = B.acc;
+      const double* const vv = B.v;
+      const double* const mwp = B.mw;
+      double* const outp = B.out;
+      const int pitch = B.pitch, epi = B.epi;
       FrontState st;
 #pragma unroll
       for (int a = 0; a < kFK + 1; ++a)
@@ -1090,7 +1098,7 @@ __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(
           const bool rin = (unsigned)c < (unsigned)ny;
 #pragma unroll
           for (int e = 0; e < kFC; ++e) {
-            if (rin && cin[e] && B.v) wn.v[e] = (float)__ldg(B.v + gx0 + e + (int64_t)nx * c);
+            if (rin && cin[e] && vv) wn.v[e] = (float)__ldg(vv + gx0 + e + (int64_t)nx * c);
             an.v[e] = w0 * wn.v[e];
           }
         } else {
@@ -1115,22 +1123,22 @@ __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(
           const FV a = front_acc(st);
           if (!LAST) {
             // rows are padded to a multiple of 4 floats: a group's columns past nx are padding
-            const int64_t gi = gx0 + (int64_t)B.pitch * y;
-            fv_store(B.w[2 * qo + 1] + gi, o);
-            fv_store(B.w[2 * qo] + gi, pv);
-            fv_store(B.acc + gi, a);
+            const int64_t gi = gx0 + (int64_t)pitch * y;
+            fv_store(wout1 + gi, o);
+            fv_store(wout0 + gi, pv);
+            fv_store(accp + gi, a);
           } else {
             const int64_t gi = gx0 + (int64_t)nx * y;
 #pragma unroll
             for (int e = 0; e < kFC; ++e) {
               if (gx0 + e >= nx) break;
-              if (B.epi == 0) {
-                B.out[gi + e] = (double)a.v[e];
+              if (epi == 0) {
+                outp[gi + e] = (double)a.v[e];
               } else {
-                const double vi = __ldg(B.v + gi + e);
+                const double vi = __ldg(vv + gi + e);
                 const double ov = vi - (double)a.v[e];
-                B.out[gi + e] = ov;
-                part = fma(B.mw ? vi * __ldg(B.mw + gi + e) : vi, ov, part);
+                outp[gi + e] = ov;
+                part = fma(mwp ? vi * __ldg(mwp + gi + e) : vi, ov, part);
               }
             }
           }
@@ -1174,6 +1182,274 @@ __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(
       mbar_wait(&s_bar[warp][1], parity[1], kMbarPolls);
     }
     __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ 2-D, double-float, wavefront
+// The double-float residual wave solves of the FP64 correction (2-D, second order, c = 1; forced
+// or not) in the wavefront form of k_batch_front: a work item is a strip of 64 columns (56 output
+// columns, KD = 4 on each side halo) and SD rows, ONE WARP advances it KD time levels in a single
+// pass down the rows with the levels' rows in register rings; lane l holds columns 2l, 2l + 1 as
+// hi/lo pairs, x neighbours of its outer columns by shuffles.  Input rows (W^n, W^{n-1}, the
+// filter sums; W^0 = v in the first sweep) and the forcing rows are read straight from global
+// memory one clock ahead; the forcing of the rows in flight is kept in a register ring.  No
+// shared memory and no block-wide barrier; a strip of sweep j waits only for its problem's sweep
+// j - 1 (per-problem completion counters).  The updates are the double-float operations of
+// k_batch_block2d_df in the same order (bitwise equal results):
+//   Taylor start  W^1 = W^0 + (dt^2 / 2) (sum_m ih2_m ((W_- + W_+) - 2 W^0) - f)
+//   step          df_leapfrog: b W^n - W^{n-1} + a_x (W_l + W_r) + a_y (W_d + W_u) - fph_n f
+//   filter        acc = w_0 W^0, then df_fma_acc(acc, w_{n+1}, W^{n+1})
+constexpr int kDK = 4;                 // time levels per sweep
+constexpr int kDTW = 64 - 2 * kDK;     // output columns of a strip (56)
+constexpr int kDS = 128;               // output rows of a work item
+constexpr int kDWarps = 4;             // warps per CTA
+
+struct DfFront {         // the registers of one lane (two columns)
+  dfl L[kDK + 1][3][2];  // level t - 1 at index t: L[0] = W^{n-1}, L[1] = W^n, L[t + 1] = level t
+  dfl A[kDK + 1][2];     // filter sums of the rows in flight: A[t] is row c - t at clock c
+  dfl F[kDK + 1][2];     // forcing of the rows in flight: F[t] is row c - t
+};
+
+__device__ __forceinline__ dfl df_shfl_up(dfl a) {
+  return {__shfl_up_sync(0xffffffffu, a.hi, 1), __shfl_up_sync(0xffffffffu, a.lo, 1)};
+}
+__device__ __forceinline__ dfl df_shfl_down(dfl a) {
+  return {__shfl_down_sync(0xffffffffu, a.hi, 1), __shfl_down_sync(0xffffffffu, a.lo, 1)};
+}
+
+template <int PH, bool FIRST, bool FORCED>
+__device__ __forceinline__ void dfront_clock(DfFront& st, int c, const dfl* wn, const dfl* wp, const dfl* an,
+                                             const dfl* fr, const dfl* wt, const dfl* fph, const dfl* coef,
+                                             dfl b, dfl ih2x, dfl ih2y, dfl hdt2, const bool* cin, int ny, dfl* o,
+                                             dfl* pv) {
+  constexpr int r3 = PH % 3;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    st.L[0][r3][e] = wp[e];
+    st.L[1][r3][e] = wn[e];
+    st.A[0][e] = an[e];
+    if (FORCED) st.F[0][e] = fr[e];
+  }
+#pragma unroll
+  for (int t = 1; t <= kDK; ++t) {
+    const int y = c - t;
+    const int im = (PH - t - 1 + 30) % 3, i0 = (PH - t + 30) % 3, ip = (PH - t + 1 + 30) % 3;
+    const dfl* up = st.L[t][im];
+    const dfl* mid = st.L[t][i0];
+    const dfl* dn = st.L[t][ip];
+    const dfl l = df_shfl_up(mid[1]);
+    const dfl r = df_shfl_down(mid[0]);
+    const bool rin = (unsigned)y < (unsigned)ny;
+    dfl n[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const dfl xl = e == 0 ? l : mid[0];
+      const dfl xr = e == 1 ? r : mid[1];
+      if (FIRST && t == 1) {   // Taylor start
+        const dfl sx = df_add(xl, xr);
+        const dfl sy = df_add(up[e], dn[e]);
+        const dfl c2x = {2.0f * mid[e].hi, 2.0f * mid[e].lo};
+        dfl Lp = df_add(df_zero(), df_mul(ih2x, df_sub(sx, c2x)));
+        Lp = df_add(Lp, df_mul(ih2y, df_sub(sy, c2x)));
+        if (FORCED) Lp = df_sub(Lp, st.F[t][e]);
+        n[e] = df_add(mid[e], df_mul(hdt2, Lp));
+      } else {
+        const dfs sm[2] = {df_pair_sum(xl, xr), df_pair_sum(up[e], dn[e])};
+        n[e] = df_leapfrog<2, FORCED>(b, mid[e], st.L[t - 1][i0][e], coef, sm, fph[t - 1],
+                                      FORCED ? st.F[t][e] : df_zero());
+      }
+      if (!(rin && cin[e])) n[e] = df_zero();
+      st.A[t][e] = df_fma_acc(st.A[t][e], wt[t - 1], n[e]);
+    }
+    if (t < kDK) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) st.L[t + 1][i0][e] = n[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        o[e] = n[e];
+        pv[e] = st.L[kDK][i0][e];
+      }
+    }
+  }
+}
+
+// end of a clock: the rows in flight move on by one
+template <bool FORCED>
+__device__ __forceinline__ void dfront_shift(DfFront& st) {
+#pragma unroll
+  for (int t = kDK; t >= 1; --t)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      st.A[t][e] = st.A[t - 1][e];
+      if (FORCED) st.F[t][e] = st.F[t - 1][e];
+    }
+}
+
+template <bool FORCED>
+__global__ void __launch_bounds__(kDWarps * 32, 2) k_batch_front_df(const BTile<dfl>* __restrict__ P,
+                                                                    const int* __restrict__ nact, int J,
+                                                                    const int64_t* __restrict__ joff,
+                                                                    unsigned* pcnt, const dfl* __restrict__ wtab,
+                                                                    const dfl* __restrict__ ptab, int* err) {
+  __shared__ int64_t s_tile0[kBatchMaxProblems + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int np = nact[0];
+  for (int p = threadIdx.x; p <= np; p += blockDim.x)
+    s_tile0[p] = p < np ? P[p].tile0 : P[np - 1].tile0 + P[np - 1].ntiles;
+  __syncthreads();
+  const int64_t G = (int64_t)gridDim.x * kDWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kDWarps + warp;
+  const int64_t nitems = joff[J];
+  int j = 0, p = 0;
+  for (int64_t it = gw; it < nitems; it += G) {
+    while (joff[j + 1] <= it) {
+      ++j;
+      p = 0;
+    }
+    const int64_t item = it - joff[j];
+    while (s_tile0[p + 1] <= item) ++p;
+    const int qi = (j + 1) & 1, qo = j & 1;
+    const BTile<dfl>& B = P[p];
+    if (B.halt && *B.halt != 0.0) continue;
+    const int t = (int)(item - B.tile0);
+    const int sx = t % B.tiles_x, sy = t / B.tiles_x;
+    const int nx = B.nx, ny = B.ny;
+    const int x0 = sx * kDTW - kDK;
+    const int Y0 = sy * kDS, Y1 = min(Y0 + kDS, ny);
+    const int c0 = Y0 - kDK, c1 = Y1 - 1 + kDK;   // clocks (input rows) of this item
+    const int n0 = j * kDK;
+    const int kk = min(kDK, B.nt - n0);
+    const bool first = j == 0, last = n0 + kk == B.nt;
+    if (!first) {   // every strip of this problem's previous sweep is done
+      bool ok = true;
+      if (lane == 0) ok = wait_count(pcnt + p, (unsigned)(j * B.ntiles), err);
+      if (!__shfl_sync(0xffffffffu, ok, 0)) return;
+    }
+    dfl wt[kDK], fph[kDK];
+#pragma unroll
+    for (int s = 0; s < kDK; ++s) {   // the tables carry kDK zero entries past every problem's nt
+      wt[s] = wtab[B.wofs + n0 + 1 + s];
+      fph[s] = FORCED ? ptab[B.wofs + n0 + s] : df_zero();
+    }
+    const dfl w0 = first ? wtab[B.wofs] : df_zero();
+    const int gx0 = x0 + 2 * lane;
+    const bool cin[2] = {gx0 >= 0 && gx0 < nx, gx0 + 1 >= 0 && gx0 + 1 < nx};
+    const bool outc = 2 * lane >= kDK && 2 * lane < 64 - kDK && gx0 < nx;   // output columns
+    const dfl coef[2] = {B.ax, B.ay};
+    const dfl bb = B.b, ih2x = B.ih2x, ih2y = B.ih2y, hdt2 = {0.5f * B.dt2.hi, 0.5f * B.dt2.lo};
+    // the descriptor's fields in registers (the stores below could otherwise alias it)
+    const dfl* const wcur = B.w[2 * qi + 1];
+    const dfl* const wprv = B.w[2 * qi];
+    dfl* const wout1 = B.w[2 * qo + 1];
+    dfl* const wout0 = B.w[2 * qo];
+    dfl* const accp = B.acc;
+    const double* const vv = B.v;
+    const double* const fv = B.f;
+    const double* const mwp = B.mw;
+    double* const outp = B.out;
+    const int epi = B.epi;
+    DfFront st;
+#pragma unroll
+    for (int a = 0; a < kDK + 1; ++a)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) st.L[a][r][e] = df_zero();
+        st.A[a][e] = df_zero();
+        st.F[a][e] = df_zero();
+      }
+    // input row c (its filter sum is read only at the output columns, the others are discarded)
+    auto fetch = [&](int c, dfl* wn, dfl* wp, dfl* an, dfl* fr) {
+      const bool rin = (unsigned)c < (unsigned)ny;
+      const int64_t gi = gx0 + (int64_t)nx * c;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const bool in = rin && cin[e];
+        if (first) {
+          wn[e] = (in && vv) ? df_from(__ldg(vv + gi + e)) : df_zero();
+          wp[e] = df_zero();
+          an[e] = df_mul(w0, wn[e]);
+        } else {   // written by other warps in the previous sweep: coherent loads
+          if (in) {
+            const float2 a = __ldcg(reinterpret_cast<const float2*>(wcur + gi + e));
+            const float2 b2 = __ldcg(reinterpret_cast<const float2*>(wprv + gi + e));
+            wn[e] = dfl{a.x, a.y};
+            wp[e] = dfl{b2.x, b2.y};
+          } else {
+            wn[e] = wp[e] = df_zero();
+          }
+          if (in && outc) {
+            const float2 a = __ldcg(reinterpret_cast<const float2*>(accp + gi + e));
+            an[e] = dfl{a.x, a.y};
+          } else {
+            an[e] = df_zero();
+          }
+        }
+        fr[e] = (FORCED && in && fv) ? df_from(__ldg(fv + gi + e)) : df_zero();
+      }
+    };
+    dfl nwn[2], nwp[2], nan[2], nfr[2];
+    fetch(c0, nwn, nwp, nan, nfr);
+    double part = 0.0;
+    int c = c0;
+    auto clock = [&](auto ph, auto fst, auto lst) {
+      constexpr int PH = decltype(ph)::value;
+      constexpr bool FIRST = decltype(fst)::value, LAST = decltype(lst)::value;
+      const dfl wn[2] = {nwn[0], nwn[1]}, wp[2] = {nwp[0], nwp[1]};
+      const dfl an[2] = {nan[0], nan[1]}, fr[2] = {nfr[0], nfr[1]};
+      if (c + 1 <= c1) fetch(c + 1, nwn, nwp, nan, nfr);   // one clock ahead
+      dfl o[2], pv[2];
+      dfront_clock<PH, FIRST, FORCED>(st, c, wn, wp, an, fr, wt, fph, coef, bb, ih2x, ih2y, hdt2, cin, ny, o, pv);
+      const int y = c - kDK;
+      if (y >= Y0 && y < Y1 && outc) {
+        const int64_t gi = gx0 + (int64_t)nx * y;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (gx0 + e >= nx) break;
+          const dfl a = st.A[kDK][e];
+          if (!LAST) {
+            wout1[gi + e] = o[e];
+            wout0[gi + e] = pv[e];
+            accp[gi + e] = a;
+          } else if (epi == 0) {
+            outp[gi + e] = df_to(a);
+          } else {
+            const double vi = __ldg(vv + gi + e);
+            const double ov = vi - df_to(a);
+            outp[gi + e] = ov;
+            part = fma(mwp ? vi * __ldg(mwp + gi + e) : vi, ov, part);
+          }
+        }
+      }
+      dfront_shift<FORCED>(st);
+      ++c;
+    };
+    auto run = [&](auto fst, auto lst) {
+      while (c <= c1) {
+        clock(std::integral_constant<int, 0>(), fst, lst);
+        if (c > c1) break;
+        clock(std::integral_constant<int, 1>(), fst, lst);
+        if (c > c1) break;
+        clock(std::integral_constant<int, 2>(), fst, lst);
+      }
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    if (first) {
+      if (last) run(T_(), T_());
+      else run(T_(), F_());
+    } else {
+      if (last) run(F_(), T_());
+      else run(F_(), F_());
+    }
+    if (last && epi == 1) {
+      part = warp_sum(part);
+      if (lane == 0) B.partials[t] = part;
+    }
+    __threadfence();   // publish this strip's stores, then count it
+    __syncwarp();
+    if (lane == 0) atomicAdd(pcnt + p, 1u);
   }
 }
 
@@ -1743,6 +2019,114 @@ constexpr int kBDfK = 4;   // sub-steps per sweep of the double-float roles
 // double-float pairs in the same 8-byte buffers, 2-D second order with c = 1 only).
 // Problems are ordered by their number of sweeps (descending), so the active problems of sweep j
 // are a prefix.
+// ------------------------------------------------------------------ double-float wavefront role (host)
+template <bool FORCED>
+static cudaError_t launch_front_df(cudaStream_t st, const Wave& w, unsigned* bar, int* err) {
+  (void)bar;   // no grid barrier: per-problem completion counters, zeroed before every launch
+  const BTile<dfl>* P = (const BTile<dfl>*)w.desc;
+  const dfl* wt = (const dfl*)w.wtab;
+  const dfl* ph = (const dfl*)w.ptab;
+  int J = w.J;
+  const int* na = w.nact;
+  const int64_t* jo = w.joff;
+  unsigned* pc = w.pcnt;
+  const cudaError_t e = cudaMemsetAsync(w.pcnt, 0, w.np * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&P, (void*)&na, (void*)&J, (void*)&jo, (void*)&pc, (void*)&wt, (void*)&ph, (void*)&err};
+  return cudaLaunchCooperativeKernel((const void*)k_batch_front_df<FORCED>, dim3(w.nblocks), dim3(kDWarps * 32), args,
+                                     0, st);
+}
+
+// descriptor tables of the double-float wavefront role (strips of 64 columns x kDS rows)
+static whv_status make_wave_front_df(BatchCtx& c, const RoleIO& io, bool forced, Wave* out) {
+  const int np = c.np;
+  const int K = kDK;
+  Wave w;
+  w.K = K;
+  std::vector<int> order(np), nsw(np);
+  for (int p = 0; p < np; ++p) nsw[p] = (c.tgs[p].nt + K - 1) / K;
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nsw[a] > nsw[b]; });
+  w.J = nsw[order[0]];
+  std::vector<dfl> wtab, ptab;
+  std::vector<BFin> fin(np);
+  std::vector<BTile<dfl>> d(np);
+  int64_t tile0 = 0;
+  for (int k = 0; k < np; ++k) {
+    const int p = order[k];
+    whv_grid g = c.grids[p];
+    const TimeGridH& tg = c.tgs[p];
+    void* const* bufs = g->wbuf64;
+    if (!g->acc64 || !bufs[0]) return fail(c.g0, WHV_ERR_INVALID, "batched: stepping buffers missing");
+    const int wofs = (int)wtab.size();
+    for (int n = 0; n <= tg.nt; ++n) {
+      wtab.push_back(df_from(tg.weight[n]));
+      ptab.push_back(df_from(tg.dt * tg.dt * tg.phase[n]));   // the forcing factor dt^2 cos(omega_hat t^n)
+    }
+    for (int n = 0; n < K; ++n) {   // the last sweep may read past the problem's nt
+      wtab.push_back(dfl{0.0f, 0.0f});
+      ptab.push_back(dfl{0.0f, 0.0f});
+    }
+    const double h2x = g->h[0] * g->h[0], h2y = g->h[1] * g->h[1];
+    BTile<dfl> B{};
+    for (int m = 0; m < 4; ++m) B.w[m] = (dfl*)bufs[m];
+    B.acc = (dfl*)g->acc64;
+    B.v = io.v[p]; B.f = io.f[p]; B.out = io.out[p];
+    B.c2 = nullptr; B.mw = g->mw; B.partials = chan(g, CH_STEP);
+    B.halt = io.halt ? g->scal + S_HALT : nullptr;
+    B.nx = g->n[0]; B.ny = g->n[1]; B.nt = tg.nt;
+    B.tiles_x = (g->n[0] + kDTW - 1) / kDTW;
+    B.ntiles = B.tiles_x * ((g->n[1] + kDS - 1) / kDS);
+    B.epi = io.epi; B.wofs = wofs;
+    B.ih2x = df_from(1.0 / h2x);
+    B.ih2y = df_from(1.0 / h2y);
+    B.dt2 = df_from(tg.dt * tg.dt);
+    const double ax = tg.dt * tg.dt / h2x, ay = tg.dt * tg.dt / h2y;
+    B.ax = df_from(ax); B.ay = df_from(ay); B.b = df_from(2.0 - 2.0 * (ax + ay));
+    B.tile0 = tile0;
+    if (io.epi == 1 && B.ntiles > chan_cap(g, CH_STEP))
+      return fail(c.g0, WHV_ERR_INVALID, "batched: grid too large for its reduction channel");
+    fin[k] = BFin{chan(g, CH_STEP), io.halt ? g->scal + S_HALT : nullptr, g->scal, B.ntiles};
+    d[k] = B;
+    tile0 += B.ntiles;
+  }
+  std::vector<int> nact(w.J);
+  for (int j = 0; j < w.J; ++j) {
+    int a = 0;
+    while (a < np && nsw[order[a]] > j) ++a;
+    nact[j] = a;
+  }
+  std::vector<int64_t> joff(w.J + 1, 0);   // strips of sweep j: those of its active problems
+  for (int j = 0; j < w.J; ++j) joff[j + 1] = joff[j] + (nact[j] < np ? d[nact[j]].tile0 : tile0);
+  B_CUDA(c.g0, c.alloc(&w.desc, np * sizeof(BTile<dfl>)));
+  B_CUDA(c.g0, c.alloc(&w.nact, w.J * sizeof(int)));
+  B_CUDA(c.g0, c.alloc(&w.joff, (w.J + 1) * sizeof(int64_t)));
+  B_CUDA(c.g0, c.alloc(&w.pcnt, np * sizeof(unsigned)));
+  B_CUDA(c.g0, c.alloc(&w.wtab, wtab.size() * sizeof(dfl)));
+  B_CUDA(c.g0, c.alloc(&w.ptab, ptab.size() * sizeof(dfl)));
+  B_CUDA(c.g0, c.alloc(&w.fin, np * sizeof(BFin)));
+  B_CUDA(c.g0, cudaMemcpy(w.desc, d.data(), np * sizeof(BTile<dfl>), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.nact, nact.data(), w.J * sizeof(int), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.joff, joff.data(), (w.J + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.wtab, wtab.data(), wtab.size() * sizeof(dfl), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.ptab, ptab.data(), ptab.size() * sizeof(dfl), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.fin, fin.data(), np * sizeof(BFin), cudaMemcpyHostToDevice));
+  w.np = np;
+  int per_sm = 0;
+  if (forced) {
+    w.launch = &launch_front_df<true>;
+    B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_front_df<true>, kDWarps * 32, 0));
+  } else {
+    w.launch = &launch_front_df<false>;
+    B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_front_df<false>, kDWarps * 32, 0));
+  }
+  if (per_sm < 1) return fail(c.g0, WHV_ERR_INVALID, "batched: kernel cannot be resident on an SM");
+  w.smem = 0;
+  w.nblocks = (int)std::min<int64_t>((int64_t)per_sm * c.sms, std::max<int64_t>((tile0 + kDWarps - 1) / kDWarps, 1));
+  *out = w;
+  return WHV_OK;
+}
+
 template <typename T, int DIM, int ORDER, bool VARC>
 static whv_status make_wave(BatchCtx& c, const RoleIO& io, Wave* out) {
   const int np = c.np;
@@ -1757,6 +2141,8 @@ static whv_status make_wave(BatchCtx& c, const RoleIO& io, Wave* out) {
   if constexpr (std::is_same<T, float>::value && DIM == 2 && ORDER == 2 && !VARC)
     if (front_role(w.K, forced)) return make_wave_front(c, io, out);
     else if (tma_role(w.K, forced)) return make_wave_tma(c, io, w.K, out);
+  if constexpr (DF)
+    if (tma_env() >= 3) return make_wave_front_df(c, io, forced, out);
   std::vector<int> order(np), nsw(np);
   for (int p = 0; p < np; ++p) nsw[p] = (c.tgs[p].nt + w.K - 1) / w.K;
   std::iota(order.begin(), order.end(), 0);

@@ -383,8 +383,8 @@ def run_reference_c2(args):
 KERNEL_SOURCES = {
     "k_block2d": ("stencil_blocked.cu", "quad2d.cuh", "whv_device.cuh"),
     "k_step3d": (("stencil.cu", "k_step3d"), "stencil_ops.cuh", "whv_device.cuh"),
-    "k_step3d2": (("stencil.cu", "k_step3d2"), ("stencil.cu", "ld2"), ("stencil.cu", "ld2rw"), ("stencil.cu", "st2"),
-                  "stencil_ops.cuh", "whv_device.cuh"),
+    "k_step3d2": (("stencil.cu", "k_step3d2"), ("stencil.cu", "s3d2_plane"), "tma.cuh", "stencil_ops.cuh",
+                  "whv_device.cuh"),
     "k_batch_block2d": (("batch.cu", "k_batch_block2d"), "quad2d.cuh", "whv_device.cuh"),
     "k_batch_tma": (("batch.cu", "k_batch_tma"), ("batch.cu", "tma_issue"), ("batch.cu", "tma_live_item"),
                     "quad2d.cuh", "tma.cuh", "whv_device.cuh"),

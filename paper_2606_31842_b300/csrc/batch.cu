@@ -1728,19 +1728,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // the driver's tensor-map encoder, fetched once through the runtime (no link to libcuda)
-static EncodeTiledFn encode_tiled() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
-  return fn;
-}
+static EncodeTiledFn encode_tiled() { return (EncodeTiledFn)tensor_map_encoder(); }
 
 // The FP32 f = 0 roles of 2-D second-order c = 1 batches: k = 8 runs the wavefront kernel
 // (k_batch_front), k = 4 and 12 the TMA-fed staged kernel with two rows of cells per thread, other

@@ -133,6 +133,21 @@ __global__ void k_speed_setup(const double* __restrict__ c2in, double* __restric
   }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver library)
+void* tensor_map_encoder() {
+  static void* fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = p;
+  }
+  return fn;
+}
+
 }  // namespace whv
 
 using namespace whv;
@@ -155,7 +170,7 @@ static void free_all(whv_grid g) {
                   g->t, g->fd, g->krylov, g->small, g->small2, g->partials, g->counters, g->scal,
                   g->basis.d_coef, g->basis.AW, g->basis.Einv, g->basis.QAW, g->basis.cU, g->basis.cV,
                   g->basis.cs, g->basis.cT, g->basis.cc, g->basis.cR, g->basis.coff, g->basis.cowner, g->wbuf64[0], g->wbuf64[1], g->wbuf64[2],
-                  g->wbuf64[3], g->acc64, g->tw[0], g->tw[1], g->tw[2], g->tw[3], g->tacc, g->xo, g->ro, g->bo, g->wtab_small, g->face64[0], g->face64[1],
+                  g->wbuf64[3], g->acc64, g->tw[0], g->tw[1], g->tw[2], g->tw[3], g->tacc, g->pw3[0], g->pw3[1], g->pw3[2], g->pw3[3], g->pacc3, g->maps3, g->xo, g->ro, g->bo, g->wtab_small, g->face64[0], g->face64[1],
                   g->face64[2], g->face32[0], g->face32[1], g->face32[2]};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -19,8 +19,11 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda.h>   // CUtensorMap and its encoding enums (the encoder is fetched through the runtime)
+
 #include "df64.cuh"
 #include "stencil_ops.cuh"
+#include "tma.cuh"
 #include "whv_device.cuh"
 #include "whv_internal.cuh"
 
@@ -365,235 +368,211 @@ __global__ void __launch_bounds__(256) k_step3d(const T* __restrict__ wc, T* __r
 // into the other buffer pair), halving the state traffic of single steps.  A CTA of 17 warps
 // owns a tile of 64 x 32 nodes in x, y and marches through planes z; lane l of warp row w holds
 // the two adjacent columns x0 + 2l, x0 + 2l + 1 of the two region rows 2w, 2w + 1 (region row r
-// is y = y0 - 1 + r: rows 1 .. 32 are the tile, 0 and 33 its ring), 8-byte loads and stores where
-// the rows allow it.  At plane z, step A computes W^{n+1}(z) on the tile and its one-node ring
-// from W^n at z - 1, z, z + 1 (plane z staged in shared memory with the two columns and one row
-// beyond the ring, the z neighbours in registers); lanes 0 and 31 also compute the ring columns
-// x0 - 1 and x0 + 64.  Step B then computes W^{n+2}(z - 1) on the tile from W^{n+1} at z - 2,
-// z - 1 (registers and the stage written at the previous plane) and z.  The grid is persistent:
-// the (tile column, plane) pairs of the whole grid are split into equal contiguous ranges, one
-// per CTA; a range covering parts of two tile columns marches each part (one extra plane of
-// step A at its start).  The planes are processed four at a time with the register rings
-// (W^n at four planes, W^{n+1} at four, the rest at two) indexed by the plane's phase, so that
-// no value is moved between registers.  Nodes outside the domain are 0 (the Dirichlet values).
-// Same operations in the same order as two k_step3d steps:
+// is y = y0 - 1 + r: rows 1 .. 32 are the tile, 0 and 33 its ring).  The state lives in
+// row-padded ("pitched") FP32 buffers so that every plane of W^n (72 x 36 nodes: the tile, its
+// ring, the column beyond the ring and one row beyond it), of W^{n-1} (same box) and of the filter
+// sums (the tile) is copied into shared memory by the copy engine (TMA, one elected thread, an
+// mbarrier per stage with a bounded wait), two or three planes ahead: W^n in a ring of five
+// stages, W^{n-1} and the filter sums in rings of three.  At plane z, step A computes W^{n+1}(z)
+// on the tile and its one-node ring (lanes 0 and 31 also the ring columns x0 - 1 and x0 + 64)
+// into a double-buffered stage; step B computes W^{n+2}(z - 1) on the tile from W^{n+1} at z - 2,
+// z - 1 (registers and the stage written at the previous plane) and z, and writes W^{n+1},
+// W^{n+2} and the filter sum of plane z - 1.  One barrier per plane.  The grid is persistent: the
+// (tile column, plane) pairs are split into equal contiguous ranges, one per CTA, ordered slab by
+// slab (slabs of one range's thickness, column by column inside a slab) so that neighbouring tile
+// columns pass the same planes at the same time and their halo reads meet in L2.  Nodes outside
+// the domain are 0 (copies outside the tensor read as zero).  Same operations in the same order
+// as two k_step3d steps:
 //   W^{n+1} = fma(az, zm + zp, fma(ay, ym + yp, fma(ax, xm + xp, fma(b, W^n, -W^{n-1}))))
 //   acc = fma(w_{n+2}, W^{n+2}, fma(w_{n+1}, W^{n+1}, acc))
 // Global traffic per node and 2 steps: read W^{n-1}, W^n, acc, write W^{n+1}, W^{n+2}, acc
-// (24 B instead of 40 B), plus the ring re-reads.  V2: rows of an even number of nodes, whose
-// column pairs are 8-byte aligned (otherwise two 4-byte accesses).  A plane holds < 2^31 nodes.
+// (24 B instead of 40 B), plus the ring re-reads.  If a copy does not arrive within the bounded
+// wait, the CTA raises the breakdown flag S_FLAG of the grid and leaves (after a bounded drain).
 constexpr int k3W = 64;               // tile columns (two per lane)
 constexpr int k3H = 32;               // tile rows
 constexpr int k3WR = k3H / 2 + 1;     // warp rows (two region rows each: tile + one ring row per side)
-constexpr int k3PC = k3W + 4;         // staged columns x0 - 2 .. x0 + 65 (column c is x0 - 2 + c)
+constexpr int k3BX = k3W + 8;         // staged columns x0 - 4 .. x0 + 67 (column c is x0 - 4 + c)
+constexpr int k3BY = k3H + 4;         // staged rows y0 - 2 .. y0 + 33 (row pr is region row pr - 1)
+constexpr int k3NW = 5, k3NP = 3;     // stages of W^n; of W^{n-1} and of the filter sums
+constexpr int k3SPlane = k3BX * k3BY;                       // floats of a W^n / W^{n-1} stage
+constexpr int k3APlane = k3W * k3H;                         // floats of a filter-sum stage
+constexpr int k3QPlane = k3BX * (k3H + 2);                  // floats of a W^{n+1} stage (rows 0 .. 33)
+constexpr int k3Smem = 4 * ((k3NW + k3NP) * k3SPlane + k3NP * k3APlane + 2 * k3QPlane) + 128;
 
-template <bool V2>
-__device__ __forceinline__ float2 ld2(const float* __restrict__ p, bool in0, bool in1) {
-  float2 r = make_float2(0.f, 0.f);
-  if (V2) {
-    if (in0) r = __ldg(reinterpret_cast<const float2*>(p));
-  } else {
-    if (in0) r.x = __ldg(p);
-    if (in1) r.y = __ldg(p + 1);
-  }
-  return r;
-}
-template <bool V2>
-__device__ __forceinline__ float2 ld2rw(const float* p, bool in0, bool in1) {
-  // the filter sums are read and written by the same kernel: no read-only path
-  float2 r = make_float2(0.f, 0.f);
-  if (V2) {
-    if (in0) r = *reinterpret_cast<const float2*>(p);
-  } else {
-    if (in0) r.x = p[0];
-    if (in1) r.y = p[1];
-  }
-  return r;
-}
-template <bool V2>
-__device__ __forceinline__ void st2(float* p, float2 v, bool in0, bool in1) {
-  if (V2) {
-    if (in0) *reinterpret_cast<float2*>(p) = v;
-  } else {
-    if (in0) p[0] = v.x;
-    if (in1) p[1] = v.y;
-  }
-}
-
-struct S3d2 {            // registers of one thread, rings indexed by the plane's phase k = z - zb
-  float2 c[4][2];        // W^n of the own nodes: c[(k + d) & 3] is plane z + d (d = -1 .. 2)
-  float r[4][2];         // W^n of the ring node, likewise
-  float2 q[4][2];        // W^{n+1} of the own nodes: q[k & 3] is plane z
-  float2 wp[2][2];       // W^{n-1} of the own nodes: wp[k & 1] is plane z
-  float wr[2][2];        // W^{n-1} of the ring node
-  float2 ac[2][2];       // filter sums of the own nodes: ac[k & 1] is plane z
-  float rb[2][2];        // W^n of the column beyond the ring: rb[k & 1] is plane z
-  float2 xr[2];          // W^n of the extra staged row
-  float2 aA[2][2];       // filter sums after step n + 1: aA[k & 1] is plane z
+struct Maps3d2 {         // tensor maps of the pitched buffers (one per buffer)
+  CUtensorMap w[4];      // 72 x 36 x 1 boxes of the two (W^{n-1}, W^n) pairs
+  CUtensorMap acc;       // 64 x 32 x 1 boxes of the filter sums
 };
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+constexpr uint32_t kMbarPolls3 = 1u << 22;   // bound on the polls of one stage's mbarrier
+__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
 struct Geo3d2 {          // per-thread geometry of the current range
-  const float *gc, *gp;  // W^n, W^{n-1}
-  float *op, *oc, *acc;
+  float *op, *oc, *acc;  // pitched outputs
   const double *v, *mw;
   double* out;
-  int64_t plane;
-  int nz, zs, ze, zl1, zl2;          // zl1 / zl2: last plane a prefetch of z + 1 / z + 2 may read
-  int co[2], r1o[2], r2o[2], xo;     // in-plane offsets: own pair, ring node, column beyond, extra row
-  bool own0[2], own1[2], trow[2], ry[2], rt1[2], rt2[2], xrin, xin0, xin1, edge, xrow;
-  int pc, pr1, pr2, sx;              // staged columns (own, ring, beyond), staged extra row
+  int64_t ppitch, plane;               // pitched plane; unpadded plane (FP64 epilogue)
+  int nx, ny, nz, pitch, zs, ze, x0, y0;
+  int co[2], uo[2];                    // own pair: pitched / unpadded in-plane offsets
+  bool own0[2], own1[2], trow[2], rt1[2], xin0, xin1, edge;
+  int pc, pr1;                         // staged columns of the own pair and of the ring node
 };
 
-template <int PH, int KIND, bool V2>
-__device__ __forceinline__ void s3d2_plane(S3d2& S, const Geo3d2& G, int z, int wr, float (*P)[k3H + 4][k3PC],
-                                           float (*Q)[k3H + 2][k3PC], const StepCoef<float>& cf, float w2,
-                                           double& part) {
-  constexpr int b = PH & 1;
-  constexpr int M = (PH + 3) & 3, C0 = PH, CP = (PH + 1) & 3, CN = (PH + 2) & 3;   // z-1, z, z+1, z+2
-  constexpr int Q0 = PH, Q1 = (PH + 3) & 3, Q2 = (PH + 2) & 3;                     // W^{n+1}: z, z-1, z-2
-  constexpr int T0 = PH & 1, T1 = (PH + 1) & 1;                                     // plane z, z + 1
-  const int64_t zo = (int64_t)z * G.plane;
-  // stage W^n(z): own nodes, the ring column and the column beyond it, the extra row
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int sr = 2 * wr + i + 1;
-    *reinterpret_cast<float2*>(&P[b][sr][G.pc]) = S.c[C0][i];
-    if (G.edge) {
-      P[b][sr][G.pr1] = S.r[C0][i];
-      P[b][sr][G.pr2] = S.rb[T0][i];
-    }
-  }
-  if (G.xrow) *reinterpret_cast<float2*>(&P[b][G.sx][G.pc]) = S.xr[T0];
-  // prefetch W^n(z + 2) (own, ring), W^n(z + 1) (beyond the ring, extra row), W^{n-1}(z + 1), acc(z + 1)
-  const bool z1 = z + 1 <= G.zl1, z2 = z + 2 <= G.zl2, za = z + 1 < G.ze;
-  const float* g2 = G.gc + zo + 2 * G.plane;
-  const float* g1 = G.gc + zo + G.plane;
-  const float* p1 = G.gp + zo + G.plane;
-  const float* a1p = G.acc + zo + G.plane;
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    S.c[CN][i] = ld2<V2>(g2 + G.co[i], z2 && G.own0[i], z2 && G.own1[i]);
-    S.wp[T1][i] = ld2<V2>(p1 + G.co[i], z1 && G.own0[i], z1 && G.own1[i]);
-    S.ac[T1][i] = ld2rw<V2>(a1p + G.co[i], za && G.trow[i] && G.xin0, za && G.trow[i] && G.xin1);
-    S.r[CN][i] = (z2 && G.ry[i]) ? __ldg(g2 + G.r1o[i]) : 0.f;
-    S.wr[T1][i] = (z1 && G.rt1[i]) ? __ldg(p1 + G.r1o[i]) : 0.f;
-    S.rb[T1][i] = (z1 && G.rt2[i]) ? __ldg(g1 + G.r2o[i]) : 0.f;
-  }
-  S.xr[T1] = ld2<V2>(g1 + G.xo, z1 && G.xrin && G.xin0, z1 && G.xrin && G.xin1);
-  __syncthreads();
+struct Q3d2 {            // W^{n+1} of the own nodes: q[k & 3] is plane z; filter sums after step n + 1
+  float2 q[4][2];
+};
+
+template <int PH, int KIND>
+__device__ __forceinline__ void s3d2_plane(Q3d2& S, const Geo3d2& G, int z, int wr, const float* SW,
+                                           const float* SP, const float* SA, float* SQ, int kw, int kp,
+                                           const StepCoef<float>& cf, float w2, double& part) {
+  constexpr int Q0 = PH, Q1 = (PH + 3) & 3, Q2 = (PH + 2) & 3;   // W^{n+1}: z, z - 1, z - 2
+  const int kwm = kw == 0 ? k3NW - 1 : kw - 1, kwp = kw + 1 == k3NW ? 0 : kw + 1;
+  const int kpm = kp == 0 ? k3NP - 1 : kp - 1;
+  const float* W0 = SW + kw * k3SPlane;    // W^n(z)
+  const float* Wm = SW + kwm * k3SPlane;   // W^n(z - 1)
+  const float* Wp = SW + kwp * k3SPlane;   // W^n(z + 1)
+  const float* Pp = SP + kp * k3SPlane;    // W^{n-1}(z)
+  float* Qz = SQ + (PH & 1) * k3QPlane;    // W^{n+1}(z)
   const bool zin = (unsigned)z < (unsigned)G.nz;
   // step A: W^{n+1}(z) of the own nodes (region rows 0 .. 33) and of the ring node
+  float2 cm[2];
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const int sr = 2 * wr + i + 1;
-    const float2 c0 = S.c[C0][i], cm = S.c[M][i], cp = S.c[CP][i], wpv = S.wp[T0][i];
-    const float xm = P[b][sr][G.pc - 1], xp = P[b][sr][G.pc + 2];
-    const float2 up = i == 0 ? *reinterpret_cast<const float2*>(&P[b][sr - 1][G.pc]) : S.c[C0][0];
-    const float2 dn = i == 1 ? *reinterpret_cast<const float2*>(&P[b][sr + 1][G.pc]) : S.c[C0][1];
+    const int sr = 2 * wr + i + 1;   // staged row of region row 2 wr + i
+    const int l = sr * k3BX + G.pc;
+    const float2 c0 = lds2(W0 + l), cp = lds2(Wp + l), wpv = lds2(Pp + l);
+    cm[i] = lds2(Wm + l);
+    const float xm = W0[l - 1], xp = W0[l + 2];
+    const float2 up = lds2(W0 + l - k3BX), dn = lds2(W0 + l + k3BX);
     float u0 = fmaf(cf.b, c0.x, -wpv.x);
     u0 = fmaf(cf.a[0], xm + c0.y, u0);
     u0 = fmaf(cf.a[1], up.x + dn.x, u0);
-    u0 = fmaf(cf.a[2], cm.x + cp.x, u0);
+    u0 = fmaf(cf.a[2], cm[i].x + cp.x, u0);
     float u1 = fmaf(cf.b, c0.y, -wpv.y);
     u1 = fmaf(cf.a[0], c0.x + xp, u1);
     u1 = fmaf(cf.a[1], up.y + dn.y, u1);
-    u1 = fmaf(cf.a[2], cm.y + cp.y, u1);
+    u1 = fmaf(cf.a[2], cm[i].y + cp.y, u1);
     S.q[Q0][i] = make_float2((zin && G.own0[i]) ? u0 : 0.f, (zin && G.own1[i]) ? u1 : 0.f);
-    *reinterpret_cast<float2*>(&Q[b][sr - 1][G.pc]) = S.q[Q0][i];
+    *reinterpret_cast<float2*>(Qz + (sr - 1) * k3BX + G.pc) = S.q[Q0][i];
     if (G.edge && G.trow[i]) {
-      float w = fmaf(cf.b, S.r[C0][i], -S.wr[T0][i]);
-      w = fmaf(cf.a[0], P[b][sr][G.pr1 - 1] + P[b][sr][G.pr1 + 1], w);
-      w = fmaf(cf.a[1], P[b][sr - 1][G.pr1] + P[b][sr + 1][G.pr1], w);
-      w = fmaf(cf.a[2], S.r[M][i] + S.r[CP][i], w);
-      Q[b][sr - 1][G.pr1] = (zin && G.rt1[i]) ? w : 0.f;
+      const int lr = sr * k3BX + G.pr1;
+      float w = fmaf(cf.b, W0[lr], -Pp[lr]);
+      w = fmaf(cf.a[0], W0[lr - 1] + W0[lr + 1], w);
+      w = fmaf(cf.a[1], W0[lr - k3BX] + W0[lr + k3BX], w);
+      w = fmaf(cf.a[2], Wm[lr] + Wp[lr], w);
+      Qz[lr - k3BX] = (zin && G.rt1[i]) ? w : 0.f;
     }
   }
-  float2 accN[2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-    accN[i] = make_float2(fmaf(cf.w1, S.q[Q0][i].x, S.ac[T0][i].x), fmaf(cf.w1, S.q[Q0][i].y, S.ac[T0][i].y));
   // step B: W^{n+2}(z - 1) on the tile rows, from Q[(z - 1) & 1]
   if (z > G.zs) {
-    const float(*R)[k3PC] = Q[b ^ 1];
-    const int64_t zm1 = zo - G.plane;
+    const float* R = SQ + ((PH + 1) & 1) * k3QPlane;
+    const float* Az = SA + kpm * k3APlane;   // filter sums of plane z - 1
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       if (!G.trow[i]) continue;
       const int qr = 2 * wr + i;
-      const float2 q1 = S.q[Q1][i], q2 = S.q[Q2][i], a1 = S.q[Q0][i], cm = S.c[M][i];
-      const float xm = R[qr][G.pc - 1], xp = R[qr][G.pc + 2];
-      const float2 up = i == 0 ? *reinterpret_cast<const float2*>(&R[qr - 1][G.pc]) : S.q[Q1][0];
-      const float2 dn = i == 1 ? *reinterpret_cast<const float2*>(&R[qr + 1][G.pc]) : S.q[Q1][1];
-      float u0 = fmaf(cf.b, q1.x, -cm.x);
+      const int l = qr * k3BX + G.pc;
+      const float2 q1 = S.q[Q1][i], q2 = S.q[Q2][i], a1 = S.q[Q0][i];
+      const float xm = R[l - 1], xp = R[l + 2];
+      const float2 up = i == 0 ? lds2(R + l - k3BX) : S.q[Q1][0];
+      const float2 dn = i == 1 ? lds2(R + l + k3BX) : S.q[Q1][1];
+      float u0 = fmaf(cf.b, q1.x, -cm[i].x);
       u0 = fmaf(cf.a[0], xm + q1.y, u0);
       u0 = fmaf(cf.a[1], up.x + dn.x, u0);
       u0 = fmaf(cf.a[2], q2.x + a1.x, u0);
-      float u1 = fmaf(cf.b, q1.y, -cm.y);
+      float u1 = fmaf(cf.b, q1.y, -cm[i].y);
       u1 = fmaf(cf.a[0], q1.x + xp, u1);
       u1 = fmaf(cf.a[1], up.y + dn.y, u1);
       u1 = fmaf(cf.a[2], q2.y + a1.y, u1);
-      const float2 a = make_float2(fmaf(w2, u0, S.aA[T1][i].x), fmaf(w2, u1, S.aA[T1][i].y));
-      const int64_t idx = zm1 + G.co[i];
+      const float2 ap = lds2(Az + (qr - 1) * k3W + 2 * (threadIdx.x & 31));
+      const float2 a = make_float2(fmaf(w2, u0, fmaf(cf.w1, q1.x, ap.x)), fmaf(w2, u1, fmaf(cf.w1, q1.y, ap.y)));
       if (KIND == K_STEP) {
-        st2<V2>(G.op + idx, q1, G.xin0, G.xin1);
-        st2<V2>(G.oc + idx, make_float2(u0, u1), G.xin0, G.xin1);
-        st2<V2>(G.acc + idx, a, G.xin0, G.xin1);
-      } else if (KIND == K_LAST_OUT) {
-        if (G.xin0) G.out[idx] = (double)a.x;
-        if (G.xin1) G.out[idx + 1] = (double)a.y;
-      } else {
+        const int64_t idx = (int64_t)(z - 1) * G.ppitch + G.co[i];
+        // pitched rows hold a multiple of 4 floats: a pair's second column past nx is padding
         if (G.xin0) {
-          const double vi = G.v[idx];
-          const double o = vi - (double)a.x;
-          G.out[idx] = o;
-          part = fma(G.mw ? vi * G.mw[idx] : vi, o, part);
+          *reinterpret_cast<float2*>(G.op + idx) = q1;
+          *reinterpret_cast<float2*>(G.oc + idx) = make_float2(u0, u1);
+          *reinterpret_cast<float2*>(G.acc + idx) = a;
         }
-        if (G.xin1) {
-          const double vi = G.v[idx + 1];
-          const double o = vi - (double)a.y;
-          G.out[idx + 1] = o;
-          part = fma(G.mw ? vi * G.mw[idx + 1] : vi, o, part);
+      } else {
+        const int64_t idx = (int64_t)(z - 1) * G.plane + G.uo[i];
+        if (KIND == K_LAST_OUT) {
+          if (G.xin0) G.out[idx] = (double)a.x;
+          if (G.xin1) G.out[idx + 1] = (double)a.y;
+        } else {
+          if (G.xin0) {
+            const double vi = G.v[idx];
+            const double o = vi - (double)a.x;
+            G.out[idx] = o;
+            part = fma(G.mw ? vi * G.mw[idx] : vi, o, part);
+          }
+          if (G.xin1) {
+            const double vi = G.v[idx + 1];
+            const double o = vi - (double)a.y;
+            G.out[idx + 1] = o;
+            part = fma(G.mw ? vi * G.mw[idx + 1] : vi, o, part);
+          }
         }
       }
     }
   }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) S.aA[T0][i] = accN[i];
 }
 
-template <int KIND, bool V2>
-__global__ void __launch_bounds__(32 * k3WR, 1) k_step3d2(const float* __restrict__ gp, const float* __restrict__ gc,
+// Buffer indices: in_p / in_c = the W^{n-1} / W^n buffers (0 .. 3) of the maps, outputs op / oc.
+template <int KIND>
+__global__ void __launch_bounds__(32 * k3WR, 1) k_step3d2(const Maps3d2* __restrict__ maps, int in_p, int in_c,
                                                          float* __restrict__ op, float* __restrict__ oc,
                                                          float* __restrict__ acc, const double* __restrict__ v,
                                                          const double* __restrict__ mw, double* __restrict__ out,
-                                                         int nx, int ny, int nz, int cx, int ncol, int slab,
-                                                         int64_t units, StepCoef<float> cf, float w2,
-                                                         double* partials, unsigned* counter, double* scal_out) {
-  // double-buffered stages (one barrier per plane): at phase k the CTA writes P[k & 1] (W^n(z),
-  // region rows -1 .. 34) before the barrier and Q[k & 1] (W^{n+1}(z), rows 0 .. 33) after it;
-  // step B reads Q[(k - 1) & 1], written before the barrier.  Phases count from the range's first
-  // plane, so a range starts with an extra barrier.
-  __shared__ __align__(16) float P[2][k3H + 4][k3PC];
-  __shared__ __align__(16) float Q[2][k3H + 2][k3PC];
+                                                         int nx, int ny, int nz, int pitch, int cx, int ncol,
+                                                         int slab, int64_t units, StepCoef<float> cf, float w2,
+                                                         double* partials, unsigned* counter, double* scal_out,
+                                                         double* flag) {
+  extern __shared__ unsigned char s3raw[];
+  float* const SW = reinterpret_cast<float*>(((uintptr_t)s3raw + 127) & ~(uintptr_t)127);   // [5][36][72]
+  float* const SP = SW + k3NW * k3SPlane;                                                      // [3][36][72]
+  float* const SA = SP + k3NP * k3SPlane;                                                      // [3][32][64]
+  float* const SQ = SA + k3NP * k3APlane;                                                      // [2][34][72]
+  __shared__ __align__(8) uint64_t barW[k3NW], barP[k3NP], barA[k3NP];
+  __shared__ int s_fail;
   const int lane = threadIdx.x, wr = threadIdx.y;
+  const bool leader = lane == 0 && wr == 0;
+  if (leader) {
+    for (int s = 0; s < k3NW; ++s) mbar_init(&barW[s], 1);
+    for (int s = 0; s < k3NP; ++s) {
+      mbar_init(&barP[s], 1);
+      mbar_init(&barA[s], 1);
+    }
+    mbar_init_fence();
+    s_fail = 0;
+  }
+  __syncthreads();
+  const CUtensorMap* mapC = &maps->w[in_c];
+  const CUtensorMap* mapP = &maps->w[in_p];
+  const CUtensorMap* mapA = &maps->acc;
+  unsigned parW = 0u, parP = 0u, parA = 0u;   // phase parity of each stage (bit s)
   Geo3d2 G;
-  G.gc = gc; G.gp = gp; G.op = op; G.oc = oc; G.acc = acc; G.v = v; G.mw = mw; G.out = out;
+  G.op = op; G.oc = oc; G.acc = acc; G.v = v; G.mw = mw; G.out = out;
+  G.nx = nx; G.ny = ny; G.nz = nz; G.pitch = pitch;
+  G.ppitch = (int64_t)pitch * ny;
   G.plane = (int64_t)nx * ny;
-  G.nz = nz;
   G.edge = lane == 0 || lane == 31;
-  G.pc = 2 * lane + 2;
-  G.pr1 = lane == 0 ? 1 : k3W + 2;
-  G.pr2 = lane == 0 ? 0 : k3W + 3;
-  const int xrow = wr == 0 ? -1 : (wr == k3WR - 1 ? k3H + 2 : -2);   // extra staged row, if any
-  G.xrow = xrow >= -1;
-  G.sx = xrow + 1;
+  G.pc = 2 * lane + 4;
+  G.pr1 = lane == 0 ? 3 : k3W + 4;
   double part = 0.0;
+  bool failed = false;
   const int64_t u_end = units * (blockIdx.x + 1) / gridDim.x;
   const int64_t per_slab = (int64_t)ncol * slab;
-  for (int64_t u = units * blockIdx.x / gridDim.x; u < u_end;) {
-    // unit u -> (slab, tile column, plane): slabs of `slab` planes (the last one thinner), each
-    // slab's units column by column, so that CTAs with neighbouring ranges march neighbouring
-    // tile columns through the same planes at the same time (their halo reads meet in L2)
+  for (int64_t u = units * blockIdx.x / gridDim.x; u < u_end && !failed;) {
+    // unit u -> (slab, tile column, plane)
     const int64_t sl = u / per_slab;
     const int zlo = (int)(sl * slab);
     const int thick = min(slab, nz - zlo);
@@ -602,69 +581,124 @@ __global__ void __launch_bounds__(32 * k3WR, 1) k_step3d2(const float* __restric
     G.zs = zlo + (int)(rem - (int64_t)cid * thick);
     G.ze = (int)min((int64_t)zlo + thick, (int64_t)G.zs + (u_end - u));
     u += G.ze - G.zs;
-    G.zl1 = min(G.ze, nz - 1);
-    G.zl2 = min(G.ze + 1, nz - 1);
-    const int x0 = (cid % cx) * k3W, y0 = (cid / cx) * k3H;
-    const int xl = x0 + 2 * lane;
+    G.x0 = (cid % cx) * k3W;
+    G.y0 = (cid / cx) * k3H;
+    const int xl = G.x0 + 2 * lane;
     G.xin0 = xl < nx;
     G.xin1 = xl + 1 < nx;
-    const int xr1 = lane == 0 ? x0 - 1 : x0 + k3W, xr2 = lane == 0 ? x0 - 2 : x0 + k3W + 1;
-    const bool rx1 = G.edge && xr1 >= 0 && xr1 < nx, rx2 = G.edge && xr2 >= 0 && xr2 < nx;
+    const int xr1 = lane == 0 ? G.x0 - 1 : G.x0 + k3W;
+    const bool rx1 = G.edge && xr1 >= 0 && xr1 < nx;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      const int r = 2 * wr + i, y = y0 - 1 + r;
+      const int r = 2 * wr + i, y = G.y0 - 1 + r;
       const bool yin = y >= 0 && y < ny;
       G.trow[i] = yin && r >= 1 && r <= k3H;
       G.own0[i] = yin && G.xin0;
       G.own1[i] = yin && G.xin1;
-      G.ry[i] = rx1 && yin;
       G.rt1[i] = rx1 && G.trow[i];
-      G.rt2[i] = rx2 && G.trow[i];
-      G.co[i] = yin ? xl + nx * y : 0;
-      G.r1o[i] = yin ? xr1 + nx * y : 0;
-      G.r2o[i] = yin ? xr2 + nx * y : 0;
+      G.co[i] = yin ? xl + pitch * y : 0;
+      G.uo[i] = yin ? xl + nx * y : 0;
     }
-    const int yx = y0 - 1 + xrow;
-    G.xrin = G.xrow && yx >= 0 && yx < ny;
-    G.xo = G.xrin ? xl + nx * yx : 0;
-    S3d2 S;
     const int zb = G.zs - 1;
-    auto zok = [&](int z) { return z >= 0 && z < nz; };
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {   // W^n at zb - 1, zb, zb + 1 (phase 0: c[0] is plane zb)
-        const int z = zb - 1 + d;
-        const bool ok = zok(z);
-        const float* g = gc + (int64_t)z * G.plane;
-        S.c[(d + 3) & 3][i] = ld2<V2>(g + G.co[i], ok && G.own0[i], ok && G.own1[i]);
-        S.r[(d + 3) & 3][i] = (ok && G.ry[i]) ? __ldg(g + G.r1o[i]) : 0.f;
-      }
-      const bool ok = zok(zb);
-      const int64_t zo = (int64_t)zb * G.plane;
-      S.wp[0][i] = ld2<V2>(gp + zo + G.co[i], ok && G.own0[i], ok && G.own1[i]);
-      S.wr[0][i] = (ok && G.rt1[i]) ? __ldg(gp + zo + G.r1o[i]) : 0.f;
-      S.rb[0][i] = (ok && G.rt2[i]) ? __ldg(gc + zo + G.r2o[i]) : 0.f;
-      S.ac[0][i] = make_float2(0.f, 0.f);   // acc(zs - 1) is not needed (no step B there)
-      S.aA[1][i] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int d = 0; d < 4; ++d) S.q[d][i] = make_float2(0.f, 0.f);
+    // copies of plane zz into its stage (issued by one thread; zz outside the grid reads zeros)
+    auto issue_w = [&](int zz, int slot) {
+      mbar_arrive_expect_tx(&barW[slot], k3SPlane * 4);
+      tma_load_3d(SW + slot * k3SPlane, mapC, G.x0 - 4, G.y0 - 2, zz, &barW[slot]);
+    };
+    auto issue_p = [&](int zz, int slot) {
+      mbar_arrive_expect_tx(&barP[slot], k3SPlane * 4);
+      tma_load_3d(SP + slot * k3SPlane, mapP, G.x0 - 4, G.y0 - 2, zz, &barP[slot]);
+    };
+    auto issue_a = [&](int zz, int slot) {
+      mbar_arrive_expect_tx(&barA[slot], k3APlane * 4);
+      tma_load_3d(SA + slot * k3APlane, mapA, G.x0, G.y0, zz, &barA[slot]);
+    };
+    __syncthreads();   // the previous range's reads of the stages are done
+    // stage slots: W^n plane zz in (zz - zb + 1) mod 5, W^{n-1} and acc plane zz in (zz - zb) mod 3
+    if (leader) {
+      issue_w(zb - 1, 0);
+      issue_w(zb, 1);
+      issue_w(zb + 1, 2);
+      if (zb + 2 <= G.ze + 1) issue_w(zb + 2, 3);
+      issue_p(zb, 0);
+      if (zb + 1 <= G.ze) issue_p(zb + 1, 1);
     }
-    S.xr[0] = ld2<V2>(gc + (int64_t)zb * G.plane + G.xo, zok(zb) && G.xrin && G.xin0, zok(zb) && G.xrin && G.xin1);
-    __syncthreads();   // the previous range's last reads of the stages are done
-    // planes zb .. ze, four at a time (phase k = z - zb: the stage parity and the register rings
-    // follow the phase)
-    for (int z = zb;;) {
-      s3d2_plane<0, KIND, V2>(S, G, z, wr, P, Q, cf, w2, part); if (++z > G.ze) break;
-      s3d2_plane<1, KIND, V2>(S, G, z, wr, P, Q, cf, w2, part); if (++z > G.ze) break;
-      s3d2_plane<2, KIND, V2>(S, G, z, wr, P, Q, cf, w2, part); if (++z > G.ze) break;
-      s3d2_plane<3, KIND, V2>(S, G, z, wr, P, Q, cf, w2, part); if (++z > G.ze) break;
+    Q3d2 S;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) S.q[d][0] = S.q[d][1] = make_float2(0.f, 0.f);
+    int kw = 1, kp = 0;   // stages of W^n(z) and of plane z
+    int z = zb;
+    // wait for a stage's copies (every thread), flip its parity
+    auto wait = [&](uint64_t* bar, unsigned& par, int slot) {
+      if (!mbar_wait(&bar[slot], (par >> slot) & 1u, kMbarPolls3)) failed = true;
+      par ^= 1u << slot;
+    };
+    // the planes' stages needed before the loop: W^n(zb - 1), W^n(zb)
+    wait(barW, parW, 0);
+    wait(barW, parW, 1);
+    auto plane = [&](auto ph) {
+      constexpr int PH = decltype(ph)::value;
+      // W^n(z + 1), W^{n-1}(z) and acc(z - 1) have landed (issued at least two planes ago)
+      const int kwp = kw + 1 == k3NW ? 0 : kw + 1;
+      wait(barW, parW, kwp);
+      wait(barP, parP, kp);
+      const int kpm = kp == 0 ? k3NP - 1 : kp - 1;
+      if (z > G.zs) wait(barA, parA, kpm);
+      if (__syncthreads_or(failed)) {
+        failed = true;
+        return;
+      }
+      // the next copies, into stages last read at the previous plane
+      if (leader) {
+        const int kw3 = kw + 3 >= k3NW ? kw + 3 - k3NW : kw + 3, kp2 = kp + 2 >= k3NP ? kp + 2 - k3NP : kp + 2;
+        const int kp1 = kp + 1 == k3NP ? 0 : kp + 1;
+        if (z + 3 <= G.ze + 1) issue_w(z + 3, kw3);
+        if (z + 2 <= G.ze) issue_p(z + 2, kp2);
+        if (z + 1 >= G.zs && z + 1 < G.ze) issue_a(z + 1, kp1);
+      }
+      s3d2_plane<PH, KIND>(S, G, z, wr, SW, SP, SA, SQ, kw, kp, cf, w2, part);
+      kw = kwp;
+      kp = kp + 1 == k3NP ? 0 : kp + 1;
+      ++z;
+    };
+    // planes zb .. ze, four at a time (phase k = z - zb: the W^{n+1} stage and registers follow it)
+    for (;;) {
+      plane(std::integral_constant<int, 0>()); if (failed || z > G.ze) break;
+      plane(std::integral_constant<int, 1>()); if (failed || z > G.ze) break;
+      plane(std::integral_constant<int, 2>()); if (failed || z > G.ze) break;
+      plane(std::integral_constant<int, 3>()); if (failed || z > G.ze) break;
     }
   }
-  if (KIND == K_LAST_AV) {
+  if (failed) {   // a copy that did not arrive: report, then a bounded drain of the stages
+    if (leader) {
+      *flag = 1.0;
+      for (int s = 0; s < k3NW; ++s) mbar_wait(&barW[s], (parW >> s) & 1u, kMbarPolls3);
+      for (int s = 0; s < k3NP; ++s) {
+        mbar_wait(&barP[s], (parP >> s) & 1u, kMbarPolls3);
+        mbar_wait(&barA[s], (parA >> s) & 1u, kMbarPolls3);
+      }
+    }
+    __syncthreads();
+  }
+  if (KIND == K_LAST_AV) {   // (also after a failure: the grid's reduction counter stays consistent)
     part = block_sum(part);
     double total;
     if (grid_reduce(part, partials, counter, &total) && flat_tid() == 0) *scal_out = total;
+  }
+}
+
+// unpadded -> pitched copies of the state a two-step chain starts from
+__global__ void __launch_bounds__(256) k_to_pitched3(const float* __restrict__ a, const float* __restrict__ b,
+                                                     const float* __restrict__ c, float* __restrict__ pa,
+                                                     float* __restrict__ pb, float* __restrict__ pc, int nx,
+                                                     int64_t n, int pitch) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t x = i % nx, yz = i / nx;
+    const int64_t pi = x + (int64_t)pitch * yz;
+    pa[pi] = a[i];
+    pb[pi] = b[i];
+    pc[pi] = c[i];
   }
 }
 
@@ -846,7 +880,10 @@ void step3d2_init() {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step3d2<K_STEP, true>, 32 * k3WR, 0);
+  const void* fns[] = {(const void*)k_step3d2<K_STEP>, (const void*)k_step3d2<K_LAST_OUT>,
+                       (const void*)k_step3d2<K_LAST_AV>};
+  for (const void* f : fns) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, k3Smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step3d2<K_STEP>, 32 * k3WR, k3Smem);
   s3d2_slots = std::max(1, sms * std::max(per_sm, 1));
 }
 
@@ -867,6 +904,56 @@ static Grid3d2 grid_3d2(whv_grid g) {
   return q;
 }
 
+typedef CUresult (*EncodeTiled3Fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static bool encode_box3(EncodeTiled3Fn enc, CUtensorMap* map, float* base, int nx, int ny, int nz, int pitch,
+                        int bx, int by) {
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)pitch * sizeof(float), (cuuint64_t)pitch * ny * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1u};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+// pitched FP32 state of the two-step 3-D kernel (rows padded to a multiple of 4 floats: the copy
+// engine needs 16-byte row strides) and its tensor maps; called outside any stream capture
+whv_status ensure_pitched3(whv_grid g) {
+  if (g->pw3[0]) return WHV_OK;
+  const EncodeTiled3Fn enc = (EncodeTiled3Fn)tensor_map_encoder();
+  if (!enc) return fail(g, WHV_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  const int pitch = (nx + 3) / 4 * 4;
+  const size_t bytes = (size_t)pitch * ny * nz * sizeof(float);
+  float* bufs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  for (int m = 0; m < 5 && e == cudaSuccess; ++m) {
+    e = cudaMalloc(&bufs[m], bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bufs[m], 0, bytes, g->stream);   // padding columns stay 0
+  }
+  Maps3d2 M;
+  void* dm = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&dm, sizeof(Maps3d2));
+  bool ok = e == cudaSuccess;
+  for (int m = 0; m < 4 && ok; ++m) ok = encode_box3(enc, &M.w[m], bufs[m], nx, ny, nz, pitch, k3BX, k3BY);
+  if (ok) ok = encode_box3(enc, &M.acc, bufs[4], nx, ny, nz, pitch, k3W, k3H);
+  if (ok) e = cudaMemcpy(dm, &M, sizeof(Maps3d2), cudaMemcpyHostToDevice);
+  if (!ok || e != cudaSuccess) {
+    for (float* b : bufs) if (b) cudaFree(b);
+    if (dm) cudaFree(dm);
+    return !ok ? fail(g, WHV_ERR_CUDA, "cuTensorMapEncodeTiled failed (two-step 3-D buffers)")
+               : cuda_fail(g, e, "two-step 3-D buffers");
+  }
+  for (int m = 0; m < 4; ++m) g->pw3[m] = bufs[m];
+  g->pacc3 = bufs[4];
+  g->maps3 = dm;
+  g->pitch3 = pitch;
+  return WHV_OK;
+}
+
 // Steps n = 1 .. nt-1 of a 3-D f = 0 FP32 wave solve (c = 1, second order) after the Taylor
 // start (W^0 in buf[0], W^1 in buf[1], acc): one single step when their number is odd, then
 // two-step passes alternating between the buffer pairs (0, 1) and (2, 3); the last launch writes
@@ -882,7 +969,6 @@ static whv_status two_step_3d(whv_grid g, const TimeGridH& tg, const double* v, 
   const Grid3d2 q = grid_3d2(g);
   const dim3 g2(q.blocks), b2(32, k3WR, 1);
   if (q.blocks > chan_cap(g, CH_STEP)) return fail(g, WHV_ERR_INVALID, "grid too large for the fused reduction");
-  const bool v2 = nx % 2 == 0;
   const LaunchShape ls = shape_of(g);
   float* wprev = buf[0];
   float* wcur = buf[1];
@@ -904,25 +990,30 @@ static whv_status two_step_3d(whv_grid g, const TimeGridH& tg, const double* v, 
     float* t = wprev; wprev = wcur; wcur = t;
     n = 2;
   }
+  if (n < tg.nt) {   // the chain of two-step passes runs on the pitched copies of the state
+    const int64_t N = g->N;
+    k_to_pitched3<<<(int)std::min<int64_t>((N + 255) / 256, 4096), 256, 0, g->stream>>>(
+        wprev, wcur, acc, g->pw3[0], g->pw3[1], g->pacc3, nx, N, g->pitch3);
+    WHV_CUDA(g, cudaGetLastError());
+    ++nl;
+  }
+  int ip = 0;   // the pitched pair holding (W^{n-1}, W^n): buffers ip, ip + 1
   while (n < tg.nt) {   // W^n -> W^{n+2}
     cf.w1 = (float)tg.weight[n + 1];
     const float w2 = (float)tg.weight[n + 2];
     const bool last = n + 2 == tg.nt;
-    const bool in01 = wprev == buf[0] || wprev == buf[1];   // (wprev, wcur) is one of the pairs
-    float* op = in01 ? buf[2] : buf[0];
-    float* oc = in01 ? buf[3] : buf[1];
+    const int oq = 2 - ip;
+    float* op = g->pw3[oq];
+    float* oc = g->pw3[oq + 1];
     const int kind = !last ? K_STEP : (epi == 0 ? K_LAST_OUT : K_LAST_AV);
-    auto kern = kind == K_STEP ? (v2 ? k_step3d2<K_STEP, true> : k_step3d2<K_STEP, false>)
-              : kind == K_LAST_OUT ? (v2 ? k_step3d2<K_LAST_OUT, true> : k_step3d2<K_LAST_OUT, false>)
-                                   : (v2 ? k_step3d2<K_LAST_AV, true> : k_step3d2<K_LAST_AV, false>);
-    kern<<<g2, b2, 0, g->stream>>>(wprev, wcur, op, oc, acc, kind == K_LAST_AV ? v : nullptr,
-                                   kind == K_LAST_AV ? g->mw : nullptr, kind == K_STEP ? nullptr : out, nx, ny, nz,
-                                   q.cx, q.ncol, q.slab, q.units, cf, w2, kind == K_LAST_AV ? part : nullptr,
-                                   kind == K_LAST_AV ? cnt : nullptr, kind == K_LAST_AV ? g->scal + S_PQ : nullptr);
+    auto kern = kind == K_STEP ? k_step3d2<K_STEP> : (kind == K_LAST_OUT ? k_step3d2<K_LAST_OUT> : k_step3d2<K_LAST_AV>);
+    kern<<<g2, b2, k3Smem, g->stream>>>((const Maps3d2*)g->maps3, ip, ip + 1, op, oc, g->pacc3,
+                                        kind == K_LAST_AV ? v : nullptr, kind == K_LAST_AV ? g->mw : nullptr,
+                                        kind == K_STEP ? nullptr : out, nx, ny, nz, g->pitch3, q.cx, q.ncol, q.slab,
+                                        q.units, cf, w2, part, cnt, g->scal + S_PQ, g->scal + S_FLAG);
     WHV_CUDA(g, cudaGetLastError());
     ++nl;
-    wprev = op;
-    wcur = oc;
+    ip = oq;
     n += 2;
   }
   *launches = nl;
@@ -961,7 +1052,7 @@ static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v,
   }
   if constexpr (DIM == 3 && ORDER == 2 && !VARC && !FORCE && sizeof(T) == 4) {
     // two steps per launch when set (or chosen by the autotuner), planes of < 2^31 nodes
-    if (g->kblock >= 2 && (int64_t)g->n[0] * g->n[1] < (int64_t(1) << 31)) {
+    if (g->kblock >= 2 && g->pw3[0] && (int64_t)g->n[0] * g->n[1] < (int64_t(1) << 31)) {
       int nl = 0;
       whv_status s = two_step_3d(g, tg, v, out, epi, &nl, bufs, accbuf);
       *nlaunch += nl;
@@ -1197,6 +1288,10 @@ extern "C" whv_status whv_apply_pi(whv_grid g, const whv_params* p, const double
 extern "C" whv_status whv_set_steps_per_sweep(whv_grid g, int k) {
   if (!g) return fail(nullptr, WHV_ERR_INVALID, "grid is NULL");
   if (k < 0 || k > 16) return fail(g, WHV_ERR_INVALID, "steps per sweep must be in [0, 16]");
+  if (k >= 2 && g->dim == 3 && g->order == 2 && !g->c2 && !g->cons && g->precision == WHV_FP32_STEP) {
+    const whv_status s = ensure_pitched3(g);   // the two-step kernel's buffers, outside any capture
+    if (s != WHV_OK) return s;
+  }
   g->kblock = k;
   return WHV_OK;
 }
@@ -1226,7 +1321,8 @@ extern "C" whv_status whv_autotune(whv_grid g, const whv_params* p, int* best) {
   }
   // 2-D: per step and blocked sweeps of k steps; 3-D FP32 (c = 1): per step and two steps per launch
   std::vector<int> cands = {1};
-  if (g->dim == 3 && g->order == 2 && !g->c2 && g->precision == WHV_FP32_STEP) cands.push_back(2);
+  if (g->dim == 3 && g->order == 2 && !g->c2 && g->precision == WHV_FP32_STEP && ensure_pitched3(g) == WHV_OK)
+    cands.push_back(2);
   if (g->dim == 2)
     for (int k : {2, 4, 6, 8, 10, 12, 16}) cands.push_back(k);
   const int nc = (int)cands.size();

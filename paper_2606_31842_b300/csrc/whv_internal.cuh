@@ -110,6 +110,12 @@ struct whv_grid_s {
   float* tw[4] = {nullptr, nullptr, nullptr, nullptr};
   float* tacc = nullptr;
   int tpitch = 0;
+  // FP32 state of the two-step 3-D kernel (k_step3d2), rows padded to pitch3 floats, and the
+  // device copy of its tensor maps; allocated outside any stream capture, on first use
+  float* pw3[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* pacc3 = nullptr;
+  void* maps3 = nullptr;
+  int pitch3 = 0;
   double *xo = nullptr, *ro = nullptr, *bo = nullptr;
 
   // FP64 Krylov work vectors
@@ -210,6 +216,8 @@ whv_status blocked_steps_2d(whv_grid g, const TimeGridH& tg, const double* v, do
                             int k_want, int* launches, void* const* bufs, void* acc);
 void blocked_init();
 void step3d2_init();   // stencil.cu: resident CTA slots of the persistent two-step 3-D kernel
+whv_status ensure_pitched3(whv_grid g);   // stencil.cu: buffers and tensor maps of the two-step 3-D kernel
+void* tensor_map_encoder();               // core.cu: cuTensorMapEncodeTiled (driver entry point) or nullptr
 
 // single-CTA wave solve for small grids (stencil_blocked.cu)
 bool small_grid(whv_grid g);

@@ -554,6 +554,9 @@ __global__ void __launch_bounds__(32 * k3WR, 1) k_step3d2(const Maps3d2* __restr
     mbar_init_fence();
     s_fail = 0;
   }
+  // launched as a programmatic dependent of the previous pass: wait for its results before any
+  // global access (returns at once when there is no such dependency)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
   const CUtensorMap* mapC = &maps->w[in_c];
   const CUtensorMap* mapP = &maps->w[in_p];
@@ -1007,11 +1010,24 @@ static whv_status two_step_3d(whv_grid g, const TimeGridH& tg, const double* v, 
     float* oc = g->pw3[oq + 1];
     const int kind = !last ? K_STEP : (epi == 0 ? K_LAST_OUT : K_LAST_AV);
     auto kern = kind == K_STEP ? k_step3d2<K_STEP> : (kind == K_LAST_OUT ? k_step3d2<K_LAST_OUT> : k_step3d2<K_LAST_AV>);
-    kern<<<g2, b2, k3Smem, g->stream>>>((const Maps3d2*)g->maps3, ip, ip + 1, op, oc, g->pacc3,
-                                        kind == K_LAST_AV ? v : nullptr, kind == K_LAST_AV ? g->mw : nullptr,
-                                        kind == K_STEP ? nullptr : out, nx, ny, nz, g->pitch3, q.cx, q.ncol, q.slab,
-                                        q.units, cf, w2, part, cnt, g->scal + S_PQ, g->scal + S_FLAG);
-    WHV_CUDA(g, cudaGetLastError());
+    // programmatic dependent launch: the pass's CTAs may be scheduled as the previous kernel's
+    // exit; they wait (griddepcontrol.wait) for its completion before touching global memory
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = g2;
+    lc.blockDim = b2;
+    lc.dynamicSmemBytes = k3Smem;
+    lc.stream = g->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    const double* vk = kind == K_LAST_AV ? v : nullptr;
+    const double* mwk = kind == K_LAST_AV ? g->mw : nullptr;
+    double* outk = kind == K_STEP ? nullptr : out;
+    WHV_CUDA(g, cudaLaunchKernelEx(&lc, kern, (const Maps3d2*)g->maps3, ip, ip + 1, op, oc, g->pacc3, vk, mwk, outk,
+                                   nx, ny, nz, g->pitch3, q.cx, q.ncol, q.slab, q.units, cf, w2, part, cnt,
+                                   g->scal + S_PQ, g->scal + S_FLAG));
     ++nl;
     ip = oq;
     n += 2;

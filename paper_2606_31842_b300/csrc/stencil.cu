@@ -37,12 +37,14 @@ __global__ void __launch_bounds__(256) k_first(const double* __restrict__ v, T* 
                                                T* __restrict__ w1, T* __restrict__ acc,
                                                const T* __restrict__ c2,
                                                const double* __restrict__ f, int nx, int ny, int nz,
-                                               StepCoef<T> cf) {
+                                               StepCoef<T> cf, int wpitch) {
+  // (wpitch: row length of the written arrays -- nx, or the padded rows of the 3-D two-step chain)
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= nx || y >= ny) return;
   const int64_t idx = x + (int64_t)nx * (y + (int64_t)ny * z);
+  const int64_t widx = x + (int64_t)wpitch * (y + (int64_t)ny * z);
   T W0 = T(0), L = T(0);
   if (!ZERO_V) {
     W0 = (T)v[idx];
@@ -51,9 +53,9 @@ __global__ void __launch_bounds__(256) k_first(const double* __restrict__ v, T* 
   }
   if (FORCE) L -= (T)f[idx];  // cos(0) = 1
   const T W1 = fma(T(0.5) * cf.dt2, L, W0);
-  w0[idx] = W0;
-  w1[idx] = W1;
-  acc[idx] = fma(cf.w1, W1, cf.w0 * W0);
+  w0[widx] = W0;
+  w1[widx] = W1;
+  acc[widx] = fma(cf.w1, W1, cf.w0 * W0);
 }
 
 template <typename T, int DIM, int ORDER, bool VARC, bool FORCE, int KIND>
@@ -962,7 +964,7 @@ whv_status ensure_pitched3(whv_grid g) {
 // two-step passes alternating between the buffer pairs (0, 1) and (2, 3); the last launch writes
 // the epilogue.
 static whv_status two_step_3d(whv_grid g, const TimeGridH& tg, const double* v, double* out, int epi,
-                              int* launches, void* const* bufs, void* accbuf) {
+                              int* launches, void* const* bufs, void* accbuf, bool prepitched) {
   float* buf[4] = {(float*)bufs[0], (float*)bufs[1], (float*)bufs[2], (float*)bufs[3]};
   float* acc = (float*)accbuf;
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
@@ -976,7 +978,7 @@ static whv_status two_step_3d(whv_grid g, const TimeGridH& tg, const double* v, 
   float* wprev = buf[0];
   float* wcur = buf[1];
   int n = 1, nl = 0;
-  if ((tg.nt - 1) % 2 == 1) {   // one single step first (the last one when nt = 2)
+  if (!prepitched && (tg.nt - 1) % 2 == 1) {   // one single step first (the last one when nt = 2)
     cf.w1 = (float)tg.weight[2];
     const bool last = tg.nt == 2;
     if (!last)
@@ -993,7 +995,7 @@ static whv_status two_step_3d(whv_grid g, const TimeGridH& tg, const double* v, 
     float* t = wprev; wprev = wcur; wcur = t;
     n = 2;
   }
-  if (n < tg.nt) {   // the chain of two-step passes runs on the pitched copies of the state
+  if (n < tg.nt && !prepitched) {   // the chain of two-step passes runs on pitched copies of the state
     const int64_t N = g->N;
     k_to_pitched3<<<(int)std::min<int64_t>((N + 255) / 256, 4096), 256, 0, g->stream>>>(
         wprev, wcur, acc, g->pw3[0], g->pw3[1], g->pacc3, nx, N, g->pitch3);
@@ -1052,10 +1054,26 @@ static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v,
   StepCoef<T> cf = coef_of<T>(g, tg);
   dim3 fgrid = ls.grid;
   if (DIM == 3) fgrid.z = nz;   // the first-step kernel takes one plane per z block
+  // the 3-D two-step chain (two steps per launch when set or chosen by the autotuner, planes of
+  // < 2^31 nodes) runs on padded rows; with an even number of steps after the first one, the
+  // first step writes them directly
+  bool two_step = false, prepitched = false;
+  if constexpr (DIM == 3 && ORDER == 2 && !VARC && !FORCE && sizeof(T) == 4) {
+    two_step = g->kblock >= 2 && g->pw3[0] && (int64_t)g->n[0] * g->n[1] < (int64_t(1) << 31);
+    prepitched = two_step && (tg.nt - 1) % 2 == 0 && tg.nt > 1;
+    if (prepitched) {
+      b0 = (T*)g->pw3[0];
+      b1 = (T*)g->pw3[1];
+      acc = (T*)g->pacc3;
+    }
+  }
+  const int wpitch = prepitched ? g->pitch3 : nx;
   if (v)
-    k_first<T, DIM, ORDER, VARC, FORCE, false><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, c2, f, nx, ny, nz, cf);
+    k_first<T, DIM, ORDER, VARC, FORCE, false><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, c2, f, nx, ny, nz, cf,
+                                                                                  wpitch);
   else
-    k_first<T, DIM, ORDER, VARC, FORCE, true><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, c2, f, nx, ny, nz, cf);
+    k_first<T, DIM, ORDER, VARC, FORCE, true><<<fgrid, ls.block, 0, g->stream>>>(v, b0, b1, acc, c2, f, nx, ny, nz, cf,
+                                                                                 wpitch);
   WHV_CUDA(g, cudaGetLastError());
   *nlaunch = 1;
   if constexpr (DIM == 2 && !FORCE) {
@@ -1066,14 +1084,11 @@ static whv_status launch_solve(whv_grid g, const TimeGridH& tg, const double* v,
       return s;
     }
   }
-  if constexpr (DIM == 3 && ORDER == 2 && !VARC && !FORCE && sizeof(T) == 4) {
-    // two steps per launch when set (or chosen by the autotuner), planes of < 2^31 nodes
-    if (g->kblock >= 2 && g->pw3[0] && (int64_t)g->n[0] * g->n[1] < (int64_t(1) << 31)) {
-      int nl = 0;
-      whv_status s = two_step_3d(g, tg, v, out, epi, &nl, bufs, accbuf);
-      *nlaunch += nl;
-      return s;
-    }
+  if (two_step) {
+    int nl = 0;
+    whv_status s = two_step_3d(g, tg, v, out, epi, &nl, bufs, accbuf, prepitched);
+    *nlaunch += nl;
+    return s;
   }
   *nlaunch += tg.nt - 1;
   // after the first step: W^{n-1} in b0, W^n in b1

@@ -423,8 +423,8 @@ struct Geo3d2 {          // per-thread geometry of the current range
   int64_t ppitch, plane;               // pitched plane; unpadded plane (FP64 epilogue)
   int nx, ny, nz, pitch, zs, ze, x0, y0;
   int co[2], uo[2];                    // own pair: pitched / unpadded in-plane offsets
-  bool own0[2], own1[2], trow[2], rt1[2], xin0, xin1, edge;
-  int pc, pr1;                         // staged columns of the own pair and of the ring node
+  bool own0[2], own1[2], trow[2], xin0, xin1;
+  int pc;                              // staged column of the own pair
 };
 
 struct Q3d2 {            // W^{n+1} of the own nodes: q[k & 3] is plane z; filter sums after step n + 1
@@ -444,7 +444,24 @@ __device__ __forceinline__ void s3d2_plane(Q3d2& S, const Geo3d2& G, int z, int 
   const float* Pp = SP + kp * k3SPlane;    // W^{n-1}(z)
   float* Qz = SQ + (PH & 1) * k3QPlane;    // W^{n+1}(z)
   const bool zin = (unsigned)z < (unsigned)G.nz;
-  // step A: W^{n+1}(z) of the own nodes (region rows 0 .. 33) and of the ring node
+  if (wr == k3WR) {   // the ring warp: step A on the ring columns x0 - 1 and x0 + 64 of the tile rows
+    const int r = (threadIdx.x & 31) + 1;   // region row
+    const int y = G.y0 - 1 + r;
+    const bool yin = y < G.ny;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int c = side == 0 ? 3 : k3W + 4;   // staged column
+      const int x = G.x0 - 4 + c;
+      const int lr = (r + 1) * k3BX + c;
+      float w = fmaf(cf.b, W0[lr], -Pp[lr]);
+      w = fmaf(cf.a[0], W0[lr - 1] + W0[lr + 1], w);
+      w = fmaf(cf.a[1], W0[lr - k3BX] + W0[lr + k3BX], w);
+      w = fmaf(cf.a[2], Wm[lr] + Wp[lr], w);
+      Qz[lr - k3BX] = (zin && yin && x >= 0 && x < G.nx) ? w : 0.f;
+    }
+    return;
+  }
+  // step A: W^{n+1}(z) of the own nodes (region rows 0 .. 33)
   float2 cm[2];
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
@@ -464,14 +481,6 @@ __device__ __forceinline__ void s3d2_plane(Q3d2& S, const Geo3d2& G, int z, int 
     u1 = fmaf(cf.a[2], cm[i].y + cp.y, u1);
     S.q[Q0][i] = make_float2((zin && G.own0[i]) ? u0 : 0.f, (zin && G.own1[i]) ? u1 : 0.f);
     *reinterpret_cast<float2*>(Qz + (sr - 1) * k3BX + G.pc) = S.q[Q0][i];
-    if (G.edge && G.trow[i]) {
-      const int lr = sr * k3BX + G.pr1;
-      float w = fmaf(cf.b, W0[lr], -Pp[lr]);
-      w = fmaf(cf.a[0], W0[lr - 1] + W0[lr + 1], w);
-      w = fmaf(cf.a[1], W0[lr - k3BX] + W0[lr + k3BX], w);
-      w = fmaf(cf.a[2], Wm[lr] + Wp[lr], w);
-      Qz[lr - k3BX] = (zin && G.rt1[i]) ? w : 0.f;
-    }
   }
   // step B: W^{n+2}(z - 1) on the tile rows, from Q[(z - 1) & 1]
   if (z > G.zs) {
@@ -530,7 +539,7 @@ __device__ __forceinline__ void s3d2_plane(Q3d2& S, const Geo3d2& G, int z, int 
 
 // Buffer indices: in_p / in_c = the W^{n-1} / W^n buffers (0 .. 3) of the maps, outputs op / oc.
 template <int KIND>
-__global__ void __launch_bounds__(32 * k3WR, 1) k_step3d2(const Maps3d2* __restrict__ maps, int in_p, int in_c,
+__global__ void __launch_bounds__(32 * (k3WR + 1), 1) k_step3d2(const Maps3d2* __restrict__ maps, int in_p, int in_c,
                                                          float* __restrict__ op, float* __restrict__ oc,
                                                          float* __restrict__ acc, const double* __restrict__ v,
                                                          const double* __restrict__ mw, double* __restrict__ out,
@@ -569,9 +578,7 @@ __global__ void __launch_bounds__(32 * k3WR, 1) k_step3d2(const Maps3d2* __restr
   G.nx = nx; G.ny = ny; G.nz = nz; G.pitch = pitch;
   G.ppitch = (int64_t)pitch * ny;
   G.plane = (int64_t)nx * ny;
-  G.edge = lane == 0 || lane == 31;
   G.pc = 2 * lane + 4;
-  G.pr1 = lane == 0 ? 3 : k3W + 4;
   double part = 0.0;
   bool failed = false;
   const int64_t u_end = units * (blockIdx.x + 1) / gridDim.x;
@@ -591,8 +598,6 @@ __global__ void __launch_bounds__(32 * k3WR, 1) k_step3d2(const Maps3d2* __restr
     const int xl = G.x0 + 2 * lane;
     G.xin0 = xl < nx;
     G.xin1 = xl + 1 < nx;
-    const int xr1 = lane == 0 ? G.x0 - 1 : G.x0 + k3W;
-    const bool rx1 = G.edge && xr1 >= 0 && xr1 < nx;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       const int r = 2 * wr + i, y = G.y0 - 1 + r;
@@ -600,7 +605,6 @@ __global__ void __launch_bounds__(32 * k3WR, 1) k_step3d2(const Maps3d2* __restr
       G.trow[i] = yin && r >= 1 && r <= k3H;
       G.own0[i] = yin && G.xin0;
       G.own1[i] = yin && G.xin1;
-      G.rt1[i] = rx1 && G.trow[i];
       G.co[i] = yin ? xl + pitch * y : 0;
       G.uo[i] = yin ? xl + nx * y : 0;
     }
@@ -888,7 +892,7 @@ void step3d2_init() {
   const void* fns[] = {(const void*)k_step3d2<K_STEP>, (const void*)k_step3d2<K_LAST_OUT>,
                        (const void*)k_step3d2<K_LAST_AV>};
   for (const void* f : fns) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, k3Smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step3d2<K_STEP>, 32 * k3WR, k3Smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step3d2<K_STEP>, 32 * (k3WR + 1), k3Smem);
   s3d2_slots = std::max(1, sms * std::max(per_sm, 1));
 }
 
@@ -972,7 +976,7 @@ static whv_status two_step_3d(whv_grid g, const TimeGridH& tg, const double* v, 
   double* part = chan(g, CH_STEP);
   unsigned* cnt = g->counters + CH_STEP;
   const Grid3d2 q = grid_3d2(g);
-  const dim3 g2(q.blocks), b2(32, k3WR, 1);
+  const dim3 g2(q.blocks), b2(32, k3WR + 1, 1);   // 17 warp rows and the ring warp
   if (q.blocks > chan_cap(g, CH_STEP)) return fail(g, WHV_ERR_INVALID, "grid too large for the fused reduction");
   const LaunchShape ls = shape_of(g);
   float* wprev = buf[0];

@@ -367,8 +367,8 @@ __global__ void __launch_bounds__(256) k_step3d(const T* __restrict__ wc, T* __r
 }
 
 // 3-D 7-point, FP32, c = 1, f = 0: TWO leapfrog steps per pass (W^{n-1}, W^n -> W^{n+1}, W^{n+2}
-// into the other buffer pair), halving the state traffic of single steps.  A CTA of 17 warps
-// owns a tile of 64 x 32 nodes in x, y and marches through planes z; lane l of warp row w holds
+// into the other buffer pair), halving the state traffic of single steps.  A CTA of 18 warps
+// owns a tile of 64 x 32 nodes in x, y and marches through planes z; lane l of warp row w < 17 holds
 // the two adjacent columns x0 + 2l, x0 + 2l + 1 of the two region rows 2w, 2w + 1 (region row r
 // is y = y0 - 1 + r: rows 1 .. 32 are the tile, 0 and 33 its ring).  The state lives in
 // row-padded ("pitched") FP32 buffers so that every plane of W^n (72 x 36 nodes: the tile, its
@@ -376,8 +376,8 @@ __global__ void __launch_bounds__(256) k_step3d(const T* __restrict__ wc, T* __r
 // sums (the tile) is copied into shared memory by the copy engine (TMA, one elected thread, an
 // mbarrier per stage with a bounded wait), two or three planes ahead: W^n in a ring of five
 // stages, W^{n-1} and the filter sums in rings of three.  At plane z, step A computes W^{n+1}(z)
-// on the tile and its one-node ring (lanes 0 and 31 also the ring columns x0 - 1 and x0 + 64)
-// into a double-buffered stage; step B computes W^{n+2}(z - 1) on the tile from W^{n+1} at z - 2,
+// on the tile and its one-node ring into a double-buffered stage (the ring columns x0 - 1 and
+// x0 + 64 by the 18th warp, which takes no part in step B); step B computes W^{n+2}(z - 1) on the tile from W^{n+1} at z - 2,
 // z - 1 (registers and the stage written at the previous plane) and z, and writes W^{n+1},
 // W^{n+2} and the filter sum of plane z - 1.  One barrier per plane.  The grid is persistent: the
 // (tile column, plane) pairs are split into equal contiguous ranges, one per CTA, ordered slab by

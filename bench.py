@@ -69,6 +69,9 @@ def parse(argv=None):
     ap.add_argument("--check-every", type=int, default=1,
                     help="convergence test every k iterations; 1 keeps the CG loop on the device (a graph "
                          "with a conditional node), k > 1 launches one iteration graph per step from the host")
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="FP32 stepping: relative reduction each inner CG solve of the correction aims for "
+                         "(0 = the library default)")
     ap.add_argument("--eigs", default="lanczos", choices=["lanczos", "thick"],
                     help="variable-speed workload: one 1024-step Lanczos run, or thick-restart Lanczos (basis 3 nd + 4)")
     ap.add_argument("--lanczos-fp64", action="store_true",
@@ -505,7 +508,7 @@ class C4Batch:
     class sharing that class's closed-form basis; forcings resident on the device (and pinned on
     the host for the end-to-end leg)."""
 
-    def __init__(self, whv, I, stream, fp32, nsrc, residual="df64", check_every=1):
+    def __init__(self, whv, I, stream, fp32, nsrc, residual="df64", check_every=1, inner_tol=0.0):
         import torch
         self.whv, self.stream = whv, stream
         prec = whv.WHV_FP32_STEP if fp32 else whv.WHV_FP64
@@ -515,7 +518,8 @@ class C4Batch:
             for om in I.C4_OMEGAS:
                 w = I.WORKLOADS[f"c4_{n}_{int(om)}"]
                 prm = whv.make_params(om, method="cg", tol=w.tol, maxit=3000, refine_fp64=fp32,
-                                      residual_df64=fp32 and residual == "df64", check_every=check_every)
+                                      residual_df64=fp32 and residual == "df64", check_every=check_every,
+                                      inner_tol=inner_tol)
                 owner = None
                 for src in range(nsrc):
                     g = whv.Grid(w.npts, precision=prec, stream=stream)
@@ -759,7 +763,7 @@ def run_c4(args):
     stream = torch.cuda.Stream()
     nsrc = args.sources if args.sources > 0 else I.C4_SOURCES
     fp32 = args.precision == "fp32"
-    B = C4Batch(whv, I, stream, fp32, nsrc, args.residual, args.check_every)
+    B = C4Batch(whv, I, stream, fp32, nsrc, args.residual, args.check_every, args.inner_tol)
     if args.steps_per_sweep > 0:
         B.grids[0].whv_set_steps_per_sweep(args.steps_per_sweep)
         kb, ktag = args.steps_per_sweep, "fixed"

@@ -1086,6 +1086,22 @@ __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(
       __syncwarp();
       double part = 0.0;
       int c = c0;
+      // FP64 values read one clock ahead and converted or used only at the next clock: the initial
+      // state of input row c (first sweep), v of output row c - K (last sweep, A p epilogue)
+      double nv[kFC];
+      auto fetch_v = [&](auto fst, auto lst, int cc) {
+        constexpr bool FIRST = decltype(fst)::value, LAST = decltype(lst)::value;
+        if (FIRST) {
+          const bool rin = (unsigned)cc < (unsigned)ny;
+#pragma unroll
+          for (int e = 0; e < kFC; ++e) nv[e] = (rin && cin[e] && vv) ? __ldg(vv + gx0 + e + (int64_t)nx * cc) : 0.0;
+        } else if (LAST) {
+          const int y = cc - kFK;
+          const bool ok = epi != 0 && y >= Y0 && y < Y1 && outc;
+#pragma unroll
+          for (int e = 0; e < kFC; ++e) nv[e] = (ok && gx0 + e < nx) ? __ldg(vv + gx0 + e + (int64_t)nx * y) : 0.0;
+        }
+      };
       // clocks in groups of three (the phase of the level rings is c - c0 mod 3)
       // (the first and the last sweep are separate instances, so that the loop of the other
       // sweeps carries neither the Taylor start nor the FP64 epilogue)
@@ -1093,12 +1109,15 @@ __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(
         constexpr int PH = decltype(ph)::value;
         constexpr bool FIRST = decltype(fst)::value, LAST = decltype(lst)::value;
         const int rel = c - c0, blk = rel / kFRB, row = rel % kFRB, slot = blk & 1;
+        double vc[kFC];
+#pragma unroll
+        for (int e = 0; e < kFC; ++e) vc[e] = nv[e];
+        if ((FIRST || LAST) && c + 1 <= c1) fetch_v(fst, lst, c + 1);
         FV wn = fv_zero(), wp = fv_zero(), an = fv_zero();
         if (FIRST) {
-          const bool rin = (unsigned)c < (unsigned)ny;
 #pragma unroll
           for (int e = 0; e < kFC; ++e) {
-            if (rin && cin[e] && vv) wn.v[e] = (float)__ldg(vv + gx0 + e + (int64_t)nx * c);
+            wn.v[e] = (float)vc[e];
             an.v[e] = w0 * wn.v[e];
           }
         } else {
@@ -1135,7 +1154,7 @@ __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(
               if (epi == 0) {
                 outp[gi + e] = (double)a.v[e];
               } else {
-                const double vi = __ldg(vv + gi + e);
+                const double vi = vc[e];
                 const double ov = vi - (double)a.v[e];
                 outp[gi + e] = ov;
                 part = fma(mwp ? vi * __ldg(mwp + gi + e) : vi, ov, part);
@@ -1147,6 +1166,7 @@ __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(
         ++c;
       };
       auto run = [&](auto fst, auto lst) {
+        fetch_v(fst, lst, c0);
         while (c <= c1) {
           clock(std::integral_constant<int, 0>(), fst, lst);
           if (c > c1) break;
@@ -1359,17 +1379,18 @@ __global__ void __launch_bounds__(kDWarps * 32, 2) k_batch_front_df(const BTile<
         st.A[a][e] = df_zero();
         st.F[a][e] = df_zero();
       }
-    // input row c (its filter sum is read only at the output columns, the others are discarded)
-    auto fetch = [&](int c, dfl* wn, dfl* wp, dfl* an, dfl* fr) {
+    // input row c, loaded one clock ahead (its filter sum is read only at the output columns, the
+    // others are discarded); the FP64 initial state and forcing stay raw here and are converted
+    // when the clock uses them, so that no load is waited for one clock early
+    auto fetch = [&](auto fst, int c, dfl* wn, dfl* wp, dfl* an, double* vr, double* fr) {
+      constexpr bool FIRST = decltype(fst)::value;
       const bool rin = (unsigned)c < (unsigned)ny;
       const int64_t gi = gx0 + (int64_t)nx * c;
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const bool in = rin && cin[e];
-        if (first) {
-          wn[e] = (in && vv) ? df_from(__ldg(vv + gi + e)) : df_zero();
-          wp[e] = df_zero();
-          an[e] = df_mul(w0, wn[e]);
+        if (FIRST) {
+          vr[e] = (in && vv) ? __ldg(vv + gi + e) : 0.0;
         } else {   // written by other warps in the previous sweep: coherent loads
           if (in) {
             const float2 a = __ldcg(reinterpret_cast<const float2*>(wcur + gi + e));
@@ -1386,19 +1407,31 @@ __global__ void __launch_bounds__(kDWarps * 32, 2) k_batch_front_df(const BTile<
             an[e] = df_zero();
           }
         }
-        fr[e] = (FORCED && in && fv) ? df_from(__ldg(fv + gi + e)) : df_zero();
+        if (FORCED) fr[e] = (in && fv) ? __ldg(fv + gi + e) : 0.0;
       }
     };
-    dfl nwn[2], nwp[2], nan[2], nfr[2];
-    fetch(c0, nwn, nwp, nan, nfr);
+    dfl nwn[2], nwp[2], nan[2];
+    double nvr[2], nfr[2];
     double part = 0.0;
     int c = c0;
     auto clock = [&](auto ph, auto fst, auto lst) {
       constexpr int PH = decltype(ph)::value;
       constexpr bool FIRST = decltype(fst)::value, LAST = decltype(lst)::value;
-      const dfl wn[2] = {nwn[0], nwn[1]}, wp[2] = {nwp[0], nwp[1]};
-      const dfl an[2] = {nan[0], nan[1]}, fr[2] = {nfr[0], nfr[1]};
-      if (c + 1 <= c1) fetch(c + 1, nwn, nwp, nan, nfr);   // one clock ahead
+      dfl wn[2], wp[2], an[2], fr[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        if (FIRST) {
+          wn[e] = df_from(nvr[e]);
+          wp[e] = df_zero();
+          an[e] = df_mul(w0, wn[e]);
+        } else {
+          wn[e] = nwn[e];
+          wp[e] = nwp[e];
+          an[e] = nan[e];
+        }
+        fr[e] = FORCED ? df_from(nfr[e]) : df_zero();
+      }
+      if (c + 1 <= c1) fetch(fst, c + 1, nwn, nwp, nan, nvr, nfr);   // one clock ahead
       dfl o[2], pv[2];
       dfront_clock<PH, FIRST, FORCED>(st, c, wn, wp, an, fr, wt, fph, coef, bb, ih2x, ih2y, hdt2, cin, ny, o, pv);
       const int y = c - kDK;
@@ -1426,6 +1459,7 @@ __global__ void __launch_bounds__(kDWarps * 32, 2) k_batch_front_df(const BTile<
       ++c;
     };
     auto run = [&](auto fst, auto lst) {
+      fetch(fst, c0, nwn, nwp, nan, nvr, nfr);
       while (c <= c1) {
         clock(std::integral_constant<int, 0>(), fst, lst);
         if (c > c1) break;

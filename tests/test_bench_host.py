@@ -58,11 +58,11 @@ def test_traffic_is_null_once_the_kernel_changes(tmp_path, monkeypatch):
     j = src.index("T acc_c = acc[idx];")
     p.write_text(src[:j] + "T acc_c = acc[idx] * T(1);" + src[j + len("T acc_c = acc[idx];"):])
     assert bench.traffic_for("k_step3d", "fp32") is None
-    assert bench.traffic_for("k_batch_front", "fp32") is not None
+    assert bench.traffic_for("k_step3d2", "fp32") is not None
     # a shared header drops every kernel built from it
     h = root / "paper_2606_31842_b300" / "csrc" / "whv_device.cuh"
     h.write_text(h.read_text() + "\nconstexpr int kEdited = 1;\n")
-    assert bench.traffic_for("k_batch_front", "fp32") is None
+    assert bench.traffic_for("k_step3d2", "fp32") is None
     assert bench.traffic_for("unknown_kernel", "fp32") is None
 
 

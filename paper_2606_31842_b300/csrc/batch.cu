@@ -1205,43 +1205,70 @@ __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(
   }
 }
 
-// ------------------------------------------------------------------ 2-D, double-float, wavefront
+// ------------------------------------------------------------------ 2-D wavefront, two columns per lane
 // The double-float residual wave solves of the FP64 correction (2-D, second order, c = 1; forced
-// or not) in the wavefront form of k_batch_front: a work item is a strip of 64 columns (56 output
-// columns, KD = 4 on each side halo) and SD rows, ONE WARP advances it KD time levels in a single
-// pass down the rows with the levels' rows in register rings; lane l holds columns 2l, 2l + 1 as
-// hi/lo pairs, x neighbours of its outer columns by shuffles.  Input rows (W^n, W^{n-1}, the
-// filter sums; W^0 = v in the first sweep) and the forcing rows are read straight from global
-// memory one clock ahead; the forcing of the rows in flight is kept in a register ring.  No
-// shared memory and no block-wide barrier; a strip of sweep j waits only for its problem's sweep
-// j - 1 (per-problem completion counters).  The updates are the double-float operations of
-// k_batch_block2d_df in the same order (bitwise equal results):
+// or not), and the forced FP32 wave solve of b, in the wavefront form of k_batch_front: a work item
+// is a strip of 64 columns (64 - 2K output columns, K on each side halo) and kDS rows, ONE WARP
+// advances it K time levels in a single pass down the rows with the levels' rows in register
+// rings; lane l holds columns 2l, 2l + 1 (T = dfl: hi/lo pairs), x neighbours of its outer columns
+// by shuffles.  Input rows (W^n, W^{n-1}, the filter sums; W^0 = v in the first sweep) and the
+// forcing rows are read straight from global memory one clock ahead (FP64 values raw, converted
+// when used); the forcing of the rows in flight is kept in a register ring.  No shared memory and
+// no block-wide barrier; a strip of sweep j waits only for its problem's sweep j - 1 (per-problem
+// completion counters).  The updates are those of the staged kernels in the same order (bitwise
+// equal results): T = dfl the double-float operations of k_batch_block2d_df,
 //   Taylor start  W^1 = W^0 + (dt^2 / 2) (sum_m ih2_m ((W_- + W_+) - 2 W^0) - f)
 //   step          df_leapfrog: b W^n - W^{n-1} + a_x (W_l + W_r) + a_y (W_d + W_u) - fph_n f
 //   filter        acc = w_0 W^0, then df_fma_acc(acc, w_{n+1}, W^{n+1})
-constexpr int kDK = 4;                 // time levels per sweep
-constexpr int kDTW = 64 - 2 * kDK;     // output columns of a strip (56)
+// T = float the FP32 operations of k_batch_block2d,
+//   Taylor start  W^1 = fma(dt^2 / 2, L W^0, W^0), then fma(-(dt^2 / 2) cos(omega_hat t^0), f, .)
+//   step          fma(a_y, W_d + W_u, fma(a_x, W_l + W_r, fma(b, W^n, -W^{n-1}))),
+//                 then fma(-dt^2 cos(omega_hat t^n), f, .)
+//   filter        acc = w_0 W^0, then fma(w_{n+1}, W^{n+1}, acc)
+constexpr int kDK = 4;                 // time levels per sweep of the double-float roles
 constexpr int kDS = 128;               // output rows of a work item
 constexpr int kDWarps = 4;             // warps per CTA
+template <int K>
+__host__ __device__ constexpr int wf_tw() { return 64 - 2 * K; }   // output columns of a strip
 
-struct DfFront {         // the registers of one lane (two columns)
-  dfl L[kDK + 1][3][2];  // level t - 1 at index t: L[0] = W^{n-1}, L[1] = W^n, L[t + 1] = level t
-  dfl A[kDK + 1][2];     // filter sums of the rows in flight: A[t] is row c - t at clock c
-  dfl F[kDK + 1][2];     // forcing of the rows in flight: F[t] is row c - t
+template <typename T, int K>
+struct WFront {          // the registers of one lane (two columns)
+  T L[K + 1][3][2];      // level t - 1 at index t: L[0] = W^{n-1}, L[1] = W^n, L[t + 1] = level t
+  T A[K + 1][2];         // filter sums of the rows in flight: A[t] is row c - t at clock c
+  T F[K + 1][2];         // forcing of the rows in flight: F[t] is row c - t
 };
 
-__device__ __forceinline__ dfl df_shfl_up(dfl a) {
+__device__ __forceinline__ dfl wf_shfl_up(dfl a) {
   return {__shfl_up_sync(0xffffffffu, a.hi, 1), __shfl_up_sync(0xffffffffu, a.lo, 1)};
 }
-__device__ __forceinline__ dfl df_shfl_down(dfl a) {
+__device__ __forceinline__ dfl wf_shfl_down(dfl a) {
   return {__shfl_down_sync(0xffffffffu, a.hi, 1), __shfl_down_sync(0xffffffffu, a.lo, 1)};
 }
+__device__ __forceinline__ float wf_shfl_up(float a) { return __shfl_up_sync(0xffffffffu, a, 1); }
+__device__ __forceinline__ float wf_shfl_down(float a) { return __shfl_down_sync(0xffffffffu, a, 1); }
+template <typename T>
+__device__ __forceinline__ T wf_zero() {
+  if constexpr (std::is_same<T, dfl>::value) return dfl{0.0f, 0.0f};
+  else return 0.0f;
+}
+template <typename T>
+__device__ __forceinline__ T wf_from(double x) {
+  if constexpr (std::is_same<T, dfl>::value) return df_from(x);
+  else return (float)x;
+}
+__device__ __forceinline__ double wf_to(dfl a) { return df_to(a); }
+__device__ __forceinline__ double wf_to(float a) { return (double)a; }
 
-template <int PH, bool FIRST, bool FORCED>
-__device__ __forceinline__ void dfront_clock(DfFront& st, int c, const dfl* wn, const dfl* wp, const dfl* an,
-                                             const dfl* fr, const dfl* wt, const dfl* fph, const dfl* coef,
-                                             dfl b, dfl ih2x, dfl ih2y, dfl hdt2, const bool* cin, int ny, dfl* o,
-                                             dfl* pv) {
+template <typename T>
+struct WfCoef {          // per-item constants of the level updates
+  T ax, ay, b, ih2x, ih2y, hdt2;
+};
+
+template <typename T, int K, int PH, bool FIRST, bool FORCED>
+__device__ __forceinline__ void wf_clock(WFront<T, K>& st, int c, const T* wn, const T* wp, const T* an, const T* fr,
+                                         const T* wt, const T* fph, const WfCoef<T>& q, const bool* cin, int ny,
+                                         T* o, T* pv) {
+  constexpr bool DF = std::is_same<T, dfl>::value;
   constexpr int r3 = PH % 3;
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
@@ -1251,54 +1278,68 @@ __device__ __forceinline__ void dfront_clock(DfFront& st, int c, const dfl* wn, 
     if (FORCED) st.F[0][e] = fr[e];
   }
 #pragma unroll
-  for (int t = 1; t <= kDK; ++t) {
+  for (int t = 1; t <= K; ++t) {
     const int y = c - t;
     const int im = (PH - t - 1 + 30) % 3, i0 = (PH - t + 30) % 3, ip = (PH - t + 1 + 30) % 3;
-    const dfl* up = st.L[t][im];
-    const dfl* mid = st.L[t][i0];
-    const dfl* dn = st.L[t][ip];
-    const dfl l = df_shfl_up(mid[1]);
-    const dfl r = df_shfl_down(mid[0]);
+    const T* up = st.L[t][im];
+    const T* mid = st.L[t][i0];
+    const T* dn = st.L[t][ip];
+    const T l = wf_shfl_up(mid[1]);
+    const T r = wf_shfl_down(mid[0]);
     const bool rin = (unsigned)y < (unsigned)ny;
-    dfl n[2];
+    T n[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      const dfl xl = e == 0 ? l : mid[0];
-      const dfl xr = e == 1 ? r : mid[1];
-      if (FIRST && t == 1) {   // Taylor start
-        const dfl sx = df_add(xl, xr);
-        const dfl sy = df_add(up[e], dn[e]);
-        const dfl c2x = {2.0f * mid[e].hi, 2.0f * mid[e].lo};
-        dfl Lp = df_add(df_zero(), df_mul(ih2x, df_sub(sx, c2x)));
-        Lp = df_add(Lp, df_mul(ih2y, df_sub(sy, c2x)));
-        if (FORCED) Lp = df_sub(Lp, st.F[t][e]);
-        n[e] = df_add(mid[e], df_mul(hdt2, Lp));
+      const T xl = e == 0 ? l : mid[0];
+      const T xr = e == 1 ? r : mid[1];
+      if constexpr (DF) {
+        if (FIRST && t == 1) {   // Taylor start
+          const dfl sx = df_add(xl, xr);
+          const dfl sy = df_add(up[e], dn[e]);
+          const dfl c2x = {2.0f * mid[e].hi, 2.0f * mid[e].lo};
+          dfl Lp = df_add(df_zero(), df_mul(q.ih2x, df_sub(sx, c2x)));
+          Lp = df_add(Lp, df_mul(q.ih2y, df_sub(sy, c2x)));
+          if (FORCED) Lp = df_sub(Lp, st.F[t][e]);
+          n[e] = df_add(mid[e], df_mul(q.hdt2, Lp));
+        } else {
+          const dfl coef[2] = {q.ax, q.ay};
+          const dfs sm[2] = {df_pair_sum(xl, xr), df_pair_sum(up[e], dn[e])};
+          n[e] = df_leapfrog<2, FORCED>(q.b, mid[e], st.L[t - 1][i0][e], coef, sm, fph[t - 1],
+                                        FORCED ? st.F[t][e] : df_zero());
+        }
+        if (!(rin && cin[e])) n[e] = df_zero();
+        st.A[t][e] = df_fma_acc(st.A[t][e], wt[t - 1], n[e]);
       } else {
-        const dfs sm[2] = {df_pair_sum(xl, xr), df_pair_sum(up[e], dn[e])};
-        n[e] = df_leapfrog<2, FORCED>(b, mid[e], st.L[t - 1][i0][e], coef, sm, fph[t - 1],
-                                      FORCED ? st.F[t][e] : df_zero());
+        if (FIRST && t == 1) {   // Taylor start
+          float L0 = fmaf(-2.0f, mid[e], xl + xr) * q.ih2x;
+          L0 = fmaf(fmaf(-2.0f, mid[e], up[e] + dn[e]), q.ih2y, L0);
+          n[e] = fmaf(q.hdt2, L0, mid[e]);
+        } else {
+          n[e] = fmaf(q.ay, up[e] + dn[e], fmaf(q.ax, xl + xr, fmaf(q.b, mid[e], -st.L[t - 1][i0][e])));
+        }
+        if (FORCED) n[e] = fmaf(-fph[t - 1], st.F[t][e], n[e]);
+        n[e] = (rin && cin[e]) ? n[e] : 0.0f;
+        st.A[t][e] = fmaf(wt[t - 1], n[e], st.A[t][e]);
       }
-      if (!(rin && cin[e])) n[e] = df_zero();
-      st.A[t][e] = df_fma_acc(st.A[t][e], wt[t - 1], n[e]);
     }
-    if (t < kDK) {
+    if (t < K) {
 #pragma unroll
       for (int e = 0; e < 2; ++e) st.L[t + 1][i0][e] = n[e];
     } else {
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         o[e] = n[e];
-        pv[e] = st.L[kDK][i0][e];
+        pv[e] = st.L[K][i0][e];
       }
     }
   }
 }
 
 // end of a clock: the rows in flight move on by one
-template <bool FORCED>
-__device__ __forceinline__ void dfront_shift(DfFront& st) {
+template <typename T, int K, bool FORCED>
+__device__ __forceinline__ void wf_shift(WFront<T, K>& st) {
 #pragma unroll
-  for (int t = kDK; t >= 1; --t)
+  for (int t = K; t >= 1; --t)
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       st.A[t][e] = st.A[t - 1][e];
@@ -1306,12 +1347,15 @@ __device__ __forceinline__ void dfront_shift(DfFront& st) {
     }
 }
 
-template <bool FORCED>
-__global__ void __launch_bounds__(kDWarps * 32, 2) k_batch_front_df(const BTile<dfl>* __restrict__ P,
-                                                                    const int* __restrict__ nact, int J,
-                                                                    const int64_t* __restrict__ joff,
-                                                                    unsigned* pcnt, const dfl* __restrict__ wtab,
-                                                                    const dfl* __restrict__ ptab, int* err) {
+// ptab: the double-float roles take the forcing factor dt^2 cos(omega_hat t^n) whole; the FP32
+// role takes cos(omega_hat t^n) and forms the factor as k_batch_block2d does
+template <typename T, int K, bool FORCED>
+__global__ void __launch_bounds__(kDWarps * 32, std::is_same<T, dfl>::value ? 2 : 3)
+    k_batch_front2(const BTile<T>* __restrict__ P, const int* __restrict__ nact, int J,
+                   const int64_t* __restrict__ joff, unsigned* pcnt, const T* __restrict__ wtab,
+                   const T* __restrict__ ptab, int* err) {
+  constexpr bool DF = std::is_same<T, dfl>::value;
+  constexpr int TW = wf_tw<K>();
   __shared__ int64_t s_tile0[kBatchMaxProblems + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int np = nact[0];
@@ -1330,59 +1374,62 @@ __global__ void __launch_bounds__(kDWarps * 32, 2) k_batch_front_df(const BTile<
     const int64_t item = it - joff[j];
     while (s_tile0[p + 1] <= item) ++p;
     const int qi = (j + 1) & 1, qo = j & 1;
-    const BTile<dfl>& B = P[p];
+    const BTile<T>& B = P[p];
     if (B.halt && *B.halt != 0.0) continue;
     const int t = (int)(item - B.tile0);
     const int sx = t % B.tiles_x, sy = t / B.tiles_x;
     const int nx = B.nx, ny = B.ny;
-    const int x0 = sx * kDTW - kDK;
+    const int x0 = sx * TW - K;
     const int Y0 = sy * kDS, Y1 = min(Y0 + kDS, ny);
-    const int c0 = Y0 - kDK, c1 = Y1 - 1 + kDK;   // clocks (input rows) of this item
-    const int n0 = j * kDK;
-    const int kk = min(kDK, B.nt - n0);
+    const int c0 = Y0 - K, c1 = Y1 - 1 + K;   // clocks (input rows) of this item
+    const int n0 = j * K;
+    const int kk = min(K, B.nt - n0);
     const bool first = j == 0, last = n0 + kk == B.nt;
     if (!first) {   // every strip of this problem's previous sweep is done
       bool ok = true;
       if (lane == 0) ok = wait_count(pcnt + p, (unsigned)(j * B.ntiles), err);
       if (!__shfl_sync(0xffffffffu, ok, 0)) return;
     }
-    dfl wt[kDK], fph[kDK];
+    T wt[K], fph[K];
 #pragma unroll
-    for (int s = 0; s < kDK; ++s) {   // the tables carry kDK zero entries past every problem's nt
+    for (int s = 0; s < K; ++s) {   // the tables carry K zero entries past every problem's nt
       wt[s] = wtab[B.wofs + n0 + 1 + s];
-      fph[s] = FORCED ? ptab[B.wofs + n0 + s] : df_zero();
+      if constexpr (DF) fph[s] = FORCED ? ptab[B.wofs + n0 + s] : df_zero();
+      else fph[s] = FORCED ? (n0 + s > 0 ? B.dt2 : 0.5f * B.dt2) * ptab[B.wofs + n0 + s] : 0.0f;
     }
-    const dfl w0 = first ? wtab[B.wofs] : df_zero();
+    const T w0 = first ? wtab[B.wofs] : wf_zero<T>();
     const int gx0 = x0 + 2 * lane;
     const bool cin[2] = {gx0 >= 0 && gx0 < nx, gx0 + 1 >= 0 && gx0 + 1 < nx};
-    const bool outc = 2 * lane >= kDK && 2 * lane < 64 - kDK && gx0 < nx;   // output columns
-    const dfl coef[2] = {B.ax, B.ay};
-    const dfl bb = B.b, ih2x = B.ih2x, ih2y = B.ih2y, hdt2 = {0.5f * B.dt2.hi, 0.5f * B.dt2.lo};
+    const bool outc = 2 * lane >= K && 2 * lane < 64 - K && gx0 < nx;   // output columns
+    WfCoef<T> q;
+    q.ax = B.ax; q.ay = B.ay; q.b = B.b; q.ih2x = B.ih2x; q.ih2y = B.ih2y;
+    if constexpr (DF) q.hdt2 = dfl{0.5f * B.dt2.hi, 0.5f * B.dt2.lo};
+    else q.hdt2 = 0.5f * B.dt2;
     // the descriptor's fields in registers (the stores below could otherwise alias it)
-    const dfl* const wcur = B.w[2 * qi + 1];
-    const dfl* const wprv = B.w[2 * qi];
-    dfl* const wout1 = B.w[2 * qo + 1];
-    dfl* const wout0 = B.w[2 * qo];
-    dfl* const accp = B.acc;
+    const T* const wcur = B.w[2 * qi + 1];
+    const T* const wprv = B.w[2 * qi];
+    T* const wout1 = B.w[2 * qo + 1];
+    T* const wout0 = B.w[2 * qo];
+    T* const accp = B.acc;
     const double* const vv = B.v;
     const double* const fv = B.f;
     const double* const mwp = B.mw;
     double* const outp = B.out;
     const int epi = B.epi;
-    DfFront st;
+    WFront<T, K> st;
 #pragma unroll
-    for (int a = 0; a < kDK + 1; ++a)
+    for (int a = 0; a < K + 1; ++a)
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
 #pragma unroll
-        for (int r = 0; r < 3; ++r) st.L[a][r][e] = df_zero();
-        st.A[a][e] = df_zero();
-        st.F[a][e] = df_zero();
+        for (int r = 0; r < 3; ++r) st.L[a][r][e] = wf_zero<T>();
+        st.A[a][e] = wf_zero<T>();
+        st.F[a][e] = wf_zero<T>();
       }
     // input row c, loaded one clock ahead (its filter sum is read only at the output columns, the
     // others are discarded); the FP64 initial state and forcing stay raw here and are converted
     // when the clock uses them, so that no load is waited for one clock early
-    auto fetch = [&](auto fst, int c, dfl* wn, dfl* wp, dfl* an, double* vr, double* fr) {
+    auto fetch = [&](auto fst, int c, T* wn, T* wp, T* an, double* vr, double* fr) {
       constexpr bool FIRST = decltype(fst)::value;
       const bool rin = (unsigned)c < (unsigned)ny;
       const int64_t gi = gx0 + (int64_t)nx * c;
@@ -1392,70 +1439,77 @@ __global__ void __launch_bounds__(kDWarps * 32, 2) k_batch_front_df(const BTile<
         if (FIRST) {
           vr[e] = (in && vv) ? __ldg(vv + gi + e) : 0.0;
         } else {   // written by other warps in the previous sweep: coherent loads
-          if (in) {
-            const float2 a = __ldcg(reinterpret_cast<const float2*>(wcur + gi + e));
-            const float2 b2 = __ldcg(reinterpret_cast<const float2*>(wprv + gi + e));
-            wn[e] = dfl{a.x, a.y};
-            wp[e] = dfl{b2.x, b2.y};
+          if constexpr (DF) {
+            if (in) {
+              const float2 a = __ldcg(reinterpret_cast<const float2*>(wcur + gi + e));
+              const float2 b2 = __ldcg(reinterpret_cast<const float2*>(wprv + gi + e));
+              wn[e] = dfl{a.x, a.y};
+              wp[e] = dfl{b2.x, b2.y};
+            } else {
+              wn[e] = wp[e] = df_zero();
+            }
+            if (in && outc) {
+              const float2 a = __ldcg(reinterpret_cast<const float2*>(accp + gi + e));
+              an[e] = dfl{a.x, a.y};
+            } else {
+              an[e] = df_zero();
+            }
           } else {
-            wn[e] = wp[e] = df_zero();
-          }
-          if (in && outc) {
-            const float2 a = __ldcg(reinterpret_cast<const float2*>(accp + gi + e));
-            an[e] = dfl{a.x, a.y};
-          } else {
-            an[e] = df_zero();
+            wn[e] = in ? __ldcg(wcur + gi + e) : 0.0f;
+            wp[e] = in ? __ldcg(wprv + gi + e) : 0.0f;
+            an[e] = (in && outc) ? __ldcg(accp + gi + e) : 0.0f;
           }
         }
         if (FORCED) fr[e] = (in && fv) ? __ldg(fv + gi + e) : 0.0;
       }
     };
-    dfl nwn[2], nwp[2], nan[2];
+    T nwn[2], nwp[2], nan[2];
     double nvr[2], nfr[2];
     double part = 0.0;
     int c = c0;
     auto clock = [&](auto ph, auto fst, auto lst) {
       constexpr int PH = decltype(ph)::value;
       constexpr bool FIRST = decltype(fst)::value, LAST = decltype(lst)::value;
-      dfl wn[2], wp[2], an[2], fr[2];
+      T wn[2], wp[2], an[2], fr[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         if (FIRST) {
-          wn[e] = df_from(nvr[e]);
-          wp[e] = df_zero();
-          an[e] = df_mul(w0, wn[e]);
+          wn[e] = wf_from<T>(nvr[e]);
+          wp[e] = wf_zero<T>();
+          if constexpr (DF) an[e] = df_mul(w0, wn[e]);
+          else an[e] = w0 * wn[e];
         } else {
           wn[e] = nwn[e];
           wp[e] = nwp[e];
           an[e] = nan[e];
         }
-        fr[e] = FORCED ? df_from(nfr[e]) : df_zero();
+        fr[e] = FORCED ? wf_from<T>(nfr[e]) : wf_zero<T>();
       }
       if (c + 1 <= c1) fetch(fst, c + 1, nwn, nwp, nan, nvr, nfr);   // one clock ahead
-      dfl o[2], pv[2];
-      dfront_clock<PH, FIRST, FORCED>(st, c, wn, wp, an, fr, wt, fph, coef, bb, ih2x, ih2y, hdt2, cin, ny, o, pv);
-      const int y = c - kDK;
+      T o[2], pv[2];
+      wf_clock<T, K, PH, FIRST, FORCED>(st, c, wn, wp, an, fr, wt, fph, q, cin, ny, o, pv);
+      const int y = c - K;
       if (y >= Y0 && y < Y1 && outc) {
         const int64_t gi = gx0 + (int64_t)nx * y;
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           if (gx0 + e >= nx) break;
-          const dfl a = st.A[kDK][e];
+          const T a = st.A[K][e];
           if (!LAST) {
             wout1[gi + e] = o[e];
             wout0[gi + e] = pv[e];
             accp[gi + e] = a;
           } else if (epi == 0) {
-            outp[gi + e] = df_to(a);
+            outp[gi + e] = wf_to(a);
           } else {
             const double vi = __ldg(vv + gi + e);
-            const double ov = vi - df_to(a);
+            const double ov = vi - wf_to(a);
             outp[gi + e] = ov;
             part = fma(mwp ? vi * __ldg(mwp + gi + e) : vi, ov, part);
           }
         }
       }
-      dfront_shift<FORCED>(st);
+      wf_shift<T, K, FORCED>(st);
       ++c;
     };
     auto run = [&](auto fst, auto lst) {
@@ -2041,13 +2095,13 @@ constexpr int kBDfK = 4;   // sub-steps per sweep of the double-float roles
 // double-float pairs in the same 8-byte buffers, 2-D second order with c = 1 only).
 // Problems are ordered by their number of sweeps (descending), so the active problems of sweep j
 // are a prefix.
-// ------------------------------------------------------------------ double-float wavefront role (host)
-template <bool FORCED>
-static cudaError_t launch_front_df(cudaStream_t st, const Wave& w, unsigned* bar, int* err) {
+// ------------------------------------------------------------------ two-column wavefront roles (host)
+template <typename T, int K, bool FORCED>
+static cudaError_t launch_front2(cudaStream_t st, const Wave& w, unsigned* bar, int* err) {
   (void)bar;   // no grid barrier: per-problem completion counters, zeroed before every launch
-  const BTile<dfl>* P = (const BTile<dfl>*)w.desc;
-  const dfl* wt = (const dfl*)w.wtab;
-  const dfl* ph = (const dfl*)w.ptab;
+  const BTile<T>* P = (const BTile<T>*)w.desc;
+  const T* wt = (const T*)w.wtab;
+  const T* ph = (const T*)w.ptab;
   int J = w.J;
   const int* na = w.nact;
   const int64_t* jo = w.joff;
@@ -2055,14 +2109,18 @@ static cudaError_t launch_front_df(cudaStream_t st, const Wave& w, unsigned* bar
   const cudaError_t e = cudaMemsetAsync(w.pcnt, 0, w.np * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&P, (void*)&na, (void*)&J, (void*)&jo, (void*)&pc, (void*)&wt, (void*)&ph, (void*)&err};
-  return cudaLaunchCooperativeKernel((const void*)k_batch_front_df<FORCED>, dim3(w.nblocks), dim3(kDWarps * 32), args,
-                                     0, st);
+  return cudaLaunchCooperativeKernel((const void*)k_batch_front2<T, K, FORCED>, dim3(w.nblocks), dim3(kDWarps * 32),
+                                     args, 0, st);
 }
 
-// descriptor tables of the double-float wavefront role (strips of 64 columns x kDS rows)
-static whv_status make_wave_front_df(BatchCtx& c, const RoleIO& io, bool forced, Wave* out) {
+// descriptor tables of a two-column wavefront role (strips of 64 columns x kDS rows, K levels per
+// sweep): T = dfl the double-float roles in the grids' 8-byte buffers, T = float the FP32 roles in
+// their FP32 buffers
+template <typename T, int K>
+static whv_status make_wave_front2(BatchCtx& c, const RoleIO& io, bool forced, Wave* out) {
+  constexpr bool DF = std::is_same<T, dfl>::value;
+  constexpr int TW = wf_tw<K>();
   const int np = c.np;
-  const int K = kDK;
   Wave w;
   w.K = K;
   std::vector<int> order(np), nsw(np);
@@ -2070,41 +2128,42 @@ static whv_status make_wave_front_df(BatchCtx& c, const RoleIO& io, bool forced,
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nsw[a] > nsw[b]; });
   w.J = nsw[order[0]];
-  std::vector<dfl> wtab, ptab;
+  std::vector<T> wtab, ptab;
   std::vector<BFin> fin(np);
-  std::vector<BTile<dfl>> d(np);
+  std::vector<BTile<T>> d(np);
   int64_t tile0 = 0;
   for (int k = 0; k < np; ++k) {
     const int p = order[k];
     whv_grid g = c.grids[p];
     const TimeGridH& tg = c.tgs[p];
-    void* const* bufs = g->wbuf64;
-    if (!g->acc64 || !bufs[0]) return fail(c.g0, WHV_ERR_INVALID, "batched: stepping buffers missing");
+    void* const* bufs = DF ? g->wbuf64 : g->wbuf;
+    void* const accb = DF ? g->acc64 : g->acc;
+    if (!accb || !bufs[0]) return fail(c.g0, WHV_ERR_INVALID, "batched: stepping buffers missing");
     const int wofs = (int)wtab.size();
     for (int n = 0; n <= tg.nt; ++n) {
-      wtab.push_back(df_from(tg.weight[n]));
-      ptab.push_back(df_from(tg.dt * tg.dt * tg.phase[n]));   // the forcing factor dt^2 cos(omega_hat t^n)
+      wtab.push_back(cvt<T>(tg.weight[n]));
+      ptab.push_back(cvt<T>(DF ? tg.dt * tg.dt * tg.phase[n] : tg.phase[n]));
     }
     for (int n = 0; n < K; ++n) {   // the last sweep may read past the problem's nt
-      wtab.push_back(dfl{0.0f, 0.0f});
-      ptab.push_back(dfl{0.0f, 0.0f});
+      wtab.push_back(cvt<T>(0.0));
+      ptab.push_back(cvt<T>(0.0));
     }
     const double h2x = g->h[0] * g->h[0], h2y = g->h[1] * g->h[1];
-    BTile<dfl> B{};
-    for (int m = 0; m < 4; ++m) B.w[m] = (dfl*)bufs[m];
-    B.acc = (dfl*)g->acc64;
+    BTile<T> B{};
+    for (int m = 0; m < 4; ++m) B.w[m] = (T*)bufs[m];
+    B.acc = (T*)accb;
     B.v = io.v[p]; B.f = io.f[p]; B.out = io.out[p];
     B.c2 = nullptr; B.mw = g->mw; B.partials = chan(g, CH_STEP);
     B.halt = io.halt ? g->scal + S_HALT : nullptr;
     B.nx = g->n[0]; B.ny = g->n[1]; B.nt = tg.nt;
-    B.tiles_x = (g->n[0] + kDTW - 1) / kDTW;
+    B.tiles_x = (g->n[0] + TW - 1) / TW;
     B.ntiles = B.tiles_x * ((g->n[1] + kDS - 1) / kDS);
     B.epi = io.epi; B.wofs = wofs;
-    B.ih2x = df_from(1.0 / h2x);
-    B.ih2y = df_from(1.0 / h2y);
-    B.dt2 = df_from(tg.dt * tg.dt);
+    B.ih2x = cvt<T>(1.0 / h2x);
+    B.ih2y = cvt<T>(1.0 / h2y);
+    B.dt2 = cvt<T>(tg.dt * tg.dt);
     const double ax = tg.dt * tg.dt / h2x, ay = tg.dt * tg.dt / h2y;
-    B.ax = df_from(ax); B.ay = df_from(ay); B.b = df_from(2.0 - 2.0 * (ax + ay));
+    B.ax = cvt<T>(ax); B.ay = cvt<T>(ay); B.b = cvt<T>(2.0 - 2.0 * (ax + ay));
     B.tile0 = tile0;
     if (io.epi == 1 && B.ntiles > chan_cap(g, CH_STEP))
       return fail(c.g0, WHV_ERR_INVALID, "batched: grid too large for its reduction channel");
@@ -2120,27 +2179,27 @@ static whv_status make_wave_front_df(BatchCtx& c, const RoleIO& io, bool forced,
   }
   std::vector<int64_t> joff(w.J + 1, 0);   // strips of sweep j: those of its active problems
   for (int j = 0; j < w.J; ++j) joff[j + 1] = joff[j] + (nact[j] < np ? d[nact[j]].tile0 : tile0);
-  B_CUDA(c.g0, c.alloc(&w.desc, np * sizeof(BTile<dfl>)));
+  B_CUDA(c.g0, c.alloc(&w.desc, np * sizeof(BTile<T>)));
   B_CUDA(c.g0, c.alloc(&w.nact, w.J * sizeof(int)));
   B_CUDA(c.g0, c.alloc(&w.joff, (w.J + 1) * sizeof(int64_t)));
   B_CUDA(c.g0, c.alloc(&w.pcnt, np * sizeof(unsigned)));
-  B_CUDA(c.g0, c.alloc(&w.wtab, wtab.size() * sizeof(dfl)));
-  B_CUDA(c.g0, c.alloc(&w.ptab, ptab.size() * sizeof(dfl)));
+  B_CUDA(c.g0, c.alloc(&w.wtab, wtab.size() * sizeof(T)));
+  B_CUDA(c.g0, c.alloc(&w.ptab, ptab.size() * sizeof(T)));
   B_CUDA(c.g0, c.alloc(&w.fin, np * sizeof(BFin)));
-  B_CUDA(c.g0, cudaMemcpy(w.desc, d.data(), np * sizeof(BTile<dfl>), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.desc, d.data(), np * sizeof(BTile<T>), cudaMemcpyHostToDevice));
   B_CUDA(c.g0, cudaMemcpy(w.nact, nact.data(), w.J * sizeof(int), cudaMemcpyHostToDevice));
   B_CUDA(c.g0, cudaMemcpy(w.joff, joff.data(), (w.J + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
-  B_CUDA(c.g0, cudaMemcpy(w.wtab, wtab.data(), wtab.size() * sizeof(dfl), cudaMemcpyHostToDevice));
-  B_CUDA(c.g0, cudaMemcpy(w.ptab, ptab.data(), ptab.size() * sizeof(dfl), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.wtab, wtab.data(), wtab.size() * sizeof(T), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.ptab, ptab.data(), ptab.size() * sizeof(T), cudaMemcpyHostToDevice));
   B_CUDA(c.g0, cudaMemcpy(w.fin, fin.data(), np * sizeof(BFin), cudaMemcpyHostToDevice));
   w.np = np;
   int per_sm = 0;
   if (forced) {
-    w.launch = &launch_front_df<true>;
-    B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_front_df<true>, kDWarps * 32, 0));
+    w.launch = &launch_front2<T, K, true>;
+    B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_front2<T, K, true>, kDWarps * 32, 0));
   } else {
-    w.launch = &launch_front_df<false>;
-    B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_front_df<false>, kDWarps * 32, 0));
+    w.launch = &launch_front2<T, K, false>;
+    B_CUDA(c.g0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_front2<T, K, false>, kDWarps * 32, 0));
   }
   if (per_sm < 1) return fail(c.g0, WHV_ERR_INVALID, "batched: kernel cannot be resident on an SM");
   w.smem = 0;
@@ -2160,11 +2219,13 @@ static whv_status make_wave(BatchCtx& c, const RoleIO& io, Wave* out) {
   static_assert(!DF || (DIM == 2 && ORDER == 2 && !VARC), "double-float roles: 2-D, second order, c = 1");
   Wave w;
   w.K = DF ? kBDfK : (blocked ? batch_k(c.g0, fp64) : 1);
-  if constexpr (std::is_same<T, float>::value && DIM == 2 && ORDER == 2 && !VARC)
+  if constexpr (std::is_same<T, float>::value && DIM == 2 && ORDER == 2 && !VARC) {
     if (front_role(w.K, forced)) return make_wave_front(c, io, out);
     else if (tma_role(w.K, forced)) return make_wave_tma(c, io, w.K, out);
+    else if (forced && w.K == kFK && tma_env() >= 3) return make_wave_front2<float, kFK>(c, io, true, out);
+  }
   if constexpr (DF)
-    if (tma_env() >= 3) return make_wave_front_df(c, io, forced, out);
+    if (tma_env() >= 3) return make_wave_front2<dfl, kDK>(c, io, forced, out);
   std::vector<int> order(np), nsw(np);
   for (int p = 0; p < np; ++p) nsw[p] = (c.tgs[p].nt + w.K - 1) / w.K;
   std::iota(order.begin(), order.end(), 0);

@@ -266,3 +266,33 @@ def test_tma_fed_sweeps_equal_staged_sweeps_bitwise(k_tma, k_ref):
         assert IND.relmax(a.cpu().numpy(), ref.cpu().numpy()) < 2e-5
     for g in grids:
         g.close()
+
+
+def test_forced_fp32_wavefront_equals_staged_sweeps_bitwise():
+    """Forced FP32 batched wave solves (the b solve of the FP64 correction): at k = 8 the
+    two-column wavefront kernel (eight levels per pass, the forcing of the rows in flight in a
+    register ring) and k_batch_block2d at k = 6 run the same FP32 operations, so their outputs are
+    equal bit for bit, with and without a forcing and with and without an initial state; both match
+    the single-grid FP32 wave solve, and the forced FP64 batched solve matches the oracle."""
+    stream = torch.cuda.Stream()
+    grids, params, vs, fs = [], [], [], []
+    for i, (n, om, seed) in enumerate(SPEC):
+        grids.append(whv.Grid((n, n), precision=whv.WHV_FP32_STEP, stream=stream))
+        params.append(whv.make_params(om))
+        vs.append(dev(I.random_field((n - 2, n - 2), 80 + i)) if i % 3 != 1 else
+                  torch.zeros((n - 2) * (n - 2), dtype=torch.float64, device="cuda"))
+        fs.append(dev(I.gaussian((n, n), I.source_centers(90 + i, 1, 2)[0], 0.05, om ** 2))
+                  if i % 3 != 2 else None)
+    assert sum(tiles((n, n), 8) for n, _, _ in SPEC) > 2 * sms()
+    out = {}
+    for k in (8, 6):
+        grids[0].whv_set_steps_per_sweep(k)
+        out[k] = whv.whv_apply_pi_batched(grids, params, vs, fs)
+    for i, ((n, om, _), a, b) in enumerate(zip(SPEC, out[8], out[6])):
+        assert torch.equal(a, b), (n, om)
+        single = whv.Grid((n, n), precision=whv.WHV_FP32_STEP)
+        ref = single.whv_apply_pi(params[i], vs[i], fs[i])
+        single.close()
+        assert IND.relmax(a.cpu().numpy(), ref.cpu().numpy()) < 2e-5
+    for g in grids:
+        g.close()

@@ -8,6 +8,12 @@
 //    nodes plus a halo of width kr, r the stencil radius) and advances it k steps in registers
 //    and shared memory; then all CTAs meet at a grid barrier.  Global traffic is 3 reads and 3
 //    writes per node per k steps (plus the halo) instead of 5 accesses per step.
+//  - 2-D, second order, c = 1 (the default path of the batched squares): wavefront kernels in
+//    which ONE warp advances a strip of columns several time levels in a single pass down the
+//    rows, with the levels' rows in register rings: k_batch_front for the FP32 A p of the CG loop
+//    (k = 8, inputs by TMA), k_batch_front2 for the double-float residual roles (4 levels) and the
+//    forced FP32 b role (8 levels).  A strip waits only for its own problem's previous sweep
+//    (per-problem completion counters) instead of a grid barrier.
 //  - 3-D grids: k_batch_wave sweeps one step at a time (tiles of 32 x 8 nodes per z plane).
 // Problems are sorted by their number of sweeps, so the active ones are a prefix of the list;
 // stopped problems are skipped a whole problem at a time.  The barrier spins with an iteration

@@ -1826,8 +1826,10 @@ static EncodeTiledFn encode_tiled() { return (EncodeTiledFn)tensor_map_encoder()
 
 // The FP32 f = 0 roles of 2-D second-order c = 1 batches: k = 8 runs the wavefront kernel
 // (k_batch_front), k = 4 and 12 the TMA-fed staged kernel with two rows of cells per thread, other
-// k k_batch_block2d.  WHV_BATCH_TMA in the environment is a diagnostic switch (0: k_batch_block2d
-// for every k; 1 or 2: the staged TMA-fed kernel with one or two rows per thread for k = 4, 8, 12):
+// k k_batch_block2d; the forced FP32 role at k = 8 and the double-float roles run the two-column
+// wavefront kernel (k_batch_front2).  WHV_BATCH_TMA in the environment is a diagnostic switch (0:
+// k_batch_block2d / k_batch_block2d_df for every role; 1 or 2: the staged TMA-fed kernel with one
+// or two rows per thread for the f = 0 FP32 roles at k = 4, 8, 12, the staged kernels otherwise):
 // all of them give the same results bit for bit.
 static int tma_env() {
   static const int env = [] { const char* e = getenv("WHV_BATCH_TMA"); return e ? atoi(e) : 3; }();

@@ -606,6 +606,8 @@ struct BTileT {
   int64_t tile0;
   int nx, ny, nt, tiles_x, ntiles, epi, wofs, pitch;
   float ax, ay, b, ih2x, ih2y, dt2;
+  int64_t tile0b;        // wavefront kernel, work items of 2 kFS rows: first item, count
+  int ntilesb;
 };
 
 struct BMaps {           // tensor maps of one problem's pitched buffers
@@ -831,7 +833,8 @@ __global__ void __launch_bounds__(kBThreads / R, R) k_batch_tma(const BTileT* __
 // ------------------------------------------------------------------ 2-D, FP32, wavefront
 // The f = 0 FP32 wave solve of the 5-point stencil with c = 1 (every A p of the batched CG loop)
 // as a wavefront in registers: a work item is a strip of W = 32 C columns (the W - 2K middle ones
-// are its output, K on each side are halo) and S rows of one problem, and ONE WARP advances it K
+// are its output, K on each side are halo) and S rows of one problem (S = kFS or 2 kFS, chosen per
+// launch from its parallel work), and ONE WARP advances it K
 // time levels in a single pass down the rows.  Lane l holds columns C l .. C l + C - 1; at clock
 // c the warp takes input row c (W^n, W^{n-1} and the filter sums, copied by the copy engine into
 // the warp's own shared-memory blocks of FRB rows, two blocks in flight) and computes level t of
@@ -851,7 +854,11 @@ constexpr int kFK = 8;                 // time levels per sweep
 constexpr int kFC = 4;                 // columns per lane
 constexpr int kFW = 32 * kFC;          // strip width
 constexpr int kFTW = kFW - 2 * kFK;    // output columns of a strip
-constexpr int kFS = 128;               // output rows of a work item
+constexpr int kFS = 128;               // output rows of a work item (or 2 kFS, see k_batch_front)
+// a launch takes items of 2 kFS rows (fewer halo rows per output row) when its work, in item
+// sweeps of that height, is at least this many times the number of warps times its longest chain
+// of sweeps (the sweeps of one problem run one after another); else kFS rows, for parallelism
+constexpr double kFBigRatio = 2.0;
 constexpr int kFRB = 8;                // rows per copied block
 constexpr int kFWarps = 4;             // warps per CTA
 constexpr int kFBlockBytes = (kFW + kFW + kFTW) * kFRB * 4;   // W^n, W^{n-1}, filter sums of FRB rows
@@ -996,16 +1003,44 @@ __device__ __forceinline__ bool wait_count(const unsigned* cnt, unsigned target,
 __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(const BTileT* __restrict__ P,
                                                               const BMapsF* __restrict__ M,
                                                               const int* __restrict__ nact, int J,
-                                                              const int64_t* __restrict__ joff, unsigned* pcnt,
-                                                              const float* __restrict__ wtab, int* err) {
+                                                              const int64_t* __restrict__ joff,
+                                                              const int64_t* __restrict__ joffb, int rows_mode,
+                                                              unsigned* pcnt, const float* __restrict__ wtab,
+                                                              int* err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* const base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   __shared__ int64_t s_tile0[kBatchMaxProblems + 1];
   __shared__ __align__(8) uint64_t s_bar[kFWarps][2];
+  __shared__ int s_big;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int np = nact[0];
+  // item height of this launch (rows_mode 0: by the rule at kFBigRatio; 1: kFS; 2: 2 kFS), the
+  // same in every CTA: the active problems' item sweeps at 2 kFS rows against the longest chain
+  if (warp == 0) {
+    bool big = rows_mode == 2;
+    if (rows_mode == 0) {
+      double work = 0.0;
+      int longest = 0;
+      for (int p = lane; p < np; p += 32) {
+        const BTileT& B = P[p];
+        if (B.halt && *B.halt != 0.0) continue;
+        const int sw = (B.nt + kFK - 1) / kFK;
+        work += (double)B.ntilesb * sw;
+        longest = max(longest, sw);
+      }
+      work = warp_sum(work);
+      longest = __reduce_max_sync(0xffffffffu, longest);
+      big = work >= kFBigRatio * (double)longest * (double)gridDim.x * kFWarps;
+    }
+    if (lane == 0) s_big = big ? 1 : 0;
+  }
+  __syncthreads();
+  const bool big = s_big != 0;
+  const int64_t* const jo = big ? joffb : joff;
+  const int rows = big ? 2 * kFS : kFS;
   for (int p = threadIdx.x; p <= np; p += blockDim.x)
-    s_tile0[p] = p < np ? P[p].tile0 : P[np - 1].tile0 + P[np - 1].ntiles;
+    s_tile0[p] = p < np ? (big ? P[p].tile0b : P[p].tile0)
+                        : (big ? P[np - 1].tile0b + P[np - 1].ntilesb : P[np - 1].tile0 + P[np - 1].ntiles);
   if (lane == 0) {
     mbar_init(&s_bar[warp][0], 1);
     mbar_init(&s_bar[warp][1], 1);
@@ -1020,24 +1055,25 @@ __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(
   // work items of all sweeps in one sequence (sweep by sweep, the active problems' strips in
   // order), taken round-robin by the warps; a strip of sweep j waits only for the strips of its
   // own problem's sweep j - 1 (per-problem completion counters), not for the whole grid
-  const int64_t nitems = joff[J];
+  const int64_t nitems = jo[J];
   int j = 0, p = 0;
   for (int64_t it = gw; it < nitems && !failed; it += G) {
-    while (joff[j + 1] <= it) {
+    while (jo[j + 1] <= it) {
       ++j;
       p = 0;
     }
-    const int64_t item = it - joff[j];
+    const int64_t item = it - jo[j];
     while (s_tile0[p + 1] <= item) ++p;
     const int qi = (j + 1) & 1, qo = j & 1;
     {
       const BTileT& B = P[p];
       if (B.halt && *B.halt != 0.0) continue;
-      const int t = (int)(item - B.tile0);
+      const int t = (int)(item - (big ? B.tile0b : B.tile0));
+      const int ntl = big ? B.ntilesb : B.ntiles;
       const int sx = t % B.tiles_x, sy = t / B.tiles_x;
       const int nx = B.nx, ny = B.ny;
       const int x0 = sx * kFTW - kFK;
-      const int Y0 = sy * kFS, Y1 = min(Y0 + kFS, ny);
+      const int Y0 = sy * rows, Y1 = min(Y0 + rows, ny);
       const int c0 = Y0 - kFK, c1 = Y1 - 1 + kFK;       // clocks (input rows) of this item
       const int n0 = j * kFK;
       const int kk = min(kFK, B.nt - n0);
@@ -1077,7 +1113,7 @@ __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(
       if (!first) {   // every strip of this problem's previous sweep is done: its stores, then the copies
         bool ok = true;
         if (lane == 0) {
-          ok = wait_count(pcnt + p, (unsigned)(j * B.ntiles), err);
+          ok = wait_count(pcnt + p, (unsigned)(j * ntl), err);
           if (ok) fence_proxy_async_global();
         }
         if (!__shfl_sync(0xffffffffu, ok, 0)) {
@@ -1192,7 +1228,11 @@ __global__ void __launch_bounds__(kFWarps * 32, kFC == 4 ? 2 : 3) k_batch_front(
       }
       if (last && B.epi == 1) {
         part = warp_sum(part);
-        if (lane == 0) B.partials[t] = part;
+        if (lane == 0) {
+          B.partials[t] = part;
+          // the finishing kernel sums B.ntiles partials: taller items leave the rest at zero
+          if (big && B.ntilesb + t < B.ntiles) B.partials[B.ntilesb + t] = 0.0;
+        }
       }
       // publish this strip: its stores to every thread and to the copy engine, then the count
       fence_proxy_async_global();
@@ -1669,6 +1709,8 @@ struct Wave {
   BFin* fin = nullptr;
   int J = 0, K = 1, nblocks = 1;
   int64_t* joff = nullptr;     // wavefront role: first work item of each sweep (J + 1 entries)
+  int64_t* joffb = nullptr;    // ... with work items of 2 kFS rows (k_batch_front)
+  int rows_mode = 0;           // k_batch_front item height: 0 by launch, 1 kFS, 2 2 kFS
   unsigned* pcnt = nullptr;    // ... and per-problem completion counters
   int np = 0;
   size_t smem = 0;
@@ -1989,10 +2031,13 @@ static cudaError_t launch_front(cudaStream_t st, const Wave& w, unsigned* bar, i
   int J = w.J;
   const int* na = w.nact;
   const int64_t* jo = w.joff;
+  const int64_t* job = w.joffb;
+  int rm = w.rows_mode;
   unsigned* pc = w.pcnt;
   const cudaError_t e = cudaMemsetAsync(w.pcnt, 0, w.np * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  void* args[] = {(void*)&P, (void*)&M, (void*)&na, (void*)&J, (void*)&jo, (void*)&pc, (void*)&wt, (void*)&err};
+  void* args[] = {(void*)&P,   (void*)&M,  (void*)&na, (void*)&J,  (void*)&jo,
+                  (void*)&job, (void*)&rm, (void*)&pc, (void*)&wt, (void*)&err};
   return cudaLaunchCooperativeKernel((const void*)k_batch_front, dim3(w.nblocks), dim3(kFWarps * 32), args, w.smem,
                                      st);
 }
@@ -2022,7 +2067,7 @@ static whv_status make_wave_front(BatchCtx& c, const RoleIO& io, Wave* out) {
   std::vector<BFin> fin(np);
   std::vector<BTileT> d(np);
   std::vector<BMapsF> maps(np);
-  int64_t tile0 = 0;
+  int64_t tile0 = 0, tile0b = 0;
   for (int k = 0; k < np; ++k) {
     const int p = order[k];
     whv_grid g = c.grids[p];
@@ -2042,6 +2087,7 @@ static whv_status make_wave_front(BatchCtx& c, const RoleIO& io, Wave* out) {
     B.nx = g->n[0]; B.ny = g->n[1]; B.nt = tg.nt; B.pitch = g->tpitch;
     B.tiles_x = (g->n[0] + kFTW - 1) / kFTW;
     B.ntiles = B.tiles_x * ((g->n[1] + kFS - 1) / kFS);
+    B.ntilesb = B.tiles_x * ((g->n[1] + 2 * kFS - 1) / (2 * kFS));
     B.epi = io.epi; B.wofs = wofs;
     B.ih2x = (float)(1.0 / h2x);
     B.ih2y = (float)(1.0 / h2y);
@@ -2049,6 +2095,7 @@ static whv_status make_wave_front(BatchCtx& c, const RoleIO& io, Wave* out) {
     const double ax = tg.dt * tg.dt / h2x, ay = tg.dt * tg.dt / h2y;
     B.ax = (float)ax; B.ay = (float)ay; B.b = (float)(2.0 - 2.0 * (ax + ay));
     B.tile0 = tile0;
+    B.tile0b = tile0b;
     for (int m = 0; m < 4; ++m)
       if (!encode_rows(&maps[k].w[m], g->tw[m], g->n[0], g->n[1], g->tpitch, kFW))
         return fail(c.g0, WHV_ERR_CUDA, "batched: cuTensorMapEncodeTiled failed (state buffers)");
@@ -2059,6 +2106,7 @@ static whv_status make_wave_front(BatchCtx& c, const RoleIO& io, Wave* out) {
     fin[k] = BFin{chan(g, CH_STEP), io.halt ? g->scal + S_HALT : nullptr, g->scal, B.ntiles};
     d[k] = B;
     tile0 += B.ntiles;
+    tile0b += B.ntilesb;
   }
   std::vector<int> nact(w.J);
   for (int j = 0; j < w.J; ++j) {
@@ -2066,12 +2114,25 @@ static whv_status make_wave_front(BatchCtx& c, const RoleIO& io, Wave* out) {
     while (a < np && nsw[order[a]] > j) ++a;
     nact[j] = a;
   }
-  std::vector<int64_t> joff(w.J + 1, 0);   // strips of sweep j: those of its active problems
-  for (int j = 0; j < w.J; ++j) joff[j + 1] = joff[j] + (nact[j] < np ? d[nact[j]].tile0 : tile0);
+  // strips of sweep j: those of its active problems (work items of kFS and of 2 kFS rows)
+  std::vector<int64_t> joff(w.J + 1, 0), joffb(w.J + 1, 0);
+  for (int j = 0; j < w.J; ++j) {
+    joff[j + 1] = joff[j] + (nact[j] < np ? d[nact[j]].tile0 : tile0);
+    joffb[j + 1] = joffb[j] + (nact[j] < np ? d[nact[j]].tile0b : tile0b);
+  }
   B_CUDA(c.g0, c.alloc(&w.joff, (w.J + 1) * sizeof(int64_t)));
+  B_CUDA(c.g0, c.alloc(&w.joffb, (w.J + 1) * sizeof(int64_t)));
   B_CUDA(c.g0, c.alloc(&w.pcnt, np * sizeof(unsigned)));
   B_CUDA(c.g0, cudaMemcpy(w.joff, joff.data(), (w.J + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  B_CUDA(c.g0, cudaMemcpy(w.joffb, joffb.data(), (w.J + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
   w.np = np;
+  // WHV_FRONT_ROWS in the environment fixes the item height (128 or 256 rows; a diagnostic and
+  // test switch: both give the same wave-solve outputs bit for bit)
+  {
+    const char* e = getenv("WHV_FRONT_ROWS");
+    const int r = e ? atoi(e) : 0;
+    w.rows_mode = r == kFS ? 1 : (r == 2 * kFS ? 2 : 0);
+  }
   B_CUDA(c.g0, c.alloc(&w.desc, np * sizeof(BTileT)));
   B_CUDA(c.g0, c.alloc(&w.maps, np * sizeof(BMapsF)));
   B_CUDA(c.g0, c.alloc(&w.nact, w.J * sizeof(int)));

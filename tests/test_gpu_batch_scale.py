@@ -296,3 +296,50 @@ def test_forced_fp32_wavefront_equals_staged_sweeps_bitwise():
         assert IND.relmax(a.cpu().numpy(), ref.cpu().numpy()) < 2e-5
     for g in grids:
         g.close()
+
+
+@pytest.mark.parametrize("rows", [128, 256])
+def test_wavefront_item_heights_equal_staged_sweeps_bitwise(rows, monkeypatch):
+    """FP32 f = 0 batched wave solves at k = 8 with the wavefront kernel's work items fixed at 128
+    or 256 rows (WHV_FRONT_ROWS; by default each launch picks one): both heights run the same
+    operations per node, so the outputs equal k_batch_block2d's at k = 6 bit for bit."""
+    stream = torch.cuda.Stream()
+    grids, params, vs = [], [], []
+    for i, (n, om, seed) in enumerate(SPEC):
+        grids.append(whv.Grid((n, n), precision=whv.WHV_FP32_STEP, stream=stream))
+        params.append(whv.make_params(om))
+        vs.append(dev(I.random_field((n - 2, n - 2), 120 + i)))
+    out = {}
+    monkeypatch.setenv("WHV_FRONT_ROWS", str(rows))
+    for k in (8, 6):
+        grids[0].whv_set_steps_per_sweep(k)
+        out[k] = whv.whv_apply_pi_batched(grids, params, vs)
+    for (n, om, _), a, b in zip(SPEC, out[8], out[6]):
+        assert torch.equal(a, b), (n, om, rows)
+    for g in grids:
+        g.close()
+
+
+def test_fp32_batch_cg_with_tall_wavefront_items(monkeypatch):
+    """Fixed-iteration batched FP32 CG at k = 8 with 256-row wavefront items (the per-item partial
+    sums of p^T A p are grouped differently, the rest of the table zero-filled): iterates agree with
+    the 128-row run to the rounding of those sums and with single-grid FP32 solves."""
+    stream = torch.cuda.Stream()
+    it = 3
+    res = {}
+    for rows in (128, 256):
+        monkeypatch.setenv("WHV_FRONT_ROWS", str(rows))
+        grids, params, fs, spec = build(whv.WHV_FP32_STEP, stream, k=8, maxit=it)
+        us, infos = whv.whv_solve_batched(grids, params, fs)
+        assert all(i["iterations"] == it for i in infos)
+        res[rows] = [u.cpu().numpy() for u in us]
+        for g in grids:
+            g.close()
+    for (n, om, f), a, b, prm in zip(spec, res[128], res[256], params):
+        assert IND.relmax(b, a) < 1e-6, (n, om)
+        s1 = whv.Grid((n, n), precision=whv.WHV_FP32_STEP)
+        s1.whv_set_steps_per_sweep(1)
+        s1.whv_set_deflation_basis(prm, ND, whv.WHV_BASIS_CLOSED_FORM)
+        u1 = s1.whv_solve(prm, dev(f))[0]
+        s1.close()
+        assert IND.relmax(b, u1.cpu().numpy()) < 2e-5

@@ -86,8 +86,9 @@ enum {
   WHV_REFINE_FP64 = 2,        /* iterative refinement on the full system b = Pi_h(0; f): the residual
                                  r = b - A x is formed with FP64 wave solves; each correction is the
                                  modal solve of r's deflated components (W diag(1/mu) W^T M r) plus a
-                                 Krylov solve of the rest in the grid's stepping precision to relative
-                                 tolerance inner_tol; repeated until the FP64 residual meets tol.
+                                 Krylov solve of the rest in the grid's stepping precision (the first
+                                 to relative tolerance inner_tol, later ones to half the remaining
+                                 gap to tol); repeated until the FP64 residual meets tol.
                                  Lets FP32 stepping reach FP64 residuals and corrects approximate
                                  (Lanczos) eigenvectors.  Needs a Krylov method (DCG, AGMRES and
                                  ABICGSTAB use the basis themselves: no modal step); allocates 3 (FP64
@@ -114,7 +115,9 @@ typedef struct {
   int maxit;          /* maximum operator applications in the iteration                          */
   int check_every;    /* test convergence every k iterations (CG/FPI); <= 0 selects 1             */
   int flags;          /* WHV_TRUE_RESIDUAL | WHV_REFINE_FP64 | WHV_RESIDUAL_DF64                  */
-  double inner_tol;   /* WHV_REFINE_FP64: relative tolerance of each correction solve; <= 0: 1e-3 */
+  double inner_tol;   /* WHV_REFINE_FP64: relative tolerance of the first correction solve (later
+                         ones aim at half the remaining gap to tol, at most 10 times tighter);
+                         <= 0: 1e-3 */
 } whv_params;
 
 typedef struct {
@@ -323,7 +326,8 @@ whv_status whv_apply_pi_vjp(whv_grid grid, const whv_params* p, const double* v_
  * every problem has converged or hit its maxit.
  * WHV_REFINE_FP64 in params[].flags (all problems or none) adds FP64 residual correction: b and
  * r = b - A u of the full system come from FP64 batched wave solves, the deflated components of r
- * are solved modally and the rest by the batched CG loop to params[p].inner_tol (default 1e-3),
+ * are solved modally and the rest by the batched CG loop (first pass to params[p].inner_tol, default
+ * 1e-3; later passes to half the remaining gap to tol),
  * repeated until each problem's FP64 residual ||b - A u|| / ||b|| <= tol (reported in
  * true_rel_residual).  Without it infos report the recursive residual of the deflated system and
  * true_rel_residual = -1.  Temporary device memory: the descriptor tables (a few KB); with

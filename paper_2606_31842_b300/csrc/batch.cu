@@ -2892,8 +2892,7 @@ static whv_status batched_solve(BatchCtx& c, const double* const* f_dev, double*
         if (!active[p]) continue;
         const whv_params& P = c.params[p];
         rr[p] = c.grids[p]->scal_host[S_TMP2];
-        // inner tolerance: the requested fraction, but no tighter than the outer target needs
-        const double itol = std::max(P.inner_tol > 0.0 ? P.inner_tol : 1e-3, 0.5 * P.tol / std::max(rel[p], 1e-300));
+        const double itol = correction_tol(P.inner_tol > 0.0 ? P.inner_tol : 1e-3, P.tol, rel[p], pass);
         stop[p] = itol * itol * rr[p];
         mx[p] = P.maxit - total_its[p];
       }

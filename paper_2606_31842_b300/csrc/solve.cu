@@ -806,7 +806,7 @@ static whv_status outer_solve(SolveCtx& c, int method, const whv_params* p, cons
     TRY(fetch_scalars(g));
     const double rr = g->scal_host[S_TMP2];
     InnerResult Ri;
-    const double itol = fp64_res ? std::max(inner_tol, 0.5 * p->tol / std::max(R.rel, 1e-300))
+    const double itol = fp64_res ? correction_tol(inner_tol, p->tol, R.rel, outer)
                                  : p->tol * sqrt(bb / std::max(rr, 1e-300));
     TRY(inner_solve(c, method, p, g->ro, rr, false, itol, p->maxit - its, nullptr, &Ri));
     if (log_on())

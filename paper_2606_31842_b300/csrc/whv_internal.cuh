@@ -148,6 +148,16 @@ namespace whv {
 
 // per-block partial sums of reduction channel ch, and how many blocks it can hold
 inline double* chan(whv_grid g, int ch) { return g->partials + g->chan_off[ch]; }
+
+// Relative tolerance of correction solve number `pass` (0: the first) of the FP64 residual
+// correction, at outer residual rel: the first takes the requested fraction `inner` (a loose pass:
+// its accuracy is limited by the stepping precision, which the later passes correct); later ones
+// aim at half the remaining gap to tol, no tighter than inner / 10.
+inline double correction_tol(double inner, double tol, double rel, int pass) {
+  const double need = 0.5 * tol / (rel > 1e-300 ? rel : 1e-300);
+  const double floor_ = pass == 0 ? inner : 0.1 * inner;
+  return need > floor_ ? need : floor_;
+}
 inline int64_t chan_cap(whv_grid g, int ch) { return g->chan_cap[ch]; }
 
 // ------------------------------------------------------------------ host helpers (core.cu)
